@@ -1,0 +1,246 @@
+/*
+ * hm.h -- C ABI of the GB300 H-matrix boundary-element library.
+ *
+ * Method: Harbrecht & Zaspel, "A scalable H-matrix approach for the solution
+ * of boundary integral equations on multi-GPU clusters" (arXiv 1806.11558):
+ * a Galerkin discretisation of the single-layer Laplace operator
+ * (Sec. 2.1 Example 2.1, Sec. 2.2 Eq. 4) with piecewise-constant elements on
+ * flat triangles, approximated by an H-matrix (Sec. 2.3: Morton-ordered
+ * cluster tree, Algorithm 1 block tree under Eq. 5, dense near field,
+ * adaptive cross approximation of admissible blocks), applied in an
+ * H-matrix-vector product and solved by a Krylov method (Sec. 4.1).
+ *
+ * Conventions shared by every call
+ *  - Pointers named d_* are CUDA device pointers owned by the caller; the
+ *    library never frees them.  Handles (hm_tree, hm_matrix) are owned by the
+ *    library until hm_free.  A matrix keeps a reference to its tree: free the
+ *    matrix before the tree.
+ *  - User vectors are in the caller's original panel order (the index maps
+ *    idx_1 = idx_2 = "the index of the panel" of Sec. 3.2); the Morton
+ *    permutation is applied internally.
+ *  - Calls are ordered on `stream` (NULL = the legacy default stream).  Calls
+ *    that report host-side results (counts, info structs) synchronise the
+ *    stream before returning.
+ *  - Every call returns an hm_status.  On failure no output handle is
+ *    created (*out is set to NULL) and hm_last_error() describes the cause.
+ *    Argument errors are detected before any computation is queued (the
+ *    vertex-index range check of hm_build_tree is a small device kernel that
+ *    runs before anything else).
+ *  - Kernels never trap: every bounded wait that gives up makes the call
+ *    return HM_ETIMEOUT with the device context left usable.
+ */
+#ifndef HM_H
+#define HM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Symbols of the C ABI are the only ones the shared library exports. */
+#if defined(__GNUC__)
+#define HM_API __attribute__((visibility("default")))
+#else
+#define HM_API
+#endif
+
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st *hm_stream_t;
+
+typedef enum {
+    HM_OK = 0,
+    HM_EINVAL = 1,     /* invalid argument (sizes, NULL pointers, ranges)            */
+    HM_ENOMEM = 2,     /* device or host allocation failed                           */
+    HM_ECUDA = 3,      /* a CUDA runtime / driver call failed                        */
+    HM_ENOCONV = 4,    /* the solver reached its iteration limit; best x is returned */
+    HM_ETIMEOUT = 5,   /* a bounded device-side wait gave up                         */
+    HM_EINTERNAL = 6   /* an internal consistency check failed                       */
+} hm_status;
+
+typedef enum { HM_F64 = 0, HM_F32 = 1, HM_BF16 = 2 } hm_dtype;
+
+typedef struct hm_tree hm_tree;     /* opaque, library-owned */
+typedef struct hm_matrix hm_matrix; /* opaque, library-owned */
+
+/* Cluster / block tree parameters (Sec. 2.3).
+ *  eta        : admissibility parameter of Eq. 5, eta >= 0.
+ *  leaf_size  : C_leaf of condition (C3), 1 <= leaf_size <= 254. */
+typedef struct {
+    double eta;
+    int32_t leaf_size;
+} hm_tree_params;
+
+/* Assembly parameters.
+ *  aca_eps      : relative ACA stopping tolerance, > 0.
+ *  aca_kmax     : largest ACA rank per block, 1 <= aca_kmax <= 128.
+ *  ss_order     : Gauss-Legendre order of the regularised touching-pair
+ *                 integrals, 1 <= ss_order <= 16.
+ *  factor_dtype : HM_F64 (FP64 only), or HM_F32 / HM_BF16 to also keep a
+ *                 low-precision copy of the low-rank factors.
+ *  dense_dtype  : HM_F64 (FP64 only) or HM_F32 to also keep an FP32 copy of
+ *                 the dense near field.
+ *  The FP64 master copy is always kept. */
+typedef struct {
+    double aca_eps;
+    int32_t aca_kmax;
+    int32_t ss_order;
+    hm_dtype factor_dtype;
+    hm_dtype dense_dtype;
+} hm_assemble_params;
+
+/* Solver parameters.
+ *  restart    : GMRES restart length m (GMRES(m)), 1 <= restart <= 128.
+ *  max_iter   : total Arnoldi steps allowed (over all restarts / refinements).
+ *  rel_tol    : stop when ||b - H x|| <= rel_tol ||b|| (FP64 residual).
+ *  refine     : 0 = plain FP64 GMRES on the FP64 H-matrix;
+ *               1 = iterative refinement: inner GMRES on the inner_dtype
+ *                   operator (FP64 Krylov vectors, Hessenberg and Givens),
+ *                   outer residual in FP64.
+ *  max_refine : largest number of refinement steps (refine = 1).
+ *  inner_tol  : relative tolerance of each inner solve (refine = 1).
+ *  inner_dtype: HM_F32 or HM_BF16 (factors of that type, dense FP32). */
+typedef struct {
+    int32_t restart;
+    int32_t max_iter;
+    double rel_tol;
+    int32_t refine;
+    int32_t max_refine;
+    double inner_tol;
+    hm_dtype inner_dtype;
+} hm_solve_params;
+
+typedef struct {
+    int32_t status;       /* hm_status of the solve                               */
+    int32_t iters;        /* Arnoldi steps taken (inner steps when refining)       */
+    int32_t restarts;     /* GMRES cycles                                          */
+    int32_t refine_steps; /* outer refinement steps (0 when refine = 0)            */
+    double rel_resid;     /* final ||b - H x|| / ||b|| with the FP64 operator       */
+    double seconds;       /* wall time of the call                                 */
+} hm_solve_info;
+
+typedef struct {
+    int64_t n;              /* panels = unknowns                                  */
+    int64_t n_clusters;     /* clusters of the cluster tree                       */
+    int32_t depth;          /* depth of the cluster tree                          */
+    int32_t max_leaf;       /* largest leaf cluster                               */
+    int64_t n_dense;        /* non-admissible leaves of the block tree            */
+    int64_t n_adm;          /* admissible leaves                                  */
+    int64_t dense_entries;  /* sum of |tau||sigma| over non-admissible leaves     */
+    int64_t adm_rows_cols;  /* sum of |tau| + |sigma| over admissible leaves      */
+    int64_t n_singular;     /* touching panel pairs (shared vertex or edge)       */
+    double seconds;         /* wall time of hm_build_tree                         */
+} hm_tree_info;
+
+typedef struct {
+    int64_t dense_entries;  /* stored FP64 near-field entries                     */
+    int64_t lr_entries;     /* stored FP64 factor entries, sum k_b (|tau|+|sigma|) */
+    int32_t max_rank;
+    int32_t kmax_hit;       /* admissible blocks that stopped at aca_kmax         */
+    double mean_rank;
+    double s_nearfield;     /* device seconds: regular near-field kernel          */
+    double s_singular;      /* device seconds: touching-pair kernel               */
+    double s_aca;           /* device seconds: batched ACA kernel                 */
+    double s_total;         /* wall seconds of hm_assemble                        */
+    int64_t bytes_f64;      /* device bytes of the FP64 matrix data               */
+    int64_t bytes_low;      /* device bytes of the low-precision copies           */
+} hm_matrix_info;
+
+/* Build the Morton-ordered cluster tree and the block cluster tree of a
+ * triangle mesh (Sec. 2.3, Algorithm 1, Eq. 5; Sec. 3.1 "Spatial data
+ * structure").
+ *  d_vertices : [n_vertices][3] doubles (device), vertex coordinates.
+ *  d_tris     : [n_tris][3] int32 (device), vertex indices of each flat
+ *               triangle, each in [0, n_vertices).  n_tris >= 1.
+ *  The nodes X_h are the triangle centroids ((v0 + v1) + v2) / 3; the Morton
+ *  code quantises them on a 2^21 grid over the cube of side max extent; ties
+ *  are ordered by original index; clusters are halved by cardinality
+ *  (|tau_1| = floor(|tau| / 2)) until |tau| <= leaf_size.
+ *  Errors: HM_EINVAL for NULL pointers, n_tris < 1, n_vertices < 3,
+ *  n_tris > 2^28, a vertex index out of range, eta < 0 or leaf_size out of
+ *  [1, 254]. */
+HM_API hm_status hm_build_tree(const double *d_vertices, int64_t n_vertices, const int32_t *d_tris, int64_t n_tris,
+                        const hm_tree_params *params, hm_stream_t stream, hm_tree **out);
+
+/* Assemble the H-matrix approximation of the Galerkin matrix
+ * a_ij = int_Ti int_Tj 1/(4 pi |x - y|) dsigma_y dsigma_x (Eq. 4, Sec. 3.3):
+ * every non-admissible leaf is evaluated densely (7x7 tensor of the
+ * degree-5 7-point rule for disjoint panels, Sauter-Schwab regularised
+ * Gauss-Legendre of order ss_order for panels sharing a vertex or an edge,
+ * Sec. 4.1), every admissible leaf is compressed by ACA with partial pivoting
+ * to relative tolerance aca_eps with entries evaluated on the fly (Sec. 2.3).
+ *  Errors: HM_EINVAL for bad parameters, HM_ENOMEM when the matrix does not
+ *  fit in device memory. */
+HM_API hm_status hm_assemble(const hm_tree *tree, const hm_assemble_params *params, hm_stream_t stream,
+                      hm_matrix **out);
+
+/* Galerkin load vector for point-source Dirichlet data (Sec. 2.2):
+ * f[s][i] = int_Ti g_s dsigma with g_s(x) = 1 / (4 pi |x - p_s|), by the
+ * 7-point rule.
+ *  d_sources : [n_sources][3] doubles (device).
+ *  d_f       : [n_sources][n] doubles (device), original panel order.
+ *  Errors: HM_EINVAL for NULL pointers or n_sources < 1. */
+HM_API hm_status hm_load_vector(const hm_tree *tree, const double *d_sources, int32_t n_sources, double *d_f,
+                         hm_stream_t stream);
+
+/* H-matrix-vector product (Sec. 2.3): y = alpha * op(H) x + beta * y, with
+ * op(H) = H (trans = 0) or H^T (trans = 1), applied column by column to nrhs
+ * right-hand sides stored as [nrhs][n] (original panel order).
+ *  prec : HM_F64 uses the FP64 master; HM_F32 / HM_BF16 use the
+ *         low-precision copies (FP32 accumulation; they must have been
+ *         requested in hm_assemble).
+ *  d_x, d_y : device pointers, must not overlap.
+ *  Errors: HM_EINVAL for NULL pointers, nrhs < 1, a precision whose copy was
+ *  not assembled, or trans not in {0, 1}. */
+HM_API hm_status hm_matvec(const hm_matrix *A, int32_t trans, int32_t nrhs, hm_dtype prec, const double *d_x, double *d_y,
+                    double alpha, double beta, hm_stream_t stream);
+
+/* Solve op(H) x = b with restarted GMRES (Sec. 4.1 solves with a Krylov
+ * method; GMRES(m) with classical Gram-Schmidt applied twice, Givens
+ * rotations and the Hessenberg least-squares problem in FP64), optionally as
+ * FP64 iterative refinement around a low-precision inner operator.
+ *  d_b : [nrhs][n] right-hand sides (device, original order).
+ *  d_x : [nrhs][n] solutions (device); the initial guess is zero.
+ *  info: host pointer, may be NULL; filled for the last right-hand side.
+ *  Returns HM_ENOCONV (with the best x stored) when max_iter is reached. */
+HM_API hm_status hm_solve(const hm_matrix *A, int32_t trans, int32_t nrhs, const double *d_b, double *d_x,
+                   const hm_solve_params *params, hm_stream_t stream, hm_solve_info *info);
+
+/* Frees an hm_tree or hm_matrix handle (NULL is a no-op). */
+HM_API void hm_free(void *handle);
+
+/* Tree introspection (synchronises the stream of the tree). */
+HM_API hm_status hm_tree_get_info(const hm_tree *tree, hm_tree_info *info);
+
+/* d_perm[k] = original index of the panel at Morton position k ([n] int32,
+ * device). */
+HM_API hm_status hm_tree_get_perm(const hm_tree *tree, int32_t *d_perm);
+
+/* Leaves of the block tree as [count][4] int32 (row_begin, row_end,
+ * col_begin, col_end) in Morton positions, written to d_out (device) when
+ * capacity >= count; *count always receives the number of leaves.
+ * dense = 1: non-admissible leaves; dense = 0: admissible leaves. */
+HM_API hm_status hm_tree_get_leaves(const hm_tree *tree, int32_t dense, int32_t *d_out, int64_t capacity, int64_t *count);
+
+HM_API hm_status hm_matrix_get_info(const hm_matrix *A, hm_matrix_info *info);
+
+/* Copies the FP64 H-matrix to host memory in a plain layout, so that it can be
+ * re-applied independently:
+ *  dense leaves b = 0..n_dense-1 in the order of hm_tree_get_leaves(dense=1):
+ *     h_dense[h_dense_off[b] + i * n_b + j] = a(row_begin + i, col_begin + j)
+ *  admissible leaves b = 0..n_adm-1 in the order of hm_tree_get_leaves(dense=0):
+ *     rank h_rank[b]; U_b (m_b x k_b, column-major) at h_uw + h_u_off[b];
+ *     W_b (n_b x k_b, column-major) at h_uw + h_w_off[b]; block ~ U_b W_b^T.
+ * Pass NULL value pointers to query the sizes only: *n_dense_vals and
+ * *n_lr_vals receive the element counts of h_dense and h_uw. */
+HM_API hm_status hm_matrix_export(const hm_matrix *A, double *h_dense, int64_t *h_dense_off, int32_t *h_rank, double *h_uw,
+                           int64_t *h_u_off, int64_t *h_w_off, int64_t *n_dense_vals, int64_t *n_lr_vals);
+
+/* Message of the last failure on the calling thread ("" when none). */
+HM_API const char *hm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HM_H */

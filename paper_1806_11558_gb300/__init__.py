@@ -1,0 +1,235 @@
+"""Python binding of the GB300 H-matrix BEM library (libhm.so, C ABI in include/hm.h).
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  The functions carry the names of the C entry points and take
+CUDA tensors (torch) for the device pointers; the stream is torch's current
+stream unless one is given.  There is no CPU fallback: using the binding
+without a built libhm.so raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhm.so")
+
+HM_OK, HM_EINVAL, HM_ENOMEM, HM_ECUDA, HM_ENOCONV, HM_ETIMEOUT, HM_EINTERNAL = range(7)
+HM_F64, HM_F32, HM_BF16 = 0, 1, 2
+STATUS_NAMES = {0: "HM_OK", 1: "HM_EINVAL", 2: "HM_ENOMEM", 3: "HM_ECUDA", 4: "HM_ENOCONV", 5: "HM_ETIMEOUT",
+                6: "HM_EINTERNAL"}
+
+EXPORTED = ["hm_build_tree", "hm_assemble", "hm_load_vector", "hm_matvec", "hm_solve", "hm_free",
+            "hm_tree_get_info", "hm_tree_get_perm", "hm_tree_get_leaves", "hm_matrix_get_info",
+            "hm_matrix_export", "hm_last_error"]
+
+
+class HMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class TreeParams(ctypes.Structure):
+    _fields_ = [("eta", ctypes.c_double), ("leaf_size", ctypes.c_int32)]
+
+
+class AssembleParams(ctypes.Structure):
+    _fields_ = [("aca_eps", ctypes.c_double), ("aca_kmax", ctypes.c_int32), ("ss_order", ctypes.c_int32),
+                ("factor_dtype", ctypes.c_int), ("dense_dtype", ctypes.c_int)]
+
+
+class SolveParams(ctypes.Structure):
+    _fields_ = [("restart", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("rel_tol", ctypes.c_double),
+                ("refine", ctypes.c_int32), ("max_refine", ctypes.c_int32), ("inner_tol", ctypes.c_double),
+                ("inner_dtype", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("restarts", ctypes.c_int32),
+                ("refine_steps", ctypes.c_int32), ("rel_resid", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+
+class TreeInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("n_clusters", ctypes.c_int64), ("depth", ctypes.c_int32),
+                ("max_leaf", ctypes.c_int32), ("n_dense", ctypes.c_int64), ("n_adm", ctypes.c_int64),
+                ("dense_entries", ctypes.c_int64), ("adm_rows_cols", ctypes.c_int64),
+                ("n_singular", ctypes.c_int64), ("seconds", ctypes.c_double)]
+
+
+class MatrixInfo(ctypes.Structure):
+    _fields_ = [("dense_entries", ctypes.c_int64), ("lr_entries", ctypes.c_int64), ("max_rank", ctypes.c_int32),
+                ("kmax_hit", ctypes.c_int32), ("mean_rank", ctypes.c_double), ("s_nearfield", ctypes.c_double),
+                ("s_singular", ctypes.c_double), ("s_aca", ctypes.c_double), ("s_total", ctypes.c_double),
+                ("bytes_f64", ctypes.c_int64), ("bytes_low", ctypes.c_int64)]
+
+
+def struct_dict(s):
+    return {k: getattr(s, k) for k, _ in s._fields_}
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libhm.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libhm.so is not built (run __graft_entry__.build() or "
+                               "python paper_1806_11558_gb300/build.py)")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I32, I64, D, I = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+        sig = {
+            "hm_build_tree": [P, I64, P, I64, P, P, P],
+            "hm_assemble": [P, P, P, P],
+            "hm_load_vector": [P, P, I32, P, P],
+            "hm_matvec": [P, I32, I32, I, P, P, D, D, P],
+            "hm_solve": [P, I32, I32, P, P, P, P, P],
+            "hm_tree_get_info": [P, P],
+            "hm_tree_get_perm": [P, P],
+            "hm_tree_get_leaves": [P, I32, P, I64, P],
+            "hm_matrix_get_info": [P, P],
+            "hm_matrix_export": [P, P, P, P, P, P, P, P, P],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = I
+        L.hm_free.argtypes = [P]
+        L.hm_free.restype = None
+        L.hm_last_error.argtypes = []
+        L.hm_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def hm_last_error() -> str:
+    return lib().hm_last_error().decode()
+
+
+def _check(status):
+    if status != HM_OK:
+        raise HMError(status, hm_last_error())
+    return status
+
+
+def _stream(stream):
+    if stream is not None:
+        return ctypes.c_void_p(int(stream))
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t, dtype=None):
+    import torch
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError("expected dtype %s, got %s" % (dtype, t.dtype))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def hm_build_tree(vertices, tris, eta=1.5, leaf_size=64, stream=None):
+    """vertices: CUDA float64 [nv, 3]; tris: CUDA int32 [n, 3].  Returns a tree handle."""
+    import torch
+    out = ctypes.c_void_p()
+    prm = TreeParams(float(eta), int(leaf_size))
+    _check(lib().hm_build_tree(_ptr(vertices, torch.float64), vertices.shape[0], _ptr(tris, torch.int32),
+                               tris.shape[0], ctypes.byref(prm), _stream(stream), ctypes.byref(out)))
+    return out
+
+
+def hm_assemble(tree, aca_eps=1e-6, aca_kmax=64, ss_order=8, factor_dtype=HM_F64, dense_dtype=HM_F64, stream=None):
+    out = ctypes.c_void_p()
+    prm = AssembleParams(float(aca_eps), int(aca_kmax), int(ss_order), int(factor_dtype), int(dense_dtype))
+    _check(lib().hm_assemble(tree, ctypes.byref(prm), _stream(stream), ctypes.byref(out)))
+    return out
+
+
+def hm_load_vector(tree, sources, f, stream=None):
+    """sources: CUDA float64 [ns, 3]; f: CUDA float64 [ns, n] (written)."""
+    import torch
+    _check(lib().hm_load_vector(tree, _ptr(sources, torch.float64), sources.shape[0], _ptr(f, torch.float64),
+                                _stream(stream)))
+    return f
+
+
+def hm_matvec(A, x, y, trans=0, prec=HM_F64, alpha=1.0, beta=0.0, stream=None):
+    """y = alpha op(H) x + beta y; x, y CUDA float64 [n] or [nrhs, n]."""
+    import torch
+    nrhs = 1 if x.dim() == 1 else x.shape[0]
+    _check(lib().hm_matvec(A, int(trans), nrhs, int(prec), _ptr(x, torch.float64), _ptr(y, torch.float64),
+                           float(alpha), float(beta), _stream(stream)))
+    return y
+
+
+def hm_solve(A, b, x, trans=0, restart=30, max_iter=3000, rel_tol=1e-10, refine=0, max_refine=20, inner_tol=1e-4,
+             inner_dtype=HM_F32, stream=None, raise_on_noconv=True):
+    """Solves op(H) x = b; returns the SolveInfo of the (last) right-hand side."""
+    import torch
+    nrhs = 1 if b.dim() == 1 else b.shape[0]
+    prm = SolveParams(int(restart), int(max_iter), float(rel_tol), int(refine), int(max_refine), float(inner_tol),
+                      int(inner_dtype))
+    info = SolveInfo()
+    st = lib().hm_solve(A, int(trans), nrhs, _ptr(b, torch.float64), _ptr(x, torch.float64), ctypes.byref(prm),
+                        _stream(stream), ctypes.byref(info))
+    if st == HM_ENOCONV and not raise_on_noconv:
+        return info
+    _check(st)
+    return info
+
+
+def hm_free(handle):
+    if handle:
+        lib().hm_free(handle)
+
+
+def hm_tree_get_info(tree) -> dict:
+    info = TreeInfo()
+    _check(lib().hm_tree_get_info(tree, ctypes.byref(info)))
+    return struct_dict(info)
+
+
+def hm_tree_get_perm(tree, n):
+    import torch
+    perm = torch.empty(n, dtype=torch.int32, device="cuda")
+    _check(lib().hm_tree_get_perm(tree, _ptr(perm)))
+    return perm
+
+
+def hm_tree_get_leaves(tree, dense: bool):
+    import torch
+    cnt = ctypes.c_int64(0)
+    _check(lib().hm_tree_get_leaves(tree, int(dense), None, 0, ctypes.byref(cnt)))
+    out = torch.empty((max(cnt.value, 1), 4), dtype=torch.int32, device="cuda")
+    _check(lib().hm_tree_get_leaves(tree, int(dense), _ptr(out), cnt.value, ctypes.byref(cnt)))
+    return out[:cnt.value]
+
+
+def hm_matrix_get_info(A) -> dict:
+    info = MatrixInfo()
+    _check(lib().hm_matrix_get_info(A, ctypes.byref(info)))
+    return struct_dict(info)
+
+
+def hm_matrix_export(A, n_dense: int, n_adm: int):
+    """Host copy of the FP64 H-matrix (numpy arrays, plain layout of hm.h)."""
+    import numpy as np
+    nd = ctypes.c_int64(0)
+    nl = ctypes.c_int64(0)
+    _check(lib().hm_matrix_export(A, None, None, None, None, None, None, ctypes.byref(nd), ctypes.byref(nl)))
+    dense = np.zeros(max(nd.value, 1))
+    doff = np.zeros(max(n_dense, 1), dtype=np.int64)
+    rank = np.zeros(max(n_adm, 1), dtype=np.int32)
+    uw = np.zeros(max(nl.value, 1))
+    uoff = np.zeros(max(n_adm, 1), dtype=np.int64)
+    woff = np.zeros(max(n_adm, 1), dtype=np.int64)
+    P = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    _check(lib().hm_matrix_export(A, P(dense), P(doff), P(rank), P(uw), P(uoff), P(woff), ctypes.byref(nd),
+                                  ctypes.byref(nl)))
+    return dict(dense=dense[:nd.value], dense_off=doff[:n_dense], rank=rank[:n_adm], uw=uw[:nl.value],
+                u_off=uoff[:n_adm], w_off=woff[:n_adm])

@@ -1,0 +1,528 @@
+// aca.cu -- batched adaptive cross approximation of all admissible blocks.
+//
+// Sec. 2.3: every admissible leaf tau x sigma is approximated by a rank-k
+// matrix U W^T built by ACA ("a pivoted Gauss elimination ... by successive
+// rank-one updates"), with matrix entries evaluated on the fly.  Sec. 3.1
+// "Batching": all blocks of uneven size are handled by one launch.
+//
+// ACA with partial pivoting, per block (m x n, local indices):
+//   i_1 = 0.  Step r: residual row  ~u = B(i_r, :) - sum_l U(i_r, l) W(:, l)^T,
+//   column pivot j_r = argmax_{unused j} |~u_j| (lowest j on ties),
+//   delta = ~u(j_r); a zero row (delta == 0 at r = 1, |delta| <= 2^-50 |delta_1|
+//   later) is marked used and replaced by the lowest unused row;
+//   W(:, r) = ~u / delta, U(:, r) = B(:, j_r) - sum_l W(j_r, l) U(:, l);
+//   ||S_r||^2 += 2 sum_{l<r} (u_r.u_l)(w_l.w_r) + ||u_r||^2 ||w_r||^2;
+//   stop when ||u_r|| ||w_r|| <= eps ||S_r|| or r = min(m, n, kmax);
+//   next row i_{r+1} = argmax_{unused i} |u_r(i)|.
+//
+// One persistent kernel.  Each CTA first takes large blocks (m + n above a
+// threshold) from a work counter, largest first, and runs the ACA with all
+// its threads (CTA-wide argmax and dot products through shared memory); when
+// none are left each warp takes small blocks on its own (shuffle argmax,
+// shuffle dot products, no block barriers).  All reductions have a fixed
+// order, so the factors are identical from run to run.  Converged factors are
+// copied from per-worker scratch to a bump-allocated arena; blocks that do not
+// fit are reported and re-run after the arena grows.
+#include <algorithm>
+
+#include "entry.cuh"
+
+namespace hm {
+
+constexpr int ACA_THREADS = 256;
+constexpr int ACA_WARPS = ACA_THREADS / 32;
+constexpr int SMALL_MAX_DIM = 256;  // warp-mode blocks: m, n <= this
+
+struct AcaArgs {
+    const double *pt;
+    int64_t npad;
+    const double *V;
+    const int32_t *adm;
+    int64_t n_big, n_all;
+    double eps;
+    int kmax;
+    QuadParams qp;
+    double *scr_big;
+    int64_t big_stride;
+    double *scr_small;
+    int64_t small_stride;
+    int big_words_r, big_words_c;  // bitmap words in CTA mode
+    double *arena;
+    int64_t arena_cap;
+    unsigned long long *arena_top;
+    int32_t *rank;
+    int64_t *uw_off;
+    unsigned long long *q_big, *q_small;
+    int *kmax_hit;
+    const int32_t *todo;  // optional subset of block ids (re-run after overflow)
+    int64_t n_todo;
+};
+
+struct Best {
+    double a;  // |value|
+    int idx;   // index (INT_MAX = none)
+    double v;  // signed value
+};
+
+__device__ __forceinline__ bool better(const Best &x, const Best &y) {
+    return x.a > y.a || (x.a == y.a && x.idx < y.idx);
+}
+
+__device__ __forceinline__ Best warp_argmax(Best b) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        Best c;
+        c.a = __shfl_xor_sync(0xffffffffu, b.a, o);
+        c.idx = __shfl_xor_sync(0xffffffffu, b.idx, o);
+        c.v = __shfl_xor_sync(0xffffffffu, b.v, o);
+        if (better(c, b)) b = c;
+    }
+    return b;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// shared scratch of one ACA worker (CTA or warp)
+struct AcaShared {
+    double *fix;    // [32]  fixed panel record
+    double *vec;    // [kmax] U(i_r, :) or W(j_r, :)
+    double *red;    // [ACA_WARPS] sum partials (CTA mode)
+    Best *bred;     // [ACA_WARPS] argmax partials (CTA mode)
+    uint32_t *urow, *ucol;
+    long long *ibc; // broadcast slot (CTA mode)
+};
+
+template <bool CTA>
+struct Grp {
+    __device__ __forceinline__ static int size() { return CTA ? ACA_THREADS : 32; }
+    __device__ __forceinline__ static int rank() { return CTA ? (int)threadIdx.x : (int)(threadIdx.x & 31); }
+    __device__ __forceinline__ static void sync() {
+        if (CTA) __syncthreads();
+        else __syncwarp();
+    }
+    __device__ __forceinline__ static double sum(double v, const AcaShared &sh) {
+        v = warp_sum(v);
+        if (!CTA) return v;
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        if (lane == 0) sh.red[w] = v;
+        __syncthreads();
+        double t = 0.0;
+        for (int k = 0; k < ACA_WARPS; ++k) t += sh.red[k];
+        __syncthreads();
+        return t;
+    }
+    __device__ __forceinline__ static Best argmax(Best b, const AcaShared &sh) {
+        b = warp_argmax(b);
+        if (!CTA) return b;
+        const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+        if (lane == 0) sh.bred[w] = b;
+        __syncthreads();
+        Best t = sh.bred[0];
+        for (int k = 1; k < ACA_WARPS; ++k)
+            if (better(sh.bred[k], t)) t = sh.bred[k];
+        __syncthreads();
+        return t;
+    }
+    // value of group thread 0, to every thread of the group
+    __device__ __forceinline__ static long long bcast(long long v, const AcaShared &sh) {
+        if (!CTA) return __shfl_sync(0xffffffffu, v, 0);
+        if (threadIdx.x == 0) *sh.ibc = v;
+        __syncthreads();
+        long long r = *sh.ibc;
+        __syncthreads();
+        return r;
+    }
+};
+
+__device__ __forceinline__ bool bit(const uint32_t *bm, int k) { return (bm[k >> 5] >> (k & 31)) & 1u; }
+
+// entry (row panel record r, column panel record c) of the Galerkin matrix
+__device__ __forceinline__ double aca_entry(const double *r, const double *c, const AcaArgs &A) {
+    const int32_t a[3] = {(int32_t)r[PT_VID], (int32_t)r[PT_VID + 1], (int32_t)r[PT_VID + 2]};
+    const int32_t b[3] = {(int32_t)c[PT_VID], (int32_t)c[PT_VID + 1], (int32_t)c[PT_VID + 2]};
+    const int kind = shared_vertices(a, b);
+    if (kind) return singular_entry_serial(A.V, a, b, kind, r[PT_AREA], c[PT_AREA], A.qp);
+    return regular_entry(r, 1, c, 1, A.qp);
+}
+
+__device__ __forceinline__ void load_panel(const AcaArgs &A, int64_t k, double *rec) {
+#pragma unroll
+    for (int q = 0; q < PT_ROWS; ++q) rec[q] = A.pt[(int64_t)q * A.npad + k];
+}
+
+// ACA of one block; U (m x kmax) and W (n x kmax) column-major in scratch.
+template <bool CTA>
+__device__ int aca_block(const AcaArgs &A, int rb, int m, int cb, int n, double *U, double *W, const AcaShared &sh,
+                         bool *hit_kmax) {
+    using G = Grp<CTA>;
+    const int gs = G::size(), t = G::rank();
+    const int wr = (m + 31) >> 5, wc = (n + 31) >> 5;
+    for (int k = t; k < wr; k += gs) sh.urow[k] = 0u;
+    for (int k = t; k < wc; k += gs) sh.ucol[k] = 0u;
+    G::sync();
+    const int rmax = min(A.kmax, min(m, n));
+    const double tiny = 8.881784197001252e-16;  // 2^-50
+    int r = 0, i = 0;
+    double s2 = 0.0, delta1 = 0.0;
+    bool converged = false;
+    double rec[PT_ROWS];
+    while (r < rmax) {
+        // ---- residual of row i ----
+        if (t < PT_ROWS) sh.fix[t] = A.pt[(int64_t)t * A.npad + rb + i];
+        for (int l = t; l < r; l += gs) sh.vec[l] = U[(int64_t)l * m + i];
+        G::sync();
+        Best best{-1.0, 0x7fffffff, 0.0};
+        for (int j = t; j < n; j += gs) {
+            load_panel(A, cb + j, rec);
+            double v = aca_entry(sh.fix, rec, A);
+            for (int l = 0; l < r; ++l) v -= sh.vec[l] * W[(int64_t)l * n + j];
+            W[(int64_t)r * n + j] = v;
+            if (!bit(sh.ucol, j)) {
+                const Best c{fabs(v), j, v};
+                if (better(c, best)) best = c;
+            }
+        }
+        best = G::argmax(best, sh);
+        if (t == 0) sh.urow[i >> 5] |= 1u << (i & 31);
+        G::sync();
+        const double delta = best.v;
+        const bool zero_row = (r == 0) ? (delta == 0.0) : (fabs(delta) <= tiny * delta1);
+        if (zero_row || best.idx == 0x7fffffff) {
+            // lowest unused row
+            int cand = 0x7fffffff;
+            for (int k = t; k < m; k += gs)
+                if (!bit(sh.urow, k)) { cand = k; break; }
+            Best c{0.0, cand, 0.0};
+            c = G::argmax(c, sh);
+            if (c.idx == 0x7fffffff) break;
+            i = c.idx;
+            continue;
+        }
+        if (r == 0) delta1 = fabs(delta);
+        const int jp = best.idx;
+        double nw2 = 0.0;
+        for (int j = t; j < n; j += gs) {
+            const double w = W[(int64_t)r * n + j] / delta;
+            W[(int64_t)r * n + j] = w;
+            nw2 += w * w;
+        }
+        // ---- residual of column jp ----
+        if (t < PT_ROWS) sh.fix[t] = A.pt[(int64_t)t * A.npad + cb + jp];
+        for (int l = t; l < r; l += gs) sh.vec[l] = W[(int64_t)l * n + jp];
+        G::sync();
+        double nu2 = 0.0;
+        Best nb{-1.0, 0x7fffffff, 0.0};
+        for (int k = t; k < m; k += gs) {
+            load_panel(A, rb + k, rec);
+            double u = aca_entry(rec, sh.fix, A);
+            for (int l = 0; l < r; ++l) u -= sh.vec[l] * U[(int64_t)l * m + k];
+            U[(int64_t)r * m + k] = u;
+            nu2 += u * u;
+            if (!bit(sh.urow, k)) {
+                const Best c{fabs(u), k, u};
+                if (better(c, nb)) nb = c;
+            }
+        }
+        if (t == 0) sh.ucol[jp >> 5] |= 1u << (jp & 31);
+        nu2 = G::sum(nu2, sh);
+        nw2 = G::sum(nw2, sh);
+        // ---- Frobenius norm of the approximant ----
+        double cross = 0.0;
+        for (int l = 0; l < r; ++l) {
+            double du = 0.0, dw = 0.0;
+            for (int k = t; k < m; k += gs) du += U[(int64_t)r * m + k] * U[(int64_t)l * m + k];
+            for (int j = t; j < n; j += gs) dw += W[(int64_t)l * n + j] * W[(int64_t)r * n + j];
+            du = G::sum(du, sh);
+            dw = G::sum(dw, sh);
+            cross += du * dw;
+        }
+        s2 = s2 + 2.0 * cross + nu2 * nw2;
+        ++r;
+        nb = G::argmax(nb, sh);
+        if (sqrt(nu2) * sqrt(nw2) <= A.eps * sqrt(s2)) { converged = true; break; }
+        if (nb.idx == 0x7fffffff) { converged = true; break; }
+        i = nb.idx;
+        G::sync();
+    }
+    *hit_kmax = !converged && r == A.kmax && r < min(m, n);
+    return r;
+}
+
+// copy the first k columns of U and W to the arena (bump allocation)
+template <bool CTA>
+__device__ void aca_store(const AcaArgs &A, int64_t b, int m, int n, int k, const double *U, const double *W,
+                          const AcaShared &sh) {
+    using G = Grp<CTA>;
+    const int gs = G::size(), t = G::rank();
+    const int64_t need = (int64_t)k * (m + n);
+    long long off = 0;
+    if (t == 0) off = (long long)atomicAdd(A.arena_top, (unsigned long long)need);
+    off = G::bcast(off, sh);
+    if (t == 0) A.rank[b] = k;
+    if ((int64_t)off + need > A.arena_cap) {
+        if (t == 0) A.uw_off[b] = -1;
+        return;
+    }
+    if (t == 0) A.uw_off[b] = (int64_t)off;
+    double *dst = A.arena + off;
+    const int64_t mk = (int64_t)m * k, nk = (int64_t)n * k;
+    for (int64_t e = t; e < mk; e += gs) dst[e] = U[e];
+    for (int64_t e = t; e < nk; e += gs) dst[mk + e] = W[e];
+}
+
+__global__ void __launch_bounds__(ACA_THREADS) aca_kernel(AcaArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double s_red[ACA_WARPS];
+    __shared__ Best s_bred[ACA_WARPS];
+    __shared__ long long s_ibc;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    // ---------------- phase 1: large blocks, whole CTA ----------------
+    {
+        AcaShared sh;
+        double *d = reinterpret_cast<double *>(smem_raw);
+        sh.fix = d;
+        sh.vec = d + 32;
+        sh.red = s_red;
+        sh.bred = s_bred;
+        sh.ibc = &s_ibc;
+        sh.urow = reinterpret_cast<uint32_t *>(d + 32 + MAX_KMAX);
+        sh.ucol = sh.urow + A.big_words_r;
+        double *U = A.scr_big + (int64_t)blockIdx.x * A.big_stride;
+        for (;;) {
+            long long q = 0;
+            if (threadIdx.x == 0) q = (long long)atomicAdd(A.q_big, 1ull);
+            q = Grp<true>::bcast(q, sh);
+            const int64_t nbig = A.todo ? A.n_todo : A.n_big;
+            if (q >= nbig) break;
+            const int64_t b = A.todo ? A.todo[q] : q;
+            const int32_t rb = A.adm[4 * b], re = A.adm[4 * b + 1], cb = A.adm[4 * b + 2], ce = A.adm[4 * b + 3];
+            const int m = re - rb, n = ce - cb;
+            double *W = U + (int64_t)m * A.kmax;
+            bool hit = false;
+            const int k = aca_block<true>(A, rb, m, cb, n, U, W, sh, &hit);
+            if (hit && threadIdx.x == 0) atomicAdd(A.kmax_hit, 1);
+            __syncthreads();
+            aca_store<true>(A, b, m, n, k, U, W, sh);
+            __syncthreads();
+        }
+    }
+    if (A.todo) return;
+
+    // ---------------- phase 2: small blocks, one warp each ----------------
+    {
+        AcaShared sh;
+        const int words = (SMALL_MAX_DIM + 31) / 32;
+        double *d = reinterpret_cast<double *>(smem_raw) + (int64_t)warp * (32 + MAX_KMAX + words);
+        sh.fix = d;
+        sh.vec = d + 32;
+        sh.red = nullptr;
+        sh.bred = nullptr;
+        sh.ibc = nullptr;
+        sh.urow = reinterpret_cast<uint32_t *>(d + 32 + MAX_KMAX);
+        sh.ucol = sh.urow + words;
+        double *U = A.scr_small + ((int64_t)blockIdx.x * ACA_WARPS + warp) * A.small_stride;
+        for (;;) {
+            int q = 0;
+            if (lane == 0) q = (int)atomicAdd(A.q_small, 1ull);
+            q = __shfl_sync(0xffffffffu, q, 0);
+            const int64_t b = A.n_big + q;
+            if (b >= A.n_all) break;
+            const int32_t rb = A.adm[4 * b], re = A.adm[4 * b + 1], cb = A.adm[4 * b + 2], ce = A.adm[4 * b + 3];
+            const int m = re - rb, n = ce - cb;
+            double *W = U + (int64_t)m * A.kmax;
+            bool hit = false;
+            const int k = aca_block<false>(A, rb, m, cb, n, U, W, sh, &hit);
+            if (hit && lane == 0) atomicAdd(A.kmax_hit, 1);
+            __syncwarp();
+            aca_store<false>(A, b, m, n, k, U, W, sh);
+            __syncwarp();
+        }
+    }
+}
+
+__global__ void aca_overflow_list(const int64_t *uw_off, int64_t na, int32_t *list, int *count) {
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < na; b += (int64_t)gridDim.x * blockDim.x)
+        if (uw_off[b] < 0) list[atomicAdd(count, 1)] = (int32_t)b;
+}
+
+__global__ void rank_to_i64(const int32_t *rank, int64_t na, int64_t *out) {
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < na; b += (int64_t)gridDim.x * blockDim.x)
+        out[b] = rank[b];
+}
+
+__global__ void rank_stats(const int32_t *rank, int64_t na, unsigned long long *sum, int *maxr) {
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < na; b += (int64_t)gridDim.x * blockDim.x) {
+        atomicAdd(sum, (unsigned long long)rank[b]);
+        atomicMax(maxr, rank[b]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host
+// ---------------------------------------------------------------------------
+void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStream_t s, double *sec) {
+    const int64_t na = tr->n_adm;
+    const int kmax = A->params.aca_kmax;
+    A->rank.alloc(sizeof(int32_t) * std::max<int64_t>(na, 1));
+    A->uw_off.alloc(sizeof(int64_t) * std::max<int64_t>(na, 1));
+    A->t_off.alloc(sizeof(int64_t) * (na + 1));
+    if (na == 0) {
+        A->uw.alloc(16);
+        A->lr_entries = 0;
+        A->total_rank = 0;
+        *sec = 0.0;
+        return;
+    }
+    // block sizes on the host: split into CTA-wide and warp-wide work
+    std::vector<int32_t> h_adm(4 * na);
+    HM_CUDA_CHECK(cudaMemcpyAsync(h_adm.data(), tr->adm.p, sizeof(int32_t) * 4 * na, cudaMemcpyDeviceToHost, s));
+    HM_CUDA_CHECK(cudaStreamSynchronize(s));
+    // blocks are in level order (largest first); small = both dims <= SMALL_MAX_DIM and
+    // m + n <= small_sum, chosen so that one warp per block keeps the tail short
+    const int small_sum = 320;
+    int64_t n_big = 0;
+    int max_m_big = 1, max_n_big = 1, max_sum_small = 2;
+    // order: big blocks first (they already come first within the level order)
+    std::vector<int32_t> big, small;
+    for (int64_t b = 0; b < na; ++b) {
+        const int m = h_adm[4 * b + 1] - h_adm[4 * b], n = h_adm[4 * b + 3] - h_adm[4 * b + 2];
+        if (m <= SMALL_MAX_DIM && n <= SMALL_MAX_DIM && m + n <= small_sum) small.push_back((int32_t)b);
+        else big.push_back((int32_t)b);
+    }
+    n_big = (int64_t)big.size();
+    // CTA-mode scratch and bitmaps fit every block (a re-run after arena
+    // growth processes any block CTA-wide)
+    for (int64_t b = 0; b < na; ++b) {
+        max_m_big = std::max(max_m_big, h_adm[4 * b + 1] - h_adm[4 * b]);
+        max_n_big = std::max(max_n_big, h_adm[4 * b + 3] - h_adm[4 * b + 2]);
+    }
+    for (int32_t b : small)
+        max_sum_small = std::max(max_sum_small, h_adm[4 * b + 1] - h_adm[4 * b] + h_adm[4 * b + 3] - h_adm[4 * b + 2]);
+    // the kernel addresses blocks by position: store them big-first
+    bool reordered = false;
+    for (int64_t k = 0; k < n_big; ++k)
+        if (big[k] != k) { reordered = true; break; }
+    if (reordered) fail(HM_EINTERNAL, "admissible blocks are not ordered largest first");
+
+    int occ = 0;
+    const int words_r = (max_m_big + 31) / 32, words_c = (max_n_big + 31) / 32;
+    const int small_words = (SMALL_MAX_DIM + 31) / 32;
+    const size_t smem_big = sizeof(double) * (32 + MAX_KMAX) + sizeof(uint32_t) * (words_r + words_c);
+    const size_t smem_small = (size_t)ACA_WARPS * sizeof(double) * (32 + MAX_KMAX + small_words);
+    const size_t smem = std::max(smem_big, smem_small);
+    HM_CUDA_CHECK(cudaFuncSetAttribute(aca_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    HM_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, aca_kernel, ACA_THREADS, smem));
+    if (occ < 1) fail(HM_EINTERNAL, "ACA kernel does not fit on an SM");
+    const int grid = num_sms() * occ;
+
+    AcaArgs a{};
+    a.pt = tr->pt.as<double>();
+    a.npad = tr->npad;
+    a.V = tr->V.as<double>();
+    a.adm = tr->adm.as<int32_t>();
+    a.n_big = n_big;
+    a.n_all = na;
+    a.eps = A->params.aca_eps;
+    a.kmax = kmax;
+    a.qp = qp;
+    a.big_stride = (int64_t)(max_m_big + max_n_big) * kmax;
+    a.small_stride = (int64_t)max_sum_small * kmax;
+    a.big_words_r = words_r;
+    a.big_words_c = words_c;
+    DBuf scr_big, scr_small, ctr;
+    scr_big.alloc(sizeof(double) * a.big_stride * grid);
+    scr_small.alloc(sizeof(double) * a.small_stride * grid * ACA_WARPS);
+    ctr.alloc(sizeof(unsigned long long) * 4);
+    a.scr_big = scr_big.as<double>();
+    a.scr_small = scr_small.as<double>();
+    a.arena_top = ctr.as<unsigned long long>();
+    a.q_big = ctr.as<unsigned long long>() + 1;
+    a.q_small = ctr.as<unsigned long long>() + 2;
+    a.kmax_hit = reinterpret_cast<int *>(ctr.as<unsigned long long>() + 3);
+    a.rank = A->rank.as<int32_t>();
+    a.uw_off = A->uw_off.as<int64_t>();
+    a.todo = nullptr;
+    a.n_todo = 0;
+
+    // arena: sum (m + n) * k_guess, grown and the overflowed blocks re-run if needed
+    int64_t k_guess = std::min<int64_t>(kmax, 20);
+    int64_t cap = tr->adm_rows_cols * k_guess;
+    DBuf arena;
+    arena.alloc(sizeof(double) * cap);
+    a.arena = arena.as<double>();
+    a.arena_cap = cap;
+    HM_CUDA_CHECK(cudaMemsetAsync(ctr.p, 0, sizeof(unsigned long long) * 4, s));
+    cudaEvent_t e0, e1;
+    HM_CUDA_CHECK(cudaEventCreate(&e0));
+    HM_CUDA_CHECK(cudaEventCreate(&e1));
+    HM_CUDA_CHECK(cudaEventRecord(e0, s));
+    aca_kernel<<<grid, ACA_THREADS, smem, s>>>(a);
+    HM_LAUNCH_CHECK();
+    HM_CUDA_CHECK(cudaEventRecord(e1, s));
+    HM_CUDA_CHECK(cudaEventSynchronize(e1));
+    float ms = 0;
+    HM_CUDA_CHECK(cudaEventElapsedTime(&ms, e0, e1));
+    *sec = ms * 1e-3;
+    unsigned long long top = read_scalar(a.arena_top, s);
+    if ((int64_t)top > cap) {
+        // grow: keep what fits, re-run the blocks that did not fit (CTA-wide)
+        DBuf list, cnt;
+        list.alloc(sizeof(int32_t) * na);
+        cnt.alloc(sizeof(int));
+        HM_CUDA_CHECK(cudaMemsetAsync(cnt.p, 0, sizeof(int), s));
+        aca_overflow_list<<<256, 256, 0, s>>>(a.uw_off, na, list.as<int32_t>(), cnt.as<int>());
+        HM_LAUNCH_CHECK();
+        const int nover = read_scalar(cnt.as<int>(), s);
+        // offsets only grow, so every reservation that fit ends at or below
+        // cap; keep [0, cap) and restart the bump pointer there
+        const int64_t used = cap;
+        const int64_t newcap = (int64_t)top + (int64_t)top / 8 + 1;
+        DBuf grown;
+        grown.alloc(sizeof(double) * newcap);
+        HM_CUDA_CHECK(cudaMemcpyAsync(grown.p, arena.p, sizeof(double) * used, cudaMemcpyDeviceToDevice, s));
+        arena = std::move(grown);
+        a.arena = arena.as<double>();
+        a.arena_cap = newcap;
+        a.todo = list.as<int32_t>();
+        a.n_todo = nover;
+        unsigned long long used_u = (unsigned long long)used;
+        HM_CUDA_CHECK(cudaMemcpyAsync(a.arena_top, &used_u, sizeof(used_u), cudaMemcpyHostToDevice, s));
+        HM_CUDA_CHECK(cudaMemsetAsync(a.q_big, 0, sizeof(unsigned long long), s));
+        aca_kernel<<<grid, ACA_THREADS, smem, s>>>(a);
+        HM_LAUNCH_CHECK();
+        top = read_scalar(a.arena_top, s);
+        if ((int64_t)top > newcap) fail(HM_ENOMEM, "ACA factor arena overflow after growth");
+    }
+    // shrink the arena to what is used
+    A->lr_entries = (int64_t)top;
+    A->uw.alloc(sizeof(double) * std::max<int64_t>(A->lr_entries, 1));
+    HM_CUDA_CHECK(cudaMemcpyAsync(A->uw.p, arena.p, sizeof(double) * A->lr_entries, cudaMemcpyDeviceToDevice, s));
+    // t offsets (prefix sum of ranks)
+    rank_to_i64<<<256, 256, 0, s>>>(A->rank.as<int32_t>(), na, A->t_off.as<int64_t>());
+    HM_LAUNCH_CHECK();
+    HM_CUDA_CHECK(cudaMemsetAsync(A->t_off.as<int64_t>() + na, 0, sizeof(int64_t), s));
+    A->total_rank = exclusive_scan_i64(A->t_off.as<int64_t>(), A->t_off.as<int64_t>(), na + 1, s);
+    {
+        DBuf st;
+        st.alloc(sizeof(unsigned long long) * 2);
+        HM_CUDA_CHECK(cudaMemsetAsync(st.p, 0, sizeof(unsigned long long) * 2, s));
+        rank_stats<<<256, 256, 0, s>>>(A->rank.as<int32_t>(), na, st.as<unsigned long long>(),
+                                       reinterpret_cast<int *>(st.as<unsigned long long>() + 1));
+        HM_LAUNCH_CHECK();
+        unsigned long long h[2];
+        HM_CUDA_CHECK(cudaMemcpyAsync(h, st.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+        HM_CUDA_CHECK(cudaStreamSynchronize(s));
+        A->info.mean_rank = (double)h[0] / (double)na;
+        A->info.max_rank = (int)(h[1] & 0xffffffffu);
+        A->info.kmax_hit = read_scalar(a.kmax_hit, s);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+}
+
+}  // namespace hm

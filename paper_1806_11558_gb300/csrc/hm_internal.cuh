@@ -1,0 +1,187 @@
+// hm_internal.cuh -- internal declarations of the GB300 H-matrix BEM library.
+//
+// Device data layout (Morton order throughout; "Npad" = n rounded up to 8):
+//   panel table PT : double [PT_ROWS][Npad]; row q (0..6) = x of the 7 quadrature
+//                    points, rows 7..13 = y, rows 14..20 = z, row 21 = |T|,
+//                    rows 22..24 = the three vertex indices (exact as doubles).
+//                    Component-major so that one 2-D TMA box stages a whole
+//                    cluster of panels, and consecutive panels are consecutive
+//                    doubles in shared memory (conflict-free per-lane loads).
+//   dense near field: one row-major panel per leaf row cluster rho, of
+//                    |rho| x K_rho doubles, K_rho = sum of the widths of the
+//                    non-admissible leaves in rho's block row, concatenated in
+//                    column order (no padding).  Block b's entry (i, j) lives at
+//                    dense_base[b] + i * dense_ld[b] + j.
+//   low-rank factors: per admissible leaf b, U_b (m x k_b, column-major) then
+//                    W_b (n x k_b, column-major) at uw_off[b]; block ~ U_b W_b^T.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/hm.h"
+
+namespace hm {
+
+constexpr int NQ = 7;          // points of the triangle rule
+constexpr int PT_ROWS = 25;    // rows of the panel table
+constexpr int PT_AREA = 21;
+constexpr int PT_VID = 22;
+constexpr int MAX_SS = 16;     // largest Gauss-Legendre order for touching pairs
+constexpr int MAX_LEAF = 256;  // largest C_leaf
+constexpr int MAX_KMAX = 128;  // largest ACA rank
+
+// ----------------------------------------------------------------------------
+// errors: internal code throws hm::Failure; the C ABI converts it to a status
+// ----------------------------------------------------------------------------
+struct Failure {
+    hm_status status;
+    std::string msg;
+};
+
+void set_last_error(const std::string &msg);
+[[noreturn]] void fail(hm_status s, const char *fmt, ...);
+
+#define HM_CUDA_CHECK(call)                                                                        \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            ::hm::fail(e_ == cudaErrorMemoryAllocation ? HM_ENOMEM : HM_ECUDA, "%s:%d %s: %s",     \
+                       __FILE__, __LINE__, #call, cudaGetErrorString(e_));                         \
+    } while (0)
+
+#define HM_LAUNCH_CHECK() HM_CUDA_CHECK(cudaGetLastError())
+
+// ----------------------------------------------------------------------------
+// device memory: RAII buffer (cudaMalloc / cudaFree)
+// ----------------------------------------------------------------------------
+struct DBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DBuf() = default;
+    DBuf(const DBuf &) = delete;
+    DBuf &operator=(const DBuf &) = delete;
+    DBuf(DBuf &&o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+    DBuf &operator=(DBuf &&o) noexcept {
+        if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+        return *this;
+    }
+    ~DBuf() { release(); }
+    void alloc(size_t nbytes);
+    void release();
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// Reads a device value synchronously on `s`.
+template <class T> T read_scalar(const T *d, cudaStream_t s) {
+    T h;
+    HM_CUDA_CHECK(cudaMemcpyAsync(&h, d, sizeof(T), cudaMemcpyDeviceToHost, s));
+    HM_CUDA_CHECK(cudaStreamSynchronize(s));
+    return h;
+}
+
+int num_sms();
+
+// ----------------------------------------------------------------------------
+// quadrature data passed by value to kernels (lives in the parameter bank)
+// ----------------------------------------------------------------------------
+struct QuadParams {
+    double bary[NQ][3];  // 7-point rule, barycentric
+    double w[NQ];        // weights, sum 1
+    int ss_n;            // Gauss-Legendre order on [0, 1] for touching pairs
+    double gx[MAX_SS];
+    double gw[MAX_SS];
+};
+
+// 7-point rule from its closed form; Gauss-Legendre nodes by Newton's method
+// on the Legendre polynomial (three-term recurrence).
+QuadParams make_quad(int ss_order);
+
+// ----------------------------------------------------------------------------
+// primitives (prims.cu)
+// ----------------------------------------------------------------------------
+// exclusive scan of n int64 values (in may equal out); returns the total
+int64_t exclusive_scan_i64(const int64_t *d_in, int64_t *d_out, int64_t n, cudaStream_t s);
+// stable ascending sort of 64-bit keys with 32-bit payloads (LSD radix);
+// keys/vals are sorted in place, d_tmp_* are scratch of the same sizes
+void radix_sort_u64(uint64_t *d_keys, int32_t *d_vals, uint64_t *d_tmp_keys, int32_t *d_tmp_vals, int64_t n,
+                    int key_bits, cudaStream_t s);
+void gather_i32(const int32_t *d_src, const int32_t *d_idx, int32_t *d_dst, int64_t n, cudaStream_t s);
+
+// ----------------------------------------------------------------------------
+// TMA tensor maps (driver entry point resolved through the runtime)
+// ----------------------------------------------------------------------------
+void make_tensor_map_2d_f64(CUtensorMap *map, const double *base, uint64_t dim0, uint64_t dim1, uint32_t box0,
+                            uint32_t box1);
+
+}  // namespace hm
+
+// ----------------------------------------------------------------------------
+// the opaque handles of the C ABI
+// ----------------------------------------------------------------------------
+constexpr uint32_t HM_TREE_MAGIC = 0x48545245u;    // "HTRE"
+constexpr uint32_t HM_MATRIX_MAGIC = 0x484d4154u;  // "HMAT"
+
+struct hm_tree {
+    uint32_t magic = HM_TREE_MAGIC;
+    int64_t n = 0, nv = 0, npad = 0;
+    int32_t leaf = 0;
+    double eta = 0.0;
+    hm::DBuf V;        // [nv][3] double, copy of the caller's vertices
+    hm::DBuf trim;     // [n][3] int32, triangles in Morton order
+    hm::DBuf pt;       // [PT_ROWS][npad] double, panel table (Morton order)
+    hm::DBuf cent;     // [n][3] double, centroids in Morton order
+    hm::DBuf perm;     // [n] int32, Morton position -> original index
+    hm::DBuf iperm;    // [n] int32, original index -> Morton position
+    // cluster tree
+    int64_t n_clusters = 0;
+    int32_t depth = 0;
+    hm::DBuf cl_range;  // [nc][2] int32 (begin, end), breadth-first
+    hm::DBuf cl_box;    // [nc][6] double (lo xyz, hi xyz)
+    int64_t n_leaf = 0;
+    int32_t max_leaf = 0;
+    hm::DBuf leaf_begin;  // [n_leaf + 1] int32, begins of the leaf clusters (ascending)
+    // block tree
+    int64_t n_dense = 0, n_adm = 0;
+    hm::DBuf dense;       // [n_dense][4] int32, sorted by (row_begin, col_begin), rows = one leaf cluster
+    hm::DBuf dense_base;  // [n_dense] int64, offset of entry (0, 0) in the near-field arena
+    hm::DBuf dense_ld;    // [n_dense] int32, row stride in the arena
+    int64_t dense_entries = 0;
+    hm::DBuf rho_off;     // [n_leaf + 1] int64, arena offset of each leaf row cluster's panel
+    hm::DBuf rho_K;       // [n_leaf] int32, width of the panel
+    hm::DBuf rho_colptr;  // [n_leaf + 1] int64, into colidx
+    hm::DBuf colidx;      // [sum K] int32, Morton column of each panel column
+    int32_t max_dense_dim = 0;
+    hm::DBuf adm;         // [n_adm][4] int32, in block-tree level order (largest first)
+    int64_t adm_rows_cols = 0;
+    hm::DBuf lr_rowptr;   // [n_leaf + 1] int64: admissible leaves whose rows cover each leaf cluster
+    hm::DBuf lr_list;     // [..] int32 block ids (ascending per leaf cluster)
+    int64_t singular_cap = 0;  // upper bound on touching pairs
+    int64_t n_singular = 0;    // filled by hm_assemble
+    double seconds = 0.0;
+    CUtensorMap pt_map;   // TMA map of the panel table, box [PT_ROWS][box_cols]
+    int32_t box_cols = 0;
+};
+
+struct hm_matrix {
+    uint32_t magic = HM_MATRIX_MAGIC;
+    const hm_tree *tree = nullptr;
+    hm_assemble_params params{};
+    hm::DBuf dense;     // near-field arena, double
+    hm::DBuf dense32;   // optional FP32 copy
+    hm::DBuf rank;      // [n_adm] int32
+    hm::DBuf uw_off;    // [n_adm] int64
+    hm::DBuf uw;        // factor arena, double
+    hm::DBuf uw32;      // optional FP32 copy
+    hm::DBuf uwbf;      // optional BF16 copy
+    int64_t lr_entries = 0;
+    hm::DBuf t_off;     // [n_adm] int64, prefix sum of ranks
+    int64_t total_rank = 0;
+    hm_matrix_info info{};
+};

@@ -1,0 +1,232 @@
+// nearfield.cu -- dense (non-admissible) leaves of the block tree.
+//
+// Sec. 3.3 "Pre-computation of matrix blocks": every entry of every
+// non-admissible leaf is evaluated once and stored contiguously without
+// padding.  Here the storage unit is the row panel of a leaf row cluster (all
+// dense blocks of that block row side by side), which is what the
+// row-owned H-matrix-vector product streams.
+//
+// nearfield_kernel: one CTA per dense block.  One elected thread stages the
+// row cluster's and the column cluster's panel records (7 quadrature points,
+// area, vertex ids) into shared memory with two 2-D TMA box loads completing
+// on an mbarrier; every thread then evaluates entries with the 7x7 rule.
+// Pairs that share a vertex are queued (warp-aggregated append) for
+// singular_kernel, which gives each such entry one warp: the lanes split the
+// regions x n^3 Gauss points of the regularised integral.
+#include "entry.cuh"
+
+namespace hm {
+
+struct SingularItem {
+    int64_t off;  // arena offset of the entry
+    int32_t i;    // Morton row
+    int32_t j;    // Morton column
+};
+
+// ---------------------------------------------------------------------------
+// TMA / mbarrier (inline PTX)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], "
+        "[%2];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_addr(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+// Bounded wait: gives up after max_iter polls (sets *err) so a lost
+// transaction can never hang the GPU.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase, int *err, int code) {
+    for (long it = 0; it < (1L << 26); ++it)
+        if (mbar_try_wait(bar, phase)) return true;
+    atomicExch(err, code);
+    return false;
+}
+
+// ---------------------------------------------------------------------------
+// regular near-field entries
+// ---------------------------------------------------------------------------
+constexpr int NF_THREADS = 128;
+
+__global__ void __launch_bounds__(NF_THREADS) nearfield_kernel(const __grid_constant__ CUtensorMap pt_map,
+                                                                const int32_t *__restrict__ dense,
+                                                                const int64_t *__restrict__ base,
+                                                                const int32_t *__restrict__ ld, int box_cols,
+                                                                const QuadParams qp, double *__restrict__ arena,
+                                                                SingularItem *__restrict__ sing,
+                                                                unsigned long long *sing_count, int64_t sing_cap,
+                                                                int *err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    const int64_t b = blockIdx.x;
+    const int32_t rb = dense[4 * b], re = dense[4 * b + 1], cb = dense[4 * b + 2], ce = dense[4 * b + 3];
+    const int32_t rb_al = rb & ~1, cb_al = cb & ~1;
+    const int tile_bytes = ((PT_ROWS * box_cols * 8) + 127) / 128 * 128;
+    double *tR = reinterpret_cast<double *>(smem_raw);
+    double *tC = reinterpret_cast<double *>(smem_raw + tile_bytes);
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(&bar, 2u * PT_ROWS * box_cols * 8u);
+        tma_load_2d(tR, &pt_map, &bar, rb_al, 0);
+        tma_load_2d(tC, &pt_map, &bar, cb_al, 0);
+    }
+    if (!mbar_wait_bounded(&bar, 0, err, 2)) {
+        // the copies may still land: wait once more (bounded) before leaving
+        mbar_wait_bounded(&bar, 0, err, 2);
+        return;
+    }
+    const int m = re - rb, n = ce - cb, mn = m * n;
+    const int ro = rb - rb_al, co = cb - cb_al;
+    const int64_t blk_base = base[b];
+    const int32_t blk_ld = ld[b];
+    const int lane = threadIdx.x & 31;
+    for (int e0 = 0; e0 < mn; e0 += NF_THREADS) {
+        const int e = e0 + threadIdx.x;
+        const bool valid = e < mn;
+        const int i = valid ? e / n : 0, j = valid ? e - (e / n) * n : 0;
+        const double *R = tR + i + ro;
+        const double *C = tC + j + co;
+        int32_t vr[3], vc[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            vr[k] = (int32_t)R[(PT_VID + k) * box_cols];
+            vc[k] = (int32_t)C[(PT_VID + k) * box_cols];
+        }
+        const bool touch = valid && shared_vertices(vr, vc) > 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, touch);
+        if (bal) {
+            const int leader = __ffs(bal) - 1;
+            unsigned long long slot = 0;
+            if (lane == leader) slot = atomicAdd(sing_count, (unsigned long long)__popc(bal));
+            slot = __shfl_sync(0xffffffffu, slot, leader);
+            if (touch) {
+                const unsigned long long k = slot + __popc(bal & ((1u << lane) - 1u));
+                if ((int64_t)k < sing_cap) {
+                    sing[k].off = blk_base + (int64_t)i * blk_ld + j;
+                    sing[k].i = rb + i;
+                    sing[k].j = cb + j;
+                } else {
+                    atomicExch(err, 3);
+                }
+            }
+        }
+        if (valid && !touch) arena[blk_base + (int64_t)i * blk_ld + j] = regular_entry(R, box_cols, C, box_cols, qp);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// touching pairs: one warp per entry
+// ---------------------------------------------------------------------------
+__global__ void singular_kernel(const SingularItem *__restrict__ items, int64_t count, const int32_t *__restrict__ trim,
+                                const double *__restrict__ V, const double *__restrict__ pt, int64_t npad,
+                                const QuadParams qp, double *__restrict__ arena) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (w >= count) return;
+    const SingularItem it = items[w];
+    const int32_t *ta = trim + 3 * (int64_t)it.i, *tb = trim + 3 * (int64_t)it.j;
+    const int32_t a[3] = {ta[0], ta[1], ta[2]}, bb[3] = {tb[0], tb[1], tb[2]};
+    const int kind = shared_vertices(a, bb);
+    int32_t P[3], Q[3];
+    touch_orient(a, bb, kind, P, Q);
+    const PairGeom g = pair_geom(V, P, Q);
+    const int n = qp.ss_n, n2 = n * n, n3 = n2 * n;
+    const int total = ss_regions(kind) * n3;
+    double s = 0.0;
+    for (int t = lane; t < total; t += 32) {
+        const int r = t / n3, rem = t - r * n3;
+        const int k1 = rem / n2, k2 = (rem / n) % n, k3 = rem % n;
+        s += ss_point(g, kind, r, k1, k2, k3, qp);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+        const double ai = pt[(int64_t)PT_AREA * npad + it.i], aj = pt[(int64_t)PT_AREA * npad + it.j];
+        arena[it.off] = 4.0 * ai * aj * (s / 3.0) * INV_4PI;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host
+// ---------------------------------------------------------------------------
+void assemble_nearfield(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStream_t s, int *d_err,
+                        double *sec_regular, double *sec_singular) {
+    A->dense.alloc(sizeof(double) * std::max<int64_t>(tr->dense_entries, 1));
+    DBuf items, cnt;
+    items.alloc(sizeof(SingularItem) * std::max<int64_t>(tr->singular_cap, 1));
+    cnt.alloc(sizeof(unsigned long long));
+    HM_CUDA_CHECK(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long), s));
+    const int tile_bytes = ((PT_ROWS * tr->box_cols * 8) + 127) / 128 * 128;
+    const int smem = 2 * tile_bytes;
+    HM_CUDA_CHECK(cudaFuncSetAttribute(nearfield_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    cudaEvent_t e0, e1, e2;
+    HM_CUDA_CHECK(cudaEventCreate(&e0));
+    HM_CUDA_CHECK(cudaEventCreate(&e1));
+    HM_CUDA_CHECK(cudaEventCreate(&e2));
+    HM_CUDA_CHECK(cudaEventRecord(e0, s));
+    if (tr->n_dense > 0) {
+        nearfield_kernel<<<(unsigned)tr->n_dense, NF_THREADS, smem, s>>>(
+            tr->pt_map, tr->dense.as<int32_t>(), tr->dense_base.as<int64_t>(), tr->dense_ld.as<int32_t>(),
+            tr->box_cols, qp, A->dense.as<double>(), items.as<SingularItem>(), cnt.as<unsigned long long>(),
+            tr->singular_cap, d_err);
+        HM_LAUNCH_CHECK();
+    }
+    HM_CUDA_CHECK(cudaEventRecord(e1, s));
+    const int64_t nsing = (int64_t)read_scalar(cnt.as<unsigned long long>(), s);
+    if (nsing > tr->singular_cap) fail(HM_EINTERNAL, "touching-pair queue overflow (%lld > %lld)", (long long)nsing,
+                                      (long long)tr->singular_cap);
+    const_cast<hm_tree *>(tr)->n_singular = nsing;
+    if (nsing > 0) {
+        const int64_t threads = nsing * 32;
+        singular_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+            items.as<SingularItem>(), nsing, tr->trim.as<int32_t>(), tr->V.as<double>(), tr->pt.as<double>(),
+            tr->npad, qp, A->dense.as<double>());
+        HM_LAUNCH_CHECK();
+    }
+    HM_CUDA_CHECK(cudaEventRecord(e2, s));
+    HM_CUDA_CHECK(cudaEventSynchronize(e2));
+    float ms1 = 0, ms2 = 0;
+    HM_CUDA_CHECK(cudaEventElapsedTime(&ms1, e0, e1));
+    HM_CUDA_CHECK(cudaEventElapsedTime(&ms2, e1, e2));
+    *sec_regular = ms1 * 1e-3;
+    *sec_singular = ms2 * 1e-3;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(e2);
+}
+
+}  // namespace hm
