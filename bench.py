@@ -1,0 +1,401 @@
+"""Benchmark of the H-matrix BEM hot path on one GB300 (or N replicas).
+
+A step is one pass of the whole path over one synthetic problem:
+Morton tree + block tree, near-field assembly, batched ACA, load vector,
+FP64 GMRES solve and the FP32-factor / FP64-refinement solve.
+Workload: bumped icosphere level 7 (327,680 flat triangles, 8 seeded real
+spherical harmonics l <= 4, amplitude 0.1), point source p = (3, 0, 0),
+C_leaf = 64, eta = 1.5, ACA eps = 1e-7, FP64 master with FP32 copies,
+solves to a relative residual of 1e-12 (1e-8 relative solution accuracy).
+
+`value` is seconds per step (lower is better); the JSON line also carries the
+per-phase seconds, H-matvec GB/s, the error of the mixed-precision solution
+against the FP64 one, the roofline of the dominant kernel and the CPU oracle
+timed on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(workload="bumped icosphere level 7, Galerkin single-layer Laplace, P0",
+                panels=327680, leaf_size=64, eta=1.5, aca_eps=1e-7, aca_kmax=64, ss_order=8,
+                source=[3.0, 0.0, 0.0], solve_rel_tol=1e-12, inner="fp32 factors + fp32 near field",
+                inner_tol=1e-4, restart=30)
+METRIC = "H-matrix setup s, H-matvec GB/s, solve s at 1e-8 rel. accuracy: mixed vs FP64"
+FLOPS_PER_PAIR = 11  # 3 sub + 3 mul + 2 add (|x-y|^2) + rsqrt + multiply-add (weight)
+PAIRS_PER_ENTRY = 49
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def _inputs():
+    import meshgen
+    cfg = meshgen.config("precision")
+    return cfg["V"], cfg["T"]
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv") if os.path.isdir(
+            os.path.join(ROOT, "gpurun_out")) else "/tmp/hm_clocks.csv"
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+    import paper_1806_11558_gb300 as hm
+    from paper_1806_11558_gb300 import build as hb
+
+    hb.build()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    V, T = _inputs()
+    n = T.shape[0]
+    Vd = torch.from_numpy(V).to(dev)
+    Td = torch.from_numpy(T).to(dev)
+    src = torch.tensor([WORKLOAD["source"]], dtype=torch.float64, device=dev)
+    f = torch.empty((1, n), dtype=torch.float64, device=dev)
+    x64 = torch.zeros(n, dtype=torch.float64, device=dev)
+    xmx = torch.zeros(n, dtype=torch.float64, device=dev)
+    W = WORKLOAD
+
+    def step(Vdev, Tdev, keep=False):
+        t = {}
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        e[0].record(stream)
+        tree = hm.hm_build_tree(Vdev, Tdev, eta=W["eta"], leaf_size=W["leaf_size"])
+        e[1].record(stream)
+        A = hm.hm_assemble(tree, aca_eps=W["aca_eps"], aca_kmax=W["aca_kmax"], ss_order=W["ss_order"],
+                           factor_dtype=hm.HM_F32, dense_dtype=hm.HM_F32)
+        e[2].record(stream)
+        hm.hm_load_vector(tree, src, f)
+        e[3].record(stream)
+        i64 = hm.hm_solve(A, f[0], x64, rel_tol=W["solve_rel_tol"], restart=W["restart"], max_iter=5000)
+        e[4].record(stream)
+        imx = hm.hm_solve(A, f[0], xmx, rel_tol=W["solve_rel_tol"], restart=W["restart"], max_iter=5000, refine=1,
+                          inner_tol=W["inner_tol"], inner_dtype=hm.HM_F32, max_refine=50)
+        e[5].record(stream)
+        torch.cuda.synchronize()
+        t["tree_s"] = e[0].elapsed_time(e[1]) / 1e3
+        t["assemble_s"] = e[1].elapsed_time(e[2]) / 1e3
+        t["load_s"] = e[2].elapsed_time(e[3]) / 1e3
+        t["solve_fp64_s"] = e[3].elapsed_time(e[4]) / 1e3
+        t["solve_mixed_s"] = e[4].elapsed_time(e[5]) / 1e3
+        t["step_s"] = e[0].elapsed_time(e[5]) / 1e3
+        t["minfo"] = hm.hm_matrix_get_info(A)
+        t["tinfo"] = hm.hm_tree_get_info(tree)
+        t["iters_fp64"] = i64.iters
+        t["iters_mixed"] = imx.iters
+        t["refine_steps"] = imx.refine_steps
+        t["resid_fp64"] = i64.rel_resid
+        t["resid_mixed"] = imx.rel_resid
+        if keep:
+            return t, tree, A
+        hm.hm_free(A)
+        hm.hm_free(tree)
+        return t
+
+    for _ in range(args.warmup):
+        step(Vd, Td)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(dev.index)
+    clocks.start()
+    l0 = hm.hm_kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    results = [step(Vd, Td) for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = hm.hm_kernel_launches() - l0
+    ck = clocks.stop()
+    total_s = ev0.elapsed_time(ev1) / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([total_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_s = float(tt.item())
+    per_step = total_s / args.steps
+
+    # mixed vs FP64 solution error, matvec GB/s (separate, untimed for `value`)
+    last, tree, A = step(Vd, Td, keep=True)
+    err_mixed = float(torch.linalg.norm(xmx - x64) / torch.linalg.norm(x64))
+    mi, ti = last["minfo"], last["tinfo"]
+    xs = torch.randn(n, dtype=torch.float64, device=dev)
+    ys = torch.empty_like(xs)
+    mv = {}
+    for name, prec, esz in (("fp64", hm.HM_F64, 8), ("fp32", hm.HM_F32, 4)):
+        for _ in range(3):
+            hm.hm_matvec(A, xs, ys, prec=prec)
+        torch.cuda.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        reps = 10
+        a0.record(stream)
+        for _ in range(reps):
+            hm.hm_matvec(A, xs, ys, prec=prec)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        sec = a0.elapsed_time(a1) / 1e3 / reps
+        byts = (mi["dense_entries"] + mi["lr_entries"]) * esz + n * 8 * 4
+        mv[name] = {"s": sec, "gbs": byts / sec / 1e9, "bytes": byts}
+    # BF16 factors: one extra assembly and refined solve, reported beside
+    A16 = hm.hm_assemble(tree, aca_eps=W["aca_eps"], aca_kmax=W["aca_kmax"], ss_order=W["ss_order"],
+                         factor_dtype=hm.HM_BF16, dense_dtype=hm.HM_F32)
+    xbf = torch.zeros_like(x64)
+    b0 = torch.cuda.Event(enable_timing=True)
+    b1 = torch.cuda.Event(enable_timing=True)
+    b0.record(stream)
+    ibf = hm.hm_solve(A16, f[0], xbf, rel_tol=W["solve_rel_tol"], restart=W["restart"], max_iter=5000, refine=1,
+                      inner_tol=1e-2, inner_dtype=hm.HM_BF16, max_refine=80, raise_on_noconv=False)
+    b1.record(stream)
+    torch.cuda.synchronize()
+    bf16 = {"solve_s": b0.elapsed_time(b1) / 1e3, "err_vs_fp64": float(torch.linalg.norm(xbf - x64) /
+                                                                        torch.linalg.norm(x64)),
+            "iters": ibf.iters, "refine_steps": ibf.refine_steps, "rel_resid": ibf.rel_resid}
+    hm.hm_free(A16)
+
+    # e2e: the same step through the C ABI from pinned host buffers, host<->device copies timed
+    Vh = torch.from_numpy(V).pin_memory()
+    Th = torch.from_numpy(T).pin_memory()
+    xh = torch.empty(n, dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 2))
+    torch.cuda.synchronize()
+    c0 = torch.cuda.Event(enable_timing=True)
+    c1 = torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    for _ in range(e2e_steps):
+        Vd2 = Vh.to(dev, non_blocking=True)
+        Td2 = Th.to(dev, non_blocking=True)
+        step(Vd2, Td2)
+        xh.copy_(xmx, non_blocking=True)
+    c1.record(stream)
+    torch.cuda.synchronize()
+    e2e_s = c0.elapsed_time(c1) / 1e3 / e2e_steps
+
+    # roofline of the dominant kernel (the batched ACA): FP64 arithmetic.
+    # Algorithmic work = entry evaluations (sum_b k_b (m_b + n_b) = stored
+    # factor entries) x 49 kernel evaluations x FLOPS_PER_PAIR, per launch,
+    # over the kernel's CUDA-event duration measured inside hm_assemble.
+    peaks, peak_src = _peaks()
+    fp64_peak_tflops = 1.25  # nominal FP64 rate of GB300 (2 DFMA / SM / clock at 2.07 GHz x 152 SMs)
+    aca_flops = mi["lr_entries"] * PAIRS_PER_ENTRY * FLOPS_PER_PAIR
+    aca_s = sum(r["minfo"]["s_aca"] for r in results) / len(results)
+    nf_s = sum(r["minfo"]["s_nearfield"] for r in results) / len(results)
+    nf_flops = ti["dense_entries"] * PAIRS_PER_ENTRY * FLOPS_PER_PAIR
+    aca_tf = aca_flops / aca_s / 1e12
+    roofline = {"kernel": "aca_kernel", "bound": "alu", "achieved": aca_tf, "peak": fp64_peak_tflops,
+                "unit": "TFLOP/s", "frac": aca_tf / fp64_peak_tflops, "traffic": None,
+                "peak_source": "FP64 nominal 1.25 TFLOP/s (no FP64 figure in MEASURED_PEAKS.json)",
+                "launch_s": aca_s, "entries_evaluated": mi["lr_entries"]}
+    nearfield_roof = {"kernel": "nearfield_kernel", "bound": "alu", "launch_s": nf_s,
+                      "achieved": nf_flops / nf_s / 1e12, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
+                      "frac": nf_flops / nf_s / 1e12 / fp64_peak_tflops}
+    matvec_roof = {"kernel": "row_kernel + lr_project_kernel (fp32 copy)", "bound": "hbm",
+                   "achieved": mv["fp32"]["gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                   "frac": mv["fp32"]["gbs"] / peaks["hbm_gbs"], "peak_source": peak_src}
+    hm.hm_free(A)
+    hm.hm_free(tree)
+
+    out = {
+        "metric": METRIC, "value": per_step, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64 (mixed solve: f32 factors, f64 refinement)",
+        "data": "synthetic (seeded bumped icosphere, no dataset)",
+        "config": dict(WORKLOAD, parallelism="replicas" if world > 1 else "single GPU",
+                       l2="inputs larger than L2 (near field %.1f GB, factors %.1f GB)" % (
+                           mi["dense_entries"] * 8 / 1e9, mi["lr_entries"] * 8 / 1e9)),
+        "setup_s": sum(r["tree_s"] + r["assemble_s"] for r in results) / len(results),
+        "tree_s": sum(r["tree_s"] for r in results) / len(results),
+        "assemble_s": sum(r["assemble_s"] for r in results) / len(results),
+        "nearfield_s": nf_s, "singular_s": sum(r["minfo"]["s_singular"] for r in results) / len(results),
+        "aca_s": aca_s,
+        "solve_fp64_s": sum(r["solve_fp64_s"] for r in results) / len(results),
+        "solve_mixed_s": sum(r["solve_mixed_s"] for r in results) / len(results),
+        "iters_fp64": last["iters_fp64"], "iters_mixed": last["iters_mixed"], "refine_steps": last["refine_steps"],
+        "resid_fp64": last["resid_fp64"], "resid_mixed": last["resid_mixed"], "mixed_vs_fp64_rel_err": err_mixed,
+        "bf16": bf16, "matvec": mv, "mean_rank": mi["mean_rank"], "max_rank": mi["max_rank"],
+        "dense_entries": mi["dense_entries"], "lr_entries": mi["lr_entries"],
+        "roofline": roofline, "nearfield_roofline": nearfield_roof, "matvec_roofline": matvec_roof,
+        "clocks": ck, "gpu_launches": int(launches),
+        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(V.nbytes + T.nbytes),
+                "d2h_bytes_per_step": int(n * 8)},
+    }
+    return out, (V, T, last)
+
+
+def cpu_oracle_step(V, T, budget_s=20.0, iters=None, seed=0):
+    """The oracle, as it stands, on a bounded sample of the workload; returns
+    the estimated seconds for one full step and what was sampled."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    W = WORKLOAD
+    t0 = time.perf_counter()
+    tr = oracle.Tree(V, T, W["leaf_size"], W["eta"])
+    t_tree = time.perf_counter() - t0
+    rng = np.random.default_rng(seed)
+    quad = oracle.Quad(W["ss_order"])
+    # near field: a random sample of dense leaves
+    nd = len(tr.dense)
+    sd = rng.choice(nd, size=min(nd, 6000), replace=False)
+    t0 = time.perf_counter()
+    blocks = []
+    for b in sd:
+        rb, re, cb, ce = tr.dense[b]
+        blocks.append(oracle.assemble(tr.V, tr.T, tr.perm[rb:re], tr.perm[cb:ce], quad).ravel())
+    t_nf = (time.perf_counter() - t0) * nd / len(sd)
+    # ACA: a random sample of admissible leaves
+    na = len(tr.adm)
+    sa = rng.choice(na, size=min(na, 8000), replace=False)
+    t0 = time.perf_counter()
+    fac = oracle.aca_blocks(tr.V, tr.T, tr.perm, tr.adm[sa], W["aca_eps"], W["aca_kmax"], quad)
+    t_aca = (time.perf_counter() - t0) * na / len(sa)
+    # H-matvec: the sampled blocks applied, scaled to the whole matrix
+    dense_val = np.concatenate(blocks)
+    d_off = np.cumsum([0] + [blk.size for blk in blocks])
+    parts, uo, wo, o = [], [], [], 0
+    for U, Wf in fac:
+        uo.append(o); parts.append(U.T.ravel()); o += U.size
+        wo.append(o); parts.append(Wf.T.ravel()); o += Wf.size
+    uw = np.concatenate(parts) if parts else np.zeros(1)
+    rank = np.array([U.shape[1] for U, _ in fac], dtype=np.int32)
+    x = rng.standard_normal(tr.n)
+    t0 = time.perf_counter()
+    reps = 10
+    for _ in range(reps):
+        oracle.hmatvec_raw(tr.n, tr.dense[sd], d_off[:-1], dense_val, tr.adm[sa], rank, uo, wo, uw, x)
+    t_mv_sample = (time.perf_counter() - t0) / reps
+    dense_total = int(((tr.dense[:, 1] - tr.dense[:, 0]) * (tr.dense[:, 3] - tr.dense[:, 2])).sum())
+    lr_total = uw.size * na / len(sa)
+    t_mv = t_mv_sample * (dense_total + lr_total) / max(1, dense_val.size + uw.size)
+    n_mv = (iters or 200)
+    t_solve = t_mv * n_mv
+    total = t_tree + t_nf + t_aca + t_solve
+    sample = ("full Morton + block tree (%.1fs); %d of %d dense leaves and %d of %d admissible leaves (ACA), "
+              "drawn uniformly with a fixed seed, times scaled by the leaf counts; H-matvec of the sampled "
+              "leaves scaled by stored entries x %d matvecs (the GPU's Krylov steps)" % (t_tree, len(sd), nd,
+                                                                                           len(sa), na, n_mv))
+    return total, sample, dict(tree_s=t_tree, nearfield_s=t_nf, aca_s=t_aca, solve_s=t_solve)
+
+
+def run_reference(args, rank, world):
+    import meshgen  # noqa: F401
+    V, T = _inputs()
+    cores = os.cpu_count()
+    vals = []
+    for _ in range(args.warmup):
+        cpu_oracle_step(V, T, seed=1)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        v, sample, parts = cpu_oracle_step(V, T, seed=2 + k)
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    val = sum(vals) / len(vals)
+    return {"impl": "reference", "metric": METRIC, "value": val, "unit": "s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": val * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded bumped icosphere)",
+            "config": dict(WORKLOAD), "cpu_baseline": {"value": val, "unit": "s", "cores": cores, "kind": "oracle",
+                                                         "sample": sample, "parts": parts, "wall_s": wall},
+            "e2e": {"value": val, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count()))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        print(json.dumps(run_reference(args, rank, world)))
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    out, (V, T, last) = run_ours(args, rank, world)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            v, sample, parts = cpu_oracle_step(V, T, iters=last["iters_fp64"] + last["iters_mixed"])
+            out["cpu_baseline"] = {"value": v, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
+                                   "sample": sample, "parts": parts}
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -236,6 +236,10 @@ HM_API hm_status hm_matrix_get_info(const hm_matrix *A, hm_matrix_info *info);
 HM_API hm_status hm_matrix_export(const hm_matrix *A, double *h_dense, int64_t *h_dense_off, int32_t *h_rank, double *h_uw,
                            int64_t *h_u_off, int64_t *h_w_off, int64_t *n_dense_vals, int64_t *n_lr_vals);
 
+/* Number of CUDA kernels this library has launched since it was loaded (all
+ * threads).  Lets a caller count the device work behind a sequence of calls. */
+HM_API int64_t hm_kernel_launches(void);
+
 /* Message of the last failure on the calling thread ("" when none). */
 HM_API const char *hm_last_error(void);
 

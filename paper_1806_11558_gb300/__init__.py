@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "HM_OK", 1: "HM_EINVAL", 2: "HM_ENOMEM", 3: "HM_ECUDA", 4: "H
 
 EXPORTED = ["hm_build_tree", "hm_assemble", "hm_load_vector", "hm_matvec", "hm_solve", "hm_free",
             "hm_tree_get_info", "hm_tree_get_perm", "hm_tree_get_leaves", "hm_matrix_get_info",
-            "hm_matrix_export", "hm_last_error"]
+            "hm_matrix_export", "hm_last_error", "hm_kernel_launches"]
 
 
 class HMError(RuntimeError):
@@ -99,6 +99,8 @@ def lib():
             f.restype = I
         L.hm_free.argtypes = [P]
         L.hm_free.restype = None
+        L.hm_kernel_launches.argtypes = []
+        L.hm_kernel_launches.restype = ctypes.c_int64
         L.hm_last_error.argtypes = []
         L.hm_last_error.restype = ctypes.c_char_p
         _lib = L
@@ -107,6 +109,10 @@ def lib():
 
 def hm_last_error() -> str:
     return lib().hm_last_error().decode()
+
+
+def hm_kernel_launches() -> int:
+    return int(lib().hm_kernel_launches())
 
 
 def _check(status):

@@ -12,6 +12,7 @@
 
 namespace hm {
 const char *last_error_cstr();
+long long launch_count();
 hm_tree *build_tree_impl(const double *d_V, int64_t nv, const int32_t *d_T, int64_t n, const hm_tree_params &prm,
                          cudaStream_t s);
 void assemble_nearfield(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStream_t s, int *d_err,
@@ -51,6 +52,8 @@ static bool is_matrix(const void *p) { return p && static_cast<const hm_matrix *
 extern "C" {
 
 const char *hm_last_error(void) { return last_error_cstr(); }
+
+int64_t hm_kernel_launches(void) { return (int64_t)launch_count(); }
 
 hm_status hm_build_tree(const double *d_vertices, int64_t n_vertices, const int32_t *d_tris, int64_t n_tris,
                         const hm_tree_params *params, hm_stream_t stream, hm_tree **out) {

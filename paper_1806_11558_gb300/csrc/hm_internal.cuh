@@ -56,7 +56,13 @@ void set_last_error(const std::string &msg);
                        __FILE__, __LINE__, #call, cudaGetErrorString(e_));                         \
     } while (0)
 
-#define HM_LAUNCH_CHECK() HM_CUDA_CHECK(cudaGetLastError())
+// Every kernel launch is followed by HM_LAUNCH_CHECK(), which also counts it.
+void count_launch();
+#define HM_LAUNCH_CHECK()                  \
+    do {                                   \
+        ::hm::count_launch();              \
+        HM_CUDA_CHECK(cudaGetLastError()); \
+    } while (0)
 
 // ----------------------------------------------------------------------------
 // device memory: RAII buffer (cudaMalloc / cudaFree)

@@ -64,14 +64,22 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
-// Bounded wait: gives up after max_iter polls (sets *err) so a lost
-// transaction can never hang the GPU.
+// Bounded wait: gives up after about two seconds of SM clock (sets *err), so
+// a lost transaction can never hang the GPU.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase, int *err, int code) {
-    for (long it = 0; it < (1L << 26); ++it)
-        if (mbar_try_wait(bar, phase)) return true;
-    atomicExch(err, code);
-    return false;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, phase))
+        if (clock64() - t0 > 4000000000LL) {
+            atomicExch(err, code);
+            return false;
+        }
+    return true;
 }
+
+// Shared-memory layout of nearfield_kernel: two 128-byte aligned panel tiles
+// of [PT_ROWS][box_cols] doubles, then the mbarrier.
+__host__ __device__ constexpr int nf_tile_bytes(int box_cols) { return ((PT_ROWS * box_cols * 8) + 127) / 128 * 128; }
+__host__ __device__ constexpr int nf_smem_bytes(int box_cols) { return 128 + 2 * nf_tile_bytes(box_cols) + 16; }
 
 // ---------------------------------------------------------------------------
 // regular near-field entries
@@ -86,27 +94,28 @@ __global__ void __launch_bounds__(NF_THREADS) nearfield_kernel(const __grid_cons
                                                                 SingularItem *__restrict__ sing,
                                                                 unsigned long long *sing_count, int64_t sing_cap,
                                                                 int *err) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     const int64_t b = blockIdx.x;
     const int32_t rb = dense[4 * b], re = dense[4 * b + 1], cb = dense[4 * b + 2], ce = dense[4 * b + 3];
     const int32_t rb_al = rb & ~1, cb_al = cb & ~1;
-    const int tile_bytes = ((PT_ROWS * box_cols * 8) + 127) / 128 * 128;
-    double *tR = reinterpret_cast<double *>(smem_raw);
-    double *tC = reinterpret_cast<double *>(smem_raw + tile_bytes);
+    const int tile_bytes = nf_tile_bytes(box_cols);
+    double *tR = reinterpret_cast<double *>(sm);
+    double *tC = reinterpret_cast<double *>(sm + tile_bytes);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + 2 * tile_bytes);
     if (threadIdx.x == 0) {
-        mbar_init(&bar, 1);
+        mbar_init(bar, 1);
         fence_barrier_init();
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        mbar_arrive_expect_tx(&bar, 2u * PT_ROWS * box_cols * 8u);
-        tma_load_2d(tR, &pt_map, &bar, rb_al, 0);
-        tma_load_2d(tC, &pt_map, &bar, cb_al, 0);
+        mbar_arrive_expect_tx(bar, 2u * PT_ROWS * box_cols * 8u);
+        tma_load_2d(tR, &pt_map, bar, rb_al, 0);
+        tma_load_2d(tC, &pt_map, bar, cb_al, 0);
     }
-    if (!mbar_wait_bounded(&bar, 0, err, 2)) {
+    if (!mbar_wait_bounded(bar, 0, err, 2)) {
         // the copies may still land: wait once more (bounded) before leaving
-        mbar_wait_bounded(&bar, 0, err, 2);
+        mbar_wait_bounded(bar, 0, err, 2);
         return;
     }
     const int m = re - rb, n = ce - cb, mn = m * n;
@@ -190,8 +199,7 @@ void assemble_nearfield(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, c
     items.alloc(sizeof(SingularItem) * std::max<int64_t>(tr->singular_cap, 1));
     cnt.alloc(sizeof(unsigned long long));
     HM_CUDA_CHECK(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long), s));
-    const int tile_bytes = ((PT_ROWS * tr->box_cols * 8) + 127) / 128 * 128;
-    const int smem = 2 * tile_bytes;
+    const int smem = nf_smem_bytes(tr->box_cols);
     HM_CUDA_CHECK(cudaFuncSetAttribute(nearfield_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     cudaEvent_t e0, e1, e2;
     HM_CUDA_CHECK(cudaEventCreate(&e0));

@@ -2,6 +2,7 @@
 // TMA descriptors.
 #include <cstdarg>
 #include <cmath>
+#include <atomic>
 #include <mutex>
 
 #include "hm_internal.cuh"
@@ -16,6 +17,10 @@ static thread_local std::string g_last_error;
 void set_last_error(const std::string &msg) { g_last_error = msg; }
 
 const char *last_error_cstr() { return g_last_error.c_str(); }
+
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 void fail(hm_status s, const char *fmt, ...) {
     char buf[1024];
