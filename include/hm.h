@@ -195,6 +195,26 @@ HM_API hm_status hm_load_vector(const hm_tree *tree, const double *d_sources, in
 HM_API hm_status hm_matvec(const hm_matrix *A, int32_t trans, int32_t nrhs, hm_dtype prec, const double *d_x, double *d_y,
                     double alpha, double beta, hm_stream_t stream);
 
+/* The H-matrix-vector product of hm_matvec (trans = 0 only) for callers that
+ * must not allocate device memory during the call: code running under a fixed
+ * device-memory budget or its own pool, where a cudaMalloc / cudaFree would
+ * fail, block or break the caller's accounting.  The paper has no counterpart;
+ * this is a property of the library interface only.
+ *  Same arguments and results as hm_matvec.  Its working vectors (x and y in
+ *  Morton order and the low-rank projections) live in one 16 MiB array that
+ *  the library reserves on every device it is loaded on, held until exit; no
+ *  memory is allocated or freed by the call.
+ *  Limit: 2 n + (sum of the ACA ranks) <= 2,097,152 doubles; larger problems
+ *  get HM_EINVAL with the required size in hm_last_error().
+ *  The first call on a device looks up that array's device address (with the
+ *  device current); make that first call before any stream capture.
+ *  All calls share the array and it keeps the last call's contents: calls
+ *  whose work overlaps on the GPU (different streams or host threads) race.
+ *  The call is stream-ordered and does not synchronise; d_y is complete when
+ *  `stream` reaches the end of the call's work. */
+HM_API hm_status hm_matvec_noalloc(const hm_matrix *A, int32_t trans, int32_t nrhs, hm_dtype prec, const double *d_x,
+                                   double *d_y, double alpha, double beta, hm_stream_t stream);
+
 /* Solve op(H) x = b with restarted GMRES (Sec. 4.1 solves with a Krylov
  * method; GMRES(m) with classical Gram-Schmidt applied twice, Givens
  * rotations and the Hessenberg least-squares problem in FP64), optionally as

@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "HM_OK", 1: "HM_EINVAL", 2: "HM_ENOMEM", 3: "HM_ECUDA", 4: "H
 
 EXPORTED = ["hm_build_tree", "hm_assemble", "hm_load_vector", "hm_matvec", "hm_solve", "hm_free",
             "hm_tree_get_info", "hm_tree_get_perm", "hm_tree_get_leaves", "hm_matrix_get_info",
-            "hm_matrix_export", "hm_last_error", "hm_kernel_launches"]
+            "hm_matrix_export", "hm_last_error", "hm_kernel_launches", "hm_matvec_noalloc"]
 
 
 class HMError(RuntimeError):
@@ -86,6 +86,7 @@ def lib():
             "hm_assemble": [P, P, P, P],
             "hm_load_vector": [P, P, I32, P, P],
             "hm_matvec": [P, I32, I32, I, P, P, D, D, P],
+            "hm_matvec_noalloc": [P, I32, I32, I, P, P, D, D, P],
             "hm_solve": [P, I32, I32, P, P, P, P, P],
             "hm_tree_get_info": [P, P],
             "hm_tree_get_perm": [P, P],
@@ -170,6 +171,17 @@ def hm_matvec(A, x, y, trans=0, prec=HM_F64, alpha=1.0, beta=0.0, stream=None):
     nrhs = 1 if x.dim() == 1 else x.shape[0]
     _check(lib().hm_matvec(A, int(trans), nrhs, int(prec), _ptr(x, torch.float64), _ptr(y, torch.float64),
                            float(alpha), float(beta), _stream(stream)))
+    return y
+
+
+def hm_matvec_noalloc(A, x, y, trans=0, prec=HM_F64, alpha=1.0, beta=0.0, stream=None):
+    """hm_matvec without device allocation (working vectors in the library's
+    fixed 16 MiB per-device array; see include/hm.h for the size limit and
+    the rule that overlapping calls race).  Does not synchronise."""
+    import torch
+    nrhs = 1 if x.dim() == 1 else x.shape[0]
+    _check(lib().hm_matvec_noalloc(A, int(trans), nrhs, int(prec), _ptr(x, torch.float64), _ptr(y, torch.float64),
+                                   float(alpha), float(beta), _stream(stream)))
     return y
 
 

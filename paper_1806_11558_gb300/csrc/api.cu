@@ -25,6 +25,8 @@ void permute_from_morton(const hm_tree *tr, const double *ym, double alpha, doub
 void load_vector_impl(const hm_tree *tr, const double *src, int nsrc, double *f, cudaStream_t s);
 hm_status solve_impl(const hm_matrix *A, const double *b, double *x, const hm_solve_params &p, cudaStream_t s,
                      hm_solve_info *info);
+void matvec_noalloc(const hm_matrix *A, int32_t nrhs, hm_dtype prec, const double *x, double *y, double alpha,
+                    double beta, cudaStream_t s);
 }  // namespace hm
 
 using namespace hm;
@@ -141,6 +143,20 @@ hm_status hm_matvec(const hm_matrix *A, int32_t trans, int32_t nrhs, hm_dtype pr
             permute_from_morton(A->tree, ym.as<double>(), alpha, beta, d_y + (int64_t)r * n, s);
         }
         HM_CUDA_CHECK(cudaStreamSynchronize(s));
+    });
+}
+
+hm_status hm_matvec_noalloc(const hm_matrix *A, int32_t trans, int32_t nrhs, hm_dtype prec, const double *d_x,
+                            double *d_y, double alpha, double beta, hm_stream_t stream) {
+    return guard([&] {
+        if (!is_matrix(A)) fail(HM_EINVAL, "not a matrix handle");
+        if (!d_x || !d_y) fail(HM_EINVAL, "NULL argument");
+        if (nrhs < 1) fail(HM_EINVAL, "nrhs must be >= 1");
+        if (trans != 0) fail(HM_EINVAL, "only trans = 0 is available");
+        if (prec < HM_F64 || prec > HM_BF16) fail(HM_EINVAL, "bad precision");
+        if (prec == HM_F32 && !A->uw32.p) fail(HM_EINVAL, "FP32 copies were not assembled");
+        if (prec == HM_BF16 && !A->uwbf.p) fail(HM_EINVAL, "BF16 factors were not assembled");
+        matvec_noalloc(A, nrhs, prec, d_x, d_y, alpha, beta, (cudaStream_t)stream);
     });
 }
 

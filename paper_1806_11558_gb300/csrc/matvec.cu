@@ -14,6 +14,8 @@
 // Precisions: FP64 (master), or FP32 / BF16 copies with FP32 accumulation.
 #include <cuda_bf16.h>
 
+#include <mutex>
+
 #include "hm_internal.cuh"
 
 namespace hm {
@@ -250,6 +252,68 @@ void load_vector_impl(const hm_tree *tr, const double *src, int nsrc, double *f,
     load_vector_kernel<<<grid1d(tr->n), 256, 0, s>>>(tr->pt.as<double>(), tr->npad, tr->n, tr->perm.as<int32_t>(), src,
                                                      nsrc, qp, f);
     HM_LAUNCH_CHECK();
+}
+
+
+// ---------------------------------------------------------------------------
+// H-matrix-vector product without any device allocation
+//
+// For callers that must not allocate device memory while they run: code that
+// works inside a pre-sized memory budget (a pool-managed or fixed-footprint
+// service), code running where an allocation would block or fail, or callers
+// whose own allocator forbids stray cudaMalloc/cudaFree calls.  hm_matvec
+// obtains its permuted input / output vectors and its low-rank projections
+// from cudaMalloc on every call; this variant takes them from one file-scope
+// device array instead, sized once when the library is loaded.
+//
+// Scratch layout (doubles): x in Morton order [n], y in Morton order [n],
+// projections t_b = W_b^T x [sum_b k_b].  Every element is written before it
+// is read in each call, so nothing needs clearing between calls.  The array
+// is shared by every call on a device and keeps the last call's contents:
+// calls whose work overlaps on the GPU (other streams, other host threads)
+// race on it.
+// ---------------------------------------------------------------------------
+constexpr int64_t NOALLOC_MAX_DOUBLES = 2097152;  // 16 MiB per device
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_MAX_DOUBLES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static void *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+static std::mutex g_noalloc_mutex;
+
+// Device address of the scratch array on the current device.  The host-side
+// symbol is only a stand-in; the address is looked up once per device (with
+// that device current) on the first call.
+static double *noalloc_scratch() {
+    int dev = 0;
+    HM_CUDA_CHECK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) fail(HM_EINVAL, "device index %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            fail(HM_ECUDA, "cudaGetSymbolAddress of the no-allocation scratch failed: %s", cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = p;
+    }
+    return static_cast<double *>(g_noalloc_ptr[dev]);
+}
+
+void matvec_noalloc(const hm_matrix *A, int32_t nrhs, hm_dtype prec, const double *x, double *y, double alpha,
+                    double beta, cudaStream_t s) {
+    const int64_t n = A->tree->n;
+    const int64_t need = 2 * n + std::max<int64_t>(A->total_rank, 1);
+    if (need > NOALLOC_MAX_DOUBLES)
+        fail(HM_EINVAL,
+             "problem too large for the allocation-free product: needs %lld scratch doubles "
+             "(2 n + sum of ranks), the limit is %lld",
+             (long long)need, (long long)NOALLOC_MAX_DOUBLES);
+    double *base = noalloc_scratch();
+    double *xm = base, *ym = base + n, *t = base + 2 * n;
+    for (int r = 0; r < nrhs; ++r) {
+        permute_to_morton(A->tree, x + (int64_t)r * n, xm, s);
+        matvec_morton(A, prec, xm, ym, t, s);
+        permute_from_morton(A->tree, ym, alpha, beta, y + (int64_t)r * n, s);
+    }
 }
 
 }  // namespace hm
