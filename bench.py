@@ -44,9 +44,12 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+CASE = "precision"
+
+
 def _inputs():
     import meshgen
-    cfg = meshgen.config("precision")
+    cfg = meshgen.config(CASE)
     return cfg["V"], cfg["T"]
 
 
@@ -156,6 +159,11 @@ def run_ours(args, rank, world):
         hm.hm_free(tree)
         return t
 
+    if args.profile_step:
+        r = step(Vd, Td)
+        return {"profile_step": args.case, "step_s": r["step_s"], "aca_s": r["minfo"]["s_aca"],
+                "nearfield_s": r["minfo"]["s_nearfield"], "iters_fp64": r["iters_fp64"],
+                "iters_mixed": r["iters_mixed"]}, None
     for _ in range(args.warmup):
         step(Vd, Td)
     if world > 1:
@@ -371,7 +379,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", default="precision",
+                    help="mesh recipe of meshgen.config (default: the precision workload); other cases are "
+                         "for profiling and parity runs, not bench lines")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="run exactly one step (no warm-up, no extras) and print its phase times")
     args = ap.parse_args()
+    global CASE
+    CASE = args.case
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count()))
@@ -385,7 +400,12 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         dist.init_process_group("nccl")
-    out, (V, T, last) = run_ours(args, rank, world)
+    out, extra = run_ours(args, rank, world)
+    if args.profile_step:
+        if rank == 0:
+            print(json.dumps(out))
+        return
+    V, T, last = extra
     if rank == 0:
         if not args.no_cpu_baseline:
             v, sample, parts = cpu_oracle_step(V, T, iters=last["iters_fp64"] + last["iters_mixed"])

@@ -201,11 +201,13 @@ HM_API hm_status hm_matvec(const hm_matrix *A, int32_t trans, int32_t nrhs, hm_d
  * fail, block or break the caller's accounting.  The paper has no counterpart;
  * this is a property of the library interface only.
  *  Same arguments and results as hm_matvec.  Its working vectors (x and y in
- *  Morton order and the low-rank projections) live in one 16 MiB array that
+ *  Morton order, the low-rank projections, and their FP32 roundings for the
+ *  low-precision copies) live in one 16 MiB array that
  *  the library reserves on every device it is loaded on, held until exit; no
  *  memory is allocated or freed by the call.
- *  Limit: 2 n + (sum of the ACA ranks) <= 2,097,152 doubles; larger problems
- *  get HM_EINVAL with the required size in hm_last_error().
+ *  Limit: 2 n + K doubles plus n + K floats must fit in 2,097,152 doubles
+ *  (K = sum of the ACA ranks; about 2.5 n + 1.5 K <= 2,097,152); larger
+ *  problems get HM_EINVAL with the required size in hm_last_error().
  *  The first call on a device looks up that array's device address (with the
  *  device current); make that first call before any stream capture.
  *  All calls share the array and it keeps the last call's contents: calls

@@ -26,6 +26,7 @@
 #include <algorithm>
 
 #include "entry.cuh"
+#include "ff.cuh"
 
 namespace hm {
 
@@ -35,6 +36,7 @@ constexpr int SMALL_MAX_DIM = 256;  // warp-mode blocks: m, n <= this
 
 struct AcaArgs {
     const double *pt;
+    const float *pf;
     int64_t npad;
     const double *V;
     const int32_t *adm;
@@ -88,7 +90,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // shared scratch of one ACA worker (CTA or warp)
 struct AcaShared {
-    double *fix;    // [32]  fixed panel record
+    float *fix;     // [64]  fixed panel record (float panel table row)
     double *vec;    // [kmax] U(i_r, :) or W(j_r, :)
     double *red;    // [ACA_WARPS] sum partials (CTA mode)
     Best *bred;     // [ACA_WARPS] argmax partials (CTA mode)
@@ -140,18 +142,22 @@ struct Grp {
 
 __device__ __forceinline__ bool bit(const uint32_t *bm, int k) { return (bm[k >> 5] >> (k & 31)) & 1u; }
 
-// entry (row panel record r, column panel record c) of the Galerkin matrix
-__device__ __forceinline__ double aca_entry(const double *r, const double *c, const AcaArgs &A) {
-    const int32_t a[3] = {(int32_t)r[PT_VID], (int32_t)r[PT_VID + 1], (int32_t)r[PT_VID + 2]};
-    const int32_t b[3] = {(int32_t)c[PT_VID], (int32_t)c[PT_VID + 1], (int32_t)c[PT_VID + 2]};
+// entry (row panel record r at Morton position gi, column panel record c at
+// gj) of the Galerkin matrix: far-field pairs in float-float, touching pairs
+// (which admissible blocks do not contain in practice) by the FP64 rule
+__device__ __forceinline__ double aca_entry(const float *r, int64_t gi, const float *c, int64_t gj, const AcaArgs &A) {
+    const int32_t a[3] = {__float_as_int(r[PF_VID]), __float_as_int(r[PF_VID + 1]), __float_as_int(r[PF_VID + 2])};
+    const int32_t b[3] = {__float_as_int(c[PF_VID]), __float_as_int(c[PF_VID + 1]), __float_as_int(c[PF_VID + 2])};
     const int kind = shared_vertices(a, b);
-    if (kind) return singular_entry_serial(A.V, a, b, kind, r[PT_AREA], c[PT_AREA], A.qp);
-    return regular_entry(r, 1, c, 1, A.qp);
+    if (kind)
+        return singular_entry_serial(A.V, a, b, kind, A.pt[(int64_t)PT_AREA * A.npad + gi],
+                                     A.pt[(int64_t)PT_AREA * A.npad + gj], A.qp);
+    return regular_entry_ff(r, 1, c, 1, A.qp.w_h, A.qp.w_l);
 }
 
-__device__ __forceinline__ void load_panel(const AcaArgs &A, int64_t k, double *rec) {
+__device__ __forceinline__ void load_panel(const AcaArgs &A, int64_t k, float *rec) {
 #pragma unroll
-    for (int q = 0; q < PT_ROWS; ++q) rec[q] = A.pt[(int64_t)q * A.npad + k];
+    for (int q = 0; q < PF_ROWS; ++q) rec[q] = A.pf[(int64_t)q * A.npad + k];
 }
 
 // ACA of one block; U (m x kmax) and W (n x kmax) column-major in scratch.
@@ -169,16 +175,16 @@ __device__ int aca_block(const AcaArgs &A, int rb, int m, int cb, int n, double 
     int r = 0, i = 0;
     double s2 = 0.0, delta1 = 0.0;
     bool converged = false;
-    double rec[PT_ROWS];
+    float rec[PF_ROWS];
     while (r < rmax) {
         // ---- residual of row i ----
-        if (t < PT_ROWS) sh.fix[t] = A.pt[(int64_t)t * A.npad + rb + i];
+        for (int q = t; q < PF_ROWS; q += gs) sh.fix[q] = A.pf[(int64_t)q * A.npad + rb + i];
         for (int l = t; l < r; l += gs) sh.vec[l] = U[(int64_t)l * m + i];
         G::sync();
         Best best{-1.0, 0x7fffffff, 0.0};
         for (int j = t; j < n; j += gs) {
             load_panel(A, cb + j, rec);
-            double v = aca_entry(sh.fix, rec, A);
+            double v = aca_entry(sh.fix, rb + i, rec, cb + j, A);
             for (int l = 0; l < r; ++l) v -= sh.vec[l] * W[(int64_t)l * n + j];
             W[(int64_t)r * n + j] = v;
             if (!bit(sh.ucol, j)) {
@@ -211,14 +217,14 @@ __device__ int aca_block(const AcaArgs &A, int rb, int m, int cb, int n, double 
             nw2 += w * w;
         }
         // ---- residual of column jp ----
-        if (t < PT_ROWS) sh.fix[t] = A.pt[(int64_t)t * A.npad + cb + jp];
+        for (int q = t; q < PF_ROWS; q += gs) sh.fix[q] = A.pf[(int64_t)q * A.npad + cb + jp];
         for (int l = t; l < r; l += gs) sh.vec[l] = W[(int64_t)l * n + jp];
         G::sync();
         double nu2 = 0.0;
         Best nb{-1.0, 0x7fffffff, 0.0};
         for (int k = t; k < m; k += gs) {
             load_panel(A, rb + k, rec);
-            double u = aca_entry(rec, sh.fix, A);
+            double u = aca_entry(rec, rb + k, sh.fix, cb + jp, A);
             for (int l = 0; l < r; ++l) u -= sh.vec[l] * U[(int64_t)l * m + k];
             U[(int64_t)r * m + k] = u;
             nu2 += u * u;
@@ -268,13 +274,19 @@ __device__ void aca_store(const AcaArgs &A, int64_t b, int m, int n, int k, cons
         return;
     }
     if (t == 0) A.uw_off[b] = (int64_t)off;
+    // U_b column-major (m x k); W_b row-major (n x k): row j of W_b holds the
+    // k coefficients of column j of the block, which the projection W_b^T x
+    // reads contiguously
     double *dst = A.arena + off;
     const int64_t mk = (int64_t)m * k, nk = (int64_t)n * k;
     for (int64_t e = t; e < mk; e += gs) dst[e] = U[e];
-    for (int64_t e = t; e < nk; e += gs) dst[mk + e] = W[e];
+    for (int64_t e = t; e < nk; e += gs) {
+        const int64_t j = e / k, l = e - j * k;
+        dst[mk + e] = W[l * n + j];
+    }
 }
 
-__global__ void __launch_bounds__(ACA_THREADS) aca_kernel(AcaArgs A) {
+__global__ void __launch_bounds__(ACA_THREADS, 2) aca_kernel(AcaArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double s_red[ACA_WARPS];
     __shared__ Best s_bred[ACA_WARPS];
@@ -285,7 +297,7 @@ __global__ void __launch_bounds__(ACA_THREADS) aca_kernel(AcaArgs A) {
     {
         AcaShared sh;
         double *d = reinterpret_cast<double *>(smem_raw);
-        sh.fix = d;
+        sh.fix = reinterpret_cast<float *>(d);
         sh.vec = d + 32;
         sh.red = s_red;
         sh.bred = s_bred;
@@ -318,7 +330,7 @@ __global__ void __launch_bounds__(ACA_THREADS) aca_kernel(AcaArgs A) {
         AcaShared sh;
         const int words = (SMALL_MAX_DIM + 31) / 32;
         double *d = reinterpret_cast<double *>(smem_raw) + (int64_t)warp * (32 + MAX_KMAX + words);
-        sh.fix = d;
+        sh.fix = reinterpret_cast<float *>(d);
         sh.vec = d + 32;
         sh.red = nullptr;
         sh.bred = nullptr;
@@ -422,6 +434,7 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
 
     AcaArgs a{};
     a.pt = tr->pt.as<double>();
+    a.pf = tr->pf.as<float>();
     a.npad = tr->npad;
     a.V = tr->V.as<double>();
     a.adm = tr->adm.as<int32_t>();

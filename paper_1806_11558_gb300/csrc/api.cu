@@ -19,7 +19,10 @@ void assemble_nearfield(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, c
                         double *sec_regular, double *sec_singular);
 void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStream_t s, double *sec);
 void make_low_copies(hm_matrix *A, cudaStream_t s);
-void matvec_morton(const hm_matrix *A, hm_dtype prec, const double *xm, double *ym, double *t, cudaStream_t s);
+void matvec_morton(const hm_matrix *A, hm_dtype prec, const MatvecWork &w, cudaStream_t s);
+int64_t matvec_work_doubles(const hm_matrix *A);
+MatvecWork matvec_work_at(const hm_matrix *A, double *base);
+void build_lr_desc(hm_matrix *A, cudaStream_t s);
 void permute_to_morton(const hm_tree *tr, const double *x, double *xm, cudaStream_t s);
 void permute_from_morton(const hm_tree *tr, const double *ym, double alpha, double beta, double *y, cudaStream_t s);
 void load_vector_impl(const hm_tree *tr, const double *src, int nsrc, double *f, cudaStream_t s);
@@ -92,6 +95,7 @@ hm_status hm_assemble(const hm_tree *tree, const hm_assemble_params *params, hm_
         double sr = 0, ss = 0, sa = 0;
         assemble_nearfield(tree, A.get(), qp, s, err.as<int>(), &sr, &ss);
         assemble_aca(tree, A.get(), qp, s, &sa);
+        build_lr_desc(A.get(), s);
         make_low_copies(A.get(), s);
         HM_CUDA_CHECK(cudaStreamSynchronize(s));
         const int e = read_scalar(err.as<int>(), s);
@@ -133,14 +137,13 @@ hm_status hm_matvec(const hm_matrix *A, int32_t trans, int32_t nrhs, hm_dtype pr
         if (prec < HM_F64 || prec > HM_BF16) fail(HM_EINVAL, "bad precision");
         cudaStream_t s = (cudaStream_t)stream;
         const int64_t n = A->tree->n;
-        DBuf xm, ym, t;
-        xm.alloc(sizeof(double) * n);
-        ym.alloc(sizeof(double) * n);
-        t.alloc(sizeof(double) * std::max<int64_t>(A->total_rank, 1));
+        DBuf work;
+        work.alloc(sizeof(double) * matvec_work_doubles(A));
+        const MatvecWork w = matvec_work_at(A, work.as<double>());
         for (int r = 0; r < nrhs; ++r) {
-            permute_to_morton(A->tree, d_x + (int64_t)r * n, xm.as<double>(), s);
-            matvec_morton(A, prec, xm.as<double>(), ym.as<double>(), t.as<double>(), s);
-            permute_from_morton(A->tree, ym.as<double>(), alpha, beta, d_y + (int64_t)r * n, s);
+            permute_to_morton(A->tree, d_x + (int64_t)r * n, w.xm, s);
+            matvec_morton(A, prec, w, s);
+            permute_from_morton(A->tree, w.ym, alpha, beta, d_y + (int64_t)r * n, s);
         }
         HM_CUDA_CHECK(cudaStreamSynchronize(s));
     });
@@ -272,17 +275,23 @@ hm_status hm_matrix_export(const hm_matrix *A, double *h_dense, int64_t *h_dense
                 for (int j = 0; j < n; ++j) h_dense[o + (int64_t)i * n + j] = arena[base[b] + (int64_t)i * ld[b] + j];
             o += (int64_t)m * n;
         }
+        std::vector<double> fac(std::max<int64_t>(A->lr_entries, 1));
         if (na) {
             HM_CUDA_CHECK(cudaMemcpy(adm.data(), tr->adm.p, sizeof(int32_t) * 4 * na, cudaMemcpyDeviceToHost));
             HM_CUDA_CHECK(cudaMemcpy(rank.data(), A->rank.p, sizeof(int32_t) * na, cudaMemcpyDeviceToHost));
             HM_CUDA_CHECK(cudaMemcpy(uwo.data(), A->uw_off.p, sizeof(int64_t) * na, cudaMemcpyDeviceToHost));
-            HM_CUDA_CHECK(cudaMemcpy(h_uw, A->uw.p, sizeof(double) * A->lr_entries, cudaMemcpyDeviceToHost));
+            HM_CUDA_CHECK(cudaMemcpy(fac.data(), A->uw.p, sizeof(double) * A->lr_entries, cudaMemcpyDeviceToHost));
         }
+        // U_b as stored (column-major); W_b stored row-major, exported column-major
         for (int64_t b = 0; b < na; ++b) {
-            const int m = adm[4 * b + 1] - adm[4 * b];
-            h_rank[b] = rank[b];
+            const int m = adm[4 * b + 1] - adm[4 * b], n = adm[4 * b + 3] - adm[4 * b + 2], k = rank[b];
+            h_rank[b] = k;
             h_u_off[b] = uwo[b];
-            h_w_off[b] = uwo[b] + (int64_t)m * rank[b];
+            h_w_off[b] = uwo[b] + (int64_t)m * k;
+            for (int64_t e = 0; e < (int64_t)m * k; ++e) h_uw[uwo[b] + e] = fac[uwo[b] + e];
+            for (int j = 0; j < n; ++j)
+                for (int l = 0; l < k; ++l)
+                    h_uw[h_w_off[b] + (int64_t)l * n + j] = fac[h_w_off[b] + (int64_t)j * k + l];
         }
     });
 }

@@ -13,7 +13,7 @@
 //                    column order (no padding).  Block b's entry (i, j) lives at
 //                    dense_base[b] + i * dense_ld[b] + j.
 //   low-rank factors: per admissible leaf b, U_b (m x k_b, column-major) then
-//                    W_b (n x k_b, column-major) at uw_off[b]; block ~ U_b W_b^T.
+//                    W_b (n x k_b, row-major) at uw_off[b]; block ~ U_b W_b^T.
 #pragma once
 
 #include <cuda.h>
@@ -103,6 +103,8 @@ struct QuadParams {
     int ss_n;            // Gauss-Legendre order on [0, 1] for touching pairs
     double gx[MAX_SS];
     double gw[MAX_SS];
+    float w_h[NQ];       // the 7 weights as float pairs (w = w_h + w_l)
+    float w_l[NQ];
 };
 
 // 7-point rule from its closed form; Gauss-Legendre nodes by Newton's method
@@ -142,6 +144,7 @@ struct hm_tree {
     hm::DBuf V;        // [nv][3] double, copy of the caller's vertices
     hm::DBuf trim;     // [n][3] int32, triangles in Morton order
     hm::DBuf pt;       // [PT_ROWS][npad] double, panel table (Morton order)
+    hm::DBuf pf;       // [PF_ROWS][npad] float, far-field panel table (see ff.cuh)
     hm::DBuf cent;     // [n][3] double, centroids in Morton order
     hm::DBuf perm;     // [n] int32, Morton position -> original index
     hm::DBuf iperm;    // [n] int32, original index -> Morton position
@@ -175,6 +178,23 @@ struct hm_tree {
     int32_t box_cols = 0;
 };
 
+// One admissible block as seen by one leaf row cluster rho of its rows.
+struct LrDesc {
+    int64_t uoff;  // element offset of U_b(row r0(rho) - rb, 0) in the factor arena
+    int64_t toff;  // offset of t_b = W_b^T x in the projection vector
+    int32_t ld;    // m_b, the column stride of U_b
+    int32_t k;     // rank
+};
+
+// Working vectors of one H-matrix-vector product (Morton order).
+struct MatvecWork {
+    double *xm;   // [n]  input
+    double *ym;   // [n]  output
+    double *t;    // [total_rank] projections (FP64 product)
+    float *x32;   // [n]  input rounded to FP32 (low-precision products)
+    float *t32;   // [total_rank] projections (low-precision products)
+};
+
 struct hm_matrix {
     uint32_t magic = HM_MATRIX_MAGIC;
     const hm_tree *tree = nullptr;
@@ -189,5 +209,6 @@ struct hm_matrix {
     int64_t lr_entries = 0;
     hm::DBuf t_off;     // [n_adm] int64, prefix sum of ranks
     int64_t total_rank = 0;
+    hm::DBuf lr_desc;   // [lr_list size] LrDesc: U rows of each (leaf row cluster, block) pair
     hm_matrix_info info{};
 };

@@ -53,25 +53,53 @@ __global__ void scatter_perm_kernel(const double *ym, const int32_t *perm, int64
 }
 
 // ---------------------------------------------------------------------------
-// t_b = W_b^T x_sigma
+// t_b = W_b^T x_sigma, W_b row-major (n x k).  One warp per block: with
+// G = floor(32 / k) lane groups, lane (g, l) accumulates column l over rows
+// j = g, g + G, ..., so every load instruction reads G*k consecutive
+// elements; the G partials of a column are then summed in a fixed order.
 // ---------------------------------------------------------------------------
-template <class TF>
-__global__ void lr_project_kernel(const int32_t *__restrict__ adm, int64_t na, const int32_t *__restrict__ rank,
-                                  const int64_t *__restrict__ uw_off, const int64_t *__restrict__ t_off,
-                                  const TF *__restrict__ uw, const double *__restrict__ xm, double *__restrict__ t) {
+template <class TF, class TX, class TT>
+__global__ void __launch_bounds__(256) lr_project_kernel(
+    const int32_t *__restrict__ adm, int64_t na, const int32_t *__restrict__ rank, const int64_t *__restrict__ uw_off,
+    const int64_t *__restrict__ t_off, const TF *__restrict__ uw, const TX *__restrict__ x, TT *__restrict__ t) {
     using A = typename Acc<TF>::type;
-    const int lane = threadIdx.x & 31;
+    __shared__ A s_part[8][32];
+    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
     const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t b = w0; b < na; b += nw) {
+        const int k = rank[b];
+        if (k == 0) continue;
         const int32_t rb = adm[4 * b], re = adm[4 * b + 1], cb = adm[4 * b + 2], ce = adm[4 * b + 3];
-        const int m = re - rb, n = ce - cb, k = rank[b];
+        const int m = re - rb, n = ce - cb;
         const TF *W = uw + uw_off[b] + (int64_t)m * k;
-        for (int l = 0; l < k; ++l) {
+        const int64_t to = t_off[b];
+        for (int c0 = 0; c0 < k; c0 += 32) {
+            const int kc = min(32, k - c0);
+            const int G = 32 / kc;
+            const int g = lane / kc, l = lane - g * kc;
             A acc = 0;
-            for (int j = lane; j < n; j += 32) acc += ld_el<TF>(W + (int64_t)l * n + j) * (A)xm[cb + j];
-            acc = warp_reduce(acc);
-            if (lane == 0) t[t_off[b] + l] = (double)acc;
+            if (g < G) {
+                const TF *Wc = W + c0 + l;
+                int j = g;
+                for (; j + 3 * G < n; j += 4 * G) {
+                    const A w0v = ld_el<TF>(Wc + (int64_t)j * k), w1v = ld_el<TF>(Wc + (int64_t)(j + G) * k);
+                    const A w2v = ld_el<TF>(Wc + (int64_t)(j + 2 * G) * k), w3v = ld_el<TF>(Wc + (int64_t)(j + 3 * G) * k);
+                    acc += w0v * (A)x[cb + j];
+                    acc += w1v * (A)x[cb + j + G];
+                    acc += w2v * (A)x[cb + j + 2 * G];
+                    acc += w3v * (A)x[cb + j + 3 * G];
+                }
+                for (; j < n; j += G) acc += ld_el<TF>(Wc + (int64_t)j * k) * (A)x[cb + j];
+            }
+            s_part[wl][lane] = acc;
+            __syncwarp();
+            if (lane < kc) {
+                A s = 0;
+                for (int q = 0; q < G; ++q) s += s_part[wl][q * kc + lane];
+                t[to + c0 + lane] = (TT)s;
+            }
+            __syncwarp();
         }
     }
 }
@@ -81,13 +109,12 @@ __global__ void lr_project_kernel(const int32_t *__restrict__ adm, int64_t na, c
 // ---------------------------------------------------------------------------
 constexpr int ROW_THREADS = 256;
 
-template <class TD, class TF>
+template <class TD, class TF, class TX, class TT>
 __global__ void __launch_bounds__(ROW_THREADS) row_kernel(
     const int32_t *__restrict__ leaf_begin, const int64_t *__restrict__ rho_off, const int32_t *__restrict__ rho_K,
     const int64_t *__restrict__ rho_colptr, const int32_t *__restrict__ colidx, const TD *__restrict__ dense,
-    const int64_t *__restrict__ lr_rowptr, const int32_t *__restrict__ lr_list, const int32_t *__restrict__ adm,
-    const int32_t *__restrict__ rank, const int64_t *__restrict__ uw_off, const int64_t *__restrict__ t_off,
-    const TF *__restrict__ uw, const double *__restrict__ t, const double *__restrict__ xm, double *__restrict__ ym) {
+    const int64_t *__restrict__ lr_rowptr, const LrDesc *__restrict__ desc, const TF *__restrict__ uw,
+    const TT *__restrict__ t, const TX *__restrict__ x, double *__restrict__ ym) {
     using AD = typename Acc<TD>::type;
     using AF = typename Acc<TF>::type;
     __shared__ AD s_dense[MAX_LEAF];
@@ -96,7 +123,7 @@ __global__ void __launch_bounds__(ROW_THREADS) row_kernel(
     const int32_t r0 = leaf_begin[rho], r1 = leaf_begin[rho + 1];
     const int mr = r1 - r0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = ROW_THREADS / 32;
-    // dense near field: warp per row
+    // dense near field: warp per row of rho's panel, lanes along the row
     {
         const int K = rho_K[rho];
         const TD *P = dense + rho_off[rho];
@@ -104,7 +131,17 @@ __global__ void __launch_bounds__(ROW_THREADS) row_kernel(
         for (int i = warp; i < mr; i += nwarp) {
             AD acc = 0;
             const TD *row = P + (int64_t)i * K;
-            for (int k = lane; k < K; k += 32) acc += ld_el<TD>(row + k) * (AD)xm[ci[k]];
+            int k = lane;
+            for (; k + 96 < K; k += 128) {
+                const int c0 = ci[k], c1 = ci[k + 32], c2 = ci[k + 64], c3 = ci[k + 96];
+                const AD a0 = ld_el<TD>(row + k), a1 = ld_el<TD>(row + k + 32);
+                const AD a2 = ld_el<TD>(row + k + 64), a3 = ld_el<TD>(row + k + 96);
+                acc += a0 * (AD)x[c0];
+                acc += a1 * (AD)x[c1];
+                acc += a2 * (AD)x[c2];
+                acc += a3 * (AD)x[c3];
+            }
+            for (; k < K; k += 32) acc += ld_el<TD>(row + k) * (AD)x[ci[k]];
             acc = warp_reduce(acc);
             if (lane == 0) s_dense[i] = acc;
         }
@@ -116,12 +153,19 @@ __global__ void __launch_bounds__(ROW_THREADS) row_kernel(
     AF acc = 0;
     if (p < phases) {
         for (int64_t q = l0 + p; q < l1; q += phases) {
-            const int32_t b = lr_list[q];
-            const int m = adm[4 * b + 1] - adm[4 * b], k = rank[b];
-            const int off = r0 - adm[4 * b] + i;
-            const TF *U = uw + uw_off[b];
-            const double *tb = t + t_off[b];
-            for (int l = 0; l < k; ++l) acc += ld_el<TF>(U + (int64_t)l * m + off) * (AF)tb[l];
+            const LrDesc d = desc[q];
+            const TF *U = uw + d.uoff + i;
+            const TT *tb = t + d.toff;
+            int l = 0;
+            for (; l + 3 < d.k; l += 4) {
+                const AF u0 = ld_el<TF>(U + (int64_t)l * d.ld), u1 = ld_el<TF>(U + (int64_t)(l + 1) * d.ld);
+                const AF u2 = ld_el<TF>(U + (int64_t)(l + 2) * d.ld), u3 = ld_el<TF>(U + (int64_t)(l + 3) * d.ld);
+                acc += u0 * (AF)tb[l];
+                acc += u1 * (AF)tb[l + 1];
+                acc += u2 * (AF)tb[l + 2];
+                acc += u3 * (AF)tb[l + 3];
+            }
+            for (; l < d.k; ++l) acc += ld_el<TF>(U + (int64_t)l * d.ld) * (AF)tb[l];
         }
     }
     s_lr[threadIdx.x] = acc;
@@ -131,6 +175,29 @@ __global__ void __launch_bounds__(ROW_THREADS) row_kernel(
         for (int q = 0; q < phases; ++q) s += s_lr[q * mr + threadIdx.x];
         ym[r0 + threadIdx.x] = (double)s_dense[threadIdx.x] + (double)s;
     }
+}
+
+// descriptors of the (leaf row cluster, admissible block) pairs
+__global__ void lr_desc_kernel(const int32_t *leaf_begin, int64_t nleaf, const int64_t *lr_rowptr,
+                               const int32_t *lr_list, const int32_t *adm, const int32_t *rank, const int64_t *uw_off,
+                               const int64_t *t_off, LrDesc *desc) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nleaf; r += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t r0 = leaf_begin[r];
+        for (int64_t q = lr_rowptr[r]; q < lr_rowptr[r + 1]; ++q) {
+            const int32_t b = lr_list[q];
+            LrDesc d;
+            d.uoff = uw_off[b] + (r0 - adm[4 * b]);
+            d.toff = t_off[b];
+            d.ld = adm[4 * b + 1] - adm[4 * b];
+            d.k = rank[b];
+            desc[q] = d;
+        }
+    }
+}
+
+__global__ void round_f32_kernel(const double *a, int64_t n, float *o) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        o[i] = (float)a[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -151,42 +218,80 @@ void permute_from_morton(const hm_tree *tr, const double *ym, double alpha, doub
     HM_LAUNCH_CHECK();
 }
 
-template <class TD, class TF>
-static void matvec_impl(const hm_matrix *A, const TD *dense, const TF *uw, const double *xm, double *ym, double *t,
+void build_lr_desc(hm_matrix *A, cudaStream_t s) {
+    const hm_tree *tr = A->tree;
+    const int64_t np = read_scalar(tr->lr_rowptr.as<int64_t>() + tr->n_leaf, s);
+    A->lr_desc.alloc(sizeof(LrDesc) * std::max<int64_t>(np, 1));
+    if (np == 0) return;
+    lr_desc_kernel<<<grid1d(tr->n_leaf), 256, 0, s>>>(tr->leaf_begin.as<int32_t>(), tr->n_leaf,
+                                                     tr->lr_rowptr.as<int64_t>(), tr->lr_list.as<int32_t>(),
+                                                     tr->adm.as<int32_t>(), A->rank.as<int32_t>(),
+                                                     A->uw_off.as<int64_t>(), A->t_off.as<int64_t>(),
+                                                     A->lr_desc.as<LrDesc>());
+    HM_LAUNCH_CHECK();
+}
+
+template <class TD, class TF, class TX, class TT>
+static void matvec_impl(const hm_matrix *A, const TD *dense, const TF *uw, const TX *x, TT *t, double *ym,
                         cudaStream_t s) {
     const hm_tree *tr = A->tree;
     if (tr->n_adm > 0) {
         const int64_t warps = tr->n_adm;
-        lr_project_kernel<TF><<<grid1d(warps * 32), 256, 0, s>>>(tr->adm.as<int32_t>(), tr->n_adm,
-                                                                 A->rank.as<int32_t>(), A->uw_off.as<int64_t>(),
-                                                                 A->t_off.as<int64_t>(), uw, xm, t);
+        lr_project_kernel<TF, TX, TT><<<grid1d(warps * 32), 256, 0, s>>>(
+            tr->adm.as<int32_t>(), tr->n_adm, A->rank.as<int32_t>(), A->uw_off.as<int64_t>(),
+            A->t_off.as<int64_t>(), uw, x, t);
         HM_LAUNCH_CHECK();
     }
-    row_kernel<TD, TF><<<(unsigned)tr->n_leaf, ROW_THREADS, 0, s>>>(
+    row_kernel<TD, TF, TX, TT><<<(unsigned)tr->n_leaf, ROW_THREADS, 0, s>>>(
         tr->leaf_begin.as<int32_t>(), tr->rho_off.as<int64_t>(), tr->rho_K.as<int32_t>(),
         tr->rho_colptr.as<int64_t>(), tr->colidx.as<int32_t>(), dense, tr->lr_rowptr.as<int64_t>(),
-        tr->lr_list.as<int32_t>(), tr->adm.as<int32_t>(), A->rank.as<int32_t>(), A->uw_off.as<int64_t>(),
-        A->t_off.as<int64_t>(), uw, t, xm, ym);
+        A->lr_desc.as<LrDesc>(), uw, t, x, ym);
     HM_LAUNCH_CHECK();
 }
 
-// y_m = H x_m in Morton order; t: scratch of total_rank doubles
-void matvec_morton(const hm_matrix *A, hm_dtype prec, const double *xm, double *ym, double *t, cudaStream_t s) {
+// w.ym = H w.xm in Morton order.  FP64 uses w.t; the low-precision copies use
+// w.x32 (x rounded once) and w.t32, with FP32 accumulation.
+void matvec_morton(const hm_matrix *A, hm_dtype prec, const MatvecWork &w, cudaStream_t s) {
+    const int64_t n = A->tree->n;
     switch (prec) {
         case HM_F64:
-            matvec_impl<double, double>(A, A->dense.as<double>(), A->uw.as<double>(), xm, ym, t, s);
+            matvec_impl<double, double, double, double>(A, A->dense.as<double>(), A->uw.as<double>(), w.xm, w.t, w.ym,
+                                                        s);
             break;
         case HM_F32:
-            if (!A->dense32.p || !A->uw32.p) fail(HM_EINVAL, "FP32 copies were not assembled");
-            matvec_impl<float, float>(A, A->dense32.as<float>(), A->uw32.as<float>(), xm, ym, t, s);
-            break;
         case HM_BF16:
-            if (!A->dense32.p || !A->uwbf.p) fail(HM_EINVAL, "BF16 factors / FP32 near field were not assembled");
-            matvec_impl<float, __nv_bfloat16>(A, A->dense32.as<float>(), A->uwbf.as<__nv_bfloat16>(), xm, ym, t, s);
+            if (!A->dense32.p || (prec == HM_F32 ? !A->uw32.p : !A->uwbf.p))
+                fail(HM_EINVAL, "the low-precision copies for this precision were not assembled");
+            round_f32_kernel<<<grid1d(n), 256, 0, s>>>(w.xm, n, w.x32);
+            HM_LAUNCH_CHECK();
+            if (prec == HM_F32)
+                matvec_impl<float, float, float, float>(A, A->dense32.as<float>(), A->uw32.as<float>(), w.x32, w.t32,
+                                                        w.ym, s);
+            else
+                matvec_impl<float, __nv_bfloat16, float, float>(A, A->dense32.as<float>(), A->uwbf.as<__nv_bfloat16>(),
+                                                                w.x32, w.t32, w.ym, s);
             break;
         default:
             fail(HM_EINVAL, "unknown precision %d", (int)prec);
     }
+}
+
+// Device workspace of hm_matvec / the solver: xm, ym [n], t [total_rank]
+// doubles, then x32 [n] and t32 [total_rank] floats.
+int64_t matvec_work_doubles(const hm_matrix *A) {
+    const int64_t n = A->tree->n, r = std::max<int64_t>(A->total_rank, 1);
+    return 2 * n + r + (n + 1) / 2 + (r + 1) / 2;
+}
+
+MatvecWork matvec_work_at(const hm_matrix *A, double *base) {
+    const int64_t n = A->tree->n, r = std::max<int64_t>(A->total_rank, 1);
+    MatvecWork w;
+    w.xm = base;
+    w.ym = base + n;
+    w.t = base + 2 * n;
+    w.x32 = reinterpret_cast<float *>(base + 2 * n + r);
+    w.t32 = reinterpret_cast<float *>(base + 2 * n + r + (n + 1) / 2);
+    return w;
 }
 
 // ---------------------------------------------------------------------------
@@ -266,9 +371,11 @@ void load_vector_impl(const hm_tree *tr, const double *src, int nsrc, double *f,
 // from cudaMalloc on every call; this variant takes them from one file-scope
 // device array instead, sized once when the library is loaded.
 //
-// Scratch layout (doubles): x in Morton order [n], y in Morton order [n],
-// projections t_b = W_b^T x [sum_b k_b].  Every element is written before it
-// is read in each call, so nothing needs clearing between calls.  The array
+// Scratch layout: the product's working vectors (x and y in Morton order,
+// the projections t_b = W_b^T x, and their FP32 roundings for the
+// low-precision copies): 2 n + sum_b k_b doubles plus n + sum_b k_b floats.
+// Every element is written before it is read in each call, so nothing needs
+// clearing between calls.  The array
 // is shared by every call on a device and keeps the last call's contents:
 // calls whose work overlaps on the GPU (other streams, other host threads)
 // race on it.
@@ -301,18 +408,17 @@ static double *noalloc_scratch() {
 void matvec_noalloc(const hm_matrix *A, int32_t nrhs, hm_dtype prec, const double *x, double *y, double alpha,
                     double beta, cudaStream_t s) {
     const int64_t n = A->tree->n;
-    const int64_t need = 2 * n + std::max<int64_t>(A->total_rank, 1);
+    const int64_t need = matvec_work_doubles(A);
     if (need > NOALLOC_MAX_DOUBLES)
         fail(HM_EINVAL,
              "problem too large for the allocation-free product: needs %lld scratch doubles "
-             "(2 n + sum of ranks), the limit is %lld",
+             "(3 (n + sum of ranks) / 2 + n / 2), the limit is %lld",
              (long long)need, (long long)NOALLOC_MAX_DOUBLES);
-    double *base = noalloc_scratch();
-    double *xm = base, *ym = base + n, *t = base + 2 * n;
+    const MatvecWork w = matvec_work_at(A, noalloc_scratch());
     for (int r = 0; r < nrhs; ++r) {
-        permute_to_morton(A->tree, x + (int64_t)r * n, xm, s);
-        matvec_morton(A, prec, xm, ym, t, s);
-        permute_from_morton(A->tree, ym, alpha, beta, y + (int64_t)r * n, s);
+        permute_to_morton(A->tree, x + (int64_t)r * n, w.xm, s);
+        matvec_morton(A, prec, w, s);
+        permute_from_morton(A->tree, w.ym, alpha, beta, y + (int64_t)r * n, s);
     }
 }
 

@@ -81,6 +81,10 @@ QuadParams make_quad(int ss_order) {
             q.w[1 + 3 * o + k] = wa[o];
         }
     }
+    for (int k = 0; k < NQ; ++k) {
+        q.w_h[k] = (float)q.w[k];
+        q.w_l[k] = (float)(q.w[k] - (double)q.w_h[k]);
+    }
     // Gauss-Legendre on [-1, 1]: roots of P_n by Newton's method started from
     // cos(pi (k + 3/4) / (n + 1/2)); weights 2 / ((1 - x^2) P_n'(x)^2); then
     // mapped to [0, 1].

@@ -16,7 +16,18 @@
 
 namespace hm {
 
-void matvec_morton(const hm_matrix *A, hm_dtype prec, const double *xm, double *ym, double *t, cudaStream_t s);
+void matvec_morton(const hm_matrix *A, hm_dtype prec, const MatvecWork &w, cudaStream_t s);
+int64_t matvec_work_doubles(const hm_matrix *A);
+MatvecWork matvec_work_at(const hm_matrix *A, double *base);
+
+// y = op(H) x in Morton order through the solver's workspace (x, y may be any vectors)
+static void apply(const hm_matrix *A, hm_dtype prec, const double *x, double *y, DBuf &work, cudaStream_t s) {
+    MatvecWork w = matvec_work_at(A, work.as<double>());
+    const int64_t n = A->tree->n;
+    HM_CUDA_CHECK(cudaMemcpyAsync(w.xm, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    matvec_morton(A, prec, w, s);
+    HM_CUDA_CHECK(cudaMemcpyAsync(y, w.ym, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+}
 
 constexpr int DOT_THREADS = 256;
 constexpr int DOT_CHUNK = 8;  // vectors per register pass
@@ -151,7 +162,7 @@ struct Gmres {
     int m;
     int nblk;
     DBuf V, w, ax, part, h, H, cs, sn, g, y, est, t, nrm;
-    Gmres(int64_t n_, int m_, int64_t total_rank) : n(n_), m(m_) {
+    Gmres(int64_t n_, int m_, int64_t work_doubles) : n(n_), m(m_) {
         nblk = std::max(1, std::min<int>(4 * num_sms(), (int)((n + 1023) / 1024)));
         V.alloc(sizeof(double) * (int64_t)(m + 1) * n);
         w.alloc(sizeof(double) * n);
@@ -164,7 +175,7 @@ struct Gmres {
         g.alloc(sizeof(double) * (m + 1));
         y.alloc(sizeof(double) * m);
         est.alloc(sizeof(double) * 2);
-        t.alloc(sizeof(double) * std::max<int64_t>(total_rank, 1));
+        t.alloc(sizeof(double) * work_doubles);
         nrm.alloc(sizeof(double) * 2);
     }
     // out[0..nv) = V_l . w (accumulate adds to out)
@@ -198,7 +209,7 @@ static hm_status gmres(const hm_matrix *A, hm_dtype prec, const double *b, doubl
     if (x_is_zero) {
         HM_CUDA_CHECK(cudaMemcpyAsync(V, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     } else {
-        matvec_morton(A, prec, x, G.ax.as<double>(), G.t.as<double>(), s);
+        apply(A, prec, x, G.ax.as<double>(), G.t, s);
         residual_kernel<<<g1(n), 256, 0, s>>>(b, G.ax.as<double>(), n, V);
         HM_LAUNCH_CHECK();
     }
@@ -215,7 +226,7 @@ static hm_status gmres(const hm_matrix *A, hm_dtype prec, const double *b, doubl
         for (int j = 0; j < m; ++j) {
             double *vj = V + (int64_t)j * n;
             double *w = G.w.as<double>();
-            matvec_morton(A, prec, vj, w, G.t.as<double>(), s);
+            apply(A, prec, vj, w, G.t, s);
             // CGS2
             G.dots(V, j + 1, w, G.h.as<double>(), 0, s);
             sub_combo_kernel<<<g1(n), 256, 0, s>>>(V, n, j + 1, G.h.as<double>(), n, w);
@@ -250,7 +261,7 @@ static hm_status gmres(const hm_matrix *A, hm_dtype prec, const double *b, doubl
         add_combo_kernel<<<g1(n), 256, 0, s>>>(V, n, k, G.y.as<double>(), n, x);
         HM_LAUNCH_CHECK();
         // true residual -> V_0 for the next cycle
-        matvec_morton(A, prec, x, G.ax.as<double>(), G.t.as<double>(), s);
+        apply(A, prec, x, G.ax.as<double>(), G.t, s);
         residual_kernel<<<g1(n), 256, 0, s>>>(b, G.ax.as<double>(), n, V);
         HM_LAUNCH_CHECK();
         beta = std::sqrt(G.norm2_host(V, s));
@@ -272,7 +283,7 @@ hm_status solve_impl(const hm_matrix *A, const double *b_orig, double *x_orig, c
     x.alloc(sizeof(double) * n);
     permute_to_morton(tr, b_orig, b.as<double>(), s);
     HM_CUDA_CHECK(cudaMemsetAsync(x.p, 0, sizeof(double) * n, s));
-    Gmres G(n, p.restart, A->total_rank);
+    Gmres G(n, p.restart, matvec_work_doubles(A));
     int iters = 0, cycles = 0, steps = 0;
     double relres = 1.0;
     hm_status st;
@@ -299,7 +310,7 @@ hm_status solve_impl(const hm_matrix *A, const double *b_orig, double *x_orig, c
                   inner, true);
             axpy_kernel<<<g1(n), 256, 0, s>>>(1.0, d.as<double>(), n, x.as<double>());
             HM_LAUNCH_CHECK();
-            matvec_morton(A, HM_F64, x.as<double>(), ax.as<double>(), G.t.as<double>(), s);
+            apply(A, HM_F64, x.as<double>(), ax.as<double>(), G.t, s);
             residual_kernel<<<g1(n), 256, 0, s>>>(b.as<double>(), ax.as<double>(), n, r.as<double>());
             HM_LAUNCH_CHECK();
             relres = std::sqrt(G.norm2_host(r.as<double>(), s)) / bnorm;

@@ -12,7 +12,7 @@
 #include <memory>
 #include <numeric>
 
-#include "hm_internal.cuh"
+#include "ff.cuh"
 
 namespace hm {
 
@@ -107,17 +107,32 @@ __global__ void morton_kernel(const double *cent, int64_t n, const double *grid,
 
 // panel table in Morton order
 __global__ void panel_table_kernel(const double *V, const int32_t *T, const int32_t *perm, const double *cent,
-                                   int64_t n, int64_t npad, QuadParams qp, double *pt, double *cent_s, int32_t *trim,
-                                   int32_t *iperm) {
+                                   int64_t n, int64_t npad, QuadParams qp, double *pt, float *pf, double *cent_s,
+                                   int32_t *trim, int32_t *iperm) {
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const int32_t i = perm[k];
         const int32_t t0 = T[3 * (int64_t)i], t1 = T[3 * (int64_t)i + 1], t2 = T[3 * (int64_t)i + 2];
         const double *a = V + 3 * (int64_t)t0, *b = V + 3 * (int64_t)t1, *c = V + 3 * (int64_t)t2;
         for (int q = 0; q < NQ; ++q)
-            for (int d = 0; d < 3; ++d)
-                pt[(int64_t)(7 * d + q) * npad + k] =
-                    __dadd_rn(__dadd_rn(__dmul_rn(qp.bary[q][0], a[d]), __dmul_rn(qp.bary[q][1], b[d])),
-                              __dmul_rn(qp.bary[q][2], c[d]));
+            for (int d = 0; d < 3; ++d) {
+                const double xq = __dadd_rn(__dadd_rn(__dmul_rn(qp.bary[q][0], a[d]), __dmul_rn(qp.bary[q][1], b[d])),
+                                            __dmul_rn(qp.bary[q][2], c[d]));
+                pt[(int64_t)(7 * d + q) * npad + k] = xq;
+                // far-field record: offset from the centroid as a float pair
+                float h, l;
+                split_double(__dsub_rn(xq, cent[3 * (int64_t)i + d]), h, l);
+                pf[(int64_t)(PF_AH + 7 * d + q) * npad + k] = h;
+                pf[(int64_t)(PF_AL + 7 * d + q) * npad + k] = l;
+            }
+        for (int d = 0; d < 3; ++d) {
+            float h, l;
+            split_double(cent[3 * (int64_t)i + d], h, l);
+            pf[(int64_t)(PF_CH + d) * npad + k] = h;
+            pf[(int64_t)(PF_CL + d) * npad + k] = l;
+        }
+        pf[(int64_t)(PF_VID + 0) * npad + k] = __int_as_float(t0);
+        pf[(int64_t)(PF_VID + 1) * npad + k] = __int_as_float(t1);
+        pf[(int64_t)(PF_VID + 2) * npad + k] = __int_as_float(t2);
         double e1[3], e2[3];
         for (int d = 0; d < 3; ++d) {
             e1[d] = __dsub_rn(b[d], a[d]);
@@ -127,7 +142,14 @@ __global__ void panel_table_kernel(const double *V, const int32_t *T, const int3
         double x1 = __dsub_rn(__dmul_rn(e1[2], e2[0]), __dmul_rn(e1[0], e2[2]));
         double x2 = __dsub_rn(__dmul_rn(e1[0], e2[1]), __dmul_rn(e1[1], e2[0]));
         double nn = __dadd_rn(__dadd_rn(__dmul_rn(x0, x0), __dmul_rn(x1, x1)), __dmul_rn(x2, x2));
-        pt[(int64_t)PT_AREA * npad + k] = __dmul_rn(0.5, __dsqrt_rn(nn));
+        const double area = __dmul_rn(0.5, __dsqrt_rn(nn));
+        pt[(int64_t)PT_AREA * npad + k] = area;
+        {
+            float h, l;
+            split_double(area / SQRT_4PI, h, l);
+            pf[(int64_t)PF_WA * npad + k] = h;
+            pf[(int64_t)(PF_WA + 1) * npad + k] = l;
+        }
         pt[(int64_t)(PT_VID + 0) * npad + k] = (double)t0;
         pt[(int64_t)(PT_VID + 1) * npad + k] = (double)t1;
         pt[(int64_t)(PT_VID + 2) * npad + k] = (double)t2;
@@ -415,11 +437,14 @@ hm_tree *build_tree_impl(const double *d_V, int64_t nv, const int32_t *d_T, int6
     const QuadParams qp = make_quad(1);
     tr->pt.alloc(sizeof(double) * PT_ROWS * npad);
     HM_CUDA_CHECK(cudaMemsetAsync(tr->pt.p, 0, sizeof(double) * PT_ROWS * npad, s));
+    tr->pf.alloc(sizeof(float) * PF_ROWS * npad);
+    HM_CUDA_CHECK(cudaMemsetAsync(tr->pf.p, 0, sizeof(float) * PF_ROWS * npad, s));
     tr->cent.alloc(sizeof(double) * 3 * n);
     tr->trim.alloc(sizeof(int32_t) * 3 * n);
     tr->iperm.alloc(sizeof(int32_t) * n);
     panel_table_kernel<<<grid_for(n), 256, 0, s>>>(V, T.as<int32_t>(), tr->perm.as<int32_t>(), cent.as<double>(), n,
-                                                  npad, qp, tr->pt.as<double>(), tr->cent.as<double>(),
+                                                  npad, qp, tr->pt.as<double>(), tr->pf.as<float>(),
+                                                  tr->cent.as<double>(),
                                                   tr->trim.as<int32_t>(), tr->iperm.as<int32_t>());
     HM_LAUNCH_CHECK();
 
