@@ -205,9 +205,11 @@ HM_API hm_status hm_matvec(const hm_matrix *A, int32_t trans, int32_t nrhs, hm_d
  *  low-precision copies) live in one 16 MiB array that
  *  the library reserves on every device it is loaded on, held until exit; no
  *  memory is allocated or freed by the call.
- *  Limit: 2 n + K doubles plus n + K floats must fit in 2,097,152 doubles
- *  (K = sum of the ACA ranks; about 2.5 n + 1.5 K <= 2,097,152); larger
- *  problems get HM_EINVAL with the required size in hm_last_error().
+ *  Limit: 2 n + K + P doubles plus n + K + P floats must fit in 2,097,152
+ *  doubles (K = sum of the ACA ranks, P = the column-cluster partials of the
+ *  low-rank projections, about K times the mean number of leaf clusters an
+ *  admissible block spans); larger problems get HM_EINVAL with the required
+ *  size in hm_last_error().
  *  The first call on a device looks up that array's device address (with the
  *  device current); make that first call before any stream capture.
  *  All calls share the array and it keeps the last call's contents: calls

@@ -142,22 +142,36 @@ struct Grp {
 
 __device__ __forceinline__ bool bit(const uint32_t *bm, int k) { return (bm[k >> 5] >> (k & 31)) & 1u; }
 
-// entry (row panel record r at Morton position gi, column panel record c at
-// gj) of the Galerkin matrix: far-field pairs in float-float, touching pairs
-// (which admissible blocks do not contain in practice) by the FP64 rule
-__device__ __forceinline__ double aca_entry(const float *r, int64_t gi, const float *c, int64_t gj, const AcaArgs &A) {
-    const int32_t a[3] = {__float_as_int(r[PF_VID]), __float_as_int(r[PF_VID + 1]), __float_as_int(r[PF_VID + 2])};
-    const int32_t b[3] = {__float_as_int(c[PF_VID]), __float_as_int(c[PF_VID + 1]), __float_as_int(c[PF_VID + 2])};
-    const int kind = shared_vertices(a, b);
-    if (kind)
-        return singular_entry_serial(A.V, a, b, kind, A.pt[(int64_t)PT_AREA * A.npad + gi],
-                                     A.pt[(int64_t)PT_AREA * A.npad + gj], A.qp);
-    return regular_entry_ff(r, 1, c, 1, A.qp.w_h, A.qp.w_l);
+// One out-of-line copy of the far-field evaluation shared by every call site
+// (row and column passes, CTA and warp workers).
+__device__ __noinline__ static double far_entry(const float *r, int rs, const float *c, int cs, const float *wh,
+                                                const float *wl) {
+    return regular_entry_ff(r, rs, c, cs, wh, wl);
 }
 
-__device__ __forceinline__ void load_panel(const AcaArgs &A, int64_t k, float *rec) {
-#pragma unroll
-    for (int q = 0; q < PF_ROWS; ++q) rec[q] = A.pf[(int64_t)q * A.npad + k];
+// Entry of the Galerkin matrix for the row panel at Morton position gi and the
+// column panel at gj; `fix` is the shared-memory record of the panel that is
+// fixed during the pass (the row panel when fixed_is_row, else the column
+// panel), the other record is read from the float panel table.  Far-field
+// pairs in float-float; touching pairs (which admissible blocks do not contain
+// in practice) by the FP64 regularised rule.
+__device__ __forceinline__ double aca_entry(const float *fix, bool fixed_is_row, int64_t gi, int64_t gj,
+                                            const AcaArgs &A) {
+    const int64_t var = fixed_is_row ? gj : gi;
+    const float *rec = A.pf + var;
+    const int64_t st = A.npad;
+    const int32_t vf[3] = {__float_as_int(fix[PF_VID]), __float_as_int(fix[PF_VID + 1]),
+                           __float_as_int(fix[PF_VID + 2])};
+    const int32_t vv[3] = {__float_as_int(rec[PF_VID * st]), __float_as_int(rec[(PF_VID + 1) * st]),
+                           __float_as_int(rec[(PF_VID + 2) * st])};
+    const int kind = shared_vertices(vf, vv);
+    if (kind) {
+        const double ai = A.pt[(int64_t)PT_AREA * A.npad + gi], aj = A.pt[(int64_t)PT_AREA * A.npad + gj];
+        return fixed_is_row ? singular_entry_serial(A.V, vf, vv, kind, ai, aj, A.qp)
+                            : singular_entry_serial(A.V, vv, vf, kind, ai, aj, A.qp);
+    }
+    return fixed_is_row ? far_entry(fix, 1, rec, (int)st, A.qp.w_h, A.qp.w_l)
+                        : far_entry(rec, (int)st, fix, 1, A.qp.w_h, A.qp.w_l);
 }
 
 // ACA of one block; U (m x kmax) and W (n x kmax) column-major in scratch.
@@ -175,7 +189,6 @@ __device__ int aca_block(const AcaArgs &A, int rb, int m, int cb, int n, double 
     int r = 0, i = 0;
     double s2 = 0.0, delta1 = 0.0;
     bool converged = false;
-    float rec[PF_ROWS];
     while (r < rmax) {
         // ---- residual of row i ----
         for (int q = t; q < PF_ROWS; q += gs) sh.fix[q] = A.pf[(int64_t)q * A.npad + rb + i];
@@ -183,8 +196,7 @@ __device__ int aca_block(const AcaArgs &A, int rb, int m, int cb, int n, double 
         G::sync();
         Best best{-1.0, 0x7fffffff, 0.0};
         for (int j = t; j < n; j += gs) {
-            load_panel(A, cb + j, rec);
-            double v = aca_entry(sh.fix, rb + i, rec, cb + j, A);
+            double v = aca_entry(sh.fix, true, rb + i, cb + j, A);
             for (int l = 0; l < r; ++l) v -= sh.vec[l] * W[(int64_t)l * n + j];
             W[(int64_t)r * n + j] = v;
             if (!bit(sh.ucol, j)) {
@@ -223,8 +235,7 @@ __device__ int aca_block(const AcaArgs &A, int rb, int m, int cb, int n, double 
         double nu2 = 0.0;
         Best nb{-1.0, 0x7fffffff, 0.0};
         for (int k = t; k < m; k += gs) {
-            load_panel(A, rb + k, rec);
-            double u = aca_entry(rec, rb + k, sh.fix, cb + jp, A);
+            double u = aca_entry(sh.fix, false, rb + k, cb + jp, A);
             for (int l = 0; l < r; ++l) u -= sh.vec[l] * U[(int64_t)l * m + k];
             U[(int64_t)r * m + k] = u;
             nu2 += u * u;
@@ -377,16 +388,21 @@ __global__ void rank_stats(const int32_t *rank, int64_t na, unsigned long long *
 // ---------------------------------------------------------------------------
 // host
 // ---------------------------------------------------------------------------
-void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStream_t s, double *sec) {
+// ACA of every admissible leaf.  Output: A->rank, A->t_off, A->total_rank,
+// A->lr_entries, and the factors in `uw` (per block U_b column-major then W_b
+// row-major at uw_off[b]), exactly sized.
+void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStream_t s, double *sec, DBuf &uw,
+                  DBuf &uw_off) {
     const int64_t na = tr->n_adm;
     const int kmax = A->params.aca_kmax;
     A->rank.alloc(sizeof(int32_t) * std::max<int64_t>(na, 1));
-    A->uw_off.alloc(sizeof(int64_t) * std::max<int64_t>(na, 1));
+    uw_off.alloc(sizeof(int64_t) * std::max<int64_t>(na, 1));
     A->t_off.alloc(sizeof(int64_t) * (na + 1));
     if (na == 0) {
-        A->uw.alloc(16);
+        uw.alloc(16);
         A->lr_entries = 0;
         A->total_rank = 0;
+        HM_CUDA_CHECK(cudaMemsetAsync(A->t_off.p, 0, sizeof(int64_t), s));
         *sec = 0.0;
         return;
     }
@@ -458,7 +474,7 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
     a.q_small = ctr.as<unsigned long long>() + 2;
     a.kmax_hit = reinterpret_cast<int *>(ctr.as<unsigned long long>() + 3);
     a.rank = A->rank.as<int32_t>();
-    a.uw_off = A->uw_off.as<int64_t>();
+    a.uw_off = uw_off.as<int64_t>();
     a.todo = nullptr;
     a.n_todo = 0;
 
@@ -513,8 +529,8 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
     }
     // shrink the arena to what is used
     A->lr_entries = (int64_t)top;
-    A->uw.alloc(sizeof(double) * std::max<int64_t>(A->lr_entries, 1));
-    HM_CUDA_CHECK(cudaMemcpyAsync(A->uw.p, arena.p, sizeof(double) * A->lr_entries, cudaMemcpyDeviceToDevice, s));
+    uw.alloc(sizeof(double) * std::max<int64_t>(A->lr_entries, 1));
+    HM_CUDA_CHECK(cudaMemcpyAsync(uw.p, arena.p, sizeof(double) * A->lr_entries, cudaMemcpyDeviceToDevice, s));
     // t offsets (prefix sum of ranks)
     rank_to_i64<<<256, 256, 0, s>>>(A->rank.as<int32_t>(), na, A->t_off.as<int64_t>());
     HM_LAUNCH_CHECK();

@@ -17,12 +17,13 @@ hm_tree *build_tree_impl(const double *d_V, int64_t nv, const int32_t *d_T, int6
                          cudaStream_t s);
 void assemble_nearfield(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStream_t s, int *d_err,
                         double *sec_regular, double *sec_singular);
-void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStream_t s, double *sec);
+void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStream_t s, double *sec, DBuf &uw,
+                  DBuf &uw_off);
+void build_lr_panels(hm_matrix *A, const DBuf &uw, const DBuf &uw_off, cudaStream_t s);
 void make_low_copies(hm_matrix *A, cudaStream_t s);
 void matvec_morton(const hm_matrix *A, hm_dtype prec, const MatvecWork &w, cudaStream_t s);
 int64_t matvec_work_doubles(const hm_matrix *A);
 MatvecWork matvec_work_at(const hm_matrix *A, double *base);
-void build_lr_desc(hm_matrix *A, cudaStream_t s);
 void permute_to_morton(const hm_tree *tr, const double *x, double *xm, cudaStream_t s);
 void permute_from_morton(const hm_tree *tr, const double *ym, double alpha, double beta, double *y, cudaStream_t s);
 void load_vector_impl(const hm_tree *tr, const double *src, int nsrc, double *f, cudaStream_t s);
@@ -94,21 +95,25 @@ hm_status hm_assemble(const hm_tree *tree, const hm_assemble_params *params, hm_
         HM_CUDA_CHECK(cudaMemsetAsync(err.p, 0, sizeof(int), s));
         double sr = 0, ss = 0, sa = 0;
         assemble_nearfield(tree, A.get(), qp, s, err.as<int>(), &sr, &ss);
-        assemble_aca(tree, A.get(), qp, s, &sa);
-        build_lr_desc(A.get(), s);
+        {
+            DBuf uw, uw_off;
+            assemble_aca(tree, A.get(), qp, s, &sa, uw, uw_off);
+            build_lr_panels(A.get(), uw, uw_off, s);
+            HM_CUDA_CHECK(cudaStreamSynchronize(s));
+        }
         make_low_copies(A.get(), s);
         HM_CUDA_CHECK(cudaStreamSynchronize(s));
         const int e = read_scalar(err.as<int>(), s);
         if (e == 2) fail(HM_ETIMEOUT, "a panel staging wait timed out");
         if (e) fail(HM_EINTERNAL, "device error code %d during assembly", e);
         hm_matrix_info &I = A->info;
-        I.dense_entries = tree->dense_entries;
+        I.dense_entries = tree->dense_true;
         I.lr_entries = A->lr_entries;
         I.s_nearfield = sr;
         I.s_singular = ss;
         I.s_aca = sa;
-        I.bytes_f64 = (int64_t)(A->dense.bytes + A->uw.bytes);
-        I.bytes_low = (int64_t)(A->dense32.bytes + A->uw32.bytes + A->uwbf.bytes);
+        I.bytes_f64 = (int64_t)(A->dense.bytes + A->up.bytes + A->wp.bytes);
+        I.bytes_low = (int64_t)(A->dense32.bytes + A->up32.bytes + A->upbf.bytes + A->wp32.bytes + A->wpbf.bytes);
         I.s_total = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         *out = A.release();
     });
@@ -132,8 +137,8 @@ hm_status hm_matvec(const hm_matrix *A, int32_t trans, int32_t nrhs, hm_dtype pr
         if (nrhs < 1) fail(HM_EINVAL, "nrhs must be >= 1");
         if (trans != 0 && trans != 1) fail(HM_EINVAL, "trans must be 0 or 1");
         if (trans == 1) fail(HM_EINVAL, "the transposed product is not available in this build");
-        if (prec == HM_F32 && !A->uw32.p) fail(HM_EINVAL, "FP32 copies were not assembled");
-        if (prec == HM_BF16 && !A->uwbf.p) fail(HM_EINVAL, "BF16 factors were not assembled");
+        if (prec == HM_F32 && !A->up32.p) fail(HM_EINVAL, "FP32 copies were not assembled");
+        if (prec == HM_BF16 && !A->upbf.p) fail(HM_EINVAL, "BF16 factors were not assembled");
         if (prec < HM_F64 || prec > HM_BF16) fail(HM_EINVAL, "bad precision");
         cudaStream_t s = (cudaStream_t)stream;
         const int64_t n = A->tree->n;
@@ -157,8 +162,8 @@ hm_status hm_matvec_noalloc(const hm_matrix *A, int32_t trans, int32_t nrhs, hm_
         if (nrhs < 1) fail(HM_EINVAL, "nrhs must be >= 1");
         if (trans != 0) fail(HM_EINVAL, "only trans = 0 is available");
         if (prec < HM_F64 || prec > HM_BF16) fail(HM_EINVAL, "bad precision");
-        if (prec == HM_F32 && !A->uw32.p) fail(HM_EINVAL, "FP32 copies were not assembled");
-        if (prec == HM_BF16 && !A->uwbf.p) fail(HM_EINVAL, "BF16 factors were not assembled");
+        if (prec == HM_F32 && !A->up32.p) fail(HM_EINVAL, "FP32 copies were not assembled");
+        if (prec == HM_BF16 && !A->upbf.p) fail(HM_EINVAL, "BF16 factors were not assembled");
         matvec_noalloc(A, nrhs, prec, d_x, d_y, alpha, beta, (cudaStream_t)stream);
     });
 }
@@ -178,8 +183,8 @@ hm_status hm_solve(const hm_matrix *A, int32_t trans, int32_t nrhs, const double
         if (params->refine) {
             if (params->max_refine < 1) fail(HM_EINVAL, "max_refine must be >= 1");
             if (!(params->inner_tol > 0.0)) fail(HM_EINVAL, "inner_tol must be > 0");
-            if (params->inner_dtype == HM_F32 && !A->uw32.p) fail(HM_EINVAL, "FP32 copies were not assembled");
-            if (params->inner_dtype == HM_BF16 && !A->uwbf.p) fail(HM_EINVAL, "BF16 factors were not assembled");
+            if (params->inner_dtype == HM_F32 && !A->up32.p) fail(HM_EINVAL, "FP32 copies were not assembled");
+            if (params->inner_dtype == HM_BF16 && !A->upbf.p) fail(HM_EINVAL, "BF16 factors were not assembled");
             if (params->inner_dtype < HM_F64 || params->inner_dtype > HM_BF16) fail(HM_EINVAL, "bad inner_dtype");
         }
         const int64_t n = A->tree->n;
@@ -215,7 +220,7 @@ hm_status hm_tree_get_info(const hm_tree *tree, hm_tree_info *info) {
         info->max_leaf = tree->max_leaf;
         info->n_dense = tree->n_dense;
         info->n_adm = tree->n_adm;
-        info->dense_entries = tree->dense_entries;
+        info->dense_entries = tree->dense_true;
         info->adm_rows_cols = tree->adm_rows_cols;
         info->n_singular = tree->n_singular;
         info->seconds = tree->seconds;
@@ -252,21 +257,22 @@ hm_status hm_matrix_export(const hm_matrix *A, double *h_dense, int64_t *h_dense
     return guard([&] {
         if (!is_matrix(A) || !n_dense_vals || !n_lr_vals) fail(HM_EINVAL, "bad argument");
         const hm_tree *tr = A->tree;
-        *n_dense_vals = tr->dense_entries;
+        *n_dense_vals = tr->dense_true;
         *n_lr_vals = A->lr_entries;
         if (!h_dense && !h_uw) return;
         if (!h_dense || !h_dense_off || !h_rank || !h_uw || !h_u_off || !h_w_off) fail(HM_EINVAL, "NULL buffer");
-        const int64_t nd = tr->n_dense, na = tr->n_adm;
-        std::vector<int32_t> den(4 * nd), adm(4 * na), ld(nd), rank(na);
-        std::vector<int64_t> base(nd), uwo(na);
+        const int64_t nd = tr->n_dense, na = tr->n_adm, nl = tr->n_leaf;
+        auto get = [](void *dst, const DBuf &src, size_t bytes) {
+            if (bytes) HM_CUDA_CHECK(cudaMemcpy(dst, src.p, bytes, cudaMemcpyDeviceToHost));
+        };
+        // dense leaves, row-major per block
+        std::vector<int32_t> den(4 * nd), ld(nd);
+        std::vector<int64_t> base(nd);
         std::vector<double> arena(tr->dense_entries);
-        if (nd) {
-            HM_CUDA_CHECK(cudaMemcpy(den.data(), tr->dense.p, sizeof(int32_t) * 4 * nd, cudaMemcpyDeviceToHost));
-            HM_CUDA_CHECK(cudaMemcpy(base.data(), tr->dense_base.p, sizeof(int64_t) * nd, cudaMemcpyDeviceToHost));
-            HM_CUDA_CHECK(cudaMemcpy(ld.data(), tr->dense_ld.p, sizeof(int32_t) * nd, cudaMemcpyDeviceToHost));
-            HM_CUDA_CHECK(cudaMemcpy(arena.data(), A->dense.p, sizeof(double) * tr->dense_entries,
-                                     cudaMemcpyDeviceToHost));
-        }
+        get(den.data(), tr->dense, sizeof(int32_t) * 4 * nd);
+        get(base.data(), tr->dense_base, sizeof(int64_t) * nd);
+        get(ld.data(), tr->dense_ld, sizeof(int32_t) * nd);
+        get(arena.data(), A->dense, sizeof(double) * tr->dense_entries);
         int64_t o = 0;
         for (int64_t b = 0; b < nd; ++b) {
             const int m = den[4 * b + 1] - den[4 * b], n = den[4 * b + 3] - den[4 * b + 2];
@@ -275,23 +281,60 @@ hm_status hm_matrix_export(const hm_matrix *A, double *h_dense, int64_t *h_dense
                 for (int j = 0; j < n; ++j) h_dense[o + (int64_t)i * n + j] = arena[base[b] + (int64_t)i * ld[b] + j];
             o += (int64_t)m * n;
         }
-        std::vector<double> fac(std::max<int64_t>(A->lr_entries, 1));
-        if (na) {
-            HM_CUDA_CHECK(cudaMemcpy(adm.data(), tr->adm.p, sizeof(int32_t) * 4 * na, cudaMemcpyDeviceToHost));
-            HM_CUDA_CHECK(cudaMemcpy(rank.data(), A->rank.p, sizeof(int32_t) * na, cudaMemcpyDeviceToHost));
-            HM_CUDA_CHECK(cudaMemcpy(uwo.data(), A->uw_off.p, sizeof(int64_t) * na, cudaMemcpyDeviceToHost));
-            HM_CUDA_CHECK(cudaMemcpy(fac.data(), A->uw.p, sizeof(double) * A->lr_entries, cudaMemcpyDeviceToHost));
-        }
-        // U_b as stored (column-major); W_b stored row-major, exported column-major
+        if (na == 0) return;
+        // low-rank factors: U_b gathered back from the row panels, W_b from the
+        // column panels (column-major in the export)
+        std::vector<int32_t> adm(4 * na), rank(na), leaf_begin(nl + 1), up_K(nl), wp_K(nl), koff, lr_list, wkoff,
+            lr_collist;
+        std::vector<int64_t> lr_rowptr(nl + 1), up_off(nl + 1), lr_colptr(nl + 1), wp_off(nl + 1);
+        get(adm.data(), tr->adm, sizeof(int32_t) * 4 * na);
+        get(rank.data(), A->rank, sizeof(int32_t) * na);
+        get(leaf_begin.data(), tr->leaf_begin, sizeof(int32_t) * (nl + 1));
+        get(lr_rowptr.data(), tr->lr_rowptr, sizeof(int64_t) * (nl + 1));
+        get(lr_colptr.data(), tr->lr_colptr, sizeof(int64_t) * (nl + 1));
+        get(up_off.data(), A->up_off, sizeof(int64_t) * (nl + 1));
+        get(wp_off.data(), A->wp_off, sizeof(int64_t) * (nl + 1));
+        get(up_K.data(), A->up_K, sizeof(int32_t) * nl);
+        get(wp_K.data(), A->wp_K, sizeof(int32_t) * nl);
+        const int64_t np = lr_rowptr[nl], npc = lr_colptr[nl];
+        koff.resize(np);
+        lr_list.resize(np);
+        wkoff.resize(npc);
+        lr_collist.resize(npc);
+        get(koff.data(), A->up_koff, sizeof(int32_t) * np);
+        get(lr_list.data(), tr->lr_list, sizeof(int32_t) * np);
+        get(wkoff.data(), A->wp_koff, sizeof(int32_t) * npc);
+        get(lr_collist.data(), tr->lr_collist, sizeof(int32_t) * npc);
+        std::vector<double> up(A->up_entries), wp(A->wp_entries);
+        get(up.data(), A->up, sizeof(double) * A->up_entries);
+        get(wp.data(), A->wp, sizeof(double) * A->wp_entries);
+        o = 0;
         for (int64_t b = 0; b < na; ++b) {
             const int m = adm[4 * b + 1] - adm[4 * b], n = adm[4 * b + 3] - adm[4 * b + 2], k = rank[b];
             h_rank[b] = k;
-            h_u_off[b] = uwo[b];
-            h_w_off[b] = uwo[b] + (int64_t)m * k;
-            for (int64_t e = 0; e < (int64_t)m * k; ++e) h_uw[uwo[b] + e] = fac[uwo[b] + e];
-            for (int j = 0; j < n; ++j)
-                for (int l = 0; l < k; ++l)
-                    h_uw[h_w_off[b] + (int64_t)l * n + j] = fac[h_w_off[b] + (int64_t)j * k + l];
+            h_u_off[b] = o;
+            h_w_off[b] = o + (int64_t)m * k;
+            o += (int64_t)(m + n) * k;
+        }
+        for (int64_t c = 0; c < nl; ++c) {
+            const int32_t c0 = leaf_begin[c], mc = leaf_begin[c + 1] - c0;
+            for (int64_t q = lr_colptr[c]; q < lr_colptr[c + 1]; ++q) {
+                const int32_t b = lr_collist[q];
+                const int n = adm[4 * b + 3] - adm[4 * b + 2], k = rank[b], off = c0 - adm[4 * b + 2];
+                for (int j = 0; j < mc; ++j)
+                    for (int l = 0; l < k; ++l)
+                        h_uw[h_w_off[b] + (int64_t)l * n + off + j] = wp[wp_off[c] + (int64_t)j * wp_K[c] + wkoff[q] + l];
+            }
+        }
+        for (int64_t r = 0; r < nl; ++r) {
+            const int32_t r0 = leaf_begin[r], mr = leaf_begin[r + 1] - r0;
+            for (int64_t q = lr_rowptr[r]; q < lr_rowptr[r + 1]; ++q) {
+                const int32_t b = lr_list[q];
+                const int m = adm[4 * b + 1] - adm[4 * b], k = rank[b], off = r0 - adm[4 * b];
+                for (int i = 0; i < mr; ++i)
+                    for (int l = 0; l < k; ++l)
+                        h_uw[h_u_off[b] + (int64_t)l * m + off + i] = up[up_off[r] + (int64_t)i * up_K[r] + koff[q] + l];
+            }
         }
     });
 }

@@ -82,7 +82,9 @@ __device__ __forceinline__ double regular_entry_ff(const float *__restrict__ R, 
             bl[d][q] = C[(PF_AL + 7 * d + q) * cs];
         }
     float acc_h = 0.0f, acc_l = 0.0f;
-#pragma unroll
+    // the outer loop stays rolled: the 7-fold inner body is ~500 instructions
+    // and one copy of it keeps the instruction cache warm
+#pragma unroll 1
     for (int p = 0; p < NQ; ++p) {
         // X_p = D + a_p
         float Xh[3], Xl[3];

@@ -8,12 +8,19 @@
 //                    cluster of panels, and consecutive panels are consecutive
 //                    doubles in shared memory (conflict-free per-lane loads).
 //   dense near field: one row-major panel per leaf row cluster rho, of
-//                    |rho| x K_rho doubles, K_rho = sum of the widths of the
-//                    non-admissible leaves in rho's block row, concatenated in
-//                    column order (no padding).  Block b's entry (i, j) lives at
+//                    |rho| x Kd_rho, Kd_rho = sum of the widths of the
+//                    non-admissible leaves in rho's block row (concatenated in
+//                    column order) rounded up to a multiple of 8, so that every
+//                    row starts on a 16-byte boundary in FP64, FP32 and BF16;
+//                    padding columns hold 0.  Block b's entry (i, j) lives at
 //                    dense_base[b] + i * dense_ld[b] + j.
-//   low-rank factors: per admissible leaf b, U_b (m x k_b, column-major) then
-//                    W_b (n x k_b, row-major) at uw_off[b]; block ~ U_b W_b^T.
+//   low-rank rows:   for each rho a second row-major panel |rho| x Ku_rho that
+//                    concatenates U_b(rows of rho, :) over the admissible
+//                    leaves b whose rows cover rho (Ku_rho = sum of their
+//                    ranks, rounded up to 8), with the index t_off[b] + l of
+//                    the projection each column multiplies.
+//   W factors:       per admissible leaf, W_b row-major (n_b x k_b) at w_off[b]
+//                    in a compact arena; the block is U_b W_b^T.
 #pragma once
 
 #include <cuda.h>
@@ -161,16 +168,20 @@ struct hm_tree {
     hm::DBuf dense;       // [n_dense][4] int32, sorted by (row_begin, col_begin), rows = one leaf cluster
     hm::DBuf dense_base;  // [n_dense] int64, offset of entry (0, 0) in the near-field arena
     hm::DBuf dense_ld;    // [n_dense] int32, row stride in the arena
-    int64_t dense_entries = 0;
+    int64_t dense_entries = 0;  // arena size (with row padding)
+    int64_t dense_true = 0;     // sum over non-admissible leaves of |tau||sigma|
     hm::DBuf rho_off;     // [n_leaf + 1] int64, arena offset of each leaf row cluster's panel
     hm::DBuf rho_K;       // [n_leaf] int32, width of the panel
     hm::DBuf rho_colptr;  // [n_leaf + 1] int64, into colidx
-    hm::DBuf colidx;      // [sum K] int32, Morton column of each panel column
+    hm::DBuf colidx;      // [sum Kd] int32, Morton column of each panel column (0 for padding)
     int32_t max_dense_dim = 0;
     hm::DBuf adm;         // [n_adm][4] int32, in block-tree level order (largest first)
     int64_t adm_rows_cols = 0;
     hm::DBuf lr_rowptr;   // [n_leaf + 1] int64: admissible leaves whose rows cover each leaf cluster
     hm::DBuf lr_list;     // [..] int32 block ids (ascending per leaf cluster)
+    hm::DBuf lr_colptr;   // [n_leaf + 1] int64: admissible leaves whose columns cover each leaf cluster
+    hm::DBuf lr_collist;  // [..] int32 block ids (ascending per leaf cluster)
+    hm::DBuf lr_bcolptr;  // [n_adm + 1] int64: first (block, column leaf cluster) pair of each block
     int64_t singular_cap = 0;  // upper bound on touching pairs
     int64_t n_singular = 0;    // filled by hm_assemble
     double seconds = 0.0;
@@ -178,37 +189,47 @@ struct hm_tree {
     int32_t box_cols = 0;
 };
 
-// One admissible block as seen by one leaf row cluster rho of its rows.
-struct LrDesc {
-    int64_t uoff;  // element offset of U_b(row r0(rho) - rb, 0) in the factor arena
-    int64_t toff;  // offset of t_b = W_b^T x in the projection vector
-    int32_t ld;    // m_b, the column stride of U_b
-    int32_t k;     // rank
-};
-
 // Working vectors of one H-matrix-vector product (Morton order).
 struct MatvecWork {
     double *xm;   // [n]  input
     double *ym;   // [n]  output
     double *t;    // [total_rank] projections (FP64 product)
+    double *p;    // [n_partials] per-column-cluster partial projections (FP64)
     float *x32;   // [n]  input rounded to FP32 (low-precision products)
     float *t32;   // [total_rank] projections (low-precision products)
+    float *p32;   // [n_partials] partial projections (low-precision products)
 };
 
 struct hm_matrix {
     uint32_t magic = HM_MATRIX_MAGIC;
     const hm_tree *tree = nullptr;
     hm_assemble_params params{};
-    hm::DBuf dense;     // near-field arena, double
+    hm::DBuf dense;     // near-field row panels, double
     hm::DBuf dense32;   // optional FP32 copy
     hm::DBuf rank;      // [n_adm] int32
-    hm::DBuf uw_off;    // [n_adm] int64
-    hm::DBuf uw;        // factor arena, double
-    hm::DBuf uw32;      // optional FP32 copy
-    hm::DBuf uwbf;      // optional BF16 copy
-    int64_t lr_entries = 0;
     hm::DBuf t_off;     // [n_adm] int64, prefix sum of ranks
     int64_t total_rank = 0;
-    hm::DBuf lr_desc;   // [lr_list size] LrDesc: U rows of each (leaf row cluster, block) pair
+    int64_t lr_entries = 0;  // sum_b k_b (m_b + n_b)
+    // U_b rows, grouped by leaf row cluster
+    hm::DBuf up;        // low-rank row panels, double
+    hm::DBuf up32;      // optional FP32 copy
+    hm::DBuf upbf;      // optional BF16 copy
+    hm::DBuf up_off;    // [n_leaf + 1] int64, panel offsets
+    hm::DBuf up_K;      // [n_leaf] int32, padded panel widths
+    hm::DBuf up_colptr; // [n_leaf + 1] int64, into tidx
+    hm::DBuf tidx;      // [sum Ku] int32, projection index of each panel column (0 for padding)
+    hm::DBuf up_koff;   // [lr_list size] int32, first panel column of each (rho, block) pair
+    int64_t up_entries = 0;
+    // W_b rows, grouped by leaf column cluster kappa: panel |kappa| x Kw
+    hm::DBuf wp;        // low-rank column panels, double
+    hm::DBuf wp32;      // optional FP32 copy
+    hm::DBuf wpbf;      // optional BF16 copy
+    hm::DBuf wp_off;    // [n_leaf + 1] int64, panel offsets
+    hm::DBuf wp_K;      // [n_leaf] int32, padded panel widths
+    hm::DBuf wp_colptr; // [n_leaf + 1] int64, into the partial-projection vector
+    hm::DBuf wp_koff;   // [lr_collist size] int32, first panel column of each (kappa, block) pair
+    hm::DBuf pofs;      // [sum over blocks of column leaf clusters] int64: partial offsets per block
+    int64_t wp_entries = 0;
+    int64_t n_partials = 0;  // length of the partial-projection vector
     hm_matrix_info info{};
 };

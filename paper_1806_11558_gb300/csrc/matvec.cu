@@ -1,17 +1,17 @@
 // matvec.cu -- H-matrix-vector product (Sec. 2.3): dense leaves apply their
 // stored block, admissible leaves apply U_b (W_b^T x_sigma).
 //
-// Two passes, no floating-point atomics (results are bit-identical from run to
-// run):
-//   lr_project_kernel : t_b = W_b^T x_sigma for every admissible leaf (one warp
-//                       per leaf, lanes stream the columns of W_b).
-//   row_kernel        : one CTA per leaf row cluster rho owns y_rho:
-//                       y_rho = P_rho x(colidx) + sum_{b covers rho} U_b(rho, :) t_b,
-//                       where P_rho is rho's row panel of the near field (warp
-//                       per row, lanes stream the row) and the low-rank part is
-//                       split over (row, block-phase) threads and summed in a
-//                       fixed order.
-// Precisions: FP64 (master), or FP32 / BF16 copies with FP32 accumulation.
+// The factors are regrouped after assembly so that every pass streams
+// row-major panels with 16-byte loads (see hm_internal.cuh):
+//   col_kernel  : per leaf column cluster kappa, x_kappa^T times the panel of
+//                 W_b rows over the blocks whose columns cover kappa;
+//   tsum_kernel : t_b = sum of those partials over the column clusters of b;
+//   row_kernel  : per leaf row cluster rho, y_rho = (near-field panel) x(colidx)
+//                 + (U_b rows panel) t(tidx), with the gathered vector staged
+//                 in shared memory once per column chunk.
+// No floating-point atomics: every sum has a fixed order, so results are
+// bit-identical from run to run.  Precisions: FP64 (master), or FP32 / BF16
+// copies with FP32 accumulation.
 #include <cuda_bf16.h>
 
 #include <mutex>
@@ -53,144 +53,309 @@ __global__ void scatter_perm_kernel(const double *ym, const int32_t *perm, int64
 }
 
 // ---------------------------------------------------------------------------
-// t_b = W_b^T x_sigma, W_b row-major (n x k).  One warp per block: with
-// G = floor(32 / k) lane groups, lane (g, l) accumulates column l over rows
-// j = g, g + G, ..., so every load instruction reads G*k consecutive
-// elements; the G partials of a column are then summed in a fixed order.
+// 16-byte vector loads of panel rows (rows start on 16-byte boundaries)
 // ---------------------------------------------------------------------------
-template <class TF, class TX, class TT>
-__global__ void __launch_bounds__(256) lr_project_kernel(
-    const int32_t *__restrict__ adm, int64_t na, const int32_t *__restrict__ rank, const int64_t *__restrict__ uw_off,
-    const int64_t *__restrict__ t_off, const TF *__restrict__ uw, const TX *__restrict__ x, TT *__restrict__ t) {
+template <class T> struct V16;
+template <> struct V16<double> {
+    static constexpr int N = 2;
+    __device__ __forceinline__ static void load(const double *p, double (&v)[2]) {
+        const double2 d = __ldg(reinterpret_cast<const double2 *>(p));
+        v[0] = d.x;
+        v[1] = d.y;
+    }
+};
+template <> struct V16<float> {
+    static constexpr int N = 4;
+    __device__ __forceinline__ static void load(const float *p, float (&v)[4]) {
+        const float4 d = __ldg(reinterpret_cast<const float4 *>(p));
+        v[0] = d.x;
+        v[1] = d.y;
+        v[2] = d.z;
+        v[3] = d.w;
+    }
+};
+template <> struct V16<__nv_bfloat16> {
+    static constexpr int N = 8;
+    __device__ __forceinline__ static void load(const __nv_bfloat16 *p, float (&v)[8]) {
+        const uint4 d = __ldg(reinterpret_cast<const uint4 *>(p));
+        const uint32_t w[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            v[2 * q] = __uint_as_float(w[q] << 16);
+            v[2 * q + 1] = __uint_as_float(w[q] & 0xffff0000u);
+        }
+    }
+};
+
+// N consecutive column indices (N * 4 bytes, aligned like the values)
+template <int N> __device__ __forceinline__ void ld_idx(const int32_t *p, int (&o)[N]);
+template <> __device__ __forceinline__ void ld_idx<2>(const int32_t *p, int (&o)[2]) {
+    const int2 v = __ldg(reinterpret_cast<const int2 *>(p));
+    o[0] = v.x;
+    o[1] = v.y;
+}
+template <> __device__ __forceinline__ void ld_idx<4>(const int32_t *p, int (&o)[4]) {
+    const int4 v = __ldg(reinterpret_cast<const int4 *>(p));
+    o[0] = v.x;
+    o[1] = v.y;
+    o[2] = v.z;
+    o[3] = v.w;
+}
+template <> __device__ __forceinline__ void ld_idx<8>(const int32_t *p, int (&o)[8]) {
+    const int4 v = __ldg(reinterpret_cast<const int4 *>(p)), w = __ldg(reinterpret_cast<const int4 *>(p + 4));
+    o[0] = v.x;
+    o[1] = v.y;
+    o[2] = v.z;
+    o[3] = v.w;
+    o[4] = w.x;
+    o[5] = w.y;
+    o[6] = w.z;
+    o[7] = w.w;
+}
+
+// ---------------------------------------------------------------------------
+// Phase A, t_b = W_b^T x_sigma, in two steps:
+//  col_kernel : one CTA per leaf column cluster kappa computes the row vector
+//               x_kappa^T Wt_kappa of kappa's column panel (the rows of every
+//               W_b whose columns cover kappa, side by side): each thread owns
+//               16 bytes of columns and accumulates over the |kappa| rows in
+//               registers, so every thread keeps |kappa| independent 16-byte
+//               loads in flight and no reduction is needed.
+//  tsum_kernel: t_b(l) = sum over the column clusters of sigma_b of those
+//               partials, in increasing cluster order (fixed order).
+// ---------------------------------------------------------------------------
+constexpr int COL_THREADS = 256;
+
+template <class TF, class TX, class TP>
+__global__ void __launch_bounds__(COL_THREADS) col_kernel(const int32_t *__restrict__ leaf_begin,
+                                                          const int64_t *__restrict__ wp_off,
+                                                          const int32_t *__restrict__ wp_K,
+                                                          const int64_t *__restrict__ wp_colptr,
+                                                          const TF *__restrict__ wp, const TX *__restrict__ x,
+                                                          TP *__restrict__ p) {
     using A = typename Acc<TF>::type;
-    __shared__ A s_part[8][32];
-    const int lane = threadIdx.x & 31, wl = threadIdx.x >> 5;
+    constexpr int N = V16<TF>::N;
+    __shared__ A s_x[MAX_LEAF];
+    const int64_t kap = blockIdx.x;
+    const int32_t c0 = leaf_begin[kap], mc = leaf_begin[kap + 1] - c0;
+    for (int j = threadIdx.x; j < mc; j += COL_THREADS) s_x[j] = (A)x[c0 + j];
+    __syncthreads();
+    const int Kw = wp_K[kap];
+    const TF *W = wp + wp_off[kap];
+    TP *out = p + wp_colptr[kap];
+    const int nv = Kw / N;
+    for (int v = threadIdx.x; v < nv; v += COL_THREADS) {
+        A acc[N];
+#pragma unroll
+        for (int e = 0; e < N; ++e) acc[e] = 0;
+        const TF *col = W + (int64_t)v * N;
+        int j = 0;
+        for (; j + 3 < mc; j += 4) {
+            A w0[N], w1[N], w2[N], w3[N];
+            V16<TF>::load(col + (int64_t)j * Kw, w0);
+            V16<TF>::load(col + (int64_t)(j + 1) * Kw, w1);
+            V16<TF>::load(col + (int64_t)(j + 2) * Kw, w2);
+            V16<TF>::load(col + (int64_t)(j + 3) * Kw, w3);
+#pragma unroll
+            for (int e = 0; e < N; ++e) {
+                acc[e] += w0[e] * s_x[j];
+                acc[e] += w1[e] * s_x[j + 1];
+                acc[e] += w2[e] * s_x[j + 2];
+                acc[e] += w3[e] * s_x[j + 3];
+            }
+        }
+        for (; j < mc; ++j) {
+            A w0[N];
+            V16<TF>::load(col + (int64_t)j * Kw, w0);
+#pragma unroll
+            for (int e = 0; e < N; ++e) acc[e] += w0[e] * s_x[j];
+        }
+#pragma unroll
+        for (int e = 0; e < N; ++e) out[v * N + e] = (TP)acc[e];
+    }
+}
+
+template <class TP, class TT>
+__global__ void tsum_kernel(int64_t na, const int32_t *__restrict__ rank, const int64_t *__restrict__ t_off,
+                            const int64_t *__restrict__ bcolptr, const int64_t *__restrict__ pofs,
+                            const TP *__restrict__ p, TT *__restrict__ t) {
+    const int lane = threadIdx.x & 31;
     const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t b = w0; b < na; b += nw) {
         const int k = rank[b];
-        if (k == 0) continue;
-        const int32_t rb = adm[4 * b], re = adm[4 * b + 1], cb = adm[4 * b + 2], ce = adm[4 * b + 3];
-        const int m = re - rb, n = ce - cb;
-        const TF *W = uw + uw_off[b] + (int64_t)m * k;
-        const int64_t to = t_off[b];
-        for (int c0 = 0; c0 < k; c0 += 32) {
-            const int kc = min(32, k - c0);
-            const int G = 32 / kc;
-            const int g = lane / kc, l = lane - g * kc;
-            A acc = 0;
-            if (g < G) {
-                const TF *Wc = W + c0 + l;
-                int j = g;
-                for (; j + 3 * G < n; j += 4 * G) {
-                    const A w0v = ld_el<TF>(Wc + (int64_t)j * k), w1v = ld_el<TF>(Wc + (int64_t)(j + G) * k);
-                    const A w2v = ld_el<TF>(Wc + (int64_t)(j + 2 * G) * k), w3v = ld_el<TF>(Wc + (int64_t)(j + 3 * G) * k);
-                    acc += w0v * (A)x[cb + j];
-                    acc += w1v * (A)x[cb + j + G];
-                    acc += w2v * (A)x[cb + j + 2 * G];
-                    acc += w3v * (A)x[cb + j + 3 * G];
-                }
-                for (; j < n; j += G) acc += ld_el<TF>(Wc + (int64_t)j * k) * (A)x[cb + j];
-            }
-            s_part[wl][lane] = acc;
-            __syncwarp();
-            if (lane < kc) {
-                A s = 0;
-                for (int q = 0; q < G; ++q) s += s_part[wl][q * kc + lane];
-                t[to + c0 + lane] = (TT)s;
-            }
-            __syncwarp();
+        const int64_t q0 = bcolptr[b], q1 = bcolptr[b + 1];
+        for (int l = lane; l < k; l += 32) {
+            TP acc = 0;
+            for (int64_t q = q0; q < q1; ++q) acc += p[pofs[q] + l];
+            t[t_off[b] + l] = (TT)acc;
         }
     }
 }
 
 // ---------------------------------------------------------------------------
-// y_rho = dense panel part + low-rank part, one CTA per leaf row cluster
+// y_rho = P_rho x(colidx) + Ut_rho t(tidx): one CTA per leaf row cluster.
+// Every row of a panel multiplies the same gathered vector, so the CTA
+// gathers it once per column chunk into shared memory; then each warp takes
+// RB rows at a time and streams them with 16-byte loads against the staged
+// chunk (one shared-memory vector feeds RB independent global loads).
 // ---------------------------------------------------------------------------
 constexpr int ROW_THREADS = 256;
+constexpr int ROW_WARPS = ROW_THREADS / 32;
+constexpr int ROW_CHUNK = 2048;  // columns staged per pass (multiple of 8)
+constexpr int RB = 4;            // rows per warp per pass: a row group is RB * ROW_WARPS rows
+
+// Partial sums (per lane) of rows g0 + warp + ROW_WARPS * u, u < RB, of a
+// row-major panel P (|rho| x L) times z(idx), staging z(idx) chunk by chunk.
+template <class T, class Z, class A>
+__device__ __forceinline__ void panel_rows(const T *__restrict__ P, int L, const int32_t *__restrict__ idx,
+                                           const Z *__restrict__ z, int mr, int g0, A *s_z, A (&a)[RB]) {
+    constexpr int N = V16<T>::N;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const T *rows[RB];
+    bool live[RB];
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+        const int r = g0 + warp + ROW_WARPS * u;
+        live[u] = r < mr;
+        rows[u] = P + (int64_t)(live[u] ? r : 0) * L;
+        a[u] = 0;
+    }
+    for (int c0 = 0; c0 < L; c0 += ROW_CHUNK) {
+        const int cl = min(ROW_CHUNK, L - c0);
+        __syncthreads();
+        for (int k = threadIdx.x; k < cl; k += ROW_THREADS) s_z[k] = (A)z[idx[c0 + k]];
+        __syncthreads();
+        const int nv = cl / N;
+        for (int v = lane; v < nv; v += 32) {
+            A zv[N];
+#pragma unroll
+            for (int e = 0; e < N; ++e) zv[e] = s_z[v * N + e];
+#pragma unroll
+            for (int u = 0; u < RB; ++u) {
+                if (!live[u]) continue;
+                A pv[N];
+                V16<T>::load(rows[u] + c0 + (int64_t)v * N, pv);
+#pragma unroll
+                for (int e = 0; e < N; ++e) a[u] += pv[e] * zv[e];
+            }
+        }
+    }
+}
 
 template <class TD, class TF, class TX, class TT>
 __global__ void __launch_bounds__(ROW_THREADS) row_kernel(
     const int32_t *__restrict__ leaf_begin, const int64_t *__restrict__ rho_off, const int32_t *__restrict__ rho_K,
     const int64_t *__restrict__ rho_colptr, const int32_t *__restrict__ colidx, const TD *__restrict__ dense,
-    const int64_t *__restrict__ lr_rowptr, const LrDesc *__restrict__ desc, const TF *__restrict__ uw,
-    const TT *__restrict__ t, const TX *__restrict__ x, double *__restrict__ ym) {
+    const int64_t *__restrict__ up_off, const int32_t *__restrict__ up_K, const int64_t *__restrict__ up_colptr,
+    const int32_t *__restrict__ tidx, const TF *__restrict__ up, const TT *__restrict__ t, const TX *__restrict__ x,
+    double *__restrict__ ym) {
     using AD = typename Acc<TD>::type;
     using AF = typename Acc<TF>::type;
-    __shared__ AD s_dense[MAX_LEAF];
-    __shared__ AF s_lr[ROW_THREADS];
+    __shared__ __align__(16) unsigned char s_raw[ROW_CHUNK * sizeof(AD)];
     const int64_t rho = blockIdx.x;
     const int32_t r0 = leaf_begin[rho], r1 = leaf_begin[rho + 1];
     const int mr = r1 - r0;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = ROW_THREADS / 32;
-    // dense near field: warp per row of rho's panel, lanes along the row
-    {
-        const int K = rho_K[rho];
-        const TD *P = dense + rho_off[rho];
-        const int32_t *ci = colidx + rho_colptr[rho];
-        for (int i = warp; i < mr; i += nwarp) {
-            AD acc = 0;
-            const TD *row = P + (int64_t)i * K;
-            int k = lane;
-            for (; k + 96 < K; k += 128) {
-                const int c0 = ci[k], c1 = ci[k + 32], c2 = ci[k + 64], c3 = ci[k + 96];
-                const AD a0 = ld_el<TD>(row + k), a1 = ld_el<TD>(row + k + 32);
-                const AD a2 = ld_el<TD>(row + k + 64), a3 = ld_el<TD>(row + k + 96);
-                acc += a0 * (AD)x[c0];
-                acc += a1 * (AD)x[c1];
-                acc += a2 * (AD)x[c2];
-                acc += a3 * (AD)x[c3];
-            }
-            for (; k < K; k += 32) acc += ld_el<TD>(row + k) * (AD)x[ci[k]];
-            acc = warp_reduce(acc);
-            if (lane == 0) s_dense[i] = acc;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const TD *P = dense + rho_off[rho];
+    const int Kd = rho_K[rho];
+    const int32_t *ci = colidx + rho_colptr[rho];
+    const TF *Q = up + up_off[rho];
+    const int Ku = up_K[rho];
+    const int32_t *ti = tidx + up_colptr[rho];
+    for (int g0 = 0; g0 < mr; g0 += RB * ROW_WARPS) {
+        AD ad[RB];
+        AF af[RB];
+        panel_rows<TD, TX, AD>(P, Kd, ci, x, mr, g0, reinterpret_cast<AD *>(s_raw), ad);
+        panel_rows<TF, TT, AF>(Q, Ku, ti, t, mr, g0, reinterpret_cast<AF *>(s_raw), af);
+#pragma unroll
+        for (int u = 0; u < RB; ++u) {
+            const int r = g0 + warp + ROW_WARPS * u;
+            const AD d = warp_reduce(ad[u]);
+            const AF f = warp_reduce(af[u]);
+            if (lane == 0 && r < mr) ym[r0 + r] = (double)d + (double)f;
         }
-    }
-    // low rank: thread (i, p) with p = phase over the blocks covering rho
-    const int64_t l0 = lr_rowptr[rho], l1 = lr_rowptr[rho + 1];
-    const int phases = ROW_THREADS / mr;  // >= 1 since mr <= MAX_LEAF <= ROW_THREADS
-    const int i = threadIdx.x % mr, p = threadIdx.x / mr;
-    AF acc = 0;
-    if (p < phases) {
-        for (int64_t q = l0 + p; q < l1; q += phases) {
-            const LrDesc d = desc[q];
-            const TF *U = uw + d.uoff + i;
-            const TT *tb = t + d.toff;
-            int l = 0;
-            for (; l + 3 < d.k; l += 4) {
-                const AF u0 = ld_el<TF>(U + (int64_t)l * d.ld), u1 = ld_el<TF>(U + (int64_t)(l + 1) * d.ld);
-                const AF u2 = ld_el<TF>(U + (int64_t)(l + 2) * d.ld), u3 = ld_el<TF>(U + (int64_t)(l + 3) * d.ld);
-                acc += u0 * (AF)tb[l];
-                acc += u1 * (AF)tb[l + 1];
-                acc += u2 * (AF)tb[l + 2];
-                acc += u3 * (AF)tb[l + 3];
-            }
-            for (; l < d.k; ++l) acc += ld_el<TF>(U + (int64_t)l * d.ld) * (AF)tb[l];
-        }
-    }
-    s_lr[threadIdx.x] = acc;
-    __syncthreads();
-    if (threadIdx.x < mr) {
-        AF s = 0;
-        for (int q = 0; q < phases; ++q) s += s_lr[q * mr + threadIdx.x];
-        ym[r0 + threadIdx.x] = (double)s_dense[threadIdx.x] + (double)s;
     }
 }
 
-// descriptors of the (leaf row cluster, admissible block) pairs
-__global__ void lr_desc_kernel(const int32_t *leaf_begin, int64_t nleaf, const int64_t *lr_rowptr,
-                               const int32_t *lr_list, const int32_t *adm, const int32_t *rank, const int64_t *uw_off,
-                               const int64_t *t_off, LrDesc *desc) {
+// ---------------------------------------------------------------------------
+// packing of the ACA factors into low-rank row panels and the W arena
+// ---------------------------------------------------------------------------
+// per leaf row cluster: padded width of its low-rank panel and the first
+// panel column of each of its (rho, block) pairs
+__global__ void up_width_kernel(const int32_t *leaf_begin, int64_t nleaf, const int64_t *lr_rowptr,
+                                const int32_t *lr_list, const int32_t *rank, int32_t *koff, int32_t *up_K,
+                                int64_t *up_size, int64_t *up_kpad) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nleaf; r += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t r0 = leaf_begin[r];
+        int64_t acc = 0;
         for (int64_t q = lr_rowptr[r]; q < lr_rowptr[r + 1]; ++q) {
-            const int32_t b = lr_list[q];
-            LrDesc d;
-            d.uoff = uw_off[b] + (r0 - adm[4 * b]);
-            d.toff = t_off[b];
-            d.ld = adm[4 * b + 1] - adm[4 * b];
-            d.k = rank[b];
-            desc[q] = d;
+            koff[q] = (int32_t)acc;
+            acc += rank[lr_list[q]];
+        }
+        const int64_t Kp = (acc + 7) / 8 * 8;
+        up_K[r] = (int32_t)Kp;
+        up_size[r] = (int64_t)(leaf_begin[r + 1] - leaf_begin[r]) * Kp;
+        up_kpad[r] = Kp;
+    }
+}
+
+__global__ void up_pack_kernel(const int32_t *leaf_begin, const int64_t *lr_rowptr, const int32_t *lr_list,
+                               const int32_t *adm, const int32_t *rank, const int64_t *t_off, const int64_t *uw_off,
+                               const double *uw, const int32_t *koff, const int64_t *up_off, const int32_t *up_K,
+                               const int64_t *up_colptr, double *up, int32_t *tidx) {
+    const int64_t r = blockIdx.x;
+    const int32_t r0 = leaf_begin[r], mr = leaf_begin[r + 1] - r0;
+    const int Ku = up_K[r];
+    double *Q = up + up_off[r];
+    int32_t *ti = tidx + up_colptr[r];
+    for (int64_t q = lr_rowptr[r]; q < lr_rowptr[r + 1]; ++q) {
+        const int32_t b = lr_list[q];
+        const int k = rank[b], m = adm[4 * b + 1] - adm[4 * b], off = r0 - adm[4 * b], c = koff[q];
+        const double *U = uw + uw_off[b];
+        for (int e = threadIdx.x; e < mr * k; e += blockDim.x) {
+            const int i = e / k, l = e - (e / k) * k;
+            Q[(int64_t)i * Ku + c + l] = U[(int64_t)l * m + off + i];
+        }
+        for (int l = threadIdx.x; l < k; l += blockDim.x) ti[c + l] = (int32_t)(t_off[b] + l);
+    }
+}
+
+// column panels of W: per leaf column cluster kappa, W_b(rows of kappa, :)
+// over the admissible leaves whose columns cover kappa
+__global__ void wp_pack_kernel(const int32_t *leaf_begin, const int64_t *lr_colptr, const int32_t *lr_collist,
+                               const int32_t *adm, const int32_t *rank, const int64_t *uw_off, const double *uw,
+                               const int32_t *koff, const int64_t *wp_off, const int32_t *wp_K, double *wp) {
+    const int64_t kap = blockIdx.x;
+    const int32_t c0 = leaf_begin[kap], mc = leaf_begin[kap + 1] - c0;
+    const int Kw = wp_K[kap];
+    double *Wt = wp + wp_off[kap];
+    for (int64_t q = lr_colptr[kap]; q < lr_colptr[kap + 1]; ++q) {
+        const int32_t b = lr_collist[q];
+        const int k = rank[b], m = adm[4 * b + 1] - adm[4 * b], off = c0 - adm[4 * b + 2], c = koff[q];
+        const double *W = uw + uw_off[b] + (int64_t)m * k;  // row-major n x k
+        for (int e = threadIdx.x; e < mc * k; e += blockDim.x) {
+            const int j = e / k, l = e - (e / k) * k;
+            Wt[(int64_t)j * Kw + c + l] = W[(int64_t)(off + j) * k + l];
+        }
+    }
+}
+
+// offset of the partial projection of each (block, column leaf cluster) pair
+__global__ void pofs_kernel(const int32_t *leaf_begin, int64_t nleaf, const int64_t *lr_colptr,
+                            const int32_t *lr_collist, const int32_t *adm, const int64_t *wp_colptr,
+                            const int32_t *koff, const int64_t *bcolptr, int64_t *pofs) {
+    for (int64_t kap = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; kap < nleaf;
+         kap += (int64_t)gridDim.x * blockDim.x) {
+        for (int64_t q = lr_colptr[kap]; q < lr_colptr[kap + 1]; ++q) {
+            const int32_t b = lr_collist[q];
+            int64_t lo = 0, hi = nleaf;
+            const int32_t cb = adm[4 * b + 2];
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (leaf_begin[mid] < cb) lo = mid + 1;
+                else hi = mid;
+            }
+            pofs[bcolptr[b] + (kap - lo)] = wp_colptr[kap] + koff[q];
         }
     }
 }
@@ -218,34 +383,92 @@ void permute_from_morton(const hm_tree *tr, const double *ym, double alpha, doub
     HM_LAUNCH_CHECK();
 }
 
-void build_lr_desc(hm_matrix *A, cudaStream_t s) {
+// Regroups the ACA output (uw: U_b column-major then W_b row-major at
+// uw_off[b]) into the low-rank row panels (U) and column panels (W).
+void build_lr_panels(hm_matrix *A, const DBuf &uw, const DBuf &uw_off, cudaStream_t s) {
     const hm_tree *tr = A->tree;
-    const int64_t np = read_scalar(tr->lr_rowptr.as<int64_t>() + tr->n_leaf, s);
-    A->lr_desc.alloc(sizeof(LrDesc) * std::max<int64_t>(np, 1));
-    if (np == 0) return;
-    lr_desc_kernel<<<grid1d(tr->n_leaf), 256, 0, s>>>(tr->leaf_begin.as<int32_t>(), tr->n_leaf,
-                                                     tr->lr_rowptr.as<int64_t>(), tr->lr_list.as<int32_t>(),
-                                                     tr->adm.as<int32_t>(), A->rank.as<int32_t>(),
-                                                     A->uw_off.as<int64_t>(), A->t_off.as<int64_t>(),
-                                                     A->lr_desc.as<LrDesc>());
+    const int64_t nl = tr->n_leaf, na = tr->n_adm;
+    const int64_t np = read_scalar(tr->lr_rowptr.as<int64_t>() + nl, s);
+    A->up_koff.alloc(sizeof(int32_t) * std::max<int64_t>(np, 1));
+    A->up_K.alloc(sizeof(int32_t) * nl);
+    A->up_off.alloc(sizeof(int64_t) * (nl + 1));
+    A->up_colptr.alloc(sizeof(int64_t) * (nl + 1));
+    DBuf size, kpad;
+    size.alloc(sizeof(int64_t) * (nl + 1));
+    kpad.alloc(sizeof(int64_t) * (nl + 1));
+    up_width_kernel<<<grid1d(nl), 256, 0, s>>>(tr->leaf_begin.as<int32_t>(), nl, tr->lr_rowptr.as<int64_t>(),
+                                              tr->lr_list.as<int32_t>(), A->rank.as<int32_t>(),
+                                              A->up_koff.as<int32_t>(), A->up_K.as<int32_t>(), size.as<int64_t>(),
+                                              kpad.as<int64_t>());
     HM_LAUNCH_CHECK();
+    HM_CUDA_CHECK(cudaMemsetAsync(size.as<int64_t>() + nl, 0, sizeof(int64_t), s));
+    HM_CUDA_CHECK(cudaMemsetAsync(kpad.as<int64_t>() + nl, 0, sizeof(int64_t), s));
+    A->up_entries = exclusive_scan_i64(size.as<int64_t>(), A->up_off.as<int64_t>(), nl + 1, s);
+    const int64_t ncol = exclusive_scan_i64(kpad.as<int64_t>(), A->up_colptr.as<int64_t>(), nl + 1, s);
+    A->up.alloc(sizeof(double) * std::max<int64_t>(A->up_entries, 8));
+    HM_CUDA_CHECK(cudaMemsetAsync(A->up.p, 0, sizeof(double) * std::max<int64_t>(A->up_entries, 8), s));
+    A->tidx.alloc(sizeof(int32_t) * std::max<int64_t>(ncol, 8));
+    HM_CUDA_CHECK(cudaMemsetAsync(A->tidx.p, 0, sizeof(int32_t) * std::max<int64_t>(ncol, 8), s));
+    if (na > 0 && nl > 0) {
+        up_pack_kernel<<<(unsigned)nl, 256, 0, s>>>(
+            tr->leaf_begin.as<int32_t>(), tr->lr_rowptr.as<int64_t>(), tr->lr_list.as<int32_t>(),
+            tr->adm.as<int32_t>(), A->rank.as<int32_t>(), A->t_off.as<int64_t>(), uw_off.as<int64_t>(),
+            uw.as<double>(), A->up_koff.as<int32_t>(), A->up_off.as<int64_t>(), A->up_K.as<int32_t>(),
+            A->up_colptr.as<int64_t>(), A->up.as<double>(), A->tidx.as<int32_t>());
+        HM_LAUNCH_CHECK();
+    }
+    // W column panels and the partial-projection map
+    A->wp_koff.alloc(sizeof(int32_t) * std::max<int64_t>(read_scalar(tr->lr_colptr.as<int64_t>() + nl, s), 1));
+    A->wp_K.alloc(sizeof(int32_t) * nl);
+    A->wp_off.alloc(sizeof(int64_t) * (nl + 1));
+    A->wp_colptr.alloc(sizeof(int64_t) * (nl + 1));
+    up_width_kernel<<<grid1d(nl), 256, 0, s>>>(tr->leaf_begin.as<int32_t>(), nl, tr->lr_colptr.as<int64_t>(),
+                                              tr->lr_collist.as<int32_t>(), A->rank.as<int32_t>(),
+                                              A->wp_koff.as<int32_t>(), A->wp_K.as<int32_t>(), size.as<int64_t>(),
+                                              kpad.as<int64_t>());
+    HM_LAUNCH_CHECK();
+    HM_CUDA_CHECK(cudaMemsetAsync(size.as<int64_t>() + nl, 0, sizeof(int64_t), s));
+    HM_CUDA_CHECK(cudaMemsetAsync(kpad.as<int64_t>() + nl, 0, sizeof(int64_t), s));
+    A->wp_entries = exclusive_scan_i64(size.as<int64_t>(), A->wp_off.as<int64_t>(), nl + 1, s);
+    A->n_partials = exclusive_scan_i64(kpad.as<int64_t>(), A->wp_colptr.as<int64_t>(), nl + 1, s);
+    A->wp.alloc(sizeof(double) * std::max<int64_t>(A->wp_entries, 8));
+    HM_CUDA_CHECK(cudaMemsetAsync(A->wp.p, 0, sizeof(double) * std::max<int64_t>(A->wp_entries, 8), s));
+    const int64_t npairs = read_scalar(tr->lr_bcolptr.as<int64_t>() + na, s);
+    A->pofs.alloc(sizeof(int64_t) * std::max<int64_t>(npairs, 1));
+    if (na > 0 && nl > 0) {
+        wp_pack_kernel<<<(unsigned)nl, 256, 0, s>>>(tr->leaf_begin.as<int32_t>(), tr->lr_colptr.as<int64_t>(),
+                                                   tr->lr_collist.as<int32_t>(), tr->adm.as<int32_t>(),
+                                                   A->rank.as<int32_t>(), uw_off.as<int64_t>(), uw.as<double>(),
+                                                   A->wp_koff.as<int32_t>(), A->wp_off.as<int64_t>(),
+                                                   A->wp_K.as<int32_t>(), A->wp.as<double>());
+        HM_LAUNCH_CHECK();
+        pofs_kernel<<<grid1d(nl), 256, 0, s>>>(tr->leaf_begin.as<int32_t>(), nl, tr->lr_colptr.as<int64_t>(),
+                                              tr->lr_collist.as<int32_t>(), tr->adm.as<int32_t>(),
+                                              A->wp_colptr.as<int64_t>(), A->wp_koff.as<int32_t>(),
+                                              tr->lr_bcolptr.as<int64_t>(), A->pofs.as<int64_t>());
+        HM_LAUNCH_CHECK();
+    }
 }
 
 template <class TD, class TF, class TX, class TT>
-static void matvec_impl(const hm_matrix *A, const TD *dense, const TF *uw, const TX *x, TT *t, double *ym,
-                        cudaStream_t s) {
+static void matvec_impl(const hm_matrix *A, const TD *dense, const TF *up, const TF *wp, const TX *x, TT *p, TT *t,
+                        double *ym, cudaStream_t s) {
     const hm_tree *tr = A->tree;
     if (tr->n_adm > 0) {
-        const int64_t warps = tr->n_adm;
-        lr_project_kernel<TF, TX, TT><<<grid1d(warps * 32), 256, 0, s>>>(
-            tr->adm.as<int32_t>(), tr->n_adm, A->rank.as<int32_t>(), A->uw_off.as<int64_t>(),
-            A->t_off.as<int64_t>(), uw, x, t);
+        col_kernel<TF, TX, TT><<<(unsigned)tr->n_leaf, COL_THREADS, 0, s>>>(
+            tr->leaf_begin.as<int32_t>(), A->wp_off.as<int64_t>(), A->wp_K.as<int32_t>(), A->wp_colptr.as<int64_t>(),
+            wp, x, p);
+        HM_LAUNCH_CHECK();
+        tsum_kernel<TT, TT><<<grid1d(tr->n_adm * 32), 256, 0, s>>>(tr->n_adm, A->rank.as<int32_t>(),
+                                                                  A->t_off.as<int64_t>(),
+                                                                  tr->lr_bcolptr.as<int64_t>(),
+                                                                  A->pofs.as<int64_t>(), p, t);
         HM_LAUNCH_CHECK();
     }
     row_kernel<TD, TF, TX, TT><<<(unsigned)tr->n_leaf, ROW_THREADS, 0, s>>>(
         tr->leaf_begin.as<int32_t>(), tr->rho_off.as<int64_t>(), tr->rho_K.as<int32_t>(),
-        tr->rho_colptr.as<int64_t>(), tr->colidx.as<int32_t>(), dense, tr->lr_rowptr.as<int64_t>(),
-        A->lr_desc.as<LrDesc>(), uw, t, x, ym);
+        tr->rho_colptr.as<int64_t>(), tr->colidx.as<int32_t>(), dense, A->up_off.as<int64_t>(),
+        A->up_K.as<int32_t>(), A->up_colptr.as<int64_t>(), A->tidx.as<int32_t>(), up, t, x, ym);
     HM_LAUNCH_CHECK();
 }
 
@@ -255,42 +478,48 @@ void matvec_morton(const hm_matrix *A, hm_dtype prec, const MatvecWork &w, cudaS
     const int64_t n = A->tree->n;
     switch (prec) {
         case HM_F64:
-            matvec_impl<double, double, double, double>(A, A->dense.as<double>(), A->uw.as<double>(), w.xm, w.t, w.ym,
-                                                        s);
+            matvec_impl<double, double, double, double>(A, A->dense.as<double>(), A->up.as<double>(),
+                                                        A->wp.as<double>(), w.xm, w.p, w.t, w.ym, s);
             break;
         case HM_F32:
         case HM_BF16:
-            if (!A->dense32.p || (prec == HM_F32 ? !A->uw32.p : !A->uwbf.p))
+            if (!A->dense32.p || (prec == HM_F32 ? !A->up32.p : !A->upbf.p))
                 fail(HM_EINVAL, "the low-precision copies for this precision were not assembled");
             round_f32_kernel<<<grid1d(n), 256, 0, s>>>(w.xm, n, w.x32);
             HM_LAUNCH_CHECK();
             if (prec == HM_F32)
-                matvec_impl<float, float, float, float>(A, A->dense32.as<float>(), A->uw32.as<float>(), w.x32, w.t32,
-                                                        w.ym, s);
+                matvec_impl<float, float, float, float>(A, A->dense32.as<float>(), A->up32.as<float>(),
+                                                        A->wp32.as<float>(), w.x32, w.p32, w.t32, w.ym, s);
             else
-                matvec_impl<float, __nv_bfloat16, float, float>(A, A->dense32.as<float>(), A->uwbf.as<__nv_bfloat16>(),
-                                                                w.x32, w.t32, w.ym, s);
+                matvec_impl<float, __nv_bfloat16, float, float>(A, A->dense32.as<float>(),
+                                                                A->upbf.as<__nv_bfloat16>(),
+                                                                A->wpbf.as<__nv_bfloat16>(), w.x32, w.p32, w.t32,
+                                                                w.ym, s);
             break;
         default:
             fail(HM_EINVAL, "unknown precision %d", (int)prec);
     }
 }
 
-// Device workspace of hm_matvec / the solver: xm, ym [n], t [total_rank]
-// doubles, then x32 [n] and t32 [total_rank] floats.
+// Device workspace of hm_matvec / the solver: xm, ym [n], t [K], p [P]
+// doubles, then x32 [n], t32 [K], p32 [P] floats (K = sum of ranks, P = the
+// partial projections of the column panels).
 int64_t matvec_work_doubles(const hm_matrix *A) {
-    const int64_t n = A->tree->n, r = std::max<int64_t>(A->total_rank, 1);
-    return 2 * n + r + (n + 1) / 2 + (r + 1) / 2;
+    const int64_t n = A->tree->n, r = std::max<int64_t>(A->total_rank, 1), q = std::max<int64_t>(A->n_partials, 1);
+    return 2 * n + r + q + (n + 1) / 2 + (r + 1) / 2 + (q + 1) / 2;
 }
 
 MatvecWork matvec_work_at(const hm_matrix *A, double *base) {
-    const int64_t n = A->tree->n, r = std::max<int64_t>(A->total_rank, 1);
+    const int64_t n = A->tree->n, r = std::max<int64_t>(A->total_rank, 1), q = std::max<int64_t>(A->n_partials, 1);
     MatvecWork w;
     w.xm = base;
     w.ym = base + n;
     w.t = base + 2 * n;
-    w.x32 = reinterpret_cast<float *>(base + 2 * n + r);
-    w.t32 = reinterpret_cast<float *>(base + 2 * n + r + (n + 1) / 2);
+    w.p = base + 2 * n + r;
+    double *f = base + 2 * n + r + q;
+    w.x32 = reinterpret_cast<float *>(f);
+    w.t32 = reinterpret_cast<float *>(f + (n + 1) / 2);
+    w.p32 = reinterpret_cast<float *>(f + (n + 1) / 2 + (r + 1) / 2);
     return w;
 }
 
@@ -309,19 +538,26 @@ __global__ void to_bf16_kernel(const double *a, int64_t n, __nv_bfloat16 *o) {
 
 void make_low_copies(hm_matrix *A, cudaStream_t s) {
     const hm_assemble_params &p = A->params;
-    const int64_t nd = A->tree->dense_entries, nf = A->lr_entries;
+    const int64_t nd = A->tree->dense_entries, nu = std::max<int64_t>(A->up_entries, 8),
+                  nw = std::max<int64_t>(A->wp_entries, 8);
     if (p.dense_dtype == HM_F32 || p.factor_dtype != HM_F64) {
         A->dense32.alloc(sizeof(float) * std::max<int64_t>(nd, 1));
         to_f32_kernel<<<grid1d(nd), 256, 0, s>>>(A->dense.as<double>(), nd, A->dense32.as<float>());
         HM_LAUNCH_CHECK();
     }
     if (p.factor_dtype == HM_F32) {
-        A->uw32.alloc(sizeof(float) * std::max<int64_t>(nf, 1));
-        to_f32_kernel<<<grid1d(nf), 256, 0, s>>>(A->uw.as<double>(), nf, A->uw32.as<float>());
+        A->up32.alloc(sizeof(float) * nu);
+        A->wp32.alloc(sizeof(float) * nw);
+        to_f32_kernel<<<grid1d(nu), 256, 0, s>>>(A->up.as<double>(), nu, A->up32.as<float>());
+        HM_LAUNCH_CHECK();
+        to_f32_kernel<<<grid1d(nw), 256, 0, s>>>(A->wp.as<double>(), nw, A->wp32.as<float>());
         HM_LAUNCH_CHECK();
     } else if (p.factor_dtype == HM_BF16) {
-        A->uwbf.alloc(sizeof(__nv_bfloat16) * std::max<int64_t>(nf, 1));
-        to_bf16_kernel<<<grid1d(nf), 256, 0, s>>>(A->uw.as<double>(), nf, A->uwbf.as<__nv_bfloat16>());
+        A->upbf.alloc(sizeof(__nv_bfloat16) * nu);
+        A->wpbf.alloc(sizeof(__nv_bfloat16) * nw);
+        to_bf16_kernel<<<grid1d(nu), 256, 0, s>>>(A->up.as<double>(), nu, A->upbf.as<__nv_bfloat16>());
+        HM_LAUNCH_CHECK();
+        to_bf16_kernel<<<grid1d(nw), 256, 0, s>>>(A->wp.as<double>(), nw, A->wpbf.as<__nv_bfloat16>());
         HM_LAUNCH_CHECK();
     }
 }
@@ -372,8 +608,9 @@ void load_vector_impl(const hm_tree *tr, const double *src, int nsrc, double *f,
 // device array instead, sized once when the library is loaded.
 //
 // Scratch layout: the product's working vectors (x and y in Morton order,
-// the projections t_b = W_b^T x, and their FP32 roundings for the
-// low-precision copies): 2 n + sum_b k_b doubles plus n + sum_b k_b floats.
+// the projections t_b = W_b^T x and their per-column-cluster partials, and
+// the FP32 roundings of those for the low-precision copies): 2 n + K + P
+// doubles plus n + K + P floats (K = sum of ranks, P = partials).
 // Every element is written before it is read in each call, so nothing needs
 // clearing between calls.  The array
 // is shared by every call on a device and keeps the last call's contents:
@@ -412,7 +649,7 @@ void matvec_noalloc(const hm_matrix *A, int32_t nrhs, hm_dtype prec, const doubl
     if (need > NOALLOC_MAX_DOUBLES)
         fail(HM_EINVAL,
              "problem too large for the allocation-free product: needs %lld scratch doubles "
-             "(3 (n + sum of ranks) / 2 + n / 2), the limit is %lld",
+             "(2 n + K + P doubles and n + K + P floats), the limit is %lld",
              (long long)need, (long long)NOALLOC_MAX_DOUBLES);
     const MatvecWork w = matvec_work_at(A, noalloc_scratch());
     for (int r = 0; r < nrhs; ++r) {

@@ -194,7 +194,9 @@ __global__ void singular_kernel(const SingularItem *__restrict__ items, int64_t 
 // ---------------------------------------------------------------------------
 void assemble_nearfield(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStream_t s, int *d_err,
                         double *sec_regular, double *sec_singular) {
+    // padding columns of the row panels must read as 0
     A->dense.alloc(sizeof(double) * std::max<int64_t>(tr->dense_entries, 1));
+    HM_CUDA_CHECK(cudaMemsetAsync(A->dense.p, 0, sizeof(double) * std::max<int64_t>(tr->dense_entries, 1), s));
     DBuf items, cnt;
     items.alloc(sizeof(SingularItem) * std::max<int64_t>(tr->singular_cap, 1));
     cnt.alloc(sizeof(unsigned long long));

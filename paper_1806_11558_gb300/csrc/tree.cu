@@ -298,52 +298,54 @@ __device__ __forceinline__ int64_t lower_bound_i32(const int32_t *a, int64_t n, 
     return lo;
 }
 
-// per leaf row cluster: first dense block, panel width K, panel size
+// per leaf row cluster: first dense block, padded panel width, panel size
 __global__ void rho_kernel(const int32_t *den_sorted, int64_t nd, const int64_t *wpre, const int32_t *leaf_begin,
                            int64_t nleaf, int64_t *rho_first, int32_t *rho_K, int64_t *rho_size,
-                           int64_t *rho_colptr) {
+                           int64_t *rho_kpad) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nleaf; r += (int64_t)gridDim.x * blockDim.x) {
         const int64_t s = lower_bound_i32(den_sorted, nd, leaf_begin[r], 4);
         const int64_t e = lower_bound_i32(den_sorted, nd, leaf_begin[r + 1], 4);
-        const int64_t ws = s < nd ? wpre[s] : wpre[nd];
-        const int64_t we = e < nd ? wpre[e] : wpre[nd];
+        const int64_t K = wpre[e] - wpre[s];
+        const int64_t Kp = (K + 7) / 8 * 8;
         rho_first[r] = s;
-        rho_K[r] = (int32_t)(we - ws);
-        rho_size[r] = (int64_t)(leaf_begin[r + 1] - leaf_begin[r]) * (we - ws);
-        rho_colptr[r] = ws;
+        rho_K[r] = (int32_t)Kp;
+        rho_size[r] = (int64_t)(leaf_begin[r + 1] - leaf_begin[r]) * Kp;
+        rho_kpad[r] = Kp;
     }
 }
 
 // dense block -> arena base / ld, and the panel's column index list
+// (padding columns keep index 0 and value 0)
 __global__ void dense_layout_kernel(const int32_t *den_sorted, int64_t nd, const int64_t *wpre,
-                                    const int32_t *leaf_begin, int64_t nleaf, const int64_t *rho_off,
-                                    const int64_t *rho_colptr, const int32_t *rho_K, int64_t *base, int32_t *ld,
-                                    int32_t *colidx) {
+                                    const int32_t *leaf_begin, int64_t nleaf, const int64_t *rho_first,
+                                    const int64_t *rho_off, const int64_t *rho_colptr, const int32_t *rho_K,
+                                    int64_t *base, int32_t *ld, int32_t *colidx) {
     for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < nd; b += (int64_t)gridDim.x * blockDim.x) {
         const int32_t rb = den_sorted[4 * b], cb = den_sorted[4 * b + 2], ce = den_sorted[4 * b + 3];
         const int64_t r = lower_bound_i32(leaf_begin, nleaf, rb, 1);
-        const int64_t koff = wpre[b] - rho_colptr[r];
+        const int64_t koff = wpre[b] - wpre[rho_first[r]];
         base[b] = rho_off[r] + koff;
         ld[b] = rho_K[r];
-        for (int32_t j = 0; j < ce - cb; ++j) colidx[wpre[b] + j] = cb + j;
+        for (int32_t j = 0; j < ce - cb; ++j) colidx[rho_colptr[r] + koff + j] = cb + j;
     }
 }
 
-// admissible block -> number of leaf row clusters its rows cover
-__global__ void lr_count_kernel(const int32_t *adm, int64_t na, const int32_t *leaf_begin, int64_t nleaf,
+// admissible block -> number of leaf clusters its rows (side = 0) or its
+// columns (side = 2) cover
+__global__ void lr_count_kernel(const int32_t *adm, int64_t na, const int32_t *leaf_begin, int64_t nleaf, int side,
                                 int64_t *cnt) {
     for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < na; b += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t l0 = lower_bound_i32(leaf_begin, nleaf + 1, adm[4 * b], 1);
-        const int64_t l1 = lower_bound_i32(leaf_begin, nleaf + 1, adm[4 * b + 1], 1);
+        const int64_t l0 = lower_bound_i32(leaf_begin, nleaf + 1, adm[4 * b + side], 1);
+        const int64_t l1 = lower_bound_i32(leaf_begin, nleaf + 1, adm[4 * b + side + 1], 1);
         cnt[b] = l1 - l0;
     }
 }
 
-__global__ void lr_pairs_kernel(const int32_t *adm, int64_t na, const int32_t *leaf_begin, int64_t nleaf,
+__global__ void lr_pairs_kernel(const int32_t *adm, int64_t na, const int32_t *leaf_begin, int64_t nleaf, int side,
                                 const int64_t *off, uint64_t *key, int32_t *val) {
     for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < na; b += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t l0 = lower_bound_i32(leaf_begin, nleaf + 1, adm[4 * b], 1);
-        const int64_t l1 = lower_bound_i32(leaf_begin, nleaf + 1, adm[4 * b + 1], 1);
+        const int64_t l0 = lower_bound_i32(leaf_begin, nleaf + 1, adm[4 * b + side], 1);
+        const int64_t l1 = lower_bound_i32(leaf_begin, nleaf + 1, adm[4 * b + side + 1], 1);
         for (int64_t l = l0; l < l1; ++l) {
             key[off[b] + l - l0] = ((uint64_t)l << 32) | (uint64_t)b;
             val[off[b] + l - l0] = (int32_t)b;
@@ -364,6 +366,11 @@ __global__ void valence_kernel(const int32_t *T, int64_t n, int32_t *val) {
 __global__ void square_kernel(const int32_t *v, int64_t n, int64_t *out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = (int64_t)v[i] * v[i];
+}
+
+__global__ void block_size_kernel(const int32_t *quad, int64_t n, int64_t *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (int64_t)(quad[4 * i + 1] - quad[4 * i]) * (quad[4 * i + 3] - quad[4 * i + 2]);
 }
 
 __global__ void i64_from_i32_diff_kernel(const int32_t *quad, int64_t n, int64_t *out) {
@@ -580,67 +587,89 @@ hm_tree *build_tree_impl(const double *d_V, int64_t nv, const int32_t *d_T, int6
                                                             tr->dense.as<int32_t>(), width.as<int64_t>());
         HM_LAUNCH_CHECK();
         HM_CUDA_CHECK(cudaMemsetAsync(width.as<int64_t>() + n_den, 0, sizeof(int64_t), s));
-        const int64_t total_w = exclusive_scan_i64(width.as<int64_t>(), width.as<int64_t>(), n_den + 1, s);
+        exclusive_scan_i64(width.as<int64_t>(), width.as<int64_t>(), n_den + 1, s);
         const int64_t nl = tr->n_leaf;
-        DBuf rho_first, rho_size;
+        DBuf rho_first, rho_size, kpad;
         rho_first.alloc(sizeof(int64_t) * nl);
         rho_size.alloc(sizeof(int64_t) * (nl + 1));
+        kpad.alloc(sizeof(int64_t) * (nl + 1));
         tr->rho_K.alloc(sizeof(int32_t) * nl);
         tr->rho_colptr.alloc(sizeof(int64_t) * (nl + 1));
         tr->rho_off.alloc(sizeof(int64_t) * (nl + 1));
         rho_kernel<<<grid_for(nl), 256, 0, s>>>(tr->dense.as<int32_t>(), n_den, width.as<int64_t>(),
                                                 tr->leaf_begin.as<int32_t>(), nl, rho_first.as<int64_t>(),
                                                 tr->rho_K.as<int32_t>(), rho_size.as<int64_t>(),
-                                                tr->rho_colptr.as<int64_t>());
+                                                kpad.as<int64_t>());
         HM_LAUNCH_CHECK();
         HM_CUDA_CHECK(cudaMemsetAsync(rho_size.as<int64_t>() + nl, 0, sizeof(int64_t), s));
-        HM_CUDA_CHECK(cudaMemcpyAsync(tr->rho_colptr.as<int64_t>() + nl, &total_w, sizeof(int64_t),
-                                      cudaMemcpyHostToDevice, s));
+        HM_CUDA_CHECK(cudaMemsetAsync(kpad.as<int64_t>() + nl, 0, sizeof(int64_t), s));
+        const int64_t total_kp = exclusive_scan_i64(kpad.as<int64_t>(), tr->rho_colptr.as<int64_t>(), nl + 1, s);
         tr->dense_entries = exclusive_scan_i64(rho_size.as<int64_t>(), tr->rho_off.as<int64_t>(), nl + 1, s);
         tr->dense_base.alloc(sizeof(int64_t) * n_den);
         tr->dense_ld.alloc(sizeof(int32_t) * n_den);
-        tr->colidx.alloc(sizeof(int32_t) * std::max<int64_t>(total_w, 1));
+        tr->colidx.alloc(sizeof(int32_t) * std::max<int64_t>(total_kp, 1));
+        HM_CUDA_CHECK(cudaMemsetAsync(tr->colidx.p, 0, sizeof(int32_t) * std::max<int64_t>(total_kp, 1), s));
         dense_layout_kernel<<<grid_for(n_den), 256, 0, s>>>(
             tr->dense.as<int32_t>(), n_den, width.as<int64_t>(), tr->leaf_begin.as<int32_t>(), nl,
-            tr->rho_off.as<int64_t>(), tr->rho_colptr.as<int64_t>(), tr->rho_K.as<int32_t>(),
-            tr->dense_base.as<int64_t>(), tr->dense_ld.as<int32_t>(), tr->colidx.as<int32_t>());
+            rho_first.as<int64_t>(), tr->rho_off.as<int64_t>(), tr->rho_colptr.as<int64_t>(),
+            tr->rho_K.as<int32_t>(), tr->dense_base.as<int64_t>(), tr->dense_ld.as<int32_t>(),
+            tr->colidx.as<int32_t>());
         HM_LAUNCH_CHECK();
+        // stored entries without padding: sum over dense leaves of m * n
+        DBuf mn;
+        mn.alloc(sizeof(int64_t) * (n_den + 1));
+        block_size_kernel<<<grid_for(n_den), 256, 0, s>>>(tr->dense.as<int32_t>(), n_den, mn.as<int64_t>());
+        HM_LAUNCH_CHECK();
+        tr->dense_true = exclusive_scan_i64(mn.as<int64_t>(), mn.as<int64_t>(), n_den, s);
     }
     // largest dense dimension (for the TMA box)
     tr->max_dense_dim = std::max(max_leaf, std::min<int32_t>((int32_t)n, max_leaf + 1));
 
-    // admissible leaves: sum of |tau| + |sigma|, and per-leaf-row-cluster lists
+    // admissible leaves: sum of |tau| + |sigma|, and for every leaf cluster the
+    // admissible leaves whose rows (resp. columns) cover it, ascending
     {
         const int64_t nl = tr->n_leaf;
-        DBuf cnt;
-        cnt.alloc(sizeof(int64_t) * (n_adm + 1));
         if (n_adm) {
+            DBuf cnt;
+            cnt.alloc(sizeof(int64_t) * (n_adm + 1));
             i64_from_i32_diff_kernel<<<grid_for(n_adm), 256, 0, s>>>(tr->adm.as<int32_t>(), n_adm, cnt.as<int64_t>());
             HM_LAUNCH_CHECK();
             tr->adm_rows_cols = exclusive_scan_i64(cnt.as<int64_t>(), cnt.as<int64_t>(), n_adm, s);
-            lr_count_kernel<<<grid_for(n_adm), 256, 0, s>>>(tr->adm.as<int32_t>(), n_adm,
-                                                            tr->leaf_begin.as<int32_t>(), nl, cnt.as<int64_t>());
-            HM_LAUNCH_CHECK();
         }
-        const int64_t np = exclusive_scan_i64(cnt.as<int64_t>(), cnt.as<int64_t>(), n_adm, s);
-        tr->lr_rowptr.alloc(sizeof(int64_t) * (nl + 1));
-        HM_CUDA_CHECK(cudaMemsetAsync(tr->lr_rowptr.p, 0, sizeof(int64_t) * (nl + 1), s));
-        tr->lr_list.alloc(sizeof(int32_t) * std::max<int64_t>(np, 1));
-        if (np) {
-            DBuf key, kt, vt;
-            key.alloc(sizeof(uint64_t) * np);
-            kt.alloc(sizeof(uint64_t) * np);
-            vt.alloc(sizeof(int32_t) * np);
-            lr_pairs_kernel<<<grid_for(n_adm), 256, 0, s>>>(tr->adm.as<int32_t>(), n_adm,
-                                                            tr->leaf_begin.as<int32_t>(), nl, cnt.as<int64_t>(),
-                                                            key.as<uint64_t>(), tr->lr_list.as<int32_t>());
-            HM_LAUNCH_CHECK();
-            radix_sort_u64(key.as<uint64_t>(), tr->lr_list.as<int32_t>(), kt.as<uint64_t>(), vt.as<int32_t>(), np, 64,
-                           s);
-            lr_rowcount_kernel<<<grid_for(np), 256, 0, s>>>(key.as<uint64_t>(), np, tr->lr_rowptr.as<int64_t>());
-            HM_LAUNCH_CHECK();
-            exclusive_scan_i64(tr->lr_rowptr.as<int64_t>(), tr->lr_rowptr.as<int64_t>(), nl + 1, s);
-        }
+        auto build_csr = [&](int side, DBuf &ptr, DBuf &list, DBuf *bptr) {
+            ptr.alloc(sizeof(int64_t) * (nl + 1));
+            HM_CUDA_CHECK(cudaMemsetAsync(ptr.p, 0, sizeof(int64_t) * (nl + 1), s));
+            DBuf cnt;
+            cnt.alloc(sizeof(int64_t) * (n_adm + 1));
+            HM_CUDA_CHECK(cudaMemsetAsync(cnt.p, 0, sizeof(int64_t) * (n_adm + 1), s));
+            if (n_adm) {
+                lr_count_kernel<<<grid_for(n_adm), 256, 0, s>>>(tr->adm.as<int32_t>(), n_adm,
+                                                                tr->leaf_begin.as<int32_t>(), nl, side,
+                                                                cnt.as<int64_t>());
+                HM_LAUNCH_CHECK();
+            }
+            const int64_t np = exclusive_scan_i64(cnt.as<int64_t>(), cnt.as<int64_t>(), n_adm + 1, s);
+            list.alloc(sizeof(int32_t) * std::max<int64_t>(np, 1));
+            if (np) {
+                DBuf key, kt, vt;
+                key.alloc(sizeof(uint64_t) * np);
+                kt.alloc(sizeof(uint64_t) * np);
+                vt.alloc(sizeof(int32_t) * np);
+                lr_pairs_kernel<<<grid_for(n_adm), 256, 0, s>>>(tr->adm.as<int32_t>(), n_adm,
+                                                                tr->leaf_begin.as<int32_t>(), nl, side,
+                                                                cnt.as<int64_t>(), key.as<uint64_t>(),
+                                                                list.as<int32_t>());
+                HM_LAUNCH_CHECK();
+                radix_sort_u64(key.as<uint64_t>(), list.as<int32_t>(), kt.as<uint64_t>(), vt.as<int32_t>(), np, 64,
+                               s);
+                lr_rowcount_kernel<<<grid_for(np), 256, 0, s>>>(key.as<uint64_t>(), np, ptr.as<int64_t>());
+                HM_LAUNCH_CHECK();
+                exclusive_scan_i64(ptr.as<int64_t>(), ptr.as<int64_t>(), nl + 1, s);
+            }
+            if (bptr) *bptr = std::move(cnt);
+        };
+        build_csr(0, tr->lr_rowptr, tr->lr_list, nullptr);
+        build_csr(2, tr->lr_colptr, tr->lr_collist, &tr->lr_bcolptr);
     }
 
     // upper bound on touching pairs: sum over vertices of valence^2
