@@ -29,7 +29,7 @@ sys.path.insert(0, ROOT)
 WORKLOAD = dict(workload="bumped icosphere level 7, Galerkin single-layer Laplace, P0",
                 panels=327680, leaf_size=64, eta=1.5, aca_eps=1e-7, aca_kmax=64, ss_order=8,
                 source=[3.0, 0.0, 0.0], solve_rel_tol=1e-12, inner="fp32 factors + fp32 near field",
-                inner_tol=1e-4, restart=30)
+                inner_tol=1e-4, restart=30, precond=os.environ.get("HM_BENCH_PRECOND", "1") == "1")
 METRIC = "H-matrix setup s, H-matvec GB/s, solve s at 1e-8 rel. accuracy: mixed vs FP64"
 FLOPS_PER_PAIR = 11  # 3 sub + 3 mul + 2 add (|x-y|^2) + rsqrt + multiply-add (weight)
 PAIRS_PER_ENTRY = 49
@@ -134,10 +134,12 @@ def run_ours(args, rank, world):
         e[2].record(stream)
         hm.hm_load_vector(tree, src, f)
         e[3].record(stream)
-        i64 = hm.hm_solve(A, f[0], x64, rel_tol=W["solve_rel_tol"], restart=W["restart"], max_iter=5000)
+        i64 = hm.hm_solve(A, f[0], x64, rel_tol=W["solve_rel_tol"], restart=W["restart"], max_iter=5000,
+                          precond=int(W["precond"]))
         e[4].record(stream)
         imx = hm.hm_solve(A, f[0], xmx, rel_tol=W["solve_rel_tol"], restart=W["restart"], max_iter=5000, refine=1,
-                          inner_tol=W["inner_tol"], inner_dtype=hm.HM_F32, max_refine=50)
+                          inner_tol=W["inner_tol"], inner_dtype=hm.HM_F32, max_refine=50,
+                          precond=int(W["precond"]))
         e[5].record(stream)
         torch.cuda.synchronize()
         t["tree_s"] = e[0].elapsed_time(e[1]) / 1e3
@@ -219,7 +221,8 @@ def run_ours(args, rank, world):
     b1 = torch.cuda.Event(enable_timing=True)
     b0.record(stream)
     ibf = hm.hm_solve(A16, f[0], xbf, rel_tol=W["solve_rel_tol"], restart=W["restart"], max_iter=5000, refine=1,
-                      inner_tol=1e-2, inner_dtype=hm.HM_BF16, max_refine=80, raise_on_noconv=False)
+                      inner_tol=1e-2, inner_dtype=hm.HM_BF16, max_refine=80, raise_on_noconv=False,
+                      precond=int(W["precond"]))
     b1.record(stream)
     torch.cuda.synchronize()
     bf16 = {"solve_s": b0.elapsed_time(b1) / 1e3, "err_vs_fp64": float(torch.linalg.norm(xbf - x64) /

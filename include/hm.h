@@ -99,7 +99,13 @@ typedef struct {
  *                   outer residual in FP64.
  *  max_refine : largest number of refinement steps (refine = 1).
  *  inner_tol  : relative tolerance of each inner solve (refine = 1).
- *  inner_dtype: HM_F32 or HM_BF16 (factors of that type, dense FP32). */
+ *  inner_dtype: HM_F32 or HM_BF16 (factors of that type, dense FP32).
+ *  precond    : 0 = none (the paper's unpreconditioned Krylov solve);
+ *               1 = right block-Jacobi preconditioning with the inverses of
+ *                   the diagonal blocks of the leaf clusters (FP64, computed
+ *                   on the first such solve and kept with the matrix).  The
+ *                   residual and the stopping test are those of the
+ *                   unpreconditioned system. */
 typedef struct {
     int32_t restart;
     int32_t max_iter;
@@ -108,6 +114,7 @@ typedef struct {
     int32_t max_refine;
     double inner_tol;
     hm_dtype inner_dtype;
+    int32_t precond;
 } hm_solve_params;
 
 typedef struct {

@@ -178,6 +178,7 @@ hm_status hm_solve(const hm_matrix *A, int32_t trans, int32_t nrhs, const double
         if (trans != 0 && trans != 1) fail(HM_EINVAL, "trans must be 0 or 1");
         if (trans == 1) fail(HM_EINVAL, "the transposed solve is not available in this build");
         if (params->restart < 1 || params->restart > 128) fail(HM_EINVAL, "restart must be in [1, 128]");
+        if (params->precond != 0 && params->precond != 1) fail(HM_EINVAL, "precond must be 0 or 1");
         if (params->max_iter < 1) fail(HM_EINVAL, "max_iter must be >= 1");
         if (!(params->rel_tol > 0.0)) fail(HM_EINVAL, "rel_tol must be > 0");
         if (params->refine) {

@@ -231,5 +231,8 @@ struct hm_matrix {
     hm::DBuf pofs;      // [sum over blocks of column leaf clusters] int64: partial offsets per block
     int64_t wp_entries = 0;
     int64_t n_partials = 0;  // length of the partial-projection vector
+    // block-Jacobi preconditioner: inverse of each leaf cluster's diagonal block
+    hm::DBuf bj;        // [sum |rho|^2] double, row-major per leaf cluster
+    hm::DBuf bj_off;    // [n_leaf + 1] int64
     hm_matrix_info info{};
 };

@@ -157,11 +157,121 @@ __global__ void set_g0_kernel(double *g, const double *nrm2, int m) {
 
 static unsigned g1(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8192)); }
 
+// ---------------------------------------------------------------------------
+// block-Jacobi preconditioner on the leaf clusters' diagonal blocks
+// ---------------------------------------------------------------------------
+__global__ void bj_size_kernel(const int32_t *leaf_begin, int64_t nl, int64_t *sz) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nl; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = leaf_begin[r + 1] - leaf_begin[r];
+        sz[r] = m * m;
+    }
+}
+
+// D_rho = A(rho, rho), read from rho's near-field row panel: the columns whose
+// index falls inside rho
+__global__ void bj_extract_kernel(const int32_t *leaf_begin, const int64_t *rho_off, const int32_t *rho_K,
+                                  const int64_t *rho_colptr, const int32_t *colidx, const double *dense,
+                                  const int64_t *bj_off, double *bj) {
+    const int64_t r = blockIdx.x;
+    const int32_t r0 = leaf_begin[r], m = leaf_begin[r + 1] - r0;
+    const int K = rho_K[r];
+    const double *P = dense + rho_off[r];
+    const int32_t *ci = colidx + rho_colptr[r];
+    double *D = bj + bj_off[r];
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) D[e] = 0.0;
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        const int c = ci[k] - r0;
+        if (c >= 0 && c < m && k < K) {
+            // padding columns carry index 0 and value 0: they may alias column 0
+            // of the first leaf only with a zero value, which is skipped
+            for (int i = 0; i < m; ++i) {
+                const double v = P[(int64_t)i * K + k];
+                if (v != 0.0) D[i * m + c] = v;
+            }
+        }
+    }
+}
+
+// In-place Gauss-Jordan inversion of the SPD block D (pivots stay positive,
+// no pivoting needed).
+__global__ void bj_invert_kernel(const int32_t *leaf_begin, const int64_t *bj_off, double *bj) {
+    const int64_t r = blockIdx.x;
+    const int m = leaf_begin[r + 1] - leaf_begin[r];
+    double *D = bj + bj_off[r];
+    __shared__ double s_piv;
+    for (int p = 0; p < m; ++p) {
+        if (threadIdx.x == 0) {
+            s_piv = 1.0 / D[p * m + p];
+            D[p * m + p] = 1.0;
+        }
+        __syncthreads();
+        const double piv = s_piv;
+        for (int j = threadIdx.x; j < m; j += blockDim.x) D[p * m + j] *= piv;
+        __syncthreads();
+        for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+            const int i = e / m, j = e - (e / m) * m;
+            if (i == p || j == p) continue;
+            D[i * m + j] -= D[i * m + p] * D[p * m + j];
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < m; i += blockDim.x)
+            if (i != p) D[i * m + p] = -D[i * m + p] * D[p * m + p];
+        __syncthreads();
+    }
+}
+
+// z_rho = D_rho^{-1} v_rho, one warp per row
+__global__ void bj_apply_kernel(const int32_t *leaf_begin, const int64_t *bj_off, const double *bj, const double *v,
+                                double *z) {
+    const int64_t r = blockIdx.x;
+    const int32_t r0 = leaf_begin[r], m = leaf_begin[r + 1] - r0;
+    const double *D = bj + bj_off[r];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = warp; i < m; i += nw) {
+        double acc = 0.0;
+        for (int j = lane; j < m; j += 32) acc += D[i * m + j] * v[r0 + j];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) z[r0 + i] = acc;
+    }
+}
+
+static void bj_setup(const hm_matrix *Ac, cudaStream_t s) {
+    hm_matrix *A = const_cast<hm_matrix *>(Ac);  // cache owned by the matrix
+    if (A->bj.p) return;
+    const hm_tree *tr = A->tree;
+    const int64_t nl = tr->n_leaf;
+    A->bj_off.alloc(sizeof(int64_t) * (nl + 1));
+    bj_size_kernel<<<g1(nl), 256, 0, s>>>(tr->leaf_begin.as<int32_t>(), nl, A->bj_off.as<int64_t>());
+    HM_LAUNCH_CHECK();
+    HM_CUDA_CHECK(cudaMemsetAsync(A->bj_off.as<int64_t>() + nl, 0, sizeof(int64_t), s));
+    const int64_t tot = exclusive_scan_i64(A->bj_off.as<int64_t>(), A->bj_off.as<int64_t>(), nl + 1, s);
+    DBuf bj;
+    bj.alloc(sizeof(double) * std::max<int64_t>(tot, 1));
+    bj_extract_kernel<<<(unsigned)nl, 256, 0, s>>>(tr->leaf_begin.as<int32_t>(), tr->rho_off.as<int64_t>(),
+                                                  tr->rho_K.as<int32_t>(), tr->rho_colptr.as<int64_t>(),
+                                                  tr->colidx.as<int32_t>(), A->dense.as<double>(),
+                                                  A->bj_off.as<int64_t>(), bj.as<double>());
+    HM_LAUNCH_CHECK();
+    bj_invert_kernel<<<(unsigned)nl, 256, 0, s>>>(tr->leaf_begin.as<int32_t>(), A->bj_off.as<int64_t>(),
+                                                 bj.as<double>());
+    HM_LAUNCH_CHECK();
+    HM_CUDA_CHECK(cudaStreamSynchronize(s));
+    A->bj = std::move(bj);
+}
+
+static void bj_apply(const hm_matrix *A, const double *v, double *z, cudaStream_t s) {
+    const hm_tree *tr = A->tree;
+    bj_apply_kernel<<<(unsigned)tr->n_leaf, 128, 0, s>>>(tr->leaf_begin.as<int32_t>(), A->bj_off.as<int64_t>(),
+                                                        A->bj.as<double>(), v, z);
+    HM_LAUNCH_CHECK();
+}
+
 struct Gmres {
     int64_t n;
     int m;
     int nblk;
-    DBuf V, w, ax, part, h, H, cs, sn, g, y, est, t, nrm;
+    DBuf V, w, ax, part, h, H, cs, sn, g, y, est, t, nrm, z, d;
     Gmres(int64_t n_, int m_, int64_t work_doubles) : n(n_), m(m_) {
         nblk = std::max(1, std::min<int>(4 * num_sms(), (int)((n + 1023) / 1024)));
         V.alloc(sizeof(double) * (int64_t)(m + 1) * n);
@@ -176,6 +286,8 @@ struct Gmres {
         y.alloc(sizeof(double) * m);
         est.alloc(sizeof(double) * 2);
         t.alloc(sizeof(double) * work_doubles);
+        z.alloc(sizeof(double) * n);
+        d.alloc(sizeof(double) * n);
         nrm.alloc(sizeof(double) * 2);
     }
     // out[0..nv) = V_l . w (accumulate adds to out)
@@ -195,7 +307,8 @@ struct Gmres {
 // GMRES(m) for op x = b (Morton order), x in/out.  Returns the status; iters
 // and cycles accumulate; relres = final true residual / ||b||.
 static hm_status gmres(const hm_matrix *A, hm_dtype prec, const double *b, double *x, double tol, int maxit,
-                       Gmres &G, cudaStream_t s, int &iters, int &cycles, double &relres, bool x_is_zero) {
+                       Gmres &G, cudaStream_t s, int &iters, int &cycles, double &relres, bool x_is_zero,
+                       bool precond) {
     const int64_t n = G.n;
     const int m = G.m;
     double *V = G.V.as<double>();
@@ -226,7 +339,13 @@ static hm_status gmres(const hm_matrix *A, hm_dtype prec, const double *b, doubl
         for (int j = 0; j < m; ++j) {
             double *vj = V + (int64_t)j * n;
             double *w = G.w.as<double>();
-            apply(A, prec, vj, w, G.t, s);
+            if (precond) {
+                // right preconditioning: w = H (M^{-1} v_j)
+                bj_apply(A, vj, G.z.as<double>(), s);
+                apply(A, prec, G.z.as<double>(), w, G.t, s);
+            } else {
+                apply(A, prec, vj, w, G.t, s);
+            }
             // CGS2
             G.dots(V, j + 1, w, G.h.as<double>(), 0, s);
             sub_combo_kernel<<<g1(n), 256, 0, s>>>(V, n, j + 1, G.h.as<double>(), n, w);
@@ -258,8 +377,18 @@ static hm_status gmres(const hm_matrix *A, hm_dtype prec, const double *b, doubl
         }
         trisolve_kernel<<<1, 32, 0, s>>>(G.H.as<double>(), m + 1, k, G.g.as<double>(), G.y.as<double>());
         HM_LAUNCH_CHECK();
-        add_combo_kernel<<<g1(n), 256, 0, s>>>(V, n, k, G.y.as<double>(), n, x);
-        HM_LAUNCH_CHECK();
+        if (precond) {
+            // x += M^{-1} (V y)
+            HM_CUDA_CHECK(cudaMemsetAsync(G.d.p, 0, sizeof(double) * n, s));
+            add_combo_kernel<<<g1(n), 256, 0, s>>>(V, n, k, G.y.as<double>(), n, G.d.as<double>());
+            HM_LAUNCH_CHECK();
+            bj_apply(A, G.d.as<double>(), G.z.as<double>(), s);
+            axpy_kernel<<<g1(n), 256, 0, s>>>(1.0, G.z.as<double>(), n, x);
+            HM_LAUNCH_CHECK();
+        } else {
+            add_combo_kernel<<<g1(n), 256, 0, s>>>(V, n, k, G.y.as<double>(), n, x);
+            HM_LAUNCH_CHECK();
+        }
         // true residual -> V_0 for the next cycle
         apply(A, prec, x, G.ax.as<double>(), G.t, s);
         residual_kernel<<<g1(n), 256, 0, s>>>(b, G.ax.as<double>(), n, V);
@@ -284,11 +413,14 @@ hm_status solve_impl(const hm_matrix *A, const double *b_orig, double *x_orig, c
     permute_to_morton(tr, b_orig, b.as<double>(), s);
     HM_CUDA_CHECK(cudaMemsetAsync(x.p, 0, sizeof(double) * n, s));
     Gmres G(n, p.restart, matvec_work_doubles(A));
+    const bool pc = p.precond == 1;
+    if (pc) bj_setup(A, s);
     int iters = 0, cycles = 0, steps = 0;
     double relres = 1.0;
     hm_status st;
     if (!p.refine) {
-        st = gmres(A, HM_F64, b.as<double>(), x.as<double>(), p.rel_tol, p.max_iter, G, s, iters, cycles, relres, true);
+        st = gmres(A, HM_F64, b.as<double>(), x.as<double>(), p.rel_tol, p.max_iter, G, s, iters, cycles, relres, true,
+                   pc);
     } else {
         DBuf r, d, ax;
         r.alloc(sizeof(double) * n);
@@ -307,7 +439,7 @@ hm_status solve_impl(const hm_matrix *A, const double *b_orig, double *x_orig, c
             HM_CUDA_CHECK(cudaMemsetAsync(d.p, 0, sizeof(double) * n, s));
             double inner = 1.0;
             gmres(A, p.inner_dtype, r.as<double>(), d.as<double>(), p.inner_tol, p.max_iter, G, s, iters, cycles,
-                  inner, true);
+                  inner, true, pc);
             axpy_kernel<<<g1(n), 256, 0, s>>>(1.0, d.as<double>(), n, x.as<double>());
             HM_LAUNCH_CHECK();
             apply(A, HM_F64, x.as<double>(), ax.as<double>(), G.t, s);

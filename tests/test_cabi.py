@@ -45,7 +45,7 @@ def test_invalid_arguments_rejected(hm):
     assert L.hm_assemble(ctypes.cast(junk, ctypes.c_void_p), ctypes.byref(ap), None, ctypes.byref(out)) == hm.HM_EINVAL
     assert L.hm_assemble(None, ctypes.byref(ap), None, ctypes.byref(out)) == hm.HM_EINVAL
     assert L.hm_matvec(None, 0, 1, 0, fake, fake, 1.0, 0.0, None) == hm.HM_EINVAL
-    sp = hm.SolveParams(30, 100, 1e-10, 0, 1, 1e-4, 1)
+    sp = hm.SolveParams(30, 100, 1e-10, 0, 1, 1e-4, 1, 0)
     assert L.hm_solve(None, 0, 1, fake, fake, ctypes.byref(sp), None, None) == hm.HM_EINVAL
     hm.hm_free(None)
 

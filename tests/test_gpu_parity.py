@@ -157,6 +157,13 @@ def test_solve_fp64_and_mixed(orc, ico3):
     xm, im = g.solve(f, rel_tol=1e-12, refine=1, inner_tol=1e-4, inner_dtype=1)
     assert im.rel_resid <= 1e-12 and im.refine_steps >= 1
     assert np.linalg.norm(xm - x64) / np.linalg.norm(x64) < 1e-8
+    # block-Jacobi right preconditioning: same operator, same solution, fewer steps
+    xp, ip = g.solve(f, rel_tol=1e-12, precond=1)
+    assert ip.rel_resid <= 1e-12 and ip.iters < info.iters
+    assert np.linalg.norm(xp - xo) / np.linalg.norm(xo) < 1e-8
+    xpm, ipm = g.solve(f, rel_tol=1e-12, refine=1, inner_tol=1e-4, inner_dtype=1, precond=1)
+    assert ipm.rel_resid <= 1e-12
+    assert np.linalg.norm(xpm - xo) / np.linalg.norm(xo) < 1e-8
 
 
 def test_solve_dense_limit_matches_lu(orc):
