@@ -151,6 +151,10 @@ typedef struct {
     double s_total;         /* wall seconds of hm_assemble                        */
     int64_t bytes_f64;      /* device bytes of the FP64 matrix data               */
     int64_t bytes_low;      /* device bytes of the low-precision copies           */
+    int64_t aca_entries;    /* entries the ACA evaluated, sum k_b (|tau|+|sigma|)
+                               over the blocks it approximated (the transposed
+                               partner of an approximated block reuses its
+                               factors, the matrix being symmetric)            */
 } hm_matrix_info;
 
 /* Build the Morton-ordered cluster tree and the block cluster tree of a

@@ -62,7 +62,7 @@ class MatrixInfo(ctypes.Structure):
     _fields_ = [("dense_entries", ctypes.c_int64), ("lr_entries", ctypes.c_int64), ("max_rank", ctypes.c_int32),
                 ("kmax_hit", ctypes.c_int32), ("mean_rank", ctypes.c_double), ("s_nearfield", ctypes.c_double),
                 ("s_singular", ctypes.c_double), ("s_aca", ctypes.c_double), ("s_total", ctypes.c_double),
-                ("bytes_f64", ctypes.c_int64), ("bytes_low", ctypes.c_int64)]
+                ("bytes_f64", ctypes.c_int64), ("bytes_low", ctypes.c_int64), ("aca_entries", ctypes.c_int64)]
 
 
 def struct_dict(s):

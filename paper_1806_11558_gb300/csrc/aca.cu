@@ -33,6 +33,8 @@ namespace hm {
 constexpr int ACA_THREADS = 256;
 constexpr int ACA_WARPS = ACA_THREADS / 32;
 constexpr int SMALL_MAX_DIM = 256;  // warp-mode blocks: m, n <= this
+// per-warp shared doubles in warp mode: fixed record, U/W row values, bitmaps, norm terms
+constexpr int WARP_SMEM_DOUBLES = 32 + MAX_KMAX + (SMALL_MAX_DIM + 31) / 32 + (2 + 2 * MAX_KMAX + 1) / 2;
 
 struct AcaArgs {
     const double *pt;
@@ -40,7 +42,8 @@ struct AcaArgs {
     int64_t npad;
     const double *V;
     const int32_t *adm;
-    int64_t n_big, n_all;
+    const int32_t *work;  // blocks to approximate, largest first: [0, n_big) CTA-wide, then warp-wide
+    int64_t n_big, n_work;
     double eps;
     int kmax;
     QuadParams qp;
@@ -96,7 +99,66 @@ struct AcaShared {
     Best *bred;     // [ACA_WARPS] argmax partials (CTA mode)
     uint32_t *urow, *ucol;
     long long *ibc; // broadcast slot (CTA mode)
+    float *stage;   // norm terms per warp: CTA [ACA_WARPS][NORM_STRIDE], warp [NORM_STRIDE]
+    float *res;     // reduced norm terms [NORM_STRIDE]
 };
+
+constexpr int NORM_STRIDE = 2 + 2 * MAX_KMAX;
+
+// Terms of the Frobenius norm of the approximant after step r, accumulated in
+// FP32 from the FP32 shadows Uf / Wf of the factor columns (the estimate only
+// decides when to stop): res[0] = |u_r|^2, res[1] = |w_r|^2,
+// res[2 + l] = u_r . u_l, res[2 + r + l] = w_l . w_r (l < r).  One pass over
+// the columns, per-warp shuffle reductions, one shared-memory round.
+template <bool CTA>
+__device__ void norm_terms(const float *Uf, const float *Wf, int m, int n, int r, const AcaShared &sh) {
+    const int gs = CTA ? ACA_THREADS : 32, t = CTA ? (int)threadIdx.x : (int)(threadIdx.x & 31);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nvals = 2 + 2 * r;
+    const float *ur = Uf + (int64_t)r * m, *wr = Wf + (int64_t)r * n;
+    float *st = CTA ? sh.stage + warp * NORM_STRIDE : sh.stage;
+    for (int c0 = 0; c0 < nvals; c0 += 8) {
+        float acc[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[c] = 0.0f;
+        for (int k = t; k < m; k += gs) {
+            const float u = ur[k];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int v = c0 + c;
+                if (v == 0) acc[c] = fmaf(u, u, acc[c]);
+                else if (v >= 2 && v < 2 + r) acc[c] = fmaf(u, Uf[(int64_t)(v - 2) * m + k], acc[c]);
+            }
+        }
+        for (int j = t; j < n; j += gs) {
+            const float w = wr[j];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int v = c0 + c;
+                if (v == 1) acc[c] = fmaf(w, w, acc[c]);
+                else if (v >= 2 + r && v < nvals) acc[c] = fmaf(w, Wf[(int64_t)(v - 2 - r) * n + j], acc[c]);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            float a = acc[c];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (lane == 0 && c0 + c < nvals) st[c0 + c] = a;
+        }
+    }
+    if (CTA) {
+        __syncthreads();
+        for (int v = t; v < nvals; v += gs) {
+            float a = 0.0f;
+            for (int w = 0; w < ACA_WARPS; ++w) a += sh.stage[w * NORM_STRIDE + v];
+            sh.res[v] = a;
+        }
+        __syncthreads();
+    } else {
+        __syncwarp();
+    }
+}
 
 template <bool CTA>
 struct Grp {
@@ -176,8 +238,8 @@ __device__ __forceinline__ double aca_entry(const float *fix, bool fixed_is_row,
 
 // ACA of one block; U (m x kmax) and W (n x kmax) column-major in scratch.
 template <bool CTA>
-__device__ int aca_block(const AcaArgs &A, int rb, int m, int cb, int n, double *U, double *W, const AcaShared &sh,
-                         bool *hit_kmax) {
+__device__ int aca_block(const AcaArgs &A, int rb, int m, int cb, int n, double *U, double *W, float *Uf, float *Wf,
+                         const AcaShared &sh, bool *hit_kmax) {
     using G = Grp<CTA>;
     const int gs = G::size(), t = G::rank();
     const int wr = (m + 31) >> 5, wc = (n + 31) >> 5;
@@ -222,41 +284,33 @@ __device__ int aca_block(const AcaArgs &A, int rb, int m, int cb, int n, double 
         }
         if (r == 0) delta1 = fabs(delta);
         const int jp = best.idx;
-        double nw2 = 0.0;
         for (int j = t; j < n; j += gs) {
             const double w = W[(int64_t)r * n + j] / delta;
             W[(int64_t)r * n + j] = w;
-            nw2 += w * w;
+            Wf[(int64_t)r * n + j] = (float)w;
         }
         // ---- residual of column jp ----
         for (int q = t; q < PF_ROWS; q += gs) sh.fix[q] = A.pf[(int64_t)q * A.npad + cb + jp];
         for (int l = t; l < r; l += gs) sh.vec[l] = W[(int64_t)l * n + jp];
         G::sync();
-        double nu2 = 0.0;
         Best nb{-1.0, 0x7fffffff, 0.0};
         for (int k = t; k < m; k += gs) {
             double u = aca_entry(sh.fix, false, rb + k, cb + jp, A);
             for (int l = 0; l < r; ++l) u -= sh.vec[l] * U[(int64_t)l * m + k];
             U[(int64_t)r * m + k] = u;
-            nu2 += u * u;
+            Uf[(int64_t)r * m + k] = (float)u;
             if (!bit(sh.urow, k)) {
                 const Best c{fabs(u), k, u};
                 if (better(c, nb)) nb = c;
             }
         }
         if (t == 0) sh.ucol[jp >> 5] |= 1u << (jp & 31);
-        nu2 = G::sum(nu2, sh);
-        nw2 = G::sum(nw2, sh);
         // ---- Frobenius norm of the approximant ----
+        norm_terms<CTA>(Uf, Wf, m, n, r, sh);
+        const float *res = CTA ? sh.res : sh.stage;
+        const double nu2 = res[0], nw2 = res[1];
         double cross = 0.0;
-        for (int l = 0; l < r; ++l) {
-            double du = 0.0, dw = 0.0;
-            for (int k = t; k < m; k += gs) du += U[(int64_t)r * m + k] * U[(int64_t)l * m + k];
-            for (int j = t; j < n; j += gs) dw += W[(int64_t)l * n + j] * W[(int64_t)r * n + j];
-            du = G::sum(du, sh);
-            dw = G::sum(dw, sh);
-            cross += du * dw;
-        }
+        for (int l = 0; l < r; ++l) cross += (double)res[2 + l] * (double)res[2 + r + l];
         s2 = s2 + 2.0 * cross + nu2 * nw2;
         ++r;
         nb = G::argmax(nb, sh);
@@ -315,6 +369,8 @@ __global__ void __launch_bounds__(ACA_THREADS, 2) aca_kernel(AcaArgs A) {
         sh.ibc = &s_ibc;
         sh.urow = reinterpret_cast<uint32_t *>(d + 32 + MAX_KMAX);
         sh.ucol = sh.urow + A.big_words_r;
+        sh.stage = reinterpret_cast<float *>(sh.ucol + A.big_words_c + ((A.big_words_r + A.big_words_c) & 1));
+        sh.res = sh.stage + ACA_WARPS * NORM_STRIDE;
         double *U = A.scr_big + (int64_t)blockIdx.x * A.big_stride;
         for (;;) {
             long long q = 0;
@@ -322,12 +378,14 @@ __global__ void __launch_bounds__(ACA_THREADS, 2) aca_kernel(AcaArgs A) {
             q = Grp<true>::bcast(q, sh);
             const int64_t nbig = A.todo ? A.n_todo : A.n_big;
             if (q >= nbig) break;
-            const int64_t b = A.todo ? A.todo[q] : q;
+            const int64_t b = A.todo ? A.todo[q] : A.work[q];
             const int32_t rb = A.adm[4 * b], re = A.adm[4 * b + 1], cb = A.adm[4 * b + 2], ce = A.adm[4 * b + 3];
             const int m = re - rb, n = ce - cb;
             double *W = U + (int64_t)m * A.kmax;
+            float *Uf = reinterpret_cast<float *>(W + (int64_t)n * A.kmax);
+            float *Wf = Uf + (int64_t)m * A.kmax;
             bool hit = false;
-            const int k = aca_block<true>(A, rb, m, cb, n, U, W, sh, &hit);
+            const int k = aca_block<true>(A, rb, m, cb, n, U, W, Uf, Wf, sh, &hit);
             if (hit && threadIdx.x == 0) atomicAdd(A.kmax_hit, 1);
             __syncthreads();
             aca_store<true>(A, b, m, n, k, U, W, sh);
@@ -340,7 +398,7 @@ __global__ void __launch_bounds__(ACA_THREADS, 2) aca_kernel(AcaArgs A) {
     {
         AcaShared sh;
         const int words = (SMALL_MAX_DIM + 31) / 32;
-        double *d = reinterpret_cast<double *>(smem_raw) + (int64_t)warp * (32 + MAX_KMAX + words);
+        double *d = reinterpret_cast<double *>(smem_raw) + (int64_t)warp * WARP_SMEM_DOUBLES;
         sh.fix = reinterpret_cast<float *>(d);
         sh.vec = d + 32;
         sh.red = nullptr;
@@ -348,18 +406,22 @@ __global__ void __launch_bounds__(ACA_THREADS, 2) aca_kernel(AcaArgs A) {
         sh.ibc = nullptr;
         sh.urow = reinterpret_cast<uint32_t *>(d + 32 + MAX_KMAX);
         sh.ucol = sh.urow + words;
+        sh.stage = reinterpret_cast<float *>(d + 32 + MAX_KMAX + words);
+        sh.res = sh.stage;
         double *U = A.scr_small + ((int64_t)blockIdx.x * ACA_WARPS + warp) * A.small_stride;
         for (;;) {
             int q = 0;
             if (lane == 0) q = (int)atomicAdd(A.q_small, 1ull);
             q = __shfl_sync(0xffffffffu, q, 0);
-            const int64_t b = A.n_big + q;
-            if (b >= A.n_all) break;
+            if (A.n_big + q >= A.n_work) break;
+            const int64_t b = A.work[A.n_big + q];
             const int32_t rb = A.adm[4 * b], re = A.adm[4 * b + 1], cb = A.adm[4 * b + 2], ce = A.adm[4 * b + 3];
             const int m = re - rb, n = ce - cb;
             double *W = U + (int64_t)m * A.kmax;
+            float *Uf = reinterpret_cast<float *>(W + (int64_t)n * A.kmax);
+            float *Wf = Uf + (int64_t)m * A.kmax;
             bool hit = false;
-            const int k = aca_block<false>(A, rb, m, cb, n, U, W, sh, &hit);
+            const int k = aca_block<false>(A, rb, m, cb, n, U, W, Uf, Wf, sh, &hit);
             if (hit && lane == 0) atomicAdd(A.kmax_hit, 1);
             __syncwarp();
             aca_store<false>(A, b, m, n, k, U, W, sh);
@@ -371,6 +433,23 @@ __global__ void __launch_bounds__(ACA_THREADS, 2) aca_kernel(AcaArgs A) {
 __global__ void aca_overflow_list(const int64_t *uw_off, int64_t na, int32_t *list, int *count) {
     for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < na; b += (int64_t)gridDim.x * blockDim.x)
         if (uw_off[b] < 0) list[atomicAdd(count, 1)] = (int32_t)b;
+}
+
+// blocks below the diagonal with a partner take its rank (their factors are
+// the partner's, transposed)
+__global__ void mirror_rank_kernel(const int32_t *adm, const int32_t *tp, int64_t na, int32_t *rank, int64_t *uw_off) {
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < na; b += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t p = tp[b];
+        if (p >= 0 && adm[4 * b] > adm[4 * b + 2]) {
+            rank[b] = rank[p];
+            uw_off[b] = uw_off[p];
+        }
+    }
+}
+
+__global__ void lr_size_kernel(const int32_t *adm, const int32_t *rank, int64_t na, int64_t *out) {
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < na; b += (int64_t)gridDim.x * blockDim.x)
+        out[b] = (int64_t)rank[b] * ((adm[4 * b + 1] - adm[4 * b]) + (adm[4 * b + 3] - adm[4 * b + 2]));
 }
 
 __global__ void rank_to_i64(const int32_t *rank, int64_t na, int64_t *out) {
@@ -406,23 +485,24 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
         *sec = 0.0;
         return;
     }
-    // block sizes on the host: split into CTA-wide and warp-wide work
-    std::vector<int32_t> h_adm(4 * na);
+    // block sizes on the host; the matrix is symmetric, so of a pair of blocks
+    // with swapped ranges only the one above the diagonal is approximated
+    std::vector<int32_t> h_adm(4 * na), h_tp(na);
     HM_CUDA_CHECK(cudaMemcpyAsync(h_adm.data(), tr->adm.p, sizeof(int32_t) * 4 * na, cudaMemcpyDeviceToHost, s));
+    HM_CUDA_CHECK(cudaMemcpyAsync(h_tp.data(), tr->adm_tp.p, sizeof(int32_t) * na, cudaMemcpyDeviceToHost, s));
     HM_CUDA_CHECK(cudaStreamSynchronize(s));
     // blocks are in level order (largest first); small = both dims <= SMALL_MAX_DIM and
     // m + n <= small_sum, chosen so that one warp per block keeps the tail short
     const int small_sum = 320;
-    int64_t n_big = 0;
     int max_m_big = 1, max_n_big = 1, max_sum_small = 2;
-    // order: big blocks first (they already come first within the level order)
     std::vector<int32_t> big, small;
     for (int64_t b = 0; b < na; ++b) {
+        if (h_tp[b] >= 0 && h_adm[4 * b] > h_adm[4 * b + 2]) continue;
         const int m = h_adm[4 * b + 1] - h_adm[4 * b], n = h_adm[4 * b + 3] - h_adm[4 * b + 2];
         if (m <= SMALL_MAX_DIM && n <= SMALL_MAX_DIM && m + n <= small_sum) small.push_back((int32_t)b);
         else big.push_back((int32_t)b);
     }
-    n_big = (int64_t)big.size();
+    const int64_t n_big = (int64_t)big.size();
     // CTA-mode scratch and bitmaps fit every block (a re-run after arena
     // growth processes any block CTA-wide)
     for (int64_t b = 0; b < na; ++b) {
@@ -431,17 +511,21 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
     }
     for (int32_t b : small)
         max_sum_small = std::max(max_sum_small, h_adm[4 * b + 1] - h_adm[4 * b] + h_adm[4 * b + 3] - h_adm[4 * b + 2]);
-    // the kernel addresses blocks by position: store them big-first
-    bool reordered = false;
-    for (int64_t k = 0; k < n_big; ++k)
-        if (big[k] != k) { reordered = true; break; }
-    if (reordered) fail(HM_EINTERNAL, "admissible blocks are not ordered largest first");
+    std::vector<int32_t> work(big);
+    work.insert(work.end(), small.begin(), small.end());
+    DBuf d_work;
+    d_work.alloc(sizeof(int32_t) * std::max<size_t>(work.size(), 1));
+    HM_CUDA_CHECK(cudaMemcpyAsync(d_work.p, work.data(), sizeof(int32_t) * work.size(), cudaMemcpyHostToDevice, s));
+    HM_CUDA_CHECK(cudaMemsetAsync(uw_off.p, 0, sizeof(int64_t) * na, s));
+    HM_CUDA_CHECK(cudaMemsetAsync(A->rank.p, 0, sizeof(int32_t) * na, s));
 
     int occ = 0;
     const int words_r = (max_m_big + 31) / 32, words_c = (max_n_big + 31) / 32;
     const int small_words = (SMALL_MAX_DIM + 31) / 32;
-    const size_t smem_big = sizeof(double) * (32 + MAX_KMAX) + sizeof(uint32_t) * (words_r + words_c);
-    const size_t smem_small = (size_t)ACA_WARPS * sizeof(double) * (32 + MAX_KMAX + small_words);
+    const size_t smem_big = sizeof(double) * (32 + MAX_KMAX) + sizeof(uint32_t) * (words_r + words_c + 1) +
+                            sizeof(float) * (ACA_WARPS + 1) * NORM_STRIDE;
+    const size_t smem_small = (size_t)ACA_WARPS * sizeof(double) * WARP_SMEM_DOUBLES;
+    (void)small_words;
     const size_t smem = std::max(smem_big, smem_small);
     HM_CUDA_CHECK(cudaFuncSetAttribute(aca_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     HM_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, aca_kernel, ACA_THREADS, smem));
@@ -454,13 +538,15 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
     a.npad = tr->npad;
     a.V = tr->V.as<double>();
     a.adm = tr->adm.as<int32_t>();
+    a.work = d_work.as<int32_t>();
     a.n_big = n_big;
-    a.n_all = na;
+    a.n_work = (int64_t)work.size();
     a.eps = A->params.aca_eps;
     a.kmax = kmax;
     a.qp = qp;
-    a.big_stride = (int64_t)(max_m_big + max_n_big) * kmax;
-    a.small_stride = (int64_t)max_sum_small * kmax;
+    // per worker: U, W (double) and their FP32 shadows, (m + n) * kmax * 1.5 doubles
+    a.big_stride = ((int64_t)(max_m_big + max_n_big) * kmax * 3 + 1) / 2;
+    a.small_stride = ((int64_t)max_sum_small * kmax * 3 + 1) / 2;
     a.big_words_r = words_r;
     a.big_words_c = words_c;
     DBuf scr_big, scr_small, ctr;
@@ -528,9 +614,21 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
         if ((int64_t)top > newcap) fail(HM_ENOMEM, "ACA factor arena overflow after growth");
     }
     // shrink the arena to what is used
-    A->lr_entries = (int64_t)top;
-    uw.alloc(sizeof(double) * std::max<int64_t>(A->lr_entries, 1));
-    HM_CUDA_CHECK(cudaMemcpyAsync(uw.p, arena.p, sizeof(double) * A->lr_entries, cudaMemcpyDeviceToDevice, s));
+    const int64_t used = (int64_t)top;
+    A->info.aca_entries = used;
+    uw.alloc(sizeof(double) * std::max<int64_t>(used, 1));
+    HM_CUDA_CHECK(cudaMemcpyAsync(uw.p, arena.p, sizeof(double) * used, cudaMemcpyDeviceToDevice, s));
+    mirror_rank_kernel<<<256, 256, 0, s>>>(tr->adm.as<int32_t>(), tr->adm_tp.as<int32_t>(), na, A->rank.as<int32_t>(),
+                                           uw_off.as<int64_t>());
+    HM_LAUNCH_CHECK();
+    {
+        // stored factor entries of the operator: sum_b k_b (m_b + n_b) over all blocks
+        DBuf sz;
+        sz.alloc(sizeof(int64_t) * (na + 1));
+        lr_size_kernel<<<256, 256, 0, s>>>(tr->adm.as<int32_t>(), A->rank.as<int32_t>(), na, sz.as<int64_t>());
+        HM_LAUNCH_CHECK();
+        A->lr_entries = exclusive_scan_i64(sz.as<int64_t>(), sz.as<int64_t>(), na, s);
+    }
     // t offsets (prefix sum of ranks)
     rank_to_i64<<<256, 256, 0, s>>>(A->rank.as<int32_t>(), na, A->t_off.as<int64_t>());
     HM_LAUNCH_CHECK();

@@ -106,7 +106,7 @@ hm_status hm_assemble(const hm_tree *tree, const hm_assemble_params *params, hm_
         const int e = read_scalar(err.as<int>(), s);
         if (e == 2) fail(HM_ETIMEOUT, "a panel staging wait timed out");
         if (e) fail(HM_EINTERNAL, "device error code %d during assembly", e);
-        hm_matrix_info &I = A->info;
+        hm_matrix_info &I = A->info;  // mean / max rank, kmax hits and ACA entries are set by the ACA
         I.dense_entries = tree->dense_true;
         I.lr_entries = A->lr_entries;
         I.s_nearfield = sr;

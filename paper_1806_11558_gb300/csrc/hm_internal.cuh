@@ -168,6 +168,7 @@ struct hm_tree {
     hm::DBuf dense;       // [n_dense][4] int32, sorted by (row_begin, col_begin), rows = one leaf cluster
     hm::DBuf dense_base;  // [n_dense] int64, offset of entry (0, 0) in the near-field arena
     hm::DBuf dense_ld;    // [n_dense] int32, row stride in the arena
+    hm::DBuf dense_tp;    // [n_dense] int32, leaf with swapped ranges, or -1
     int64_t dense_entries = 0;  // arena size (with row padding)
     int64_t dense_true = 0;     // sum over non-admissible leaves of |tau||sigma|
     hm::DBuf rho_off;     // [n_leaf + 1] int64, arena offset of each leaf row cluster's panel
@@ -176,6 +177,7 @@ struct hm_tree {
     hm::DBuf colidx;      // [sum Kd] int32, Morton column of each panel column (0 for padding)
     int32_t max_dense_dim = 0;
     hm::DBuf adm;         // [n_adm][4] int32, in block-tree level order (largest first)
+    hm::DBuf adm_tp;      // [n_adm] int32, leaf with swapped ranges, or -1
     int64_t adm_rows_cols = 0;
     hm::DBuf lr_rowptr;   // [n_leaf + 1] int64: admissible leaves whose rows cover each leaf cluster
     hm::DBuf lr_list;     // [..] int32 block ids (ascending per leaf cluster)

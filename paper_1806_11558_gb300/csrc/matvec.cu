@@ -299,10 +299,16 @@ __global__ void up_width_kernel(const int32_t *leaf_begin, int64_t nleaf, const 
     }
 }
 
+// A block below the diagonal with a partner p uses p's factors transposed:
+// U_b = W_p (row-major n_p x k) and W_b = U_p (column-major m_p x k).
+__device__ __forceinline__ bool is_mirror(const int32_t *adm, const int32_t *tp, int32_t b) {
+    return tp[b] >= 0 && adm[4 * b] > adm[4 * b + 2];
+}
+
 __global__ void up_pack_kernel(const int32_t *leaf_begin, const int64_t *lr_rowptr, const int32_t *lr_list,
-                               const int32_t *adm, const int32_t *rank, const int64_t *t_off, const int64_t *uw_off,
-                               const double *uw, const int32_t *koff, const int64_t *up_off, const int32_t *up_K,
-                               const int64_t *up_colptr, double *up, int32_t *tidx) {
+                               const int32_t *adm, const int32_t *tp, const int32_t *rank, const int64_t *t_off,
+                               const int64_t *uw_off, const double *uw, const int32_t *koff, const int64_t *up_off,
+                               const int32_t *up_K, const int64_t *up_colptr, double *up, int32_t *tidx) {
     const int64_t r = blockIdx.x;
     const int32_t r0 = leaf_begin[r], mr = leaf_begin[r + 1] - r0;
     const int Ku = up_K[r];
@@ -310,11 +316,22 @@ __global__ void up_pack_kernel(const int32_t *leaf_begin, const int64_t *lr_rowp
     int32_t *ti = tidx + up_colptr[r];
     for (int64_t q = lr_rowptr[r]; q < lr_rowptr[r + 1]; ++q) {
         const int32_t b = lr_list[q];
-        const int k = rank[b], m = adm[4 * b + 1] - adm[4 * b], off = r0 - adm[4 * b], c = koff[q];
-        const double *U = uw + uw_off[b];
-        for (int e = threadIdx.x; e < mr * k; e += blockDim.x) {
-            const int i = e / k, l = e - (e / k) * k;
-            Q[(int64_t)i * Ku + c + l] = U[(int64_t)l * m + off + i];
+        const int k = rank[b], off = r0 - adm[4 * b], c = koff[q];
+        if (is_mirror(adm, tp, b)) {
+            const int32_t p = tp[b];
+            const int mp = adm[4 * p + 1] - adm[4 * p];
+            const double *Wp = uw + uw_off[p] + (int64_t)mp * k;
+            for (int e = threadIdx.x; e < mr * k; e += blockDim.x) {
+                const int i = e / k, l = e - (e / k) * k;
+                Q[(int64_t)i * Ku + c + l] = Wp[(int64_t)(off + i) * k + l];
+            }
+        } else {
+            const int m = adm[4 * b + 1] - adm[4 * b];
+            const double *U = uw + uw_off[b];
+            for (int e = threadIdx.x; e < mr * k; e += blockDim.x) {
+                const int i = e / k, l = e - (e / k) * k;
+                Q[(int64_t)i * Ku + c + l] = U[(int64_t)l * m + off + i];
+            }
         }
         for (int l = threadIdx.x; l < k; l += blockDim.x) ti[c + l] = (int32_t)(t_off[b] + l);
     }
@@ -323,19 +340,31 @@ __global__ void up_pack_kernel(const int32_t *leaf_begin, const int64_t *lr_rowp
 // column panels of W: per leaf column cluster kappa, W_b(rows of kappa, :)
 // over the admissible leaves whose columns cover kappa
 __global__ void wp_pack_kernel(const int32_t *leaf_begin, const int64_t *lr_colptr, const int32_t *lr_collist,
-                               const int32_t *adm, const int32_t *rank, const int64_t *uw_off, const double *uw,
-                               const int32_t *koff, const int64_t *wp_off, const int32_t *wp_K, double *wp) {
+                               const int32_t *adm, const int32_t *tp, const int32_t *rank, const int64_t *uw_off,
+                               const double *uw, const int32_t *koff, const int64_t *wp_off, const int32_t *wp_K,
+                               double *wp) {
     const int64_t kap = blockIdx.x;
     const int32_t c0 = leaf_begin[kap], mc = leaf_begin[kap + 1] - c0;
     const int Kw = wp_K[kap];
     double *Wt = wp + wp_off[kap];
     for (int64_t q = lr_colptr[kap]; q < lr_colptr[kap + 1]; ++q) {
         const int32_t b = lr_collist[q];
-        const int k = rank[b], m = adm[4 * b + 1] - adm[4 * b], off = c0 - adm[4 * b + 2], c = koff[q];
-        const double *W = uw + uw_off[b] + (int64_t)m * k;  // row-major n x k
-        for (int e = threadIdx.x; e < mc * k; e += blockDim.x) {
-            const int j = e / k, l = e - (e / k) * k;
-            Wt[(int64_t)j * Kw + c + l] = W[(int64_t)(off + j) * k + l];
+        const int k = rank[b], off = c0 - adm[4 * b + 2], c = koff[q];
+        if (is_mirror(adm, tp, b)) {
+            const int32_t p = tp[b];
+            const int mp = adm[4 * p + 1] - adm[4 * p];
+            const double *Up = uw + uw_off[p];  // column-major m_p x k
+            for (int e = threadIdx.x; e < mc * k; e += blockDim.x) {
+                const int j = e / k, l = e - (e / k) * k;
+                Wt[(int64_t)j * Kw + c + l] = Up[(int64_t)l * mp + off + j];
+            }
+        } else {
+            const int m = adm[4 * b + 1] - adm[4 * b];
+            const double *W = uw + uw_off[b] + (int64_t)m * k;  // row-major n x k
+            for (int e = threadIdx.x; e < mc * k; e += blockDim.x) {
+                const int j = e / k, l = e - (e / k) * k;
+                Wt[(int64_t)j * Kw + c + l] = W[(int64_t)(off + j) * k + l];
+            }
         }
     }
 }
@@ -412,7 +441,8 @@ void build_lr_panels(hm_matrix *A, const DBuf &uw, const DBuf &uw_off, cudaStrea
     if (na > 0 && nl > 0) {
         up_pack_kernel<<<(unsigned)nl, 256, 0, s>>>(
             tr->leaf_begin.as<int32_t>(), tr->lr_rowptr.as<int64_t>(), tr->lr_list.as<int32_t>(),
-            tr->adm.as<int32_t>(), A->rank.as<int32_t>(), A->t_off.as<int64_t>(), uw_off.as<int64_t>(),
+            tr->adm.as<int32_t>(), tr->adm_tp.as<int32_t>(), A->rank.as<int32_t>(), A->t_off.as<int64_t>(),
+            uw_off.as<int64_t>(),
             uw.as<double>(), A->up_koff.as<int32_t>(), A->up_off.as<int64_t>(), A->up_K.as<int32_t>(),
             A->up_colptr.as<int64_t>(), A->up.as<double>(), A->tidx.as<int32_t>());
         HM_LAUNCH_CHECK();
@@ -438,7 +468,8 @@ void build_lr_panels(hm_matrix *A, const DBuf &uw, const DBuf &uw_off, cudaStrea
     if (na > 0 && nl > 0) {
         wp_pack_kernel<<<(unsigned)nl, 256, 0, s>>>(tr->leaf_begin.as<int32_t>(), tr->lr_colptr.as<int64_t>(),
                                                    tr->lr_collist.as<int32_t>(), tr->adm.as<int32_t>(),
-                                                   A->rank.as<int32_t>(), uw_off.as<int64_t>(), uw.as<double>(),
+                                                   tr->adm_tp.as<int32_t>(), A->rank.as<int32_t>(),
+                                                   uw_off.as<int64_t>(), uw.as<double>(),
                                                    A->wp_koff.as<int32_t>(), A->wp_off.as<int64_t>(),
                                                    A->wp_K.as<int32_t>(), A->wp.as<double>());
         HM_LAUNCH_CHECK();

@@ -6,13 +6,15 @@
 // dense blocks of that block row side by side), which is what the
 // row-owned H-matrix-vector product streams.
 //
-// nearfield_kernel: one CTA per dense block.  One elected thread stages the
+// nearfield_kernel: one CTA per dense block (of a pair of blocks with swapped
+// ranges, only the one above the diagonal works and writes both, the matrix
+// being symmetric).  One elected thread stages the
 // row cluster's and the column cluster's panel records (7 quadrature points,
 // area, vertex ids) into shared memory with two 2-D TMA box loads completing
 // on an mbarrier; every thread then evaluates entries with the 7x7 rule.
 // Pairs that share a vertex are queued (warp-aggregated append) for
 // singular_kernel, which gives each such entry one warp: the lanes split the
-// regions x n^3 Gauss points of the regularised integral.
+// Gauss points of the regularised integral.
 #include "entry.cuh"
 
 namespace hm {
@@ -89,7 +91,8 @@ constexpr int NF_THREADS = 128;
 __global__ void __launch_bounds__(NF_THREADS) nearfield_kernel(const __grid_constant__ CUtensorMap pt_map,
                                                                 const int32_t *__restrict__ dense,
                                                                 const int64_t *__restrict__ base,
-                                                                const int32_t *__restrict__ ld, int box_cols,
+                                                                const int32_t *__restrict__ ld,
+                                                                const int32_t *__restrict__ tp, int box_cols,
                                                                 const QuadParams qp, double *__restrict__ arena,
                                                                 SingularItem *__restrict__ sing,
                                                                 unsigned long long *sing_count, int64_t sing_cap,
@@ -98,6 +101,12 @@ __global__ void __launch_bounds__(NF_THREADS) nearfield_kernel(const __grid_cons
     unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     const int64_t b = blockIdx.x;
     const int32_t rb = dense[4 * b], re = dense[4 * b + 1], cb = dense[4 * b + 2], ce = dense[4 * b + 3];
+    // the matrix is symmetric: of a pair of leaves with swapped ranges the one
+    // above the diagonal evaluates the regular entries and stores them in
+    // both; the one below has nothing to do
+    const int32_t partner = tp[b];
+    const bool mirror = partner >= 0 && partner != b;
+    if (mirror && rb > cb) return;
     const int32_t rb_al = rb & ~1, cb_al = cb & ~1;
     const int tile_bytes = nf_tile_bytes(box_cols);
     double *tR = reinterpret_cast<double *>(sm);
@@ -122,6 +131,8 @@ __global__ void __launch_bounds__(NF_THREADS) nearfield_kernel(const __grid_cons
     const int ro = rb - rb_al, co = cb - cb_al;
     const int64_t blk_base = base[b];
     const int32_t blk_ld = ld[b];
+    const int64_t par_base = mirror ? base[partner] : 0;
+    const int32_t par_ld = mirror ? ld[partner] : 0;
     const int lane = threadIdx.x & 31;
     for (int e0 = 0; e0 < mn; e0 += NF_THREADS) {
         const int e = e0 + threadIdx.x;
@@ -138,28 +149,55 @@ __global__ void __launch_bounds__(NF_THREADS) nearfield_kernel(const __grid_cons
         const bool touch = valid && shared_vertices(vr, vc) > 0;
         const unsigned bal = __ballot_sync(0xffffffffu, touch);
         if (bal) {
+            // touching pairs are evaluated in both orientations (the
+            // regularised rule depends on which panel comes first)
+            const int per = mirror ? 2 : 1;
             const int leader = __ffs(bal) - 1;
             unsigned long long slot = 0;
-            if (lane == leader) slot = atomicAdd(sing_count, (unsigned long long)__popc(bal));
+            if (lane == leader) slot = atomicAdd(sing_count, (unsigned long long)(per * __popc(bal)));
             slot = __shfl_sync(0xffffffffu, slot, leader);
             if (touch) {
-                const unsigned long long k = slot + __popc(bal & ((1u << lane) - 1u));
-                if ((int64_t)k < sing_cap) {
+                const unsigned long long k = slot + per * __popc(bal & ((1u << lane) - 1u));
+                if ((int64_t)k + per <= sing_cap) {
                     sing[k].off = blk_base + (int64_t)i * blk_ld + j;
                     sing[k].i = rb + i;
                     sing[k].j = cb + j;
+                    if (mirror) {
+                        sing[k + 1].off = par_base + (int64_t)j * par_ld + i;
+                        sing[k + 1].i = cb + j;
+                        sing[k + 1].j = rb + i;
+                    }
                 } else {
                     atomicExch(err, 3);
                 }
             }
         }
-        if (valid && !touch) arena[blk_base + (int64_t)i * blk_ld + j] = regular_entry(R, box_cols, C, box_cols, qp);
+        if (valid && !touch) {
+            const double a = regular_entry(R, box_cols, C, box_cols, qp);
+            arena[blk_base + (int64_t)i * blk_ld + j] = a;
+            if (mirror) arena[par_base + (int64_t)j * par_ld + i] = a;
+        }
     }
 }
 
 // ---------------------------------------------------------------------------
 // touching pairs: one warp per entry
+//
+// The rule is the tensor Gauss-Legendre rule in (eta1, eta2, eta3) over the
+// Sauter-Schwab regions (entry.cuh).  For flat panels part of each integrand
+// is a low-degree polynomial that an n-point Gauss rule integrates exactly,
+// so the same rule value needs fewer evaluations:
+//  * identical panels: chi(u) - chi(v) = J (u - v) and in every region
+//    u - v = eta1 eta2 d(eta3) while the Jacobian is eta1^2 eta2, so the
+//    integrand is eta1 / |J d(eta3)|: the eta1 and eta2 sums are exactly 1/2
+//    and 1, the six regions pair up, and the value is
+//    sum_k w_k [1/|J(e_k,1)| + 1/|J(1,e_k)| + 1/|J(-e_k,1-e_k)|];
+//  * common edge: D = eta1 D'(eta2, eta3) and Jacobian = eta1^2 j'(eta2), so
+//    the eta1 sum is exactly 1/2 and a 2-D sum remains;
+//  * common vertex: the full 3-D sum.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ double inv_norm3(double x, double y, double z) { return rsqrt(fma(x, x, fma(y, y, z * z))); }
+
 __global__ void singular_kernel(const SingularItem *__restrict__ items, int64_t count, const int32_t *__restrict__ trim,
                                 const double *__restrict__ V, const double *__restrict__ pt, int64_t npad,
                                 const QuadParams qp, double *__restrict__ arena) {
@@ -174,12 +212,44 @@ __global__ void singular_kernel(const SingularItem *__restrict__ items, int64_t 
     touch_orient(a, bb, kind, P, Q);
     const PairGeom g = pair_geom(V, P, Q);
     const int n = qp.ss_n, n2 = n * n, n3 = n2 * n;
-    const int total = ss_regions(kind) * n3;
     double s = 0.0;
-    for (int t = lane; t < total; t += 32) {
-        const int r = t / n3, rem = t - r * n3;
-        const int k1 = rem / n2, k2 = (rem / n) % n, k3 = rem % n;
-        s += ss_point(g, kind, r, k1, k2, k3, qp);
+    if (kind == 3) {
+        // 1-D: three classes of regions, each counted twice with the eta1 / eta2 sums 1/2 and 1
+        for (int t = lane; t < 3 * n; t += 32) {
+            const int c = t / n, k = t - c * n;
+            const double e = qp.gx[k];
+            double s0, s1;
+            if (c == 0) { s0 = e; s1 = 1.0; }
+            else if (c == 1) { s0 = 1.0; s1 = e; }
+            else { s0 = -e; s1 = 1.0 - e; }
+            s += qp.gw[k] * inv_norm3(s0 * g.a1[0] + s1 * g.a2[0], s0 * g.a1[1] + s1 * g.a2[1],
+                                      s0 * g.a1[2] + s1 * g.a2[2]);
+        }
+    } else if (kind == 2) {
+        // 2-D: D' = d0 a1 + u1 a2 - v1 b2 over the five regions, eta1 sum = 1/2
+        for (int t = lane; t < 5 * n2; t += 32) {
+            const int r = t / n2, rem = t - r * n2, k2 = rem / n, k3 = rem - k2 * n;
+            const double e2 = qp.gx[k2], e3 = qp.gx[k3], e23 = e2 * e3;
+            double d0, u1, v1, jp;
+            switch (r) {
+                case 0: d0 = e2; u1 = e3; v1 = 1.0 - e2; jp = 1.0; break;
+                case 1: d0 = e23; u1 = 1.0; v1 = e2 - e23; jp = e2; break;
+                case 2: d0 = -e2; u1 = 1.0 - e2; v1 = e23; jp = e2; break;
+                case 3: d0 = -e23; u1 = e2 - e23; v1 = 1.0; jp = e2; break;
+                default: d0 = -e23; u1 = 1.0 - e23; v1 = e2; jp = e2; break;
+            }
+            const double dx = d0 * g.a1[0] + u1 * g.a2[0] - v1 * g.b2[0];
+            const double dy = d0 * g.a1[1] + u1 * g.a2[1] - v1 * g.b2[1];
+            const double dz = d0 * g.a1[2] + u1 * g.a2[2] - v1 * g.b2[2];
+            s += qp.gw[k2] * qp.gw[k3] * jp * inv_norm3(dx, dy, dz);
+        }
+        s *= 0.5;
+    } else {
+        for (int t = lane; t < 2 * n3; t += 32) {
+            const int r = t / n3, rem = t - r * n3;
+            const int k1 = rem / n2, k2 = (rem / n) % n, k3 = rem % n;
+            s += ss_point(g, kind, r, k1, k2, k3, qp);
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -211,7 +281,7 @@ void assemble_nearfield(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, c
     if (tr->n_dense > 0) {
         nearfield_kernel<<<(unsigned)tr->n_dense, NF_THREADS, smem, s>>>(
             tr->pt_map, tr->dense.as<int32_t>(), tr->dense_base.as<int64_t>(), tr->dense_ld.as<int32_t>(),
-            tr->box_cols, qp, A->dense.as<double>(), items.as<SingularItem>(), cnt.as<unsigned long long>(),
+            tr->dense_tp.as<int32_t>(), tr->box_cols, qp, A->dense.as<double>(), items.as<SingularItem>(), cnt.as<unsigned long long>(),
             tr->singular_cap, d_err);
         HM_LAUNCH_CHECK();
     }

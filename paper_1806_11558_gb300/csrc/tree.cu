@@ -368,6 +368,34 @@ __global__ void square_kernel(const int32_t *v, int64_t n, int64_t *out) {
         out[i] = (int64_t)v[i] * v[i];
 }
 
+// keys (row_begin << 32 | col_begin) of a leaf list, with identity payloads
+__global__ void leaf_keys_kernel(const int32_t *q, int64_t n, uint64_t *key, int32_t *idx) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        key[i] = ((uint64_t)(uint32_t)q[4 * i] << 32) | (uint32_t)q[4 * i + 2];
+        idx[i] = (int32_t)i;
+    }
+}
+
+// Transposed partner of each leaf: the leaf with exactly the swapped row and
+// column ranges (binary search over the sorted keys), or -1.
+__global__ void partner_kernel(const int32_t *q, int64_t n, const uint64_t *skey, const int32_t *sidx, int32_t *tp) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t want = ((uint64_t)(uint32_t)q[4 * i + 2] << 32) | (uint32_t)q[4 * i];
+        int64_t lo = 0, hi = n;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (skey[mid] < want) lo = mid + 1;
+            else hi = mid;
+        }
+        int32_t r = -1;
+        if (lo < n && skey[lo] == want) {
+            const int32_t j = sidx[lo];
+            if (q[4 * j + 1] == q[4 * i + 3] && q[4 * j + 3] == q[4 * i + 1]) r = j;
+        }
+        tp[i] = r;
+    }
+}
+
 __global__ void block_size_kernel(const int32_t *quad, int64_t n, int64_t *out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = (int64_t)(quad[4 * i + 1] - quad[4 * i]) * (quad[4 * i + 3] - quad[4 * i + 2]);
@@ -621,6 +649,19 @@ hm_tree *build_tree_impl(const double *d_V, int64_t nv, const int32_t *d_T, int6
         block_size_kernel<<<grid_for(n_den), 256, 0, s>>>(tr->dense.as<int32_t>(), n_den, mn.as<int64_t>());
         HM_LAUNCH_CHECK();
         tr->dense_true = exclusive_scan_i64(mn.as<int64_t>(), mn.as<int64_t>(), n_den, s);
+        // transposed partners (the list is sorted by (row_begin, col_begin))
+        tr->dense_tp.alloc(sizeof(int32_t) * std::max<int64_t>(n_den, 1));
+        if (n_den) {
+            DBuf k2, i2;
+            k2.alloc(sizeof(uint64_t) * n_den);
+            i2.alloc(sizeof(int32_t) * n_den);
+            leaf_keys_kernel<<<grid_for(n_den), 256, 0, s>>>(tr->dense.as<int32_t>(), n_den, k2.as<uint64_t>(),
+                                                             i2.as<int32_t>());
+            HM_LAUNCH_CHECK();
+            partner_kernel<<<grid_for(n_den), 256, 0, s>>>(tr->dense.as<int32_t>(), n_den, k2.as<uint64_t>(),
+                                                           i2.as<int32_t>(), tr->dense_tp.as<int32_t>());
+            HM_LAUNCH_CHECK();
+        }
     }
     // largest dense dimension (for the TMA box)
     tr->max_dense_dim = std::max(max_leaf, std::min<int32_t>((int32_t)n, max_leaf + 1));
@@ -670,6 +711,22 @@ hm_tree *build_tree_impl(const double *d_V, int64_t nv, const int32_t *d_T, int6
         };
         build_csr(0, tr->lr_rowptr, tr->lr_list, nullptr);
         build_csr(2, tr->lr_colptr, tr->lr_collist, &tr->lr_bcolptr);
+        // transposed partners of the admissible leaves
+        tr->adm_tp.alloc(sizeof(int32_t) * std::max<int64_t>(n_adm, 1));
+        if (n_adm) {
+            DBuf k2, i2, kt, it;
+            k2.alloc(sizeof(uint64_t) * n_adm);
+            i2.alloc(sizeof(int32_t) * n_adm);
+            kt.alloc(sizeof(uint64_t) * n_adm);
+            it.alloc(sizeof(int32_t) * n_adm);
+            leaf_keys_kernel<<<grid_for(n_adm), 256, 0, s>>>(tr->adm.as<int32_t>(), n_adm, k2.as<uint64_t>(),
+                                                             i2.as<int32_t>());
+            HM_LAUNCH_CHECK();
+            radix_sort_u64(k2.as<uint64_t>(), i2.as<int32_t>(), kt.as<uint64_t>(), it.as<int32_t>(), n_adm, 64, s);
+            partner_kernel<<<grid_for(n_adm), 256, 0, s>>>(tr->adm.as<int32_t>(), n_adm, k2.as<uint64_t>(),
+                                                           i2.as<int32_t>(), tr->adm_tp.as<int32_t>());
+            HM_LAUNCH_CHECK();
+        }
     }
 
     // upper bound on touching pairs: sum over vertices of valence^2
