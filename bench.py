@@ -29,7 +29,7 @@ sys.path.insert(0, ROOT)
 WORKLOAD = dict(workload="bumped icosphere level 7, Galerkin single-layer Laplace, P0",
                 panels=327680, leaf_size=64, eta=1.5, aca_eps=1e-7, aca_kmax=64, ss_order=8,
                 source=[3.0, 0.0, 0.0], solve_rel_tol=1e-12, inner="fp32 factors + fp32 near field",
-                inner_tol=1e-4, restart=30, precond=os.environ.get("HM_BENCH_PRECOND", "1") == "1")
+                inner_tol=1e-4, restart=int(os.environ.get("HM_BENCH_RESTART", "60")), precond=os.environ.get("HM_BENCH_PRECOND", "1") == "1")
 METRIC = "H-matrix setup s, H-matvec GB/s, solve s at 1e-8 rel. accuracy: mixed vs FP64"
 FLOPS_PER_PAIR = 11  # 3 sub + 3 mul + 2 add (|x-y|^2) + rsqrt + multiply-add (weight)
 PAIRS_PER_ENTRY = 49

@@ -275,6 +275,15 @@ HM_API hm_status hm_matrix_export(const hm_matrix *A, double *h_dense, int64_t *
  * threads).  Lets a caller count the device work behind a sequence of calls. */
 HM_API int64_t hm_kernel_launches(void);
 
+/* One leaf of the H-matrix as a dense row-major m x n array written to d_out
+ * (device, caller-owned, m * n doubles): the stored entries of a
+ * non-admissible leaf (dense = 1), or the product U_b W_b^T of an admissible
+ * leaf (dense = 0); `index` as in hm_tree_get_leaves.  Introspection for
+ * checks on large problems, where hm_matrix_export would not fit in host
+ * memory.  Errors: HM_EINVAL for a bad handle, index or NULL pointer. */
+HM_API hm_status hm_matrix_get_block(const hm_matrix *A, int32_t dense, int64_t index, double *d_out,
+                                     hm_stream_t stream);
+
 /* Message of the last failure on the calling thread ("" when none). */
 HM_API const char *hm_last_error(void);
 

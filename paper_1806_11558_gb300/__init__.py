@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "HM_OK", 1: "HM_EINVAL", 2: "HM_ENOMEM", 3: "HM_ECUDA", 4: "H
 
 EXPORTED = ["hm_build_tree", "hm_assemble", "hm_load_vector", "hm_matvec", "hm_solve", "hm_free",
             "hm_tree_get_info", "hm_tree_get_perm", "hm_tree_get_leaves", "hm_matrix_get_info",
-            "hm_matrix_export", "hm_last_error", "hm_kernel_launches", "hm_matvec_noalloc"]
+            "hm_matrix_export", "hm_last_error", "hm_kernel_launches", "hm_matvec_noalloc", "hm_matrix_get_block"]
 
 
 class HMError(RuntimeError):
@@ -93,6 +93,7 @@ def lib():
             "hm_tree_get_leaves": [P, I32, P, I64, P],
             "hm_matrix_get_info": [P, P],
             "hm_matrix_export": [P, P, P, P, P, P, P, P, P],
+            "hm_matrix_get_block": [P, I32, I64, P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -232,6 +233,14 @@ def hm_matrix_get_info(A) -> dict:
     info = MatrixInfo()
     _check(lib().hm_matrix_get_info(A, ctypes.byref(info)))
     return struct_dict(info)
+
+
+def hm_matrix_get_block(A, dense: bool, index: int, m: int, n: int, stream=None):
+    """Leaf `index` of the H-matrix as a dense (m, n) CUDA float64 tensor."""
+    import torch
+    out = torch.empty((m, n), dtype=torch.float64, device="cuda")
+    _check(lib().hm_matrix_get_block(A, int(dense), int(index), _ptr(out), _stream(stream)))
+    return out
 
 
 def hm_matrix_export(A, n_dense: int, n_adm: int):

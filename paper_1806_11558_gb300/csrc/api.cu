@@ -29,6 +29,7 @@ void permute_from_morton(const hm_tree *tr, const double *ym, double alpha, doub
 void load_vector_impl(const hm_tree *tr, const double *src, int nsrc, double *f, cudaStream_t s);
 hm_status solve_impl(const hm_matrix *A, const double *b, double *x, const hm_solve_params &p, cudaStream_t s,
                      hm_solve_info *info);
+void get_block(const hm_matrix *A, int dense, int64_t b, double *out, cudaStream_t s);
 void matvec_noalloc(const hm_matrix *A, int32_t nrhs, hm_dtype prec, const double *x, double *y, double alpha,
                     double beta, cudaStream_t s);
 }  // namespace hm
@@ -243,6 +244,13 @@ hm_status hm_tree_get_leaves(const hm_tree *tree, int32_t dense, int32_t *d_out,
         if (d_out && capacity >= n && n > 0)
             HM_CUDA_CHECK(cudaMemcpy(d_out, dense ? tree->dense.p : tree->adm.p, sizeof(int32_t) * 4 * n,
                                      cudaMemcpyDeviceToDevice));
+    });
+}
+
+hm_status hm_matrix_get_block(const hm_matrix *A, int32_t dense, int64_t index, double *d_out, hm_stream_t stream) {
+    return guard([&] {
+        if (!is_matrix(A) || !d_out) fail(HM_EINVAL, "bad argument");
+        get_block(A, dense != 0, index, d_out, (cudaStream_t)stream);
     });
 }
 

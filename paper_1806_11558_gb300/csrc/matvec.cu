@@ -555,6 +555,79 @@ MatvecWork matvec_work_at(const hm_matrix *A, double *base) {
 }
 
 // ---------------------------------------------------------------------------
+// one leaf as a dense array (introspection)
+// ---------------------------------------------------------------------------
+__global__ void get_dense_block_kernel(const int64_t base, const int32_t ld, int m, int n, const double *dense,
+                                       double *out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)m * n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / n), j = (int)(e - (e / n) * n);
+        out[e] = dense[base + (int64_t)i * ld + j];
+    }
+}
+
+__device__ __forceinline__ int64_t find_in(const int32_t *list, int64_t lo, int64_t hi, int32_t v) {
+    for (; lo < hi; ++lo)  // lists are short (the blocks of one leaf cluster)
+        if (list[lo] == v) break;
+    return lo;
+}
+
+__device__ __forceinline__ int64_t leaf_of(const int32_t *leaf_begin, int64_t nl, int32_t row) {
+    int64_t lo = 0, hi = nl;  // last leaf with begin <= row
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (leaf_begin[mid] <= row) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void get_lr_block_kernel(int32_t b, int32_t rb, int32_t cb, int m, int n, int k,
+                                    const int32_t *leaf_begin, int64_t nl, const int64_t *lr_rowptr,
+                                    const int32_t *lr_list, const int32_t *up_koff, const int64_t *up_off,
+                                    const int32_t *up_K, const double *up, const int64_t *lr_colptr,
+                                    const int32_t *lr_collist, const int32_t *wp_koff, const int64_t *wp_off,
+                                    const int32_t *wp_K, const double *wp, double *out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)m * n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / n), j = (int)(e - (e / n) * n);
+        const int64_t r = leaf_of(leaf_begin, nl, rb + i), c = leaf_of(leaf_begin, nl, cb + j);
+        const int64_t qr = find_in(lr_list, lr_rowptr[r], lr_rowptr[r + 1], b);
+        const int64_t qc = find_in(lr_collist, lr_colptr[c], lr_colptr[c + 1], b);
+        const double *Ur = up + up_off[r] + (int64_t)(rb + i - leaf_begin[r]) * up_K[r] + up_koff[qr];
+        const double *Wr = wp + wp_off[c] + (int64_t)(cb + j - leaf_begin[c]) * wp_K[c] + wp_koff[qc];
+        double acc = 0.0;
+        for (int l = 0; l < k; ++l) acc += Ur[l] * Wr[l];
+        out[e] = acc;
+    }
+}
+
+void get_block(const hm_matrix *A, int dense, int64_t b, double *out, cudaStream_t s) {
+    const hm_tree *tr = A->tree;
+    const int64_t nb = dense ? tr->n_dense : tr->n_adm;
+    if (b < 0 || b >= nb) fail(HM_EINVAL, "leaf index %lld out of range", (long long)b);
+    int32_t q[4];
+    HM_CUDA_CHECK(cudaMemcpyAsync(q, (dense ? tr->dense.as<int32_t>() : tr->adm.as<int32_t>()) + 4 * b,
+                                  sizeof(q), cudaMemcpyDeviceToHost, s));
+    HM_CUDA_CHECK(cudaStreamSynchronize(s));
+    const int m = q[1] - q[0], n = q[3] - q[2];
+    if (dense) {
+        const int64_t base = read_scalar(tr->dense_base.as<int64_t>() + b, s);
+        const int32_t ld = read_scalar(tr->dense_ld.as<int32_t>() + b, s);
+        get_dense_block_kernel<<<grid1d((int64_t)m * n), 256, 0, s>>>(base, ld, m, n, A->dense.as<double>(), out);
+        HM_LAUNCH_CHECK();
+    } else {
+        const int k = read_scalar(A->rank.as<int32_t>() + b, s);
+        get_lr_block_kernel<<<grid1d((int64_t)m * n), 256, 0, s>>>(
+            (int32_t)b, q[0], q[2], m, n, k, tr->leaf_begin.as<int32_t>(), tr->n_leaf, tr->lr_rowptr.as<int64_t>(),
+            tr->lr_list.as<int32_t>(), A->up_koff.as<int32_t>(), A->up_off.as<int64_t>(), A->up_K.as<int32_t>(),
+            A->up.as<double>(), tr->lr_colptr.as<int64_t>(), tr->lr_collist.as<int32_t>(), A->wp_koff.as<int32_t>(),
+            A->wp_off.as<int64_t>(), A->wp_K.as<int32_t>(), A->wp.as<double>(), out);
+        HM_LAUNCH_CHECK();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // low-precision copies
 // ---------------------------------------------------------------------------
 __global__ void to_f32_kernel(const double *a, int64_t n, float *o) {

@@ -41,6 +41,12 @@ class GpuH:
         ti = self.info()
         return self.hm.hm_matrix_export(self.A, ti["n_dense"], ti["n_adm"])
 
+    def block(self, dense, index, blk):
+        rb, re, cb, ce = blk
+        out = self.hm.hm_matrix_get_block(self.A, dense, index, int(re - rb), int(ce - cb))
+        self.torch.cuda.synchronize()
+        return out.cpu().numpy()
+
     def matvec(self, x, prec=0):
         torch = self.torch
         xd = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
