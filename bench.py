@@ -46,6 +46,75 @@ def _peaks():
 
 CASE = "precision"
 
+# Nominal ALU peaks of GB300 (152 SMs at 2.07 GHz): FP64 2 DFMA / SM / clock,
+# FP32 128 FFMA / SM / clock; FMA = 2 flops.
+FP64_PEAK_TFLOPS = 152 * 2.07e9 * 2 * 2 / 1e12   # 1.26
+FP32_PEAK_TFLOPS = 152 * 2.07e9 * 128 * 2 / 1e12  # 80.5
+# FP32 flops of one pair evaluation in the double-float far-field entry of the
+# ACA (TwoSum 6, TwoProduct 2 with its FMA counted 2, ...): 93 per pair
+FF_FLOPS_PER_PAIR = 93
+
+# DRAM traffic per launch from an ncu capture, valid while the kernel's source
+# file is unchanged (sha256 of the file at capture time); null otherwise.
+TRAFFIC = {}
+
+
+def _file_sha(rel):
+    import hashlib
+    with open(os.path.join(ROOT, rel), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def kernel_table(trace, steps):
+    """Traced kernels of the timed region, largest device time first."""
+    tot = sum(ms for _, ms in trace.values()) or 1.0
+    rows = sorted(trace.items(), key=lambda kv: -kv[1][1])
+    return {name: {"launches_per_step": c / steps, "ms_per_step": ms / steps, "ms_per_launch": ms / max(c, 1),
+                   "share_of_traced": ms / tot} for name, (c, ms) in rows}
+
+
+def algorithmic_work(mi, ti, dense_leaves, n):
+    """Algorithmic work per launch of each traced kernel: (bound, amount, unit)."""
+    u = mi["u_entries"]
+    w = mi["lr_entries"] - u
+    d = mi["dense_entries"]
+    rb, re_, cb, ce = dense_leaves.T
+    # the near-field kernel evaluates each mirrored pair of leaves once (the
+    # ~2% touching positions among them, handed to the touching-pair kernel,
+    # are counted too)
+    nf_entries = int(((re_ - rb) * (ce - cb))[rb <= cb].sum())
+    K = mi["mean_rank"] * ti["n_adm"]  # sum of ranks = length of t
+    nl = (ti["n_clusters"] + 1) // 2  # leaf clusters of the binary cluster tree; partials = sum over them of K_w
+    return {
+        "row_kernel.f64": ("alu", 2.0 * (d + u), "flop"),
+        "col_kernel.f64": ("alu", 2.0 * w, "flop"),
+        "row_kernel.f32": ("hbm", 4.0 * (d + u) + 4.0 * (n + K) + 8.0 * n, "byte"),
+        "col_kernel.f32": ("hbm", 4.0 * w + 4.0 * n + 4.0 * w * nl / n, "byte"),
+        "row_kernel.bf16": ("hbm", 4.0 * d + 2.0 * u + 4.0 * (n + K) + 8.0 * n, "byte"),
+        "col_kernel.bf16": ("hbm", 2.0 * w + 4.0 * n + 4.0 * w * nl / n, "byte"),
+        "nearfield_kernel": ("alu", float(nf_entries) * PAIRS_PER_ENTRY * FLOPS_PER_PAIR, "flop"),
+        "aca_kernel": ("alu32", float(mi["aca_entries"]) * PAIRS_PER_ENTRY * FF_FLOPS_PER_PAIR, "flop"),
+    }
+
+
+def roofline_entry(name, kt, wk, peaks, peak_src):
+    bound, amount, unit = wk
+    t = kt["ms_per_launch"] / 1e3
+    if bound == "hbm":
+        ach, peak, u, src = amount / t / 1e9, peaks["hbm_gbs"], "GB/s", peak_src + " HBM copy bandwidth"
+    elif bound == "alu":
+        ach, peak, u, src = amount / t / 1e12, FP64_PEAK_TFLOPS, "TFLOP/s", "nominal FP64 (unit counts x clock)"
+    else:
+        ach, peak, u, src = amount / t / 1e12, FP32_PEAK_TFLOPS, "TFLOP/s", "nominal FP32 (unit counts x clock)"
+    tr = TRAFFIC.get(name)
+    traffic = None
+    if tr is not None and _file_sha(tr["source"]) == tr["sha256"]:
+        traffic = tr["bytes_per_launch"]
+    return {"kernel": name, "bound": "alu" if bound.startswith("alu") else bound, "achieved": ach, "peak": peak,
+            "unit": u, "frac": ach / peak, "traffic": traffic, "peak_source": src,
+            "algorithmic_" + unit + "s_per_launch": amount, "launch_ms": kt["ms_per_launch"],
+            "launches_per_step": kt["launches_per_step"]}
+
 
 def _inputs():
     import meshgen
@@ -174,6 +243,7 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     clocks = Clocks(dev.index)
     clocks.start()
+    hm.hm_trace_enable(True)
     l0 = hm.hm_kernel_launches()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -182,6 +252,8 @@ def run_ours(args, rank, world):
     ev1.record(stream)
     torch.cuda.synchronize()
     launches = hm.hm_kernel_launches() - l0
+    hm.hm_trace_enable(False)
+    trace = hm.hm_trace_read()
     ck = clocks.stop()
     total_s = ev0.elapsed_time(ev1) / 1e3
     if world > 1:
@@ -248,27 +320,22 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     e2e_s = c0.elapsed_time(c1) / 1e3 / e2e_steps
 
-    # roofline of the dominant kernel (the batched ACA): FP64 arithmetic.
-    # Algorithmic work = entry evaluations (sum_b k_b (m_b + n_b) = stored
-    # factor entries) x 49 kernel evaluations x FLOPS_PER_PAIR, per launch,
-    # over the kernel's CUDA-event duration measured inside hm_assemble.
+    # roofline of the dominant kernel: the traced kernel with the largest
+    # device time over the timed steps; achieved = its algorithmic work per
+    # launch / its mean launch time (CUDA events on its own stream)
     peaks, peak_src = _peaks()
-    fp64_peak_tflops = 1.25  # nominal FP64 rate of GB300 (2 DFMA / SM / clock at 2.07 GHz x 152 SMs)
-    aca_flops = mi["aca_entries"] * PAIRS_PER_ENTRY * FLOPS_PER_PAIR
-    aca_s = sum(r["minfo"]["s_aca"] for r in results) / len(results)
+    leaves = hm.hm_tree_get_leaves(tree, True).cpu().numpy().astype("int64")
+    kernels = kernel_table(trace, args.steps)
+    work = algorithmic_work(mi, ti, leaves, n)
+    roofline = None
+    for name, kt in kernels.items():
+        if name in work:
+            roofline = roofline_entry(name, kt, work[name], peaks, peak_src)
+            break
+    others = {name: roofline_entry(name, kt, work[name], peaks, peak_src)
+              for name, kt in kernels.items() if name in work and (roofline is None or name != roofline["kernel"])}
     nf_s = sum(r["minfo"]["s_nearfield"] for r in results) / len(results)
-    nf_flops = ti["dense_entries"] * PAIRS_PER_ENTRY * FLOPS_PER_PAIR
-    aca_tf = aca_flops / aca_s / 1e12
-    roofline = {"kernel": "aca_kernel", "bound": "alu", "achieved": aca_tf, "peak": fp64_peak_tflops,
-                "unit": "TFLOP/s", "frac": aca_tf / fp64_peak_tflops, "traffic": None,
-                "peak_source": "FP64 nominal 1.25 TFLOP/s (no FP64 figure in MEASURED_PEAKS.json)",
-                "launch_s": aca_s, "entries_evaluated": mi["aca_entries"]}
-    nearfield_roof = {"kernel": "nearfield_kernel", "bound": "alu", "launch_s": nf_s,
-                      "achieved": nf_flops / nf_s / 1e12, "peak": fp64_peak_tflops, "unit": "TFLOP/s",
-                      "frac": nf_flops / nf_s / 1e12 / fp64_peak_tflops}
-    matvec_roof = {"kernel": "row_kernel + lr_project_kernel (fp32 copy)", "bound": "hbm",
-                   "achieved": mv["fp32"]["gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                   "frac": mv["fp32"]["gbs"] / peaks["hbm_gbs"], "peak_source": peak_src}
+    aca_s = sum(r["minfo"]["s_aca"] for r in results) / len(results)
     hm.hm_free(A)
     hm.hm_free(tree)
 
@@ -291,7 +358,7 @@ def run_ours(args, rank, world):
         "resid_fp64": last["resid_fp64"], "resid_mixed": last["resid_mixed"], "mixed_vs_fp64_rel_err": err_mixed,
         "bf16": bf16, "matvec": mv, "mean_rank": mi["mean_rank"], "max_rank": mi["max_rank"],
         "dense_entries": mi["dense_entries"], "lr_entries": mi["lr_entries"],
-        "roofline": roofline, "nearfield_roofline": nearfield_roof, "matvec_roofline": matvec_roof,
+        "roofline": roofline, "kernels": kernels, "rooflines_other": others,
         "clocks": ck, "gpu_launches": int(launches),
         "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(V.nbytes + T.nbytes),
                 "d2h_bytes_per_step": int(n * 8)},

@@ -135,7 +135,10 @@ typedef struct {
     int64_t n_adm;          /* admissible leaves                                  */
     int64_t dense_entries;  /* sum of |tau||sigma| over non-admissible leaves     */
     int64_t adm_rows_cols;  /* sum of |tau| + |sigma| over admissible leaves      */
-    int64_t n_singular;     /* touching panel pairs (shared vertex or edge)       */
+    int64_t n_singular;     /* Sauter-Schwab evaluations of the last assembly:
+                               touching pairs (shared vertex, edge or panel),
+                               a common-vertex pair of a symmetric block
+                               counted once                                    */
     double seconds;         /* wall time of hm_build_tree                         */
 } hm_tree_info;
 
@@ -155,6 +158,7 @@ typedef struct {
                                over the blocks it approximated (the transposed
                                partner of an approximated block reuses its
                                factors, the matrix being symmetric)            */
+    int64_t u_entries;      /* stored entries of the U factors, sum k_b |tau|     */
 } hm_matrix_info;
 
 /* Build the Morton-ordered cluster tree and the block cluster tree of a
@@ -201,6 +205,8 @@ HM_API hm_status hm_load_vector(const hm_tree *tree, const double *d_sources, in
  *         low-precision copies (FP32 accumulation; they must have been
  *         requested in hm_assemble).
  *  d_x, d_y : device pointers, must not overlap.
+ *  Stream-ordered: the call queues the work on `stream` and returns; its
+ *  working vectors come from the stream-ordered pool (cudaMallocAsync).
  *  Errors: HM_EINVAL for NULL pointers, nrhs < 1, a precision whose copy was
  *  not assembled, or trans not in {0, 1}. */
 HM_API hm_status hm_matvec(const hm_matrix *A, int32_t trans, int32_t nrhs, hm_dtype prec, const double *d_x, double *d_y,
@@ -274,6 +280,27 @@ HM_API hm_status hm_matrix_export(const hm_matrix *A, double *h_dense, int64_t *
 /* Number of CUDA kernels this library has launched since it was loaded (all
  * threads).  Lets a caller count the device work behind a sequence of calls. */
 HM_API int64_t hm_kernel_launches(void);
+
+/* Kernel timing trace.  hm_trace_enable(1) clears the trace and starts it;
+ * while it runs, the library brackets each launch of its main kernels (the
+ * near-field, touching-pair and ACA kernels, the three kernels of the
+ * H-matvec per precision, and the solver's block-Jacobi, dot-product and
+ * update kernels) with a pair of CUDA events recorded on the launching stream
+ * (not while that stream is being captured).  hm_trace_enable(0) stops it and
+ * keeps what was recorded.  The library has no counterpart in the paper; it
+ * exists so that a caller can time single kernels inside a longer sequence. */
+HM_API hm_status hm_trace_enable(int32_t on);
+
+typedef struct {
+    char name[48];    /* kernel name, with ".f64" / ".f32" / ".bf16" for the matvec */
+    int64_t launches; /* traced launches                                            */
+    double ms;        /* summed device time of those launches, milliseconds         */
+} hm_trace_entry;
+
+/* Per-kernel totals of the trace: up to `capacity` entries into out (host),
+ * *count receives the number of distinct kernels.  Waits for the recorded
+ * events.  Errors: HM_EINVAL for NULL count, HM_ECUDA for a failed event. */
+HM_API hm_status hm_trace_read(hm_trace_entry *out, int32_t capacity, int32_t *count);
 
 /* One leaf of the H-matrix as a dense row-major m x n array written to d_out
  * (device, caller-owned, m * n doubles): the stored entries of a

@@ -22,7 +22,8 @@ STATUS_NAMES = {0: "HM_OK", 1: "HM_EINVAL", 2: "HM_ENOMEM", 3: "HM_ECUDA", 4: "H
 
 EXPORTED = ["hm_build_tree", "hm_assemble", "hm_load_vector", "hm_matvec", "hm_solve", "hm_free",
             "hm_tree_get_info", "hm_tree_get_perm", "hm_tree_get_leaves", "hm_matrix_get_info",
-            "hm_matrix_export", "hm_last_error", "hm_kernel_launches", "hm_matvec_noalloc", "hm_matrix_get_block"]
+            "hm_matrix_export", "hm_last_error", "hm_kernel_launches", "hm_matvec_noalloc", "hm_matrix_get_block",
+            "hm_trace_enable", "hm_trace_read"]
 
 
 class HMError(RuntimeError):
@@ -62,7 +63,12 @@ class MatrixInfo(ctypes.Structure):
     _fields_ = [("dense_entries", ctypes.c_int64), ("lr_entries", ctypes.c_int64), ("max_rank", ctypes.c_int32),
                 ("kmax_hit", ctypes.c_int32), ("mean_rank", ctypes.c_double), ("s_nearfield", ctypes.c_double),
                 ("s_singular", ctypes.c_double), ("s_aca", ctypes.c_double), ("s_total", ctypes.c_double),
-                ("bytes_f64", ctypes.c_int64), ("bytes_low", ctypes.c_int64), ("aca_entries", ctypes.c_int64)]
+                ("bytes_f64", ctypes.c_int64), ("bytes_low", ctypes.c_int64), ("aca_entries", ctypes.c_int64),
+                ("u_entries", ctypes.c_int64)]
+
+
+class TraceEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("ms", ctypes.c_double)]
 
 
 def struct_dict(s):
@@ -94,6 +100,8 @@ def lib():
             "hm_matrix_get_info": [P, P],
             "hm_matrix_export": [P, P, P, P, P, P, P, P, P],
             "hm_matrix_get_block": [P, I32, I64, P, P],
+            "hm_trace_enable": [I32],
+            "hm_trace_read": [P, I32, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -115,6 +123,20 @@ def hm_last_error() -> str:
 
 def hm_kernel_launches() -> int:
     return int(lib().hm_kernel_launches())
+
+
+def hm_trace_enable(on: bool = True):
+    """Start (clearing it) or stop the per-kernel CUDA-event trace."""
+    _check(lib().hm_trace_enable(int(bool(on))))
+
+
+def hm_trace_read() -> dict:
+    """{kernel name: (launches, device ms)} of the trace."""
+    cnt = ctypes.c_int32(0)
+    _check(lib().hm_trace_read(None, 0, ctypes.byref(cnt)))
+    buf = (TraceEntry * max(1, cnt.value))()
+    _check(lib().hm_trace_read(buf, cnt.value, ctypes.byref(cnt)))
+    return {buf[k].name.decode(): (int(buf[k].launches), float(buf[k].ms)) for k in range(cnt.value)}
 
 
 def _check(status):

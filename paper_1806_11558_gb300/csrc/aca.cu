@@ -447,9 +447,11 @@ __global__ void mirror_rank_kernel(const int32_t *adm, const int32_t *tp, int64_
     }
 }
 
-__global__ void lr_size_kernel(const int32_t *adm, const int32_t *rank, int64_t na, int64_t *out) {
+// k_b (m_b + n_b) per block, or k_b m_b (rows_only)
+__global__ void lr_size_kernel(const int32_t *adm, const int32_t *rank, int64_t na, int rows_only, int64_t *out) {
     for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < na; b += (int64_t)gridDim.x * blockDim.x)
-        out[b] = (int64_t)rank[b] * ((adm[4 * b + 1] - adm[4 * b]) + (adm[4 * b + 3] - adm[4 * b + 2]));
+        out[b] = (int64_t)rank[b] *
+                 ((adm[4 * b + 1] - adm[4 * b]) + (rows_only ? 0 : (adm[4 * b + 3] - adm[4 * b + 2])));
 }
 
 __global__ void rank_to_i64(const int32_t *rank, int64_t na, int64_t *out) {
@@ -576,8 +578,11 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
     HM_CUDA_CHECK(cudaEventCreate(&e0));
     HM_CUDA_CHECK(cudaEventCreate(&e1));
     HM_CUDA_CHECK(cudaEventRecord(e0, s));
-    aca_kernel<<<grid, ACA_THREADS, smem, s>>>(a);
-    HM_LAUNCH_CHECK();
+    {
+        Trace trace("aca_kernel", s);
+        aca_kernel<<<grid, ACA_THREADS, smem, s>>>(a);
+        HM_LAUNCH_CHECK();
+    }
     HM_CUDA_CHECK(cudaEventRecord(e1, s));
     HM_CUDA_CHECK(cudaEventSynchronize(e1));
     float ms = 0;
@@ -608,6 +613,7 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
         unsigned long long used_u = (unsigned long long)used;
         HM_CUDA_CHECK(cudaMemcpyAsync(a.arena_top, &used_u, sizeof(used_u), cudaMemcpyHostToDevice, s));
         HM_CUDA_CHECK(cudaMemsetAsync(a.q_big, 0, sizeof(unsigned long long), s));
+        Trace trace("aca_kernel", s);
         aca_kernel<<<grid, ACA_THREADS, smem, s>>>(a);
         HM_LAUNCH_CHECK();
         top = read_scalar(a.arena_top, s);
@@ -625,9 +631,12 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
         // stored factor entries of the operator: sum_b k_b (m_b + n_b) over all blocks
         DBuf sz;
         sz.alloc(sizeof(int64_t) * (na + 1));
-        lr_size_kernel<<<256, 256, 0, s>>>(tr->adm.as<int32_t>(), A->rank.as<int32_t>(), na, sz.as<int64_t>());
+        lr_size_kernel<<<256, 256, 0, s>>>(tr->adm.as<int32_t>(), A->rank.as<int32_t>(), na, 0, sz.as<int64_t>());
         HM_LAUNCH_CHECK();
         A->lr_entries = exclusive_scan_i64(sz.as<int64_t>(), sz.as<int64_t>(), na, s);
+        lr_size_kernel<<<256, 256, 0, s>>>(tr->adm.as<int32_t>(), A->rank.as<int32_t>(), na, 1, sz.as<int64_t>());
+        HM_LAUNCH_CHECK();
+        A->info.u_entries = exclusive_scan_i64(sz.as<int64_t>(), sz.as<int64_t>(), na, s);
     }
     // t offsets (prefix sum of ranks)
     rank_to_i64<<<256, 256, 0, s>>>(A->rank.as<int32_t>(), na, A->t_off.as<int64_t>());

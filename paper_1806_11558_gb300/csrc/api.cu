@@ -8,6 +8,8 @@
 #include <cmath>
 #include <memory>
 
+#include <cstring>
+
 #include "hm_internal.cuh"
 
 namespace hm {
@@ -143,15 +145,14 @@ hm_status hm_matvec(const hm_matrix *A, int32_t trans, int32_t nrhs, hm_dtype pr
         if (prec < HM_F64 || prec > HM_BF16) fail(HM_EINVAL, "bad precision");
         cudaStream_t s = (cudaStream_t)stream;
         const int64_t n = A->tree->n;
-        DBuf work;
-        work.alloc(sizeof(double) * matvec_work_doubles(A));
+        SBuf work;
+        work.alloc(sizeof(double) * matvec_work_doubles(A), s);
         const MatvecWork w = matvec_work_at(A, work.as<double>());
         for (int r = 0; r < nrhs; ++r) {
             permute_to_morton(A->tree, d_x + (int64_t)r * n, w.xm, s);
             matvec_morton(A, prec, w, s);
             permute_from_morton(A->tree, w.ym, alpha, beta, d_y + (int64_t)r * n, s);
         }
-        HM_CUDA_CHECK(cudaStreamSynchronize(s));
     });
 }
 
@@ -244,6 +245,24 @@ hm_status hm_tree_get_leaves(const hm_tree *tree, int32_t dense, int32_t *d_out,
         if (d_out && capacity >= n && n > 0)
             HM_CUDA_CHECK(cudaMemcpy(d_out, dense ? tree->dense.p : tree->adm.p, sizeof(int32_t) * 4 * n,
                                      cudaMemcpyDeviceToDevice));
+    });
+}
+
+hm_status hm_trace_enable(int32_t on) {
+    return guard([&] { trace_enable(on != 0); });
+}
+
+hm_status hm_trace_read(hm_trace_entry *out, int32_t capacity, int32_t *count) {
+    return guard([&] {
+        if (!count) fail(HM_EINVAL, "NULL count");
+        const std::vector<TraceTotal> t = trace_read();
+        *count = (int32_t)t.size();
+        for (int32_t k = 0; out && k < capacity && k < (int32_t)t.size(); ++k) {
+            std::memset(out[k].name, 0, sizeof(out[k].name));
+            std::strncpy(out[k].name, t[k].name.c_str(), sizeof(out[k].name) - 1);
+            out[k].launches = t[k].launches;
+            out[k].ms = t[k].ms;
+        }
     });
 }
 

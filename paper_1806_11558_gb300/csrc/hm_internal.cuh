@@ -71,6 +71,26 @@ void count_launch();
         HM_CUDA_CHECK(cudaGetLastError()); \
     } while (0)
 
+// Kernel timing trace: while enabled (hm_trace_enable), a Trace object
+// records a CUDA event on the launching stream when it is made and another
+// when it goes out of scope, so the launches between them are timed on the
+// device; nothing is recorded while the stream is being captured.
+struct Trace {
+    int slot = -1;
+    cudaStream_t s = nullptr;
+    Trace(const char *name, cudaStream_t stream);
+    ~Trace();
+    Trace(const Trace &) = delete;
+    Trace &operator=(const Trace &) = delete;
+};
+void trace_enable(bool on);
+struct TraceTotal {
+    std::string name;
+    long long launches;
+    double ms;
+};
+std::vector<TraceTotal> trace_read();
+
 // ----------------------------------------------------------------------------
 // device memory: RAII buffer (cudaMalloc / cudaFree)
 // ----------------------------------------------------------------------------
@@ -88,6 +108,28 @@ struct DBuf {
     ~DBuf() { release(); }
     void alloc(size_t nbytes);
     void release();
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// Stream-ordered scratch (cudaMallocAsync / cudaFreeAsync on one stream): the
+// memory is usable by work queued on that stream after the allocation and is
+// returned to the pool after the work queued before the release, so a call
+// that only needs temporary space does not synchronise.
+struct SBuf {
+    void *p = nullptr;
+    cudaStream_t s = nullptr;
+    SBuf() = default;
+    SBuf(const SBuf &) = delete;
+    SBuf &operator=(const SBuf &) = delete;
+    ~SBuf() {
+        if (p) cudaFreeAsync(p, s);
+    }
+    void alloc(size_t nbytes, cudaStream_t stream) {
+        if (p) cudaFreeAsync(p, s);
+        p = nullptr;
+        s = stream;
+        HM_CUDA_CHECK(cudaMallocAsync(&p, nbytes ? nbytes : 16, stream));
+    }
     template <class T> T *as() const { return static_cast<T *>(p); }
 };
 

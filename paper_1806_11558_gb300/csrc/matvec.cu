@@ -202,12 +202,16 @@ __global__ void tsum_kernel(int64_t na, const int32_t *__restrict__ rank, const 
 // ---------------------------------------------------------------------------
 constexpr int ROW_THREADS = 256;
 constexpr int ROW_WARPS = ROW_THREADS / 32;
-constexpr int ROW_CHUNK = 2048;  // columns staged per pass (multiple of 8)
-constexpr int RB = 4;            // rows per warp per pass: a row group is RB * ROW_WARPS rows
+constexpr int ROW_CHUNK = 4096;  // columns staged per pass (multiple of 8)
+// Rows per warp per pass (RB): a row group is RB * ROW_WARPS rows.  The host
+// picks the smallest RB whose group covers the largest leaf cluster, so the
+// gathered vector is staged once per chunk and every warp keeps RB 16-byte
+// loads in flight per step; rows past the cluster's end issue no loads.
+constexpr int row_rb_for(int max_leaf) { return max_leaf <= 32 ? 4 : max_leaf <= 40 ? 5 : max_leaf <= 64 ? 8 : 12; }
 
 // Partial sums (per lane) of rows g0 + warp + ROW_WARPS * u, u < RB, of a
 // row-major panel P (|rho| x L) times z(idx), staging z(idx) chunk by chunk.
-template <class T, class Z, class A>
+template <int RB, class T, class Z, class A>
 __device__ __forceinline__ void panel_rows(const T *__restrict__ P, int L, const int32_t *__restrict__ idx,
                                            const Z *__restrict__ z, int mr, int g0, A *s_z, A (&a)[RB]) {
     constexpr int N = V16<T>::N;
@@ -243,7 +247,7 @@ __device__ __forceinline__ void panel_rows(const T *__restrict__ P, int L, const
     }
 }
 
-template <class TD, class TF, class TX, class TT>
+template <int RB, class TD, class TF, class TX, class TT>
 __global__ void __launch_bounds__(ROW_THREADS) row_kernel(
     const int32_t *__restrict__ leaf_begin, const int64_t *__restrict__ rho_off, const int32_t *__restrict__ rho_K,
     const int64_t *__restrict__ rho_colptr, const int32_t *__restrict__ colidx, const TD *__restrict__ dense,
@@ -266,8 +270,8 @@ __global__ void __launch_bounds__(ROW_THREADS) row_kernel(
     for (int g0 = 0; g0 < mr; g0 += RB * ROW_WARPS) {
         AD ad[RB];
         AF af[RB];
-        panel_rows<TD, TX, AD>(P, Kd, ci, x, mr, g0, reinterpret_cast<AD *>(s_raw), ad);
-        panel_rows<TF, TT, AF>(Q, Ku, ti, t, mr, g0, reinterpret_cast<AF *>(s_raw), af);
+        panel_rows<RB, TD, TX, AD>(P, Kd, ci, x, mr, g0, reinterpret_cast<AD *>(s_raw), ad);
+        panel_rows<RB, TF, TT, AF>(Q, Ku, ti, t, mr, g0, reinterpret_cast<AF *>(s_raw), af);
 #pragma unroll
         for (int u = 0; u < RB; ++u) {
             const int r = g0 + warp + ROW_WARPS * u;
@@ -481,22 +485,42 @@ void build_lr_panels(hm_matrix *A, const DBuf &uw, const DBuf &uw_off, cudaStrea
     }
 }
 
+// Trace names of the three kernels of one product, per precision
+struct MvNames {
+    const char *col, *tsum, *row;
+};
+constexpr MvNames MV_F64{"col_kernel.f64", "tsum_kernel.f64", "row_kernel.f64"};
+constexpr MvNames MV_F32{"col_kernel.f32", "tsum_kernel.f32", "row_kernel.f32"};
+constexpr MvNames MV_BF16{"col_kernel.bf16", "tsum_kernel.bf16", "row_kernel.bf16"};
+
 template <class TD, class TF, class TX, class TT>
 static void matvec_impl(const hm_matrix *A, const TD *dense, const TF *up, const TF *wp, const TX *x, TT *p, TT *t,
-                        double *ym, cudaStream_t s) {
+                        double *ym, const MvNames &nm, cudaStream_t s) {
     const hm_tree *tr = A->tree;
     if (tr->n_adm > 0) {
+        Trace tr_col(nm.col, s);
         col_kernel<TF, TX, TT><<<(unsigned)tr->n_leaf, COL_THREADS, 0, s>>>(
             tr->leaf_begin.as<int32_t>(), A->wp_off.as<int64_t>(), A->wp_K.as<int32_t>(), A->wp_colptr.as<int64_t>(),
             wp, x, p);
         HM_LAUNCH_CHECK();
+    }
+    if (tr->n_adm > 0) {
+        Trace tr_tsum(nm.tsum, s);
         tsum_kernel<TT, TT><<<grid1d(tr->n_adm * 32), 256, 0, s>>>(tr->n_adm, A->rank.as<int32_t>(),
                                                                   A->t_off.as<int64_t>(),
                                                                   tr->lr_bcolptr.as<int64_t>(),
                                                                   A->pofs.as<int64_t>(), p, t);
         HM_LAUNCH_CHECK();
     }
-    row_kernel<TD, TF, TX, TT><<<(unsigned)tr->n_leaf, ROW_THREADS, 0, s>>>(
+    auto kern = row_kernel<12, TD, TF, TX, TT>;
+    switch (row_rb_for(tr->max_leaf)) {
+        case 4: kern = row_kernel<4, TD, TF, TX, TT>; break;
+        case 5: kern = row_kernel<5, TD, TF, TX, TT>; break;
+        case 8: kern = row_kernel<8, TD, TF, TX, TT>; break;
+        default: break;
+    }
+    Trace tr_row(nm.row, s);
+    kern<<<(unsigned)tr->n_leaf, ROW_THREADS, 0, s>>>(
         tr->leaf_begin.as<int32_t>(), tr->rho_off.as<int64_t>(), tr->rho_K.as<int32_t>(),
         tr->rho_colptr.as<int64_t>(), tr->colidx.as<int32_t>(), dense, A->up_off.as<int64_t>(),
         A->up_K.as<int32_t>(), A->up_colptr.as<int64_t>(), A->tidx.as<int32_t>(), up, t, x, ym);
@@ -510,7 +534,7 @@ void matvec_morton(const hm_matrix *A, hm_dtype prec, const MatvecWork &w, cudaS
     switch (prec) {
         case HM_F64:
             matvec_impl<double, double, double, double>(A, A->dense.as<double>(), A->up.as<double>(),
-                                                        A->wp.as<double>(), w.xm, w.p, w.t, w.ym, s);
+                                                        A->wp.as<double>(), w.xm, w.p, w.t, w.ym, MV_F64, s);
             break;
         case HM_F32:
         case HM_BF16:
@@ -520,12 +544,12 @@ void matvec_morton(const hm_matrix *A, hm_dtype prec, const MatvecWork &w, cudaS
             HM_LAUNCH_CHECK();
             if (prec == HM_F32)
                 matvec_impl<float, float, float, float>(A, A->dense32.as<float>(), A->up32.as<float>(),
-                                                        A->wp32.as<float>(), w.x32, w.p32, w.t32, w.ym, s);
+                                                        A->wp32.as<float>(), w.x32, w.p32, w.t32, w.ym, MV_F32, s);
             else
                 matvec_impl<float, __nv_bfloat16, float, float>(A, A->dense32.as<float>(),
                                                                 A->upbf.as<__nv_bfloat16>(),
                                                                 A->wpbf.as<__nv_bfloat16>(), w.x32, w.p32, w.t32,
-                                                                w.ym, s);
+                                                                w.ym, MV_BF16, s);
             break;
         default:
             fail(HM_EINVAL, "unknown precision %d", (int)prec);

@@ -20,9 +20,10 @@
 namespace hm {
 
 struct SingularItem {
-    int64_t off;  // arena offset of the entry
-    int32_t i;    // Morton row
-    int32_t j;    // Morton column
+    int64_t off;   // arena offset of the entry
+    int64_t off2;  // arena offset of the transposed entry that receives the same value, or -1
+    int32_t i;     // Morton row
+    int32_t j;     // Morton column
 };
 
 // ---------------------------------------------------------------------------
@@ -146,24 +147,38 @@ __global__ void __launch_bounds__(NF_THREADS) nearfield_kernel(const __grid_cons
             vr[k] = (int32_t)R[(PT_VID + k) * box_cols];
             vc[k] = (int32_t)C[(PT_VID + k) * box_cols];
         }
-        const bool touch = valid && shared_vertices(vr, vc) > 0;
-        const unsigned bal = __ballot_sync(0xffffffffu, touch);
-        if (bal) {
-            // touching pairs are evaluated in both orientations (the
-            // regularised rule depends on which panel comes first)
-            const int per = mirror ? 2 : 1;
-            const int leader = __ffs(bal) - 1;
+        const int kind = valid ? shared_vertices(vr, vc) : 0;
+        const bool touch = kind > 0;
+        // Touching pairs go to the Sauter-Schwab queue.  A common-edge pair is
+        // evaluated in both orientations: the regularised rule depends on
+        // which panel comes first, by up to ~1e-10 at n_ss = 8.  A
+        // common-vertex pair gives the same value in both orientations up to
+        // rounding (the two regions are mirror images), so it is evaluated
+        // once and stored at (i, j) and (j, i): by the upper block of a
+        // mirrored pair, or inside a diagonal block by the entry with i < j.
+        const bool diag = partner == b;
+        const bool once = kind == 1 && (mirror || diag);
+        const bool skip = once && diag && i > j;
+        const int per = !touch || skip ? 0 : (mirror && !once) ? 2 : 1;
+        const unsigned b1 = __ballot_sync(0xffffffffu, per == 1), b2 = __ballot_sync(0xffffffffu, per == 2);
+        if (b1 | b2) {
+            const int leader = __ffs(b1 | b2) - 1;
             unsigned long long slot = 0;
-            if (lane == leader) slot = atomicAdd(sing_count, (unsigned long long)(per * __popc(bal)));
+            if (lane == leader) slot = atomicAdd(sing_count, (unsigned long long)(__popc(b1) + 2 * __popc(b2)));
             slot = __shfl_sync(0xffffffffu, slot, leader);
-            if (touch) {
-                const unsigned long long k = slot + per * __popc(bal & ((1u << lane) - 1u));
+            if (per > 0) {
+                const unsigned lower = (1u << lane) - 1u;
+                const unsigned long long k = slot + __popc(b1 & lower) + 2 * __popc(b2 & lower);
                 if ((int64_t)k + per <= sing_cap) {
+                    const int64_t off_t = mirror ? par_base + (int64_t)j * par_ld + i
+                                                 : blk_base + (int64_t)j * blk_ld + i;
                     sing[k].off = blk_base + (int64_t)i * blk_ld + j;
+                    sing[k].off2 = once ? off_t : -1;
                     sing[k].i = rb + i;
                     sing[k].j = cb + j;
-                    if (mirror) {
-                        sing[k + 1].off = par_base + (int64_t)j * par_ld + i;
+                    if (per == 2) {
+                        sing[k + 1].off = off_t;
+                        sing[k + 1].off2 = -1;
                         sing[k + 1].i = cb + j;
                         sing[k + 1].j = rb + i;
                     }
@@ -255,7 +270,9 @@ __global__ void singular_kernel(const SingularItem *__restrict__ items, int64_t 
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) {
         const double ai = pt[(int64_t)PT_AREA * npad + it.i], aj = pt[(int64_t)PT_AREA * npad + it.j];
-        arena[it.off] = 4.0 * ai * aj * (s / 3.0) * INV_4PI;
+        const double a = 4.0 * ai * aj * (s / 3.0) * INV_4PI;
+        arena[it.off] = a;
+        if (it.off2 >= 0) arena[it.off2] = a;
     }
 }
 
@@ -279,6 +296,7 @@ void assemble_nearfield(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, c
     HM_CUDA_CHECK(cudaEventCreate(&e2));
     HM_CUDA_CHECK(cudaEventRecord(e0, s));
     if (tr->n_dense > 0) {
+        Trace trace("nearfield_kernel", s);
         nearfield_kernel<<<(unsigned)tr->n_dense, NF_THREADS, smem, s>>>(
             tr->pt_map, tr->dense.as<int32_t>(), tr->dense_base.as<int64_t>(), tr->dense_ld.as<int32_t>(),
             tr->dense_tp.as<int32_t>(), tr->box_cols, qp, A->dense.as<double>(), items.as<SingularItem>(), cnt.as<unsigned long long>(),
@@ -292,6 +310,7 @@ void assemble_nearfield(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, c
     const_cast<hm_tree *>(tr)->n_singular = nsing;
     if (nsing > 0) {
         const int64_t threads = nsing * 32;
+        Trace trace("singular_kernel", s);
         singular_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
             items.as<SingularItem>(), nsing, tr->trim.as<int32_t>(), tr->V.as<double>(), tr->pt.as<double>(),
             tr->npad, qp, A->dense.as<double>());

@@ -22,6 +22,78 @@ static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
+// ----------------------------------------------------------------------------
+// kernel timing trace
+// ----------------------------------------------------------------------------
+namespace {
+struct TraceRec {
+    const char *name;
+    cudaEvent_t a, b;
+};
+std::mutex g_trace_mu;
+std::atomic<bool> g_trace_on{false};
+std::vector<TraceRec> g_trace_recs;
+std::vector<cudaEvent_t> g_trace_pool;
+
+cudaEvent_t trace_event() {  // caller holds g_trace_mu
+    if (!g_trace_pool.empty()) {
+        cudaEvent_t e = g_trace_pool.back();
+        g_trace_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    HM_CUDA_CHECK(cudaEventCreate(&e));
+    return e;
+}
+}  // namespace
+
+Trace::Trace(const char *name, cudaStream_t stream) : s(stream) {
+    if (!g_trace_on.load(std::memory_order_relaxed)) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    HM_CUDA_CHECK(cudaStreamIsCapturing(stream, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return;
+    std::lock_guard<std::mutex> lk(g_trace_mu);
+    TraceRec r{name, trace_event(), trace_event()};
+    HM_CUDA_CHECK(cudaEventRecord(r.a, stream));
+    slot = (int)g_trace_recs.size();
+    g_trace_recs.push_back(r);
+}
+
+Trace::~Trace() {
+    if (slot < 0) return;
+    std::lock_guard<std::mutex> lk(g_trace_mu);
+    if (slot < (int)g_trace_recs.size()) cudaEventRecord(g_trace_recs[slot].b, s);
+}
+
+void trace_enable(bool on) {
+    std::lock_guard<std::mutex> lk(g_trace_mu);
+    if (on) {
+        for (auto &r : g_trace_recs) {
+            HM_CUDA_CHECK(cudaEventSynchronize(r.b));
+            g_trace_pool.push_back(r.a);
+            g_trace_pool.push_back(r.b);
+        }
+        g_trace_recs.clear();
+    }
+    g_trace_on.store(on);
+}
+
+std::vector<TraceTotal> trace_read() {
+    std::lock_guard<std::mutex> lk(g_trace_mu);
+    std::vector<TraceTotal> out;
+    for (auto &r : g_trace_recs) {
+        HM_CUDA_CHECK(cudaEventSynchronize(r.b));
+        float ms = 0.0f;
+        HM_CUDA_CHECK(cudaEventElapsedTime(&ms, r.a, r.b));
+        size_t k = 0;
+        while (k < out.size() && out[k].name != r.name) ++k;
+        if (k == out.size()) out.push_back(TraceTotal{r.name, 0, 0.0});
+        out[k].launches += 1;
+        out[k].ms += ms;
+    }
+    return out;
+}
+
 void fail(hm_status s, const char *fmt, ...) {
     char buf[1024];
     va_list ap;

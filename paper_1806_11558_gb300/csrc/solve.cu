@@ -20,13 +20,13 @@ void matvec_morton(const hm_matrix *A, hm_dtype prec, const MatvecWork &w, cudaS
 int64_t matvec_work_doubles(const hm_matrix *A);
 MatvecWork matvec_work_at(const hm_matrix *A, double *base);
 
-// y = op(H) x in Morton order through the solver's workspace (x, y may be any vectors)
+// y = op(H) x in Morton order (x and y distinct vectors of the solver); the
+// projections live in the solver's workspace
 static void apply(const hm_matrix *A, hm_dtype prec, const double *x, double *y, DBuf &work, cudaStream_t s) {
     MatvecWork w = matvec_work_at(A, work.as<double>());
-    const int64_t n = A->tree->n;
-    HM_CUDA_CHECK(cudaMemcpyAsync(w.xm, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    w.xm = const_cast<double *>(x);
+    w.ym = y;
     matvec_morton(A, prec, w, s);
-    HM_CUDA_CHECK(cudaMemcpyAsync(y, w.ym, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
 }
 
 constexpr int DOT_THREADS = 256;
@@ -262,6 +262,7 @@ static void bj_setup(const hm_matrix *Ac, cudaStream_t s) {
 
 static void bj_apply(const hm_matrix *A, const double *v, double *z, cudaStream_t s) {
     const hm_tree *tr = A->tree;
+    Trace trace("bj_apply_kernel", s);
     bj_apply_kernel<<<(unsigned)tr->n_leaf, 128, 0, s>>>(tr->leaf_begin.as<int32_t>(), A->bj_off.as<int64_t>(),
                                                         A->bj.as<double>(), v, z);
     HM_LAUNCH_CHECK();
@@ -292,6 +293,7 @@ struct Gmres {
     }
     // out[0..nv) = V_l . w (accumulate adds to out)
     void dots(const double *Vb, int nv, const double *wv, double *out, int accumulate, cudaStream_t s) {
+        Trace trace("gmres_dots", s);
         dots_partial_kernel<<<nblk, DOT_THREADS, 0, s>>>(Vb, n, nv, wv, n, part.as<double>());
         HM_LAUNCH_CHECK();
         dots_final_kernel<<<1, std::max(32, ((nv + 31) / 32) * 32), 0, s>>>(part.as<double>(), nblk, nv, out,
@@ -348,11 +350,17 @@ static hm_status gmres(const hm_matrix *A, hm_dtype prec, const double *b, doubl
             }
             // CGS2
             G.dots(V, j + 1, w, G.h.as<double>(), 0, s);
-            sub_combo_kernel<<<g1(n), 256, 0, s>>>(V, n, j + 1, G.h.as<double>(), n, w);
-            HM_LAUNCH_CHECK();
+            {
+                Trace trace("gmres_sub_combo", s);
+                sub_combo_kernel<<<g1(n), 256, 0, s>>>(V, n, j + 1, G.h.as<double>(), n, w);
+                HM_LAUNCH_CHECK();
+            }
             G.dots(V, j + 1, w, G.y.as<double>(), 0, s);
-            sub_combo_kernel<<<g1(n), 256, 0, s>>>(V, n, j + 1, G.y.as<double>(), n, w);
-            HM_LAUNCH_CHECK();
+            {
+                Trace trace("gmres_sub_combo", s);
+                sub_combo_kernel<<<g1(n), 256, 0, s>>>(V, n, j + 1, G.y.as<double>(), n, w);
+                HM_LAUNCH_CHECK();
+            }
             // h += h2 (second pass coefficients) : reuse dots_final with accumulate
             {
                 // h[l] += y[l]
