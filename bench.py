@@ -29,7 +29,7 @@ sys.path.insert(0, ROOT)
 WORKLOAD = dict(workload="bumped icosphere level 7, Galerkin single-layer Laplace, P0",
                 panels=327680, leaf_size=64, eta=1.5, aca_eps=1e-7, aca_kmax=64, ss_order=8,
                 source=[3.0, 0.0, 0.0], solve_rel_tol=1e-12, inner="fp32 factors + fp32 near field",
-                inner_tol=1e-4, restart=int(os.environ.get("HM_BENCH_RESTART", "60")), precond=os.environ.get("HM_BENCH_PRECOND", "1") == "1")
+                inner_tol=1e-4, restart=int(os.environ.get("HM_BENCH_RESTART", "128")), precond=os.environ.get("HM_BENCH_PRECOND", "1") == "1")
 METRIC = "H-matrix setup s, H-matvec GB/s, solve s at 1e-8 rel. accuracy: mixed vs FP64"
 FLOPS_PER_PAIR = 11  # 3 sub + 3 mul + 2 add (|x-y|^2) + rsqrt + multiply-add (weight)
 PAIRS_PER_ENTRY = 49
@@ -291,13 +291,17 @@ def run_ours(args, rank, world):
     xbf = torch.zeros_like(x64)
     b0 = torch.cuda.Event(enable_timing=True)
     b1 = torch.cuda.Event(enable_timing=True)
+    hm.hm_trace_enable(True)
     b0.record(stream)
     ibf = hm.hm_solve(A16, f[0], xbf, rel_tol=W["solve_rel_tol"], restart=W["restart"], max_iter=5000, refine=1,
                       inner_tol=1e-2, inner_dtype=hm.HM_BF16, max_refine=80, raise_on_noconv=False,
                       precond=int(W["precond"]))
     b1.record(stream)
     torch.cuda.synchronize()
-    bf16 = {"solve_s": b0.elapsed_time(b1) / 1e3, "err_vs_fp64": float(torch.linalg.norm(xbf - x64) /
+    hm.hm_trace_enable(False)
+    bf16_kernels = kernel_table(hm.hm_trace_read(), 1)
+    bf16 = {"kernels": {k: v for k, v in bf16_kernels.items() if v["share_of_traced"] > 0.01},
+            "solve_s": b0.elapsed_time(b1) / 1e3, "err_vs_fp64": float(torch.linalg.norm(xbf - x64) /
                                                                         torch.linalg.norm(x64)),
             "iters": ibf.iters, "refine_steps": ibf.refine_steps, "rel_resid": ibf.rel_resid}
     hm.hm_free(A16)

@@ -10,7 +10,8 @@
 //   column pivot j_r = argmax_{unused j} |~u_j| (lowest j on ties),
 //   delta = ~u(j_r); a zero row (delta == 0 at r = 1, |delta| <= 2^-50 |delta_1|
 //   later) is marked used and replaced by the lowest unused row;
-//   W(:, r) = ~u / delta, U(:, r) = B(:, j_r) - sum_l W(j_r, l) U(:, l);
+//   W(:, r) = ~u / delta (as ~u times the reciprocal of delta),
+//   U(:, r) = B(:, j_r) - sum_l W(j_r, l) U(:, l);
 //   ||S_r||^2 += 2 sum_{l<r} (u_r.u_l)(w_l.w_r) + ||u_r||^2 ||w_r||^2;
 //   stop when ||u_r|| ||w_r|| <= eps ||S_r|| or r = min(m, n, kmax);
 //   next row i_{r+1} = argmax_{unused i} |u_r(i)|.
@@ -284,8 +285,9 @@ __device__ int aca_block(const AcaArgs &A, int rb, int m, int cb, int n, double 
         }
         if (r == 0) delta1 = fabs(delta);
         const int jp = best.idx;
+        const double inv_delta = 1.0 / delta;
         for (int j = t; j < n; j += gs) {
-            const double w = W[(int64_t)r * n + j] / delta;
+            const double w = W[(int64_t)r * n + j] * inv_delta;
             W[(int64_t)r * n + j] = w;
             Wf[(int64_t)r * n + j] = (float)w;
         }

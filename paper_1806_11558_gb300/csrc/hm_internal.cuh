@@ -273,6 +273,7 @@ struct hm_matrix {
     hm::DBuf wp_colptr; // [n_leaf + 1] int64, into the partial-projection vector
     hm::DBuf wp_koff;   // [lr_collist size] int32, first panel column of each (kappa, block) pair
     hm::DBuf pofs;      // [sum over blocks of column leaf clusters] int64: partial offsets per block
+    hm::DBuf tsum_b0;   // [ceil(total_rank / 32)] int32: block holding t entry 32 c
     int64_t wp_entries = 0;
     int64_t n_partials = 0;  // length of the partial-projection vector
     // block-Jacobi preconditioner: inverse of each leaf cluster's diagonal block

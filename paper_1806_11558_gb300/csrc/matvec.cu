@@ -175,21 +175,69 @@ __global__ void __launch_bounds__(COL_THREADS) col_kernel(const int32_t *__restr
     }
 }
 
+// t_b(l) = sum over the column clusters of sigma_b of the partials, in
+// increasing cluster order.  One warp per 32 consecutive entries of t
+// (coalesced stores, every lane busy whatever the ranks): b0[c] is the block
+// holding entry 32 c, the lanes load the offsets t_off of the 32 blocks from
+// there and each entry finds its block by a 5-step search over them (an
+// entry the window does not reach, possible only after blocks of rank 0,
+// searches t_off itself); the partial loads of one entry are independent
+// (four accumulators, added in a fixed order).
 template <class TP, class TT>
-__global__ void tsum_kernel(int64_t na, const int32_t *__restrict__ rank, const int64_t *__restrict__ t_off,
-                            const int64_t *__restrict__ bcolptr, const int64_t *__restrict__ pofs,
-                            const TP *__restrict__ p, TT *__restrict__ t) {
+__global__ void __launch_bounds__(256) tsum_kernel(int64_t na, int64_t nt, const int32_t *__restrict__ b0tab,
+                                                   const int64_t *__restrict__ t_off,
+                                                   const int64_t *__restrict__ bcolptr,
+                                                   const int64_t *__restrict__ pofs, const TP *__restrict__ p,
+                                                   TT *__restrict__ t) {
+    const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t b = w0; b < na; b += nw) {
-        const int k = rank[b];
-        const int64_t q0 = bcolptr[b], q1 = bcolptr[b + 1];
-        for (int l = lane; l < k; l += 32) {
-            TP acc = 0;
-            for (int64_t q = q0; q < q1; ++q) acc += p[pofs[q] + l];
-            t[t_off[b] + l] = (TT)acc;
+    const int64_t nchunk = (nt + 31) / 32;
+    for (int64_t c = w0; c < nchunk; c += nw) {
+        const int64_t b0 = b0tab[c];
+        const int64_t bl = min(b0 + lane, na);
+        const int64_t to = t_off[bl];  // t_off has na + 1 entries
+        const int64_t e = c * 32 + lane;
+        int j = 0;
+#pragma unroll
+        for (int st = 16; st > 0; st >>= 1) {
+            const int64_t tj = __shfl_sync(full, to, j + st);
+            if (tj <= e) j += st;
         }
+        const int64_t to31 = __shfl_sync(full, to, 31);
+        if (e >= nt) continue;
+        int64_t b = b0 + j;
+        if (to31 <= e && b0 + 31 < na) {
+            // beyond the window: last block with t_off <= e
+            int64_t lo = b0 + 31, hi = na;
+            while (hi - lo > 1) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (t_off[mid] <= e) lo = mid;
+                else hi = mid;
+            }
+            b = lo;
+        }
+        const int l = (int)(e - t_off[b]);
+        const int64_t qa = bcolptr[b], qb = bcolptr[b + 1];
+        TP a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        int64_t q = qa;
+        for (; q + 3 < qb; q += 4) {
+            a0 += p[pofs[q] + l];
+            a1 += p[pofs[q + 1] + l];
+            a2 += p[pofs[q + 2] + l];
+            a3 += p[pofs[q + 3] + l];
+        }
+        for (; q < qb; ++q) a0 += p[pofs[q] + l];
+        t[e] = (TT)((a0 + a1) + (a2 + a3));
+    }
+}
+
+// b0[c] = the block whose t range holds entry 32 c
+__global__ void tsum_b0_kernel(int64_t na, const int64_t *__restrict__ t_off, int32_t *__restrict__ b0) {
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < na; b += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t lo = t_off[b], hi = t_off[b + 1];
+        for (int64_t c = (lo + 31) / 32; c * 32 < hi; ++c) b0[c] = (int32_t)b;
     }
 }
 
@@ -482,6 +530,11 @@ void build_lr_panels(hm_matrix *A, const DBuf &uw, const DBuf &uw_off, cudaStrea
                                               A->wp_colptr.as<int64_t>(), A->wp_koff.as<int32_t>(),
                                               tr->lr_bcolptr.as<int64_t>(), A->pofs.as<int64_t>());
         HM_LAUNCH_CHECK();
+        A->tsum_b0.alloc(sizeof(int32_t) * std::max<int64_t>((A->total_rank + 31) / 32, 1));
+        if (A->total_rank > 0) {
+            tsum_b0_kernel<<<grid1d(na), 256, 0, s>>>(na, A->t_off.as<int64_t>(), A->tsum_b0.as<int32_t>());
+            HM_LAUNCH_CHECK();
+        }
     }
 }
 
@@ -506,10 +559,9 @@ static void matvec_impl(const hm_matrix *A, const TD *dense, const TF *up, const
     }
     if (tr->n_adm > 0) {
         Trace tr_tsum(nm.tsum, s);
-        tsum_kernel<TT, TT><<<grid1d(tr->n_adm * 32), 256, 0, s>>>(tr->n_adm, A->rank.as<int32_t>(),
-                                                                  A->t_off.as<int64_t>(),
-                                                                  tr->lr_bcolptr.as<int64_t>(),
-                                                                  A->pofs.as<int64_t>(), p, t);
+        tsum_kernel<TT, TT><<<grid1d((A->total_rank + 31) / 32 * 32), 256, 0, s>>>(
+            tr->n_adm, A->total_rank, A->tsum_b0.as<int32_t>(), A->t_off.as<int64_t>(),
+            tr->lr_bcolptr.as<int64_t>(), A->pofs.as<int64_t>(), p, t);
         HM_LAUNCH_CHECK();
     }
     auto kern = row_kernel<12, TD, TF, TX, TT>;

@@ -32,11 +32,16 @@ static void apply(const hm_matrix *A, hm_dtype prec, const double *x, double *y,
 constexpr int DOT_THREADS = 256;
 constexpr int DOT_CHUNK = 8;  // vectors per register pass
 
-// part[blk][l] = sum over this block's elements of V_l . w  (l < nv)
-__global__ void __launch_bounds__(DOT_THREADS) dots_partial_kernel(const double *__restrict__ V, int64_t ld, int nv,
-                                                                    const double *__restrict__ w, int64_t n,
-                                                                    double *__restrict__ part) {
+// out[l] = V_l . w for l < nv (+ out[l] when accumulate), one launch: every
+// block writes its partial sums part[blk][l]; the block that finishes last
+// (a ticket counter, reset by it for the next call) adds the partials of
+// each l in a fixed order (lanes over blocks, then a fixed shuffle tree).
+__global__ void __launch_bounds__(DOT_THREADS) dots_kernel(const double *__restrict__ V, int64_t ld, int nv,
+                                                            const double *__restrict__ w, int64_t n,
+                                                            double *__restrict__ part, double *__restrict__ out,
+                                                            int accumulate, unsigned int *ticket) {
     __shared__ double s[DOT_THREADS / 32][DOT_CHUNK];
+    __shared__ bool s_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t per = (n + gridDim.x - 1) / gridDim.x;
     const int64_t i0 = (int64_t)blockIdx.x * per, i1 = min(n, i0 + per);
@@ -64,15 +69,19 @@ __global__ void __launch_bounds__(DOT_THREADS) dots_partial_kernel(const double 
         }
         __syncthreads();
     }
-}
-
-// out[l] = sum_blk part[blk][l] (+ out[l] when accumulate)
-__global__ void dots_final_kernel(const double *part, int nblk, int nv, double *out, int accumulate) {
-    const int l = threadIdx.x;
-    if (l >= nv) return;
-    double t = 0.0;
-    for (int b = 0; b < nblk; ++b) t += part[(int64_t)b * nv + l];
-    out[l] = accumulate ? out[l] + t : t;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int l = warp; l < nv; l += DOT_THREADS / 32) {
+        double t = 0.0;
+        for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(part + (int64_t)b * nv + l);
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) out[l] = accumulate ? out[l] + t : t;
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
 }
 
 // w -= sum_l V_l h_l
@@ -219,20 +228,33 @@ __global__ void bj_invert_kernel(const int32_t *leaf_begin, const int64_t *bj_of
             if (i != p) D[i * m + p] = -D[i * m + p] * D[p * m + p];
         __syncthreads();
     }
+    // store the inverse transposed (column-major), as bj_apply_kernel reads it
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+        const int i = e / m, j = e - (e / m) * m;
+        if (i < j) {
+            const double t = D[i * m + j];
+            D[i * m + j] = D[j * m + i];
+            D[j * m + i] = t;
+        }
+    }
 }
 
-// z_rho = D_rho^{-1} v_rho, one warp per row
-__global__ void bj_apply_kernel(const int32_t *leaf_begin, const int64_t *bj_off, const double *bj, const double *v,
-                                double *z) {
+// z_rho = D_rho^{-1} v_rho: one thread per row over the column-major inverse
+// (consecutive threads read consecutive rows of one column), v_rho staged in
+// shared memory; each row sums its columns in order.
+constexpr int BJ_THREADS = 64;
+__global__ void __launch_bounds__(BJ_THREADS) bj_apply_kernel(const int32_t *leaf_begin, const int64_t *bj_off,
+                                                              const double *bj, const double *v, double *z) {
+    __shared__ double s_v[MAX_LEAF];
     const int64_t r = blockIdx.x;
     const int32_t r0 = leaf_begin[r], m = leaf_begin[r + 1] - r0;
     const double *D = bj + bj_off[r];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int i = warp; i < m; i += nw) {
+    for (int j = threadIdx.x; j < m; j += BJ_THREADS) s_v[j] = v[r0 + j];
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += BJ_THREADS) {
         double acc = 0.0;
-        for (int j = lane; j < m; j += 32) acc += D[i * m + j] * v[r0 + j];
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) z[r0 + i] = acc;
+        for (int j = 0; j < m; ++j) acc = fma(D[(int64_t)j * m + i], s_v[j], acc);
+        z[r0 + i] = acc;
     }
 }
 
@@ -263,7 +285,7 @@ static void bj_setup(const hm_matrix *Ac, cudaStream_t s) {
 static void bj_apply(const hm_matrix *A, const double *v, double *z, cudaStream_t s) {
     const hm_tree *tr = A->tree;
     Trace trace("bj_apply_kernel", s);
-    bj_apply_kernel<<<(unsigned)tr->n_leaf, 128, 0, s>>>(tr->leaf_begin.as<int32_t>(), A->bj_off.as<int64_t>(),
+    bj_apply_kernel<<<(unsigned)tr->n_leaf, BJ_THREADS, 0, s>>>(tr->leaf_begin.as<int32_t>(), A->bj_off.as<int64_t>(),
                                                         A->bj.as<double>(), v, z);
     HM_LAUNCH_CHECK();
 }
@@ -272,8 +294,8 @@ struct Gmres {
     int64_t n;
     int m;
     int nblk;
-    DBuf V, w, ax, part, h, H, cs, sn, g, y, est, t, nrm, z, d;
-    Gmres(int64_t n_, int m_, int64_t work_doubles) : n(n_), m(m_) {
+    DBuf V, w, ax, part, h, H, cs, sn, g, y, est, t, nrm, z, d, ticket;
+    Gmres(int64_t n_, int m_, int64_t work_doubles, cudaStream_t s) : n(n_), m(m_) {
         nblk = std::max(1, std::min<int>(4 * num_sms(), (int)((n + 1023) / 1024)));
         V.alloc(sizeof(double) * (int64_t)(m + 1) * n);
         w.alloc(sizeof(double) * n);
@@ -290,14 +312,14 @@ struct Gmres {
         z.alloc(sizeof(double) * n);
         d.alloc(sizeof(double) * n);
         nrm.alloc(sizeof(double) * 2);
+        ticket.alloc(sizeof(unsigned int));
+        HM_CUDA_CHECK(cudaMemsetAsync(ticket.p, 0, sizeof(unsigned int), s));
     }
     // out[0..nv) = V_l . w (accumulate adds to out)
     void dots(const double *Vb, int nv, const double *wv, double *out, int accumulate, cudaStream_t s) {
         Trace trace("gmres_dots", s);
-        dots_partial_kernel<<<nblk, DOT_THREADS, 0, s>>>(Vb, n, nv, wv, n, part.as<double>());
-        HM_LAUNCH_CHECK();
-        dots_final_kernel<<<1, std::max(32, ((nv + 31) / 32) * 32), 0, s>>>(part.as<double>(), nblk, nv, out,
-                                                                             accumulate);
+        dots_kernel<<<nblk, DOT_THREADS, 0, s>>>(Vb, n, nv, wv, n, part.as<double>(), out, accumulate,
+                                                 ticket.as<unsigned int>());
         HM_LAUNCH_CHECK();
     }
     double norm2_host(const double *v, cudaStream_t s) {
@@ -361,7 +383,7 @@ static hm_status gmres(const hm_matrix *A, hm_dtype prec, const double *b, doubl
                 sub_combo_kernel<<<g1(n), 256, 0, s>>>(V, n, j + 1, G.y.as<double>(), n, w);
                 HM_LAUNCH_CHECK();
             }
-            // h += h2 (second pass coefficients) : reuse dots_final with accumulate
+            // h += h2 (second pass coefficients)
             {
                 // h[l] += y[l]
                 axpy_kernel<<<1, 128, 0, s>>>(1.0, G.y.as<double>(), j + 1, G.h.as<double>());
@@ -420,7 +442,7 @@ hm_status solve_impl(const hm_matrix *A, const double *b_orig, double *x_orig, c
     x.alloc(sizeof(double) * n);
     permute_to_morton(tr, b_orig, b.as<double>(), s);
     HM_CUDA_CHECK(cudaMemsetAsync(x.p, 0, sizeof(double) * n, s));
-    Gmres G(n, p.restart, matvec_work_doubles(A));
+    Gmres G(n, p.restart, matvec_work_doubles(A), s);
     const bool pc = p.precond == 1;
     if (pc) bj_setup(A, s);
     int iters = 0, cycles = 0, steps = 0;
