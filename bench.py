@@ -384,7 +384,7 @@ def cpu_oracle_step(V, T, budget_s=20.0, iters=None, seed=0):
     quad = oracle.Quad(W["ss_order"])
     # near field: a random sample of dense leaves
     nd = len(tr.dense)
-    sd = rng.choice(nd, size=min(nd, 6000), replace=False)
+    sd = rng.choice(nd, size=min(nd, 60000), replace=False)
     t0 = time.perf_counter()
     blocks = []
     for b in sd:
@@ -393,7 +393,7 @@ def cpu_oracle_step(V, T, budget_s=20.0, iters=None, seed=0):
     t_nf = (time.perf_counter() - t0) * nd / len(sd)
     # ACA: a random sample of admissible leaves
     na = len(tr.adm)
-    sa = rng.choice(na, size=min(na, 8000), replace=False)
+    sa = rng.choice(na, size=min(na, 100000), replace=False)
     t0 = time.perf_counter()
     fac = oracle.aca_blocks(tr.V, tr.T, tr.perm, tr.adm[sa], W["aca_eps"], W["aca_kmax"], quad)
     t_aca = (time.perf_counter() - t0) * na / len(sa)
