@@ -198,6 +198,20 @@ HM_API hm_status hm_assemble(const hm_tree *tree, const hm_assemble_params *para
 HM_API hm_status hm_load_vector(const hm_tree *tree, const double *d_sources, int32_t n_sources, double *d_f,
                          hm_stream_t stream);
 
+/* Single-layer potential of a piecewise-constant density at points off the
+ * surface: the ansatz U(x) = int_Gamma u(y) / (4 pi |x - y|) dsigma_y of
+ * Sec. 2.1, which Sec. 4.3 evaluates at interior points to measure the
+ * error; 7-point rule on every panel (the points must not lie on the
+ * surface: no singular treatment).
+ *  trans = 0: d_out[k] = sum_j |T_j| sum_q w_q G(p_k, y_q^j) d_in[j]
+ *             (d_in: [n] density, original panel order; d_out: [n_points]);
+ *  trans = 1: d_out[j] = |T_j| sum_q w_q sum_k G(p_k, y_q^j) d_in[k], the
+ *             adjoint (d_in: [n_points]; d_out: [n], original order).
+ *  d_points : [n_points][3] doubles (device).  All pointers device,
+ *  caller-owned.  Errors: HM_EINVAL for NULL pointers or n_points < 0. */
+HM_API hm_status hm_potential(const hm_tree *tree, const double *d_points, int64_t n_points, int32_t trans,
+                              const double *d_in, double *d_out, hm_stream_t stream);
+
 /* H-matrix-vector product (Sec. 2.3): y = alpha * op(H) x + beta * y, with
  * op(H) = H (trans = 0) or H^T (trans = 1), applied column by column to nrhs
  * right-hand sides stored as [nrhs][n] (original panel order).
@@ -205,6 +219,10 @@ HM_API hm_status hm_load_vector(const hm_tree *tree, const double *d_sources, in
  *         low-precision copies (FP32 accumulation; they must have been
  *         requested in hm_assemble).
  *  d_x, d_y : device pointers, must not overlap.
+ *  trans = 1 applies the stored H transposed, as the adjoint of the product
+ *  (U and W exchange roles, the near field is read transposed); the first
+ *  transposed call on a matrix builds and keeps the transposed near field
+ *  (one more copy of it) and its index maps, synchronising the stream once.
  *  Stream-ordered: the call queues the work on `stream` and returns; its
  *  working vectors come from the stream-ordered pool (cudaMallocAsync).
  *  Errors: HM_EINVAL for NULL pointers, nrhs < 1, a precision whose copy was
@@ -243,6 +261,9 @@ HM_API hm_status hm_matvec_noalloc(const hm_matrix *A, int32_t trans, int32_t nr
  *  d_b : [nrhs][n] right-hand sides (device, original order).
  *  d_x : [nrhs][n] solutions (device); the initial guess is zero.
  *  info: host pointer, may be NULL; filled for the last right-hand side.
+ *  trans = 1 solves H^T x = b (the adjoint system of a gradient), with the
+ *  transposed product of hm_matvec and, when precond = 1, the transposed
+ *  block-Jacobi inverses.
  *  Returns HM_ENOCONV (with the best x stored) when max_iter is reached. */
 HM_API hm_status hm_solve(const hm_matrix *A, int32_t trans, int32_t nrhs, const double *d_b, double *d_x,
                    const hm_solve_params *params, hm_stream_t stream, hm_solve_info *info);

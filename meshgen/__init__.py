@@ -204,8 +204,19 @@ def config(name: str):
     small      : unit icosphere level 4 (5,120 panels), source p = (3,0,0)
     precision  : bumped icosphere level 7 (327,680 panels), 8 harmonics, p = (3,0,0)
     large      : unit icosphere level 8 (1,310,720 panels), 16 sources |p| in [2,4]
+    differentiation / differentiation<L> :
+                 unit icosphere level 6 (or L), Dirichlet data from p = (3,0,0),
+                 1,024 evaluation points on the sphere of radius 2.5
+                 (normalised Gaussian directions) and the target field of a
+                 point source at (0,0,3) there
     level<L>   : unit icosphere of level L with p = (3,0,0) (parity ladders)
     """
+    if name.startswith("differentiation"):
+        L = int(name[len("differentiation"):] or 6)
+        V, T = icosphere(L)
+        pts = exterior_points(MASTER_SEED + 4, 1024, 2.5)
+        return dict(V=V, T=T, sources=np.array([[3.0, 0.0, 0.0]]), leaf_size=64, eta=1.5, aca_eps=1e-6,
+                    points=pts, target_source=np.array([0.0, 0.0, 3.0]))
     if name == "small":
         V, T = icosphere(4)
         return dict(V=V, T=T, sources=np.array([[3.0, 0.0, 0.0]]), leaf_size=64, eta=1.5, aca_eps=1e-6)

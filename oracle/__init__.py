@@ -87,6 +87,8 @@ def _L():
             lib.orc_load_vector.argtypes = [P, P, I64, P, P, I64, P, P]
             lib.orc_potential.restype = None
             lib.orc_potential.argtypes = [P, P, I64, P, P, P, I64, P, P]
+            lib.orc_potential_matrix.restype = None
+            lib.orc_potential_matrix.argtypes = [P, P, I64, P, P, I64, P, P]
             lib.orc_admissible.restype = I
             lib.orc_admissible.argtypes = [P, P, P, P, D]
             lib.orc_block_tree.restype = I
@@ -293,6 +295,18 @@ def dense_matrix(V, T, quad: Quad | None = None):
     n = np.asarray(T).shape[0]
     idx = np.arange(n, dtype=np.int64)
     return assemble(V, T, idx, idx, quad)
+
+
+def potential_matrix(V, T, pts, quad: Quad | None = None):
+    """E with (S~ u_h)(p_k) = sum_j E[k, j] alpha_j (Sec. 2.1, single-layer
+    potential ansatz), 7-point rule on every panel; [n_points, n]."""
+    quad = quad or Quad()
+    V = _f64(V)
+    T = _i32(T)
+    pts = _f64(np.asarray(pts).reshape(-1, 3))
+    E = np.empty((pts.shape[0], T.shape[0]))
+    _L().orc_potential_matrix(_p(V), _p(T), T.shape[0], _p(quad.bary), _p(quad.w7), pts.shape[0], _p(pts), _p(E))
+    return E
 
 
 def ss_points(kind: int, xi, e1, e2, e3):
@@ -530,3 +544,30 @@ def point_source_potential(x, p):
     """U(x) = 1/(4 pi |x - p|), the exact interior solution."""
     x = _f64(np.asarray(x).reshape(-1, 3))
     return 1.0 / (4.0 * math.pi * np.linalg.norm(x - _f64(p)[None, :], axis=1))
+
+
+# --------------------------------------------------------------------------
+# Differentiation of a potential misfit through the solve (adjoint method)
+# --------------------------------------------------------------------------
+def misfit_loss_and_gradients(A, E, f, c, target):
+    """Dense FP64 statement of the differentiated problem.
+
+    The density alpha solves A diag(c) alpha = f (per-panel scaling c of the
+    density, c = 1 at the base point), the potential at the evaluation points
+    is Phi = E alpha, and the loss is L = mean_k (Phi_k - target_k)^2.  With
+    g = dL/dalpha = (2/K) E^T (Phi - target), the adjoint lam solves
+    (A diag(c))^T lam = g, and
+        dL/df = lam,      dL/dc_j = -alpha_j (A^T lam)_j.
+    Returns (L, alpha, dL/df, dL/dc).  Solves by LAPACK LU."""
+    A = _f64(A)
+    E = _f64(E)
+    f = _f64(f)
+    c = _f64(c)
+    target = _f64(target)
+    Ac = A * c[None, :]
+    alpha = lu_solve(Ac, f)
+    r = E @ alpha - target
+    L = float(np.mean(r * r))
+    g = (2.0 / r.shape[0]) * (E.T @ r)
+    lam = lu_solve(Ac.T.copy(), g)
+    return L, alpha, lam, -alpha * (A.T @ lam)

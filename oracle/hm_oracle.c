@@ -323,6 +323,27 @@ void orc_potential(const double *V, const int32_t *T, int64_t n, const double *a
     }
 }
 
+/* E[k][j] = |T_j| sum_q w_q / (4 pi |p_k - y_q^j|): the single-layer potential
+ * of Sec. 2.1 at point p_k of the j-th basis function (indicator of T_j), so
+ * that (S~ u_h)(p_k) = sum_j E[k][j] alpha_j.  Row-major [npts][n]. */
+void orc_potential_matrix(const double *V, const int32_t *T, int64_t n, const double *bary, const double *w7,
+                          int64_t npts, const double *pts, double *E)
+{
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < npts; ++k) {
+        for (int64_t j = 0; j < n; ++j) {
+            double y[NQ][3], d[3];
+            quad_points(V, T, j, bary, y);
+            double s = 0.0;
+            for (int q = 0; q < NQ; ++q) {
+                vsub(pts + 3 * k, y[q], d);
+                s += w7[q] / vnorm(d);
+            }
+            E[k * n + j] = tri_area(vtx(V, T, j, 0), vtx(V, T, j, 1), vtx(V, T, j, 2)) * s / (4.0 * M_PI);
+        }
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Block cluster tree: Algorithm 1 with the admissibility condition Eq. 5     */
 /* ------------------------------------------------------------------------ */

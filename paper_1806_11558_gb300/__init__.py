@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "HM_OK", 1: "HM_EINVAL", 2: "HM_ENOMEM", 3: "HM_ECUDA", 4: "H
 EXPORTED = ["hm_build_tree", "hm_assemble", "hm_load_vector", "hm_matvec", "hm_solve", "hm_free",
             "hm_tree_get_info", "hm_tree_get_perm", "hm_tree_get_leaves", "hm_matrix_get_info",
             "hm_matrix_export", "hm_last_error", "hm_kernel_launches", "hm_matvec_noalloc", "hm_matrix_get_block",
-            "hm_trace_enable", "hm_trace_read"]
+            "hm_trace_enable", "hm_trace_read", "hm_potential"]
 
 
 class HMError(RuntimeError):
@@ -101,6 +101,7 @@ def lib():
             "hm_matrix_export": [P, P, P, P, P, P, P, P, P],
             "hm_matrix_get_block": [P, I32, I64, P, P],
             "hm_trace_enable": [I32],
+            "hm_potential": [P, P, I64, I32, P, P, P],
             "hm_trace_read": [P, I32, P],
         }
         for name, args in sig.items():
@@ -186,6 +187,19 @@ def hm_load_vector(tree, sources, f, stream=None):
     _check(lib().hm_load_vector(tree, _ptr(sources, torch.float64), sources.shape[0], _ptr(f, torch.float64),
                                 _stream(stream)))
     return f
+
+
+def hm_potential(tree, points, values, out=None, trans=0, stream=None):
+    """Single-layer potential at points off the surface (trans = 0: [n]
+    density -> [n_points] values; trans = 1: the adjoint, [n_points] -> [n])."""
+    import torch
+    npts = points.shape[0]
+    if out is None:
+        m = hm_tree_get_info(tree)["n"] if trans else npts
+        out = torch.empty(m, dtype=torch.float64, device=points.device)
+    _check(lib().hm_potential(tree, _ptr(points, torch.float64), int(npts), int(trans),
+                              _ptr(values, torch.float64), _ptr(out, torch.float64), _stream(stream)))
+    return out
 
 
 def hm_matvec(A, x, y, trans=0, prec=HM_F64, alpha=1.0, beta=0.0, stream=None):

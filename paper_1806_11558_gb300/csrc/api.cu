@@ -23,15 +23,18 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
                   DBuf &uw_off);
 void build_lr_panels(hm_matrix *A, const DBuf &uw, const DBuf &uw_off, cudaStream_t s);
 void make_low_copies(hm_matrix *A, cudaStream_t s);
-void matvec_morton(const hm_matrix *A, hm_dtype prec, const MatvecWork &w, cudaStream_t s);
+void matvec_morton(const hm_matrix *A, hm_dtype prec, const MatvecWork &w, cudaStream_t s, bool trans);
+void build_transposed(const hm_matrix *A, cudaStream_t s);
 int64_t matvec_work_doubles(const hm_matrix *A);
 MatvecWork matvec_work_at(const hm_matrix *A, double *base);
 void permute_to_morton(const hm_tree *tr, const double *x, double *xm, cudaStream_t s);
 void permute_from_morton(const hm_tree *tr, const double *ym, double alpha, double beta, double *y, cudaStream_t s);
 void load_vector_impl(const hm_tree *tr, const double *src, int nsrc, double *f, cudaStream_t s);
 hm_status solve_impl(const hm_matrix *A, const double *b, double *x, const hm_solve_params &p, cudaStream_t s,
-                     hm_solve_info *info);
+                     hm_solve_info *info, bool trans);
 void get_block(const hm_matrix *A, int dense, int64_t b, double *out, cudaStream_t s);
+void potential_impl(const hm_tree *tr, const double *pts, int64_t K, int trans, const double *in, double *out,
+                    cudaStream_t s);
 void matvec_noalloc(const hm_matrix *A, int32_t nrhs, hm_dtype prec, const double *x, double *y, double alpha,
                     double beta, cudaStream_t s);
 }  // namespace hm
@@ -132,6 +135,18 @@ hm_status hm_load_vector(const hm_tree *tree, const double *d_sources, int32_t n
     });
 }
 
+hm_status hm_potential(const hm_tree *tree, const double *d_points, int64_t n_points, int32_t trans,
+                       const double *d_in, double *d_out, hm_stream_t stream) {
+    return guard([&] {
+        if (!is_tree(tree)) fail(HM_EINVAL, "not a tree handle");
+        if (n_points < 0) fail(HM_EINVAL, "n_points must be >= 0");
+        if (trans != 0 && trans != 1) fail(HM_EINVAL, "trans must be 0 or 1");
+        const bool reads = trans ? n_points > 0 : true, writes = trans ? true : n_points > 0;
+        if ((n_points > 0 && !d_points) || (reads && !d_in) || (writes && !d_out)) fail(HM_EINVAL, "NULL argument");
+        potential_impl(tree, d_points, n_points, trans, d_in, d_out, (cudaStream_t)stream);
+    });
+}
+
 hm_status hm_matvec(const hm_matrix *A, int32_t trans, int32_t nrhs, hm_dtype prec, const double *d_x, double *d_y,
                     double alpha, double beta, hm_stream_t stream) {
     return guard([&] {
@@ -139,7 +154,6 @@ hm_status hm_matvec(const hm_matrix *A, int32_t trans, int32_t nrhs, hm_dtype pr
         if (!d_x || !d_y) fail(HM_EINVAL, "NULL argument");
         if (nrhs < 1) fail(HM_EINVAL, "nrhs must be >= 1");
         if (trans != 0 && trans != 1) fail(HM_EINVAL, "trans must be 0 or 1");
-        if (trans == 1) fail(HM_EINVAL, "the transposed product is not available in this build");
         if (prec == HM_F32 && !A->up32.p) fail(HM_EINVAL, "FP32 copies were not assembled");
         if (prec == HM_BF16 && !A->upbf.p) fail(HM_EINVAL, "BF16 factors were not assembled");
         if (prec < HM_F64 || prec > HM_BF16) fail(HM_EINVAL, "bad precision");
@@ -148,9 +162,10 @@ hm_status hm_matvec(const hm_matrix *A, int32_t trans, int32_t nrhs, hm_dtype pr
         SBuf work;
         work.alloc(sizeof(double) * matvec_work_doubles(A), s);
         const MatvecWork w = matvec_work_at(A, work.as<double>());
+        if (trans) build_transposed(A, s);
         for (int r = 0; r < nrhs; ++r) {
             permute_to_morton(A->tree, d_x + (int64_t)r * n, w.xm, s);
-            matvec_morton(A, prec, w, s);
+            matvec_morton(A, prec, w, s, trans == 1);
             permute_from_morton(A->tree, w.ym, alpha, beta, d_y + (int64_t)r * n, s);
         }
     });
@@ -178,7 +193,6 @@ hm_status hm_solve(const hm_matrix *A, int32_t trans, int32_t nrhs, const double
         if (!d_b || !d_x || !params) fail(HM_EINVAL, "NULL argument");
         if (nrhs < 1) fail(HM_EINVAL, "nrhs must be >= 1");
         if (trans != 0 && trans != 1) fail(HM_EINVAL, "trans must be 0 or 1");
-        if (trans == 1) fail(HM_EINVAL, "the transposed solve is not available in this build");
         if (params->restart < 1 || params->restart > 128) fail(HM_EINVAL, "restart must be in [1, 128]");
         if (params->precond != 0 && params->precond != 1) fail(HM_EINVAL, "precond must be 0 or 1");
         if (params->max_iter < 1) fail(HM_EINVAL, "max_iter must be >= 1");
@@ -191,8 +205,10 @@ hm_status hm_solve(const hm_matrix *A, int32_t trans, int32_t nrhs, const double
             if (params->inner_dtype < HM_F64 || params->inner_dtype > HM_BF16) fail(HM_EINVAL, "bad inner_dtype");
         }
         const int64_t n = A->tree->n;
+        if (trans) build_transposed(A, (cudaStream_t)stream);
         for (int r = 0; r < nrhs; ++r) {
-            hm_status st = solve_impl(A, d_b + (int64_t)r * n, d_x + (int64_t)r * n, *params, (cudaStream_t)stream, info);
+            hm_status st = solve_impl(A, d_b + (int64_t)r * n, d_x + (int64_t)r * n, *params, (cudaStream_t)stream, info,
+                                      trans == 1);
             if (st != HM_OK) {
                 result = st;
                 set_last_error("GMRES reached max_iter before rel_tol");

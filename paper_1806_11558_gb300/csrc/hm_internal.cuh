@@ -226,6 +226,7 @@ struct hm_tree {
     hm::DBuf lr_colptr;   // [n_leaf + 1] int64: admissible leaves whose columns cover each leaf cluster
     hm::DBuf lr_collist;  // [..] int32 block ids (ascending per leaf cluster)
     hm::DBuf lr_bcolptr;  // [n_adm + 1] int64: first (block, column leaf cluster) pair of each block
+    hm::DBuf lr_browptr;  // [n_adm + 1] int64: first (block, row leaf cluster) pair of each block
     int64_t singular_cap = 0;  // upper bound on touching pairs
     int64_t n_singular = 0;    // filled by hm_assemble
     double seconds = 0.0;
@@ -274,6 +275,13 @@ struct hm_matrix {
     hm::DBuf wp_koff;   // [lr_collist size] int32, first panel column of each (kappa, block) pair
     hm::DBuf pofs;      // [sum over blocks of column leaf clusters] int64: partial offsets per block
     hm::DBuf tsum_b0;   // [ceil(total_rank / 32)] int32: block holding t entry 32 c
+    // transposed product (built on first use): the near field of H^T in the
+    // layout of the row panels (and its FP32 rounding), the partial offsets
+    // of the projections through the U panels, and the t index of every W
+    // panel column
+    hm::DBuf dense_t, dense32_t, pofs_t, tidx_t;
+    int64_t n_partials_t = 0;
+    bool trans_ready = false;
     int64_t wp_entries = 0;
     int64_t n_partials = 0;  // length of the partial-projection vector
     // block-Jacobi preconditioner: inverse of each leaf cluster's diagonal block

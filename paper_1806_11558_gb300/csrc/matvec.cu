@@ -128,16 +128,19 @@ __global__ void wp_pack_kernel(const int32_t *leaf_begin, const int64_t *lr_colp
     }
 }
 
-// offset of the partial projection of each (block, column leaf cluster) pair
+// offset of the partial projection of each (block, leaf cluster) pair: the
+// column leaf clusters of the block (side = 2, projections through the W
+// panels, product with H) or its row leaf clusters (side = 0, through the U
+// panels, product with H^T)
 __global__ void pofs_kernel(const int32_t *leaf_begin, int64_t nleaf, const int64_t *lr_colptr,
-                            const int32_t *lr_collist, const int32_t *adm, const int64_t *wp_colptr,
+                            const int32_t *lr_collist, const int32_t *adm, int side, const int64_t *wp_colptr,
                             const int32_t *koff, const int64_t *bcolptr, int64_t *pofs) {
     for (int64_t kap = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; kap < nleaf;
          kap += (int64_t)gridDim.x * blockDim.x) {
         for (int64_t q = lr_colptr[kap]; q < lr_colptr[kap + 1]; ++q) {
             const int32_t b = lr_collist[q];
             int64_t lo = 0, hi = nleaf;
-            const int32_t cb = adm[4 * b + 2];
+            const int32_t cb = adm[4 * b + side];
             while (lo < hi) {
                 const int64_t mid = (lo + hi) >> 1;
                 if (leaf_begin[mid] < cb) lo = mid + 1;
@@ -193,6 +196,7 @@ void build_lr_panels(hm_matrix *A, const DBuf &uw, const DBuf &uw_off, cudaStrea
     HM_CUDA_CHECK(cudaMemsetAsync(kpad.as<int64_t>() + nl, 0, sizeof(int64_t), s));
     A->up_entries = exclusive_scan_i64(size.as<int64_t>(), A->up_off.as<int64_t>(), nl + 1, s);
     const int64_t ncol = exclusive_scan_i64(kpad.as<int64_t>(), A->up_colptr.as<int64_t>(), nl + 1, s);
+    A->n_partials_t = ncol;  // projections through the U panels (transposed product)
     A->up.alloc(sizeof(double) * std::max<int64_t>(A->up_entries, 8));
     HM_CUDA_CHECK(cudaMemsetAsync(A->up.p, 0, sizeof(double) * std::max<int64_t>(A->up_entries, 8), s));
     A->tidx.alloc(sizeof(int32_t) * std::max<int64_t>(ncol, 8));
@@ -233,7 +237,7 @@ void build_lr_panels(hm_matrix *A, const DBuf &uw, const DBuf &uw_off, cudaStrea
                                                    A->wp_K.as<int32_t>(), A->wp.as<double>());
         HM_LAUNCH_CHECK();
         pofs_kernel<<<grid1d(nl), 256, 0, s>>>(tr->leaf_begin.as<int32_t>(), nl, tr->lr_colptr.as<int64_t>(),
-                                              tr->lr_collist.as<int32_t>(), tr->adm.as<int32_t>(),
+                                              tr->lr_collist.as<int32_t>(), tr->adm.as<int32_t>(), 2,
                                               A->wp_colptr.as<int64_t>(), A->wp_koff.as<int32_t>(),
                                               tr->lr_bcolptr.as<int64_t>(), A->pofs.as<int64_t>());
         HM_LAUNCH_CHECK();
@@ -245,6 +249,134 @@ void build_lr_panels(hm_matrix *A, const DBuf &uw, const DBuf &uw_off, cudaStrea
     }
 }
 
+// ---------------------------------------------------------------------------
+// transposed product H^T (data built on first use)
+// ---------------------------------------------------------------------------
+// Near field of H^T in the layout of the row panels: the place of dense leaf
+// b (rows rho_b, columns sigma_b) receives A(sigma_b, rho_b)^T.  The entries
+// come from b's transposed partner when the block tree has one (always for
+// Algorithm 1 on I x I with a symmetric admissibility); otherwise every
+// column j of b looks up the dense leaf that holds A(cb + j, rho_b): dense
+// leaves are sorted by (row begin, column begin) and their row ranges are
+// leaf clusters.
+constexpr int DT_MAX_COLS = 2 * MAX_LEAF;
+__global__ void to_f32_kernel(const double *a, int64_t n, float *o);
+
+__global__ void dense_transpose_kernel(const int32_t *__restrict__ dense, int64_t nd, const int64_t *__restrict__ base,
+                                       const int32_t *__restrict__ ld, const int32_t *__restrict__ tp,
+                                       const int32_t *__restrict__ leaf_begin, int64_t nleaf,
+                                       const double *__restrict__ A, double *__restrict__ AT, int *err) {
+    __shared__ int64_t s_src[DT_MAX_COLS];
+    const int64_t b = blockIdx.x;
+    const int32_t rb = dense[4 * b], re = dense[4 * b + 1], cb = dense[4 * b + 2], ce = dense[4 * b + 3];
+    const int m = re - rb, n = ce - cb;
+    const int64_t bb = base[b];
+    const int32_t lb = ld[b];
+    const int32_t p = tp[b];
+    if (p >= 0) {
+        const int64_t bp = base[p];
+        const int32_t lp = ld[p];
+        for (int e = threadIdx.x; e < m * n; e += blockDim.x) {
+            const int i = e / n, j = e - (e / n) * n;
+            AT[bb + (int64_t)i * lb + j] = A[bp + (int64_t)j * lp + i];
+        }
+        return;
+    }
+    if (n > DT_MAX_COLS) {
+        if (threadIdx.x == 0) atomicExch(err, 4);
+        return;
+    }
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const int32_t r = cb + j;
+        // leaf cluster of row r
+        int64_t lo = 0, hi = nleaf;
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (leaf_begin[mid] <= r) lo = mid;
+            else hi = mid;
+        }
+        const int32_t R = leaf_begin[lo];
+        // last dense leaf with (row begin, column begin) <= (R, rb)
+        int64_t a = -1, z = nd;
+        while (z - a > 1) {
+            const int64_t mid = (a + z) >> 1;
+            const int32_t mr = dense[4 * mid], mc = dense[4 * mid + 2];
+            if (mr < R || (mr == R && mc <= rb)) a = mid;
+            else z = mid;
+        }
+        int64_t src = -1;
+        if (a >= 0 && dense[4 * a] == R && dense[4 * a + 1] > r && dense[4 * a + 2] <= rb && dense[4 * a + 3] >= re)
+            src = base[a] + (int64_t)(r - R) * ld[a] + (rb - dense[4 * a + 2]);
+        if (src < 0) atomicExch(err, 4);
+        s_src[j] = src;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < m * n; e += blockDim.x) {
+        const int i = e / n, j = e - (e / n) * n;
+        const int64_t src = s_src[j];
+        AT[bb + (int64_t)i * lb + j] = src >= 0 ? A[src + i] : 0.0;
+    }
+}
+
+// t index of every column of the W panels (padding columns keep 0)
+__global__ void tidx_cols_kernel(const int64_t *lr_colptr, const int32_t *lr_collist, const int32_t *rank,
+                                 const int64_t *t_off, const int32_t *wp_koff, const int64_t *wp_colptr,
+                                 int32_t *tidx_t) {
+    const int64_t kap = blockIdx.x;
+    for (int64_t q = lr_colptr[kap]; q < lr_colptr[kap + 1]; ++q) {
+        const int32_t b = lr_collist[q];
+        const int k = rank[b];
+        for (int l = threadIdx.x; l < k; l += blockDim.x)
+            tidx_t[wp_colptr[kap] + wp_koff[q] + l] = (int32_t)(t_off[b] + l);
+    }
+}
+
+void build_transposed(const hm_matrix *Ac, cudaStream_t s) {
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    hm_matrix *A = const_cast<hm_matrix *>(Ac);  // cache owned by the matrix
+    if (A->trans_ready) return;
+    const hm_tree *tr = A->tree;
+    const int64_t nl = tr->n_leaf, na = tr->n_adm, nd = tr->n_dense;
+    const int64_t ne = std::max<int64_t>(tr->dense_entries, 1);
+    A->dense_t.alloc(sizeof(double) * ne);
+    HM_CUDA_CHECK(cudaMemsetAsync(A->dense_t.p, 0, sizeof(double) * ne, s));
+    DBuf err;
+    err.alloc(sizeof(int));
+    HM_CUDA_CHECK(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+    if (nd > 0) {
+        dense_transpose_kernel<<<(unsigned)nd, 128, 0, s>>>(tr->dense.as<int32_t>(), nd, tr->dense_base.as<int64_t>(),
+                                                           tr->dense_ld.as<int32_t>(), tr->dense_tp.as<int32_t>(),
+                                                           tr->leaf_begin.as<int32_t>(), nl, A->dense.as<double>(),
+                                                           A->dense_t.as<double>(), err.as<int>());
+        HM_LAUNCH_CHECK();
+    }
+    if (A->dense32.p) {
+        A->dense32_t.alloc(sizeof(float) * ne);
+        to_f32_kernel<<<grid1d(ne), 256, 0, s>>>(A->dense_t.as<double>(), ne, A->dense32_t.as<float>());
+        HM_LAUNCH_CHECK();
+    }
+    const int64_t npairs = read_scalar(tr->lr_browptr.as<int64_t>() + na, s);
+    A->pofs_t.alloc(sizeof(int64_t) * std::max<int64_t>(npairs, 1));
+    A->tidx_t.alloc(sizeof(int32_t) * std::max<int64_t>(A->n_partials, 8));
+    HM_CUDA_CHECK(cudaMemsetAsync(A->tidx_t.p, 0, sizeof(int32_t) * std::max<int64_t>(A->n_partials, 8), s));
+    if (na > 0 && nl > 0) {
+        pofs_kernel<<<grid1d(nl), 256, 0, s>>>(tr->leaf_begin.as<int32_t>(), nl, tr->lr_rowptr.as<int64_t>(),
+                                              tr->lr_list.as<int32_t>(), tr->adm.as<int32_t>(), 0,
+                                              A->up_colptr.as<int64_t>(), A->up_koff.as<int32_t>(),
+                                              tr->lr_browptr.as<int64_t>(), A->pofs_t.as<int64_t>());
+        HM_LAUNCH_CHECK();
+        tidx_cols_kernel<<<(unsigned)nl, 128, 0, s>>>(tr->lr_colptr.as<int64_t>(), tr->lr_collist.as<int32_t>(),
+                                                      A->rank.as<int32_t>(), A->t_off.as<int64_t>(),
+                                                      A->wp_koff.as<int32_t>(), A->wp_colptr.as<int64_t>(),
+                                                      A->tidx_t.as<int32_t>());
+        HM_LAUNCH_CHECK();
+    }
+    if (read_scalar(err.as<int>(), s) != 0)
+        fail(HM_EINTERNAL, "transposed near field: an entry of H^T has no stored counterpart");
+    A->trans_ready = true;
+}
+
 // Trace names of the three kernels of one product, per precision
 struct MvNames {
     const char *col, *tsum, *row;
@@ -252,23 +384,49 @@ struct MvNames {
 constexpr MvNames MV_F64{"col_kernel.f64", "tsum_kernel.f64", "row_kernel.f64"};
 constexpr MvNames MV_F32{"col_kernel.f32", "tsum_kernel.f32", "row_kernel.f32"};
 constexpr MvNames MV_BF16{"col_kernel.bf16", "tsum_kernel.bf16", "row_kernel.bf16"};
+constexpr MvNames MV_F64_T{"col_kernel.f64.t", "tsum_kernel.f64.t", "row_kernel.f64.t"};
+constexpr MvNames MV_F32_T{"col_kernel.f32.t", "tsum_kernel.f32.t", "row_kernel.f32.t"};
+constexpr MvNames MV_BF16_T{"col_kernel.bf16.t", "tsum_kernel.bf16.t", "row_kernel.bf16.t"};
+
+// Index data of one direction of the product: the projection panels (one
+// per leaf cluster, x_kappa^T times the panel gives the partials), the
+// partial offsets of each block, and the expansion panels with the t index
+// of each of their columns.  H: project through the W column panels, expand
+// through the U row panels.  H^T: project through the U panels, expand
+// through the W panels (U and W swap roles), near field transposed.
+struct MvDir {
+    const int64_t *proj_off, *proj_ptr;
+    const int32_t *proj_K;
+    const int64_t *bptr, *pofs;
+    const int64_t *exp_off, *exp_ptr;
+    const int32_t *exp_K, *exp_tidx;
+};
+
+static MvDir mv_dir(const hm_matrix *A, bool trans) {
+    const hm_tree *tr = A->tree;
+    if (!trans)
+        return MvDir{A->wp_off.as<int64_t>(), A->wp_colptr.as<int64_t>(), A->wp_K.as<int32_t>(),
+                     tr->lr_bcolptr.as<int64_t>(), A->pofs.as<int64_t>(), A->up_off.as<int64_t>(),
+                     A->up_colptr.as<int64_t>(), A->up_K.as<int32_t>(), A->tidx.as<int32_t>()};
+    return MvDir{A->up_off.as<int64_t>(), A->up_colptr.as<int64_t>(), A->up_K.as<int32_t>(),
+                 tr->lr_browptr.as<int64_t>(), A->pofs_t.as<int64_t>(), A->wp_off.as<int64_t>(),
+                 A->wp_colptr.as<int64_t>(), A->wp_K.as<int32_t>(), A->tidx_t.as<int32_t>()};
+}
 
 template <class TD, class TF, class TX, class TT>
-static void matvec_impl(const hm_matrix *A, const TD *dense, const TF *up, const TF *wp, const TX *x, TT *p, TT *t,
-                        double *ym, const MvNames &nm, cudaStream_t s) {
+static void matvec_impl(const hm_matrix *A, const TD *dense, const TF *proj, const TF *expd, const MvDir &d,
+                        const TX *x, TT *p, TT *t, double *ym, const MvNames &nm, cudaStream_t s) {
     const hm_tree *tr = A->tree;
     if (tr->n_adm > 0) {
         Trace tr_col(nm.col, s);
-        col_kernel<TF, TX, TT><<<(unsigned)tr->n_leaf, COL_THREADS, 0, s>>>(
-            tr->leaf_begin.as<int32_t>(), A->wp_off.as<int64_t>(), A->wp_K.as<int32_t>(), A->wp_colptr.as<int64_t>(),
-            wp, x, p);
+        col_kernel<TF, TX, TT><<<(unsigned)tr->n_leaf, COL_THREADS, 0, s>>>(tr->leaf_begin.as<int32_t>(), d.proj_off,
+                                                                            d.proj_K, d.proj_ptr, proj, x, p);
         HM_LAUNCH_CHECK();
     }
     if (tr->n_adm > 0) {
         Trace tr_tsum(nm.tsum, s);
         tsum_kernel<TT, TT><<<grid1d((A->total_rank + 31) / 32 * 32), 256, 0, s>>>(
-            tr->n_adm, A->total_rank, A->tsum_b0.as<int32_t>(), A->t_off.as<int64_t>(),
-            tr->lr_bcolptr.as<int64_t>(), A->pofs.as<int64_t>(), p, t);
+            tr->n_adm, A->total_rank, A->tsum_b0.as<int32_t>(), A->t_off.as<int64_t>(), d.bptr, d.pofs, p, t);
         HM_LAUNCH_CHECK();
     }
     auto kern = row_kernel<12, TD, TF, TX, TT>;
@@ -281,35 +439,47 @@ static void matvec_impl(const hm_matrix *A, const TD *dense, const TF *up, const
     Trace tr_row(nm.row, s);
     kern<<<(unsigned)tr->n_leaf, ROW_THREADS, 0, s>>>(
         tr->leaf_begin.as<int32_t>(), tr->rho_off.as<int64_t>(), tr->rho_K.as<int32_t>(),
-        tr->rho_colptr.as<int64_t>(), tr->colidx.as<int32_t>(), dense, A->up_off.as<int64_t>(),
-        A->up_K.as<int32_t>(), A->up_colptr.as<int64_t>(), A->tidx.as<int32_t>(), up, t, x, ym);
+        tr->rho_colptr.as<int64_t>(), tr->colidx.as<int32_t>(), dense, d.exp_off, d.exp_K, d.exp_ptr, d.exp_tidx,
+        expd, t, x, ym);
     HM_LAUNCH_CHECK();
 }
 
-// w.ym = H w.xm in Morton order.  FP64 uses w.t; the low-precision copies use
-// w.x32 (x rounded once) and w.t32, with FP32 accumulation.
-void matvec_morton(const hm_matrix *A, hm_dtype prec, const MatvecWork &w, cudaStream_t s) {
+// w.ym = op(H) w.xm in Morton order.  FP64 uses w.t; the low-precision
+// copies use w.x32 (x rounded once) and w.t32, with FP32 accumulation.  The
+// transposed product needs build_transposed() first.
+void matvec_morton(const hm_matrix *A, hm_dtype prec, const MatvecWork &w, cudaStream_t s, bool trans) {
     const int64_t n = A->tree->n;
+    if (trans && !A->trans_ready) fail(HM_EINTERNAL, "transposed data not built");
+    const MvDir d = mv_dir(A, trans);
     switch (prec) {
-        case HM_F64:
-            matvec_impl<double, double, double, double>(A, A->dense.as<double>(), A->up.as<double>(),
-                                                        A->wp.as<double>(), w.xm, w.p, w.t, w.ym, MV_F64, s);
+        case HM_F64: {
+            const double *dn = trans ? A->dense_t.as<double>() : A->dense.as<double>();
+            const double *pr = trans ? A->up.as<double>() : A->wp.as<double>();
+            const double *ex = trans ? A->wp.as<double>() : A->up.as<double>();
+            matvec_impl<double, double, double, double>(A, dn, pr, ex, d, w.xm, w.p, w.t, w.ym,
+                                                        trans ? MV_F64_T : MV_F64, s);
             break;
+        }
         case HM_F32:
-        case HM_BF16:
+        case HM_BF16: {
             if (!A->dense32.p || (prec == HM_F32 ? !A->up32.p : !A->upbf.p))
                 fail(HM_EINVAL, "the low-precision copies for this precision were not assembled");
             round_f32_kernel<<<grid1d(n), 256, 0, s>>>(w.xm, n, w.x32);
             HM_LAUNCH_CHECK();
-            if (prec == HM_F32)
-                matvec_impl<float, float, float, float>(A, A->dense32.as<float>(), A->up32.as<float>(),
-                                                        A->wp32.as<float>(), w.x32, w.p32, w.t32, w.ym, MV_F32, s);
-            else
-                matvec_impl<float, __nv_bfloat16, float, float>(A, A->dense32.as<float>(),
-                                                                A->upbf.as<__nv_bfloat16>(),
-                                                                A->wpbf.as<__nv_bfloat16>(), w.x32, w.p32, w.t32,
-                                                                w.ym, MV_BF16, s);
+            const float *dn = trans ? A->dense32_t.as<float>() : A->dense32.as<float>();
+            if (prec == HM_F32) {
+                const float *pr = trans ? A->up32.as<float>() : A->wp32.as<float>();
+                const float *ex = trans ? A->wp32.as<float>() : A->up32.as<float>();
+                matvec_impl<float, float, float, float>(A, dn, pr, ex, d, w.x32, w.p32, w.t32, w.ym,
+                                                        trans ? MV_F32_T : MV_F32, s);
+            } else {
+                const __nv_bfloat16 *pr = trans ? A->upbf.as<__nv_bfloat16>() : A->wpbf.as<__nv_bfloat16>();
+                const __nv_bfloat16 *ex = trans ? A->wpbf.as<__nv_bfloat16>() : A->upbf.as<__nv_bfloat16>();
+                matvec_impl<float, __nv_bfloat16, float, float>(A, dn, pr, ex, d, w.x32, w.p32, w.t32, w.ym,
+                                                                trans ? MV_BF16_T : MV_BF16, s);
+            }
             break;
+        }
         default:
             fail(HM_EINVAL, "unknown precision %d", (int)prec);
     }
@@ -319,12 +489,14 @@ void matvec_morton(const hm_matrix *A, hm_dtype prec, const MatvecWork &w, cudaS
 // doubles, then x32 [n], t32 [K], p32 [P] floats (K = sum of ranks, P = the
 // partial projections of the column panels).
 int64_t matvec_work_doubles(const hm_matrix *A) {
-    const int64_t n = A->tree->n, r = std::max<int64_t>(A->total_rank, 1), q = std::max<int64_t>(A->n_partials, 1);
+    const int64_t n = A->tree->n, r = std::max<int64_t>(A->total_rank, 1),
+                  q = std::max<int64_t>(std::max(A->n_partials, A->n_partials_t), 1);
     return 2 * n + r + q + (n + 1) / 2 + (r + 1) / 2 + (q + 1) / 2;
 }
 
 MatvecWork matvec_work_at(const hm_matrix *A, double *base) {
-    const int64_t n = A->tree->n, r = std::max<int64_t>(A->total_rank, 1), q = std::max<int64_t>(A->n_partials, 1);
+    const int64_t n = A->tree->n, r = std::max<int64_t>(A->total_rank, 1),
+                  q = std::max<int64_t>(std::max(A->n_partials, A->n_partials_t), 1);
     MatvecWork w;
     w.xm = base;
     w.ym = base + n;
@@ -484,6 +656,136 @@ void load_vector_impl(const hm_tree *tr, const double *src, int nsrc, double *f,
 
 
 // ---------------------------------------------------------------------------
+// single-layer potential at points off the surface (the ansatz of Sec. 2.1,
+// evaluated at interior points for the error measure of Sec. 4.3), 7-point
+// rule on every panel:
+//   trans = 0: u(p_k) = sum_j |T_j| sum_q w_q G(p_k, y_q^j) phi_j
+//   trans = 1: g_j    = |T_j| sum_q w_q sum_k G(p_k, y_q^j) r_k   (the adjoint)
+// ---------------------------------------------------------------------------
+constexpr int POT_THREADS = 256;  // evaluation points per CTA (trans = 0)
+constexpr int POT_CHUNK = 256;    // panels per CTA (trans = 0) / points staged per pass (trans = 1)
+constexpr double INV_4PI_D = 0.079577471545947667884441881686257181;
+
+// part[c][k] = sum over the panels of chunk c of the contributions to u(p_k)
+__global__ void __launch_bounds__(POT_THREADS) potential_partial_kernel(const double *__restrict__ pt, int64_t npad,
+                                                                        int64_t n, const int32_t *__restrict__ perm,
+                                                                        const double *__restrict__ pts, int64_t K,
+                                                                        const double *__restrict__ phi,
+                                                                        const QuadParams qp, double *__restrict__ part) {
+    __shared__ double s_x[NQ][POT_CHUNK], s_y[NQ][POT_CHUNK], s_z[NQ][POT_CHUNK], s_c[POT_CHUNK];
+    const int64_t j0 = (int64_t)blockIdx.y * POT_CHUNK;
+    const int nj = (int)min((int64_t)POT_CHUNK, n - j0);
+    for (int j = threadIdx.x; j < nj; j += POT_THREADS) {
+        const int64_t m = j0 + j;
+        for (int q = 0; q < NQ; ++q) {
+            s_x[q][j] = pt[(int64_t)q * npad + m];
+            s_y[q][j] = pt[(int64_t)(7 + q) * npad + m];
+            s_z[q][j] = pt[(int64_t)(14 + q) * npad + m];
+        }
+        s_c[j] = pt[(int64_t)PT_AREA * npad + m] * phi[perm[m]];
+    }
+    __syncthreads();
+    const int64_t k = (int64_t)blockIdx.x * POT_THREADS + threadIdx.x;
+    if (k >= K) return;
+    const double px = pts[3 * k], py = pts[3 * k + 1], pz = pts[3 * k + 2];
+    double acc = 0.0;
+    for (int j = 0; j < nj; ++j) {
+        double sj = 0.0;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const double dx = px - s_x[q][j], dy = py - s_y[q][j], dz = pz - s_z[q][j];
+            sj = fma(qp.w[q], rsqrt(fma(dx, dx, fma(dy, dy, dz * dz))), sj);
+        }
+        acc = fma(s_c[j], sj, acc);
+    }
+    part[(int64_t)blockIdx.y * K + k] = acc;
+}
+
+// u(p_k) = (1/4pi) sum over chunks in order
+__global__ void potential_sum_kernel(const double *__restrict__ part, int64_t nchunk, int64_t K, double *__restrict__ u) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K; k += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int64_t c = 0; c < nchunk; ++c) acc += part[c * K + k];
+        u[k] = acc * INV_4PI_D;
+    }
+}
+
+// g_j for one panel per thread, the points and their weights r staged in
+// shared memory chunk by chunk
+__global__ void __launch_bounds__(POT_THREADS) potential_adjoint_kernel(const double *__restrict__ pt, int64_t npad,
+                                                                        int64_t n, const int32_t *__restrict__ perm,
+                                                                        const double *__restrict__ pts, int64_t K,
+                                                                        const double *__restrict__ r,
+                                                                        const QuadParams qp, double *__restrict__ g) {
+    __shared__ double s_p[4][POT_CHUNK];
+    const int64_t m = (int64_t)blockIdx.x * POT_THREADS + threadIdx.x;
+    const bool live = m < n;
+    double x[NQ], y[NQ], z[NQ], acc[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        x[q] = live ? pt[(int64_t)q * npad + m] : 0.0;
+        y[q] = live ? pt[(int64_t)(7 + q) * npad + m] : 0.0;
+        z[q] = live ? pt[(int64_t)(14 + q) * npad + m] : 0.0;
+        acc[q] = 0.0;
+    }
+    for (int64_t k0 = 0; k0 < K; k0 += POT_CHUNK) {
+        const int nk = (int)min((int64_t)POT_CHUNK, K - k0);
+        __syncthreads();
+        for (int k = threadIdx.x; k < nk; k += POT_THREADS) {
+            s_p[0][k] = pts[3 * (k0 + k)];
+            s_p[1][k] = pts[3 * (k0 + k) + 1];
+            s_p[2][k] = pts[3 * (k0 + k) + 2];
+            s_p[3][k] = r[k0 + k];
+        }
+        __syncthreads();
+        for (int k = 0; k < nk; ++k) {
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const double dx = s_p[0][k] - x[q], dy = s_p[1][k] - y[q], dz = s_p[2][k] - z[q];
+                acc[q] = fma(s_p[3][k], rsqrt(fma(dx, dx, fma(dy, dy, dz * dz))), acc[q]);
+            }
+        }
+    }
+    if (!live) return;
+    double sj = 0.0;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) sj = fma(qp.w[q], acc[q], sj);
+    g[perm[m]] = pt[(int64_t)PT_AREA * npad + m] * sj * INV_4PI_D;
+}
+
+void potential_impl(const hm_tree *tr, const double *pts, int64_t K, int trans, const double *in, double *out,
+                    cudaStream_t s) {
+    const QuadParams qp = make_quad(1);
+    const int64_t n = tr->n;
+    if (K == 0 || n == 0) {
+        if (trans && n) HM_CUDA_CHECK(cudaMemsetAsync(out, 0, sizeof(double) * n, s));
+        if (!trans && K) HM_CUDA_CHECK(cudaMemsetAsync(out, 0, sizeof(double) * K, s));
+        return;
+    }
+    if (!trans) {
+        const int64_t nchunk = (n + POT_CHUNK - 1) / POT_CHUNK;
+        if (nchunk > 65535) fail(HM_EINVAL, "too many panels for the potential kernel (%lld)", (long long)n);
+        SBuf part;
+        part.alloc(sizeof(double) * nchunk * K, s);
+        const dim3 grid((unsigned)((K + POT_THREADS - 1) / POT_THREADS), (unsigned)nchunk);
+        {
+            Trace trace("potential_kernel", s);
+            potential_partial_kernel<<<grid, POT_THREADS, 0, s>>>(tr->pt.as<double>(), tr->npad, n,
+                                                                  tr->perm.as<int32_t>(), pts, K, in, qp,
+                                                                  part.as<double>());
+            HM_LAUNCH_CHECK();
+            potential_sum_kernel<<<grid1d(K), 256, 0, s>>>(part.as<double>(), nchunk, K, out);
+            HM_LAUNCH_CHECK();
+        }
+    } else {
+        Trace trace("potential_adjoint_kernel", s);
+        potential_adjoint_kernel<<<(unsigned)((n + POT_THREADS - 1) / POT_THREADS), POT_THREADS, 0, s>>>(
+            tr->pt.as<double>(), tr->npad, n, tr->perm.as<int32_t>(), pts, K, in, qp, out);
+        HM_LAUNCH_CHECK();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // H-matrix-vector product without any device allocation
 //
 // For callers that must not allocate device memory while they run: code that
@@ -491,8 +793,9 @@ void load_vector_impl(const hm_tree *tr, const double *src, int nsrc, double *f,
 // service), code running where an allocation would block or fail, or callers
 // whose own allocator forbids stray cudaMalloc/cudaFree calls.  hm_matvec
 // obtains its permuted input / output vectors and its low-rank projections
-// from cudaMalloc on every call; this variant takes them from one file-scope
-// device array instead, sized once when the library is loaded.
+// from the stream-ordered allocator on every call; this variant takes them
+// from one file-scope device array instead, sized once when the library is
+// loaded.
 //
 // Scratch layout: the product's working vectors (x and y in Morton order,
 // the projections t_b = W_b^T x and their per-column-cluster partials, and
@@ -541,7 +844,7 @@ void matvec_noalloc(const hm_matrix *A, int32_t nrhs, hm_dtype prec, const doubl
     const MatvecWork w = matvec_work_at(A, noalloc_scratch());
     for (int r = 0; r < nrhs; ++r) {
         permute_to_morton(A->tree, x + (int64_t)r * n, w.xm, s);
-        matvec_morton(A, prec, w, s);
+        matvec_morton(A, prec, w, s, false);
         permute_from_morton(A->tree, w.ym, alpha, beta, y + (int64_t)r * n, s);
     }
 }

@@ -16,17 +16,19 @@
 
 namespace hm {
 
-void matvec_morton(const hm_matrix *A, hm_dtype prec, const MatvecWork &w, cudaStream_t s);
+void matvec_morton(const hm_matrix *A, hm_dtype prec, const MatvecWork &w, cudaStream_t s, bool trans);
+void build_transposed(const hm_matrix *A, cudaStream_t s);
 int64_t matvec_work_doubles(const hm_matrix *A);
 MatvecWork matvec_work_at(const hm_matrix *A, double *base);
 
 // y = op(H) x in Morton order (x and y distinct vectors of the solver); the
 // projections live in the solver's workspace
-static void apply(const hm_matrix *A, hm_dtype prec, const double *x, double *y, DBuf &work, cudaStream_t s) {
+static void apply(const hm_matrix *A, hm_dtype prec, const double *x, double *y, DBuf &work, cudaStream_t s,
+                  bool trans) {
     MatvecWork w = matvec_work_at(A, work.as<double>());
     w.xm = const_cast<double *>(x);
     w.ym = y;
-    matvec_morton(A, prec, w, s);
+    matvec_morton(A, prec, w, s, trans);
 }
 
 constexpr int DOT_THREADS = 256;
@@ -241,10 +243,12 @@ __global__ void bj_invert_kernel(const int32_t *leaf_begin, const int64_t *bj_of
 
 // z_rho = D_rho^{-1} v_rho: one thread per row over the column-major inverse
 // (consecutive threads read consecutive rows of one column), v_rho staged in
-// shared memory; each row sums its columns in order.
+// shared memory; each row sums its columns in order.  trans: z = D^{-T} v,
+// the preconditioner of the transposed system (row-major reading).
 constexpr int BJ_THREADS = 64;
 __global__ void __launch_bounds__(BJ_THREADS) bj_apply_kernel(const int32_t *leaf_begin, const int64_t *bj_off,
-                                                              const double *bj, const double *v, double *z) {
+                                                              const double *bj, const double *v, double *z,
+                                                              int trans) {
     __shared__ double s_v[MAX_LEAF];
     const int64_t r = blockIdx.x;
     const int32_t r0 = leaf_begin[r], m = leaf_begin[r + 1] - r0;
@@ -253,7 +257,8 @@ __global__ void __launch_bounds__(BJ_THREADS) bj_apply_kernel(const int32_t *lea
     __syncthreads();
     for (int i = threadIdx.x; i < m; i += BJ_THREADS) {
         double acc = 0.0;
-        for (int j = 0; j < m; ++j) acc = fma(D[(int64_t)j * m + i], s_v[j], acc);
+        const int64_t si = trans ? m : 1, sj = trans ? 1 : m;
+        for (int j = 0; j < m; ++j) acc = fma(D[j * sj + i * si], s_v[j], acc);
         z[r0 + i] = acc;
     }
 }
@@ -282,11 +287,11 @@ static void bj_setup(const hm_matrix *Ac, cudaStream_t s) {
     A->bj = std::move(bj);
 }
 
-static void bj_apply(const hm_matrix *A, const double *v, double *z, cudaStream_t s) {
+static void bj_apply(const hm_matrix *A, const double *v, double *z, cudaStream_t s, bool trans) {
     const hm_tree *tr = A->tree;
     Trace trace("bj_apply_kernel", s);
     bj_apply_kernel<<<(unsigned)tr->n_leaf, BJ_THREADS, 0, s>>>(tr->leaf_begin.as<int32_t>(), A->bj_off.as<int64_t>(),
-                                                        A->bj.as<double>(), v, z);
+                                                        A->bj.as<double>(), v, z, trans ? 1 : 0);
     HM_LAUNCH_CHECK();
 }
 
@@ -332,7 +337,7 @@ struct Gmres {
 // and cycles accumulate; relres = final true residual / ||b||.
 static hm_status gmres(const hm_matrix *A, hm_dtype prec, const double *b, double *x, double tol, int maxit,
                        Gmres &G, cudaStream_t s, int &iters, int &cycles, double &relres, bool x_is_zero,
-                       bool precond) {
+                       bool precond, bool trans) {
     const int64_t n = G.n;
     const int m = G.m;
     double *V = G.V.as<double>();
@@ -346,7 +351,7 @@ static hm_status gmres(const hm_matrix *A, hm_dtype prec, const double *b, doubl
     if (x_is_zero) {
         HM_CUDA_CHECK(cudaMemcpyAsync(V, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
     } else {
-        apply(A, prec, x, G.ax.as<double>(), G.t, s);
+        apply(A, prec, x, G.ax.as<double>(), G.t, s, trans);
         residual_kernel<<<g1(n), 256, 0, s>>>(b, G.ax.as<double>(), n, V);
         HM_LAUNCH_CHECK();
     }
@@ -365,10 +370,10 @@ static hm_status gmres(const hm_matrix *A, hm_dtype prec, const double *b, doubl
             double *w = G.w.as<double>();
             if (precond) {
                 // right preconditioning: w = H (M^{-1} v_j)
-                bj_apply(A, vj, G.z.as<double>(), s);
-                apply(A, prec, G.z.as<double>(), w, G.t, s);
+                bj_apply(A, vj, G.z.as<double>(), s, trans);
+                apply(A, prec, G.z.as<double>(), w, G.t, s, trans);
             } else {
-                apply(A, prec, vj, w, G.t, s);
+                apply(A, prec, vj, w, G.t, s, trans);
             }
             // CGS2
             G.dots(V, j + 1, w, G.h.as<double>(), 0, s);
@@ -412,7 +417,7 @@ static hm_status gmres(const hm_matrix *A, hm_dtype prec, const double *b, doubl
             HM_CUDA_CHECK(cudaMemsetAsync(G.d.p, 0, sizeof(double) * n, s));
             add_combo_kernel<<<g1(n), 256, 0, s>>>(V, n, k, G.y.as<double>(), n, G.d.as<double>());
             HM_LAUNCH_CHECK();
-            bj_apply(A, G.d.as<double>(), G.z.as<double>(), s);
+            bj_apply(A, G.d.as<double>(), G.z.as<double>(), s, trans);
             axpy_kernel<<<g1(n), 256, 0, s>>>(1.0, G.z.as<double>(), n, x);
             HM_LAUNCH_CHECK();
         } else {
@@ -420,7 +425,7 @@ static hm_status gmres(const hm_matrix *A, hm_dtype prec, const double *b, doubl
             HM_LAUNCH_CHECK();
         }
         // true residual -> V_0 for the next cycle
-        apply(A, prec, x, G.ax.as<double>(), G.t, s);
+        apply(A, prec, x, G.ax.as<double>(), G.t, s, trans);
         residual_kernel<<<g1(n), 256, 0, s>>>(b, G.ax.as<double>(), n, V);
         HM_LAUNCH_CHECK();
         beta = std::sqrt(G.norm2_host(V, s));
@@ -433,7 +438,7 @@ void permute_to_morton(const hm_tree *tr, const double *x, double *xm, cudaStrea
 void permute_from_morton(const hm_tree *tr, const double *ym, double alpha, double beta, double *y, cudaStream_t s);
 
 hm_status solve_impl(const hm_matrix *A, const double *b_orig, double *x_orig, const hm_solve_params &p,
-                     cudaStream_t s, hm_solve_info *info) {
+                     cudaStream_t s, hm_solve_info *info, bool trans) {
     const auto t0 = std::chrono::steady_clock::now();
     const hm_tree *tr = A->tree;
     const int64_t n = tr->n;
@@ -450,7 +455,7 @@ hm_status solve_impl(const hm_matrix *A, const double *b_orig, double *x_orig, c
     hm_status st;
     if (!p.refine) {
         st = gmres(A, HM_F64, b.as<double>(), x.as<double>(), p.rel_tol, p.max_iter, G, s, iters, cycles, relres, true,
-                   pc);
+                   pc, trans);
     } else {
         DBuf r, d, ax;
         r.alloc(sizeof(double) * n);
@@ -469,10 +474,10 @@ hm_status solve_impl(const hm_matrix *A, const double *b_orig, double *x_orig, c
             HM_CUDA_CHECK(cudaMemsetAsync(d.p, 0, sizeof(double) * n, s));
             double inner = 1.0;
             gmres(A, p.inner_dtype, r.as<double>(), d.as<double>(), p.inner_tol, p.max_iter, G, s, iters, cycles,
-                  inner, true, pc);
+                  inner, true, pc, trans);
             axpy_kernel<<<g1(n), 256, 0, s>>>(1.0, d.as<double>(), n, x.as<double>());
             HM_LAUNCH_CHECK();
-            apply(A, HM_F64, x.as<double>(), ax.as<double>(), G.t, s);
+            apply(A, HM_F64, x.as<double>(), ax.as<double>(), G.t, s, trans);
             residual_kernel<<<g1(n), 256, 0, s>>>(b.as<double>(), ax.as<double>(), n, r.as<double>());
             HM_LAUNCH_CHECK();
             relres = std::sqrt(G.norm2_host(r.as<double>(), s)) / bnorm;

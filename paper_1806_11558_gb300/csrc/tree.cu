@@ -709,7 +709,7 @@ hm_tree *build_tree_impl(const double *d_V, int64_t nv, const int32_t *d_T, int6
             }
             if (bptr) *bptr = std::move(cnt);
         };
-        build_csr(0, tr->lr_rowptr, tr->lr_list, nullptr);
+        build_csr(0, tr->lr_rowptr, tr->lr_list, &tr->lr_browptr);
         build_csr(2, tr->lr_colptr, tr->lr_collist, &tr->lr_bcolptr);
         // transposed partners of the admissible leaves
         tr->adm_tp.alloc(sizeof(int32_t) * std::max<int64_t>(n_adm, 1));

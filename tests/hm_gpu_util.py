@@ -47,11 +47,11 @@ class GpuH:
         self.torch.cuda.synchronize()
         return out.cpu().numpy()
 
-    def matvec(self, x, prec=0):
+    def matvec(self, x, prec=0, trans=0):
         torch = self.torch
         xd = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).cuda()
         yd = torch.empty_like(xd)
-        self.hm.hm_matvec(self.A, xd, yd, prec=prec)
+        self.hm.hm_matvec(self.A, xd, yd, prec=prec, trans=trans)
         torch.cuda.synchronize()
         return yd.cpu().numpy()
 
