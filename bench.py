@@ -461,6 +461,12 @@ def main():
     args = ap.parse_args()
     global CASE
     CASE = args.case
+    if CASE != "precision":
+        # other meshes run with their own recipe's tree and ACA parameters
+        import meshgen
+        cfg = meshgen.config(CASE)
+        WORKLOAD.update(workload="%s (profiling / parity case)" % CASE, panels=int(cfg["T"].shape[0]),
+                        leaf_size=cfg["leaf_size"], eta=cfg["eta"], aca_eps=cfg["aca_eps"])
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count()))

@@ -230,6 +230,22 @@ HM_API hm_status hm_potential(const hm_tree *tree, const double *d_points, int64
 HM_API hm_status hm_matvec(const hm_matrix *A, int32_t trans, int32_t nrhs, hm_dtype prec, const double *d_x, double *d_y,
                     double alpha, double beta, hm_stream_t stream);
 
+/* The product with many right-hand sides on the tensor cores (the
+ * multi-RHS form of the H-matvec of Sec. 2.3): y = alpha H x + beta y for
+ * nrhs right-hand sides [nrhs][n] (original order), 16 at a time, each
+ * stored entry read once per 16.  Runs on the low-precision copies:
+ * prec = HM_F32 (FP32 near field and factors) or HM_BF16 (FP32 near field,
+ * BF16 factors).  The tensor-core operands are BF16 (mma m16n8k16, FP32
+ * accumulation): FP32 values, including x, are split into a BF16 pair
+ * (hi + lo) and multiplied as hi*hi + hi*lo + lo*hi, so the result carries
+ * about 16 significant bits (relative error ~1e-5 on top of the copy's own
+ * rounding) — accurate enough for the inner solves of the refinement.
+ * Stream-ordered (working vectors from the stream-ordered pool).
+ * Errors: HM_EINVAL for NULL pointers, nrhs < 1, or a precision whose copy
+ * was not assembled (HM_F64 included: the FP64 master is not used here). */
+HM_API hm_status hm_matvec_block(const hm_matrix *A, int32_t nrhs, hm_dtype prec, const double *d_x, double *d_y,
+                                 double alpha, double beta, hm_stream_t stream);
+
 /* The H-matrix-vector product of hm_matvec (trans = 0 only) for callers that
  * must not allocate device memory during the call: code running under a fixed
  * device-memory budget or its own pool, where a cudaMalloc / cudaFree would

@@ -33,6 +33,8 @@ void load_vector_impl(const hm_tree *tr, const double *src, int nsrc, double *f,
 hm_status solve_impl(const hm_matrix *A, const double *b, double *x, const hm_solve_params &p, cudaStream_t s,
                      hm_solve_info *info, bool trans);
 void get_block(const hm_matrix *A, int dense, int64_t b, double *out, cudaStream_t s);
+void matvec_mrhs(const hm_matrix *A, hm_dtype prec, int nrhs, const double *x, double *y, double alpha, double beta,
+                 cudaStream_t s);
 void potential_impl(const hm_tree *tr, const double *pts, int64_t K, int trans, const double *in, double *out,
                     cudaStream_t s);
 void matvec_noalloc(const hm_matrix *A, int32_t nrhs, hm_dtype prec, const double *x, double *y, double alpha,
@@ -168,6 +170,19 @@ hm_status hm_matvec(const hm_matrix *A, int32_t trans, int32_t nrhs, hm_dtype pr
             matvec_morton(A, prec, w, s, trans == 1);
             permute_from_morton(A->tree, w.ym, alpha, beta, d_y + (int64_t)r * n, s);
         }
+    });
+}
+
+hm_status hm_matvec_block(const hm_matrix *A, int32_t nrhs, hm_dtype prec, const double *d_x, double *d_y,
+                          double alpha, double beta, hm_stream_t stream) {
+    return guard([&] {
+        if (!is_matrix(A)) fail(HM_EINVAL, "not a matrix handle");
+        if (!d_x || !d_y) fail(HM_EINVAL, "NULL argument");
+        if (nrhs < 1) fail(HM_EINVAL, "nrhs must be >= 1");
+        if (prec != HM_F32 && prec != HM_BF16) fail(HM_EINVAL, "the block product runs on the FP32 / BF16 copies");
+        if (!A->dense32.p || (prec == HM_F32 ? !A->up32.p : !A->upbf.p))
+            fail(HM_EINVAL, "the low-precision copies for this precision were not assembled");
+        matvec_mrhs(A, prec, nrhs, d_x, d_y, alpha, beta, (cudaStream_t)stream);
     });
 }
 
