@@ -115,6 +115,14 @@ typedef struct {
     double inner_tol;
     hm_dtype inner_dtype;
     int32_t precond;
+    int32_t batched;  /* 1 = solve the nrhs systems together (trans = 0): every
+                         system runs its own GMRES, in lockstep, and each
+                         Arnoldi step applies H to all of them at once — on the
+                         FP32 / BF16 copies through the tensor-core product of
+                         hm_matvec_block (16 right-hand sides per pass), on the
+                         FP64 master one column after the other.  info reports
+                         the lockstep step count and the largest relative
+                         residual.  0 = one system after the other. */
 } hm_solve_params;
 
 typedef struct {

@@ -44,7 +44,7 @@ class AssembleParams(ctypes.Structure):
 class SolveParams(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("rel_tol", ctypes.c_double),
                 ("refine", ctypes.c_int32), ("max_refine", ctypes.c_int32), ("inner_tol", ctypes.c_double),
-                ("inner_dtype", ctypes.c_int), ("precond", ctypes.c_int32)]
+                ("inner_dtype", ctypes.c_int), ("precond", ctypes.c_int32), ("batched", ctypes.c_int32)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -234,12 +234,12 @@ def hm_matvec_noalloc(A, x, y, trans=0, prec=HM_F64, alpha=1.0, beta=0.0, stream
 
 
 def hm_solve(A, b, x, trans=0, restart=30, max_iter=3000, rel_tol=1e-10, refine=0, max_refine=20, inner_tol=1e-4,
-             inner_dtype=HM_F32, precond=0, stream=None, raise_on_noconv=True):
+             inner_dtype=HM_F32, precond=0, batched=0, stream=None, raise_on_noconv=True):
     """Solves op(H) x = b; returns the SolveInfo of the (last) right-hand side."""
     import torch
     nrhs = 1 if b.dim() == 1 else b.shape[0]
     prm = SolveParams(int(restart), int(max_iter), float(rel_tol), int(refine), int(max_refine), float(inner_tol),
-                      int(inner_dtype), int(precond))
+                      int(inner_dtype), int(precond), int(batched))
     info = SolveInfo()
     st = lib().hm_solve(A, int(trans), nrhs, _ptr(b, torch.float64), _ptr(x, torch.float64), ctypes.byref(prm),
                         _stream(stream), ctypes.byref(info))

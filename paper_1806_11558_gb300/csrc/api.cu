@@ -33,6 +33,8 @@ void load_vector_impl(const hm_tree *tr, const double *src, int nsrc, double *f,
 hm_status solve_impl(const hm_matrix *A, const double *b, double *x, const hm_solve_params &p, cudaStream_t s,
                      hm_solve_info *info, bool trans);
 void get_block(const hm_matrix *A, int dense, int64_t b, double *out, cudaStream_t s);
+hm_status solve_batched(const hm_matrix *A, int nrhs, const double *b_orig, double *x_orig, const hm_solve_params &p,
+                        cudaStream_t s, hm_solve_info *info);
 void matvec_mrhs(const hm_matrix *A, hm_dtype prec, int nrhs, const double *x, double *y, double alpha, double beta,
                  cudaStream_t s);
 void potential_impl(const hm_tree *tr, const double *pts, int64_t K, int trans, const double *in, double *out,
@@ -218,6 +220,18 @@ hm_status hm_solve(const hm_matrix *A, int32_t trans, int32_t nrhs, const double
             if (params->inner_dtype == HM_F32 && !A->up32.p) fail(HM_EINVAL, "FP32 copies were not assembled");
             if (params->inner_dtype == HM_BF16 && !A->upbf.p) fail(HM_EINVAL, "BF16 factors were not assembled");
             if (params->inner_dtype < HM_F64 || params->inner_dtype > HM_BF16) fail(HM_EINVAL, "bad inner_dtype");
+        }
+        if (params->batched != 0 && params->batched != 1) fail(HM_EINVAL, "batched must be 0 or 1");
+        if (params->batched && trans) fail(HM_EINVAL, "the batched solve is for trans = 0");
+        if (params->batched && params->refine && params->inner_dtype != HM_F64 && !A->dense32.p)
+            fail(HM_EINVAL, "the FP32 near-field copy was not assembled");
+        if (params->batched) {
+            const hm_status st = solve_batched(A, nrhs, d_b, d_x, *params, (cudaStream_t)stream, info);
+            if (st != HM_OK) {
+                result = st;
+                set_last_error("GMRES reached max_iter (or max_refine) before rel_tol");
+            }
+            return;
         }
         const int64_t n = A->tree->n;
         if (trans) build_transposed(A, (cudaStream_t)stream);

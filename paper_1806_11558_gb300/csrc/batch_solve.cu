@@ -1,0 +1,553 @@
+// batch_solve.cu -- many independent systems solved in lockstep with one
+// shared operator application per Arnoldi step.
+//
+// A system is one right-hand side restricted to one geometry of the tree:
+// system s = r * G + g owns the entries [geom_off[g], geom_off[g + 1]) of
+// column r of the [R][n] Morton-ordered vectors.  Every system runs its own
+// restarted GMRES (CGS2, Givens rotations, Hessenberg solve, all FP64, the
+// same algorithm as solve.cu), but the systems advance together, so one
+// step applies H to all R columns at once: on the FP32 / BF16 copies that is
+// the 16-right-hand-side tensor-core product of mrhs.cu; on the FP64 master
+// it is one product per column.  A system that has converged stops updating
+// (its rotations, coefficients and vectors are left alone) while the others
+// continue.  The FP64 iterative refinement around it follows solve.cu: the
+// residual B - H_64 X in FP64, the inner solves on the low-precision copy.
+// Every reduction runs in a fixed order.
+#include <chrono>
+#include <cmath>
+
+#include "hm_internal.cuh"
+
+namespace hm {
+
+void matvec_morton(const hm_matrix *A, hm_dtype prec, const MatvecWork &w, cudaStream_t s, bool trans);
+int64_t matvec_work_doubles(const hm_matrix *A);
+MatvecWork matvec_work_at(const hm_matrix *A, double *base);
+void matvec_mrhs_morton(const hm_matrix *A, hm_dtype prec, const float *X, double *Y, float *work, cudaStream_t s);
+int64_t mrhs_work_floats(const hm_matrix *A);
+void bj_setup(const hm_matrix *A, cudaStream_t s);
+void permute_to_morton(const hm_tree *tr, const double *x, double *xm, cudaStream_t s);
+void permute_from_morton(const hm_tree *tr, const double *ym, double alpha, double beta, double *y, cudaStream_t s);
+
+constexpr int BMR = 16;        // columns of one tensor-core product
+constexpr int BITEM = 8192;    // entries of one work item
+constexpr int BTHREADS = 256;
+
+struct Item {
+    int32_t sys, col;
+    int64_t i0, i1;
+};
+
+static unsigned gx(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 65535)); }
+
+// part[item][l] = V_l(col, i0:i1) . w(col, i0:i1), l < nv (0 for inactive systems)
+__global__ void __launch_bounds__(BTHREADS) bdots_kernel(const Item *__restrict__ items, const double *__restrict__ V,
+                                                         int64_t vstride, int64_t n, int nv,
+                                                         const double *__restrict__ w, const int *__restrict__ act,
+                                                         double *__restrict__ part) {
+    __shared__ double s_red[BTHREADS / 32][8];
+    const Item it = items[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool on = act[it.sys] != 0;
+    const double *wc = w + (int64_t)it.col * n;
+    for (int c0 = 0; c0 < nv; c0 += 8) {
+        double acc[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[c] = 0.0;
+        if (on) {
+            for (int64_t i = it.i0 + threadIdx.x; i < it.i1; i += BTHREADS) {
+                const double wi = wc[i];
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    if (c0 + c < nv) acc[c] = fma(V[(int64_t)(c0 + c) * vstride + (int64_t)it.col * n + i], wi, acc[c]);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            double v = acc[c];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) s_red[warp][c] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < 8 && c0 + (int)threadIdx.x < nv) {
+            double t = 0.0;
+            for (int k = 0; k < BTHREADS / 32; ++k) t += s_red[k][threadIdx.x];
+            part[(int64_t)blockIdx.x * nv + c0 + threadIdx.x] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// out[s][l] = sum over the items of s (in order) of part[item][l]; accumulate adds
+__global__ void bdots_final_kernel(const int64_t *__restrict__ iptr, int S, int nv, const double *__restrict__ part,
+                                   double *__restrict__ out, int ld, int accumulate) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < S * nv; e += gridDim.x * blockDim.x) {
+        const int s = e / nv, l = e - (e / nv) * nv;
+        double t = 0.0;
+        for (int64_t k = iptr[s]; k < iptr[s + 1]; ++k) t += part[k * nv + l];
+        out[(int64_t)s * ld + l] = accumulate ? out[(int64_t)s * ld + l] + t : t;
+    }
+}
+
+// w(col, i) -= sum_l V_l(col, i) h[s][l]   (active systems)
+__global__ void bsub_kernel(const Item *__restrict__ items, const double *__restrict__ V, int64_t vstride, int64_t n,
+                            int nv, const double *__restrict__ h, int ldh, const int *__restrict__ act,
+                            double *__restrict__ w) {
+    const Item it = items[blockIdx.x];
+    if (!act[it.sys]) return;
+    const double *hs = h + (int64_t)it.sys * ldh;
+    double *wc = w + (int64_t)it.col * n;
+    for (int64_t i = it.i0 + threadIdx.x; i < it.i1; i += blockDim.x) {
+        double a = wc[i];
+        for (int l = 0; l < nv; ++l) a -= V[(int64_t)l * vstride + (int64_t)it.col * n + i] * hs[l];
+        wc[i] = a;
+    }
+}
+
+// x(col, i) += sum_{l < k_s} V_l(col, i) y[s][l]
+__global__ void badd_kernel(const Item *__restrict__ items, const double *__restrict__ V, int64_t vstride, int64_t n,
+                            const int *__restrict__ k, const double *__restrict__ y, int ldy, double *__restrict__ x) {
+    const Item it = items[blockIdx.x];
+    const int ks = k[it.sys];
+    if (ks == 0) return;
+    const double *ys = y + (int64_t)it.sys * ldy;
+    double *xc = x + (int64_t)it.col * n;
+    for (int64_t i = it.i0 + threadIdx.x; i < it.i1; i += blockDim.x) {
+        double a = 0.0;
+        for (int l = 0; l < ks; ++l) a += V[(int64_t)l * vstride + (int64_t)it.col * n + i] * ys[l];
+        xc[i] += a;
+    }
+}
+
+// dst(col, i) = src(col, i) / sqrt(nrm2[s]) for the systems in mask (0 when the norm is 0)
+__global__ void bscale_kernel(const Item *__restrict__ items, const double *__restrict__ src, int64_t n,
+                              const double *__restrict__ nrm2, int nstride, const int *__restrict__ mask,
+                              double *__restrict__ dst) {
+    const Item it = items[blockIdx.x];
+    if (!mask[it.sys]) return;
+    const double nr = sqrt(nrm2[(int64_t)it.sys * nstride]);
+    const double *sc = src + (int64_t)it.col * n;
+    double *dc = dst + (int64_t)it.col * n;
+    for (int64_t i = it.i0 + threadIdx.x; i < it.i1; i += blockDim.x) dc[i] = nr > 0.0 ? sc[i] / nr : 0.0;
+}
+
+__global__ void bsub_vec_kernel(const double *__restrict__ a, const double *__restrict__ b, int64_t n,
+                                double *__restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = a[i] - b[i];
+}
+
+__global__ void badd_vec_kernel(const double *__restrict__ a, int64_t n, double *__restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] += a[i];
+}
+
+// h[s][l] += h2[s][l], l < nv
+__global__ void badd_coef_kernel(int S, int nv, int ld, const double *__restrict__ h2, double *__restrict__ h) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < S * nv; e += gridDim.x * blockDim.x) {
+        const int s = e / nv, l = e - (e / nv) * nv;
+        h[(int64_t)s * ld + l] += h2[(int64_t)s * ld + l];
+    }
+}
+
+// Givens step j of every active system (one thread per system); writes
+// est[s] = |g_s[j+1]| and hn[s] = ||w_s||
+__global__ void bgivens_kernel(int S, int m, int j, const int *__restrict__ act, const double *__restrict__ h,
+                               int ldh, const double *__restrict__ wn2, double *__restrict__ H,
+                               double *__restrict__ cs, double *__restrict__ sn, double *__restrict__ g,
+                               double *__restrict__ est, double *__restrict__ hn) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S || !act[s]) return;
+    double *col = H + (int64_t)s * (m + 1) * m + (int64_t)j * (m + 1);
+    double *c = cs + (int64_t)s * m, *sg = sn + (int64_t)s * m, *gs = g + (int64_t)s * (m + 1);
+    for (int l = 0; l <= j; ++l) col[l] = h[(int64_t)s * ldh + l];
+    const double hh = sqrt(wn2[s]);
+    col[j + 1] = hh;
+    for (int l = 0; l < j; ++l) {
+        const double t = c[l] * col[l] + sg[l] * col[l + 1];
+        col[l + 1] = -sg[l] * col[l] + c[l] * col[l + 1];
+        col[l] = t;
+    }
+    const double rho = hypot(col[j], col[j + 1]);
+    c[j] = rho > 0.0 ? col[j] / rho : 1.0;
+    sg[j] = rho > 0.0 ? col[j + 1] / rho : 0.0;
+    col[j] = rho;
+    col[j + 1] = 0.0;
+    gs[j + 1] = -sg[j] * gs[j];
+    gs[j] = c[j] * gs[j];
+    est[s] = fabs(gs[j + 1]);
+    hn[s] = hh;
+}
+
+// y_s = R_s^{-1} g_s over the k_s first rotations (one thread per system)
+__global__ void btrisolve_kernel(int S, int m, const int *__restrict__ k, const double *__restrict__ H,
+                                 const double *__restrict__ g, double *__restrict__ y) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const int ks = k[s];
+    const double *Hs = H + (int64_t)s * (m + 1) * m;
+    const double *gs = g + (int64_t)s * (m + 1);
+    double *ys = y + (int64_t)s * m;
+    for (int i = ks - 1; i >= 0; --i) {
+        double t = gs[i];
+        for (int c = i + 1; c < ks; ++c) t -= Hs[(int64_t)c * (m + 1) + i] * ys[c];
+        ys[i] = t / Hs[(int64_t)i * (m + 1) + i];
+    }
+}
+
+// g_s = (sqrt(nrm2[s]), 0, ...) for the systems in mask
+__global__ void bset_g0_kernel(int S, int m, const int *__restrict__ mask, const double *__restrict__ nrm2,
+                               double *__restrict__ g) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S || !mask[s]) return;
+    double *gs = g + (int64_t)s * (m + 1);
+    for (int l = 0; l <= m; ++l) gs[l] = 0.0;
+    gs[0] = sqrt(nrm2[s]);
+}
+
+// z(col) = D^{-1} v(col) on every leaf cluster, all columns (grid.y = column)
+constexpr int BBJ_THREADS = 64;
+__global__ void __launch_bounds__(BBJ_THREADS) bbj_apply_kernel(const int32_t *leaf_begin, const int64_t *bj_off,
+                                                                const double *bj, const double *v, double *z,
+                                                                int64_t n) {
+    __shared__ double s_v[MAX_LEAF];
+    const int64_t r = blockIdx.x;
+    const int64_t c = blockIdx.y;
+    const int32_t r0 = leaf_begin[r], m = leaf_begin[r + 1] - r0;
+    const double *D = bj + bj_off[r];
+    const double *vc = v + c * n;
+    double *zc = z + c * n;
+    for (int j = threadIdx.x; j < m; j += BBJ_THREADS) s_v[j] = vc[r0 + j];
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += BBJ_THREADS) {
+        double acc = 0.0;
+        for (int j = 0; j < m; ++j) acc = fma(D[(int64_t)j * m + i], s_v[j], acc);
+        zc[r0 + i] = acc;
+    }
+}
+
+// [R][n] FP64 <-> [n][16] blocks of the tensor-core product
+__global__ void to_block_kernel(const double *__restrict__ v, int64_t n, int R, float *__restrict__ X) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * BMR; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / BMR;
+        const int r = (int)(e - i * BMR);
+        X[e] = r < R ? (float)v[(int64_t)r * n + i] : 0.0f;
+    }
+}
+
+__global__ void from_block_kernel(const double *__restrict__ Y, int64_t n, int R, double *__restrict__ v) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * R; e += (int64_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / n);
+        const int64_t i = e - (int64_t)r * n;
+        v[e] = Y[i * BMR + r];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host
+// ---------------------------------------------------------------------------
+struct Batch {
+    const hm_matrix *A;
+    int64_t n;
+    int R, G, S, m;
+    bool precond;
+    std::vector<Item> items_h;
+    std::vector<int64_t> iptr_h;
+    DBuf items, iptr, V, W, Z, AX, part, h, h2, H, cs, sn, g, y, est, hn, nrm, act, cyc, kk, ones, mv, mvf;
+    int64_t vstride;
+
+    Batch(const hm_matrix *A_, int R_, int m_, bool pc, cudaStream_t s) : A(A_), R(R_), m(m_), precond(pc) {
+        const hm_tree *tr = A->tree;
+        n = tr->n;
+        std::vector<int64_t> go = tr->geom_off;
+        if (go.size() < 2) go = {0, n};
+        G = (int)go.size() - 1;
+        S = R * G;
+        iptr_h.assign(S + 1, 0);
+        for (int r = 0; r < R; ++r)
+            for (int gg = 0; gg < G; ++gg) {
+                const int sys = r * G + gg;
+                iptr_h[sys] = (int64_t)items_h.size();
+                for (int64_t i0 = go[gg]; i0 < go[gg + 1]; i0 += BITEM)
+                    items_h.push_back(Item{sys, r, i0, std::min<int64_t>(go[gg + 1], i0 + BITEM)});
+            }
+        iptr_h[S] = (int64_t)items_h.size();
+        items.alloc(sizeof(Item) * std::max<size_t>(items_h.size(), 1));
+        iptr.alloc(sizeof(int64_t) * (S + 1));
+        HM_CUDA_CHECK(cudaMemcpyAsync(items.p, items_h.data(), sizeof(Item) * items_h.size(), cudaMemcpyHostToDevice, s));
+        HM_CUDA_CHECK(cudaMemcpyAsync(iptr.p, iptr_h.data(), sizeof(int64_t) * (S + 1), cudaMemcpyHostToDevice, s));
+        vstride = (int64_t)R * n;
+        V.alloc(sizeof(double) * (int64_t)(m + 1) * vstride);
+        HM_CUDA_CHECK(cudaMemsetAsync(V.p, 0, sizeof(double) * (int64_t)(m + 1) * vstride, s));
+        W.alloc(sizeof(double) * vstride);
+        Z.alloc(sizeof(double) * vstride);
+        AX.alloc(sizeof(double) * vstride);
+        part.alloc(sizeof(double) * std::max<size_t>(items_h.size(), 1) * (m + 1));
+        h.alloc(sizeof(double) * S * (m + 1));
+        h2.alloc(sizeof(double) * S * (m + 1));
+        H.alloc(sizeof(double) * S * (int64_t)(m + 1) * m);
+        cs.alloc(sizeof(double) * S * m);
+        sn.alloc(sizeof(double) * S * m);
+        g.alloc(sizeof(double) * S * (m + 1));
+        y.alloc(sizeof(double) * S * m);
+        est.alloc(sizeof(double) * S);
+        hn.alloc(sizeof(double) * S);
+        nrm.alloc(sizeof(double) * S);
+        act.alloc(sizeof(int) * S);
+        cyc.alloc(sizeof(int) * S);
+        kk.alloc(sizeof(int) * S);
+        ones.alloc(sizeof(int) * S);
+        {
+            std::vector<int> o(S, 1);
+            HM_CUDA_CHECK(cudaMemcpyAsync(ones.p, o.data(), sizeof(int) * S, cudaMemcpyHostToDevice, s));
+            HM_CUDA_CHECK(cudaStreamSynchronize(s));
+        }
+        mv.alloc(sizeof(double) * matvec_work_doubles(A));
+        if (R > 1) mvf.alloc(sizeof(float) * mrhs_work_floats(A));
+    }
+    unsigned nitems() const { return (unsigned)items_h.size(); }
+
+    // out[s][l] = V_l . w per system, l < nv
+    void dots(const double *Vb, int nv, const double *w, const int *mask, double *out, int ld, int accumulate,
+              cudaStream_t s) {
+        Trace trace("batch_dots", s);
+        bdots_kernel<<<nitems(), BTHREADS, 0, s>>>(items.as<Item>(), Vb, vstride, n, nv, w, mask, part.as<double>());
+        HM_LAUNCH_CHECK();
+        bdots_final_kernel<<<gx((int64_t)S * nv), 256, 0, s>>>(iptr.as<int64_t>(), S, nv, part.as<double>(), out, ld,
+                                                              accumulate);
+        HM_LAUNCH_CHECK();
+    }
+    // per-system squared norms of v into nrm (host copy returned)
+    std::vector<double> norms2(const double *v, cudaStream_t s) {
+        dots(v, 1, v, ones.as<int>(), nrm.as<double>(), 1, 0, s);
+        std::vector<double> out(S);
+        HM_CUDA_CHECK(cudaMemcpyAsync(out.data(), nrm.p, sizeof(double) * S, cudaMemcpyDeviceToHost, s));
+        HM_CUDA_CHECK(cudaStreamSynchronize(s));
+        return out;
+    }
+    // y = op x for all R columns ([R][n], Morton)
+    void apply(hm_dtype prec, const double *x, double *yv, cudaStream_t s) {
+        if (prec == HM_F64 || R == 1) {
+            for (int r = 0; r < R; ++r) {
+                MatvecWork w = matvec_work_at(A, mv.as<double>());
+                w.xm = const_cast<double *>(x + (int64_t)r * n);
+                w.ym = yv + (int64_t)r * n;
+                matvec_morton(A, prec, w, s, false);
+            }
+            return;
+        }
+        float *X = mvf.as<float>();
+        double *Y = reinterpret_cast<double *>(X + (int64_t)BMR * n);
+        float *work = X + 3 * (int64_t)BMR * n;
+        for (int r0 = 0; r0 < R; r0 += BMR) {
+            const int nr = std::min(BMR, R - r0);
+            to_block_kernel<<<gx(n * BMR), 256, 0, s>>>(x + (int64_t)r0 * n, n, nr, X);
+            HM_LAUNCH_CHECK();
+            matvec_mrhs_morton(A, prec, X, Y, work, s);
+            from_block_kernel<<<gx(n * nr), 256, 0, s>>>(Y, n, nr, yv + (int64_t)r0 * n);
+            HM_LAUNCH_CHECK();
+        }
+    }
+    void bj(const double *v, double *z, cudaStream_t s) {
+        const hm_tree *tr = A->tree;
+        Trace trace("batch_bj_apply", s);
+        bbj_apply_kernel<<<dim3((unsigned)tr->n_leaf, (unsigned)R), BBJ_THREADS, 0, s>>>(
+            tr->leaf_begin.as<int32_t>(), A->bj_off.as<int64_t>(), A->bj.as<double>(), v, z, n);
+        HM_LAUNCH_CHECK();
+    }
+};
+
+// Lockstep GMRES(m) of all systems for op x = b ([R][n], Morton), x = 0 on
+// entry.  `on` marks the systems to solve (others keep x = 0); tol per
+// system relative to ||b_s||.  Returns the Arnoldi steps taken.
+static int gmres_batch(Batch &B, hm_dtype prec, const double *b, double *x, const std::vector<int> &on, double tol,
+                       int maxit, int &cycles, cudaStream_t s) {
+    const int S = B.S, m = B.m;
+    const int64_t vs = B.vstride;
+    double *V = B.V.as<double>();
+    HM_CUDA_CHECK(cudaMemsetAsync(x, 0, sizeof(double) * vs, s));
+    std::vector<double> bn2 = B.norms2(b, s);
+    std::vector<int> act(S);
+    std::vector<double> bnorm(S);
+    for (int k = 0; k < S; ++k) {
+        bnorm[k] = std::sqrt(bn2[k]);
+        act[k] = on[k] && bnorm[k] > 0.0;
+    }
+    HM_CUDA_CHECK(cudaMemcpyAsync(V, b, sizeof(double) * vs, cudaMemcpyDeviceToDevice, s));
+    int iters = 0;
+    bool first = true;
+    for (;;) {
+        // residual norms of V_0 (b in the first cycle)
+        std::vector<double> r2 = first ? bn2 : B.norms2(V, s);
+        first = false;
+        bool any = false;
+        for (int k = 0; k < S; ++k) {
+            if (act[k] && std::sqrt(r2[k]) <= tol * bnorm[k]) act[k] = 0;
+            any = any || act[k];
+        }
+        if (!any || iters >= maxit) break;
+        ++cycles;
+        std::vector<int> cyc = act;
+        HM_CUDA_CHECK(cudaMemcpyAsync(B.act.p, act.data(), sizeof(int) * S, cudaMemcpyHostToDevice, s));
+        HM_CUDA_CHECK(cudaMemcpyAsync(B.cyc.p, cyc.data(), sizeof(int) * S, cudaMemcpyHostToDevice, s));
+        HM_CUDA_CHECK(cudaMemsetAsync(B.kk.p, 0, sizeof(int) * S, s));
+        // nrm = ||V_0||^2 per system (already in r2): set g, normalise V_0
+        HM_CUDA_CHECK(cudaMemcpyAsync(B.nrm.p, r2.data(), sizeof(double) * S, cudaMemcpyHostToDevice, s));
+        bset_g0_kernel<<<(S + 127) / 128, 128, 0, s>>>(S, m, B.cyc.as<int>(), B.nrm.as<double>(), B.g.as<double>());
+        HM_LAUNCH_CHECK();
+        bscale_kernel<<<B.nitems(), 256, 0, s>>>(B.items.as<Item>(), V, B.n, B.nrm.as<double>(), 1, B.cyc.as<int>(),
+                                                 V);
+        HM_LAUNCH_CHECK();
+        std::vector<int> kk(S, 0);
+        for (int j = 0; j < m; ++j) {
+            double *vj = V + (int64_t)j * vs;
+            double *w = B.W.as<double>();
+            if (B.precond) {
+                B.bj(vj, B.Z.as<double>(), s);
+                B.apply(prec, B.Z.as<double>(), w, s);
+            } else {
+                B.apply(prec, vj, w, s);
+            }
+            // CGS2 per system: h = V^T w, w -= V h, h2 = V^T w, w -= V h2, h += h2
+            B.dots(V, j + 1, w, B.cyc.as<int>(), B.h.as<double>(), m + 1, 0, s);
+            {
+                Trace trace("batch_update", s);
+                bsub_kernel<<<B.nitems(), 256, 0, s>>>(B.items.as<Item>(), V, vs, B.n, j + 1, B.h.as<double>(), m + 1,
+                                                       B.cyc.as<int>(), w);
+                HM_LAUNCH_CHECK();
+            }
+            B.dots(V, j + 1, w, B.cyc.as<int>(), B.h2.as<double>(), m + 1, 0, s);
+            {
+                Trace trace("batch_update", s);
+                bsub_kernel<<<B.nitems(), 256, 0, s>>>(B.items.as<Item>(), V, vs, B.n, j + 1, B.h2.as<double>(),
+                                                       m + 1, B.cyc.as<int>(), w);
+                HM_LAUNCH_CHECK();
+            }
+            badd_coef_kernel<<<gx((int64_t)S * (j + 1)), 256, 0, s>>>(S, j + 1, m + 1, B.h2.as<double>(),
+                                                                     B.h.as<double>());
+            HM_LAUNCH_CHECK();
+            B.dots(w, 1, w, B.cyc.as<int>(), B.nrm.as<double>(), 1, 0, s);
+            bgivens_kernel<<<(S + 127) / 128, 128, 0, s>>>(S, m, j, B.cyc.as<int>(), B.h.as<double>(), m + 1,
+                                                          B.nrm.as<double>(), B.H.as<double>(), B.cs.as<double>(),
+                                                          B.sn.as<double>(), B.g.as<double>(), B.est.as<double>(),
+                                                          B.hn.as<double>());
+            HM_LAUNCH_CHECK();
+            std::vector<double> est(S), hn(S);
+            HM_CUDA_CHECK(cudaMemcpyAsync(est.data(), B.est.p, sizeof(double) * S, cudaMemcpyDeviceToHost, s));
+            HM_CUDA_CHECK(cudaMemcpyAsync(hn.data(), B.hn.p, sizeof(double) * S, cudaMemcpyDeviceToHost, s));
+            HM_CUDA_CHECK(cudaStreamSynchronize(s));
+            ++iters;
+            bool more = false;
+            for (int k = 0; k < S; ++k) {
+                if (!cyc[k]) continue;
+                kk[k] = j + 1;
+                if (est[k] <= tol * bnorm[k] || hn[k] == 0.0 || iters >= maxit) cyc[k] = 0;
+                more = more || cyc[k];
+            }
+            if (!more) break;
+            HM_CUDA_CHECK(cudaMemcpyAsync(B.cyc.p, cyc.data(), sizeof(int) * S, cudaMemcpyHostToDevice, s));
+            bscale_kernel<<<B.nitems(), 256, 0, s>>>(B.items.as<Item>(), w, B.n, B.nrm.as<double>(), 1,
+                                                     B.cyc.as<int>(), V + (int64_t)(j + 1) * vs);
+            HM_LAUNCH_CHECK();
+        }
+        // x += M^{-1} V y per system
+        HM_CUDA_CHECK(cudaMemcpyAsync(B.kk.p, kk.data(), sizeof(int) * S, cudaMemcpyHostToDevice, s));
+        btrisolve_kernel<<<(S + 127) / 128, 128, 0, s>>>(S, m, B.kk.as<int>(), B.H.as<double>(), B.g.as<double>(),
+                                                        B.y.as<double>());
+        HM_LAUNCH_CHECK();
+        if (B.precond) {
+            HM_CUDA_CHECK(cudaMemsetAsync(B.W.p, 0, sizeof(double) * vs, s));
+            badd_kernel<<<B.nitems(), 256, 0, s>>>(B.items.as<Item>(), V, vs, B.n, B.kk.as<int>(), B.y.as<double>(), m,
+                                                   B.W.as<double>());
+            HM_LAUNCH_CHECK();
+            B.bj(B.W.as<double>(), B.Z.as<double>(), s);
+            badd_vec_kernel<<<gx(vs), 256, 0, s>>>(B.Z.as<double>(), vs, x);
+            HM_LAUNCH_CHECK();
+        } else {
+            badd_kernel<<<B.nitems(), 256, 0, s>>>(B.items.as<Item>(), V, vs, B.n, B.kk.as<int>(), B.y.as<double>(), m,
+                                                   x);
+            HM_LAUNCH_CHECK();
+        }
+        // true residual -> V_0 (systems outside `act` keep their x; their rows of V_0 are not used)
+        B.apply(prec, x, B.AX.as<double>(), s);
+        bsub_vec_kernel<<<gx(vs), 256, 0, s>>>(b, B.AX.as<double>(), vs, V);
+        HM_LAUNCH_CHECK();
+    }
+    return iters;
+}
+
+hm_status solve_batched(const hm_matrix *A, int nrhs, const double *b_orig, double *x_orig, const hm_solve_params &p,
+                        cudaStream_t s, hm_solve_info *info) {
+    const auto t0 = std::chrono::steady_clock::now();
+    const hm_tree *tr = A->tree;
+    const int64_t n = tr->n;
+    const int64_t vs = (int64_t)nrhs * n;
+    DBuf b, x;
+    b.alloc(sizeof(double) * vs);
+    x.alloc(sizeof(double) * vs);
+    for (int r = 0; r < nrhs; ++r) permute_to_morton(tr, b_orig + (int64_t)r * n, b.as<double>() + (int64_t)r * n, s);
+    HM_CUDA_CHECK(cudaMemsetAsync(x.p, 0, sizeof(double) * vs, s));
+    const bool pc = p.precond == 1;
+    if (pc) bj_setup(A, s);
+    Batch B(A, nrhs, p.restart, pc, s);
+    const int S = B.S;
+    int iters = 0, cycles = 0, steps = 0;
+    std::vector<double> bn2 = B.norms2(b.as<double>(), s);
+    std::vector<int> on(S, 1);
+    double worst = 0.0;
+    hm_status st = HM_OK;
+    if (!p.refine) {
+        iters = gmres_batch(B, HM_F64, b.as<double>(), x.as<double>(), on, p.rel_tol, p.max_iter, cycles, s);
+        B.apply(HM_F64, x.as<double>(), B.AX.as<double>(), s);
+        bsub_vec_kernel<<<gx(vs), 256, 0, s>>>(b.as<double>(), B.AX.as<double>(), vs, B.W.as<double>());
+        HM_LAUNCH_CHECK();
+        std::vector<double> r2 = B.norms2(B.W.as<double>(), s);
+        for (int k = 0; k < S; ++k) {
+            const double rr = bn2[k] > 0.0 ? std::sqrt(r2[k] / bn2[k]) : 0.0;
+            worst = std::max(worst, rr);
+        }
+        if (worst > p.rel_tol) st = HM_ENOCONV;
+    } else {
+        DBuf r, d;
+        r.alloc(sizeof(double) * vs);
+        d.alloc(sizeof(double) * vs);
+        HM_CUDA_CHECK(cudaMemcpyAsync(r.p, b.p, sizeof(double) * vs, cudaMemcpyDeviceToDevice, s));
+        st = HM_ENOCONV;
+        for (;;) {
+            std::vector<double> r2 = B.norms2(r.as<double>(), s);
+            worst = 0.0;
+            for (int k = 0; k < S; ++k) {
+                const double rr = bn2[k] > 0.0 ? std::sqrt(r2[k] / bn2[k]) : 0.0;
+                on[k] = rr > p.rel_tol;
+                worst = std::max(worst, rr);
+            }
+            if (worst <= p.rel_tol) {
+                st = HM_OK;
+                break;
+            }
+            if (steps >= p.max_refine || iters >= p.max_iter) break;
+            ++steps;
+            iters += gmres_batch(B, p.inner_dtype, r.as<double>(), d.as<double>(), on, p.inner_tol,
+                                 p.max_iter - iters, cycles, s);
+            badd_vec_kernel<<<gx(vs), 256, 0, s>>>(d.as<double>(), vs, x.as<double>());
+            HM_LAUNCH_CHECK();
+            B.apply(HM_F64, x.as<double>(), B.AX.as<double>(), s);
+            bsub_vec_kernel<<<gx(vs), 256, 0, s>>>(b.as<double>(), B.AX.as<double>(), vs, r.as<double>());
+            HM_LAUNCH_CHECK();
+        }
+    }
+    for (int r = 0; r < nrhs; ++r)
+        permute_from_morton(tr, x.as<double>() + (int64_t)r * n, 1.0, 0.0, x_orig + (int64_t)r * n, s);
+    HM_CUDA_CHECK(cudaStreamSynchronize(s));
+    if (info) {
+        info->status = st;
+        info->iters = iters;
+        info->restarts = cycles;
+        info->refine_steps = steps;
+        info->rel_resid = worst;
+        info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return st;
+}
+
+}  // namespace hm

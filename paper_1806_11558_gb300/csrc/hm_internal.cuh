@@ -204,6 +204,9 @@ struct hm_tree {
     hm::DBuf cl_box;    // [nc][6] double (lo xyz, hi xyz)
     int64_t n_leaf = 0;
     int32_t max_leaf = 0;
+    // geometries of a batched tree: panels of geometry g occupy the Morton
+    // positions [geom_off[g], geom_off[g + 1]) (host copy; one geometry = [0, n))
+    std::vector<int64_t> geom_off;
     hm::DBuf leaf_begin;  // [n_leaf + 1] int32, begins of the leaf clusters (ascending)
     // block tree
     int64_t n_dense = 0, n_adm = 0;

@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(BJ_THREADS) bj_apply_kernel(const int32_t *lea
     }
 }
 
-static void bj_setup(const hm_matrix *Ac, cudaStream_t s) {
+void bj_setup(const hm_matrix *Ac, cudaStream_t s) {
     hm_matrix *A = const_cast<hm_matrix *>(Ac);  // cache owned by the matrix
     if (A->bj.p) return;
     const hm_tree *tr = A->tree;
