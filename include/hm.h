@@ -148,6 +148,7 @@ typedef struct {
                                a common-vertex pair of a symmetric block
                                counted once                                    */
     double seconds;         /* wall time of hm_build_tree                         */
+    int32_t n_geom;         /* geometries (1 unless built by hm_build_forest)     */
 } hm_tree_info;
 
 typedef struct {
@@ -196,6 +197,29 @@ HM_API hm_status hm_build_tree(const double *d_vertices, int64_t n_vertices, con
  *  fit in device memory. */
 HM_API hm_status hm_assemble(const hm_tree *tree, const hm_assemble_params *params, hm_stream_t stream,
                       hm_matrix **out);
+
+/* The trees of many independent geometries in one structure (batched
+ * problems): geometry g is the triangle range [h_tri_offsets[g],
+ * h_tri_offsets[g + 1]) of d_tris (indices into the shared d_vertices).  Each
+ * geometry gets its own bounding cube and Morton order (the panels of a
+ * geometry stay contiguous, geometries in input order), its own cluster tree
+ * (cardinality halving from its own root), and Algorithm 1 runs from every
+ * (root_g, root_g) pair, so no block couples two geometries: the assembled
+ * operator is block diagonal and every later call (assembly, products,
+ * solves) treats all geometries in the same launches.  A batched solve
+ * (hm_solve_params.batched) runs one GMRES per geometry and right-hand side.
+ *  h_tri_offsets: host, n_geom + 1 entries, 0 = first, n_tris = last, each
+ *  geometry non-empty.  Other arguments and errors as hm_build_tree. */
+HM_API hm_status hm_build_forest(const double *d_vertices, int64_t n_vertices, const int32_t *d_tris, int64_t n_tris,
+                                 const int64_t *h_tri_offsets, int32_t n_geom, const hm_tree_params *params,
+                                 hm_stream_t stream, hm_tree **out);
+
+/* Load vectors of a forest with sources per geometry: d_sources is
+ * [n_geom][n_per_geom][3] (device); d_f[s][i] = int_Ti 1/(4 pi |x - p_{g,s}|)
+ * with g the geometry of panel i, [n_per_geom][n] in original order.
+ * Errors: HM_EINVAL for NULL pointers or n_per_geom < 1. */
+HM_API hm_status hm_load_vector_geom(const hm_tree *tree, const double *d_sources, int32_t n_per_geom, double *d_f,
+                                     hm_stream_t stream);
 
 /* Galerkin load vector for point-source Dirichlet data (Sec. 2.2):
  * f[s][i] = int_Ti g_s dsigma with g_s(x) = 1 / (4 pi |x - p_s|), by the

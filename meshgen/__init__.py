@@ -209,8 +209,33 @@ def config(name: str):
                  1,024 evaluation points on the sphere of radius 2.5
                  (normalised Gaussian directions) and the target field of a
                  point source at (0,0,3) there
+    batching / batching<G> :
+                 64 (or G) icospheres of levels drawn uniformly from 3..6, each
+                 stretched by axis scales log-uniform in [0.5, 2], with 4
+                 exterior point sources each (|p| in [2, 4], outside the
+                 stretched ellipsoid grown by 1.1); ACA eps = 1e-5
     level<L>   : unit icosphere of level L with p = (3,0,0) (parity ladders)
     """
+    if name.startswith("batching"):
+        # batching / batching<G>: G geometries (default 64)
+        G = int(name[len("batching"):] or 64)
+        rng = np.random.Generator(np.random.PCG64(MASTER_SEED + 3))
+        levels = rng.integers(3, 7, size=G)
+        Vs, Ts, offs, srcs, scales = [], [], [0], [], []
+        nv = 0
+        for g in range(G):
+            V, T = icosphere(int(levels[g]))
+            sc = np.exp(rng.uniform(np.log(0.5), np.log(2.0), size=3))
+            V = stretch(V, sc)
+            Vs.append(V)
+            Ts.append(T + nv)
+            nv += V.shape[0]
+            offs.append(offs[-1] + T.shape[0])
+            srcs.append(point_sources(int(rng.integers(1 << 31)), 4, scales=sc))
+            scales.append(sc)
+        return dict(V=np.ascontiguousarray(np.concatenate(Vs)), T=np.ascontiguousarray(np.concatenate(Ts)),
+                    tri_offsets=np.array(offs, dtype=np.int64), sources=np.stack(srcs), levels=levels,
+                    scales=np.array(scales), leaf_size=64, eta=1.5, aca_eps=1e-5)
     if name.startswith("differentiation"):
         L = int(name[len("differentiation"):] or 6)
         V, T = icosphere(L)

@@ -23,7 +23,8 @@ STATUS_NAMES = {0: "HM_OK", 1: "HM_EINVAL", 2: "HM_ENOMEM", 3: "HM_ECUDA", 4: "H
 EXPORTED = ["hm_build_tree", "hm_assemble", "hm_load_vector", "hm_matvec", "hm_solve", "hm_free",
             "hm_tree_get_info", "hm_tree_get_perm", "hm_tree_get_leaves", "hm_matrix_get_info",
             "hm_matrix_export", "hm_last_error", "hm_kernel_launches", "hm_matvec_noalloc", "hm_matrix_get_block",
-            "hm_trace_enable", "hm_trace_read", "hm_potential", "hm_matvec_block"]
+            "hm_trace_enable", "hm_trace_read", "hm_potential", "hm_matvec_block", "hm_build_forest",
+            "hm_load_vector_geom"]
 
 
 class HMError(RuntimeError):
@@ -56,7 +57,7 @@ class TreeInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("n_clusters", ctypes.c_int64), ("depth", ctypes.c_int32),
                 ("max_leaf", ctypes.c_int32), ("n_dense", ctypes.c_int64), ("n_adm", ctypes.c_int64),
                 ("dense_entries", ctypes.c_int64), ("adm_rows_cols", ctypes.c_int64),
-                ("n_singular", ctypes.c_int64), ("seconds", ctypes.c_double)]
+                ("n_singular", ctypes.c_int64), ("seconds", ctypes.c_double), ("n_geom", ctypes.c_int32)]
 
 
 class MatrixInfo(ctypes.Structure):
@@ -94,6 +95,8 @@ def lib():
             "hm_matvec": [P, I32, I32, I, P, P, D, D, P],
             "hm_matvec_noalloc": [P, I32, I32, I, P, P, D, D, P],
             "hm_matvec_block": [P, I32, I, P, P, D, D, P],
+            "hm_build_forest": [P, I64, P, I64, P, I32, P, P, P],
+            "hm_load_vector_geom": [P, P, I32, P, P],
             "hm_solve": [P, I32, I32, P, P, P, P, P],
             "hm_tree_get_info": [P, P],
             "hm_tree_get_perm": [P, P],
@@ -173,6 +176,27 @@ def hm_build_tree(vertices, tris, eta=1.5, leaf_size=64, stream=None):
     _check(lib().hm_build_tree(_ptr(vertices, torch.float64), vertices.shape[0], _ptr(tris, torch.int32),
                                tris.shape[0], ctypes.byref(prm), _stream(stream), ctypes.byref(out)))
     return out
+
+
+def hm_build_forest(vertices, tris, tri_offsets, eta=1.5, leaf_size=64, stream=None):
+    """Trees of several geometries in one structure: geometry g = triangles
+    [tri_offsets[g], tri_offsets[g + 1]) (a host sequence of n_geom + 1 ints)."""
+    import torch
+    out = ctypes.c_void_p()
+    prm = TreeParams(float(eta), int(leaf_size))
+    off = (ctypes.c_int64 * len(tri_offsets))(*[int(v) for v in tri_offsets])
+    _check(lib().hm_build_forest(_ptr(vertices, torch.float64), vertices.shape[0], _ptr(tris, torch.int32),
+                                 tris.shape[0], off, len(tri_offsets) - 1, ctypes.byref(prm), _stream(stream),
+                                 ctypes.byref(out)))
+    return out
+
+
+def hm_load_vector_geom(tree, sources, f, stream=None):
+    """sources: CUDA float64 [n_geom, n_per_geom, 3]; f: [n_per_geom, n]."""
+    import torch
+    _check(lib().hm_load_vector_geom(tree, _ptr(sources, torch.float64), int(sources.shape[1]),
+                                     _ptr(f, torch.float64), _stream(stream)))
+    return f
 
 
 def hm_assemble(tree, aca_eps=1e-6, aca_kmax=64, ss_order=8, factor_dtype=HM_F64, dense_dtype=HM_F64, stream=None):

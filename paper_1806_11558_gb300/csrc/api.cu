@@ -16,7 +16,8 @@ namespace hm {
 const char *last_error_cstr();
 long long launch_count();
 hm_tree *build_tree_impl(const double *d_V, int64_t nv, const int32_t *d_T, int64_t n, const hm_tree_params &prm,
-                         cudaStream_t s);
+                         const std::vector<int64_t> &goff, cudaStream_t s);
+void load_vector_geom_impl(const hm_tree *tr, const double *src, int nsrc, double *f, cudaStream_t s);
 void assemble_nearfield(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStream_t s, int *d_err,
                         double *sec_regular, double *sec_singular);
 void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStream_t s, double *sec, DBuf &uw,
@@ -80,7 +81,36 @@ hm_status hm_build_tree(const double *d_vertices, int64_t n_vertices, const int3
         if (n_vertices < 3 || n_vertices > (1LL << 30)) fail(HM_EINVAL, "n_vertices must be in [3, 2^30]");
         if (!(params->eta >= 0.0) || !std::isfinite(params->eta)) fail(HM_EINVAL, "eta must be finite and >= 0");
         if (params->leaf_size < 1 || params->leaf_size > 254) fail(HM_EINVAL, "leaf_size must be in [1, 254]");
-        *out = build_tree_impl(d_vertices, n_vertices, d_tris, n_tris, *params, (cudaStream_t)stream);
+        *out = build_tree_impl(d_vertices, n_vertices, d_tris, n_tris, *params, {}, (cudaStream_t)stream);
+    });
+}
+
+hm_status hm_build_forest(const double *d_vertices, int64_t n_vertices, const int32_t *d_tris, int64_t n_tris,
+                          const int64_t *h_tri_offsets, int32_t n_geom, const hm_tree_params *params,
+                          hm_stream_t stream, hm_tree **out) {
+    if (out) *out = nullptr;
+    return guard([&] {
+        if (!out || !d_vertices || !d_tris || !params || !h_tri_offsets) fail(HM_EINVAL, "NULL argument");
+        if (n_tris < 1 || n_tris > (1LL << 28)) fail(HM_EINVAL, "n_tris must be in [1, 2^28]");
+        if (n_vertices < 3 || n_vertices > (1LL << 30)) fail(HM_EINVAL, "n_vertices must be in [3, 2^30]");
+        if (n_geom < 1 || n_geom > 65536) fail(HM_EINVAL, "n_geom must be in [1, 65536]");
+        if (!(params->eta >= 0.0) || !std::isfinite(params->eta)) fail(HM_EINVAL, "eta must be finite and >= 0");
+        if (params->leaf_size < 1 || params->leaf_size > 254) fail(HM_EINVAL, "leaf_size must be in [1, 254]");
+        std::vector<int64_t> goff(h_tri_offsets, h_tri_offsets + n_geom + 1);
+        if (goff[0] != 0 || goff[n_geom] != n_tris) fail(HM_EINVAL, "tri_offsets must start at 0 and end at n_tris");
+        for (int g = 0; g < n_geom; ++g)
+            if (goff[g + 1] <= goff[g]) fail(HM_EINVAL, "geometry %d has no triangle", g);
+        *out = build_tree_impl(d_vertices, n_vertices, d_tris, n_tris, *params, goff, (cudaStream_t)stream);
+    });
+}
+
+hm_status hm_load_vector_geom(const hm_tree *tree, const double *d_sources, int32_t n_per_geom, double *d_f,
+                              hm_stream_t stream) {
+    return guard([&] {
+        if (!is_tree(tree)) fail(HM_EINVAL, "not a tree handle");
+        if (!d_sources || !d_f) fail(HM_EINVAL, "NULL argument");
+        if (n_per_geom < 1) fail(HM_EINVAL, "n_per_geom must be >= 1");
+        load_vector_geom_impl(tree, d_sources, n_per_geom, d_f, (cudaStream_t)stream);
     });
 }
 
@@ -266,6 +296,7 @@ hm_status hm_tree_get_info(const hm_tree *tree, hm_tree_info *info) {
         info->n_clusters = tree->n_clusters;
         info->depth = tree->depth;
         info->max_leaf = tree->max_leaf;
+        info->n_geom = tree->geom_off.size() > 1 ? (int32_t)tree->geom_off.size() - 1 : 1;
         info->n_dense = tree->n_dense;
         info->n_adm = tree->n_adm;
         info->dense_entries = tree->dense_true;

@@ -647,6 +647,47 @@ __global__ void load_vector_kernel(const double *pt, int64_t npad, int64_t n, co
     }
 }
 
+// per-geometry sources: f[s][perm[k]] with the sources of the geometry of k
+__global__ void load_vector_geom_kernel(const double *pt, int64_t npad, int64_t n, const int32_t *perm,
+                                        const int64_t *goff, int G, const double *src, int nsrc, QuadParams qp,
+                                        double *f) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = G;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (goff[mid] <= k) lo = mid;
+            else hi = mid;
+        }
+        const double *sg = src + (int64_t)lo * nsrc * 3;
+        const double area = pt[(int64_t)PT_AREA * npad + k];
+        const int32_t i = perm[k];
+        for (int s = 0; s < nsrc; ++s) {
+            const double px = sg[3 * s], py = sg[3 * s + 1], pz = sg[3 * s + 2];
+            double acc = 0.0;
+            for (int q = 0; q < NQ; ++q) {
+                const double dx = pt[(int64_t)q * npad + k] - px, dy = pt[(int64_t)(7 + q) * npad + k] - py,
+                             dz = pt[(int64_t)(14 + q) * npad + k] - pz;
+                acc += qp.w[q] / sqrt(dx * dx + dy * dy + dz * dz);
+            }
+            f[(int64_t)s * n + i] = area * acc * 0.079577471545947667884441881686257181;
+        }
+    }
+}
+
+void load_vector_geom_impl(const hm_tree *tr, const double *src, int nsrc, double *f, cudaStream_t s) {
+    const QuadParams qp = make_quad(1);
+    std::vector<int64_t> go = tr->geom_off;
+    if (go.size() < 2) go = {0, tr->n};
+    const int G = (int)go.size() - 1;
+    DBuf d_go;
+    d_go.alloc(sizeof(int64_t) * (G + 1));
+    HM_CUDA_CHECK(cudaMemcpyAsync(d_go.p, go.data(), sizeof(int64_t) * (G + 1), cudaMemcpyHostToDevice, s));
+    load_vector_geom_kernel<<<grid1d(tr->n), 256, 0, s>>>(tr->pt.as<double>(), tr->npad, tr->n, tr->perm.as<int32_t>(),
+                                                          d_go.as<int64_t>(), G, src, nsrc, qp, f);
+    HM_LAUNCH_CHECK();
+    HM_CUDA_CHECK(cudaStreamSynchronize(s));
+}
+
 void load_vector_impl(const hm_tree *tr, const double *src, int nsrc, double *f, cudaStream_t s) {
     const QuadParams qp = make_quad(1);
     load_vector_kernel<<<grid1d(tr->n), 256, 0, s>>>(tr->pt.as<double>(), tr->npad, tr->n, tr->perm.as<int32_t>(), src,

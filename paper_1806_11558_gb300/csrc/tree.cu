@@ -89,12 +89,15 @@ __device__ __forceinline__ uint64_t spread3(uint64_t v) {
     return v;
 }
 
-// q_a = min(2^21 - 1, floor((c_a - lo_a) * s)); code = x bits at 3b+2, y at 3b+1, z at 3b
-__global__ void morton_kernel(const double *cent, int64_t n, const double *grid, uint64_t *code, int32_t *idx) {
-    const double lo0 = grid[0], lo1 = grid[1], lo2 = grid[2], s = grid[3];
+// q_a = min(2^21 - 1, floor((c_a - lo_a) * s)); code = x bits at 3b+2, y at 3b+1, z at 3b.
+// grid[4 g ..]: the cube of geometry g (gid[i] = geometry of panel i; NULL = one geometry)
+__global__ void morton_kernel(const double *cent, int64_t n, const double *grid, const int32_t *gid, uint64_t *code,
+                              int32_t *idx) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double *gr = grid + 4 * (gid ? gid[i] : 0);
+        const double s = gr[3];
         uint64_t q[3];
-        const double lo[3] = {lo0, lo1, lo2};
+        const double lo[3] = {gr[0], gr[1], gr[2]};
         for (int d = 0; d < 3; ++d) {
             double t = floor(__dmul_rn(__dsub_rn(cent[3 * i + d], lo[d]), s));
             uint64_t v = (uint64_t)t;
@@ -103,6 +106,25 @@ __global__ void morton_kernel(const double *cent, int64_t n, const double *grid,
         code[i] = (spread3(q[0]) << 2) | (spread3(q[1]) << 1) | spread3(q[2]);
         idx[i] = (int32_t)i;
     }
+}
+
+// gid[i] = g for the panels [off[g], off[g + 1]) of the input order
+__global__ void geom_id_kernel(const int64_t *off, int G, int64_t n, int32_t *gid) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int lo = 0, hi = G;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (off[mid] <= i) lo = mid;
+            else hi = mid;
+        }
+        gid[i] = lo;
+    }
+}
+
+// key[m] = gid[perm[m]] (second, stable pass of the (geometry, code) sort)
+__global__ void gather_gid_kernel(const int32_t *gid, const int32_t *perm, int64_t n, uint64_t *key) {
+    for (int64_t m = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; m < n; m += (int64_t)gridDim.x * blockDim.x)
+        key[m] = (uint64_t)gid[perm[m]];
 }
 
 // panel table in Morton order
@@ -417,7 +439,10 @@ static unsigned grid_for(int64_t n, int threads = 256) {
 }
 
 hm_tree *build_tree_impl(const double *d_V, int64_t nv, const int32_t *d_T, int64_t n, const hm_tree_params &prm,
-                         cudaStream_t s) {
+                         const std::vector<int64_t> &goff_in, cudaStream_t s) {
+    // geometries: triangle ranges [goff[g], goff[g + 1]) of the input (one geometry by default)
+    std::vector<int64_t> goff = goff_in.empty() ? std::vector<int64_t>{0, n} : goff_in;
+    const int G = (int)goff.size() - 1;
     auto t0 = std::chrono::steady_clock::now();
     std::unique_ptr<hm_tree> tr(new hm_tree());
     tr->n = n;
@@ -448,25 +473,50 @@ hm_tree *build_tree_impl(const double *d_V, int64_t nv, const int32_t *d_T, int6
     cent.alloc(sizeof(double) * 3 * n);
     centroid_kernel<<<grid_for(n), 256, 0, s>>>(V, T.as<int32_t>(), n, cent.as<double>());
     HM_LAUNCH_CHECK();
+    // the bounding cube of every geometry
     const int nbb = 256;
     DBuf part, grid;
     part.alloc(sizeof(double) * 6 * nbb);
-    grid.alloc(sizeof(double) * 4);
-    bbox_partial_kernel<<<nbb, 256, 0, s>>>(cent.as<double>(), n, part.as<double>());
-    HM_LAUNCH_CHECK();
-    bbox_final_kernel<<<1, 32, 0, s>>>(part.as<double>(), nbb, grid.as<double>());
-    HM_LAUNCH_CHECK();
+    grid.alloc(sizeof(double) * 4 * G);
+    for (int g = 0; g < G; ++g) {
+        const int64_t cnt = goff[g + 1] - goff[g];
+        const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(nbb, (cnt + 255) / 256));
+        bbox_partial_kernel<<<nb, 256, 0, s>>>(cent.as<double>() + 3 * goff[g], cnt, part.as<double>());
+        HM_LAUNCH_CHECK();
+        bbox_final_kernel<<<1, 32, 0, s>>>(part.as<double>(), nb, grid.as<double>() + 4 * g);
+        HM_LAUNCH_CHECK();
+    }
+    DBuf gid;
+    if (G > 1) {
+        DBuf d_goff;
+        d_goff.alloc(sizeof(int64_t) * (G + 1));
+        HM_CUDA_CHECK(cudaMemcpyAsync(d_goff.p, goff.data(), sizeof(int64_t) * (G + 1), cudaMemcpyHostToDevice, s));
+        gid.alloc(sizeof(int32_t) * n);
+        geom_id_kernel<<<grid_for(n), 256, 0, s>>>(d_goff.as<int64_t>(), G, n, gid.as<int32_t>());
+        HM_LAUNCH_CHECK();
+        HM_CUDA_CHECK(cudaStreamSynchronize(s));
+    }
     DBuf code, code_tmp, idx_tmp;
     code.alloc(sizeof(uint64_t) * n);
     code_tmp.alloc(sizeof(uint64_t) * n);
     idx_tmp.alloc(sizeof(int32_t) * n);
     tr->perm.alloc(sizeof(int32_t) * n);
-    morton_kernel<<<grid_for(n), 256, 0, s>>>(cent.as<double>(), n, grid.as<double>(), code.as<uint64_t>(),
-                                             tr->perm.as<int32_t>());
+    morton_kernel<<<grid_for(n), 256, 0, s>>>(cent.as<double>(), n, grid.as<double>(), G > 1 ? gid.as<int32_t>() : nullptr,
+                                             code.as<uint64_t>(), tr->perm.as<int32_t>());
     HM_LAUNCH_CHECK();
-    // a3: stable sort by (code, original index)
+    // a3: stable sort by (code, original index), then, for several
+    // geometries, stable by geometry: the order is (geometry, code, index)
     radix_sort_u64(code.as<uint64_t>(), tr->perm.as<int32_t>(), code_tmp.as<uint64_t>(), idx_tmp.as<int32_t>(), n, 63,
                    s);
+    if (G > 1) {
+        int bits = 1;
+        while ((1 << bits) < G) ++bits;
+        gather_gid_kernel<<<grid_for(n), 256, 0, s>>>(gid.as<int32_t>(), tr->perm.as<int32_t>(), n, code.as<uint64_t>());
+        HM_LAUNCH_CHECK();
+        radix_sort_u64(code.as<uint64_t>(), tr->perm.as<int32_t>(), code_tmp.as<uint64_t>(), idx_tmp.as<int32_t>(), n,
+                       bits, s);
+    }
+    tr->geom_off = goff;
 
     // panel table in Morton order
     const QuadParams qp = make_quad(1);
@@ -486,11 +536,13 @@ hm_tree *build_tree_impl(const double *d_V, int64_t nv, const int32_t *d_T, int6
     // a4: cardinality-based cluster tree (integer only, host), boxes on device
     std::vector<int32_t> range, child;
     std::vector<int64_t> level_start;
-    range.push_back(0);
-    range.push_back((int32_t)n);
-    child.push_back(-1);
+    for (int g = 0; g < G; ++g) {  // one root per geometry
+        range.push_back((int32_t)goff[g]);
+        range.push_back((int32_t)goff[g + 1]);
+        child.push_back(-1);
+    }
     level_start.push_back(0);
-    int64_t lb = 0, le = 1;
+    int64_t lb = 0, le = G;
     int32_t max_leaf = 0;
     std::vector<int32_t> leaf_begin;
     while (lb < le) {
@@ -540,12 +592,14 @@ hm_tree *build_tree_impl(const double *d_V, int64_t nv, const int32_t *d_T, int6
     std::vector<DBuf> adm_parts, den_parts;
     std::vector<int64_t> adm_cnt, den_cnt;
     DBuf cand;
-    cand.alloc(sizeof(int32_t) * 2);
+    cand.alloc(sizeof(int32_t) * 2 * G);
     {
-        int32_t root[2] = {0, 0};
-        HM_CUDA_CHECK(cudaMemcpyAsync(cand.p, root, sizeof(root), cudaMemcpyHostToDevice, s));
+        std::vector<int32_t> roots(2 * G);  // (root_g, root_g): blocks never pair two geometries
+        for (int g = 0; g < G; ++g) roots[2 * g] = roots[2 * g + 1] = g;
+        HM_CUDA_CHECK(cudaMemcpyAsync(cand.p, roots.data(), sizeof(int32_t) * 2 * G, cudaMemcpyHostToDevice, s));
+        HM_CUDA_CHECK(cudaStreamSynchronize(s));
     }
-    int64_t ncand = 1;
+    int64_t ncand = G;
     const double eta2 = prm.eta * prm.eta;
     while (ncand > 0) {
         DBuf flag, ca, cd, cs;
