@@ -23,6 +23,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -446,6 +448,175 @@ def run_reference(args, rank, world):
             "e2e": {"value": val, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def _ev(torch):
+    return torch.cuda.Event(enable_timing=True)
+
+
+def run_large(torch, hm):
+    """Large workload: icosphere level 8 (1,310,720 panels), leaf 128, eps 1e-6,
+    16 point sources; FP64 form (16 FP64 solves in lockstep) against the
+    mixed form (FP32 near field + BF16 factors, inner solves through the
+    16-right-hand-side tensor-core product, FP64 refinement)."""
+    import meshgen
+    cfg = meshgen.config("large")
+    n = cfg["T"].shape[0]
+    V, T = torch.from_numpy(cfg["V"]).cuda(), torch.from_numpy(cfg["T"]).cuda()
+    e = [_ev(torch) for _ in range(8)]
+    hm.hm_trace_enable(True)
+    e[0].record()
+    tree = hm.hm_build_tree(V, T, eta=cfg["eta"], leaf_size=cfg["leaf_size"])
+    A = hm.hm_assemble(tree, aca_eps=cfg["aca_eps"], aca_kmax=64, ss_order=8, factor_dtype=hm.HM_BF16,
+                       dense_dtype=hm.HM_F32)
+    e[1].record()
+    src = torch.from_numpy(np.ascontiguousarray(cfg["sources"])).cuda()
+    F = torch.empty((16, n), dtype=torch.float64, device="cuda")
+    hm.hm_load_vector(tree, src, F)
+    X = torch.randn((16, n), dtype=torch.float64, device="cuda")
+    Y = torch.empty_like(X)
+    for _ in range(2):
+        hm.hm_matvec_block(A, X, Y, prec=hm.HM_BF16)
+    e[2].record()
+    for _ in range(5):
+        hm.hm_matvec_block(A, X, Y, prec=hm.HM_BF16)
+    e[3].record()
+    opts = dict(rel_tol=1e-12, restart=128, max_iter=5000, precond=1, batched=1)
+    Xm = torch.zeros_like(F)
+    e[4].record()
+    im = hm.hm_solve(A, F, Xm, refine=1, inner_dtype=hm.HM_BF16, inner_tol=1e-2, max_refine=80, **opts)
+    e[5].record()
+    X64 = torch.zeros_like(F)
+    i64 = hm.hm_solve(A, F, X64, **opts)
+    e[6].record()
+    torch.cuda.synchronize()
+    hm.hm_trace_enable(False)
+    mi = hm.hm_matrix_get_info(A)
+    mat_bytes = mi["dense_entries"] * 4 + mi["lr_entries"] * 2
+    blk_s = e[2].elapsed_time(e[3]) / 5e3
+    err = float(torch.max(torch.linalg.norm(Xm - X64, dim=1) / torch.linalg.norm(X64, dim=1)))
+    out = {"workload": "large: icosphere level 8, 1,310,720 panels, leaf 128, eta 1.5, ACA eps 1e-6, 16 sources",
+           "setup_s": e[0].elapsed_time(e[1]) / 1e3, "nearfield_s": mi["s_nearfield"], "singular_s": mi["s_singular"],
+           "aca_s": mi["s_aca"], "mean_rank": mi["mean_rank"],
+           "block_matvec_16rhs": {"s": blk_s, "matrix_gb": mat_bytes / 1e9, "gbs": mat_bytes / blk_s / 1e9},
+           "solve_mixed_16rhs_s": e[4].elapsed_time(e[5]) / 1e3, "mixed_iters": im.iters,
+           "mixed_refine_steps": im.refine_steps, "mixed_rel_resid": im.rel_resid,
+           "solve_fp64_16rhs_s": e[5].elapsed_time(e[6]) / 1e3, "fp64_iters": i64.iters,
+           "fp64_rel_resid": i64.rel_resid, "mixed_vs_fp64_max_rel_err": err,
+           "kernels": kernel_table(hm.hm_trace_read(), 1)}
+    hm.hm_free(A)
+    hm.hm_free(tree)
+    return out
+
+
+def run_batching(torch, hm):
+    """Batching workload: 64 stretched icospheres of levels 3..6 (1.79 M panels
+    in all), 4 exterior sources each, ACA eps 1e-5, FP32 copies; everything
+    in one forest: one launch per phase for all geometries, then 256 GMRES
+    (64 geometries x 4 right-hand sides) in lockstep with FP32 inner solves
+    through the tensor-core product and FP64 refinement to 1e-6."""
+    import meshgen
+    cfg = meshgen.config("batching")
+    n = cfg["T"].shape[0]
+    V, T = torch.from_numpy(cfg["V"]).cuda(), torch.from_numpy(cfg["T"]).cuda()
+    e = [_ev(torch) for _ in range(6)]
+    hm.hm_trace_enable(True)
+    e[0].record()
+    tree = hm.hm_build_forest(V, T, cfg["tri_offsets"].tolist(), eta=cfg["eta"], leaf_size=cfg["leaf_size"])
+    e[1].record()
+    A = hm.hm_assemble(tree, aca_eps=cfg["aca_eps"], aca_kmax=64, ss_order=8, factor_dtype=hm.HM_F32,
+                       dense_dtype=hm.HM_F32)
+    e[2].record()
+    src = torch.from_numpy(np.ascontiguousarray(cfg["sources"])).cuda()
+    F = torch.empty((4, n), dtype=torch.float64, device="cuda")
+    hm.hm_load_vector_geom(tree, src, F)
+    X = torch.zeros_like(F)
+    e[3].record()
+    info = hm.hm_solve(A, F, X, rel_tol=1e-6, restart=60, max_iter=5000, precond=1, batched=1, refine=1,
+                       inner_dtype=hm.HM_F32, inner_tol=1e-4, max_refine=40)
+    e[4].record()
+    torch.cuda.synchronize()
+    hm.hm_trace_enable(False)
+    mi = hm.hm_matrix_get_info(A)
+    out = {"workload": "batching: 64 stretched icospheres, levels 3..6, %d panels, 4 sources each, eps 1e-5" % n,
+           "tree_s": e[0].elapsed_time(e[1]) / 1e3, "assemble_s": e[1].elapsed_time(e[2]) / 1e3,
+           "aca_s": mi["s_aca"], "nearfield_s": mi["s_nearfield"], "solve_s": e[3].elapsed_time(e[4]) / 1e3,
+           "systems": 256, "lockstep_iters": info.iters, "refine_steps": info.refine_steps,
+           "max_rel_resid": info.rel_resid, "kernels": kernel_table(hm.hm_trace_read(), 1)}
+    hm.hm_free(A)
+    hm.hm_free(tree)
+    return out
+
+
+def run_differentiation(torch, hm):
+    """Differentiation workload: icosphere level 6, loss = mean squared misfit
+    of the potential at 1,024 points (radius 2.5) against a point source at
+    (0,0,3); gradients with respect to the Dirichlet data and the 81,920
+    per-panel density coefficients through the adjoint solve."""
+    import meshgen
+    from paper_1806_11558_gb300.autograd import misfit_loss
+    cfg = meshgen.config("differentiation")
+    n = cfg["T"].shape[0]
+    V, T = torch.from_numpy(cfg["V"]).cuda(), torch.from_numpy(cfg["T"]).cuda()
+    e = [_ev(torch) for _ in range(5)]
+    e[0].record()
+    tree = hm.hm_build_tree(V, T, eta=cfg["eta"], leaf_size=cfg["leaf_size"])
+    A = hm.hm_assemble(tree, aca_eps=cfg["aca_eps"], aca_kmax=64, ss_order=8)
+    e[1].record()
+    src = torch.from_numpy(np.ascontiguousarray(cfg["sources"])).cuda()
+    f = torch.empty((1, n), dtype=torch.float64, device="cuda")
+    hm.hm_load_vector(tree, src, f)
+    pts = torch.from_numpy(np.ascontiguousarray(cfg["points"])).cuda()
+    p = np.asarray(cfg["target_source"])
+    target = torch.from_numpy(1.0 / (4.0 * np.pi * np.linalg.norm(cfg["points"] - p[None, :], axis=1))).cuda()
+    opts = dict(rel_tol=1e-13, restart=128, max_iter=5000, precond=1)
+    # the pieces on their own (the first solve also builds the block-Jacobi inverses)
+    t = {}
+    for name, fn in (("solve_first", lambda: hm.hm_solve(A, f[0], torch.zeros_like(f[0]), **opts)),
+                     ("solve", lambda: hm.hm_solve(A, f[0], torch.zeros_like(f[0]), **opts)),
+                     ("potential", lambda: hm.hm_potential(tree, pts, f[0].contiguous())),
+                     ("solve_adjoint_first", lambda: hm.hm_solve(A, f[0], torch.zeros_like(f[0]), trans=1, **opts)),
+                     ("solve_adjoint", lambda: hm.hm_solve(A, f[0], torch.zeros_like(f[0]), trans=1, **opts))):
+        a, b = _ev(torch), _ev(torch)
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        t[name] = {"device_s": a.elapsed_time(b) / 1e3, "wall_s": time.perf_counter() - w0}
+    for it in range(2):  # the first pass also loads torch's own elementwise kernels; the second is timed
+        fd = f[0].clone().requires_grad_(True)
+        cd = torch.ones(n, dtype=torch.float64, device="cuda", requires_grad=True)
+        torch.cuda.synchronize()
+        hm.hm_trace_enable(it == 1)
+        e[2].record()
+        L = misfit_loss(A, tree, fd, cd, pts, target, opts)
+        e[3].record()
+        L.backward()
+        e[4].record()
+        torch.cuda.synchronize()
+    hm.hm_trace_enable(False)
+    out = {"workload": "differentiation: icosphere level 6 (81,920 panels), 1,024 evaluation points, FP64",
+           "setup_s": e[0].elapsed_time(e[1]) / 1e3, "forward_s": e[2].elapsed_time(e[3]) / 1e3,
+           "backward_s": e[3].elapsed_time(e[4]) / 1e3, "loss": float(L.detach()), "pieces": t,
+           "kernels": kernel_table(hm.hm_trace_read(), 1)}
+    hm.hm_free(A)
+    hm.hm_free(tree)
+    return out
+
+
+def run_workload(name):
+    import torch
+    import paper_1806_11558_gb300 as hm
+    from paper_1806_11558_gb300 import build as hb
+    hb.build()
+    fn = {"large": run_large, "batching": run_batching, "differentiation": run_differentiation}[name]
+    ck = Clocks(torch.cuda.current_device())
+    ck.start()
+    out = fn(torch, hm)
+    out["clocks"] = ck.stop()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -458,7 +629,12 @@ def main():
                          "for profiling and parity runs, not bench lines")
     ap.add_argument("--profile-step", action="store_true",
                     help="run exactly one step (no warm-up, no extras) and print its phase times")
+    ap.add_argument("--workload", default=None, choices=["large", "batching", "differentiation"],
+                    help="measure one of the other workloads once and print its numbers (not a bench line)")
     args = ap.parse_args()
+    if args.workload:
+        print(json.dumps(run_workload(args.workload)))
+        return
     global CASE
     CASE = args.case
     if CASE != "precision":
