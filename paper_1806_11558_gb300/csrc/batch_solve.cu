@@ -25,6 +25,7 @@ int64_t matvec_work_doubles(const hm_matrix *A);
 MatvecWork matvec_work_at(const hm_matrix *A, double *base);
 void matvec_mrhs_morton(const hm_matrix *A, hm_dtype prec, const float *X, double *Y, float *work, cudaStream_t s);
 int64_t mrhs_work_floats(const hm_matrix *A);
+void mrhs_prepare(const hm_matrix *A, hm_dtype prec, cudaStream_t s);
 void bj_setup(const hm_matrix *A, cudaStream_t s);
 void permute_to_morton(const hm_tree *tr, const double *x, double *xm, cudaStream_t s);
 void permute_from_morton(const hm_tree *tr, const double *ym, double alpha, double beta, double *y, cudaStream_t s);
@@ -256,7 +257,8 @@ struct Batch {
     DBuf items, iptr, V, W, Z, AX, part, h, h2, H, cs, sn, g, y, est, hn, nrm, act, cyc, kk, ones, mv, mvf;
     int64_t vstride;
 
-    Batch(const hm_matrix *A_, int R_, int m_, bool pc, cudaStream_t s) : A(A_), R(R_), m(m_), precond(pc) {
+    Batch(const hm_matrix *A_, int R_, int m_, bool pc, hm_dtype inner, cudaStream_t s)
+        : A(A_), R(R_), m(m_), precond(pc) {
         const hm_tree *tr = A->tree;
         n = tr->n;
         std::vector<int64_t> go = tr->geom_off;
@@ -303,7 +305,10 @@ struct Batch {
             HM_CUDA_CHECK(cudaStreamSynchronize(s));
         }
         mv.alloc(sizeof(double) * matvec_work_doubles(A));
-        if (R > 1) mvf.alloc(sizeof(float) * mrhs_work_floats(A));
+        if (R > 1 && inner != HM_F64) {
+            mrhs_prepare(A, inner, s);
+            mvf.alloc(sizeof(float) * mrhs_work_floats(A));
+        }
     }
     unsigned nitems() const { return (unsigned)items_h.size(); }
 
@@ -489,7 +494,7 @@ hm_status solve_batched(const hm_matrix *A, int nrhs, const double *b_orig, doub
     HM_CUDA_CHECK(cudaMemsetAsync(x.p, 0, sizeof(double) * vs, s));
     const bool pc = p.precond == 1;
     if (pc) bj_setup(A, s);
-    Batch B(A, nrhs, p.restart, pc, s);
+    Batch B(A, nrhs, p.restart, pc, p.refine ? p.inner_dtype : HM_F64, s);
     const int S = B.S;
     int iters = 0, cycles = 0, steps = 0;
     std::vector<double> bn2 = B.norms2(b.as<double>(), s);

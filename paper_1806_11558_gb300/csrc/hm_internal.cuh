@@ -285,6 +285,14 @@ struct hm_matrix {
     hm::DBuf dense_t, dense32_t, pofs_t, tidx_t;
     int64_t n_partials_t = 0;
     bool trans_ready = false;
+    // multi-RHS projection (built on first use): the W factors of the
+    // low-precision copy grouped by block column cluster (one row-major panel
+    // |sigma| x K_sigma per cluster sigma, the blocks with that column cluster
+    // side by side), the t index of every panel column (-1 = padding) and the
+    // list of 64-column tiles (panel, first column)
+    hm::DBuf bcp, bcp_off, bcp_K, bcp_rows, bcp_col0, bcp_tidx, bcp_tiles, bcp_red;
+    int64_t bcp_ngroups = 0, bcp_ntiles = 0, bcp_nred = 0, bcp_nslots = 0;
+    int bcp_dtype = -1;  // hm_dtype of bcp, -1 = not built
     int64_t wp_entries = 0;
     int64_t n_partials = 0;  // length of the partial-projection vector
     // block-Jacobi preconditioner: inverse of each leaf cluster's diagonal block

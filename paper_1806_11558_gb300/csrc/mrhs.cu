@@ -7,10 +7,12 @@
 // entry, above what the FP32 CUDA cores deliver at HBM speed, so the three
 // passes of the product become small GEMMs on the tensor cores
 // (mma.sync m16n8k16, BF16 operands, FP32 accumulation):
-//   col_mrhs_kernel : P_kappa (16 x K_kappa) = X_kappa^T W~_kappa per leaf
-//                     column cluster (A = X^T from shared memory, B = panel
-//                     tile staged by cp.async and read with ldmatrix.trans);
-//   tsum_mrhs_kernel: t_b = sum of the partials over the clusters of b;
+//   col_bcp_kernel  : t_b (k_b x 16) = W_b^T X_sigma for every block, from
+//                     the W factors regrouped by block column cluster sigma
+//                     (one panel |sigma| x K_sigma per cluster, so t needs no
+//                     partial sums): per tile of 64 panel columns, A = X^T
+//                     from shared memory, B = panel tile staged by cp.async
+//                     and read with ldmatrix.trans;
 //   row_mrhs_kernel : Y_rho (|rho| x 16) = P_rho X(colidx) + U~_rho T(tidx)
 //                     per leaf row cluster (A = panel rows loaded straight
 //                     from HBM with 16-byte loads, B = gathered rows staged in
@@ -22,10 +24,13 @@
 // about 16 significant bits (relative error ~2^-16), enough for the inner
 // solves of the refinement (tolerance 1e-4).  No floating-point atomics.
 //
-// Layout: X [n][16] FP32 and Y [n][16] FP64 in Morton order, the partials
-// [P][16], t [K][16] (rows = panel columns / t entries, 16 right-hand sides
-// contiguous).
+// Layout: X [n][16] FP32 and Y [n][16] FP64 in Morton order, t [K][16]
+// (16 right-hand sides contiguous).
 #include <cuda_bf16.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
 
 #include "hm_internal.cuh"
 
@@ -66,11 +71,6 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool pr
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-// ---------------------------------------------------------------------------
-// col_mrhs_kernel: partials of X_kappa^T W~_kappa, one CTA per leaf column
-// cluster.  The W panel (|kappa| x Kw, row-major, BF16 or FP32) is walked in
-// tiles of 64 columns; each warp owns 8 columns of a tile.
-// ---------------------------------------------------------------------------
 constexpr int CM_THREADS = 256;
 constexpr int CM_COLS = 64;                 // panel columns per tile
 constexpr int CM_TSTRIDE = CM_COLS + 8;     // bf16 per tile row in shared memory (16-byte aligned rows)
@@ -85,46 +85,278 @@ template <> struct ColTile<float> {
     static constexpr int NSPLIT = 2;
 };
 
-template <class TF>
-__global__ void __launch_bounds__(CM_THREADS) col_mrhs_kernel(const int32_t *__restrict__ leaf_begin,
-                                                              const int64_t *__restrict__ wp_off,
-                                                              const int32_t *__restrict__ wp_K,
-                                                              const int64_t *__restrict__ wp_colptr,
-                                                              const TF *__restrict__ wp, const float *__restrict__ X,
-                                                              float *__restrict__ P) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    const int64_t kap = blockIdx.x;
-    const int32_t c0 = leaf_begin[kap], mc = leaf_begin[kap + 1] - c0;
-    const int kpad = (mc + 15) & ~15;
-    const int Kw = wp_K[kap];
-    const TF *W = wp + wp_off[kap];
-    float *out = P + wp_colptr[kap] * MR;
+// ---------------------------------------------------------------------------
+// row_mrhs_kernel: Y_rho = P_rho X(colidx) + U~_rho T(tidx), one CTA (4 warps)
+// per leaf row cluster, 16 MT rows per pass.  The panels are walked in slices
+// of 64 columns through a 3-stage cp.async pipeline: the slice's panel rows
+// and its gathered rows of X / T (as BF16 hi and lo, [column][rhs]) land in
+// shared memory while the previous slices are multiplied; warp w owns the
+// 16 columns 16 w .. 16 w + 15 of every slice (A fragments by LDS / ldmatrix,
+// B fragments by ldmatrix.trans), and the four warps' sums are added in a
+// fixed order at the end.
+// ---------------------------------------------------------------------------
+constexpr int RP_THREADS = 128;
+constexpr int RP_WARPS = RP_THREADS / 32;
+constexpr int RP_KS = 64;          // panel columns per slice
+constexpr int RP_STAGES = 3;
+constexpr int RP_APAD = 8;         // elements of padding per staged panel row
+constexpr int RP_BSTRIDE = MR + 8; // bf16 per staged column of X / T (48 bytes)
+
+__device__ __forceinline__ void ldmatrix_x4(uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3, const void *p) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(a));
+}
+
+template <int MT, class TP> struct RpStage {
+    static constexpr int A_BYTES = 16 * MT * (RP_KS + RP_APAD) * (int)sizeof(TP);
+    static constexpr int B_BYTES = 2 * RP_KS * RP_BSTRIDE * 2;
+    static constexpr int BYTES = A_BYTES + B_BYTES;
+};
+
+// the gathered row indices this thread needs for the slice at column c0
+// (columns (tid >> 2) and (tid >> 2) + 32), loaded ahead of their use
+__device__ __forceinline__ void rp_idx(const int32_t *__restrict__ idx, int K, int c0, int (&ir)[2]) {
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const int col = c0 + (threadIdx.x >> 2) + 32 * j;
+        ir[j] = col < K ? __ldg(idx + col) : 0;
+    }
+}
+
+template <int MT, class TP>
+__device__ __forceinline__ void rp_load(unsigned char *stage, const TP *__restrict__ Pn, int K, int rows_valid, int c0,
+                                        const int (&ir)[2], const __nv_bfloat16 *__restrict__ Zh,
+                                        const __nv_bfloat16 *__restrict__ Zl) {
+    TP *sA = reinterpret_cast<TP *>(stage);
+    __nv_bfloat16 *sBh = reinterpret_cast<__nv_bfloat16 *>(stage + RpStage<MT, TP>::A_BYTES);
+    __nv_bfloat16 *sBl = sBh + RP_KS * RP_BSTRIDE;
+    constexpr int PER = 16 / (int)sizeof(TP);  // elements per 16-byte copy
+    constexpr int VPR = RP_KS / PER;           // copies per row
+    for (int e = threadIdx.x; e < 16 * MT * VPR; e += RP_THREADS) {
+        const int r = e / VPR, v = e - (e / VPR) * VPR;
+        const int col = c0 + PER * v;
+        const bool ok = r < rows_valid && col < K;
+        cp_async16(sA + r * (RP_KS + RP_APAD) + PER * v, ok ? (const void *)(Pn + (int64_t)r * K + col) : (const void *)Pn,
+                   ok);
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const int c = (threadIdx.x >> 2) + 32 * j, q = threadIdx.x & 3;  // q: hi / lo x first / second 8 rhs
+        const int col = c0 + c;
+        const bool ok = col < K;
+        const __nv_bfloat16 *src = ((q & 2) ? Zl : Zh) + (int64_t)ir[j] * MR + 8 * (q & 1);
+        __nv_bfloat16 *dst = ((q & 2) ? sBl : sBh) + c * RP_BSTRIDE + 8 * (q & 1);
+        cp_async16(dst, ok ? (const void *)src : (const void *)Zh, ok);
+    }
+}
+
+template <int MT, class TP>
+__device__ __forceinline__ void rp_compute(const unsigned char *stage, float (&acc)[MT][2][4]) {
+    const TP *sA = reinterpret_cast<const TP *>(stage);
+    const __nv_bfloat16 *sBh = reinterpret_cast<const __nv_bfloat16 *>(stage + RpStage<MT, TP>::A_BYTES);
+    const __nv_bfloat16 *sBl = sBh + RP_KS * RP_BSTRIDE;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
-    // shared: X^T hi / lo [16][kpad + 8] bf16, then the tile(s) [kpad][CM_TSTRIDE] bf16 (x NSPLIT), then for
-    // FP32 panels the FP32 staging tile [kpad][CM_COLS]
-    const int xs = kpad + 8;
+    const int kb = 16 * warp;
+    uint32_t bh[2][2], bl[2][2];
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+        ldmatrix_x2_trans(bh[nt][0], bh[nt][1], sBh + (kb + (lane & 15)) * RP_BSTRIDE + 8 * nt);
+        ldmatrix_x2_trans(bl[nt][0], bl[nt][1], sBl + (kb + (lane & 15)) * RP_BSTRIDE + 8 * nt);
+    }
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt) {
+        if constexpr (sizeof(TP) == 4) {
+            const float *r0 = reinterpret_cast<const float *>(sA) + (16 * mt + g) * (RP_KS + RP_APAD) + kb + 2 * t;
+            const float *r1 = r0 + 8 * (RP_KS + RP_APAD);
+            const float2 p0 = *reinterpret_cast<const float2 *>(r0), p1 = *reinterpret_cast<const float2 *>(r0 + 8);
+            const float2 q0 = *reinterpret_cast<const float2 *>(r1), q1 = *reinterpret_cast<const float2 *>(r1 + 8);
+            float h[8], l[8];
+            split_bf16(p0.x, h[0], l[0]);
+            split_bf16(p0.y, h[1], l[1]);
+            split_bf16(q0.x, h[2], l[2]);
+            split_bf16(q0.y, h[3], l[3]);
+            split_bf16(p1.x, h[4], l[4]);
+            split_bf16(p1.y, h[5], l[5]);
+            split_bf16(q1.x, h[6], l[6]);
+            split_bf16(q1.y, h[7], l[7]);
+            // A regs: (row g, k 2t..), (row g+8, k 2t..), (row g, k 2t+8..), (row g+8, k 2t+8..)
+            const uint32_t ah0 = pack_bf16(h[0], h[1]), ah1 = pack_bf16(h[2], h[3]), ah2 = pack_bf16(h[4], h[5]),
+                           ah3 = pack_bf16(h[6], h[7]);
+            const uint32_t al0 = pack_bf16(l[0], l[1]), al1 = pack_bf16(l[2], l[3]), al2 = pack_bf16(l[4], l[5]),
+                           al3 = pack_bf16(l[6], l[7]);
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                mma_bf16(acc[mt][nt], ah0, ah1, ah2, ah3, bh[nt][0], bh[nt][1]);
+                mma_bf16(acc[mt][nt], ah0, ah1, ah2, ah3, bl[nt][0], bl[nt][1]);
+                mma_bf16(acc[mt][nt], al0, al1, al2, al3, bh[nt][0], bh[nt][1]);
+            }
+        } else {
+            // ldmatrix.x4: matrices (rows 0-7, k 0-7), (rows 8-15, k 0-7), (rows 0-7, k 8-15), (rows 8-15, k 8-15)
+            const __nv_bfloat16 *base = reinterpret_cast<const __nv_bfloat16 *>(sA) +
+                                        (16 * mt + (lane & 15)) * (RP_KS + RP_APAD) + kb + 8 * (lane >> 4);
+            uint32_t a0, a1, a2, a3;
+            ldmatrix_x4(a0, a1, a2, a3, base);
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                mma_bf16(acc[mt][nt], a0, a1, a2, a3, bh[nt][0], bh[nt][1]);
+                mma_bf16(acc[mt][nt], a0, a1, a2, a3, bl[nt][0], bl[nt][1]);
+            }
+        }
+    }
+}
+
+template <int MT, class TP>
+__device__ __forceinline__ void rp_panel(unsigned char *sm, const TP *__restrict__ Pn, int K, int rows_valid,
+                                         const int32_t *__restrict__ idx, const __nv_bfloat16 *__restrict__ Zh,
+                                         const __nv_bfloat16 *__restrict__ Zl, float (&acc)[MT][2][4]) {
+    constexpr int SB = RpStage<MT, TP>::BYTES;
+    const int ns = (K + RP_KS - 1) / RP_KS;
+    int ir[2];
+#pragma unroll
+    for (int st = 0; st < RP_STAGES - 1; ++st) {
+        if (st < ns) {
+            rp_idx(idx, K, st * RP_KS, ir);
+            rp_load<MT, TP>(sm + st * SB, Pn, K, rows_valid, st * RP_KS, ir, Zh, Zl);
+        }
+        cp_async_commit();
+    }
+    rp_idx(idx, K, (RP_STAGES - 1) * RP_KS, ir);  // indices of the next slice to load
+    for (int sl = 0; sl < ns; ++sl) {
+        cp_async_wait<RP_STAGES - 2>();
+        __syncthreads();
+        const int nx = sl + RP_STAGES - 1;
+        if (nx < ns) rp_load<MT, TP>(sm + (nx % RP_STAGES) * SB, Pn, K, rows_valid, nx * RP_KS, ir, Zh, Zl);
+        cp_async_commit();
+        rp_idx(idx, K, (nx + 1) * RP_KS, ir);  // consumed one iteration later
+        rp_compute<MT, TP>(sm + (sl % RP_STAGES) * SB, acc);
+    }
+    cp_async_wait<0>();
+    __syncthreads();
+}
+
+template <int MT, class TF>
+__global__ void __launch_bounds__(RP_THREADS) row_mrhs_kernel(
+    const int32_t *__restrict__ leaf_begin, const int64_t *__restrict__ rho_off, const int32_t *__restrict__ rho_K,
+    const int64_t *__restrict__ rho_colptr, const int32_t *__restrict__ colidx, const float *__restrict__ dense,
+    const int64_t *__restrict__ up_off, const int32_t *__restrict__ up_K, const int64_t *__restrict__ up_colptr,
+    const int32_t *__restrict__ tidx, const TF *__restrict__ up, const __nv_bfloat16 *__restrict__ Th,
+    const __nv_bfloat16 *__restrict__ Tl, const __nv_bfloat16 *__restrict__ Xh, const __nv_bfloat16 *__restrict__ Xl,
+    double *__restrict__ Y) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int64_t rho = blockIdx.x;
+    const int32_t r0 = leaf_begin[rho], mr = leaf_begin[rho + 1] - r0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+    const int Kd = rho_K[rho], Ku = up_K[rho];
+    for (int r0t = 0; r0t < mr; r0t += 16 * MT) {
+        const int rows = min(16 * MT, mr - r0t);
+        float acc[MT][2][4];
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.0f;
+        rp_panel<MT, float>(sm, dense + rho_off[rho] + (int64_t)r0t * Kd, Kd, rows, colidx + rho_colptr[rho], Xh, Xl,
+                            acc);
+        rp_panel<MT, TF>(sm, up + up_off[rho] + (int64_t)r0t * Ku, Ku, rows, tidx + up_colptr[rho], Th, Tl, acc);
+        // per-warp sums -> shared memory -> fixed-order sum over the 4 warps
+        float *red = reinterpret_cast<float *>(sm);
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                float *base = red + warp * (16 * MT) * MR;
+                const int ra = 16 * mt + g, col = 8 * nt + 2 * t;
+                base[ra * MR + col] = acc[mt][nt][0];
+                base[ra * MR + col + 1] = acc[mt][nt][1];
+                base[(ra + 8) * MR + col] = acc[mt][nt][2];
+                base[(ra + 8) * MR + col + 1] = acc[mt][nt][3];
+            }
+        __syncthreads();
+        for (int e = threadIdx.x; e < rows * MR; e += RP_THREADS) {
+            float sacc = 0.0f;
+            for (int w = 0; w < RP_WARPS; ++w) sacc += red[w * (16 * MT) * MR + e];
+            Y[(int64_t)(r0 + r0t) * MR + e] = (double)sacc;
+        }
+        __syncthreads();
+    }
+}
+
+// Xh + Xl = X (BF16 pair of every FP32 value)
+__global__ void split_rows_kernel(const float *__restrict__ X, int64_t n, __nv_bfloat16 *__restrict__ Xh,
+                                  __nv_bfloat16 *__restrict__ Xl) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        float h, l;
+        split_bf16(X[e], h, l);
+        Xh[e] = __float2bfloat16_rn(h);
+        Xl[e] = __float2bfloat16_rn(l);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// col_bcp_kernel: t_b = X_sigma^T W_b for every block, straight from the
+// panels grouped by block column cluster (no partial sums): one CTA per tile
+// of 64 panel columns; the panel rows (|sigma|, up to thousands) are walked
+// in chunks of BC_ROWS, with X_sigma^T (split hi / lo) and the W tile staged
+// in shared memory; each warp owns 8 columns.
+// ---------------------------------------------------------------------------
+constexpr int BC_ROWS = 128;
+
+// one work item: (panel, first column, first row, end row, partial slot or -1)
+constexpr int BC_ITEM = 5;
+constexpr int BC_SPLIT = 1024;  // rows of one work item (taller panels are split, partials added after)
+
+// the t rows of 64 panel columns as BF16 pairs (hi + lo = value)
+__device__ __forceinline__ void store_t_pair(__nv_bfloat16 *Th, __nv_bfloat16 *Tl, int64_t ti, int r, float v) {
+    float h, l;
+    split_bf16(v, h, l);
+    Th[ti * MR + r] = __float2bfloat16_rn(h);
+    Tl[ti * MR + r] = __float2bfloat16_rn(l);
+}
+
+template <class TF>
+__global__ void __launch_bounds__(CM_THREADS) col_bcp_kernel(const int32_t *__restrict__ items,
+                                                             const int64_t *__restrict__ off,
+                                                             const int32_t *__restrict__ Kg,
+                                                             const int32_t *__restrict__ rows,
+                                                             const int64_t *__restrict__ col0,
+                                                             const int32_t *__restrict__ tidx,
+                                                             const TF *__restrict__ bcp, const float *__restrict__ X,
+                                                             __nv_bfloat16 *__restrict__ Th,
+                                                             __nv_bfloat16 *__restrict__ Tl,
+                                                             float *__restrict__ part) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int32_t *it = items + BC_ITEM * (int64_t)blockIdx.x;
+    const int grp = it[0], n0 = it[1], slot = it[4];
+    const int32_t r0 = rows[2 * grp] + it[2], nr = it[3] - it[2];
+    const int K = Kg[grp];
+    const TF *W = bcp + off[grp] + (int64_t)it[2] * K;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+    constexpr int xs = BC_ROWS + 8;
     __nv_bfloat16 *sXh = reinterpret_cast<__nv_bfloat16 *>(sm);
     __nv_bfloat16 *sXl = sXh + MR * xs;
     __nv_bfloat16 *sT = sXl + MR * xs;
-    float *sF = reinterpret_cast<float *>(sT + ColTile<TF>::NSPLIT * kpad * CM_TSTRIDE);
-    for (int e = threadIdx.x; e < MR * kpad; e += CM_THREADS) {
-        const int r = e / kpad, k = e - (e / kpad) * kpad;
-        float h = 0.0f, l = 0.0f;
-        if (k < mc) split_bf16(X[(int64_t)(c0 + k) * MR + r], h, l);
-        sXh[r * xs + k] = __float2bfloat16_rn(h);
-        sXl[r * xs + k] = __float2bfloat16_rn(l);
-    }
-    __syncthreads();
-    const int nk = kpad / 16;
-    for (int n0 = 0; n0 < Kw; n0 += CM_COLS) {
-        // stage the tile rows [0, kpad) x columns [n0, n0 + 64); rows >= mc and columns >= Kw read as 0
+    float *sF = reinterpret_cast<float *>(sT + ColTile<TF>::NSPLIT * BC_ROWS * CM_TSTRIDE);
+    float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int k0 = 0; k0 < nr; k0 += BC_ROWS) {
+        const int kc = min(BC_ROWS, nr - k0), kpad = (kc + 15) & ~15;
+        __syncthreads();
+        for (int e = threadIdx.x; e < MR * kpad; e += CM_THREADS) {
+            const int r = e / kpad, k = e - (e / kpad) * kpad;
+            float h = 0.0f, l = 0.0f;
+            if (k < kc) split_bf16(X[(int64_t)(r0 + k0 + k) * MR + r], h, l);
+            sXh[r * xs + k] = __float2bfloat16_rn(h);
+            sXl[r * xs + k] = __float2bfloat16_rn(l);
+        }
         if constexpr (sizeof(TF) == 2) {
             for (int e = threadIdx.x; e < kpad * (CM_COLS / 8); e += CM_THREADS) {
                 const int k = e / (CM_COLS / 8), v = e - (e / (CM_COLS / 8)) * (CM_COLS / 8);
                 const int col = n0 + 8 * v;
-                const bool ok = k < mc && col < Kw;
-                cp_async16(sT + k * CM_TSTRIDE + 8 * v, ok ? (const void *)(W + (int64_t)k * Kw + col) : (const void *)W,
-                           ok);
+                const bool ok = k < kc && col < K;
+                cp_async16(sT + k * CM_TSTRIDE + 8 * v,
+                           ok ? (const void *)(W + (int64_t)(k0 + k) * K + col) : (const void *)W, ok);
             }
             cp_async_commit();
             cp_async_wait<0>();
@@ -132,9 +364,9 @@ __global__ void __launch_bounds__(CM_THREADS) col_mrhs_kernel(const int32_t *__r
             for (int e = threadIdx.x; e < kpad * (CM_COLS / 4); e += CM_THREADS) {
                 const int k = e / (CM_COLS / 4), v = e - (e / (CM_COLS / 4)) * (CM_COLS / 4);
                 const int col = n0 + 4 * v;
-                const bool ok = k < mc && col < Kw;
-                cp_async16(sF + k * CM_COLS + 4 * v, ok ? (const void *)(W + (int64_t)k * Kw + col) : (const void *)W,
-                           ok);
+                const bool ok = k < kc && col < K;
+                cp_async16(sF + k * CM_COLS + 4 * v,
+                           ok ? (const void *)(W + (int64_t)(k0 + k) * K + col) : (const void *)W, ok);
             }
             cp_async_commit();
             cp_async_wait<0>();
@@ -144,14 +376,11 @@ __global__ void __launch_bounds__(CM_THREADS) col_mrhs_kernel(const int32_t *__r
                 float h, l;
                 split_bf16(sF[e], h, l);
                 sT[k * CM_TSTRIDE + c] = __float2bfloat16_rn(h);
-                sT[kpad * CM_TSTRIDE + k * CM_TSTRIDE + c] = __float2bfloat16_rn(l);
+                sT[BC_ROWS * CM_TSTRIDE + k * CM_TSTRIDE + c] = __float2bfloat16_rn(l);
             }
         }
         __syncthreads();
-        float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        for (int ks = 0; ks < nk; ++ks) {
-            // A = X^T (16 rhs x 16 k): rows g, g + 8; k pairs (2t, 2t+1), (2t+8, 2t+9)
-            const int kb = ks * 16;
+        for (int kb = 0; kb < kpad; kb += 16) {
             const uint32_t ah0 = *reinterpret_cast<const uint32_t *>(sXh + g * xs + kb + 2 * t);
             const uint32_t ah1 = *reinterpret_cast<const uint32_t *>(sXh + (g + 8) * xs + kb + 2 * t);
             const uint32_t ah2 = *reinterpret_cast<const uint32_t *>(sXh + g * xs + kb + 2 * t + 8);
@@ -160,257 +389,106 @@ __global__ void __launch_bounds__(CM_THREADS) col_mrhs_kernel(const int32_t *__r
             const uint32_t al1 = *reinterpret_cast<const uint32_t *>(sXl + (g + 8) * xs + kb + 2 * t);
             const uint32_t al2 = *reinterpret_cast<const uint32_t *>(sXl + g * xs + kb + 2 * t + 8);
             const uint32_t al3 = *reinterpret_cast<const uint32_t *>(sXl + (g + 8) * xs + kb + 2 * t + 8);
-            // B = tile rows kb..kb+15, columns 8 warp .. +7: ldmatrix.trans, row addresses from lanes 0..15
             uint32_t b0, b1;
             ldmatrix_x2_trans(b0, b1, sT + (kb + (lane & 15)) * CM_TSTRIDE + 8 * warp);
             mma_bf16(d, ah0, ah1, ah2, ah3, b0, b1);
             mma_bf16(d, al0, al1, al2, al3, b0, b1);
             if constexpr (ColTile<TF>::NSPLIT == 2) {
                 uint32_t e0, e1;
-                ldmatrix_x2_trans(e0, e1, sT + kpad * CM_TSTRIDE + (kb + (lane & 15)) * CM_TSTRIDE + 8 * warp);
+                ldmatrix_x2_trans(e0, e1, sT + BC_ROWS * CM_TSTRIDE + (kb + (lane & 15)) * CM_TSTRIDE + 8 * warp);
                 mma_bf16(d, ah0, ah1, ah2, ah3, e0, e1);
             }
         }
-        // D (16 rhs x 8 columns): rows g, g + 8, columns 2t, 2t + 1 of this warp's 8
-        const int col = n0 + 8 * warp + 2 * t;
-        if (col < Kw) {
-            out[(int64_t)col * MR + g] = d[0];
-            out[(int64_t)col * MR + g + 8] = d[2];
+    }
+    // D (16 rhs x 8 columns of this warp) -> t rows of those columns, or the partial of this row range
+    const int cl = 8 * warp + 2 * t, col = n0 + cl;
+    if (slot >= 0) {
+        float *pp = part + (int64_t)slot * CM_COLS * MR;
+        pp[cl * MR + g] = d[0];
+        pp[cl * MR + g + 8] = d[2];
+        pp[(cl + 1) * MR + g] = d[1];
+        pp[(cl + 1) * MR + g + 8] = d[3];
+        return;
+    }
+    const int64_t cbase = col0[grp];
+    if (col < K) {
+        const int32_t ti = tidx[cbase + col];
+        if (ti >= 0) {
+            store_t_pair(Th, Tl, ti, g, d[0]);
+            store_t_pair(Th, Tl, ti, g + 8, d[2]);
         }
-        if (col + 1 < Kw) {
-            out[(int64_t)(col + 1) * MR + g] = d[1];
-            out[(int64_t)(col + 1) * MR + g + 8] = d[3];
+    }
+    if (col + 1 < K) {
+        const int32_t ti = tidx[cbase + col + 1];
+        if (ti >= 0) {
+            store_t_pair(Th, Tl, ti, g, d[1]);
+            store_t_pair(Th, Tl, ti, g + 8, d[3]);
         }
-        __syncthreads();
     }
 }
 
-// ---------------------------------------------------------------------------
-// tsum_mrhs_kernel: t_b(l, :) = sum over the clusters of b of the partials,
-// in increasing cluster order.  Two t entries per warp (16 lanes each, one
-// lane per right-hand side); the block of an entry is found from the table
-// of the block holding every 32nd entry.
-// ---------------------------------------------------------------------------
-__global__ void tsum_mrhs_kernel(int64_t na, int64_t nt, const int32_t *__restrict__ b0tab,
-                                 const int64_t *__restrict__ t_off, const int64_t *__restrict__ bptr,
-                                 const int64_t *__restrict__ pofs, const float *__restrict__ P,
-                                 float *__restrict__ T) {
-    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t q0 = tid; q0 < nt * MR; q0 += nthreads) {
-        const int64_t e = q0 / MR;
-        const int r = (int)(q0 - e * MR);
-        int64_t b = b0tab[e / 32];
-        while (b + 1 < na && t_off[b + 1] <= e) ++b;
-        const int l = (int)(e - t_off[b]);
+// tiles whose rows were split: t = sum of the partials in row order
+// (red: (panel, first column, first slot, slots) per tile)
+__global__ void bcp_reduce_kernel(const int32_t *__restrict__ red, const int32_t *__restrict__ Kg,
+                                  const int64_t *__restrict__ col0, const int32_t *__restrict__ tidx,
+                                  const float *__restrict__ part, __nv_bfloat16 *__restrict__ Th,
+                                  __nv_bfloat16 *__restrict__ Tl) {
+    const int32_t *rd = red + 4 * (int64_t)blockIdx.x;
+    const int grp = rd[0], n0 = rd[1], s0 = rd[2], ns = rd[3];
+    const int K = Kg[grp];
+    for (int e = threadIdx.x; e < CM_COLS * MR; e += blockDim.x) {
+        const int cl = e / MR, r = e - (e / MR) * MR;
+        if (n0 + cl >= K) continue;
+        const int32_t ti = tidx[col0[grp] + n0 + cl];
+        if (ti < 0) continue;
         float acc = 0.0f;
-        for (int64_t q = bptr[b]; q < bptr[b + 1]; ++q) acc += P[(pofs[q] + l) * MR + r];
-        T[e * MR + r] = acc;
+        for (int k = 0; k < ns; ++k) acc += part[((int64_t)(s0 + k) * CM_COLS + cl) * MR + r];
+        store_t_pair(Th, Tl, ti, r, acc);
     }
 }
 
-// ---------------------------------------------------------------------------
-// row_mrhs_kernel: Y_rho = P_rho X(colidx) + U~_rho T(tidx), one CTA per leaf
-// row cluster, MT tiles of 16 rows per pass.  Per staged chunk of 256 panel
-// columns every warp takes 32 of them: its A fragments come straight from the
-// panel rows with one 16-byte load per row and 16 (FP32) or 32 (BF16)
-// columns, the k order inside a 16-k step permuted consistently in A and B
-// (B read from the staged chunk at the same physical columns).
-// ---------------------------------------------------------------------------
-constexpr int RM_THREADS = 256;
-constexpr int RM_WARPS = RM_THREADS / 32;
-constexpr int RM_CHUNK = 256;           // panel columns staged per pass
-constexpr int RM_BSTRIDE = RM_CHUNK + 16;  // bf16 per right-hand side row in shared memory
-
-// FP32 panel: A fragment of rows (row g, row g + 8) for physical columns
-// 4t .. 4t + 3 of a 16-column group, split hi / lo
-__device__ __forceinline__ void a_frag_f32(const float *r0, const float *r1, bool v0, bool v1, uint32_t (&ah)[4],
-                                           uint32_t (&al)[4]) {
-    float4 p = v0 ? __ldg(reinterpret_cast<const float4 *>(r0)) : make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 q = v1 ? __ldg(reinterpret_cast<const float4 *>(r1)) : make_float4(0.f, 0.f, 0.f, 0.f);
-    float h[8], l[8];
-    split_bf16(p.x, h[0], l[0]);
-    split_bf16(p.y, h[1], l[1]);
-    split_bf16(p.z, h[2], l[2]);
-    split_bf16(p.w, h[3], l[3]);
-    split_bf16(q.x, h[4], l[4]);
-    split_bf16(q.y, h[5], l[5]);
-    split_bf16(q.z, h[6], l[6]);
-    split_bf16(q.w, h[7], l[7]);
-    // logical (2t, 2t+1) <- physical (4t, 4t+1); (2t+8, 2t+9) <- (4t+2, 4t+3)
-    ah[0] = pack_bf16(h[0], h[1]);
-    ah[1] = pack_bf16(h[4], h[5]);
-    ah[2] = pack_bf16(h[2], h[3]);
-    ah[3] = pack_bf16(h[6], h[7]);
-    al[0] = pack_bf16(l[0], l[1]);
-    al[1] = pack_bf16(l[4], l[5]);
-    al[2] = pack_bf16(l[2], l[3]);
-    al[3] = pack_bf16(l[6], l[7]);
-}
-
-template <class TP> struct RowPanel;
-// FP32 near field / factors: 4 columns per 16-byte load, three products
-template <> struct RowPanel<float> {
-    static constexpr int PER_LOAD = 4;
-};
-// BF16 factors: 8 columns per 16-byte load, exact operand, two products
-template <> struct RowPanel<__nv_bfloat16> {
-    static constexpr int PER_LOAD = 8;
-};
-
-template <int MT, class TP>
-__device__ __forceinline__ void row_mrhs_panel(const TP *__restrict__ Pn, int K, const int32_t *__restrict__ idx,
-                                               const float *__restrict__ Z, int mr, int r0t,
-                                               __nv_bfloat16 *sBh, __nv_bfloat16 *sBl, float (&acc)[MT][2][4]) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
-    for (int c0 = 0; c0 < K; c0 += RM_CHUNK) {
-        __syncthreads();
-        // gathered rows of Z for the chunk's columns, split into BF16 hi / lo, [rhs][column]
-        for (int c = threadIdx.x; c < RM_CHUNK; c += RM_THREADS) {
-            const int col = c0 + c;
-            float z[MR];
-            if (col < K) {
-                const float4 *zr = reinterpret_cast<const float4 *>(Z + (int64_t)idx[col] * MR);
-#pragma unroll
-                for (int v = 0; v < MR / 4; ++v) {
-                    const float4 q = __ldg(zr + v);
-                    z[4 * v] = q.x;
-                    z[4 * v + 1] = q.y;
-                    z[4 * v + 2] = q.z;
-                    z[4 * v + 3] = q.w;
-                }
-            } else {
-#pragma unroll
-                for (int r = 0; r < MR; ++r) z[r] = 0.0f;
-            }
-#pragma unroll
-            for (int r = 0; r < MR; ++r) {
-                float h, l;
-                split_bf16(z[r], h, l);
-                sBh[r * RM_BSTRIDE + c] = __float2bfloat16_rn(h);
-                sBl[r * RM_BSTRIDE + c] = __float2bfloat16_rn(l);
-            }
-        }
-        __syncthreads();
-        // this warp's 32 columns of the chunk
-        const int wc = warp * 32;
-        if (c0 + wc >= K) continue;
-        if constexpr (RowPanel<TP>::PER_LOAD == 4) {
-#pragma unroll
-            for (int grp = 0; grp < 2; ++grp) {
-                const int pc = wc + 16 * grp + 4 * t;  // physical column of this thread's 4 values (chunk-relative)
-                const bool colok = c0 + pc < K;
-                // B fragments at the same physical columns: rhs g (n-tile 0) and g + 8 (n-tile 1)
-                uint32_t bh[2][2], bl[2][2];
-#pragma unroll
-                for (int nt = 0; nt < 2; ++nt) {
-                    const uint2 vh = *reinterpret_cast<const uint2 *>(sBh + (g + 8 * nt) * RM_BSTRIDE + pc);
-                    const uint2 vl = *reinterpret_cast<const uint2 *>(sBl + (g + 8 * nt) * RM_BSTRIDE + pc);
-                    bh[nt][0] = vh.x;
-                    bh[nt][1] = vh.y;
-                    bl[nt][0] = vl.x;
-                    bl[nt][1] = vl.y;
-                }
-#pragma unroll
-                for (int mt = 0; mt < MT; ++mt) {
-                    const int ra = r0t + 16 * mt + g, rb = ra + 8;
-                    uint32_t ah[4], al[4];
-                    a_frag_f32(reinterpret_cast<const float *>(Pn) + (int64_t)(ra < mr ? ra : 0) * K + c0 + pc,
-                               reinterpret_cast<const float *>(Pn) + (int64_t)(rb < mr ? rb : 0) * K + c0 + pc,
-                               colok && ra < mr, colok && rb < mr, ah, al);
-#pragma unroll
-                    for (int nt = 0; nt < 2; ++nt) {
-                        mma_bf16(acc[mt][nt], ah[0], ah[1], ah[2], ah[3], bh[nt][0], bh[nt][1]);
-                        mma_bf16(acc[mt][nt], ah[0], ah[1], ah[2], ah[3], bl[nt][0], bl[nt][1]);
-                        mma_bf16(acc[mt][nt], al[0], al[1], al[2], al[3], bh[nt][0], bh[nt][1]);
-                    }
-                }
-            }
-        } else {
-            const int pc = wc + 8 * t;  // physical columns pc .. pc + 7 (chunk-relative)
-            const bool colok = c0 + pc < K;
-            // two k16 products: physical (pc .. pc+3) and (pc+4 .. pc+7)
-            uint32_t bh[2][2][2], bl[2][2][2];  // [half][n-tile][reg]
-#pragma unroll
-            for (int hf = 0; hf < 2; ++hf)
-#pragma unroll
-                for (int nt = 0; nt < 2; ++nt) {
-                    const uint2 vh = *reinterpret_cast<const uint2 *>(sBh + (g + 8 * nt) * RM_BSTRIDE + pc + 4 * hf);
-                    const uint2 vl = *reinterpret_cast<const uint2 *>(sBl + (g + 8 * nt) * RM_BSTRIDE + pc + 4 * hf);
-                    bh[hf][nt][0] = vh.x;
-                    bh[hf][nt][1] = vh.y;
-                    bl[hf][nt][0] = vl.x;
-                    bl[hf][nt][1] = vl.y;
-                }
-#pragma unroll
-            for (int mt = 0; mt < MT; ++mt) {
-                const int ra = r0t + 16 * mt + g, rb = ra + 8;
-                const uint4 zero = make_uint4(0u, 0u, 0u, 0u);
-                const uint4 p = (colok && ra < mr)
-                                    ? __ldg(reinterpret_cast<const uint4 *>(Pn + (int64_t)ra * K + c0 + pc))
-                                    : zero;
-                const uint4 q = (colok && rb < mr)
-                                    ? __ldg(reinterpret_cast<const uint4 *>(Pn + (int64_t)rb * K + c0 + pc))
-                                    : zero;
-                // half 0: logical (2t,2t+1) <- (pc, pc+1) = p.x, (2t+8, 2t+9) <- (pc+2, pc+3) = p.y
-                // half 1: p.z, p.w
-#pragma unroll
-                for (int nt = 0; nt < 2; ++nt) {
-                    mma_bf16(acc[mt][nt], p.x, q.x, p.y, q.y, bh[0][nt][0], bh[0][nt][1]);
-                    mma_bf16(acc[mt][nt], p.x, q.x, p.y, q.y, bl[0][nt][0], bl[0][nt][1]);
-                    mma_bf16(acc[mt][nt], p.z, q.z, p.w, q.w, bh[1][nt][0], bh[1][nt][1]);
-                    mma_bf16(acc[mt][nt], p.z, q.z, p.w, q.w, bl[1][nt][0], bl[1][nt][1]);
-                }
-            }
-        }
+// W_b into its block-column panel: for every leaf column cluster kappa of
+// sigma_b, the rows of kappa come from kappa's W panel (FP64 master)
+template <class TF>
+__global__ void bcp_pack_kernel(const int32_t *__restrict__ adm, const int32_t *__restrict__ rank,
+                                const int32_t *__restrict__ bgrp, const int32_t *__restrict__ bkoff,
+                                const int64_t *__restrict__ off, const int32_t *__restrict__ Kg,
+                                const int32_t *__restrict__ leaf_begin, int64_t nleaf,
+                                const int64_t *__restrict__ lr_colptr, const int32_t *__restrict__ lr_collist,
+                                const int64_t *__restrict__ wp_off, const int32_t *__restrict__ wp_K,
+                                const int32_t *__restrict__ wp_koff, const double *__restrict__ wp,
+                                TF *__restrict__ bcp) {
+    __shared__ int64_t s_q;
+    const int32_t b = blockIdx.x;
+    const int32_t cb = adm[4 * b + 2], ce = adm[4 * b + 3];
+    const int k = rank[b];
+    const int grp = bgrp[b], koff = bkoff[b], K = Kg[grp];
+    TF *P = bcp + off[grp];
+    // first leaf cluster of sigma_b
+    int64_t lo = 0, hi = nleaf;
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (leaf_begin[mid] <= cb) lo = mid;
+        else hi = mid;
     }
-}
-
-template <int MT, class TF>
-__global__ void __launch_bounds__(RM_THREADS) row_mrhs_kernel(
-    const int32_t *__restrict__ leaf_begin, const int64_t *__restrict__ rho_off, const int32_t *__restrict__ rho_K,
-    const int64_t *__restrict__ rho_colptr, const int32_t *__restrict__ colidx, const float *__restrict__ dense,
-    const int64_t *__restrict__ up_off, const int32_t *__restrict__ up_K, const int64_t *__restrict__ up_colptr,
-    const int32_t *__restrict__ tidx, const TF *__restrict__ up, const float *__restrict__ T,
-    const float *__restrict__ X, double *__restrict__ Y) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    __nv_bfloat16 *sBh = reinterpret_cast<__nv_bfloat16 *>(sm);
-    __nv_bfloat16 *sBl = sBh + MR * RM_BSTRIDE;
-    float *sRed = reinterpret_cast<float *>(sBl + MR * RM_BSTRIDE);  // [warps][16 * MT rows][16]
-    const int64_t rho = blockIdx.x;
-    const int32_t r0 = leaf_begin[rho], mr = leaf_begin[rho + 1] - r0;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
-    for (int r0t = 0; r0t < mr; r0t += 16 * MT) {
-        float acc[MT][2][4];
-#pragma unroll
-        for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < 2; ++nt)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.0f;
-        row_mrhs_panel<MT, float>(dense + rho_off[rho], rho_K[rho], colidx + rho_colptr[rho], X, mr, r0t, sBh, sBl,
-                                  acc);
-        row_mrhs_panel<MT, TF>(up + up_off[rho], up_K[rho], tidx + up_colptr[rho], T, mr, r0t, sBh, sBl, acc);
-        // per-warp partial sums -> shared memory -> fixed-order sum over warps
-#pragma unroll
-        for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < 2; ++nt) {
-                float *base = sRed + (int64_t)warp * (16 * MT) * MR;
-                const int ra = 16 * mt + g, col = 8 * nt + 2 * t;
-                base[ra * MR + col] = acc[mt][nt][0];
-                base[ra * MR + col + 1] = acc[mt][nt][1];
-                base[(ra + 8) * MR + col] = acc[mt][nt][2];
-                base[(ra + 8) * MR + col + 1] = acc[mt][nt][3];
-            }
+    for (int64_t kap = lo; kap < nleaf && leaf_begin[kap] < ce; ++kap) {
         __syncthreads();
-        const int rows = min(16 * MT, mr - r0t);
-        for (int e = threadIdx.x; e < rows * MR; e += RM_THREADS) {
-            float s = 0.0f;
-            for (int w = 0; w < RM_WARPS; ++w) s += sRed[(int64_t)w * (16 * MT) * MR + e];
-            Y[(int64_t)(r0 + r0t) * MR + e] = (double)s;
+        if (threadIdx.x == 0) {
+            int64_t q = lr_colptr[kap];
+            while (q < lr_colptr[kap + 1] && lr_collist[q] != b) ++q;
+            s_q = q;
         }
         __syncthreads();
+        const int64_t q = s_q;
+        if (q >= lr_colptr[kap + 1]) continue;  // cannot happen for a consistent block list
+        const int32_t k0 = leaf_begin[kap], mk = leaf_begin[kap + 1] - k0;
+        const double *src = wp + wp_off[kap] + wp_koff[q];
+        for (int e = threadIdx.x; e < mk * k; e += blockDim.x) {
+            const int j = e / k, l = e - (e / k) * k;
+            const double v = src[(int64_t)j * wp_K[kap] + l];
+            if constexpr (sizeof(TF) == 2) P[(int64_t)(k0 - cb + j) * K + koff + l] = __double2bfloat16(v);
+            else P[(int64_t)(k0 - cb + j) * K + koff + l] = (float)v;
+        }
     }
 }
 
@@ -445,70 +523,197 @@ __global__ void mrhs_scatter_kernel(const double *__restrict__ Y, int64_t n, int
     }
 }
 
-int64_t mrhs_work_floats(const hm_matrix *A) {
-    const int64_t n = A->tree->n;
-    return MR * (n + std::max<int64_t>(A->n_partials, 1) + std::max<int64_t>(A->total_rank, 1)) + 2 * MR * n;
+// The block-column panels of the low-precision W factors (first use per
+// precision): blocks grouped by column cluster on the host (sorted by
+// (column begin, column end, block)), panel widths rounded up to 8 columns.
+static void build_bcp(const hm_matrix *Ac, hm_dtype prec, cudaStream_t s) {
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    hm_matrix *A = const_cast<hm_matrix *>(Ac);  // cache owned by the matrix
+    if (A->bcp_dtype == (int)prec) return;
+    const hm_tree *tr = A->tree;
+    const int64_t na = tr->n_adm;
+    std::vector<int32_t> adm(4 * std::max<int64_t>(na, 1)), rank(std::max<int64_t>(na, 1));
+    if (na > 0) {
+        HM_CUDA_CHECK(cudaMemcpyAsync(adm.data(), tr->adm.p, sizeof(int32_t) * 4 * na, cudaMemcpyDeviceToHost, s));
+        HM_CUDA_CHECK(cudaMemcpyAsync(rank.data(), A->rank.p, sizeof(int32_t) * na, cudaMemcpyDeviceToHost, s));
+        HM_CUDA_CHECK(cudaStreamSynchronize(s));
+    }
+    std::vector<int32_t> order(na);
+    for (int64_t b = 0; b < na; ++b) order[b] = (int32_t)b;
+    std::sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+        if (adm[4 * x + 2] != adm[4 * y + 2]) return adm[4 * x + 2] < adm[4 * y + 2];
+        if (adm[4 * x + 3] != adm[4 * y + 3]) return adm[4 * x + 3] < adm[4 * y + 3];
+        return x < y;
+    });
+    std::vector<int64_t> t_off(na + 1, 0);
+    for (int64_t b = 0; b < na; ++b) t_off[b + 1] = t_off[b] + rank[b];
+    std::vector<int64_t> off, col0;
+    std::vector<int32_t> Kg, rows, bgrp(std::max<int64_t>(na, 1)), bkoff(std::max<int64_t>(na, 1)), tidx, tiles, red;
+    int64_t o = 0, c = 0;
+    int32_t nslots = 0;
+    for (int64_t i = 0; i < na;) {
+        int64_t j = i;
+        int32_t k = 0;
+        const int32_t cb = adm[4 * order[i] + 2], ce = adm[4 * order[i] + 3];
+        while (j < na && adm[4 * order[j] + 2] == cb && adm[4 * order[j] + 3] == ce) {
+            bgrp[order[j]] = (int32_t)Kg.size();
+            bkoff[order[j]] = k;
+            k += rank[order[j]];
+            ++j;
+        }
+        const int32_t K = std::max<int32_t>(8, (k + 7) / 8 * 8);
+        const int grp = (int)Kg.size();
+        Kg.push_back(K);
+        rows.push_back(cb);
+        rows.push_back(ce);
+        off.push_back(o);
+        col0.push_back(c);
+        tidx.resize(c + K, -1);
+        for (int64_t q = i; q < j; ++q) {
+            const int32_t b = order[q];
+            for (int32_t l = 0; l < rank[b]; ++l) tidx[c + bkoff[b] + l] = (int32_t)(t_off[b] + l);
+        }
+        const int32_t nrow = ce - cb;
+        const int32_t nsplit = (nrow + BC_SPLIT - 1) / BC_SPLIT;
+        for (int32_t n0 = 0; n0 < K; n0 += CM_COLS) {
+            if (nsplit == 1) {
+                tiles.insert(tiles.end(), {grp, n0, 0, nrow, -1});
+            } else {
+                red.insert(red.end(), {grp, n0, nslots, nsplit});
+                for (int32_t q = 0; q < nsplit; ++q)
+                    tiles.insert(tiles.end(), {grp, n0, q * BC_SPLIT, std::min(nrow, (q + 1) * BC_SPLIT), nslots + q});
+                nslots += nsplit;
+            }
+        }
+        o += (int64_t)(ce - cb) * K;
+        c += K;
+        i = j;
+    }
+    const int64_t ng = (int64_t)Kg.size();
+    auto up = [&](DBuf &d, const void *h, size_t bytes) {
+        d.alloc(std::max<size_t>(bytes, 16));
+        if (bytes) HM_CUDA_CHECK(cudaMemcpyAsync(d.p, h, bytes, cudaMemcpyHostToDevice, s));
+    };
+    up(A->bcp_off, off.data(), sizeof(int64_t) * ng);
+    up(A->bcp_K, Kg.data(), sizeof(int32_t) * ng);
+    up(A->bcp_rows, rows.data(), sizeof(int32_t) * 2 * ng);
+    up(A->bcp_col0, col0.data(), sizeof(int64_t) * ng);
+    up(A->bcp_tidx, tidx.data(), sizeof(int32_t) * tidx.size());
+    up(A->bcp_tiles, tiles.data(), sizeof(int32_t) * tiles.size());
+    up(A->bcp_red, red.data(), sizeof(int32_t) * red.size());
+    DBuf d_bgrp, d_bkoff;
+    up(d_bgrp, bgrp.data(), sizeof(int32_t) * na);
+    up(d_bkoff, bkoff.data(), sizeof(int32_t) * na);
+    const size_t esz = prec == HM_BF16 ? 2 : 4;
+    A->bcp.alloc(esz * std::max<int64_t>(o, 8));
+    HM_CUDA_CHECK(cudaMemsetAsync(A->bcp.p, 0, esz * std::max<int64_t>(o, 8), s));
+    if (na > 0) {
+        if (prec == HM_BF16)
+            bcp_pack_kernel<__nv_bfloat16><<<(unsigned)na, 128, 0, s>>>(
+                tr->adm.as<int32_t>(), A->rank.as<int32_t>(), d_bgrp.as<int32_t>(), d_bkoff.as<int32_t>(),
+                A->bcp_off.as<int64_t>(), A->bcp_K.as<int32_t>(), tr->leaf_begin.as<int32_t>(), tr->n_leaf,
+                tr->lr_colptr.as<int64_t>(), tr->lr_collist.as<int32_t>(), A->wp_off.as<int64_t>(),
+                A->wp_K.as<int32_t>(), A->wp_koff.as<int32_t>(), A->wp.as<double>(), A->bcp.as<__nv_bfloat16>());
+        else
+            bcp_pack_kernel<float><<<(unsigned)na, 128, 0, s>>>(
+                tr->adm.as<int32_t>(), A->rank.as<int32_t>(), d_bgrp.as<int32_t>(), d_bkoff.as<int32_t>(),
+                A->bcp_off.as<int64_t>(), A->bcp_K.as<int32_t>(), tr->leaf_begin.as<int32_t>(), tr->n_leaf,
+                tr->lr_colptr.as<int64_t>(), tr->lr_collist.as<int32_t>(), A->wp_off.as<int64_t>(),
+                A->wp_K.as<int32_t>(), A->wp_koff.as<int32_t>(), A->wp.as<double>(), A->bcp.as<float>());
+        HM_LAUNCH_CHECK();
+    }
+    HM_CUDA_CHECK(cudaStreamSynchronize(s));
+    A->bcp_ngroups = ng;
+    A->bcp_ntiles = (int64_t)tiles.size() / BC_ITEM;
+    A->bcp_nred = (int64_t)red.size() / 4;
+    A->bcp_nslots = nslots;
+    A->bcp_dtype = (int)prec;
 }
 
-static int col_smem(int max_leaf, bool f32) {
-    const int kpad = (max_leaf + 15) & ~15;
-    int b = 2 * MR * (kpad + 8) * 2 + (f32 ? 2 : 1) * kpad * CM_TSTRIDE * 2;
-    if (f32) b += kpad * CM_COLS * 4;
+static int bcp_smem(bool f32) {
+    int b = 2 * MR * (BC_ROWS + 8) * 2 + (f32 ? 2 : 1) * BC_ROWS * CM_TSTRIDE * 2;
+    if (f32) b += BC_ROWS * CM_COLS * 4;
     return (b + 15) & ~15;
 }
 
-template <int MT> static int row_smem() { return 2 * MR * RM_BSTRIDE * 2 + RM_WARPS * 16 * MT * MR * 4; }
+// Workspace of one 16-column product, in floats: X [n][16] FP32, Y [n][16]
+// FP64, then the work of matvec_mrhs_morton: X as BF16 pairs (hi, lo:
+// [n][16] each), t as BF16 pairs ([K][16] each) and the partials of the
+// projection tiles whose rows were split.  Call mrhs_prepare first.
+int64_t mrhs_work_floats(const hm_matrix *A) {
+    const int64_t n = A->tree->n, K = std::max<int64_t>(A->total_rank, 1);
+    return 4 * MR * n + MR * K + std::max<int64_t>(A->bcp_nslots, 1) * CM_COLS * MR;  // 48 n + 16 n + 16 K + P
+}
+
+void mrhs_prepare(const hm_matrix *A, hm_dtype prec, cudaStream_t s) {
+    if ((prec == HM_F32 && A->up32.p) || (prec == HM_BF16 && A->upbf.p)) build_bcp(A, prec, s);
+}
+
+
+
+template <int MT> static int row_smem() {
+    const int st = RP_STAGES * RpStage<MT, float>::BYTES, red = RP_WARPS * 16 * MT * MR * 4;
+    return st > red ? st : red;
+}
 
 template <class TF>
-static void matvec_mrhs_impl(const hm_matrix *A, const TF *up, const TF *wp, const float *X, float *P, float *T,
-                             double *Y, cudaStream_t s) {
+static void matvec_mrhs_impl(const hm_matrix *A, const TF *up, const float *X, double *Y, __nv_bfloat16 *Xh,
+                             __nv_bfloat16 *Xl, __nv_bfloat16 *Th, __nv_bfloat16 *Tl, float *part, cudaStream_t s) {
     const hm_tree *tr = A->tree;
+    const int64_t n = tr->n;
     const bool f32 = sizeof(TF) == 4;
-    if (tr->n_adm > 0) {
-        const int smem = col_smem(tr->max_leaf, f32);
-        HM_CUDA_CHECK(cudaFuncSetAttribute(col_mrhs_kernel<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        Trace tc(f32 ? "col_mrhs_kernel.f32" : "col_mrhs_kernel.bf16", s);
-        col_mrhs_kernel<TF><<<(unsigned)tr->n_leaf, CM_THREADS, smem, s>>>(
-            tr->leaf_begin.as<int32_t>(), A->wp_off.as<int64_t>(), A->wp_K.as<int32_t>(), A->wp_colptr.as<int64_t>(),
-            wp, X, P);
+    split_rows_kernel<<<grid1d_m(n * MR), 256, 0, s>>>(X, n * MR, Xh, Xl);
+    HM_LAUNCH_CHECK();
+    if (tr->n_adm > 0 && A->bcp_ntiles > 0) {
+        const int smem = bcp_smem(f32);
+        HM_CUDA_CHECK(cudaFuncSetAttribute(col_bcp_kernel<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        Trace tc(f32 ? "col_bcp_kernel.f32" : "col_bcp_kernel.bf16", s);
+        col_bcp_kernel<TF><<<(unsigned)A->bcp_ntiles, CM_THREADS, smem, s>>>(
+            A->bcp_tiles.as<int32_t>(), A->bcp_off.as<int64_t>(), A->bcp_K.as<int32_t>(), A->bcp_rows.as<int32_t>(),
+            A->bcp_col0.as<int64_t>(), A->bcp_tidx.as<int32_t>(), A->bcp.as<TF>(), X, Th, Tl, part);
         HM_LAUNCH_CHECK();
-    }
-    if (tr->n_adm > 0) {
-        Trace tt("tsum_mrhs_kernel", s);
-        tsum_mrhs_kernel<<<grid1d_m(A->total_rank * MR), 256, 0, s>>>(
-            tr->n_adm, A->total_rank, A->tsum_b0.as<int32_t>(), A->t_off.as<int64_t>(), tr->lr_bcolptr.as<int64_t>(),
-            A->pofs.as<int64_t>(), P, T);
-        HM_LAUNCH_CHECK();
+        if (A->bcp_nred > 0) {
+            bcp_reduce_kernel<<<(unsigned)A->bcp_nred, 256, 0, s>>>(A->bcp_red.as<int32_t>(), A->bcp_K.as<int32_t>(),
+                                                                    A->bcp_col0.as<int64_t>(),
+                                                                    A->bcp_tidx.as<int32_t>(), part, Th, Tl);
+            HM_LAUNCH_CHECK();
+        }
     }
     const int tiles = (tr->max_leaf + 15) / 16;
     auto launch = [&](auto kern, int smem) {
         HM_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         Trace tr_(f32 ? "row_mrhs_kernel.f32" : "row_mrhs_kernel.bf16", s);
-        kern<<<(unsigned)tr->n_leaf, RM_THREADS, smem, s>>>(
+        kern<<<(unsigned)tr->n_leaf, RP_THREADS, smem, s>>>(
             tr->leaf_begin.as<int32_t>(), tr->rho_off.as<int64_t>(), tr->rho_K.as<int32_t>(),
             tr->rho_colptr.as<int64_t>(), tr->colidx.as<int32_t>(), A->dense32.as<float>(), A->up_off.as<int64_t>(),
-            A->up_K.as<int32_t>(), A->up_colptr.as<int64_t>(), A->tidx.as<int32_t>(), up, T, X, Y);
+            A->up_K.as<int32_t>(), A->up_colptr.as<int64_t>(), A->tidx.as<int32_t>(), up, Th, Tl, Xh, Xl, Y);
         HM_LAUNCH_CHECK();
     };
     if (tiles <= 3) launch(row_mrhs_kernel<3, TF>, row_smem<3>());
     else if (tiles <= 5) launch(row_mrhs_kernel<5, TF>, row_smem<5>());
-    else launch(row_mrhs_kernel<4, TF>, row_smem<4>());
+    else launch(row_mrhs_kernel<8, TF>, row_smem<8>());
 }
 
 // Y (Morton [n][16] FP64) = H X (Morton [n][16] FP32) with the FP32 near field
-// and FP32 (prec = HM_F32) or BF16 (HM_BF16) factors.  work: mrhs_work_floats.
+// and FP32 (prec = HM_F32) or BF16 (HM_BF16) factors.  work: the part of the
+// workspace after X and Y (mrhs_work_floats - 48 n floats); mrhs_prepare must
+// have run for this precision.
 void matvec_mrhs_morton(const hm_matrix *A, hm_dtype prec, const float *X, double *Y, float *work, cudaStream_t s) {
     if (!A->dense32.p) fail(HM_EINVAL, "the multi-RHS product needs the FP32 near-field copy");
-    const int64_t n = A->tree->n;
-    float *P = work;
-    float *T = P + MR * std::max<int64_t>(A->n_partials, 1);
-    (void)n;
+    if (A->bcp_dtype != (int)prec) fail(HM_EINTERNAL, "multi-RHS panels not prepared for this precision");
+    const int64_t n = A->tree->n, K = std::max<int64_t>(A->total_rank, 1);
+    __nv_bfloat16 *Xh = reinterpret_cast<__nv_bfloat16 *>(work);
+    __nv_bfloat16 *Xl = Xh + MR * n;
+    __nv_bfloat16 *Th = Xl + MR * n;
+    __nv_bfloat16 *Tl = Th + MR * K;
+    float *part = reinterpret_cast<float *>(Tl + MR * K);
     if (prec == HM_F32) {
         if (!A->up32.p) fail(HM_EINVAL, "FP32 copies were not assembled");
-        matvec_mrhs_impl<float>(A, A->up32.as<float>(), A->wp32.as<float>(), X, P, T, Y, s);
+        matvec_mrhs_impl<float>(A, A->up32.as<float>(), X, Y, Xh, Xl, Th, Tl, part, s);
     } else if (prec == HM_BF16) {
         if (!A->upbf.p) fail(HM_EINVAL, "BF16 factors were not assembled");
-        matvec_mrhs_impl<__nv_bfloat16>(A, A->upbf.as<__nv_bfloat16>(), A->wpbf.as<__nv_bfloat16>(), X, P, T, Y, s);
+        matvec_mrhs_impl<__nv_bfloat16>(A, A->upbf.as<__nv_bfloat16>(), X, Y, Xh, Xl, Th, Tl, part, s);
     } else {
         fail(HM_EINVAL, "the multi-RHS product runs on the FP32 / BF16 copies");
     }
@@ -520,11 +725,11 @@ void matvec_mrhs(const hm_matrix *A, hm_dtype prec, int nrhs, const double *x, d
                  cudaStream_t s) {
     const hm_tree *tr = A->tree;
     const int64_t n = tr->n;
+    mrhs_prepare(A, prec, s);
     for (int r0 = 0; r0 < nrhs; r0 += MR) {
         const int nr = std::min(MR, nrhs - r0);
         SBuf buf;
-        const int64_t nf = mrhs_work_floats(A);
-        buf.alloc(sizeof(float) * nf, s);
+        buf.alloc(sizeof(float) * mrhs_work_floats(A), s);
         float *X = buf.as<float>();
         double *Y = reinterpret_cast<double *>(X + MR * n);  // [n][16] doubles = 2 * 16 * n floats
         float *work = X + 3 * MR * n;
