@@ -73,17 +73,7 @@ template <int N> __device__ __forceinline__ void cp_async_wait() { asm volatile(
 
 constexpr int CM_THREADS = 256;
 constexpr int CM_COLS = 64;                 // panel columns per tile
-constexpr int CM_TSTRIDE = CM_COLS + 8;     // bf16 per tile row in shared memory (16-byte aligned rows)
 
-template <class TF> struct ColTile;
-// BF16 panels: the tile goes to shared memory as is (cp.async), one operand
-template <> struct ColTile<__nv_bfloat16> {
-    static constexpr int NSPLIT = 1;
-};
-// FP32 panels: staged as FP32, then split into BF16 hi / lo tiles
-template <> struct ColTile<float> {
-    static constexpr int NSPLIT = 2;
-};
 
 // ---------------------------------------------------------------------------
 // row_mrhs_kernel: Y_rho = P_rho X(colidx) + U~_rho T(tidx), one CTA (4 warps)
@@ -298,11 +288,9 @@ __global__ void split_rows_kernel(const float *__restrict__ X, int64_t n, __nv_b
 // ---------------------------------------------------------------------------
 // col_bcp_kernel: t_b = X_sigma^T W_b for every block, straight from the
 // panels grouped by block column cluster (no partial sums): one CTA per tile
-// of 64 panel columns; the panel rows (|sigma|, up to thousands) are walked
-// in chunks of BC_ROWS, with X_sigma^T (split hi / lo) and the W tile staged
-// in shared memory; each warp owns 8 columns.
+// of 64 panel columns and at most BC_SPLIT panel rows (the rows of taller
+// panels are split over several CTAs whose partials are added afterwards).
 // ---------------------------------------------------------------------------
-constexpr int BC_ROWS = 128;
 
 // one work item: (panel, first column, first row, end row, partial slot or -1)
 constexpr int BC_ITEM = 5;
@@ -316,6 +304,92 @@ __device__ __forceinline__ void store_t_pair(__nv_bfloat16 *Th, __nv_bfloat16 *T
     Tl[ti * MR + r] = __float2bfloat16_rn(l);
 }
 
+// Pipelined over chunks of BP_KC panel rows (3 stages of cp.async): the
+// chunk's rows of X (pre-split BF16 pairs, [row][rhs]) and of the W tile land
+// in shared memory while earlier chunks are multiplied.  A = X^T fragments by
+// ldmatrix.trans from the [row][rhs] tile; B = W fragments by ldmatrix.trans
+// (BF16 panels) or by shared-memory loads split into BF16 pairs (FP32
+// panels).  Each of the 8 warps owns 8 of the 64 columns.
+constexpr int BP_KC = 64;               // panel rows per chunk
+constexpr int BP_STAGES = 3;
+constexpr int BP_XSTRIDE = MR + 8;      // bf16 per staged row of X (48 bytes)
+constexpr int BP_WS16 = CM_COLS + 8;    // bf16 per staged W row (144 bytes)
+constexpr int BP_WS32 = CM_COLS + 4;    // floats per staged W row (conflict-free column reads)
+
+template <class TF> struct BpStage {
+    static constexpr int X_BYTES = 2 * BP_KC * BP_XSTRIDE * 2;
+    static constexpr int W_BYTES = sizeof(TF) == 2 ? BP_KC * BP_WS16 * 2 : BP_KC * BP_WS32 * 4;
+    static constexpr int BYTES = X_BYTES + W_BYTES;
+};
+
+template <class TF>
+__device__ __forceinline__ void bp_load(unsigned char *stage, const TF *__restrict__ W, int K, int kc, int n0,
+                                        const __nv_bfloat16 *__restrict__ Xh, const __nv_bfloat16 *__restrict__ Xl,
+                                        int64_t xr0) {
+    __nv_bfloat16 *sXh = reinterpret_cast<__nv_bfloat16 *>(stage);
+    __nv_bfloat16 *sXl = sXh + BP_KC * BP_XSTRIDE;
+    for (int e = threadIdx.x; e < BP_KC * 4; e += CM_THREADS) {
+        const int k = e >> 2, q = e & 3;
+        const bool ok = k < kc;
+        const __nv_bfloat16 *src = ((q & 2) ? Xl : Xh) + (xr0 + k) * MR + 8 * (q & 1);
+        cp_async16(((q & 2) ? sXl : sXh) + k * BP_XSTRIDE + 8 * (q & 1), ok ? (const void *)src : (const void *)Xh,
+                   ok);
+    }
+    constexpr int PER = 16 / (int)sizeof(TF), VPR = CM_COLS / PER;
+    constexpr int WS = sizeof(TF) == 2 ? BP_WS16 : BP_WS32;
+    TF *sW = reinterpret_cast<TF *>(stage + BpStage<TF>::X_BYTES);
+    for (int e = threadIdx.x; e < BP_KC * VPR; e += CM_THREADS) {
+        const int k = e / VPR, v = e - (e / VPR) * VPR;
+        const int col = n0 + PER * v;
+        const bool ok = k < kc && col < K;
+        cp_async16(sW + k * WS + PER * v, ok ? (const void *)(W + (int64_t)k * K + col) : (const void *)W, ok);
+    }
+}
+
+template <class TF>
+__device__ __forceinline__ void bp_compute(const unsigned char *stage, float (&d)[4]) {
+    const __nv_bfloat16 *sXh = reinterpret_cast<const __nv_bfloat16 *>(stage);
+    const __nv_bfloat16 *sXl = sXh + BP_KC * BP_XSTRIDE;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
+    // ldmatrix.x4.trans of X^T: lanes 0-7 rows k 0-7 / rhs 0-7, 8-15 rows k 0-7 / rhs 8-15,
+    // 16-23 rows k 8-15 / rhs 0-7, 24-31 rows k 8-15 / rhs 8-15
+    const int xr = (lane & 7) + 8 * (lane >> 4), xc = 8 * ((lane >> 3) & 1);
+#pragma unroll
+    for (int kb = 0; kb < BP_KC; kb += 16) {
+        uint32_t ah0, ah1, ah2, ah3, al0, al1, al2, al3;
+        {
+            const uint32_t a = (uint32_t)__cvta_generic_to_shared(sXh + (kb + xr) * BP_XSTRIDE + xc);
+            asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                         : "=r"(ah0), "=r"(ah1), "=r"(ah2), "=r"(ah3)
+                         : "r"(a));
+            const uint32_t b = (uint32_t)__cvta_generic_to_shared(sXl + (kb + xr) * BP_XSTRIDE + xc);
+            asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                         : "=r"(al0), "=r"(al1), "=r"(al2), "=r"(al3)
+                         : "r"(b));
+        }
+        if constexpr (sizeof(TF) == 2) {
+            const __nv_bfloat16 *sW = reinterpret_cast<const __nv_bfloat16 *>(stage + BpStage<TF>::X_BYTES);
+            uint32_t b0, b1;
+            ldmatrix_x2_trans(b0, b1, sW + (kb + (lane & 15)) * BP_WS16 + 8 * warp);
+            mma_bf16(d, ah0, ah1, ah2, ah3, b0, b1);
+            mma_bf16(d, al0, al1, al2, al3, b0, b1);
+        } else {
+            const float *sW = reinterpret_cast<const float *>(stage + BpStage<TF>::X_BYTES);
+            const float *c = sW + 8 * warp + g;
+            float h[4], l[4];
+            split_bf16(c[(kb + 2 * t) * BP_WS32], h[0], l[0]);
+            split_bf16(c[(kb + 2 * t + 1) * BP_WS32], h[1], l[1]);
+            split_bf16(c[(kb + 2 * t + 8) * BP_WS32], h[2], l[2]);
+            split_bf16(c[(kb + 2 * t + 9) * BP_WS32], h[3], l[3]);
+            const uint32_t bh0 = pack_bf16(h[0], h[1]), bh1 = pack_bf16(h[2], h[3]);
+            const uint32_t bl0 = pack_bf16(l[0], l[1]), bl1 = pack_bf16(l[2], l[3]);
+            mma_bf16(d, ah0, ah1, ah2, ah3, bh0, bh1);
+            mma_bf16(d, al0, al1, al2, al3, bh0, bh1);
+            mma_bf16(d, ah0, ah1, ah2, ah3, bl0, bl1);
+        }
+    }
+}
+
 template <class TF>
 __global__ void __launch_bounds__(CM_THREADS) col_bcp_kernel(const int32_t *__restrict__ items,
                                                              const int64_t *__restrict__ off,
@@ -323,7 +397,9 @@ __global__ void __launch_bounds__(CM_THREADS) col_bcp_kernel(const int32_t *__re
                                                              const int32_t *__restrict__ rows,
                                                              const int64_t *__restrict__ col0,
                                                              const int32_t *__restrict__ tidx,
-                                                             const TF *__restrict__ bcp, const float *__restrict__ X,
+                                                             const TF *__restrict__ bcp,
+                                                             const __nv_bfloat16 *__restrict__ Xh,
+                                                             const __nv_bfloat16 *__restrict__ Xl,
                                                              __nv_bfloat16 *__restrict__ Th,
                                                              __nv_bfloat16 *__restrict__ Tl,
                                                              float *__restrict__ part) {
@@ -334,72 +410,27 @@ __global__ void __launch_bounds__(CM_THREADS) col_bcp_kernel(const int32_t *__re
     const int K = Kg[grp];
     const TF *W = bcp + off[grp] + (int64_t)it[2] * K;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
-    constexpr int xs = BC_ROWS + 8;
-    __nv_bfloat16 *sXh = reinterpret_cast<__nv_bfloat16 *>(sm);
-    __nv_bfloat16 *sXl = sXh + MR * xs;
-    __nv_bfloat16 *sT = sXl + MR * xs;
-    float *sF = reinterpret_cast<float *>(sT + ColTile<TF>::NSPLIT * BC_ROWS * CM_TSTRIDE);
+    constexpr int SB = BpStage<TF>::BYTES;
+    const int ns = (nr + BP_KC - 1) / BP_KC;
     float d[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    for (int k0 = 0; k0 < nr; k0 += BC_ROWS) {
-        const int kc = min(BC_ROWS, nr - k0), kpad = (kc + 15) & ~15;
-        __syncthreads();
-        for (int e = threadIdx.x; e < MR * kpad; e += CM_THREADS) {
-            const int r = e / kpad, k = e - (e / kpad) * kpad;
-            float h = 0.0f, l = 0.0f;
-            if (k < kc) split_bf16(X[(int64_t)(r0 + k0 + k) * MR + r], h, l);
-            sXh[r * xs + k] = __float2bfloat16_rn(h);
-            sXl[r * xs + k] = __float2bfloat16_rn(l);
-        }
-        if constexpr (sizeof(TF) == 2) {
-            for (int e = threadIdx.x; e < kpad * (CM_COLS / 8); e += CM_THREADS) {
-                const int k = e / (CM_COLS / 8), v = e - (e / (CM_COLS / 8)) * (CM_COLS / 8);
-                const int col = n0 + 8 * v;
-                const bool ok = k < kc && col < K;
-                cp_async16(sT + k * CM_TSTRIDE + 8 * v,
-                           ok ? (const void *)(W + (int64_t)(k0 + k) * K + col) : (const void *)W, ok);
-            }
-            cp_async_commit();
-            cp_async_wait<0>();
-        } else {
-            for (int e = threadIdx.x; e < kpad * (CM_COLS / 4); e += CM_THREADS) {
-                const int k = e / (CM_COLS / 4), v = e - (e / (CM_COLS / 4)) * (CM_COLS / 4);
-                const int col = n0 + 4 * v;
-                const bool ok = k < kc && col < K;
-                cp_async16(sF + k * CM_COLS + 4 * v,
-                           ok ? (const void *)(W + (int64_t)(k0 + k) * K + col) : (const void *)W, ok);
-            }
-            cp_async_commit();
-            cp_async_wait<0>();
-            __syncthreads();
-            for (int e = threadIdx.x; e < kpad * CM_COLS; e += CM_THREADS) {
-                const int k = e / CM_COLS, c = e - (e / CM_COLS) * CM_COLS;
-                float h, l;
-                split_bf16(sF[e], h, l);
-                sT[k * CM_TSTRIDE + c] = __float2bfloat16_rn(h);
-                sT[BC_ROWS * CM_TSTRIDE + k * CM_TSTRIDE + c] = __float2bfloat16_rn(l);
-            }
-        }
-        __syncthreads();
-        for (int kb = 0; kb < kpad; kb += 16) {
-            const uint32_t ah0 = *reinterpret_cast<const uint32_t *>(sXh + g * xs + kb + 2 * t);
-            const uint32_t ah1 = *reinterpret_cast<const uint32_t *>(sXh + (g + 8) * xs + kb + 2 * t);
-            const uint32_t ah2 = *reinterpret_cast<const uint32_t *>(sXh + g * xs + kb + 2 * t + 8);
-            const uint32_t ah3 = *reinterpret_cast<const uint32_t *>(sXh + (g + 8) * xs + kb + 2 * t + 8);
-            const uint32_t al0 = *reinterpret_cast<const uint32_t *>(sXl + g * xs + kb + 2 * t);
-            const uint32_t al1 = *reinterpret_cast<const uint32_t *>(sXl + (g + 8) * xs + kb + 2 * t);
-            const uint32_t al2 = *reinterpret_cast<const uint32_t *>(sXl + g * xs + kb + 2 * t + 8);
-            const uint32_t al3 = *reinterpret_cast<const uint32_t *>(sXl + (g + 8) * xs + kb + 2 * t + 8);
-            uint32_t b0, b1;
-            ldmatrix_x2_trans(b0, b1, sT + (kb + (lane & 15)) * CM_TSTRIDE + 8 * warp);
-            mma_bf16(d, ah0, ah1, ah2, ah3, b0, b1);
-            mma_bf16(d, al0, al1, al2, al3, b0, b1);
-            if constexpr (ColTile<TF>::NSPLIT == 2) {
-                uint32_t e0, e1;
-                ldmatrix_x2_trans(e0, e1, sT + BC_ROWS * CM_TSTRIDE + (kb + (lane & 15)) * CM_TSTRIDE + 8 * warp);
-                mma_bf16(d, ah0, ah1, ah2, ah3, e0, e1);
-            }
-        }
+#pragma unroll
+    for (int st = 0; st < BP_STAGES - 1; ++st) {
+        if (st < ns)
+            bp_load<TF>(sm + st * SB, W + (int64_t)st * BP_KC * K, K, min(BP_KC, nr - st * BP_KC), n0, Xh, Xl,
+                        r0 + st * BP_KC);
+        cp_async_commit();
     }
+    for (int c = 0; c < ns; ++c) {
+        cp_async_wait<BP_STAGES - 2>();
+        __syncthreads();
+        const int nx = c + BP_STAGES - 1;
+        if (nx < ns)
+            bp_load<TF>(sm + (nx % BP_STAGES) * SB, W + (int64_t)nx * BP_KC * K, K, min(BP_KC, nr - nx * BP_KC), n0,
+                        Xh, Xl, r0 + nx * BP_KC);
+        cp_async_commit();
+        bp_compute<TF>(sm + (c % BP_STAGES) * SB, d);
+    }
+    cp_async_wait<0>();
     // D (16 rhs x 8 columns of this warp) -> t rows of those columns, or the partial of this row range
     const int cl = 8 * warp + 2 * t, col = n0 + cl;
     if (slot >= 0) {
@@ -632,9 +663,7 @@ static void build_bcp(const hm_matrix *Ac, hm_dtype prec, cudaStream_t s) {
 }
 
 static int bcp_smem(bool f32) {
-    int b = 2 * MR * (BC_ROWS + 8) * 2 + (f32 ? 2 : 1) * BC_ROWS * CM_TSTRIDE * 2;
-    if (f32) b += BC_ROWS * CM_COLS * 4;
-    return (b + 15) & ~15;
+    return BP_STAGES * (f32 ? BpStage<float>::BYTES : BpStage<__nv_bfloat16>::BYTES);
 }
 
 // Workspace of one 16-column product, in floats: X [n][16] FP32, Y [n][16]
@@ -671,7 +700,7 @@ static void matvec_mrhs_impl(const hm_matrix *A, const TF *up, const float *X, d
         Trace tc(f32 ? "col_bcp_kernel.f32" : "col_bcp_kernel.bf16", s);
         col_bcp_kernel<TF><<<(unsigned)A->bcp_ntiles, CM_THREADS, smem, s>>>(
             A->bcp_tiles.as<int32_t>(), A->bcp_off.as<int64_t>(), A->bcp_K.as<int32_t>(), A->bcp_rows.as<int32_t>(),
-            A->bcp_col0.as<int64_t>(), A->bcp_tidx.as<int32_t>(), A->bcp.as<TF>(), X, Th, Tl, part);
+            A->bcp_col0.as<int64_t>(), A->bcp_tidx.as<int32_t>(), A->bcp.as<TF>(), Xh, Xl, Th, Tl, part);
         HM_LAUNCH_CHECK();
         if (A->bcp_nred > 0) {
             bcp_reduce_kernel<<<(unsigned)A->bcp_nred, 256, 0, s>>>(A->bcp_red.as<int32_t>(), A->bcp_K.as<int32_t>(),
