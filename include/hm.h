@@ -168,6 +168,9 @@ typedef struct {
                                partner of an approximated block reuses its
                                factors, the matrix being symmetric)            */
     int64_t u_entries;      /* stored entries of the U factors, sum k_b |tau|     */
+    int32_t aca_small_sum;  /* ACA worker split chosen by the autotuner: blocks
+                               with m + n up to this (and both dims <= 256) run
+                               on one warp, larger ones on a whole CTA        */
 } hm_matrix_info;
 
 /* Build the Morton-ordered cluster tree and the block cluster tree of a

@@ -25,6 +25,9 @@
 // copied from per-worker scratch to a bump-allocated arena; blocks that do not
 // fit are reported and re-run after the arena grows.
 #include <algorithm>
+#include <cmath>
+#include <map>
+#include <mutex>
 
 #include "entry.cuh"
 #include "ff.cuh"
@@ -495,101 +498,202 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
     HM_CUDA_CHECK(cudaMemcpyAsync(h_adm.data(), tr->adm.p, sizeof(int32_t) * 4 * na, cudaMemcpyDeviceToHost, s));
     HM_CUDA_CHECK(cudaMemcpyAsync(h_tp.data(), tr->adm_tp.p, sizeof(int32_t) * na, cudaMemcpyDeviceToHost, s));
     HM_CUDA_CHECK(cudaStreamSynchronize(s));
-    // blocks are in level order (largest first); small = both dims <= SMALL_MAX_DIM and
-    // m + n <= small_sum, chosen so that one warp per block keeps the tail short
-    const int small_sum = 320;
-    int max_m_big = 1, max_n_big = 1, max_sum_small = 2;
-    std::vector<int32_t> big, small;
-    for (int64_t b = 0; b < na; ++b) {
-        if (h_tp[b] >= 0 && h_adm[4 * b] > h_adm[4 * b + 2]) continue;
-        const int m = h_adm[4 * b + 1] - h_adm[4 * b], n = h_adm[4 * b + 3] - h_adm[4 * b + 2];
-        if (m <= SMALL_MAX_DIM && n <= SMALL_MAX_DIM && m + n <= small_sum) small.push_back((int32_t)b);
-        else big.push_back((int32_t)b);
-    }
-    const int64_t n_big = (int64_t)big.size();
-    // CTA-mode scratch and bitmaps fit every block (a re-run after arena
-    // growth processes any block CTA-wide)
+    // the blocks to approximate: the matrix is symmetric, so of a pair of
+    // blocks with swapped ranges only the one above the diagonal
+    std::vector<int32_t> upper;
+    upper.reserve(na);
+    int max_m_big = 1, max_n_big = 1;
     for (int64_t b = 0; b < na; ++b) {
         max_m_big = std::max(max_m_big, h_adm[4 * b + 1] - h_adm[4 * b]);
         max_n_big = std::max(max_n_big, h_adm[4 * b + 3] - h_adm[4 * b + 2]);
+        if (h_tp[b] >= 0 && h_adm[4 * b] > h_adm[4 * b + 2]) continue;
+        upper.push_back((int32_t)b);
     }
-    for (int32_t b : small)
-        max_sum_small = std::max(max_sum_small, h_adm[4 * b + 1] - h_adm[4 * b] + h_adm[4 * b + 3] - h_adm[4 * b + 2]);
-    std::vector<int32_t> work(big);
-    work.insert(work.end(), small.begin(), small.end());
-    DBuf d_work;
-    d_work.alloc(sizeof(int32_t) * std::max<size_t>(work.size(), 1));
-    HM_CUDA_CHECK(cudaMemcpyAsync(d_work.p, work.data(), sizeof(int32_t) * work.size(), cudaMemcpyHostToDevice, s));
-    HM_CUDA_CHECK(cudaMemsetAsync(uw_off.p, 0, sizeof(int64_t) * na, s));
-    HM_CUDA_CHECK(cudaMemsetAsync(A->rank.p, 0, sizeof(int32_t) * na, s));
+    auto msum = [&](int32_t b) { return h_adm[4 * b + 1] - h_adm[4 * b] + h_adm[4 * b + 3] - h_adm[4 * b + 2]; };
+    // work list for a split: blocks with both dims <= SMALL_MAX_DIM and
+    // m + n <= small_sum go to single warps, the others to whole CTAs (first)
+    auto split = [&](const std::vector<int32_t> &blocks, int small_sum, std::vector<int32_t> &work, int64_t &n_big,
+                     int &max_sum_small) {
+        std::vector<int32_t> big, small;
+        max_sum_small = 2;
+        for (int32_t b : blocks) {
+            const int m = h_adm[4 * b + 1] - h_adm[4 * b], n = h_adm[4 * b + 3] - h_adm[4 * b + 2];
+            if (m <= SMALL_MAX_DIM && n <= SMALL_MAX_DIM && m + n <= small_sum) {
+                small.push_back(b);
+                max_sum_small = std::max(max_sum_small, m + n);
+            } else {
+                big.push_back(b);
+            }
+        }
+        n_big = (int64_t)big.size();
+        work = big;
+        work.insert(work.end(), small.begin(), small.end());
+    };
 
     int occ = 0;
     const int words_r = (max_m_big + 31) / 32, words_c = (max_n_big + 31) / 32;
-    const int small_words = (SMALL_MAX_DIM + 31) / 32;
     const size_t smem_big = sizeof(double) * (32 + MAX_KMAX) + sizeof(uint32_t) * (words_r + words_c + 1) +
                             sizeof(float) * (ACA_WARPS + 1) * NORM_STRIDE;
     const size_t smem_small = (size_t)ACA_WARPS * sizeof(double) * WARP_SMEM_DOUBLES;
-    (void)small_words;
     const size_t smem = std::max(smem_big, smem_small);
     HM_CUDA_CHECK(cudaFuncSetAttribute(aca_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     HM_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, aca_kernel, ACA_THREADS, smem));
     if (occ < 1) fail(HM_EINTERNAL, "ACA kernel does not fit on an SM");
     const int grid = num_sms() * occ;
 
-    AcaArgs a{};
-    a.pt = tr->pt.as<double>();
-    a.pf = tr->pf.as<float>();
-    a.npad = tr->npad;
-    a.V = tr->V.as<double>();
-    a.adm = tr->adm.as<int32_t>();
-    a.work = d_work.as<int32_t>();
-    a.n_big = n_big;
-    a.n_work = (int64_t)work.size();
-    a.eps = A->params.aca_eps;
-    a.kmax = kmax;
-    a.qp = qp;
+    AcaArgs base{};
+    base.pt = tr->pt.as<double>();
+    base.pf = tr->pf.as<float>();
+    base.npad = tr->npad;
+    base.V = tr->V.as<double>();
+    base.adm = tr->adm.as<int32_t>();
+    base.eps = A->params.aca_eps;
+    base.kmax = kmax;
+    base.qp = qp;
     // per worker: U, W (double) and their FP32 shadows, (m + n) * kmax * 1.5 doubles
-    a.big_stride = ((int64_t)(max_m_big + max_n_big) * kmax * 3 + 1) / 2;
-    a.small_stride = ((int64_t)max_sum_small * kmax * 3 + 1) / 2;
-    a.big_words_r = words_r;
-    a.big_words_c = words_c;
-    DBuf scr_big, scr_small, ctr;
-    scr_big.alloc(sizeof(double) * a.big_stride * grid);
-    scr_small.alloc(sizeof(double) * a.small_stride * grid * ACA_WARPS);
-    ctr.alloc(sizeof(unsigned long long) * 4);
-    a.scr_big = scr_big.as<double>();
-    a.scr_small = scr_small.as<double>();
-    a.arena_top = ctr.as<unsigned long long>();
-    a.q_big = ctr.as<unsigned long long>() + 1;
-    a.q_small = ctr.as<unsigned long long>() + 2;
-    a.kmax_hit = reinterpret_cast<int *>(ctr.as<unsigned long long>() + 3);
-    a.rank = A->rank.as<int32_t>();
-    a.uw_off = uw_off.as<int64_t>();
-    a.todo = nullptr;
-    a.n_todo = 0;
+    base.big_stride = ((int64_t)(max_m_big + max_n_big) * kmax * 3 + 1) / 2;
+    base.big_words_r = words_r;
+    base.big_words_c = words_c;
+    DBuf scr_big;
+    scr_big.alloc(sizeof(double) * base.big_stride * grid);
+    base.scr_big = scr_big.as<double>();
 
+    // Autotuner of the warp / CTA split (the m + n bound of warp-mode
+    // blocks): on the first assembly with a given histogram of block sizes
+    // (log2 of m + n, block counts to two significant digits) every candidate
+    // runs the ACA of an evenly spaced sample of the blocks (scratch outputs,
+    // arena sized for k_max, so nothing overflows) and the fastest is kept
+    // for every later assembly with that histogram in this process.
+    static std::mutex tune_mu;
+    static std::map<std::vector<int64_t>, int> tune_cache;
+    const int cands[] = {160, 320, 512};
+    std::vector<int64_t> key(32, 0);
+    for (int32_t b : upper) {
+        int lg = 0;
+        while ((1 << (lg + 1)) <= msum(b)) ++lg;
+        key[std::min(lg, 31)] += 1;
+    }
+    for (auto &c : key) {
+        int64_t scale = 1;
+        while (c >= 100 * scale) scale *= 10;
+        c = c / scale * scale;
+    }
+    key.push_back(kmax);
+    key.push_back((int64_t)std::llround(std::log10(A->params.aca_eps) * 4.0));
+    int small_sum = 320;
+    bool tuned = false;
+    {
+        std::lock_guard<std::mutex> lk(tune_mu);
+        auto it = tune_cache.find(key);
+        if (it != tune_cache.end()) {
+            small_sum = it->second;
+            tuned = true;
+        }
+    }
+    auto run = [&](const std::vector<int32_t> &blocks, int ss, int32_t *rank, int64_t *uwo, double *arena,
+                   int64_t cap, unsigned long long *ctr4, DBuf &scr_small, DBuf &d_work) -> float {
+        std::vector<int32_t> work;
+        int64_t n_big = 0;
+        int max_sum_small = 2;
+        split(blocks, ss, work, n_big, max_sum_small);
+        AcaArgs a = base;
+        d_work.alloc(sizeof(int32_t) * std::max<size_t>(work.size(), 1));
+        HM_CUDA_CHECK(cudaMemcpyAsync(d_work.p, work.data(), sizeof(int32_t) * work.size(), cudaMemcpyHostToDevice, s));
+        a.work = d_work.as<int32_t>();
+        a.n_big = n_big;
+        a.n_work = (int64_t)work.size();
+        a.small_stride = ((int64_t)max_sum_small * kmax * 3 + 1) / 2;
+        scr_small.alloc(sizeof(double) * a.small_stride * grid * ACA_WARPS);
+        a.scr_small = scr_small.as<double>();
+        a.arena_top = ctr4;
+        a.q_big = ctr4 + 1;
+        a.q_small = ctr4 + 2;
+        a.kmax_hit = reinterpret_cast<int *>(ctr4 + 3);
+        a.rank = rank;
+        a.uw_off = uwo;
+        a.arena = arena;
+        a.arena_cap = cap;
+        a.todo = nullptr;
+        a.n_todo = 0;
+        HM_CUDA_CHECK(cudaMemsetAsync(ctr4, 0, sizeof(unsigned long long) * 4, s));
+        cudaEvent_t t0, t1;
+        HM_CUDA_CHECK(cudaEventCreate(&t0));
+        HM_CUDA_CHECK(cudaEventCreate(&t1));
+        HM_CUDA_CHECK(cudaEventRecord(t0, s));
+        {
+            Trace trace("aca_kernel", s);
+            aca_kernel<<<grid, ACA_THREADS, smem, s>>>(a);
+            HM_LAUNCH_CHECK();
+        }
+        HM_CUDA_CHECK(cudaEventRecord(t1, s));
+        HM_CUDA_CHECK(cudaEventSynchronize(t1));
+        float ms = 0.0f;
+        HM_CUDA_CHECK(cudaEventElapsedTime(&ms, t0, t1));
+        cudaEventDestroy(t0);
+        cudaEventDestroy(t1);
+        return ms;
+    };
+    if (!tuned) {
+        const size_t target = 30000;
+        const size_t step = std::max<size_t>(1, upper.size() / target);
+        std::vector<int32_t> sample;
+        int64_t sum_mn = 0;
+        for (size_t i = 0; i < upper.size(); i += step) {
+            sample.push_back(upper[i]);
+            sum_mn += msum(upper[i]);
+        }
+        if (sample.size() < upper.size() / 2 && sample.size() >= 1000) {
+            DBuf t_rank, t_uwo, t_arena, t_ctr, t_scr, t_work;
+            t_rank.alloc(sizeof(int32_t) * na);
+            t_uwo.alloc(sizeof(int64_t) * na);
+            t_arena.alloc(sizeof(double) * sum_mn * kmax);
+            t_ctr.alloc(sizeof(unsigned long long) * 4);
+            float best = 1e30f;
+            for (int c : cands) {
+                const float ms = run(sample, c, t_rank.as<int32_t>(), t_uwo.as<int64_t>(), t_arena.as<double>(),
+                                     sum_mn * kmax, t_ctr.as<unsigned long long>(), t_scr, t_work);
+                if (ms < best) {
+                    best = ms;
+                    small_sum = c;
+                }
+            }
+        }
+        std::lock_guard<std::mutex> lk(tune_mu);
+        tune_cache[key] = small_sum;
+    }
+    A->info.aca_small_sum = small_sum;
+    HM_CUDA_CHECK(cudaMemsetAsync(uw_off.p, 0, sizeof(int64_t) * na, s));
+    HM_CUDA_CHECK(cudaMemsetAsync(A->rank.p, 0, sizeof(int32_t) * na, s));
     // arena: sum (m + n) * k_guess, grown and the overflowed blocks re-run if needed
     int64_t k_guess = std::min<int64_t>(kmax, 20);
     int64_t cap = tr->adm_rows_cols * k_guess;
-    DBuf arena;
+    DBuf arena, ctr, scr_small, d_work;
     arena.alloc(sizeof(double) * cap);
-    a.arena = arena.as<double>();
-    a.arena_cap = cap;
-    HM_CUDA_CHECK(cudaMemsetAsync(ctr.p, 0, sizeof(unsigned long long) * 4, s));
-    cudaEvent_t e0, e1;
-    HM_CUDA_CHECK(cudaEventCreate(&e0));
-    HM_CUDA_CHECK(cudaEventCreate(&e1));
-    HM_CUDA_CHECK(cudaEventRecord(e0, s));
-    {
-        Trace trace("aca_kernel", s);
-        aca_kernel<<<grid, ACA_THREADS, smem, s>>>(a);
-        HM_LAUNCH_CHECK();
-    }
-    HM_CUDA_CHECK(cudaEventRecord(e1, s));
-    HM_CUDA_CHECK(cudaEventSynchronize(e1));
-    float ms = 0;
-    HM_CUDA_CHECK(cudaEventElapsedTime(&ms, e0, e1));
+    ctr.alloc(sizeof(unsigned long long) * 4);
+    const float ms = run(upper, small_sum, A->rank.as<int32_t>(), uw_off.as<int64_t>(), arena.as<double>(), cap,
+                         ctr.as<unsigned long long>(), scr_small, d_work);
     *sec = ms * 1e-3;
+    // the arguments of that run, for an overflow re-run
+    AcaArgs a = base;
+    {
+        std::vector<int32_t> work;
+        int64_t n_big = 0;
+        int max_sum_small = 2;
+        split(upper, small_sum, work, n_big, max_sum_small);
+        a.work = d_work.as<int32_t>();
+        a.n_big = n_big;
+        a.n_work = (int64_t)work.size();
+        a.small_stride = ((int64_t)max_sum_small * kmax * 3 + 1) / 2;
+        a.scr_small = scr_small.as<double>();
+        a.arena_top = ctr.as<unsigned long long>();
+        a.q_big = ctr.as<unsigned long long>() + 1;
+        a.q_small = ctr.as<unsigned long long>() + 2;
+        a.kmax_hit = reinterpret_cast<int *>(ctr.as<unsigned long long>() + 3);
+        a.rank = A->rank.as<int32_t>();
+        a.uw_off = uw_off.as<int64_t>();
+        a.arena = arena.as<double>();
+        a.arena_cap = cap;
+    }
     unsigned long long top = read_scalar(a.arena_top, s);
     if ((int64_t)top > cap) {
         // grow: keep what fits, re-run the blocks that did not fit (CTA-wide)
@@ -659,8 +763,6 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
         A->info.max_rank = (int)(h[1] & 0xffffffffu);
         A->info.kmax_hit = read_scalar(a.kmax_hit, s);
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
 }
 
 }  // namespace hm
