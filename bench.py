@@ -58,7 +58,12 @@ FF_FLOPS_PER_PAIR = 93
 
 # DRAM traffic per launch from an ncu capture, valid while the kernel's source
 # file is unchanged (sha256 of the file at capture time); null otherwise.
-TRAFFIC = {}
+TRAFFIC = {
+    "row_kernel.f64": {"source": "paper_1806_11558_gb300/csrc/mv_kernels.cuh",
+                       "sha256": "70701a252b20d346dcc90698b9f62f416efe2c775bf76cafecdbce7512461e06",
+                       "bytes_per_launch": 14.84e9 + 5.64e6,
+                       "profile": "profiles/row_kernel_f64_precision.md"},
+}
 
 
 def _file_sha(rel):
@@ -604,12 +609,39 @@ def run_differentiation(torch, hm):
     return out
 
 
+def run_blockmv(torch, hm):
+    """Small multi-RHS case (profiling): bumped icosphere level 6, leaf 128,
+    BF16 factors, three 16-right-hand-side tensor-core products."""
+    import meshgen
+    cfg = meshgen.config("bumped6")
+    n = cfg["T"].shape[0]
+    V, T = torch.from_numpy(cfg["V"]).cuda(), torch.from_numpy(cfg["T"]).cuda()
+    tree = hm.hm_build_tree(V, T, eta=1.5, leaf_size=128)
+    A = hm.hm_assemble(tree, aca_eps=1e-6, aca_kmax=64, ss_order=8, factor_dtype=hm.HM_BF16, dense_dtype=hm.HM_F32)
+    X = torch.randn((16, n), dtype=torch.float64, device="cuda")
+    Y = torch.empty_like(X)
+    a, b = _ev(torch), _ev(torch)
+    hm.hm_matvec_block(A, X, Y, prec=hm.HM_BF16)
+    a.record()
+    for _ in range(3):
+        hm.hm_matvec_block(A, X, Y, prec=hm.HM_BF16)
+    b.record()
+    torch.cuda.synchronize()
+    mi = hm.hm_matrix_get_info(A)
+    out = {"workload": "bumped icosphere level 6, leaf 128, BF16 factors, 16-RHS product", "n": n,
+           "ms": a.elapsed_time(b) / 3, "matrix_gb": (mi["dense_entries"] * 4 + mi["lr_entries"] * 2) / 1e9}
+    hm.hm_free(A)
+    hm.hm_free(tree)
+    return out
+
+
 def run_workload(name):
     import torch
     import paper_1806_11558_gb300 as hm
     from paper_1806_11558_gb300 import build as hb
     hb.build()
-    fn = {"large": run_large, "batching": run_batching, "differentiation": run_differentiation}[name]
+    fn = {"large": run_large, "batching": run_batching, "differentiation": run_differentiation,
+          "blockmv": run_blockmv}[name]
     ck = Clocks(torch.cuda.current_device())
     ck.start()
     out = fn(torch, hm)
@@ -629,7 +661,7 @@ def main():
                          "for profiling and parity runs, not bench lines")
     ap.add_argument("--profile-step", action="store_true",
                     help="run exactly one step (no warm-up, no extras) and print its phase times")
-    ap.add_argument("--workload", default=None, choices=["large", "batching", "differentiation"],
+    ap.add_argument("--workload", default=None, choices=["large", "batching", "differentiation", "blockmv"],
                     help="measure one of the other workloads once and print its numbers (not a bench line)")
     args = ap.parse_args()
     if args.workload:
