@@ -34,7 +34,7 @@
 
 namespace hm {
 
-constexpr int ACA_THREADS = 256;
+constexpr int ACA_THREADS = 128;
 constexpr int ACA_WARPS = ACA_THREADS / 32;
 constexpr int SMALL_MAX_DIM = 256;  // warp-mode blocks: m, n <= this
 // per-warp shared doubles in warp mode: fixed record, U/W row values, bitmaps, norm terms
@@ -356,7 +356,7 @@ __device__ void aca_store(const AcaArgs &A, int64_t b, int m, int n, int k, cons
     }
 }
 
-__global__ void __launch_bounds__(ACA_THREADS, 2) aca_kernel(AcaArgs A) {
+__global__ void __launch_bounds__(ACA_THREADS, 5) aca_kernel(AcaArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double s_red[ACA_WARPS];
     __shared__ Best s_bred[ACA_WARPS];
