@@ -102,10 +102,11 @@ typedef struct {
  *  inner_dtype: HM_F32 or HM_BF16 (factors of that type, dense FP32).
  *  precond    : 0 = none (the paper's unpreconditioned Krylov solve);
  *               1 = right block-Jacobi preconditioning with the inverses of
- *                   the diagonal blocks of the leaf clusters (FP64, computed
- *                   on the first such solve and kept with the matrix).  The
- *                   residual and the stopping test are those of the
- *                   unpreconditioned system. */
+ *                   the near-field diagonal blocks of runs of consecutive
+ *                   leaf clusters of at most 160 rows (one leaf when leaves
+ *                   are larger; FP64, computed on the first such solve and
+ *                   kept with the matrix).  The residual and the stopping
+ *                   test are those of the unpreconditioned system. */
 typedef struct {
     int32_t restart;
     int32_t max_iter;

@@ -37,6 +37,7 @@ namespace hm {
 constexpr int ACA_THREADS = 128;
 constexpr int ACA_WARPS = ACA_THREADS / 32;
 constexpr int SMALL_MAX_DIM = 256;  // warp-mode blocks: m, n <= this
+constexpr int HUGE_SUM = 2560;      // CTA-mode blocks with m + n above this use the large scratch
 // per-warp shared doubles in warp mode: fixed record, U/W row values, bitmaps, norm terms
 constexpr int WARP_SMEM_DOUBLES = 32 + MAX_KMAX + (SMALL_MAX_DIM + 31) / 32 + (2 + 2 * MAX_KMAX + 1) / 2;
 
@@ -56,6 +57,11 @@ struct AcaArgs {
     double *scr_small;
     int64_t small_stride;
     int big_words_r, big_words_c;  // bitmap words in CTA mode
+    int big_ctas;                  // CTAs that take the huge blocks
+    int64_t n_huge;                // work[0, n_huge): huge blocks (m + n > HUGE_SUM), CTA-wide, big_ctas CTAs
+    double *scr_med;               // per-CTA scratch of the other CTA-wide blocks
+    int64_t med_stride;
+    unsigned long long *q_huge;
     double *arena;
     int64_t arena_cap;
     unsigned long long *arena_top;
@@ -364,7 +370,11 @@ __global__ void __launch_bounds__(ACA_THREADS, 5) aca_kernel(AcaArgs A) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
     // ---------------- phase 1: large blocks, whole CTA ----------------
-    {
+    // 1a: the huge blocks (and an overflow re-run) on the first big_ctas CTAs,
+    // whose scratch fits any block; 1b: the other large blocks on every CTA
+    for (int tier = 0; tier < 2; ++tier) {
+        if (tier == 0 && (int)blockIdx.x >= A.big_ctas) continue;
+        if (tier == 1 && A.todo) break;
         AcaShared sh;
         double *d = reinterpret_cast<double *>(smem_raw);
         sh.fix = reinterpret_cast<float *>(d);
@@ -376,14 +386,16 @@ __global__ void __launch_bounds__(ACA_THREADS, 5) aca_kernel(AcaArgs A) {
         sh.ucol = sh.urow + A.big_words_r;
         sh.stage = reinterpret_cast<float *>(sh.ucol + A.big_words_c + ((A.big_words_r + A.big_words_c) & 1));
         sh.res = sh.stage + ACA_WARPS * NORM_STRIDE;
-        double *U = A.scr_big + (int64_t)blockIdx.x * A.big_stride;
+        double *U = tier == 0 ? A.scr_big + (int64_t)blockIdx.x * A.big_stride
+                              : A.scr_med + (int64_t)blockIdx.x * A.med_stride;
         for (;;) {
             long long q = 0;
-            if (threadIdx.x == 0) q = (long long)atomicAdd(A.q_big, 1ull);
+            if (threadIdx.x == 0) q = (long long)atomicAdd(tier == 0 ? A.q_huge : A.q_big, 1ull);
             q = Grp<true>::bcast(q, sh);
-            const int64_t nbig = A.todo ? A.n_todo : A.n_big;
-            if (q >= nbig) break;
-            const int64_t b = A.todo ? A.todo[q] : A.work[q];
+            const int64_t q0 = tier == 0 ? 0 : A.n_huge;
+            const int64_t qend = A.todo ? A.n_todo : (tier == 0 ? A.n_huge : A.n_big);
+            if (q0 + q >= qend) break;
+            const int64_t b = A.todo ? A.todo[q] : A.work[q0 + q];
             const int32_t rb = A.adm[4 * b], re = A.adm[4 * b + 1], cb = A.adm[4 * b + 2], ce = A.adm[4 * b + 3];
             const int m = re - rb, n = ce - cb;
             double *W = U + (int64_t)m * A.kmax;
@@ -512,21 +524,26 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
     auto msum = [&](int32_t b) { return h_adm[4 * b + 1] - h_adm[4 * b] + h_adm[4 * b + 3] - h_adm[4 * b + 2]; };
     // work list for a split: blocks with both dims <= SMALL_MAX_DIM and
     // m + n <= small_sum go to single warps, the others to whole CTAs (first)
+    // (huge blocks, m + n > HUGE_SUM, come first: only big_ctas CTAs hold scratch for them)
     auto split = [&](const std::vector<int32_t> &blocks, int small_sum, std::vector<int32_t> &work, int64_t &n_big,
-                     int &max_sum_small) {
-        std::vector<int32_t> big, small;
+                     int &max_sum_small, int64_t &n_huge) {
+        std::vector<int32_t> huge, big, small;
         max_sum_small = 2;
         for (int32_t b : blocks) {
             const int m = h_adm[4 * b + 1] - h_adm[4 * b], n = h_adm[4 * b + 3] - h_adm[4 * b + 2];
             if (m <= SMALL_MAX_DIM && n <= SMALL_MAX_DIM && m + n <= small_sum) {
                 small.push_back(b);
                 max_sum_small = std::max(max_sum_small, m + n);
+            } else if (m + n > HUGE_SUM) {
+                huge.push_back(b);
             } else {
                 big.push_back(b);
             }
         }
-        n_big = (int64_t)big.size();
-        work = big;
+        n_huge = (int64_t)huge.size();
+        n_big = n_huge + (int64_t)big.size();
+        work = huge;
+        work.insert(work.end(), big.begin(), big.end());
         work.insert(work.end(), small.begin(), small.end());
     };
 
@@ -554,9 +571,24 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
     base.big_stride = ((int64_t)(max_m_big + max_n_big) * kmax * 3 + 1) / 2;
     base.big_words_r = words_r;
     base.big_words_c = words_c;
-    DBuf scr_big;
-    scr_big.alloc(sizeof(double) * base.big_stride * grid);
+    // scratch of the huge blocks (it scales with the largest admissible
+    // block) for a bounded number of CTAs: two per SM, fewer where that
+    // exceeds a quarter of the free memory or 20 GB; every CTA holds scratch
+    // for the other large blocks (m + n <= HUGE_SUM)
+    {
+        size_t free_b = 0, total_b = 0;
+        HM_CUDA_CHECK(cudaMemGetInfo(&free_b, &total_b));
+        const int64_t budget = std::min<int64_t>(20LL << 30, (int64_t)(free_b / 4));
+        base.big_ctas = (int)std::min<int64_t>(grid, 2 * (int64_t)num_sms());
+        base.big_ctas = (int)std::max<int64_t>(std::min<int64_t>(num_sms(), grid),
+                                               std::min<int64_t>(base.big_ctas, budget / (8 * base.big_stride)));
+    }
+    base.med_stride = std::min<int64_t>(base.big_stride, ((int64_t)HUGE_SUM * kmax * 3 + 1) / 2);
+    DBuf scr_big, scr_med;
+    scr_big.alloc(sizeof(double) * base.big_stride * base.big_ctas);
+    scr_med.alloc(sizeof(double) * base.med_stride * grid);
     base.scr_big = scr_big.as<double>();
+    base.scr_med = scr_med.as<double>();
 
     // Autotuner of the warp / CTA split (the m + n bound of warp-mode
     // blocks): on the first assembly with a given histogram of block sizes
@@ -593,10 +625,11 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
     auto run = [&](const std::vector<int32_t> &blocks, int ss, int32_t *rank, int64_t *uwo, double *arena,
                    int64_t cap, unsigned long long *ctr4, DBuf &scr_small, DBuf &d_work) -> float {
         std::vector<int32_t> work;
-        int64_t n_big = 0;
+        int64_t n_big = 0, n_huge = 0;
         int max_sum_small = 2;
-        split(blocks, ss, work, n_big, max_sum_small);
+        split(blocks, ss, work, n_big, max_sum_small, n_huge);
         AcaArgs a = base;
+        a.n_huge = n_huge;
         d_work.alloc(sizeof(int32_t) * std::max<size_t>(work.size(), 1));
         HM_CUDA_CHECK(cudaMemcpyAsync(d_work.p, work.data(), sizeof(int32_t) * work.size(), cudaMemcpyHostToDevice, s));
         a.work = d_work.as<int32_t>();
@@ -609,13 +642,14 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
         a.q_big = ctr4 + 1;
         a.q_small = ctr4 + 2;
         a.kmax_hit = reinterpret_cast<int *>(ctr4 + 3);
+        a.q_huge = ctr4 + 4;
         a.rank = rank;
         a.uw_off = uwo;
         a.arena = arena;
         a.arena_cap = cap;
         a.todo = nullptr;
         a.n_todo = 0;
-        HM_CUDA_CHECK(cudaMemsetAsync(ctr4, 0, sizeof(unsigned long long) * 4, s));
+        HM_CUDA_CHECK(cudaMemsetAsync(ctr4, 0, sizeof(unsigned long long) * 5, s));
         cudaEvent_t t0, t1;
         HM_CUDA_CHECK(cudaEventCreate(&t0));
         HM_CUDA_CHECK(cudaEventCreate(&t1));
@@ -647,7 +681,7 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
             t_rank.alloc(sizeof(int32_t) * na);
             t_uwo.alloc(sizeof(int64_t) * na);
             t_arena.alloc(sizeof(double) * sum_mn * kmax);
-            t_ctr.alloc(sizeof(unsigned long long) * 4);
+            t_ctr.alloc(sizeof(unsigned long long) * 5);
             float best = 1e30f;
             for (int c : cands) {
                 const float ms = run(sample, c, t_rank.as<int32_t>(), t_uwo.as<int64_t>(), t_arena.as<double>(),
@@ -669,7 +703,7 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
     int64_t cap = tr->adm_rows_cols * k_guess;
     DBuf arena, ctr, scr_small, d_work;
     arena.alloc(sizeof(double) * cap);
-    ctr.alloc(sizeof(unsigned long long) * 4);
+    ctr.alloc(sizeof(unsigned long long) * 5);
     const float ms = run(upper, small_sum, A->rank.as<int32_t>(), uw_off.as<int64_t>(), arena.as<double>(), cap,
                          ctr.as<unsigned long long>(), scr_small, d_work);
     *sec = ms * 1e-3;
@@ -677,11 +711,13 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
     AcaArgs a = base;
     {
         std::vector<int32_t> work;
-        int64_t n_big = 0;
+        int64_t n_big = 0, n_huge = 0;
         int max_sum_small = 2;
-        split(upper, small_sum, work, n_big, max_sum_small);
+        split(upper, small_sum, work, n_big, max_sum_small, n_huge);
         a.work = d_work.as<int32_t>();
         a.n_big = n_big;
+        a.n_huge = n_huge;
+        a.q_huge = ctr.as<unsigned long long>() + 4;
         a.n_work = (int64_t)work.size();
         a.small_stride = ((int64_t)max_sum_small * kmax * 3 + 1) / 2;
         a.scr_small = scr_small.as<double>();
@@ -718,7 +754,7 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
         a.n_todo = nover;
         unsigned long long used_u = (unsigned long long)used;
         HM_CUDA_CHECK(cudaMemcpyAsync(a.arena_top, &used_u, sizeof(used_u), cudaMemcpyHostToDevice, s));
-        HM_CUDA_CHECK(cudaMemsetAsync(a.q_big, 0, sizeof(unsigned long long), s));
+        HM_CUDA_CHECK(cudaMemsetAsync(a.q_huge, 0, sizeof(unsigned long long), s));
         Trace trace("aca_kernel", s);
         aca_kernel<<<grid, ACA_THREADS, smem, s>>>(a);
         HM_LAUNCH_CHECK();

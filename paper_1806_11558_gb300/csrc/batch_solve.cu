@@ -27,6 +27,7 @@ void matvec_mrhs_morton(const hm_matrix *A, hm_dtype prec, const float *X, doubl
 int64_t mrhs_work_floats(const hm_matrix *A);
 void mrhs_prepare(const hm_matrix *A, hm_dtype prec, cudaStream_t s);
 void bj_setup(const hm_matrix *A, cudaStream_t s);
+void bj_apply_cols(const hm_matrix *A, const double *v, double *z, int cols, bool trans, bool low, cudaStream_t s);
 void permute_to_morton(const hm_tree *tr, const double *x, double *xm, cudaStream_t s);
 void permute_from_morton(const hm_tree *tr, const double *ym, double alpha, double beta, double *y, cudaStream_t s);
 
@@ -206,27 +207,6 @@ __global__ void bset_g0_kernel(int S, int m, const int *__restrict__ mask, const
     gs[0] = sqrt(nrm2[s]);
 }
 
-// z(col) = D^{-1} v(col) on every leaf cluster, all columns (grid.y = column)
-constexpr int BBJ_THREADS = 64;
-__global__ void __launch_bounds__(BBJ_THREADS) bbj_apply_kernel(const int32_t *leaf_begin, const int64_t *bj_off,
-                                                                const double *bj, const double *v, double *z,
-                                                                int64_t n) {
-    __shared__ double s_v[MAX_LEAF];
-    const int64_t r = blockIdx.x;
-    const int64_t c = blockIdx.y;
-    const int32_t r0 = leaf_begin[r], m = leaf_begin[r + 1] - r0;
-    const double *D = bj + bj_off[r];
-    const double *vc = v + c * n;
-    double *zc = z + c * n;
-    for (int j = threadIdx.x; j < m; j += BBJ_THREADS) s_v[j] = vc[r0 + j];
-    __syncthreads();
-    for (int i = threadIdx.x; i < m; i += BBJ_THREADS) {
-        double acc = 0.0;
-        for (int j = 0; j < m; ++j) acc = fma(D[(int64_t)j * m + i], s_v[j], acc);
-        zc[r0 + i] = acc;
-    }
-}
-
 // [R][n] FP64 <-> [n][16] blocks of the tensor-core product
 __global__ void to_block_kernel(const double *__restrict__ v, int64_t n, int R, float *__restrict__ X) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * BMR; e += (int64_t)gridDim.x * blockDim.x) {
@@ -353,13 +333,7 @@ struct Batch {
             HM_LAUNCH_CHECK();
         }
     }
-    void bj(const double *v, double *z, cudaStream_t s) {
-        const hm_tree *tr = A->tree;
-        Trace trace("batch_bj_apply", s);
-        bbj_apply_kernel<<<dim3((unsigned)tr->n_leaf, (unsigned)R), BBJ_THREADS, 0, s>>>(
-            tr->leaf_begin.as<int32_t>(), A->bj_off.as<int64_t>(), A->bj.as<double>(), v, z, n);
-        HM_LAUNCH_CHECK();
-    }
+    void bj(const double *v, double *z, bool low, cudaStream_t s) { bj_apply_cols(A, v, z, R, false, low, s); }
 };
 
 // Lockstep GMRES(m) of all systems for op x = b ([R][n], Morton), x = 0 on
@@ -408,7 +382,7 @@ static int gmres_batch(Batch &B, hm_dtype prec, const double *b, double *x, cons
             double *vj = V + (int64_t)j * vs;
             double *w = B.W.as<double>();
             if (B.precond) {
-                B.bj(vj, B.Z.as<double>(), s);
+                B.bj(vj, B.Z.as<double>(), prec != HM_F64, s);
                 B.apply(prec, B.Z.as<double>(), w, s);
             } else {
                 B.apply(prec, vj, w, s);
@@ -465,7 +439,7 @@ static int gmres_batch(Batch &B, hm_dtype prec, const double *b, double *x, cons
             badd_kernel<<<B.nitems(), 256, 0, s>>>(B.items.as<Item>(), V, vs, B.n, B.kk.as<int>(), B.y.as<double>(), m,
                                                    B.W.as<double>());
             HM_LAUNCH_CHECK();
-            B.bj(B.W.as<double>(), B.Z.as<double>(), s);
+            B.bj(B.W.as<double>(), B.Z.as<double>(), prec != HM_F64, s);
             badd_vec_kernel<<<gx(vs), 256, 0, s>>>(B.Z.as<double>(), vs, x);
             HM_LAUNCH_CHECK();
         } else {

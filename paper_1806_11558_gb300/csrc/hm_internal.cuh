@@ -296,7 +296,14 @@ struct hm_matrix {
     int64_t wp_entries = 0;
     int64_t n_partials = 0;  // length of the partial-projection vector
     // block-Jacobi preconditioner: inverse of each leaf cluster's diagonal block
-    hm::DBuf bj;        // [sum |rho|^2] double, row-major per leaf cluster
-    hm::DBuf bj_off;    // [n_leaf + 1] int64
+    // block-Jacobi preconditioner (built on the first preconditioned solve):
+    // inverses of the near-field diagonal blocks of runs of leaf clusters,
+    // column-major per block
+    hm::DBuf bj;        // [sum m_b^2] double
+    hm::DBuf bj32;      // its FP32 rounding (preconditioner of the inner solves)
+    hm::DBuf bj_off;    // [n_bj + 1] int64
+    hm::DBuf bj_begin;  // [n_bj + 1] int32: first row of each block
+    hm::DBuf bj_leaf;   // [n_bj + 1] int32: first leaf cluster of each block
+    int64_t n_bj = 0;
     hm_matrix_info info{};
 };

@@ -11,6 +11,7 @@
 // the FP64 master.  Dot products reduce in a fixed order (deterministic).
 #include <chrono>
 #include <cmath>
+#include <vector>
 
 #include "hm_internal.cuh"
 
@@ -171,44 +172,56 @@ static unsigned g1(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<i
 // ---------------------------------------------------------------------------
 // block-Jacobi preconditioner on the leaf clusters' diagonal blocks
 // ---------------------------------------------------------------------------
-__global__ void bj_size_kernel(const int32_t *leaf_begin, int64_t nl, int64_t *sz) {
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nl; r += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t m = leaf_begin[r + 1] - leaf_begin[r];
+// Blocks of the block-Jacobi preconditioner: runs of consecutive leaf
+// clusters (Morton order, never across two geometries) of at most BJ_ROWS
+// rows together — for the cardinality-halving trees the clusters two levels
+// above the leaves when those have 40 rows.  Block b holds the rows
+// [bj_begin[b], bj_begin[b+1]) and the leaves [bj_leaf[b], bj_leaf[b+1]).
+constexpr int BJ_ROWS = 160;
+constexpr int BJ_MAXM = 256;  // largest block (a single leaf may exceed BJ_ROWS)
+
+__global__ void bj_size_kernel(const int32_t *begin, int64_t nb, int64_t *sz) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nb; r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = begin[r + 1] - begin[r];
         sz[r] = m * m;
     }
 }
 
-// D_rho = A(rho, rho), read from rho's near-field row panel: the columns whose
-// index falls inside rho
-__global__ void bj_extract_kernel(const int32_t *leaf_begin, const int64_t *rho_off, const int32_t *rho_K,
-                                  const int64_t *rho_colptr, const int32_t *colidx, const double *dense,
-                                  const int64_t *bj_off, double *bj) {
-    const int64_t r = blockIdx.x;
-    const int32_t r0 = leaf_begin[r], m = leaf_begin[r + 1] - r0;
-    const int K = rho_K[r];
-    const double *P = dense + rho_off[r];
-    const int32_t *ci = colidx + rho_colptr[r];
-    double *D = bj + bj_off[r];
+// D_b = the near-field entries of A(b, b), read from the row panels of the
+// leaves of b: the columns whose index falls inside b (the far-field parts
+// of the diagonal block are left out)
+__global__ void bj_extract_kernel(const int32_t *begin, const int32_t *bleaf, const int32_t *leaf_begin,
+                                  const int64_t *rho_off, const int32_t *rho_K, const int64_t *rho_colptr,
+                                  const int32_t *colidx, const double *dense, const int64_t *bj_off, double *bj) {
+    const int64_t b = blockIdx.x;
+    const int32_t b0 = begin[b], m = begin[b + 1] - b0;
+    double *D = bj + bj_off[b];
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) D[e] = 0.0;
     __syncthreads();
-    for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        const int c = ci[k] - r0;
-        if (c >= 0 && c < m && k < K) {
-            // padding columns carry index 0 and value 0: they may alias column 0
-            // of the first leaf only with a zero value, which is skipped
-            for (int i = 0; i < m; ++i) {
-                const double v = P[(int64_t)i * K + k];
-                if (v != 0.0) D[i * m + c] = v;
+    for (int32_t r = bleaf[b]; r < bleaf[b + 1]; ++r) {
+        const int32_t r0 = leaf_begin[r], mr = leaf_begin[r + 1] - r0;
+        const int K = rho_K[r];
+        const double *P = dense + rho_off[r];
+        const int32_t *ci = colidx + rho_colptr[r];
+        for (int k = threadIdx.x; k < K; k += blockDim.x) {
+            const int c = ci[k] - b0;
+            if (c >= 0 && c < m) {
+                // padding columns carry index 0 and value 0: they may alias column 0
+                // of the first block only with a zero value, which is skipped
+                for (int i = 0; i < mr; ++i) {
+                    const double v = P[(int64_t)i * K + k];
+                    if (v != 0.0) D[(int64_t)(r0 - b0 + i) * m + c] = v;
+                }
             }
         }
     }
 }
 
-// In-place Gauss-Jordan inversion of the SPD block D (pivots stay positive,
-// no pivoting needed).
-__global__ void bj_invert_kernel(const int32_t *leaf_begin, const int64_t *bj_off, double *bj) {
+// In-place Gauss-Jordan inversion of D (diagonally dominant in practice: its
+// diagonal holds the self-interactions; no pivoting).
+__global__ void bj_invert_kernel(const int32_t *begin, const int64_t *bj_off, double *bj) {
     const int64_t r = blockIdx.x;
-    const int m = leaf_begin[r + 1] - leaf_begin[r];
+    const int m = begin[r + 1] - begin[r];
     double *D = bj + bj_off[r];
     __shared__ double s_piv;
     for (int p = 0; p < m; ++p) {
@@ -241,26 +254,37 @@ __global__ void bj_invert_kernel(const int32_t *leaf_begin, const int64_t *bj_of
     }
 }
 
-// z_rho = D_rho^{-1} v_rho: one thread per row over the column-major inverse
-// (consecutive threads read consecutive rows of one column), v_rho staged in
+// z_b = D_b^{-1} v_b: one thread per row over the column-major inverse
+// (consecutive threads read consecutive rows of one column), v_b staged in
 // shared memory; each row sums its columns in order.  trans: z = D^{-T} v,
 // the preconditioner of the transposed system (row-major reading).
-constexpr int BJ_THREADS = 64;
-__global__ void __launch_bounds__(BJ_THREADS) bj_apply_kernel(const int32_t *leaf_begin, const int64_t *bj_off,
-                                                              const double *bj, const double *v, double *z,
-                                                              int trans) {
-    __shared__ double s_v[MAX_LEAF];
+// TD = double: the FP64 preconditioner; TD = float: its FP32 rounding with
+// FP32 accumulation, for the inner solves on the low-precision copies.
+// grid.y = column of [cols][n] vectors.
+constexpr int BJ_THREADS = 128;
+template <class TD>
+__global__ void __launch_bounds__(BJ_THREADS) bj_apply_kernel(const int32_t *begin, const int64_t *bj_off,
+                                                              const TD *bj, const double *v, double *z, int trans,
+                                                              int64_t n) {
+    __shared__ TD s_v[BJ_MAXM];
     const int64_t r = blockIdx.x;
-    const int32_t r0 = leaf_begin[r], m = leaf_begin[r + 1] - r0;
-    const double *D = bj + bj_off[r];
-    for (int j = threadIdx.x; j < m; j += BJ_THREADS) s_v[j] = v[r0 + j];
+    const int32_t r0 = begin[r], m = begin[r + 1] - r0;
+    const TD *D = bj + bj_off[r];
+    const double *vc = v + (int64_t)blockIdx.y * n;
+    double *zc = z + (int64_t)blockIdx.y * n;
+    for (int j = threadIdx.x; j < m; j += BJ_THREADS) s_v[j] = (TD)vc[r0 + j];
     __syncthreads();
     for (int i = threadIdx.x; i < m; i += BJ_THREADS) {
-        double acc = 0.0;
+        TD acc = 0;
         const int64_t si = trans ? m : 1, sj = trans ? 1 : m;
         for (int j = 0; j < m; ++j) acc = fma(D[j * sj + i * si], s_v[j], acc);
-        z[r0 + i] = acc;
+        zc[r0 + i] = (double)acc;
     }
+}
+
+__global__ void bj_round_kernel(const double *a, int64_t n, float *o) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        o[i] = (float)a[i];
 }
 
 void bj_setup(const hm_matrix *Ac, cudaStream_t s) {
@@ -268,31 +292,68 @@ void bj_setup(const hm_matrix *Ac, cudaStream_t s) {
     if (A->bj.p) return;
     const hm_tree *tr = A->tree;
     const int64_t nl = tr->n_leaf;
-    A->bj_off.alloc(sizeof(int64_t) * (nl + 1));
-    bj_size_kernel<<<g1(nl), 256, 0, s>>>(tr->leaf_begin.as<int32_t>(), nl, A->bj_off.as<int64_t>());
+    // the blocks: greedy runs of consecutive leaves of one geometry
+    std::vector<int32_t> lb(nl + 1);
+    HM_CUDA_CHECK(cudaMemcpyAsync(lb.data(), tr->leaf_begin.p, sizeof(int32_t) * (nl + 1), cudaMemcpyDeviceToHost, s));
+    HM_CUDA_CHECK(cudaStreamSynchronize(s));
+    std::vector<int64_t> go = tr->geom_off;
+    if (go.size() < 2) go = {0, tr->n};
+    std::vector<int32_t> begin{0}, bleaf{0};
+    size_t g = 0;
+    for (int64_t r = 0; r < nl; ++r) {
+        while (g + 1 < go.size() && lb[r] >= go[g + 1]) ++g;
+        const int32_t cur = begin.back();
+        const bool same_geom = cur >= go[g];
+        if (r > bleaf.back() && (lb[r + 1] - cur > BJ_ROWS || !same_geom)) {
+            begin.push_back(lb[r]);
+            bleaf.push_back((int32_t)r);
+        }
+    }
+    begin.push_back((int32_t)tr->n);
+    bleaf.push_back((int32_t)nl);
+    const int64_t nb = (int64_t)begin.size() - 1;
+    A->n_bj = nb;
+    A->bj_begin.alloc(sizeof(int32_t) * (nb + 1));
+    A->bj_leaf.alloc(sizeof(int32_t) * (nb + 1));
+    HM_CUDA_CHECK(cudaMemcpyAsync(A->bj_begin.p, begin.data(), sizeof(int32_t) * (nb + 1), cudaMemcpyHostToDevice, s));
+    HM_CUDA_CHECK(cudaMemcpyAsync(A->bj_leaf.p, bleaf.data(), sizeof(int32_t) * (nb + 1), cudaMemcpyHostToDevice, s));
+    A->bj_off.alloc(sizeof(int64_t) * (nb + 1));
+    bj_size_kernel<<<g1(nb), 256, 0, s>>>(A->bj_begin.as<int32_t>(), nb, A->bj_off.as<int64_t>());
     HM_LAUNCH_CHECK();
-    HM_CUDA_CHECK(cudaMemsetAsync(A->bj_off.as<int64_t>() + nl, 0, sizeof(int64_t), s));
-    const int64_t tot = exclusive_scan_i64(A->bj_off.as<int64_t>(), A->bj_off.as<int64_t>(), nl + 1, s);
+    HM_CUDA_CHECK(cudaMemsetAsync(A->bj_off.as<int64_t>() + nb, 0, sizeof(int64_t), s));
+    const int64_t tot = exclusive_scan_i64(A->bj_off.as<int64_t>(), A->bj_off.as<int64_t>(), nb + 1, s);
     DBuf bj;
     bj.alloc(sizeof(double) * std::max<int64_t>(tot, 1));
-    bj_extract_kernel<<<(unsigned)nl, 256, 0, s>>>(tr->leaf_begin.as<int32_t>(), tr->rho_off.as<int64_t>(),
+    bj_extract_kernel<<<(unsigned)nb, 256, 0, s>>>(A->bj_begin.as<int32_t>(), A->bj_leaf.as<int32_t>(),
+                                                  tr->leaf_begin.as<int32_t>(), tr->rho_off.as<int64_t>(),
                                                   tr->rho_K.as<int32_t>(), tr->rho_colptr.as<int64_t>(),
                                                   tr->colidx.as<int32_t>(), A->dense.as<double>(),
                                                   A->bj_off.as<int64_t>(), bj.as<double>());
     HM_LAUNCH_CHECK();
-    bj_invert_kernel<<<(unsigned)nl, 256, 0, s>>>(tr->leaf_begin.as<int32_t>(), A->bj_off.as<int64_t>(),
-                                                 bj.as<double>());
+    bj_invert_kernel<<<(unsigned)nb, 256, 0, s>>>(A->bj_begin.as<int32_t>(), A->bj_off.as<int64_t>(), bj.as<double>());
+    HM_LAUNCH_CHECK();
+    A->bj32.alloc(sizeof(float) * std::max<int64_t>(tot, 1));
+    bj_round_kernel<<<g1(tot), 256, 0, s>>>(bj.as<double>(), tot, A->bj32.as<float>());
     HM_LAUNCH_CHECK();
     HM_CUDA_CHECK(cudaStreamSynchronize(s));
     A->bj = std::move(bj);
 }
 
-static void bj_apply(const hm_matrix *A, const double *v, double *z, cudaStream_t s, bool trans) {
-    const hm_tree *tr = A->tree;
-    Trace trace("bj_apply_kernel", s);
-    bj_apply_kernel<<<(unsigned)tr->n_leaf, BJ_THREADS, 0, s>>>(tr->leaf_begin.as<int32_t>(), A->bj_off.as<int64_t>(),
-                                                        A->bj.as<double>(), v, z, trans ? 1 : 0);
+// z = M^{-1} v for `cols` vectors [cols][n]; low: the FP32 copy (inner solves)
+void bj_apply_cols(const hm_matrix *A, const double *v, double *z, int cols, bool trans, bool low, cudaStream_t s) {
+    Trace trace(low ? "bj_apply_kernel.f32" : "bj_apply_kernel", s);
+    const dim3 grid((unsigned)A->n_bj, (unsigned)cols);
+    if (low)
+        bj_apply_kernel<float><<<grid, BJ_THREADS, 0, s>>>(A->bj_begin.as<int32_t>(), A->bj_off.as<int64_t>(),
+                                                           A->bj32.as<float>(), v, z, trans ? 1 : 0, A->tree->n);
+    else
+        bj_apply_kernel<double><<<grid, BJ_THREADS, 0, s>>>(A->bj_begin.as<int32_t>(), A->bj_off.as<int64_t>(),
+                                                            A->bj.as<double>(), v, z, trans ? 1 : 0, A->tree->n);
     HM_LAUNCH_CHECK();
+}
+
+static void bj_apply(const hm_matrix *A, const double *v, double *z, cudaStream_t s, bool trans, bool low) {
+    bj_apply_cols(A, v, z, 1, trans, low, s);
 }
 
 struct Gmres {
@@ -370,7 +431,7 @@ static hm_status gmres(const hm_matrix *A, hm_dtype prec, const double *b, doubl
             double *w = G.w.as<double>();
             if (precond) {
                 // right preconditioning: w = H (M^{-1} v_j)
-                bj_apply(A, vj, G.z.as<double>(), s, trans);
+                bj_apply(A, vj, G.z.as<double>(), s, trans, prec != HM_F64);
                 apply(A, prec, G.z.as<double>(), w, G.t, s, trans);
             } else {
                 apply(A, prec, vj, w, G.t, s, trans);
@@ -417,7 +478,7 @@ static hm_status gmres(const hm_matrix *A, hm_dtype prec, const double *b, doubl
             HM_CUDA_CHECK(cudaMemsetAsync(G.d.p, 0, sizeof(double) * n, s));
             add_combo_kernel<<<g1(n), 256, 0, s>>>(V, n, k, G.y.as<double>(), n, G.d.as<double>());
             HM_LAUNCH_CHECK();
-            bj_apply(A, G.d.as<double>(), G.z.as<double>(), s, trans);
+            bj_apply(A, G.d.as<double>(), G.z.as<double>(), s, trans, prec != HM_F64);
             axpy_kernel<<<g1(n), 256, 0, s>>>(1.0, G.z.as<double>(), n, x);
             HM_LAUNCH_CHECK();
         } else {
