@@ -31,7 +31,8 @@ sys.path.insert(0, ROOT)
 WORKLOAD = dict(workload="bumped icosphere level 7, Galerkin single-layer Laplace, P0",
                 panels=327680, leaf_size=64, eta=1.5, aca_eps=1e-7, aca_kmax=64, ss_order=8,
                 source=[3.0, 0.0, 0.0], solve_rel_tol=1e-12, inner="fp32 factors + fp32 near field",
-                inner_tol=1e-4, restart=int(os.environ.get("HM_BENCH_RESTART", "128")), precond=os.environ.get("HM_BENCH_PRECOND", "1") == "1")
+                inner_tol=1e-4, restart=int(os.environ.get("HM_BENCH_RESTART", "128")), precond=os.environ.get("HM_BENCH_PRECOND", "1") == "1",
+                use_graph=os.environ.get("HM_BENCH_GRAPH", "0") == "1")
 METRIC = "H-matrix setup s, H-matvec GB/s, solve s at 1e-8 rel. accuracy: mixed vs FP64"
 FLOPS_PER_PAIR = 11  # 3 sub + 3 mul + 2 add (|x-y|^2) + rsqrt + multiply-add (weight)
 PAIRS_PER_ENTRY = 49
@@ -52,8 +53,8 @@ CASE = "precision"
 # FP32 128 FFMA / SM / clock; FMA = 2 flops.
 FP64_PEAK_TFLOPS = 152 * 2.07e9 * 2 * 2 / 1e12   # 1.26
 FP32_PEAK_TFLOPS = 152 * 2.07e9 * 128 * 2 / 1e12  # 80.5
-# FP32 flops of one pair evaluation in the double-float far-field entry of the
-# ACA (TwoSum 6, TwoProduct 2 with its FMA counted 2, ...): 93 per pair
+# FP32 flops of one pair evaluation in the double-float entry (ACA and the
+# regular near field; TwoSum 6, TwoProduct 2 with its FMA counted 2, ...): 93 per pair
 FF_FLOPS_PER_PAIR = 93
 
 # DRAM traffic per launch from an ncu capture, valid while the kernel's source
@@ -99,7 +100,8 @@ def algorithmic_work(mi, ti, dense_leaves, n):
         "col_kernel.f32": ("hbm", 4.0 * w + 4.0 * n + 4.0 * w * nl / n, "byte"),
         "row_kernel.bf16": ("hbm", 4.0 * d + 2.0 * u + 4.0 * (n + K) + 8.0 * n, "byte"),
         "col_kernel.bf16": ("hbm", 2.0 * w + 4.0 * n + 4.0 * w * nl / n, "byte"),
-        "nearfield_kernel": ("alu", float(nf_entries) * PAIRS_PER_ENTRY * FLOPS_PER_PAIR, "flop"),
+        "nearfield_kernel": ("alu32", float(nf_entries) * PAIRS_PER_ENTRY * FF_FLOPS_PER_PAIR, "flop"),
+        "nearfield_kernel.f64": ("alu", float(nf_entries) * PAIRS_PER_ENTRY * FLOPS_PER_PAIR, "flop"),
         "aca_kernel": ("alu32", float(mi["aca_entries"]) * PAIRS_PER_ENTRY * FF_FLOPS_PER_PAIR, "flop"),
     }
 
@@ -211,11 +213,11 @@ def run_ours(args, rank, world):
         hm.hm_load_vector(tree, src, f)
         e[3].record(stream)
         i64 = hm.hm_solve(A, f[0], x64, rel_tol=W["solve_rel_tol"], restart=W["restart"], max_iter=5000,
-                          precond=int(W["precond"]))
+                          precond=int(W["precond"]), use_graph=int(W["use_graph"]))
         e[4].record(stream)
         imx = hm.hm_solve(A, f[0], xmx, rel_tol=W["solve_rel_tol"], restart=W["restart"], max_iter=5000, refine=1,
                           inner_tol=W["inner_tol"], inner_dtype=hm.HM_F32, max_refine=50,
-                          precond=int(W["precond"]))
+                          precond=int(W["precond"]), use_graph=int(W["use_graph"]))
         e[5].record(stream)
         torch.cuda.synchronize()
         t["tree_s"] = e[0].elapsed_time(e[1]) / 1e3
@@ -535,16 +537,30 @@ def run_batching(torch, hm):
     hm.hm_load_vector_geom(tree, src, F)
     X = torch.zeros_like(F)
     e[3].record()
-    info = hm.hm_solve(A, F, X, rel_tol=1e-6, restart=60, max_iter=5000, precond=1, batched=1, refine=1,
-                       inner_dtype=hm.HM_F32, inner_tol=1e-4, max_refine=40)
+    opts = dict(rel_tol=1e-6, restart=60, max_iter=5000, precond=1, batched=1, refine=1, inner_dtype=hm.HM_F32,
+                inner_tol=1e-4, max_refine=40)
+    info = hm.hm_solve(A, F, X, **opts)
     e[4].record()
     torch.cuda.synchronize()
     hm.hm_trace_enable(False)
+    # again, with the block-Jacobi inverses and the multi-RHS panels in place:
+    # host-driven Arnoldi loop, then the CUDA-graph loop
+    warm = {}
+    for name, ug in (("solve_warm_s", 0), ("solve_warm_graph_s", 1)):
+        Xw = torch.zeros_like(F)
+        a, b = _ev(torch), _ev(torch)
+        a.record()
+        iw = hm.hm_solve(A, F, Xw, use_graph=ug, **opts)
+        b.record()
+        torch.cuda.synchronize()
+        warm[name] = a.elapsed_time(b) / 1e3
+        warm[name.replace("_s", "_iters")] = iw.iters
+        warm[name.replace("_s", "_same_x")] = bool(torch.equal(Xw, X))
     mi = hm.hm_matrix_get_info(A)
     out = {"workload": "batching: 64 stretched icospheres, levels 3..6, %d panels, 4 sources each, eps 1e-5" % n,
            "tree_s": e[0].elapsed_time(e[1]) / 1e3, "assemble_s": e[1].elapsed_time(e[2]) / 1e3,
            "aca_s": mi["s_aca"], "nearfield_s": mi["s_nearfield"], "solve_s": e[3].elapsed_time(e[4]) / 1e3,
-           "systems": 256, "lockstep_iters": info.iters, "refine_steps": info.refine_steps,
+           "systems": 256, "lockstep_iters": info.iters, "refine_steps": info.refine_steps, **warm,
            "max_rel_resid": info.rel_resid, "kernels": kernel_table(hm.hm_trace_read(), 1)}
     hm.hm_free(A)
     hm.hm_free(tree)

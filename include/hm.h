@@ -80,6 +80,12 @@ typedef struct {
  *                 low-precision copy of the low-rank factors.
  *  dense_dtype  : HM_F64 (FP64 only) or HM_F32 to also keep an FP32 copy of
  *                 the dense near field.
+ *  nearfield_fp64 : 0 (default) = the regular near-field entries (dense
+ *                 leaves, panels not touching) in double-float arithmetic on
+ *                 the FP32 units (about 48 significant bits, ~1e-14
+ *                 relative), like the ACA entries; 1 = in FP64 arithmetic.
+ *                 Touching pairs are always FP64.  Leaves wider than 250
+ *                 panels always use FP64.
  *  The FP64 master copy is always kept. */
 typedef struct {
     double aca_eps;
@@ -87,6 +93,7 @@ typedef struct {
     int32_t ss_order;
     hm_dtype factor_dtype;
     hm_dtype dense_dtype;
+    int32_t nearfield_fp64;
 } hm_assemble_params;
 
 /* Solver parameters.
@@ -124,6 +131,13 @@ typedef struct {
                          FP64 master one column after the other.  info reports
                          the lockstep step count and the largest relative
                          residual.  0 = one system after the other. */
+    int32_t use_graph; /* 1 = run the Arnoldi steps of every GMRES cycle as one
+                          CUDA graph (a WHILE conditional node over one step,
+                          the stop decided on the device); the host waits
+                          once per cycle instead of once per step.  Same
+                          kernels and arithmetic, so the same iterates as 0.
+                          The graph is built on the first cycle of the call
+                          (one per precision used). */
 } hm_solve_params;
 
 typedef struct {

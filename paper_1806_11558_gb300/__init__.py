@@ -39,13 +39,14 @@ class TreeParams(ctypes.Structure):
 
 class AssembleParams(ctypes.Structure):
     _fields_ = [("aca_eps", ctypes.c_double), ("aca_kmax", ctypes.c_int32), ("ss_order", ctypes.c_int32),
-                ("factor_dtype", ctypes.c_int), ("dense_dtype", ctypes.c_int)]
+                ("factor_dtype", ctypes.c_int), ("dense_dtype", ctypes.c_int), ("nearfield_fp64", ctypes.c_int32)]
 
 
 class SolveParams(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("rel_tol", ctypes.c_double),
                 ("refine", ctypes.c_int32), ("max_refine", ctypes.c_int32), ("inner_tol", ctypes.c_double),
-                ("inner_dtype", ctypes.c_int), ("precond", ctypes.c_int32), ("batched", ctypes.c_int32)]
+                ("inner_dtype", ctypes.c_int), ("precond", ctypes.c_int32), ("batched", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -199,9 +200,11 @@ def hm_load_vector_geom(tree, sources, f, stream=None):
     return f
 
 
-def hm_assemble(tree, aca_eps=1e-6, aca_kmax=64, ss_order=8, factor_dtype=HM_F64, dense_dtype=HM_F64, stream=None):
+def hm_assemble(tree, aca_eps=1e-6, aca_kmax=64, ss_order=8, factor_dtype=HM_F64, dense_dtype=HM_F64,
+                nearfield_fp64=0, stream=None):
     out = ctypes.c_void_p()
-    prm = AssembleParams(float(aca_eps), int(aca_kmax), int(ss_order), int(factor_dtype), int(dense_dtype))
+    prm = AssembleParams(float(aca_eps), int(aca_kmax), int(ss_order), int(factor_dtype), int(dense_dtype),
+                         int(nearfield_fp64))
     _check(lib().hm_assemble(tree, ctypes.byref(prm), _stream(stream), ctypes.byref(out)))
     return out
 
@@ -258,12 +261,12 @@ def hm_matvec_noalloc(A, x, y, trans=0, prec=HM_F64, alpha=1.0, beta=0.0, stream
 
 
 def hm_solve(A, b, x, trans=0, restart=30, max_iter=3000, rel_tol=1e-10, refine=0, max_refine=20, inner_tol=1e-4,
-             inner_dtype=HM_F32, precond=0, batched=0, stream=None, raise_on_noconv=True):
+             inner_dtype=HM_F32, precond=0, batched=0, use_graph=0, stream=None, raise_on_noconv=True):
     """Solves op(H) x = b; returns the SolveInfo of the (last) right-hand side."""
     import torch
     nrhs = 1 if b.dim() == 1 else b.shape[0]
     prm = SolveParams(int(restart), int(max_iter), float(rel_tol), int(refine), int(max_refine), float(inner_tol),
-                      int(inner_dtype), int(precond), int(batched))
+                      int(inner_dtype), int(precond), int(batched), int(use_graph))
     info = SolveInfo()
     st = lib().hm_solve(A, int(trans), nrhs, _ptr(b, torch.float64), _ptr(x, torch.float64), ctypes.byref(prm),
                         _stream(stream), ctypes.byref(info))

@@ -19,7 +19,7 @@ hm_tree *build_tree_impl(const double *d_V, int64_t nv, const int32_t *d_T, int6
                          const std::vector<int64_t> &goff, cudaStream_t s);
 void load_vector_geom_impl(const hm_tree *tr, const double *src, int nsrc, double *f, cudaStream_t s);
 void assemble_nearfield(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStream_t s, int *d_err,
-                        double *sec_regular, double *sec_singular);
+                        double *sec_regular, double *sec_singular, bool fp64);
 void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStream_t s, double *sec, DBuf &uw,
                   DBuf &uw_off);
 void build_lr_panels(hm_matrix *A, const DBuf &uw, const DBuf &uw_off, cudaStream_t s);
@@ -124,6 +124,7 @@ hm_status hm_assemble(const hm_tree *tree, const hm_assemble_params *params, hm_
         if (params->ss_order < 1 || params->ss_order > MAX_SS) fail(HM_EINVAL, "ss_order must be in [1, 16]");
         if (params->factor_dtype < HM_F64 || params->factor_dtype > HM_BF16) fail(HM_EINVAL, "bad factor_dtype");
         if (params->dense_dtype != HM_F64 && params->dense_dtype != HM_F32) fail(HM_EINVAL, "bad dense_dtype");
+        if (params->nearfield_fp64 != 0 && params->nearfield_fp64 != 1) fail(HM_EINVAL, "nearfield_fp64 must be 0 or 1");
         cudaStream_t s = (cudaStream_t)stream;
         const auto t0 = std::chrono::steady_clock::now();
         std::unique_ptr<hm_matrix> A(new hm_matrix());
@@ -134,7 +135,7 @@ hm_status hm_assemble(const hm_tree *tree, const hm_assemble_params *params, hm_
         err.alloc(sizeof(int));
         HM_CUDA_CHECK(cudaMemsetAsync(err.p, 0, sizeof(int), s));
         double sr = 0, ss = 0, sa = 0;
-        assemble_nearfield(tree, A.get(), qp, s, err.as<int>(), &sr, &ss);
+        assemble_nearfield(tree, A.get(), qp, s, err.as<int>(), &sr, &ss, params->nearfield_fp64 != 0);
         {
             DBuf uw, uw_off;
             assemble_aca(tree, A.get(), qp, s, &sa, uw, uw_off);
@@ -252,6 +253,7 @@ hm_status hm_solve(const hm_matrix *A, int32_t trans, int32_t nrhs, const double
             if (params->inner_dtype < HM_F64 || params->inner_dtype > HM_BF16) fail(HM_EINVAL, "bad inner_dtype");
         }
         if (params->batched != 0 && params->batched != 1) fail(HM_EINVAL, "batched must be 0 or 1");
+        if (params->use_graph != 0 && params->use_graph != 1) fail(HM_EINVAL, "use_graph must be 0 or 1");
         if (params->batched && trans) fail(HM_EINVAL, "the batched solve is for trans = 0");
         if (params->batched && params->refine && params->inner_dtype != HM_F64 && !A->dense32.p)
             fail(HM_EINVAL, "the FP32 near-field copy was not assembled");

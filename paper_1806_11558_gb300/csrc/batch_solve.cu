@@ -12,9 +12,13 @@
 // (its rotations, coefficients and vectors are left alone) while the others
 // continue.  The FP64 iterative refinement around it follows solve.cu: the
 // residual B - H_64 X in FP64, the inner solves on the low-precision copy.
-// Every reduction runs in a fixed order.
+// Every reduction runs in a fixed order.  With use_graph the lockstep
+// Arnoldi steps of a cycle run as one CUDA graph (a WHILE node over one step,
+// the per-system stops and the end of the loop decided on the device).
 #include <chrono>
 #include <cmath>
+#include <map>
+#include <memory>
 
 #include "hm_internal.cuh"
 
@@ -46,7 +50,8 @@ static unsigned gx(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<i
 __global__ void __launch_bounds__(BTHREADS) bdots_kernel(const Item *__restrict__ items, const double *__restrict__ V,
                                                          int64_t vstride, int64_t n, int nv,
                                                          const double *__restrict__ w, const int *__restrict__ act,
-                                                         double *__restrict__ part) {
+                                                         double *__restrict__ part, const LoopCtl *ctl) {
+    if (ctl) nv = ctl->j + 1;  // graph form: V_0..V_j of step j
     __shared__ double s_red[BTHREADS / 32][8];
     const Item it = items[blockIdx.x];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -82,7 +87,8 @@ __global__ void __launch_bounds__(BTHREADS) bdots_kernel(const Item *__restrict_
 
 // out[s][l] = sum over the items of s (in order) of part[item][l]; accumulate adds
 __global__ void bdots_final_kernel(const int64_t *__restrict__ iptr, int S, int nv, const double *__restrict__ part,
-                                   double *__restrict__ out, int ld, int accumulate) {
+                                   double *__restrict__ out, int ld, int accumulate, const LoopCtl *ctl) {
+    if (ctl) nv = ctl->j + 1;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < S * nv; e += gridDim.x * blockDim.x) {
         const int s = e / nv, l = e - (e / nv) * nv;
         double t = 0.0;
@@ -94,7 +100,8 @@ __global__ void bdots_final_kernel(const int64_t *__restrict__ iptr, int S, int 
 // w(col, i) -= sum_l V_l(col, i) h[s][l]   (active systems)
 __global__ void bsub_kernel(const Item *__restrict__ items, const double *__restrict__ V, int64_t vstride, int64_t n,
                             int nv, const double *__restrict__ h, int ldh, const int *__restrict__ act,
-                            double *__restrict__ w) {
+                            double *__restrict__ w, const LoopCtl *ctl) {
+    if (ctl) nv = ctl->j + 1;
     const Item it = items[blockIdx.x];
     if (!act[it.sys]) return;
     const double *hs = h + (int64_t)it.sys * ldh;
@@ -124,7 +131,13 @@ __global__ void badd_kernel(const Item *__restrict__ items, const double *__rest
 // dst(col, i) = src(col, i) / sqrt(nrm2[s]) for the systems in mask (0 when the norm is 0)
 __global__ void bscale_kernel(const Item *__restrict__ items, const double *__restrict__ src, int64_t n,
                               const double *__restrict__ nrm2, int nstride, const int *__restrict__ mask,
-                              double *__restrict__ dst) {
+                              double *__restrict__ dst, const LoopCtl *ctl, int64_t vs, int m) {
+    if (ctl) {
+        // graph form: dst = V_j with j = ctl->j (already advanced), 1 <= j <= m
+        const int j = ctl->j;
+        if (j < 1 || j > m) return;
+        dst += (int64_t)j * vs;
+    }
     const Item it = items[blockIdx.x];
     if (!mask[it.sys]) return;
     const double nr = sqrt(nrm2[(int64_t)it.sys * nstride]);
@@ -145,7 +158,9 @@ __global__ void badd_vec_kernel(const double *__restrict__ a, int64_t n, double 
 }
 
 // h[s][l] += h2[s][l], l < nv
-__global__ void badd_coef_kernel(int S, int nv, int ld, const double *__restrict__ h2, double *__restrict__ h) {
+__global__ void badd_coef_kernel(int S, int nv, int ld, const double *__restrict__ h2, double *__restrict__ h,
+                                 const LoopCtl *ctl) {
+    if (ctl) nv = ctl->j + 1;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < S * nv; e += gridDim.x * blockDim.x) {
         const int s = e / nv, l = e - (e / nv) * nv;
         h[(int64_t)s * ld + l] += h2[(int64_t)s * ld + l];
@@ -154,12 +169,14 @@ __global__ void badd_coef_kernel(int S, int nv, int ld, const double *__restrict
 
 // Givens step j of every active system (one thread per system); writes
 // est[s] = |g_s[j+1]| and hn[s] = ||w_s||
-__global__ void bgivens_kernel(int S, int m, int j, const int *__restrict__ act, const double *__restrict__ h,
+__global__ void bgivens_kernel(int S, int m, int j, int *__restrict__ act, const double *__restrict__ h,
                                int ldh, const double *__restrict__ wn2, double *__restrict__ H,
                                double *__restrict__ cs, double *__restrict__ sn, double *__restrict__ g,
-                               double *__restrict__ est, double *__restrict__ hn) {
+                               double *__restrict__ est, double *__restrict__ hn, const LoopCtl *ctl,
+                               const double *__restrict__ thr, int *__restrict__ kk) {
+    if (ctl) j = ctl->j;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S || !act[s]) return;
+    if (s >= S || !act[s] || j < 0 || j >= m) return;
     double *col = H + (int64_t)s * (m + 1) * m + (int64_t)j * (m + 1);
     double *c = cs + (int64_t)s * m, *sg = sn + (int64_t)s * m, *gs = g + (int64_t)s * (m + 1);
     for (int l = 0; l <= j; ++l) col[l] = h[(int64_t)s * ldh + l];
@@ -179,6 +196,40 @@ __global__ void bgivens_kernel(int S, int m, int j, const int *__restrict__ act,
     gs[j] = c[j] * gs[j];
     est[s] = fabs(gs[j + 1]);
     hn[s] = hh;
+    if (ctl) {
+        // graph form: the per-system stopping test of the host loop
+        kk[s] = j + 1;
+        if (est[s] <= thr[s] || hh == 0.0 || j + 1 >= ctl->lim) act[s] = 0;
+    }
+}
+
+// Graph form, end of step j: advance ctl->j and end the loop when no system
+// is active or the cycle's step limit is reached (j grows every iteration and
+// j >= lim stops, so the loop ends after at most lim <= m iterations).
+__global__ void bstep_end_kernel(int S, int m, const int *__restrict__ act, LoopCtl *ctl,
+                                 cudaGraphConditionalHandle loop) {
+    __shared__ int s_any;
+    if (threadIdx.x == 0) s_any = 0;
+    __syncthreads();
+    int any = 0;
+    for (int k = threadIdx.x; k < S; k += blockDim.x) any |= act[k];
+    if (any) atomicOr(&s_any, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int k = ctl->j + 1;
+        ctl->j = k;
+        cudaGraphSetConditional(loop, (s_any && k < ctl->lim && k < m) ? 1u : 0u);
+    }
+}
+
+// out = V_j (all columns) with j = ctl->j
+__global__ void bvj_copy_kernel(const double *__restrict__ V, int64_t vs, int m, const LoopCtl *ctl,
+                                double *__restrict__ out) {
+    const int j = ctl->j;
+    if (j < 0 || j >= m) return;
+    const double *src = V + (int64_t)j * vs;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < vs; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = src[i];
 }
 
 // y_s = R_s^{-1} g_s over the k_s first rotations (one thread per system)
@@ -234,8 +285,9 @@ struct Batch {
     bool precond;
     std::vector<Item> items_h;
     std::vector<int64_t> iptr_h;
-    DBuf items, iptr, V, W, Z, AX, part, h, h2, H, cs, sn, g, y, est, hn, nrm, act, cyc, kk, ones, mv, mvf;
+    DBuf items, iptr, V, W, Z, AX, part, h, h2, H, cs, sn, g, y, est, hn, nrm, act, cyc, kk, ones, mv, mvf, ctl, thr, xin;
     int64_t vstride;
+    std::map<int, std::unique_ptr<LoopGraph>> graphs;  // graph form of the Arnoldi loop, keyed by precision
 
     Batch(const hm_matrix *A_, int R_, int m_, bool pc, hm_dtype inner, cudaStream_t s)
         : A(A_), R(R_), m(m_), precond(pc) {
@@ -279,6 +331,8 @@ struct Batch {
         cyc.alloc(sizeof(int) * S);
         kk.alloc(sizeof(int) * S);
         ones.alloc(sizeof(int) * S);
+        ctl.alloc(sizeof(LoopCtl));
+        thr.alloc(sizeof(double) * S);
         {
             std::vector<int> o(S, 1);
             HM_CUDA_CHECK(cudaMemcpyAsync(ones.p, o.data(), sizeof(int) * S, cudaMemcpyHostToDevice, s));
@@ -294,12 +348,13 @@ struct Batch {
 
     // out[s][l] = V_l . w per system, l < nv
     void dots(const double *Vb, int nv, const double *w, const int *mask, double *out, int ld, int accumulate,
-              cudaStream_t s) {
+              cudaStream_t s, const LoopCtl *c = nullptr) {
         Trace trace("batch_dots", s);
-        bdots_kernel<<<nitems(), BTHREADS, 0, s>>>(items.as<Item>(), Vb, vstride, n, nv, w, mask, part.as<double>());
+        bdots_kernel<<<nitems(), BTHREADS, 0, s>>>(items.as<Item>(), Vb, vstride, n, nv, w, mask, part.as<double>(),
+                                                   c);
         HM_LAUNCH_CHECK();
-        bdots_final_kernel<<<gx((int64_t)S * nv), 256, 0, s>>>(iptr.as<int64_t>(), S, nv, part.as<double>(), out, ld,
-                                                              accumulate);
+        bdots_final_kernel<<<gx((int64_t)S * (c ? m : nv)), 256, 0, s>>>(iptr.as<int64_t>(), S, nv, part.as<double>(),
+                                                                        out, ld, accumulate, c);
         HM_LAUNCH_CHECK();
     }
     // per-system squared norms of v into nrm (host copy returned)
@@ -336,11 +391,56 @@ struct Batch {
     void bj(const double *v, double *z, bool low, cudaStream_t s) { bj_apply_cols(A, v, z, R, false, low, s); }
 };
 
+// The lockstep Arnoldi loop of a cycle as a graph: one step per iteration of
+// the WHILE node, the step index in B.ctl (the same kernels as the host loop).
+static const LoopGraph &batch_step_graph(Batch &B, hm_dtype prec) {
+    auto it = B.graphs.find((int)prec);
+    if (it != B.graphs.end()) return *it->second;
+    const int S = B.S, m = B.m;
+    const int64_t vs = B.vstride;
+    if (!B.xin.p) B.xin.alloc(sizeof(double) * vs);
+    auto L = std::make_unique<LoopGraph>();
+    L->build([&](cudaStream_t cs, cudaGraphConditionalHandle loop) {
+        double *V = B.V.as<double>(), *w = B.W.as<double>();
+        LoopCtl *c = B.ctl.as<LoopCtl>();
+        bvj_copy_kernel<<<gx(vs), 256, 0, cs>>>(V, vs, m, c, B.xin.as<double>());
+        HM_LAUNCH_CHECK();
+        if (B.precond) {
+            B.bj(B.xin.as<double>(), B.Z.as<double>(), prec != HM_F64, cs);
+            B.apply(prec, B.Z.as<double>(), w, cs);
+        } else {
+            B.apply(prec, B.xin.as<double>(), w, cs);
+        }
+        B.dots(V, 0, w, B.cyc.as<int>(), B.h.as<double>(), m + 1, 0, cs, c);
+        bsub_kernel<<<B.nitems(), 256, 0, cs>>>(B.items.as<Item>(), V, vs, B.n, 0, B.h.as<double>(), m + 1,
+                                                B.cyc.as<int>(), w, c);
+        HM_LAUNCH_CHECK();
+        B.dots(V, 0, w, B.cyc.as<int>(), B.h2.as<double>(), m + 1, 0, cs, c);
+        bsub_kernel<<<B.nitems(), 256, 0, cs>>>(B.items.as<Item>(), V, vs, B.n, 0, B.h2.as<double>(), m + 1,
+                                                B.cyc.as<int>(), w, c);
+        HM_LAUNCH_CHECK();
+        badd_coef_kernel<<<gx((int64_t)S * m), 256, 0, cs>>>(S, 0, m + 1, B.h2.as<double>(), B.h.as<double>(), c);
+        HM_LAUNCH_CHECK();
+        B.dots(w, 1, w, B.cyc.as<int>(), B.nrm.as<double>(), 1, 0, cs);
+        bgivens_kernel<<<(S + 127) / 128, 128, 0, cs>>>(S, m, 0, B.cyc.as<int>(), B.h.as<double>(), m + 1,
+                                                       B.nrm.as<double>(), B.H.as<double>(), B.cs.as<double>(),
+                                                       B.sn.as<double>(), B.g.as<double>(), B.est.as<double>(),
+                                                       B.hn.as<double>(), c, B.thr.as<double>(), B.kk.as<int>());
+        HM_LAUNCH_CHECK();
+        bstep_end_kernel<<<1, 256, 0, cs>>>(S, m, B.cyc.as<int>(), c, loop);
+        HM_LAUNCH_CHECK();
+        bscale_kernel<<<B.nitems(), 256, 0, cs>>>(B.items.as<Item>(), w, B.n, B.nrm.as<double>(), 1, B.cyc.as<int>(),
+                                                  V, c, vs, m);
+        HM_LAUNCH_CHECK();
+    });
+    return *(B.graphs[(int)prec] = std::move(L));
+}
+
 // Lockstep GMRES(m) of all systems for op x = b ([R][n], Morton), x = 0 on
 // entry.  `on` marks the systems to solve (others keep x = 0); tol per
 // system relative to ||b_s||.  Returns the Arnoldi steps taken.
 static int gmres_batch(Batch &B, hm_dtype prec, const double *b, double *x, const std::vector<int> &on, double tol,
-                       int maxit, int &cycles, cudaStream_t s) {
+                       int maxit, int &cycles, cudaStream_t s, bool use_graph) {
     const int S = B.S, m = B.m;
     const int64_t vs = B.vstride;
     double *V = B.V.as<double>();
@@ -375,10 +475,22 @@ static int gmres_batch(Batch &B, hm_dtype prec, const double *b, double *x, cons
         bset_g0_kernel<<<(S + 127) / 128, 128, 0, s>>>(S, m, B.cyc.as<int>(), B.nrm.as<double>(), B.g.as<double>());
         HM_LAUNCH_CHECK();
         bscale_kernel<<<B.nitems(), 256, 0, s>>>(B.items.as<Item>(), V, B.n, B.nrm.as<double>(), 1, B.cyc.as<int>(),
-                                                 V);
+                                                 V, nullptr, 0, 0);
         HM_LAUNCH_CHECK();
         std::vector<int> kk(S, 0);
-        for (int j = 0; j < m; ++j) {
+        if (use_graph) {
+            const LoopGraph &L = batch_step_graph(B, prec);
+            std::vector<double> th(S);
+            for (int k = 0; k < S; ++k) th[k] = tol * bnorm[k];
+            HM_CUDA_CHECK(cudaMemcpyAsync(B.thr.p, th.data(), sizeof(double) * S, cudaMemcpyHostToDevice, s));
+            const LoopCtl hc{0, std::min(m, maxit - iters), 0.0};
+            HM_CUDA_CHECK(cudaMemcpyAsync(B.ctl.p, &hc, sizeof(hc), cudaMemcpyHostToDevice, s));
+            L.launch(s);
+            const int steps = read_scalar(&B.ctl.as<LoopCtl>()->j, s);
+            L.count(steps);
+            iters += steps;
+        }
+        for (int j = 0; j < (use_graph ? 0 : m); ++j) {
             double *vj = V + (int64_t)j * vs;
             double *w = B.W.as<double>();
             if (B.precond) {
@@ -392,24 +504,24 @@ static int gmres_batch(Batch &B, hm_dtype prec, const double *b, double *x, cons
             {
                 Trace trace("batch_update", s);
                 bsub_kernel<<<B.nitems(), 256, 0, s>>>(B.items.as<Item>(), V, vs, B.n, j + 1, B.h.as<double>(), m + 1,
-                                                       B.cyc.as<int>(), w);
+                                                       B.cyc.as<int>(), w, nullptr);
                 HM_LAUNCH_CHECK();
             }
             B.dots(V, j + 1, w, B.cyc.as<int>(), B.h2.as<double>(), m + 1, 0, s);
             {
                 Trace trace("batch_update", s);
                 bsub_kernel<<<B.nitems(), 256, 0, s>>>(B.items.as<Item>(), V, vs, B.n, j + 1, B.h2.as<double>(),
-                                                       m + 1, B.cyc.as<int>(), w);
+                                                       m + 1, B.cyc.as<int>(), w, nullptr);
                 HM_LAUNCH_CHECK();
             }
             badd_coef_kernel<<<gx((int64_t)S * (j + 1)), 256, 0, s>>>(S, j + 1, m + 1, B.h2.as<double>(),
-                                                                     B.h.as<double>());
+                                                                     B.h.as<double>(), nullptr);
             HM_LAUNCH_CHECK();
             B.dots(w, 1, w, B.cyc.as<int>(), B.nrm.as<double>(), 1, 0, s);
             bgivens_kernel<<<(S + 127) / 128, 128, 0, s>>>(S, m, j, B.cyc.as<int>(), B.h.as<double>(), m + 1,
                                                           B.nrm.as<double>(), B.H.as<double>(), B.cs.as<double>(),
                                                           B.sn.as<double>(), B.g.as<double>(), B.est.as<double>(),
-                                                          B.hn.as<double>());
+                                                          B.hn.as<double>(), nullptr, nullptr, nullptr);
             HM_LAUNCH_CHECK();
             std::vector<double> est(S), hn(S);
             HM_CUDA_CHECK(cudaMemcpyAsync(est.data(), B.est.p, sizeof(double) * S, cudaMemcpyDeviceToHost, s));
@@ -426,11 +538,11 @@ static int gmres_batch(Batch &B, hm_dtype prec, const double *b, double *x, cons
             if (!more) break;
             HM_CUDA_CHECK(cudaMemcpyAsync(B.cyc.p, cyc.data(), sizeof(int) * S, cudaMemcpyHostToDevice, s));
             bscale_kernel<<<B.nitems(), 256, 0, s>>>(B.items.as<Item>(), w, B.n, B.nrm.as<double>(), 1,
-                                                     B.cyc.as<int>(), V + (int64_t)(j + 1) * vs);
+                                                     B.cyc.as<int>(), V + (int64_t)(j + 1) * vs, nullptr, 0, 0);
             HM_LAUNCH_CHECK();
         }
-        // x += M^{-1} V y per system
-        HM_CUDA_CHECK(cudaMemcpyAsync(B.kk.p, kk.data(), sizeof(int) * S, cudaMemcpyHostToDevice, s));
+        // x += M^{-1} V y per system (the graph form left k_s on the device)
+        if (!use_graph) HM_CUDA_CHECK(cudaMemcpyAsync(B.kk.p, kk.data(), sizeof(int) * S, cudaMemcpyHostToDevice, s));
         btrisolve_kernel<<<(S + 127) / 128, 128, 0, s>>>(S, m, B.kk.as<int>(), B.H.as<double>(), B.g.as<double>(),
                                                         B.y.as<double>());
         HM_LAUNCH_CHECK();
@@ -476,7 +588,8 @@ hm_status solve_batched(const hm_matrix *A, int nrhs, const double *b_orig, doub
     double worst = 0.0;
     hm_status st = HM_OK;
     if (!p.refine) {
-        iters = gmres_batch(B, HM_F64, b.as<double>(), x.as<double>(), on, p.rel_tol, p.max_iter, cycles, s);
+        iters = gmres_batch(B, HM_F64, b.as<double>(), x.as<double>(), on, p.rel_tol, p.max_iter, cycles, s,
+                            p.use_graph != 0);
         B.apply(HM_F64, x.as<double>(), B.AX.as<double>(), s);
         bsub_vec_kernel<<<gx(vs), 256, 0, s>>>(b.as<double>(), B.AX.as<double>(), vs, B.W.as<double>());
         HM_LAUNCH_CHECK();
@@ -507,7 +620,7 @@ hm_status solve_batched(const hm_matrix *A, int nrhs, const double *b_orig, doub
             if (steps >= p.max_refine || iters >= p.max_iter) break;
             ++steps;
             iters += gmres_batch(B, p.inner_dtype, r.as<double>(), d.as<double>(), on, p.inner_tol,
-                                 p.max_iter - iters, cycles, s);
+                                 p.max_iter - iters, cycles, s, p.use_graph != 0);
             badd_vec_kernel<<<gx(vs), 256, 0, s>>>(d.as<double>(), vs, x.as<double>());
             HM_LAUNCH_CHECK();
             B.apply(HM_F64, x.as<double>(), B.AX.as<double>(), s);

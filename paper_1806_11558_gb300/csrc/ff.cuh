@@ -14,7 +14,9 @@
 //     normalised once at the end.
 // Differences of points are taken relative to the panel centroids, so the
 // representation error of a coordinate is relative to the panel size, not to
-// the distance from the origin.
+// the distance from the origin; that also holds for neighbouring panels, so
+// the regular near-field entries (non-touching pairs of dense leaves) use the
+// same evaluation.
 #pragma once
 
 #include "hm_internal.cuh"
@@ -63,14 +65,19 @@ constexpr double SQRT_4PI = 3.54490770181103205459633496668229036559509891224477
 // R[k * rs].  wq_h / wq_l: the 7 weights as float pairs.
 __device__ __forceinline__ double regular_entry_ff(const float *__restrict__ R, int rs, const float *__restrict__ C,
                                                    int cs, const float *wq_h, const float *wq_l) {
-    // D = c_R - c_C in float-float
+    // D = c_R - c_C in float-float, to 2^-48 |D|: the hi and lo differences
+    // are both exact (TwoSum), and only their combination rounds, so
+    // neighbouring panels (|D| ~ panel size) keep full relative accuracy
     float Dh[3], Dl[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        float s, e;
+        float s, e, t, f, u, g;
         two_sum(R[(PF_CH + d) * rs], -C[(PF_CH + d) * cs], s, e);
-        e = __fadd_rn(e, __fsub_rn(R[(PF_CL + d) * rs], C[(PF_CL + d) * cs]));
-        fast_two_sum(s, e, Dh[d], Dl[d]);
+        two_sum(R[(PF_CL + d) * rs], -C[(PF_CL + d) * cs], t, f);
+        two_sum(e, t, u, g);
+        float sh, sl;
+        two_sum(s, u, sh, sl);
+        fast_two_sum(sh, __fadd_rn(sl, __fadd_rn(g, f)), Dh[d], Dl[d]);
     }
     // column offsets b_q (hi, lo)
     float bh[3][NQ], bl[3][NQ];

@@ -144,6 +144,51 @@ template <class T> T read_scalar(const T *d, cudaStream_t s) {
 int num_sms();
 
 // ----------------------------------------------------------------------------
+// Device-driven loops as CUDA graphs (prims.cu).  A LoopGraph holds one
+// WHILE conditional node whose body is captured once from `body` on a private
+// stream; the body's last kernel decides, on the device, whether another
+// iteration runs (cudaGraphSetConditional on the handle it is given).  The
+// handle starts at 1 on every launch, so the body runs at least once; a body
+// must clear it after a bounded number of iterations.
+// ----------------------------------------------------------------------------
+struct LoopCtl {       // device-side state of an Arnoldi loop
+    int j;             // next step of the cycle
+    int lim;           // steps allowed in this cycle
+    double thr;        // stopping threshold of the residual estimate
+};
+
+struct LoopGraph {
+    cudaGraphExec_t exec = nullptr;
+    long long body_launches = 0;  // kernels of one iteration
+    LoopGraph() = default;
+    LoopGraph(const LoopGraph &) = delete;
+    LoopGraph &operator=(const LoopGraph &) = delete;
+    ~LoopGraph();
+    template <class F> void build(F &&body);  // body(cudaStream_t, cudaGraphConditionalHandle)
+    void launch(cudaStream_t s) const;
+    void count(long long iterations) const;  // adds the replayed kernels to the launch count
+};
+
+void loop_graph_begin(cudaGraph_t *g, cudaGraphConditionalHandle *h, cudaGraph_t *body, cudaStream_t *cap);
+void loop_graph_end(LoopGraph &L, cudaGraph_t g, cudaGraph_t body, cudaStream_t cap, bool ok, long long launches);
+long long launch_count();
+
+template <class F> void LoopGraph::build(F &&body) {
+    cudaGraph_t g, bg;
+    cudaGraphConditionalHandle h;
+    cudaStream_t cap;
+    loop_graph_begin(&g, &h, &bg, &cap);
+    const long long before = launch_count();
+    try {
+        body(cap, h);
+    } catch (...) {
+        loop_graph_end(*this, g, bg, cap, false, 0);
+        throw;
+    }
+    loop_graph_end(*this, g, bg, cap, true, launch_count() - before);
+}
+
+// ----------------------------------------------------------------------------
 // quadrature data passed by value to kernels (lives in the parameter bank)
 // ----------------------------------------------------------------------------
 struct QuadParams {
@@ -175,6 +220,8 @@ void gather_i32(const int32_t *d_src, const int32_t *d_idx, int32_t *d_dst, int6
 // TMA tensor maps (driver entry point resolved through the runtime)
 // ----------------------------------------------------------------------------
 void make_tensor_map_2d_f64(CUtensorMap *map, const double *base, uint64_t dim0, uint64_t dim1, uint32_t box0,
+                            uint32_t box1);
+void make_tensor_map_2d_f32(CUtensorMap *map, const float *base, uint64_t dim0, uint64_t dim1, uint32_t box0,
                             uint32_t box1);
 
 }  // namespace hm
@@ -235,6 +282,8 @@ struct hm_tree {
     double seconds = 0.0;
     CUtensorMap pt_map;   // TMA map of the panel table, box [PT_ROWS][box_cols]
     int32_t box_cols = 0;
+    CUtensorMap pf_map;   // TMA map of the float-pair table, box [PF_ROWS][box_cols_f]
+    int32_t box_cols_f = 0;  // 0: leaves too wide for one box
 };
 
 // Working vectors of one H-matrix-vector product (Morton order).

@@ -16,6 +16,7 @@
 // singular_kernel, which gives each such entry one warp: the lanes split the
 // Gauss points of the regularised integral.
 #include "entry.cuh"
+#include "ff.cuh"
 
 namespace hm {
 
@@ -80,15 +81,25 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase,
 }
 
 // Shared-memory layout of nearfield_kernel: two 128-byte aligned panel tiles
-// of [PT_ROWS][box_cols] doubles, then the mbarrier.
-__host__ __device__ constexpr int nf_tile_bytes(int box_cols) { return ((PT_ROWS * box_cols * 8) + 127) / 128 * 128; }
-__host__ __device__ constexpr int nf_smem_bytes(int box_cols) { return 128 + 2 * nf_tile_bytes(box_cols) + 16; }
+// (FP64: [PT_ROWS][box_cols] doubles; float pairs: [PF_ROWS][box_cols]
+// floats), then the mbarrier.
+__host__ __device__ constexpr int nf_rec_bytes(bool ff) { return ff ? PF_ROWS * 4 : PT_ROWS * 8; }
+__host__ __device__ constexpr int nf_tile_bytes(bool ff, int box_cols) {
+    return ((nf_rec_bytes(ff) * box_cols) + 127) / 128 * 128;
+}
+__host__ __device__ constexpr int nf_smem_bytes(bool ff, int box_cols) {
+    return 128 + 2 * nf_tile_bytes(ff, box_cols) + 16;
+}
 
 // ---------------------------------------------------------------------------
 // regular near-field entries
 // ---------------------------------------------------------------------------
 constexpr int NF_THREADS = 128;
 
+// FF: the regular entries from the float-pair table in double-float
+// arithmetic (regular_entry_ff, ~1e-14 relative) on the FP32 pipes; else from
+// the FP64 table in FP64.
+template <bool FF>
 __global__ void __launch_bounds__(NF_THREADS) nearfield_kernel(const __grid_constant__ CUtensorMap pt_map,
                                                                 const int32_t *__restrict__ dense,
                                                                 const int64_t *__restrict__ base,
@@ -108,10 +119,12 @@ __global__ void __launch_bounds__(NF_THREADS) nearfield_kernel(const __grid_cons
     const int32_t partner = tp[b];
     const bool mirror = partner >= 0 && partner != b;
     if (mirror && rb > cb) return;
-    const int32_t rb_al = rb & ~1, cb_al = cb & ~1;
-    const int tile_bytes = nf_tile_bytes(box_cols);
-    double *tR = reinterpret_cast<double *>(sm);
-    double *tC = reinterpret_cast<double *>(sm + tile_bytes);
+    // a box starts at a column whose first byte is 16-byte aligned
+    const int32_t rb_al = FF ? rb & ~3 : rb & ~1, cb_al = FF ? cb & ~3 : cb & ~1;
+    const int tile_bytes = nf_tile_bytes(FF, box_cols);
+    using Rec = typename std::conditional<FF, float, double>::type;
+    Rec *tR = reinterpret_cast<Rec *>(sm);
+    Rec *tC = reinterpret_cast<Rec *>(sm + tile_bytes);
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm + 2 * tile_bytes);
     if (threadIdx.x == 0) {
         mbar_init(bar, 1);
@@ -119,7 +132,7 @@ __global__ void __launch_bounds__(NF_THREADS) nearfield_kernel(const __grid_cons
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        mbar_arrive_expect_tx(bar, 2u * PT_ROWS * box_cols * 8u);
+        mbar_arrive_expect_tx(bar, 2u * (uint32_t)nf_rec_bytes(FF) * box_cols);
         tma_load_2d(tR, &pt_map, bar, rb_al, 0);
         tma_load_2d(tC, &pt_map, bar, cb_al, 0);
     }
@@ -139,13 +152,18 @@ __global__ void __launch_bounds__(NF_THREADS) nearfield_kernel(const __grid_cons
         const int e = e0 + threadIdx.x;
         const bool valid = e < mn;
         const int i = valid ? e / n : 0, j = valid ? e - (e / n) * n : 0;
-        const double *R = tR + i + ro;
-        const double *C = tC + j + co;
+        const Rec *R = tR + i + ro;
+        const Rec *C = tC + j + co;
         int32_t vr[3], vc[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            vr[k] = (int32_t)R[(PT_VID + k) * box_cols];
-            vc[k] = (int32_t)C[(PT_VID + k) * box_cols];
+            if constexpr (FF) {
+                vr[k] = __float_as_int(R[(PF_VID + k) * box_cols]);
+                vc[k] = __float_as_int(C[(PF_VID + k) * box_cols]);
+            } else {
+                vr[k] = (int32_t)R[(PT_VID + k) * box_cols];
+                vc[k] = (int32_t)C[(PT_VID + k) * box_cols];
+            }
         }
         const int kind = valid ? shared_vertices(vr, vc) : 0;
         const bool touch = kind > 0;
@@ -188,7 +206,11 @@ __global__ void __launch_bounds__(NF_THREADS) nearfield_kernel(const __grid_cons
             }
         }
         if (valid && !touch) {
-            const double a = regular_entry(R, box_cols, C, box_cols, qp);
+            double a;
+            if constexpr (FF)
+                a = regular_entry_ff(R, box_cols, C, box_cols, qp.w_h, qp.w_l);
+            else
+                a = regular_entry(R, box_cols, C, box_cols, qp);
             arena[blk_base + (int64_t)i * blk_ld + j] = a;
             if (mirror) arena[par_base + (int64_t)j * par_ld + i] = a;
         }
@@ -280,7 +302,7 @@ __global__ void singular_kernel(const SingularItem *__restrict__ items, int64_t 
 // host
 // ---------------------------------------------------------------------------
 void assemble_nearfield(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStream_t s, int *d_err,
-                        double *sec_regular, double *sec_singular) {
+                        double *sec_regular, double *sec_singular, bool fp64) {
     // padding columns of the row panels must read as 0
     A->dense.alloc(sizeof(double) * std::max<int64_t>(tr->dense_entries, 1));
     HM_CUDA_CHECK(cudaMemsetAsync(A->dense.p, 0, sizeof(double) * std::max<int64_t>(tr->dense_entries, 1), s));
@@ -288,19 +310,22 @@ void assemble_nearfield(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, c
     items.alloc(sizeof(SingularItem) * std::max<int64_t>(tr->singular_cap, 1));
     cnt.alloc(sizeof(unsigned long long));
     HM_CUDA_CHECK(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long), s));
-    const int smem = nf_smem_bytes(tr->box_cols);
-    HM_CUDA_CHECK(cudaFuncSetAttribute(nearfield_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    const bool ff = !fp64 && tr->box_cols_f > 0;
+    const int box = ff ? tr->box_cols_f : tr->box_cols;
+    const int smem = nf_smem_bytes(ff, box);
+    auto kern = ff ? nearfield_kernel<true> : nearfield_kernel<false>;
+    HM_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     cudaEvent_t e0, e1, e2;
     HM_CUDA_CHECK(cudaEventCreate(&e0));
     HM_CUDA_CHECK(cudaEventCreate(&e1));
     HM_CUDA_CHECK(cudaEventCreate(&e2));
     HM_CUDA_CHECK(cudaEventRecord(e0, s));
     if (tr->n_dense > 0) {
-        Trace trace("nearfield_kernel", s);
-        nearfield_kernel<<<(unsigned)tr->n_dense, NF_THREADS, smem, s>>>(
-            tr->pt_map, tr->dense.as<int32_t>(), tr->dense_base.as<int64_t>(), tr->dense_ld.as<int32_t>(),
-            tr->dense_tp.as<int32_t>(), tr->box_cols, qp, A->dense.as<double>(), items.as<SingularItem>(), cnt.as<unsigned long long>(),
-            tr->singular_cap, d_err);
+        Trace trace(ff ? "nearfield_kernel" : "nearfield_kernel.f64", s);
+        kern<<<(unsigned)tr->n_dense, NF_THREADS, smem, s>>>(
+            ff ? tr->pf_map : tr->pt_map, tr->dense.as<int32_t>(), tr->dense_base.as<int64_t>(),
+            tr->dense_ld.as<int32_t>(), tr->dense_tp.as<int32_t>(), box, qp, A->dense.as<double>(),
+            items.as<SingularItem>(), cnt.as<unsigned long long>(), tr->singular_cap, d_err);
         HM_LAUNCH_CHECK();
     }
     HM_CUDA_CHECK(cudaEventRecord(e1, s));

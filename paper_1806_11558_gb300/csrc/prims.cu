@@ -22,6 +22,54 @@ static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
+// ---------------------------------------------------------------------------
+// LoopGraph: one WHILE node, body captured into the node's child graph
+// ---------------------------------------------------------------------------
+void loop_graph_begin(cudaGraph_t *g, cudaGraphConditionalHandle *h, cudaGraph_t *body, cudaStream_t *cap) {
+    HM_CUDA_CHECK(cudaGraphCreate(g, 0));
+    HM_CUDA_CHECK(cudaGraphConditionalHandleCreate(h, *g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = *h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    HM_CUDA_CHECK(cudaGraphAddNode(&node, *g, nullptr, nullptr, 0, &np));
+    *body = np.conditional.phGraph_out[0];
+    HM_CUDA_CHECK(cudaStreamCreateWithFlags(cap, cudaStreamNonBlocking));
+    HM_CUDA_CHECK(cudaStreamBeginCaptureToGraph(*cap, *body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+}
+
+void loop_graph_end(LoopGraph &L, cudaGraph_t g, cudaGraph_t body, cudaStream_t cap, bool ok, long long launches) {
+    cudaGraph_t captured = body;
+    const cudaError_t ec = cudaStreamEndCapture(cap, &captured);
+    cudaStreamDestroy(cap);
+    if (!ok || ec != cudaSuccess) {
+        cudaGraphDestroy(g);
+        if (ok) fail(HM_ECUDA, "graph capture of the Arnoldi loop failed: %s", cudaGetErrorString(ec));
+        return;
+    }
+    // the captured launches run on replay; they are counted there
+    g_launches.fetch_sub(launches, std::memory_order_relaxed);
+    L.body_launches = launches;
+    const cudaError_t ei = cudaGraphInstantiate(&L.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+        L.exec = nullptr;
+        fail(HM_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(ei));
+    }
+}
+
+LoopGraph::~LoopGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
+}
+
+void LoopGraph::launch(cudaStream_t s) const { HM_CUDA_CHECK(cudaGraphLaunch(exec, s)); }
+
+void LoopGraph::count(long long iterations) const {
+    g_launches.fetch_add(body_launches * iterations, std::memory_order_relaxed);
+}
+
 // ----------------------------------------------------------------------------
 // kernel timing trace
 // ----------------------------------------------------------------------------
@@ -428,6 +476,21 @@ void make_tensor_map_2d_f64(CUtensorMap *map, const double *base, uint64_t dim0,
     cuuint32_t box[2] = {box0, box1};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = get_encode()(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<double *>(base), dims, strides, box,
+                              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) fail(HM_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+}
+
+void make_tensor_map_2d_f32(CUtensorMap *map, const float *base, uint64_t dim0, uint64_t dim1, uint32_t box0,
+                            uint32_t box1) {
+    if ((dim0 * sizeof(float)) % 16 != 0 || (reinterpret_cast<uintptr_t>(base) & 15) != 0 || box0 > 256 ||
+        box1 > 256 || (box0 * sizeof(float)) % 16 != 0)
+        fail(HM_EINTERNAL, "tensor map geometry violates TMA alignment rules");
+    cuuint64_t dims[2] = {dim0, dim1};
+    cuuint64_t strides[1] = {dim0 * sizeof(float)};
+    cuuint32_t box[2] = {box0, box1};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = get_encode()(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box,
                               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) fail(HM_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);

@@ -9,8 +9,16 @@
 // refinement the inner GMRES applies the FP32 / BF16 copy of H while every
 // vector, dot product and rotation stays FP64, and the outer residual uses
 // the FP64 master.  Dot products reduce in a fixed order (deterministic).
+//
+// With use_graph the Arnoldi steps of a cycle run as one CUDA graph: a WHILE
+// node whose body is one step (operator, CGS2, Givens) with the step index in
+// device memory, and the Givens kernel ends the loop on the device, so the
+// host waits once per cycle instead of once per step.  The arithmetic is the
+// same kernel for kernel, so both forms give the same iterates.
 #include <chrono>
 #include <cmath>
+#include <map>
+#include <memory>
 #include <vector>
 
 #include "hm_internal.cuh"
@@ -42,7 +50,9 @@ constexpr int DOT_CHUNK = 8;  // vectors per register pass
 __global__ void __launch_bounds__(DOT_THREADS) dots_kernel(const double *__restrict__ V, int64_t ld, int nv,
                                                             const double *__restrict__ w, int64_t n,
                                                             double *__restrict__ part, double *__restrict__ out,
-                                                            int accumulate, unsigned int *ticket) {
+                                                            int accumulate, unsigned int *ticket,
+                                                            const LoopCtl *ctl) {
+    if (ctl) nv = ctl->j + 1;  // graph form: the vectors V_0..V_j of step j
     __shared__ double s[DOT_THREADS / 32][DOT_CHUNK];
     __shared__ bool s_last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -89,7 +99,8 @@ __global__ void __launch_bounds__(DOT_THREADS) dots_kernel(const double *__restr
 
 // w -= sum_l V_l h_l
 __global__ void sub_combo_kernel(const double *__restrict__ V, int64_t ld, int nv, const double *__restrict__ h,
-                                 int64_t n, double *__restrict__ w) {
+                                 int64_t n, double *__restrict__ w, const LoopCtl *ctl) {
+    if (ctl) nv = ctl->j + 1;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         double acc = w[i];
         for (int l = 0; l < nv; ++l) acc -= V[(int64_t)l * ld + i] * h[l];
@@ -149,6 +160,70 @@ __global__ void givens_kernel(double *H, int ldh, int j, const double *h, const 
     g[j] = cs[j] * g[j];
     est[0] = fabs(g[j + 1]);
     est[1] = hn;
+}
+
+// Graph form of one step's bookkeeping (step index j = ctl->j, 0 <= j < m).
+// out = V_j
+__global__ void vj_copy_kernel(const double *__restrict__ V, int64_t n, int m, const LoopCtl *ctl,
+                               double *__restrict__ out) {
+    const int j = ctl->j;
+    if (j < 0 || j >= m) return;
+    const double *src = V + (int64_t)j * n;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = src[i];
+}
+
+// h[l] += y[l], l <= j (the second CGS pass)
+__global__ void h_accum_kernel(const double *__restrict__ y, const LoopCtl *ctl, double *__restrict__ h) {
+    for (int l = threadIdx.x; l <= ctl->j; l += blockDim.x) h[l] += 1.0 * y[l];
+}
+
+// givens_kernel for step j = ctl->j, then the stopping test of the host
+// loop (estimate at or below thr, breakdown, or the cycle's step limit):
+// ctl->j = j + 1 and the loop's condition is cleared when it stops.  Every
+// iteration advances j and j >= lim stops, so the loop ends after at most
+// lim <= m iterations.
+__global__ void givens_loop_kernel(double *H, int ldh, int m, LoopCtl *ctl, const double *h, const double *wn2,
+                                   double *cs, double *sn, double *g, double *est, cudaGraphConditionalHandle loop) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int j = ctl->j;
+    if (j < 0 || j >= m) {
+        cudaGraphSetConditional(loop, 0u);
+        return;
+    }
+    double *col = H + (int64_t)j * ldh;
+    for (int l = 0; l <= j; ++l) col[l] = h[l];
+    const double hn = sqrt(*wn2);
+    col[j + 1] = hn;
+    for (int l = 0; l < j; ++l) {
+        const double t = cs[l] * col[l] + sn[l] * col[l + 1];
+        col[l + 1] = -sn[l] * col[l] + cs[l] * col[l + 1];
+        col[l] = t;
+    }
+    const double rho = hypot(col[j], col[j + 1]);
+    cs[j] = rho > 0.0 ? col[j] / rho : 1.0;
+    sn[j] = rho > 0.0 ? col[j + 1] / rho : 0.0;
+    col[j] = rho;
+    col[j + 1] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    est[0] = fabs(g[j + 1]);
+    est[1] = hn;
+    const int k = j + 1;
+    const bool stop = est[0] <= ctl->thr || hn == 0.0 || k >= ctl->lim || k >= m;
+    ctl->j = k;
+    cudaGraphSetConditional(loop, stop ? 0u : 1u);
+}
+
+// V_{j} = w / ||w|| with j = ctl->j (already advanced), j <= m
+__global__ void scale_loop_kernel(const double *src, const double *nrm2, int64_t n, int m, const LoopCtl *ctl,
+                                  double *V) {
+    const int j = ctl->j;
+    if (j < 1 || j > m) return;
+    const double nr = sqrt(*nrm2);
+    double *dst = V + (int64_t)j * n;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = nr > 0.0 ? src[i] / nr : 0.0;
 }
 
 // back substitution R y = g (R = upper k x k of H)
@@ -360,7 +435,8 @@ struct Gmres {
     int64_t n;
     int m;
     int nblk;
-    DBuf V, w, ax, part, h, H, cs, sn, g, y, est, t, nrm, z, d, ticket;
+    DBuf V, w, ax, part, h, H, cs, sn, g, y, est, t, nrm, z, d, ticket, ctl, xin;
+    std::map<int, std::unique_ptr<LoopGraph>> graphs;  // keyed by precision, preconditioning, transpose
     Gmres(int64_t n_, int m_, int64_t work_doubles, cudaStream_t s) : n(n_), m(m_) {
         nblk = std::max(1, std::min<int>(4 * num_sms(), (int)((n + 1023) / 1024)));
         V.alloc(sizeof(double) * (int64_t)(m + 1) * n);
@@ -380,12 +456,14 @@ struct Gmres {
         nrm.alloc(sizeof(double) * 2);
         ticket.alloc(sizeof(unsigned int));
         HM_CUDA_CHECK(cudaMemsetAsync(ticket.p, 0, sizeof(unsigned int), s));
+        ctl.alloc(sizeof(LoopCtl));
     }
     // out[0..nv) = V_l . w (accumulate adds to out)
-    void dots(const double *Vb, int nv, const double *wv, double *out, int accumulate, cudaStream_t s) {
+    void dots(const double *Vb, int nv, const double *wv, double *out, int accumulate, cudaStream_t s,
+              const LoopCtl *c = nullptr) {
         Trace trace("gmres_dots", s);
         dots_kernel<<<nblk, DOT_THREADS, 0, s>>>(Vb, n, nv, wv, n, part.as<double>(), out, accumulate,
-                                                 ticket.as<unsigned int>());
+                                                 ticket.as<unsigned int>(), c);
         HM_LAUNCH_CHECK();
     }
     double norm2_host(const double *v, cudaStream_t s) {
@@ -394,11 +472,51 @@ struct Gmres {
     }
 };
 
+// The Arnoldi loop of a cycle as a graph: one step per iteration of the
+// WHILE node, the step index in G.ctl (the same kernels as the host loop).
+static const LoopGraph &step_graph(const hm_matrix *A, hm_dtype prec, Gmres &G, bool precond, bool trans) {
+    const int key = (int)prec * 4 + (precond ? 2 : 0) + (trans ? 1 : 0);
+    auto it = G.graphs.find(key);
+    if (it != G.graphs.end()) return *it->second;
+    if (!G.xin.p) G.xin.alloc(sizeof(double) * G.n);
+    auto L = std::make_unique<LoopGraph>();
+    const int64_t n = G.n;
+    const int m = G.m;
+    L->build([&](cudaStream_t cs, cudaGraphConditionalHandle loop) {
+        double *V = G.V.as<double>(), *w = G.w.as<double>();
+        LoopCtl *c = G.ctl.as<LoopCtl>();
+        vj_copy_kernel<<<g1(n), 256, 0, cs>>>(V, n, m, c, G.xin.as<double>());
+        HM_LAUNCH_CHECK();
+        if (precond) {
+            bj_apply(A, G.xin.as<double>(), G.z.as<double>(), cs, trans, prec != HM_F64);
+            apply(A, prec, G.z.as<double>(), w, G.t, cs, trans);
+        } else {
+            apply(A, prec, G.xin.as<double>(), w, G.t, cs, trans);
+        }
+        G.dots(V, 0, w, G.h.as<double>(), 0, cs, c);
+        sub_combo_kernel<<<g1(n), 256, 0, cs>>>(V, n, 0, G.h.as<double>(), n, w, c);
+        HM_LAUNCH_CHECK();
+        G.dots(V, 0, w, G.y.as<double>(), 0, cs, c);
+        sub_combo_kernel<<<g1(n), 256, 0, cs>>>(V, n, 0, G.y.as<double>(), n, w, c);
+        HM_LAUNCH_CHECK();
+        h_accum_kernel<<<1, 128, 0, cs>>>(G.y.as<double>(), c, G.h.as<double>());
+        HM_LAUNCH_CHECK();
+        G.dots(w, 1, w, G.nrm.as<double>() + 1, 0, cs);
+        givens_loop_kernel<<<1, 32, 0, cs>>>(G.H.as<double>(), m + 1, m, c, G.h.as<double>(),
+                                             G.nrm.as<double>() + 1, G.cs.as<double>(), G.sn.as<double>(),
+                                             G.g.as<double>(), G.est.as<double>(), loop);
+        HM_LAUNCH_CHECK();
+        scale_loop_kernel<<<g1(n), 256, 0, cs>>>(w, G.nrm.as<double>() + 1, n, m, c, V);
+        HM_LAUNCH_CHECK();
+    });
+    return *(G.graphs[key] = std::move(L));
+}
+
 // GMRES(m) for op x = b (Morton order), x in/out.  Returns the status; iters
 // and cycles accumulate; relres = final true residual / ||b||.
 static hm_status gmres(const hm_matrix *A, hm_dtype prec, const double *b, double *x, double tol, int maxit,
                        Gmres &G, cudaStream_t s, int &iters, int &cycles, double &relres, bool x_is_zero,
-                       bool precond, bool trans) {
+                       bool precond, bool trans, bool use_graph) {
     const int64_t n = G.n;
     const int m = G.m;
     double *V = G.V.as<double>();
@@ -426,7 +544,16 @@ static hm_status gmres(const hm_matrix *A, hm_dtype prec, const double *b, doubl
         scale_kernel<<<g1(n), 256, 0, s>>>(V, G.nrm.as<double>(), n, V);
         HM_LAUNCH_CHECK();
         int k = 0;
-        for (int j = 0; j < m; ++j) {
+        if (use_graph) {
+            const LoopGraph &L = step_graph(A, prec, G, precond, trans);
+            const LoopCtl hc{0, std::min(m, maxit - iters), tol * bnorm};
+            HM_CUDA_CHECK(cudaMemcpyAsync(G.ctl.p, &hc, sizeof(hc), cudaMemcpyHostToDevice, s));
+            L.launch(s);
+            k = read_scalar(&G.ctl.as<LoopCtl>()->j, s);
+            L.count(k);
+            iters += k;
+        }
+        for (int j = 0; j < (use_graph ? 0 : m); ++j) {
             double *vj = V + (int64_t)j * n;
             double *w = G.w.as<double>();
             if (precond) {
@@ -440,13 +567,13 @@ static hm_status gmres(const hm_matrix *A, hm_dtype prec, const double *b, doubl
             G.dots(V, j + 1, w, G.h.as<double>(), 0, s);
             {
                 Trace trace("gmres_sub_combo", s);
-                sub_combo_kernel<<<g1(n), 256, 0, s>>>(V, n, j + 1, G.h.as<double>(), n, w);
+                sub_combo_kernel<<<g1(n), 256, 0, s>>>(V, n, j + 1, G.h.as<double>(), n, w, nullptr);
                 HM_LAUNCH_CHECK();
             }
             G.dots(V, j + 1, w, G.y.as<double>(), 0, s);
             {
                 Trace trace("gmres_sub_combo", s);
-                sub_combo_kernel<<<g1(n), 256, 0, s>>>(V, n, j + 1, G.y.as<double>(), n, w);
+                sub_combo_kernel<<<g1(n), 256, 0, s>>>(V, n, j + 1, G.y.as<double>(), n, w, nullptr);
                 HM_LAUNCH_CHECK();
             }
             // h += h2 (second pass coefficients)
@@ -516,7 +643,7 @@ hm_status solve_impl(const hm_matrix *A, const double *b_orig, double *x_orig, c
     hm_status st;
     if (!p.refine) {
         st = gmres(A, HM_F64, b.as<double>(), x.as<double>(), p.rel_tol, p.max_iter, G, s, iters, cycles, relres, true,
-                   pc, trans);
+                   pc, trans, p.use_graph != 0);
     } else {
         DBuf r, d, ax;
         r.alloc(sizeof(double) * n);
@@ -535,7 +662,7 @@ hm_status solve_impl(const hm_matrix *A, const double *b_orig, double *x_orig, c
             HM_CUDA_CHECK(cudaMemsetAsync(d.p, 0, sizeof(double) * n, s));
             double inner = 1.0;
             gmres(A, p.inner_dtype, r.as<double>(), d.as<double>(), p.inner_tol, p.max_iter, G, s, iters, cycles,
-                  inner, true, pc, trans);
+                  inner, true, pc, trans, p.use_graph != 0);
             axpy_kernel<<<g1(n), 256, 0, s>>>(1.0, d.as<double>(), n, x.as<double>());
             HM_LAUNCH_CHECK();
             apply(A, HM_F64, x.as<double>(), ax.as<double>(), G.t, s, trans);

@@ -135,23 +135,27 @@ __global__ void panel_table_kernel(const double *V, const int32_t *T, const int3
         const int32_t i = perm[k];
         const int32_t t0 = T[3 * (int64_t)i], t1 = T[3 * (int64_t)i + 1], t2 = T[3 * (int64_t)i + 2];
         const double *a = V + 3 * (int64_t)t0, *b = V + 3 * (int64_t)t1, *c = V + 3 * (int64_t)t2;
-        for (int q = 0; q < NQ; ++q)
-            for (int d = 0; d < 3; ++d) {
-                const double xq = __dadd_rn(__dadd_rn(__dmul_rn(qp.bary[q][0], a[d]), __dmul_rn(qp.bary[q][1], b[d])),
-                                            __dmul_rn(qp.bary[q][2], c[d]));
-                pt[(int64_t)(7 * d + q) * npad + k] = xq;
-                // far-field record: offset from the centroid as a float pair
-                float h, l;
-                split_double(__dsub_rn(xq, cent[3 * (int64_t)i + d]), h, l);
-                pf[(int64_t)(PF_AH + 7 * d + q) * npad + k] = h;
-                pf[(int64_t)(PF_AL + 7 * d + q) * npad + k] = l;
-            }
+        // float-pair record: the centroid as (h, l) and every quadrature point
+        // as an offset from that represented centroid h + l (exact in FP64),
+        // so a point's representation error is relative to the panel size
+        double cr[3];
         for (int d = 0; d < 3; ++d) {
             float h, l;
             split_double(cent[3 * (int64_t)i + d], h, l);
             pf[(int64_t)(PF_CH + d) * npad + k] = h;
             pf[(int64_t)(PF_CL + d) * npad + k] = l;
+            cr[d] = __dadd_rn((double)h, (double)l);
         }
+        for (int q = 0; q < NQ; ++q)
+            for (int d = 0; d < 3; ++d) {
+                const double xq = __dadd_rn(__dadd_rn(__dmul_rn(qp.bary[q][0], a[d]), __dmul_rn(qp.bary[q][1], b[d])),
+                                            __dmul_rn(qp.bary[q][2], c[d]));
+                pt[(int64_t)(7 * d + q) * npad + k] = xq;
+                float h, l;
+                split_double(__dsub_rn(xq, cr[d]), h, l);
+                pf[(int64_t)(PF_AH + 7 * d + q) * npad + k] = h;
+                pf[(int64_t)(PF_AL + 7 * d + q) * npad + k] = l;
+            }
         pf[(int64_t)(PF_VID + 0) * npad + k] = __int_as_float(t0);
         pf[(int64_t)(PF_VID + 1) * npad + k] = __int_as_float(t1);
         pf[(int64_t)(PF_VID + 2) * npad + k] = __int_as_float(t2);
@@ -803,6 +807,14 @@ hm_tree *build_tree_impl(const double *d_V, int64_t nv, const int32_t *d_T, int6
     if (tr->box_cols > 256) fail(HM_EINVAL, "leaf_size too large for the panel staging box");
     make_tensor_map_2d_f64(&tr->pt_map, tr->pt.as<double>(), (uint64_t)npad, PT_ROWS, (uint32_t)tr->box_cols,
                            PT_ROWS);
+    // and of the float-pair table: box [PF_ROWS][box_cols_f], starting at a
+    // column that is a multiple of 4 (0 = too wide: the FP64 entries are used)
+    tr->box_cols_f = (tr->max_dense_dim + 3 + 3) / 4 * 4;
+    if (tr->box_cols_f <= 256)
+        make_tensor_map_2d_f32(&tr->pf_map, tr->pf.as<float>(), (uint64_t)npad, PF_ROWS, (uint32_t)tr->box_cols_f,
+                               PF_ROWS);
+    else
+        tr->box_cols_f = 0;
     HM_CUDA_CHECK(cudaStreamSynchronize(s));
     tr->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return tr.release();

@@ -64,8 +64,7 @@ def ico3(orc):
     g.close()
 
 
-def test_nearfield_entries(orc, ico3):
-    g, A = ico3
+def _nearfield_errors(orc, g, A):
     perm = g.perm()
     ex = g.export()
     dense = g.leaves(True)
@@ -84,6 +83,13 @@ def test_nearfield_entries(orc, ico3):
             worst_reg = max(worst_reg, rel[~touch].max())
         if touch.any():
             worst_sing = max(worst_sing, rel[touch].max())
+    return worst_reg, worst_sing, n_vertex, n_other
+
+
+def test_nearfield_entries(orc, ico3):
+    # regular entries in double-float arithmetic (the default)
+    g, A = ico3
+    worst_reg, worst_sing, n_vertex, n_other = _nearfield_errors(orc, g, A)
     assert worst_reg < 1e-13, worst_reg
     assert worst_sing < 1e-12, worst_sing
     # every dense leaf here is diagonal or has its transposed partner: a
@@ -91,6 +97,19 @@ def test_nearfield_entries(orc, ico3):
     # identical pairs once per position
     assert n_vertex % 2 == 0
     assert g.info()["n_singular"] == n_other + n_vertex // 2
+
+
+def test_nearfield_entries_fp64_arithmetic(orc, ico3):
+    # the same entries with FP64 arithmetic; touching pairs are unchanged
+    g0, A = ico3
+    V, T = MESHES["ico3"]
+    g = GpuH(V, T, leaf=64, eta=1.5, eps=1e-8, nearfield_fp64=1)
+    try:
+        worst_reg, worst_sing, _, _ = _nearfield_errors(orc, g, A)
+        assert worst_reg < 1e-13, worst_reg
+        assert worst_sing < 1e-12, worst_sing
+    finally:
+        g.close()
 
 
 def test_aca_blocks_within_tolerance(orc, ico3):
