@@ -81,11 +81,12 @@ typedef struct {
  *  dense_dtype  : HM_F64 (FP64 only) or HM_F32 to also keep an FP32 copy of
  *                 the dense near field.
  *  nearfield_fp64 : 0 (default) = the regular near-field entries (dense
- *                 leaves, panels not touching) in double-float arithmetic on
- *                 the FP32 units (about 48 significant bits, ~1e-14
- *                 relative), like the ACA entries; 1 = in FP64 arithmetic.
- *                 Touching pairs are always FP64.  Leaves wider than 250
- *                 panels always use FP64.
+ *                 leaves, panels not touching) and the regularised integrals
+ *                 of pairs sharing a vertex or an edge in double-float
+ *                 arithmetic on the FP32 units (about 48 significant bits,
+ *                 ~1e-14 relative), like the ACA entries; 1 = in FP64
+ *                 arithmetic.  Identical panels are always FP64.  Regular
+ *                 entries of leaves wider than 250 panels always use FP64.
  *  The FP64 master copy is always kept. */
 typedef struct {
     double aca_eps;
@@ -110,10 +111,13 @@ typedef struct {
  *  precond    : 0 = none (the paper's unpreconditioned Krylov solve);
  *               1 = right block-Jacobi preconditioning with the inverses of
  *                   the near-field diagonal blocks of runs of consecutive
- *                   leaf clusters of at most 160 rows (one leaf when leaves
- *                   are larger; FP64, computed on the first such solve and
- *                   kept with the matrix).  The residual and the stopping
- *                   test are those of the unpreconditioned system. */
+ *                   leaf clusters of at most 200 rows (one leaf when leaves
+ *                   are larger), computed on the first such solve and kept
+ *                   with the matrix: inverted in FP32 (blocks of at most 232
+ *                   rows; FP64 beyond), applied in FP64 by FP64 solves and
+ *                   in FP32 by the inner solves.  The preconditioner only
+ *                   changes the Krylov basis: the residual and the stopping
+ *                   test are those of the unpreconditioned FP64 system. */
 typedef struct {
     int32_t restart;
     int32_t max_iter;
@@ -138,6 +142,16 @@ typedef struct {
                           kernels and arithmetic, so the same iterates as 0.
                           The graph is built on the first cycle of the call
                           (one per precision used). */
+    double stall_ratio; /* refine = 1: an outer step whose FP64 residual is
+                           above stall_ratio times the previous one has not
+                           contracted (the inner operator is too inexact for
+                           the conditioning, kappa u >~ 1), and the inner
+                           precision is raised for the remaining steps:
+                           HM_BF16 -> HM_F32 (FP32 copies of the factors and
+                           the near field are made from the FP64 master and
+                           kept with the matrix when the assembly did not keep
+                           them); HM_F32 -> HM_F64.  <= 0 selects 0.5; NaN is
+                           HM_EINVAL. */
 } hm_solve_params;
 
 typedef struct {
@@ -147,6 +161,9 @@ typedef struct {
     int32_t refine_steps; /* outer refinement steps (0 when refine = 0)            */
     double rel_resid;     /* final ||b - H x|| / ||b|| with the FP64 operator       */
     double seconds;       /* wall time of the call                                 */
+    int32_t inner_dtype;  /* precision of the last inner solve (refine = 1; it is
+                             above the requested one after a stall, see
+                             stall_ratio); HM_F64 when refine = 0             */
 } hm_solve_info;
 
 typedef struct {

@@ -46,12 +46,13 @@ class SolveParams(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("rel_tol", ctypes.c_double),
                 ("refine", ctypes.c_int32), ("max_refine", ctypes.c_int32), ("inner_tol", ctypes.c_double),
                 ("inner_dtype", ctypes.c_int), ("precond", ctypes.c_int32), ("batched", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("stall_ratio", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("restarts", ctypes.c_int32),
-                ("refine_steps", ctypes.c_int32), ("rel_resid", ctypes.c_double), ("seconds", ctypes.c_double)]
+                ("refine_steps", ctypes.c_int32), ("rel_resid", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("inner_dtype", ctypes.c_int32)]
 
 
 class TreeInfo(ctypes.Structure):
@@ -261,12 +262,13 @@ def hm_matvec_noalloc(A, x, y, trans=0, prec=HM_F64, alpha=1.0, beta=0.0, stream
 
 
 def hm_solve(A, b, x, trans=0, restart=30, max_iter=3000, rel_tol=1e-10, refine=0, max_refine=20, inner_tol=1e-4,
-             inner_dtype=HM_F32, precond=0, batched=0, use_graph=0, stream=None, raise_on_noconv=True):
+             inner_dtype=HM_F32, precond=0, batched=0, use_graph=0, stall_ratio=0.5, stream=None,
+             raise_on_noconv=True):
     """Solves op(H) x = b; returns the SolveInfo of the (last) right-hand side."""
     import torch
     nrhs = 1 if b.dim() == 1 else b.shape[0]
     prm = SolveParams(int(restart), int(max_iter), float(rel_tol), int(refine), int(max_refine), float(inner_tol),
-                      int(inner_dtype), int(precond), int(batched), int(use_graph))
+                      int(inner_dtype), int(precond), int(batched), int(use_graph), float(stall_ratio))
     info = SolveInfo()
     st = lib().hm_solve(A, int(trans), nrhs, _ptr(b, torch.float64), _ptr(x, torch.float64), ctypes.byref(prm),
                         _stream(stream), ctypes.byref(info))

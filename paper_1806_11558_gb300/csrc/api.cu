@@ -254,6 +254,7 @@ hm_status hm_solve(const hm_matrix *A, int32_t trans, int32_t nrhs, const double
         }
         if (params->batched != 0 && params->batched != 1) fail(HM_EINVAL, "batched must be 0 or 1");
         if (params->use_graph != 0 && params->use_graph != 1) fail(HM_EINVAL, "use_graph must be 0 or 1");
+        if (std::isnan(params->stall_ratio)) fail(HM_EINVAL, "stall_ratio is NaN");
         if (params->batched && trans) fail(HM_EINVAL, "the batched solve is for trans = 0");
         if (params->batched && params->refine && params->inner_dtype != HM_F64 && !A->dense32.p)
             fail(HM_EINVAL, "the FP32 near-field copy was not assembled");

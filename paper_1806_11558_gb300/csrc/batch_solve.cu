@@ -34,6 +34,7 @@ void bj_setup(const hm_matrix *A, cudaStream_t s);
 void bj_apply_cols(const hm_matrix *A, const double *v, double *z, int cols, bool trans, bool low, cudaStream_t s);
 void permute_to_morton(const hm_tree *tr, const double *x, double *xm, cudaStream_t s);
 void permute_from_morton(const hm_tree *tr, const double *ym, double alpha, double beta, double *y, cudaStream_t s);
+hm_dtype raise_inner(const hm_matrix *A, hm_dtype cur, cudaStream_t s);
 
 constexpr int BMR = 16;        // columns of one tensor-core product
 constexpr int BITEM = 8192;    // entries of one work item
@@ -583,6 +584,7 @@ hm_status solve_batched(const hm_matrix *A, int nrhs, const double *b_orig, doub
     Batch B(A, nrhs, p.restart, pc, p.refine ? p.inner_dtype : HM_F64, s);
     const int S = B.S;
     int iters = 0, cycles = 0, steps = 0;
+    hm_dtype inner_dt = p.refine ? p.inner_dtype : HM_F64;
     std::vector<double> bn2 = B.norms2(b.as<double>(), s);
     std::vector<int> on(S, 1);
     double worst = 0.0;
@@ -605,6 +607,8 @@ hm_status solve_batched(const hm_matrix *A, int nrhs, const double *b_orig, doub
         d.alloc(sizeof(double) * vs);
         HM_CUDA_CHECK(cudaMemcpyAsync(r.p, b.p, sizeof(double) * vs, cudaMemcpyDeviceToDevice, s));
         st = HM_ENOCONV;
+        const double stall = p.stall_ratio > 0.0 ? p.stall_ratio : 0.5;
+        double prev = 1.0;
         for (;;) {
             std::vector<double> r2 = B.norms2(r.as<double>(), s);
             worst = 0.0;
@@ -617,9 +621,15 @@ hm_status solve_batched(const hm_matrix *A, int nrhs, const double *b_orig, doub
                 st = HM_OK;
                 break;
             }
+            // an outer step that did not contract raises the inner precision
+            if (steps > 0 && !(worst <= stall * prev) && inner_dt != HM_F64) {
+                inner_dt = raise_inner(A, inner_dt, s);
+                if (inner_dt != HM_F64) mrhs_prepare(A, inner_dt, s);
+            }
+            prev = worst;
             if (steps >= p.max_refine || iters >= p.max_iter) break;
             ++steps;
-            iters += gmres_batch(B, p.inner_dtype, r.as<double>(), d.as<double>(), on, p.inner_tol,
+            iters += gmres_batch(B, inner_dt, r.as<double>(), d.as<double>(), on, p.inner_tol,
                                  p.max_iter - iters, cycles, s, p.use_graph != 0);
             badd_vec_kernel<<<gx(vs), 256, 0, s>>>(d.as<double>(), vs, x.as<double>());
             HM_LAUNCH_CHECK();
@@ -638,6 +648,7 @@ hm_status solve_batched(const hm_matrix *A, int nrhs, const double *b_orig, doub
         info->refine_steps = steps;
         info->rel_resid = worst;
         info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        info->inner_dtype = (int32_t)inner_dt;
     }
     return st;
 }

@@ -235,9 +235,125 @@ __global__ void __launch_bounds__(NF_THREADS) nearfield_kernel(const __grid_cons
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double inv_norm3(double x, double y, double z) { return rsqrt(fma(x, x, fma(y, y, z * z))); }
 
+// Common-vertex and common-edge rules in double-float arithmetic.  The 2 n^3
+// points of the two common-vertex regions (and the 5 n^2 of the common-edge
+// 2-D sum) are tabulated once per assembly (FP64 values split into float
+// pairs): the coefficients (u0, u1, v0, v1) of D = (u0 a1 + u1 a2) -
+// (v0 b1 + v1 b2) and the weight w1 w2 w3 * jac.  Per point the products of
+// the coefficients with the edge vectors are exact (TwoProduct) up to the
+// float-pair rounding of the inputs, their high parts add exactly (TwoSum)
+// and every low part goes to one float, so D is accurate to about 2^-48 of
+// its largest term, as in FP64 up to the shorter mantissa.
+struct SSPointFF {
+    float ch[4], cl[4];  // u0, u1, v0, v1
+    float wh, wl;        // w1 w2 w3 jac
+};
+
+__global__ void ss_vertex_table_kernel(const QuadParams qp, SSPointFF *tab) {
+    const int n = qp.ss_n, n3 = n * n * n;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 2 * n3; t += gridDim.x * blockDim.x) {
+        const int r = t / n3, rem = t - r * n3;
+        const int k1 = rem / (n * n), k2 = (rem / n) % n, k3 = rem % n;
+        double c[4], jac;
+        ss_region(1, r, qp.gx[k1], qp.gx[k2], qp.gx[k3], c[0], c[1], c[2], c[3], jac);
+        SSPointFF p;
+        for (int k = 0; k < 4; ++k) split_double(c[k], p.ch[k], p.cl[k]);
+        split_double(qp.gw[k1] * qp.gw[k2] * qp.gw[k3] * jac, p.wh, p.wl);
+        tab[t] = p;
+    }
+}
+
+// The common-edge rule after the exact eta1 sum (the 2-D sum of the FP64
+// path below): D' = d0 a1 + u1 a2 - v1 b2 over the five regions, weight
+// w2 w3 jp / 2, stored as coefficients of (a1, a2, b2, b1) with the last 0.
+__global__ void ss_edge_table_kernel(const QuadParams qp, SSPointFF *tab) {
+    const int n = qp.ss_n, n2 = n * n;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < 5 * n2; t += gridDim.x * blockDim.x) {
+        const int r = t / n2, rem = t - r * n2, k2 = rem / n, k3 = rem - k2 * n;
+        const double e2 = qp.gx[k2], e3 = qp.gx[k3], e23 = e2 * e3;
+        double d0, u1, v1, jp;
+        switch (r) {
+            case 0: d0 = e2; u1 = e3; v1 = 1.0 - e2; jp = 1.0; break;
+            case 1: d0 = e23; u1 = 1.0; v1 = e2 - e23; jp = e2; break;
+            case 2: d0 = -e2; u1 = 1.0 - e2; v1 = e23; jp = e2; break;
+            case 3: d0 = -e23; u1 = e2 - e23; v1 = 1.0; jp = e2; break;
+            default: d0 = -e23; u1 = 1.0 - e23; v1 = e2; jp = e2; break;
+        }
+        SSPointFF p;
+        const double c[4] = {d0, u1, v1, 0.0};
+        for (int k = 0; k < 4; ++k) split_double(c[k], p.ch[k], p.cl[k]);
+        split_double(0.5 * (qp.gw[k2] * qp.gw[k3] * jp), p.wh, p.wl);
+        tab[t] = p;
+    }
+}
+
+// (s, e) += (a, b) for non-negative float pairs
+__device__ __forceinline__ void ff_acc(float &s, float &e, float a, float b) {
+    float t, u;
+    two_sum(s, a, t, u);
+    s = t;
+    e = __fadd_rn(e, __fadd_rn(u, b));
+}
+
+// Sum over this lane's points of w / |D|, D = c0 E0 + c1 E1 - c2 E2 - c3 E3,
+// for the edge vectors E (common vertex: (a1, a2, b1, b2); common edge:
+// (a1, a2, b2, b1) with c3 = 0) as float pairs; returned as a float pair.
+__device__ __forceinline__ void ss_sum_ff(const float Eh[4][3], const float El[4][3], const SSPointFF *__restrict__ tab,
+                                             int npts, int lane, float &acc_h, float &acc_l) {
+    acc_h = 0.0f;
+    acc_l = 0.0f;
+    for (int t = lane; t < npts; t += 32) {
+        const SSPointFF p = tab[t];
+        float dd_h = 0.0f, dd_l = 0.0f;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            // D_d = c0 a1 + c1 a2 - c2 b1 - c3 b2
+            float hs = 0.0f, lo = 0.0f;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float sg = k < 2 ? 1.0f : -1.0f;
+                float ph, pe;
+                two_prod(p.ch[k], Eh[k][d], ph, pe);
+                pe = __fmaf_rn(p.ch[k], El[k][d], pe);
+                pe = __fmaf_rn(p.cl[k], Eh[k][d], pe);
+                float t1, e1;
+                two_sum(hs, sg * ph, t1, e1);
+                hs = t1;
+                lo = __fadd_rn(lo, __fmaf_rn(sg, pe, e1));
+            }
+            float Dh, Dl;
+            fast_two_sum(hs, lo, Dh, Dl);
+            // dd += D^2
+            float qh, ql;
+            two_prod(Dh, Dh, qh, ql);
+            ql = __fmaf_rn(__fmul_rn(2.0f, Dh), Dl, ql);
+            ff_acc(dd_h, dd_l, qh, ql);
+        }
+        float r2h, r2l;
+        fast_two_sum(dd_h, dd_l, r2h, r2l);
+        // 1 / sqrt(r2): estimate + one Newton step with an exact residual
+        const float y0 = rsqrtf(r2h);
+        float yh, yl;
+        two_prod(y0, y0, yh, yl);
+        float mh, ml;
+        two_prod(r2h, yh, mh, ml);
+        ml = __fmaf_rn(r2h, yl, ml);
+        ml = __fmaf_rn(r2l, yh, ml);
+        const float del = __fsub_rn(__fsub_rn(1.0f, mh), ml);
+        const float corr = __fmul_rn(__fmul_rn(0.5f, y0), del);
+        // acc += w (y0 + corr)
+        float qh, ql;
+        two_prod(p.wh, y0, qh, ql);
+        ql = __fmaf_rn(p.wh, corr, ql);
+        ql = __fmaf_rn(p.wl, y0, ql);
+        ff_acc(acc_h, acc_l, qh, ql);
+    }
+}
+
 __global__ void singular_kernel(const SingularItem *__restrict__ items, int64_t count, const int32_t *__restrict__ trim,
                                 const double *__restrict__ V, const double *__restrict__ pt, int64_t npad,
-                                const QuadParams qp, double *__restrict__ arena) {
+                                const QuadParams qp, double *__restrict__ arena,
+                                const SSPointFF *__restrict__ vtab, const SSPointFF *__restrict__ etab) {
     const int lane = threadIdx.x & 31;
     const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (w >= count) return;
@@ -250,6 +366,7 @@ __global__ void singular_kernel(const SingularItem *__restrict__ items, int64_t 
     const PairGeom g = pair_geom(V, P, Q);
     const int n = qp.ss_n, n2 = n * n, n3 = n2 * n;
     double s = 0.0;
+    bool ff_done = false;
     if (kind == 3) {
         // 1-D: three classes of regions, each counted twice with the eta1 / eta2 sums 1/2 and 1
         for (int t = lane; t < 3 * n; t += 32) {
@@ -262,6 +379,25 @@ __global__ void singular_kernel(const SingularItem *__restrict__ items, int64_t 
             s += qp.gw[k] * inv_norm3(s0 * g.a1[0] + s1 * g.a2[0], s0 * g.a1[1] + s1 * g.a2[1],
                                       s0 * g.a1[2] + s1 * g.a2[2]);
         }
+    } else if (kind != 3 && (kind == 1 ? vtab : etab)) {
+        // double-float points; the lanes' partial sums as float pairs
+        float Eh[4][3], El[4][3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            split_double(g.a1[d], Eh[0][d], El[0][d]);
+            split_double(g.a2[d], Eh[1][d], El[1][d]);
+            split_double(kind == 1 ? g.b1[d] : g.b2[d], Eh[2][d], El[2][d]);
+            split_double(kind == 1 ? g.b2[d] : g.b1[d], Eh[3][d], El[3][d]);
+        }
+        float ah, al;
+        ss_sum_ff(Eh, El, kind == 1 ? vtab : etab, kind == 1 ? 2 * n3 : 5 * n2, lane, ah, al);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float bh = __shfl_xor_sync(0xffffffffu, ah, o), bl = __shfl_xor_sync(0xffffffffu, al, o);
+            ff_acc(ah, al, bh, bl);
+        }
+        s = (double)ah + (double)al;  // the same value on every lane
+        ff_done = true;
     } else if (kind == 2) {
         // 2-D: D' = d0 a1 + u1 a2 - v1 b2 over the five regions, eta1 sum = 1/2
         for (int t = lane; t < 5 * n2; t += 32) {
@@ -288,8 +424,10 @@ __global__ void singular_kernel(const SingularItem *__restrict__ items, int64_t 
             s += ss_point(g, kind, r, k1, k2, k3, qp);
         }
     }
+    if (!ff_done) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
     if (lane == 0) {
         const double ai = pt[(int64_t)PT_AREA * npad + it.i], aj = pt[(int64_t)PT_AREA * npad + it.j];
         const double a = 4.0 * ai * aj * (s / 3.0) * INV_4PI;
@@ -333,12 +471,23 @@ void assemble_nearfield(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, c
     if (nsing > tr->singular_cap) fail(HM_EINTERNAL, "touching-pair queue overflow (%lld > %lld)", (long long)nsing,
                                       (long long)tr->singular_cap);
     const_cast<hm_tree *>(tr)->n_singular = nsing;
+    DBuf vtab;  // freed after the synchronisation below
     if (nsing > 0) {
+        // common-vertex pairs in double-float unless FP64 entries were asked for
+        if (!fp64) {
+            const int nv = 2 * qp.ss_n * qp.ss_n * qp.ss_n, ne = 5 * qp.ss_n * qp.ss_n;
+            vtab.alloc(sizeof(SSPointFF) * (nv + ne));
+            ss_vertex_table_kernel<<<(nv + 255) / 256, 256, 0, s>>>(qp, vtab.as<SSPointFF>());
+            HM_LAUNCH_CHECK();
+            ss_edge_table_kernel<<<(ne + 255) / 256, 256, 0, s>>>(qp, vtab.as<SSPointFF>() + nv);
+            HM_LAUNCH_CHECK();
+        }
         const int64_t threads = nsing * 32;
         Trace trace("singular_kernel", s);
         singular_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
             items.as<SingularItem>(), nsing, tr->trim.as<int32_t>(), tr->V.as<double>(), tr->pt.as<double>(),
-            tr->npad, qp, A->dense.as<double>());
+            tr->npad, qp, A->dense.as<double>(), vtab.as<SSPointFF>(),
+            vtab.p ? vtab.as<SSPointFF>() + 2 * qp.ss_n * qp.ss_n * qp.ss_n : nullptr);
         HM_LAUNCH_CHECK();
     }
     HM_CUDA_CHECK(cudaEventRecord(e2, s));

@@ -249,11 +249,12 @@ static unsigned g1(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<i
 // ---------------------------------------------------------------------------
 // Blocks of the block-Jacobi preconditioner: runs of consecutive leaf
 // clusters (Morton order, never across two geometries) of at most BJ_ROWS
-// rows together — for the cardinality-halving trees the clusters two levels
-// above the leaves when those have 40 rows.  Block b holds the rows
+// rows together — five leaf clusters when those have 40 rows, greedily from
+// the start of each geometry.  Block b holds the rows
 // [bj_begin[b], bj_begin[b+1]) and the leaves [bj_leaf[b], bj_leaf[b+1]).
-constexpr int BJ_ROWS = 160;
+constexpr int BJ_ROWS = 200;
 constexpr int BJ_MAXM = 256;  // largest block (a single leaf may exceed BJ_ROWS)
+constexpr int BJ_SMEM_M = 232;  // blocks inverted in shared memory (232^2 floats = 210 KB)
 
 __global__ void bj_size_kernel(const int32_t *begin, int64_t nb, int64_t *sz) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nb; r += (int64_t)gridDim.x * blockDim.x) {
@@ -297,6 +298,7 @@ __global__ void bj_extract_kernel(const int32_t *begin, const int32_t *bleaf, co
 __global__ void bj_invert_kernel(const int32_t *begin, const int64_t *bj_off, double *bj) {
     const int64_t r = blockIdx.x;
     const int m = begin[r + 1] - begin[r];
+    if (m <= BJ_SMEM_M) return;  // inverted by bj_invert_smem_kernel
     double *D = bj + bj_off[r];
     __shared__ double s_piv;
     for (int p = 0; p < m; ++p) {
@@ -327,6 +329,64 @@ __global__ void bj_invert_kernel(const int32_t *begin, const int64_t *bj_off, do
             D[j * m + i] = t;
         }
     }
+}
+
+// The same inversion in FP32 with the block in shared memory (blocks of at
+// most BJ_SMEM_M rows; the others are left to bj_invert_kernel): the inverse
+// only preconditions, the Krylov method and its residuals stay FP64, so an
+// FP32-accurate inverse serves the FP64 solve as well as the exact one.
+// Writes the FP64 (rounded up from FP32) and FP32 copies, column-major.
+constexpr int BJ_INV_THREADS = 512;  // a 32 x 16 grid over the block
+__global__ void __launch_bounds__(BJ_INV_THREADS) bj_invert_smem_kernel(const int32_t *begin, const int64_t *bj_off,
+                                                                        double *bj, float *bj32) {
+    extern __shared__ float s_D[];
+    __shared__ float s_row[BJ_SMEM_M], s_col[BJ_SMEM_M];
+    __shared__ float s_piv;
+    const int64_t r = blockIdx.x;
+    const int m = begin[r + 1] - begin[r];
+    if (m > BJ_SMEM_M) return;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    double *D = bj + bj_off[r];
+    float *D32 = bj32 + bj_off[r];
+    for (int e = threadIdx.x; e < m * m; e += BJ_INV_THREADS) s_D[e] = (float)D[e];
+    __syncthreads();
+    constexpr int NB = (BJ_SMEM_M + 31) / 32;  // columns per thread
+    for (int p = 0; p < m; ++p) {
+        // pivot, the scaled pivot row and the pivot column, both 0 at p so
+        // that the rank-1 update leaves row and column p alone
+        if (threadIdx.x == 0) s_piv = 1.0f / s_D[p * m + p];
+        __syncthreads();
+        const float piv = s_piv;
+        for (int j = threadIdx.x; j < m; j += BJ_INV_THREADS) {
+            s_row[j] = j == p ? 0.0f : s_D[p * m + j] * piv;
+            s_col[j] = j == p ? 0.0f : s_D[j * m + p];
+        }
+        __syncthreads();
+        float rj[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) rj[b] = tx + 32 * b < m ? s_row[tx + 32 * b] : 0.0f;
+        for (int i = ty; i < m; i += BJ_INV_THREADS / 32) {
+            const float ci = s_col[i];
+            float *Di = s_D + i * m;
+#pragma unroll
+            for (int b = 0; b < NB; ++b)
+                if (tx + 32 * b < m) Di[tx + 32 * b] = fmaf(-ci, rj[b], Di[tx + 32 * b]);
+        }
+        __syncthreads();
+        // the new pivot row and column
+        for (int j = threadIdx.x; j < m; j += BJ_INV_THREADS) {
+            s_D[p * m + j] = j == p ? piv : s_row[j];
+            if (j != p) s_D[j * m + p] = -s_col[j] * piv;
+        }
+        __syncthreads();
+    }
+    // column-major (transposed) as bj_apply_kernel reads it
+    for (int i = ty; i < m; i += BJ_INV_THREADS / 32)
+        for (int j = tx; j < m; j += 32) {
+            const float v = s_D[j * m + i];
+            D[i * m + j] = (double)v;
+            D32[i * m + j] = v;
+        }
 }
 
 // z_b = D_b^{-1} v_b: one thread per row over the column-major inverse
@@ -399,17 +459,36 @@ void bj_setup(const hm_matrix *Ac, cudaStream_t s) {
     const int64_t tot = exclusive_scan_i64(A->bj_off.as<int64_t>(), A->bj_off.as<int64_t>(), nb + 1, s);
     DBuf bj;
     bj.alloc(sizeof(double) * std::max<int64_t>(tot, 1));
-    bj_extract_kernel<<<(unsigned)nb, 256, 0, s>>>(A->bj_begin.as<int32_t>(), A->bj_leaf.as<int32_t>(),
-                                                  tr->leaf_begin.as<int32_t>(), tr->rho_off.as<int64_t>(),
-                                                  tr->rho_K.as<int32_t>(), tr->rho_colptr.as<int64_t>(),
-                                                  tr->colidx.as<int32_t>(), A->dense.as<double>(),
-                                                  A->bj_off.as<int64_t>(), bj.as<double>());
-    HM_LAUNCH_CHECK();
-    bj_invert_kernel<<<(unsigned)nb, 256, 0, s>>>(A->bj_begin.as<int32_t>(), A->bj_off.as<int64_t>(), bj.as<double>());
-    HM_LAUNCH_CHECK();
+    {
+        Trace trace("bj_extract_kernel", s);
+        bj_extract_kernel<<<(unsigned)nb, 256, 0, s>>>(A->bj_begin.as<int32_t>(), A->bj_leaf.as<int32_t>(),
+                                                      tr->leaf_begin.as<int32_t>(), tr->rho_off.as<int64_t>(),
+                                                      tr->rho_K.as<int32_t>(), tr->rho_colptr.as<int64_t>(),
+                                                      tr->colidx.as<int32_t>(), A->dense.as<double>(),
+                                                      A->bj_off.as<int64_t>(), bj.as<double>());
+        HM_LAUNCH_CHECK();
+    }
     A->bj32.alloc(sizeof(float) * std::max<int64_t>(tot, 1));
-    bj_round_kernel<<<g1(tot), 256, 0, s>>>(bj.as<double>(), tot, A->bj32.as<float>());
-    HM_LAUNCH_CHECK();
+    int mmax = 0;
+    for (int64_t r = 0; r < nb; ++r) mmax = std::max(mmax, begin[r + 1] - begin[r]);
+    {
+        Trace trace("bj_invert_kernel", s);
+        const int msm = std::min(mmax, BJ_SMEM_M);
+        const int smem = (int)sizeof(float) * msm * msm;
+        HM_CUDA_CHECK(cudaFuncSetAttribute(bj_invert_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        bj_invert_smem_kernel<<<(unsigned)nb, BJ_INV_THREADS, smem, s>>>(A->bj_begin.as<int32_t>(),
+                                                                         A->bj_off.as<int64_t>(), bj.as<double>(),
+                                                                         A->bj32.as<float>());
+        HM_LAUNCH_CHECK();
+        if (mmax > BJ_SMEM_M) {
+            // wider blocks (single leaves of more than 232 rows): FP64 in global memory
+            bj_invert_kernel<<<(unsigned)nb, 256, 0, s>>>(A->bj_begin.as<int32_t>(), A->bj_off.as<int64_t>(),
+                                                          bj.as<double>());
+            HM_LAUNCH_CHECK();
+            bj_round_kernel<<<g1(tot), 256, 0, s>>>(bj.as<double>(), tot, A->bj32.as<float>());
+            HM_LAUNCH_CHECK();
+        }
+    }
     HM_CUDA_CHECK(cudaStreamSynchronize(s));
     A->bj = std::move(bj);
 }
@@ -625,6 +704,19 @@ static hm_status gmres(const hm_matrix *A, hm_dtype prec, const double *b, doubl
 void permute_to_morton(const hm_tree *tr, const double *x, double *xm, cudaStream_t s);
 void permute_from_morton(const hm_tree *tr, const double *ym, double alpha, double beta, double *y, cudaStream_t s);
 
+void ensure_f32_copies(const hm_matrix *A, cudaStream_t s);
+
+// The next inner precision after a refinement step that did not contract:
+// BF16 -> FP32 (the FP32 copies are made from the FP64 master if the
+// assembly did not keep them); FP32 -> FP64.
+hm_dtype raise_inner(const hm_matrix *A, hm_dtype cur, cudaStream_t s) {
+    if (cur == HM_BF16) {
+        ensure_f32_copies(A, s);
+        return HM_F32;
+    }
+    return HM_F64;
+}
+
 hm_status solve_impl(const hm_matrix *A, const double *b_orig, double *x_orig, const hm_solve_params &p,
                      cudaStream_t s, hm_solve_info *info, bool trans) {
     const auto t0 = std::chrono::steady_clock::now();
@@ -641,6 +733,7 @@ hm_status solve_impl(const hm_matrix *A, const double *b_orig, double *x_orig, c
     int iters = 0, cycles = 0, steps = 0;
     double relres = 1.0;
     hm_status st;
+    hm_dtype inner_dt = p.refine ? p.inner_dtype : HM_F64;
     if (!p.refine) {
         st = gmres(A, HM_F64, b.as<double>(), x.as<double>(), p.rel_tol, p.max_iter, G, s, iters, cycles, relres, true,
                    pc, trans, p.use_graph != 0);
@@ -657,19 +750,22 @@ hm_status solve_impl(const hm_matrix *A, const double *b_orig, double *x_orig, c
             st = HM_OK;
             relres = 0.0;
         }
+        const double stall = p.stall_ratio > 0.0 ? p.stall_ratio : 0.5;
         while (st != HM_OK && steps < p.max_refine && iters < p.max_iter) {
             ++steps;
             HM_CUDA_CHECK(cudaMemsetAsync(d.p, 0, sizeof(double) * n, s));
             double inner = 1.0;
-            gmres(A, p.inner_dtype, r.as<double>(), d.as<double>(), p.inner_tol, p.max_iter, G, s, iters, cycles,
-                  inner, true, pc, trans, p.use_graph != 0);
+            gmres(A, inner_dt, r.as<double>(), d.as<double>(), p.inner_tol, p.max_iter, G, s, iters, cycles, inner,
+                  true, pc, trans, p.use_graph != 0);
             axpy_kernel<<<g1(n), 256, 0, s>>>(1.0, d.as<double>(), n, x.as<double>());
             HM_LAUNCH_CHECK();
             apply(A, HM_F64, x.as<double>(), ax.as<double>(), G.t, s, trans);
             residual_kernel<<<g1(n), 256, 0, s>>>(b.as<double>(), ax.as<double>(), n, r.as<double>());
             HM_LAUNCH_CHECK();
+            const double prev = relres;
             relres = std::sqrt(G.norm2_host(r.as<double>(), s)) / bnorm;
             if (relres <= p.rel_tol) st = HM_OK;
+            else if (!(relres <= stall * prev) && inner_dt != HM_F64) inner_dt = raise_inner(A, inner_dt, s);
         }
     }
     permute_from_morton(tr, x.as<double>(), 1.0, 0.0, x_orig, s);
@@ -681,6 +777,7 @@ hm_status solve_impl(const hm_matrix *A, const double *b_orig, double *x_orig, c
         info->refine_steps = steps;
         info->rel_resid = relres;
         info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        info->inner_dtype = (int32_t)inner_dt;
     }
     return st;
 }
