@@ -351,8 +351,17 @@ HM_API hm_status hm_matvec_noalloc(const hm_matrix *A, int32_t trans, int32_t nr
 HM_API hm_status hm_solve(const hm_matrix *A, int32_t trans, int32_t nrhs, const double *d_b, double *d_x,
                    const hm_solve_params *params, hm_stream_t stream, hm_solve_info *info);
 
-/* Frees an hm_tree or hm_matrix handle (NULL is a no-op). */
+/* Frees an hm_tree or hm_matrix handle (NULL is a no-op).  Device buffers of
+ * 1 MiB or more are not unmapped but kept by the library for its later
+ * allocations (unmapping costs ~0.4 ms per GB), up to a quarter of the
+ * device memory; the library empties that cache by itself when one of its
+ * own allocations fails. */
 HM_API void hm_free(void *handle);
+
+/* Returns every device block the library keeps for reuse to the driver
+ * (for callers that need the memory for other allocations).  Synchronises
+ * the device. */
+HM_API void hm_trim(void);
 
 /* Tree introspection (synchronises the stream of the tree). */
 HM_API hm_status hm_tree_get_info(const hm_tree *tree, hm_tree_info *info);

@@ -24,7 +24,7 @@ EXPORTED = ["hm_build_tree", "hm_assemble", "hm_load_vector", "hm_matvec", "hm_s
             "hm_tree_get_info", "hm_tree_get_perm", "hm_tree_get_leaves", "hm_matrix_get_info",
             "hm_matrix_export", "hm_last_error", "hm_kernel_launches", "hm_matvec_noalloc", "hm_matrix_get_block",
             "hm_trace_enable", "hm_trace_read", "hm_potential", "hm_matvec_block", "hm_build_forest",
-            "hm_load_vector_geom"]
+            "hm_load_vector_geom", "hm_trim"]
 
 
 class HMError(RuntimeError):
@@ -116,6 +116,8 @@ def lib():
             f.restype = I
         L.hm_free.argtypes = [P]
         L.hm_free.restype = None
+        L.hm_trim.argtypes = []
+        L.hm_trim.restype = None
         L.hm_kernel_launches.argtypes = []
         L.hm_kernel_launches.restype = ctypes.c_int64
         L.hm_last_error.argtypes = []
@@ -276,6 +278,11 @@ def hm_solve(A, b, x, trans=0, restart=30, max_iter=3000, rel_tol=1e-10, refine=
         return info
     _check(st)
     return info
+
+
+def hm_trim():
+    """Returns the device blocks the library keeps for reuse to the driver."""
+    lib().hm_trim()
 
 
 def hm_free(handle):

@@ -280,6 +280,11 @@ hm_status hm_solve(const hm_matrix *A, int32_t trans, int32_t nrhs, const double
     return g != HM_OK ? g : result;
 }
 
+void hm_trim(void) {
+    cudaDeviceSynchronize();
+    cache_trim();
+}
+
 void hm_free(void *handle) {
     if (is_matrix(handle)) {
         hm_matrix *A = static_cast<hm_matrix *>(handle);

@@ -92,17 +92,38 @@ struct TraceTotal {
 std::vector<TraceTotal> trace_read();
 
 // ----------------------------------------------------------------------------
-// device memory: RAII buffer (cudaMalloc / cudaFree)
+// device memory: RAII buffer (cudaMalloc / cudaFree behind a block cache)
+//
+// Unmapping device memory costs ~0.4 ms per GB on this part, and an assembly
+// frees tens of GB of temporaries, so a released buffer of at least 1 MiB is
+// kept in a per-device cache (after a device synchronisation, the same wait a
+// cudaFree implies) and a later allocation takes the smallest cached block
+// that is large enough and at most 1/8 larger.  The cache holds at most a
+// quarter of the device memory; a failed cudaMalloc empties it and retries;
+// hm_trim() returns it to the driver.
 // ----------------------------------------------------------------------------
 struct DBuf {
     void *p = nullptr;
-    size_t bytes = 0;
+    size_t bytes = 0;  // requested size
+    size_t blk = 0;    // size of the underlying block
+    int dev = 0;
     DBuf() = default;
     DBuf(const DBuf &) = delete;
     DBuf &operator=(const DBuf &) = delete;
-    DBuf(DBuf &&o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+    DBuf(DBuf &&o) noexcept : p(o.p), bytes(o.bytes), blk(o.blk), dev(o.dev) {
+        o.p = nullptr;
+        o.bytes = o.blk = 0;
+    }
     DBuf &operator=(DBuf &&o) noexcept {
-        if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+        if (this != &o) {
+            release();
+            p = o.p;
+            bytes = o.bytes;
+            blk = o.blk;
+            dev = o.dev;
+            o.p = nullptr;
+            o.bytes = o.blk = 0;
+        }
         return *this;
     }
     ~DBuf() { release(); }
@@ -110,6 +131,7 @@ struct DBuf {
     void release();
     template <class T> T *as() const { return static_cast<T *>(p); }
 };
+void cache_trim();  // frees every cached block
 
 // Stream-ordered scratch (cudaMallocAsync / cudaFreeAsync on one stream): the
 // memory is usable by work queued on that stream after the allocation and is

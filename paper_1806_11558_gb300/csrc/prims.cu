@@ -3,6 +3,7 @@
 #include <cstdarg>
 #include <cmath>
 #include <atomic>
+#include <map>
 #include <mutex>
 
 #include "hm_internal.cuh"
@@ -154,10 +155,56 @@ void fail(hm_status s, const char *fmt, ...) {
 // ----------------------------------------------------------------------------
 // device buffers
 // ----------------------------------------------------------------------------
+// block cache of DBuf (see hm_internal.cuh)
+constexpr size_t CACHE_MIN = size_t(1) << 20;
+static std::mutex g_cache_mu;
+static std::multimap<std::pair<int, size_t>, void *> g_cache;  // (device, size) -> block
+static size_t g_cache_bytes = 0;
+
+static size_t cache_cap() {
+    static size_t cap = 0;
+    if (!cap) {
+        size_t fr = 0, tot = 0;
+        cap = cudaMemGetInfo(&fr, &tot) == cudaSuccess ? tot / 4 : (size_t(8) << 30);
+    }
+    return cap;
+}
+
+void cache_trim() {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (auto &kv : g_cache) {
+        cudaSetDevice(kv.first.first);
+        cudaFree(kv.second);
+    }
+    cudaSetDevice(cur);
+    g_cache.clear();
+    g_cache_bytes = 0;
+}
+
 void DBuf::alloc(size_t nbytes) {
     release();
     if (nbytes == 0) nbytes = 16;
+    HM_CUDA_CHECK(cudaGetDevice(&dev));
+    if (nbytes >= CACHE_MIN) {
+        std::lock_guard<std::mutex> lk(g_cache_mu);
+        auto it = g_cache.lower_bound({dev, nbytes});
+        if (it != g_cache.end() && it->first.first == dev && it->first.second <= nbytes + nbytes / 8) {
+            p = it->second;
+            blk = it->first.second;
+            bytes = nbytes;
+            g_cache_bytes -= blk;
+            g_cache.erase(it);
+            return;
+        }
+    }
     cudaError_t e = cudaMalloc(&p, nbytes);
+    if (e == cudaErrorMemoryAllocation) {
+        (void)cudaGetLastError();
+        cache_trim();
+        e = cudaMalloc(&p, nbytes);
+    }
     if (e != cudaSuccess) {
         p = nullptr;
         (void)cudaGetLastError();
@@ -165,12 +212,24 @@ void DBuf::alloc(size_t nbytes) {
              cudaGetErrorString(e));
     }
     bytes = nbytes;
+    blk = nbytes;
 }
 
 void DBuf::release() {
-    if (p) cudaFree(p);
+    if (p) {
+        bool cached = false;
+        if (blk >= CACHE_MIN && cudaDeviceSynchronize() == cudaSuccess) {
+            std::lock_guard<std::mutex> lk(g_cache_mu);
+            if (g_cache_bytes + blk <= cache_cap()) {
+                g_cache.insert({{dev, blk}, p});
+                g_cache_bytes += blk;
+                cached = true;
+            }
+        }
+        if (!cached) cudaFree(p);
+    }
     p = nullptr;
-    bytes = 0;
+    bytes = blk = 0;
 }
 
 int num_sms() {
