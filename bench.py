@@ -181,6 +181,26 @@ class Clocks:
         return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x, world):
+    """The largest of the ranks' values (the timed region's max over ranks);
+    x itself on one rank.  Works on any process-group backend: NCCL reduces
+    a device tensor, gloo a host tensor."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
 def run_ours(args, rank, world):
     import numpy as np
     import torch
@@ -246,9 +266,7 @@ def run_ours(args, rank, world):
                 "iters_mixed": r["iters_mixed"]}, None
     for _ in range(args.warmup):
         step(Vd, Td)
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    barrier(world)
     torch.cuda.synchronize()
     clocks = Clocks(dev.index)
     clocks.start()
@@ -260,16 +278,12 @@ def run_ours(args, rank, world):
     results = [step(Vd, Td) for _ in range(args.steps)]
     ev1.record(stream)
     torch.cuda.synchronize()
+    barrier(world)
     launches = hm.hm_kernel_launches() - l0
     hm.hm_trace_enable(False)
     trace = hm.hm_trace_read()
     ck = clocks.stop()
-    total_s = ev0.elapsed_time(ev1) / 1e3
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([total_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_s = float(tt.item())
+    total_s = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, world)
     per_step = total_s / args.steps
 
     # mixed vs FP64 solution error, matvec GB/s (separate, untimed for `value`)
