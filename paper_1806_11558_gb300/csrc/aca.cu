@@ -23,7 +23,12 @@
 // shuffle dot products, no block barriers).  All reductions have a fixed
 // order, so the factors are identical from run to run.  Converged factors are
 // copied from per-worker scratch to a bump-allocated arena; blocks that do not
-// fit are reported and re-run after the arena grows.
+// fit are reported and re-run after the arena grows.  The CTA workers keep the
+// factor columns as float pairs and form the residuals in double-float
+// arithmetic; the warp workers keep them in FP64 and form the residuals with
+// FP64 FMAs (measured: the float-pair residuals are 24% faster on the large
+// blocks of a level-8 sphere with 80-panel leaves, 5-8% slower on the small
+// blocks, where the FP32 units are already the busier pipe).
 #include <algorithm>
 #include <cmath>
 #include <map>
@@ -116,7 +121,7 @@ struct AcaShared {
 constexpr int NORM_STRIDE = 2 + 2 * MAX_KMAX;
 
 // Terms of the Frobenius norm of the approximant after step r, accumulated in
-// FP32 from the FP32 shadows Uf / Wf of the factor columns (the estimate only
+// FP32 from the high parts of the factor columns (the estimate only
 // decides when to stop): res[0] = |u_r|^2, res[1] = |w_r|^2,
 // res[2 + l] = u_r . u_l, res[2 + r + l] = w_l . w_r (l < r).  One pass over
 // the columns, per-warp shuffle reductions, one shared-memory round.
@@ -147,6 +152,56 @@ __device__ void norm_terms(const float *Uf, const float *Wf, int m, int n, int r
                 const int v = c0 + c;
                 if (v == 1) acc[c] = fmaf(w, w, acc[c]);
                 else if (v >= 2 + r && v < nvals) acc[c] = fmaf(w, Wf[(int64_t)(v - 2 - r) * n + j], acc[c]);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            float a = acc[c];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (lane == 0 && c0 + c < nvals) st[c0 + c] = a;
+        }
+    }
+    if (CTA) {
+        __syncthreads();
+        for (int v = t; v < nvals; v += gs) {
+            float a = 0.0f;
+            for (int w = 0; w < ACA_WARPS; ++w) a += sh.stage[w * NORM_STRIDE + v];
+            sh.res[v] = a;
+        }
+        __syncthreads();
+    } else {
+        __syncwarp();
+    }
+}
+
+template <bool CTA>
+__device__ void norm_terms(const FF *Uf, const FF *Wf, int m, int n, int r, const AcaShared &sh) {
+    const int gs = CTA ? ACA_THREADS : 32, t = CTA ? (int)threadIdx.x : (int)(threadIdx.x & 31);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nvals = 2 + 2 * r;
+    const FF *ur = Uf + (int64_t)r * m, *wr = Wf + (int64_t)r * n;
+    float *st = CTA ? sh.stage + warp * NORM_STRIDE : sh.stage;
+    for (int c0 = 0; c0 < nvals; c0 += 8) {
+        float acc[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[c] = 0.0f;
+        for (int k = t; k < m; k += gs) {
+            const float u = ur[k].h;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int v = c0 + c;
+                if (v == 0) acc[c] = fmaf(u, u, acc[c]);
+                else if (v >= 2 && v < 2 + r) acc[c] = fmaf(u, Uf[(int64_t)(v - 2) * m + k].h, acc[c]);
+            }
+        }
+        for (int j = t; j < n; j += gs) {
+            const float w = wr[j].h;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int v = c0 + c;
+                if (v == 1) acc[c] = fmaf(w, w, acc[c]);
+                else if (v >= 2 + r && v < nvals) acc[c] = fmaf(w, Wf[(int64_t)(v - 2 - r) * n + j].h, acc[c]);
             }
         }
 #pragma unroll
@@ -216,9 +271,11 @@ __device__ __forceinline__ bool bit(const uint32_t *bm, int k) { return (bm[k >>
 
 // One out-of-line copy of the far-field evaluation shared by every call site
 // (row and column passes, CTA and warp workers).
-__device__ __noinline__ static double far_entry(const float *r, int rs, const float *c, int cs, const float *wh,
-                                                const float *wl) {
-    return regular_entry_ff(r, rs, c, cs, wh, wl);
+__device__ __noinline__ static FF far_entry(const float *r, int rs, const float *c, int cs, const float *wh,
+                                            const float *wl) {
+    FF e;
+    regular_entry_ff2(r, rs, c, cs, wh, wl, e.h, e.l);
+    return e;
 }
 
 // Entry of the Galerkin matrix for the row panel at Morton position gi and the
@@ -227,8 +284,8 @@ __device__ __noinline__ static double far_entry(const float *r, int rs, const fl
 // panel), the other record is read from the float panel table.  Far-field
 // pairs in float-float; touching pairs (which admissible blocks do not contain
 // in practice) by the FP64 regularised rule.
-__device__ __forceinline__ double aca_entry(const float *fix, bool fixed_is_row, int64_t gi, int64_t gj,
-                                            const AcaArgs &A) {
+__device__ __forceinline__ FF aca_entry(const float *fix, bool fixed_is_row, int64_t gi, int64_t gj,
+                                        const AcaArgs &A) {
     const int64_t var = fixed_is_row ? gj : gi;
     const float *rec = A.pf + var;
     const int64_t st = A.npad;
@@ -239,16 +296,142 @@ __device__ __forceinline__ double aca_entry(const float *fix, bool fixed_is_row,
     const int kind = shared_vertices(vf, vv);
     if (kind) {
         const double ai = A.pt[(int64_t)PT_AREA * A.npad + gi], aj = A.pt[(int64_t)PT_AREA * A.npad + gj];
-        return fixed_is_row ? singular_entry_serial(A.V, vf, vv, kind, ai, aj, A.qp)
-                            : singular_entry_serial(A.V, vv, vf, kind, ai, aj, A.qp);
+        return ff_from(fixed_is_row ? singular_entry_serial(A.V, vf, vv, kind, ai, aj, A.qp)
+                                    : singular_entry_serial(A.V, vv, vf, kind, ai, aj, A.qp));
     }
     return fixed_is_row ? far_entry(fix, 1, rec, (int)st, A.qp.w_h, A.qp.w_l)
                         : far_entry(rec, (int)st, fix, 1, A.qp.w_h, A.qp.w_l);
 }
 
-// ACA of one block; U (m x kmax) and W (n x kmax) column-major in scratch.
+// ACA of one block (CTA workers); U (m x kmax) and W (n x kmax) column-major
+// in scratch, as float pairs: the residual rows and columns (entry minus the
+// rank-one terms so far) are formed in double-float arithmetic on the FP32
+// units, to ~2^-48 of the largest term, like the entries themselves.
 template <bool CTA>
-__device__ int aca_block(const AcaArgs &A, int rb, int m, int cb, int n, double *U, double *W, float *Uf, float *Wf,
+__device__ int aca_block(const AcaArgs &A, int rb, int m, int cb, int n, FF *U, FF *W, const AcaShared &sh,
+                         bool *hit_kmax) {
+    using G = Grp<CTA>;
+    const int gs = G::size(), t = G::rank();
+    const int wr = (m + 31) >> 5, wc = (n + 31) >> 5;
+    for (int k = t; k < wr; k += gs) sh.urow[k] = 0u;
+    for (int k = t; k < wc; k += gs) sh.ucol[k] = 0u;
+    G::sync();
+    const int rmax = min(A.kmax, min(m, n));
+    const double tiny = 8.881784197001252e-16;  // 2^-50
+    FF *vec = reinterpret_cast<FF *>(sh.vec);
+    int r = 0, i = 0;
+    double s2 = 0.0, delta1 = 0.0;
+    bool converged = false;
+    while (r < rmax) {
+        // ---- residual of row i ----
+        for (int q = t; q < PF_ROWS; q += gs) sh.fix[q] = A.pf[(int64_t)q * A.npad + rb + i];
+        for (int l = t; l < r; l += gs) vec[l] = U[(int64_t)l * m + i];
+        G::sync();
+        Best best{-1.0, 0x7fffffff, 0.0};
+        for (int j = t; j < n; j += gs) {
+            const FF e = aca_entry(sh.fix, true, rb + i, cb + j, A);
+            float hs = e.h, lo = e.l;
+            for (int l = 0; l < r; ++l) ff_sub_prod(hs, lo, vec[l], W[(int64_t)l * n + j]);
+            FF v;
+            fast_two_sum(hs, lo, v.h, v.l);
+            W[(int64_t)r * n + j] = v;
+            if (!bit(sh.ucol, j)) {
+                const double vd = ff_to(v);
+                const Best c{fabs(vd), j, vd};
+                if (better(c, best)) best = c;
+            }
+        }
+        best = G::argmax(best, sh);
+        if (t == 0) sh.urow[i >> 5] |= 1u << (i & 31);
+        G::sync();
+        const double delta = best.v;
+        const bool zero_row = (r == 0) ? (delta == 0.0) : (fabs(delta) <= tiny * delta1);
+        if (zero_row || best.idx == 0x7fffffff) {
+            // lowest unused row
+            int cand = 0x7fffffff;
+            for (int k = t; k < m; k += gs)
+                if (!bit(sh.urow, k)) { cand = k; break; }
+            Best c{0.0, cand, 0.0};
+            c = G::argmax(c, sh);
+            if (c.idx == 0x7fffffff) break;
+            i = c.idx;
+            continue;
+        }
+        if (r == 0) delta1 = fabs(delta);
+        const int jp = best.idx;
+        const FF inv_delta = ff_from(1.0 / delta);
+        for (int j = t; j < n; j += gs) W[(int64_t)r * n + j] = ff_mul(W[(int64_t)r * n + j], inv_delta);
+        // ---- residual of column jp ----
+        for (int q = t; q < PF_ROWS; q += gs) sh.fix[q] = A.pf[(int64_t)q * A.npad + cb + jp];
+        for (int l = t; l < r; l += gs) vec[l] = W[(int64_t)l * n + jp];
+        G::sync();
+        Best nb{-1.0, 0x7fffffff, 0.0};
+        for (int k = t; k < m; k += gs) {
+            const FF e = aca_entry(sh.fix, false, rb + k, cb + jp, A);
+            float hs = e.h, lo = e.l;
+            for (int l = 0; l < r; ++l) ff_sub_prod(hs, lo, vec[l], U[(int64_t)l * m + k]);
+            FF u;
+            fast_two_sum(hs, lo, u.h, u.l);
+            U[(int64_t)r * m + k] = u;
+            if (!bit(sh.urow, k)) {
+                const double ud = ff_to(u);
+                const Best c{fabs(ud), k, ud};
+                if (better(c, nb)) nb = c;
+            }
+        }
+        if (t == 0) sh.ucol[jp >> 5] |= 1u << (jp & 31);
+        // ---- Frobenius norm of the approximant ----
+        norm_terms<CTA>(U, W, m, n, r, sh);
+        const float *res = CTA ? sh.res : sh.stage;
+        const double nu2 = res[0], nw2 = res[1];
+        double cross = 0.0;
+        for (int l = 0; l < r; ++l) cross += (double)res[2 + l] * (double)res[2 + r + l];
+        s2 = s2 + 2.0 * cross + nu2 * nw2;
+        ++r;
+        nb = G::argmax(nb, sh);
+        if (sqrt(nu2) * sqrt(nw2) <= A.eps * sqrt(s2)) { converged = true; break; }
+        if (nb.idx == 0x7fffffff) { converged = true; break; }
+        i = nb.idx;
+        G::sync();
+    }
+    *hit_kmax = !converged && r == A.kmax && r < min(m, n);
+    return r;
+}
+
+// copy the first k columns of U and W to the arena (bump allocation)
+template <bool CTA>
+__device__ void aca_store(const AcaArgs &A, int64_t b, int m, int n, int k, const FF *U, const FF *W,
+                          const AcaShared &sh) {
+    using G = Grp<CTA>;
+    const int gs = G::size(), t = G::rank();
+    const int64_t need = (int64_t)k * (m + n);
+    long long off = 0;
+    if (t == 0) off = (long long)atomicAdd(A.arena_top, (unsigned long long)need);
+    off = G::bcast(off, sh);
+    if (t == 0) A.rank[b] = k;
+    if ((int64_t)off + need > A.arena_cap) {
+        if (t == 0) A.uw_off[b] = -1;
+        return;
+    }
+    if (t == 0) A.uw_off[b] = (int64_t)off;
+    // U_b column-major (m x k); W_b row-major (n x k): row j of W_b holds the
+    // k coefficients of column j of the block, which the projection W_b^T x
+    // reads contiguously
+    double *dst = A.arena + off;
+    const int64_t mk = (int64_t)m * k, nk = (int64_t)n * k;
+    for (int64_t e = t; e < mk; e += gs) dst[e] = ff_to(U[e]);
+    for (int64_t e = t; e < nk; e += gs) {
+        const int64_t j = e / k, l = e - j * k;
+        dst[mk + e] = ff_to(W[l * n + j]);
+    }
+}
+
+// The same ACA with the factor columns in FP64 (U, W) plus FP32 shadows (Uf,
+// Wf) for the norm terms, the rank-one updates of the residuals in FP64.
+// Used by the warp workers (small blocks), where the FP32 units are the
+// busier pipe; the CTA workers (large blocks) use the float-pair form.
+template <bool CTA>
+__device__ int aca_block_d(const AcaArgs &A, int rb, int m, int cb, int n, double *U, double *W, float *Uf, float *Wf,
                          const AcaShared &sh, bool *hit_kmax) {
     using G = Grp<CTA>;
     const int gs = G::size(), t = G::rank();
@@ -268,7 +451,7 @@ __device__ int aca_block(const AcaArgs &A, int rb, int m, int cb, int n, double 
         G::sync();
         Best best{-1.0, 0x7fffffff, 0.0};
         for (int j = t; j < n; j += gs) {
-            double v = aca_entry(sh.fix, true, rb + i, cb + j, A);
+            double v = ff_to(aca_entry(sh.fix, true, rb + i, cb + j, A));
             for (int l = 0; l < r; ++l) v -= sh.vec[l] * W[(int64_t)l * n + j];
             W[(int64_t)r * n + j] = v;
             if (!bit(sh.ucol, j)) {
@@ -306,7 +489,7 @@ __device__ int aca_block(const AcaArgs &A, int rb, int m, int cb, int n, double 
         G::sync();
         Best nb{-1.0, 0x7fffffff, 0.0};
         for (int k = t; k < m; k += gs) {
-            double u = aca_entry(sh.fix, false, rb + k, cb + jp, A);
+            double u = ff_to(aca_entry(sh.fix, false, rb + k, cb + jp, A));
             for (int l = 0; l < r; ++l) u -= sh.vec[l] * U[(int64_t)l * m + k];
             U[(int64_t)r * m + k] = u;
             Uf[(int64_t)r * m + k] = (float)u;
@@ -334,7 +517,6 @@ __device__ int aca_block(const AcaArgs &A, int rb, int m, int cb, int n, double 
     return r;
 }
 
-// copy the first k columns of U and W to the arena (bump allocation)
 template <bool CTA>
 __device__ void aca_store(const AcaArgs &A, int64_t b, int m, int n, int k, const double *U, const double *W,
                           const AcaShared &sh) {
@@ -398,14 +580,13 @@ __global__ void __launch_bounds__(ACA_THREADS, 5) aca_kernel(AcaArgs A) {
             const int64_t b = A.todo ? A.todo[q] : A.work[q0 + q];
             const int32_t rb = A.adm[4 * b], re = A.adm[4 * b + 1], cb = A.adm[4 * b + 2], ce = A.adm[4 * b + 3];
             const int m = re - rb, n = ce - cb;
-            double *W = U + (int64_t)m * A.kmax;
-            float *Uf = reinterpret_cast<float *>(W + (int64_t)n * A.kmax);
-            float *Wf = Uf + (int64_t)m * A.kmax;
+            FF *Uff = reinterpret_cast<FF *>(U);
+            FF *W = Uff + (int64_t)m * A.kmax;
             bool hit = false;
-            const int k = aca_block<true>(A, rb, m, cb, n, U, W, Uf, Wf, sh, &hit);
+            const int k = aca_block<true>(A, rb, m, cb, n, Uff, W, sh, &hit);
             if (hit && threadIdx.x == 0) atomicAdd(A.kmax_hit, 1);
             __syncthreads();
-            aca_store<true>(A, b, m, n, k, U, W, sh);
+            aca_store<true>(A, b, m, n, k, Uff, W, sh);
             __syncthreads();
         }
     }
@@ -438,7 +619,7 @@ __global__ void __launch_bounds__(ACA_THREADS, 5) aca_kernel(AcaArgs A) {
             float *Uf = reinterpret_cast<float *>(W + (int64_t)n * A.kmax);
             float *Wf = Uf + (int64_t)m * A.kmax;
             bool hit = false;
-            const int k = aca_block<false>(A, rb, m, cb, n, U, W, Uf, Wf, sh, &hit);
+            const int k = aca_block_d<false>(A, rb, m, cb, n, U, W, Uf, Wf, sh, &hit);
             if (hit && lane == 0) atomicAdd(A.kmax_hit, 1);
             __syncwarp();
             aca_store<false>(A, b, m, n, k, U, W, sh);
@@ -567,8 +748,8 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
     base.eps = A->params.aca_eps;
     base.kmax = kmax;
     base.qp = qp;
-    // per worker: U, W (double) and their FP32 shadows, (m + n) * kmax * 1.5 doubles
-    base.big_stride = ((int64_t)(max_m_big + max_n_big) * kmax * 3 + 1) / 2;
+    // per worker: U and W as float pairs, (m + n) * kmax * 8 bytes
+    base.big_stride = (int64_t)(max_m_big + max_n_big) * kmax;
     base.big_words_r = words_r;
     base.big_words_c = words_c;
     // scratch of the huge blocks (it scales with the largest admissible
@@ -583,7 +764,7 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
         base.big_ctas = (int)std::max<int64_t>(std::min<int64_t>(num_sms(), grid),
                                                std::min<int64_t>(base.big_ctas, budget / (8 * base.big_stride)));
     }
-    base.med_stride = std::min<int64_t>(base.big_stride, ((int64_t)HUGE_SUM * kmax * 3 + 1) / 2);
+    base.med_stride = std::min<int64_t>(base.big_stride, (int64_t)HUGE_SUM * kmax);
     DBuf scr_big, scr_med;
     scr_big.alloc(sizeof(double) * base.big_stride * base.big_ctas);
     scr_med.alloc(sizeof(double) * base.med_stride * grid);
@@ -635,7 +816,7 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
         a.work = d_work.as<int32_t>();
         a.n_big = n_big;
         a.n_work = (int64_t)work.size();
-        a.small_stride = ((int64_t)max_sum_small * kmax * 3 + 1) / 2;
+        a.small_stride = ((int64_t)max_sum_small * kmax * 3 + 1) / 2;  // U, W in FP64 + FP32 shadows
         scr_small.alloc(sizeof(double) * a.small_stride * grid * ACA_WARPS);
         a.scr_small = scr_small.as<double>();
         a.arena_top = ctr4;
@@ -719,7 +900,7 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
         a.n_huge = n_huge;
         a.q_huge = ctr.as<unsigned long long>() + 4;
         a.n_work = (int64_t)work.size();
-        a.small_stride = ((int64_t)max_sum_small * kmax * 3 + 1) / 2;
+        a.small_stride = ((int64_t)max_sum_small * kmax * 3 + 1) / 2;  // U, W in FP64 + FP32 shadows
         a.scr_small = scr_small.as<double>();
         a.arena_top = ctr.as<unsigned long long>();
         a.q_big = ctr.as<unsigned long long>() + 1;

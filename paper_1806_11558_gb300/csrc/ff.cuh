@@ -60,11 +60,50 @@ constexpr int PF_AH = 0, PF_AL = 21, PF_CH = 42, PF_CL = 45, PF_WA = 48, PF_VID 
 // sqrt(4 pi)
 constexpr double SQRT_4PI = 3.5449077018110320545963349666822903655950989122447742564276155;
 
+// A float pair h + l (|l| <= ulp(h) / 2 when normalised).
+struct __align__(8) FF {
+    float h, l;
+};
+
+__device__ __forceinline__ FF ff_from(double x) {
+    FF r;
+    split_double(x, r.h, r.l);
+    return r;
+}
+__device__ __forceinline__ double ff_to(FF a) { return (double)a.h + (double)a.l; }
+
+// a * b, normalised, to ~2^-47 relative
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+    float ph, pe;
+    two_prod(a.h, b.h, ph, pe);
+    pe = __fmaf_rn(a.h, b.l, pe);
+    pe = __fmaf_rn(a.l, b.h, pe);
+    FF r;
+    fast_two_sum(ph, pe, r.h, r.l);
+    return r;
+}
+
+// (hs, lo) -= b * c: the high parts subtract exactly (TwoSum) and every
+// rounding error goes to lo, so a chain of these followed by one
+// fast_two_sum(hs, lo) is accurate to ~2^-48 of the largest term
+__device__ __forceinline__ void ff_sub_prod(float &hs, float &lo, FF b, FF c) {
+    float ph, pe;
+    two_prod(b.h, c.h, ph, pe);
+    pe = __fmaf_rn(b.h, c.l, pe);
+    pe = __fmaf_rn(b.l, c.h, pe);
+    float s, e;
+    two_sum(hs, -ph, s, e);
+    hs = s;
+    lo = __fadd_rn(lo, __fsub_rn(e, pe));
+}
+
 // Regular entry a_ij = |Ti||Tj|/(4 pi) sum_p sum_q w_p w_q / |x_p - y_q| for
 // panel records R (row, test) and C (column, trial); element k of a record at
-// R[k * rs].  wq_h / wq_l: the 7 weights as float pairs.
-__device__ __forceinline__ double regular_entry_ff(const float *__restrict__ R, int rs, const float *__restrict__ C,
-                                                   int cs, const float *wq_h, const float *wq_l) {
+// R[k * rs].  wq_h / wq_l: the 7 weights as float pairs.  Returns the float
+// pair (eh, el), not normalised.
+__device__ __forceinline__ void regular_entry_ff2(const float *__restrict__ R, int rs, const float *__restrict__ C,
+                                                  int cs, const float *wq_h, const float *wq_l, float &eh_out,
+                                                  float &el_out) {
     // D = c_R - c_C in float-float, to 2^-48 |D|: the hi and lo differences
     // are both exact (TwoSum), and only their combination rounds, so
     // neighbouring panels (|D| ~ panel size) keep full relative accuracy
@@ -162,6 +201,14 @@ __device__ __forceinline__ double regular_entry_ff(const float *__restrict__ R, 
     two_prod(ah, wh, eh, el);
     el = __fmaf_rn(ah, wl, el);
     el = __fmaf_rn(al, wh, el);
+    eh_out = eh;
+    el_out = el;
+}
+
+__device__ __forceinline__ double regular_entry_ff(const float *__restrict__ R, int rs, const float *__restrict__ C,
+                                                   int cs, const float *wq_h, const float *wq_l) {
+    float eh, el;
+    regular_entry_ff2(R, rs, C, cs, wq_h, wq_l, eh, el);
     return (double)eh + (double)el;
 }
 
