@@ -164,6 +164,11 @@ typedef struct {
     int32_t inner_dtype;  /* precision of the last inner solve (refine = 1; it is
                              above the requested one after a stall, see
                              stall_ratio); HM_F64 when refine = 0             */
+    double kappa_est;     /* sigma_max / sigma_min of the first GMRES cycle's
+                             Hessenberg matrix (of the first inner solve when
+                             refining): a lower estimate of the condition
+                             number of op(H) (of op(H) M^-1 with precond = 1);
+                             0 for batched solves                            */
 } hm_solve_info;
 
 typedef struct {

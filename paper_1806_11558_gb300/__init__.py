@@ -52,7 +52,7 @@ class SolveParams(ctypes.Structure):
 class SolveInfo(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("restarts", ctypes.c_int32),
                 ("refine_steps", ctypes.c_int32), ("rel_resid", ctypes.c_double), ("seconds", ctypes.c_double),
-                ("inner_dtype", ctypes.c_int32)]
+                ("inner_dtype", ctypes.c_int32), ("kappa_est", ctypes.c_double)]
 
 
 class TreeInfo(ctypes.Structure):

@@ -649,6 +649,7 @@ hm_status solve_batched(const hm_matrix *A, int nrhs, const double *b_orig, doub
         info->rel_resid = worst;
         info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         info->inner_dtype = (int32_t)inner_dt;
+        info->kappa_est = 0.0;  // not estimated by the lockstep solver
     }
     return st;
 }

@@ -551,6 +551,61 @@ struct Gmres {
     }
 };
 
+// Condition estimate sigma_max / sigma_min of the k x k triangular factor R
+// of the rotated Hessenberg matrix (column-major, leading dimension ldh):
+// H_k = Q R, so R has the singular values of the Arnoldi matrix, which lie
+// inside those of the operator (of the preconditioned operator with
+// preconditioning).  Power iteration on R^T R for the largest, inverse
+// iteration (two triangular solves per step) for the smallest; host FP64.
+static double kappa_from_R(const std::vector<double> &H, int ldh, int k) {
+    if (k < 1) return 0.0;
+    auto R = [&](int i, int j) { return H[(size_t)j * ldh + i]; };
+    std::vector<double> v(k, 1.0), w(k), z(k);
+    auto normalise = [&](std::vector<double> &a) {
+        double t = 0.0;
+        for (double x : a) t += x * x;
+        t = std::sqrt(t);
+        if (t > 0.0)
+            for (double &x : a) x /= t;
+        return t;
+    };
+    normalise(v);
+    double lmax = 0.0;
+    for (int it = 0; it < 40; ++it) {
+        for (int i = 0; i < k; ++i) {  // w = R v
+            double t = 0.0;
+            for (int j = i; j < k; ++j) t += R(i, j) * v[j];
+            w[i] = t;
+        }
+        for (int j = 0; j < k; ++j) {  // z = R^T w
+            double t = 0.0;
+            for (int i = 0; i <= j; ++i) t += R(i, j) * w[i];
+            z[j] = t;
+        }
+        lmax = normalise(z);
+        v = z;
+    }
+    std::fill(v.begin(), v.end(), 1.0);
+    normalise(v);
+    double lmin_inv = 0.0;
+    for (int it = 0; it < 40; ++it) {
+        for (int j = 0; j < k; ++j) {  // R^T w = v (forward)
+            double t = v[j];
+            for (int i = 0; i < j; ++i) t -= R(i, j) * w[i];
+            w[j] = t / R(j, j);
+        }
+        for (int i = k - 1; i >= 0; --i) {  // R z = w (backward)
+            double t = w[i];
+            for (int j = i + 1; j < k; ++j) t -= R(i, j) * z[j];
+            z[i] = t / R(i, i);
+        }
+        lmin_inv = normalise(z);
+        v = z;
+    }
+    if (!(lmax > 0.0) || !(lmin_inv > 0.0) || !std::isfinite(lmin_inv)) return 0.0;
+    return std::sqrt(lmax * lmin_inv);
+}
+
 // The Arnoldi loop of a cycle as a graph: one step per iteration of the
 // WHILE node, the step index in G.ctl (the same kernels as the host loop).
 static const LoopGraph &step_graph(const hm_matrix *A, hm_dtype prec, Gmres &G, bool precond, bool trans) {
@@ -595,7 +650,7 @@ static const LoopGraph &step_graph(const hm_matrix *A, hm_dtype prec, Gmres &G, 
 // and cycles accumulate; relres = final true residual / ||b||.
 static hm_status gmres(const hm_matrix *A, hm_dtype prec, const double *b, double *x, double tol, int maxit,
                        Gmres &G, cudaStream_t s, int &iters, int &cycles, double &relres, bool x_is_zero,
-                       bool precond, bool trans, bool use_graph) {
+                       bool precond, bool trans, bool use_graph, double *kappa = nullptr) {
     const int64_t n = G.n;
     const int m = G.m;
     double *V = G.V.as<double>();
@@ -677,6 +732,13 @@ static hm_status gmres(const hm_matrix *A, hm_dtype prec, const double *b, doubl
                 HM_LAUNCH_CHECK();
             }
         }
+        if (kappa && *kappa == 0.0 && k > 0) {
+            // condition estimate from the first cycle's Hessenberg factor
+            std::vector<double> Hh((size_t)(m + 1) * k);
+            HM_CUDA_CHECK(cudaMemcpyAsync(Hh.data(), G.H.p, sizeof(double) * Hh.size(), cudaMemcpyDeviceToHost, s));
+            HM_CUDA_CHECK(cudaStreamSynchronize(s));
+            *kappa = kappa_from_R(Hh, m + 1, k);
+        }
         trisolve_kernel<<<1, 32, 0, s>>>(G.H.as<double>(), m + 1, k, G.g.as<double>(), G.y.as<double>());
         HM_LAUNCH_CHECK();
         if (precond) {
@@ -734,9 +796,10 @@ hm_status solve_impl(const hm_matrix *A, const double *b_orig, double *x_orig, c
     double relres = 1.0;
     hm_status st;
     hm_dtype inner_dt = p.refine ? p.inner_dtype : HM_F64;
+    double kappa = 0.0;
     if (!p.refine) {
         st = gmres(A, HM_F64, b.as<double>(), x.as<double>(), p.rel_tol, p.max_iter, G, s, iters, cycles, relres, true,
-                   pc, trans, p.use_graph != 0);
+                   pc, trans, p.use_graph != 0, &kappa);
     } else {
         DBuf r, d, ax;
         r.alloc(sizeof(double) * n);
@@ -756,7 +819,7 @@ hm_status solve_impl(const hm_matrix *A, const double *b_orig, double *x_orig, c
             HM_CUDA_CHECK(cudaMemsetAsync(d.p, 0, sizeof(double) * n, s));
             double inner = 1.0;
             gmres(A, inner_dt, r.as<double>(), d.as<double>(), p.inner_tol, p.max_iter, G, s, iters, cycles, inner,
-                  true, pc, trans, p.use_graph != 0);
+                  true, pc, trans, p.use_graph != 0, &kappa);
             axpy_kernel<<<g1(n), 256, 0, s>>>(1.0, d.as<double>(), n, x.as<double>());
             HM_LAUNCH_CHECK();
             apply(A, HM_F64, x.as<double>(), ax.as<double>(), G.t, s, trans);
@@ -778,6 +841,7 @@ hm_status solve_impl(const hm_matrix *A, const double *b_orig, double *x_orig, c
         info->rel_resid = relres;
         info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         info->inner_dtype = (int32_t)inner_dt;
+        info->kappa_est = kappa;
     }
     return st;
 }

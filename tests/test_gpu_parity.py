@@ -243,3 +243,26 @@ def test_degenerate_meshes(orc, case):
         assert np.linalg.norm(y - A @ x) <= 1e-9 * np.linalg.norm(A @ x)
     finally:
         g.close()
+
+
+def test_kappa_estimate_from_hessenberg(orc):
+    # sigma_max / sigma_min of the first cycle's Hessenberg factor lies inside
+    # the operator's condition number and, with a Krylov space long enough to
+    # converge, close to it (the spectrum's ends converge first); the
+    # reference is the dense oracle matrix's eigenvalue ratio (it is SPD)
+    need_gpu()
+    V, T = MESHES["ico3"]
+    g = GpuH(V, T, leaf=64, eta=1.5, eps=1e-12, kmax=128)
+    try:
+        A = orc.dense_matrix(V, T)
+        ev = np.linalg.eigvalsh(0.5 * (A + A.T))
+        kappa = ev[-1] / ev[0]
+        b = g.load_vector(np.array([[3.0, 0.0, 0.0]]))[0]
+        x, info = g.solve(b, rel_tol=1e-12, restart=128, max_iter=128, raise_on_noconv=False)
+        assert info.restarts == 1 and info.iters >= 40
+        assert 0.7 * kappa <= info.kappa_est <= 1.001 * kappa, (info.kappa_est, kappa)
+        # refined and preconditioned solves report the estimate of their operator
+        _, ip = g.solve(b, rel_tol=1e-12, restart=128, max_iter=500, precond=1)
+        assert 1.0 <= ip.kappa_est < kappa
+    finally:
+        g.close()
