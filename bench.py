@@ -253,6 +253,7 @@ def run_ours(args, rank, world):
         t["refine_steps"] = imx.refine_steps
         t["resid_fp64"] = i64.rel_resid
         t["resid_mixed"] = imx.rel_resid
+        t["kappa_est"] = i64.kappa_est
         if keep:
             return t, tree, A
         hm.hm_free(A)
@@ -382,7 +383,8 @@ def run_ours(args, rank, world):
         "solve_fp64_s": sum(r["solve_fp64_s"] for r in results) / len(results),
         "solve_mixed_s": sum(r["solve_mixed_s"] for r in results) / len(results),
         "iters_fp64": last["iters_fp64"], "iters_mixed": last["iters_mixed"], "refine_steps": last["refine_steps"],
-        "resid_fp64": last["resid_fp64"], "resid_mixed": last["resid_mixed"], "mixed_vs_fp64_rel_err": err_mixed,
+        "resid_fp64": last["resid_fp64"], "resid_mixed": last["resid_mixed"],
+        "kappa_est_fp64_solve": last["kappa_est"], "mixed_vs_fp64_rel_err": err_mixed,
         "bf16": bf16, "matvec": mv, "mean_rank": mi["mean_rank"], "max_rank": mi["max_rank"],
         "dense_entries": mi["dense_entries"], "lr_entries": mi["lr_entries"],
         "roofline": roofline, "kernels": kernels, "rooflines_other": others,
