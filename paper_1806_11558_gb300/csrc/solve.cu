@@ -40,7 +40,7 @@ static void apply(const hm_matrix *A, hm_dtype prec, const double *x, double *y,
     matvec_morton(A, prec, w, s, trans);
 }
 
-constexpr int DOT_THREADS = 256;
+constexpr int DOT_THREADS = 512;
 constexpr int DOT_CHUNK = 8;  // vectors per register pass
 
 // out[l] = V_l . w for l < nv (+ out[l] when accumulate), one launch: every
@@ -517,7 +517,10 @@ struct Gmres {
     DBuf V, w, ax, part, h, H, cs, sn, g, y, est, t, nrm, z, d, ticket, ctl, xin;
     std::map<int, std::unique_ptr<LoopGraph>> graphs;  // keyed by precision, preconditioning, transpose
     Gmres(int64_t n_, int m_, int64_t work_doubles, cudaStream_t s) : n(n_), m(m_) {
-        nblk = std::max(1, std::min<int>(4 * num_sms(), (int)((n + 1023) / 1024)));
+        // one block per SM: the last block's fixed-order sum over the blocks'
+        // partials is the serial part of a dot-product pass (measured best of
+        // 1, 2 and 4 blocks per SM with 256 and 512 threads)
+        nblk = std::max(1, std::min<int>(num_sms(), (int)((n + 1023) / 1024)));
         V.alloc(sizeof(double) * (int64_t)(m + 1) * n);
         w.alloc(sizeof(double) * n);
         ax.alloc(sizeof(double) * n);
