@@ -478,8 +478,9 @@ def _ev(torch):
 def run_large(torch, hm):
     """Large workload: icosphere level 8 (1,310,720 panels), leaf 128, eps 1e-6,
     16 point sources; FP64 form (16 FP64 solves in lockstep) against the
-    mixed form (FP32 near field + BF16 factors, inner solves through the
-    16-right-hand-side tensor-core product, FP64 refinement)."""
+    mixed forms (FP32 near field + BF16 factors, then FP32 factors added from
+    the FP64 master; inner solves through the 16-right-hand-side tensor-core
+    product, FP64 refinement)."""
     import meshgen
     cfg = meshgen.config("large")
     n = cfg["T"].shape[0]
@@ -512,6 +513,15 @@ def run_large(torch, hm):
     e[6].record()
     torch.cuda.synchronize()
     hm.hm_trace_enable(False)
+    # the same refinement with FP32 factors (the copy made from the FP64 master)
+    hm.hm_matrix_add_copy(A, hm.HM_F32)
+    X32 = torch.zeros_like(F)
+    e[7].record()
+    i32 = hm.hm_solve(A, F, X32, refine=1, inner_dtype=hm.HM_F32, inner_tol=1e-4, max_refine=40, **opts)
+    e8 = _ev(torch)
+    e8.record()
+    torch.cuda.synchronize()
+    err32 = float(torch.max(torch.linalg.norm(X32 - X64, dim=1) / torch.linalg.norm(X64, dim=1)))
     mi = hm.hm_matrix_get_info(A)
     mat_bytes = mi["dense_entries"] * 4 + mi["lr_entries"] * 2
     blk_s = e[2].elapsed_time(e[3]) / 5e3
@@ -524,6 +534,9 @@ def run_large(torch, hm):
            "mixed_refine_steps": im.refine_steps, "mixed_rel_resid": im.rel_resid,
            "solve_fp64_16rhs_s": e[5].elapsed_time(e[6]) / 1e3, "fp64_iters": i64.iters,
            "fp64_rel_resid": i64.rel_resid, "mixed_vs_fp64_max_rel_err": err,
+           "solve_mixed_fp32_16rhs_s": e[7].elapsed_time(e8) / 1e3, "mixed_fp32_iters": i32.iters,
+           "mixed_fp32_refine_steps": i32.refine_steps, "mixed_fp32_rel_resid": i32.rel_resid,
+           "mixed_fp32_vs_fp64_max_rel_err": err32,
            "kernels": kernel_table(hm.hm_trace_read(), 1)}
     hm.hm_free(A)
     hm.hm_free(tree)

@@ -363,6 +363,15 @@ HM_API hm_status hm_solve(const hm_matrix *A, int32_t trans, int32_t nrhs, const
  * own allocations fails. */
 HM_API void hm_free(void *handle);
 
+/* Adds a low-precision copy to an assembled matrix, made from its FP64
+ * master and kept with it: dtype HM_F32 = FP32 copies of the near field and
+ * the factors; HM_BF16 = BF16 factors (and the FP32 near field they run
+ * with).  A copy that exists is kept as it is.  Afterwards the matrix serves
+ * products and inner solves in that precision exactly as if the assembly had
+ * kept the copy (the same rounding of the same FP64 values).  Stream-ordered.
+ * HM_EINVAL for another dtype, HM_ENOMEM when it does not fit. */
+HM_API hm_status hm_matrix_add_copy(const hm_matrix *A, hm_dtype dtype, hm_stream_t stream);
+
 /* Returns every device block the library keeps for reuse to the driver
  * (for callers that need the memory for other allocations).  Synchronises
  * the device. */

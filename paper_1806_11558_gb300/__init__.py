@@ -24,7 +24,7 @@ EXPORTED = ["hm_build_tree", "hm_assemble", "hm_load_vector", "hm_matvec", "hm_s
             "hm_tree_get_info", "hm_tree_get_perm", "hm_tree_get_leaves", "hm_matrix_get_info",
             "hm_matrix_export", "hm_last_error", "hm_kernel_launches", "hm_matvec_noalloc", "hm_matrix_get_block",
             "hm_trace_enable", "hm_trace_read", "hm_potential", "hm_matvec_block", "hm_build_forest",
-            "hm_load_vector_geom", "hm_trim"]
+            "hm_load_vector_geom", "hm_trim", "hm_matrix_add_copy"]
 
 
 class HMError(RuntimeError):
@@ -118,6 +118,8 @@ def lib():
         L.hm_free.restype = None
         L.hm_trim.argtypes = []
         L.hm_trim.restype = None
+        L.hm_matrix_add_copy.argtypes = [P, ctypes.c_int, P]
+        L.hm_matrix_add_copy.restype = ctypes.c_int
         L.hm_kernel_launches.argtypes = []
         L.hm_kernel_launches.restype = ctypes.c_int64
         L.hm_last_error.argtypes = []
@@ -278,6 +280,11 @@ def hm_solve(A, b, x, trans=0, restart=30, max_iter=3000, rel_tol=1e-10, refine=
         return info
     _check(st)
     return info
+
+
+def hm_matrix_add_copy(A, dtype, stream=None):
+    """Adds the FP32 (HM_F32) or BF16 (HM_BF16) copy to an assembled matrix."""
+    _check(lib().hm_matrix_add_copy(A, int(dtype), _stream(stream)))
 
 
 def hm_trim():

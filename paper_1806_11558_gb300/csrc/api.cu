@@ -23,6 +23,8 @@ void assemble_nearfield(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, c
 void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStream_t s, double *sec, DBuf &uw,
                   DBuf &uw_off);
 void build_lr_panels(hm_matrix *A, const DBuf &uw, const DBuf &uw_off, cudaStream_t s);
+void ensure_f32_copies(const hm_matrix *A, cudaStream_t s);
+void ensure_bf16_copies(const hm_matrix *A, cudaStream_t s);
 void make_low_copies(hm_matrix *A, cudaStream_t s);
 void matvec_morton(const hm_matrix *A, hm_dtype prec, const MatvecWork &w, cudaStream_t s, bool trans);
 void build_transposed(const hm_matrix *A, cudaStream_t s);
@@ -278,6 +280,17 @@ hm_status hm_solve(const hm_matrix *A, int32_t trans, int32_t nrhs, const double
         }
     });
     return g != HM_OK ? g : result;
+}
+
+hm_status hm_matrix_add_copy(const hm_matrix *A, hm_dtype dtype, hm_stream_t stream) {
+    return guard([&] {
+        if (!is_matrix(A)) fail(HM_EINVAL, "not a matrix handle");
+        if (dtype != HM_F32 && dtype != HM_BF16) fail(HM_EINVAL, "dtype must be HM_F32 or HM_BF16");
+        if (dtype == HM_F32)
+            ensure_f32_copies(A, (cudaStream_t)stream);
+        else
+            ensure_bf16_copies(A, (cudaStream_t)stream);
+    });
 }
 
 void hm_trim(void) {

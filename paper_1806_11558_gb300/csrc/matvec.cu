@@ -621,6 +621,33 @@ void make_low_copies(hm_matrix *A, cudaStream_t s) {
     }
 }
 
+// BF16 copies of the factors (and the FP32 near field they run with) from the
+// FP64 master, when the assembly did not keep them.
+void ensure_bf16_copies(const hm_matrix *Ac, cudaStream_t s) {
+    hm_matrix *A = const_cast<hm_matrix *>(Ac);  // cache owned by the matrix
+    const int64_t nd = A->tree->dense_entries, nu = std::max<int64_t>(A->up_entries, 8),
+                  nw = std::max<int64_t>(A->wp_entries, 8);
+    if (!A->dense32.p) {
+        A->dense32.alloc(sizeof(float) * std::max<int64_t>(nd, 1));
+        to_f32_kernel<<<grid1d(nd), 256, 0, s>>>(A->dense.as<double>(), nd, A->dense32.as<float>());
+        HM_LAUNCH_CHECK();
+    }
+    if (!A->upbf.p) {
+        A->upbf.alloc(sizeof(__nv_bfloat16) * nu);
+        A->wpbf.alloc(sizeof(__nv_bfloat16) * nw);
+        to_bf16_kernel<<<grid1d(nu), 256, 0, s>>>(A->up.as<double>(), nu, A->upbf.as<__nv_bfloat16>());
+        HM_LAUNCH_CHECK();
+        to_bf16_kernel<<<grid1d(nw), 256, 0, s>>>(A->wp.as<double>(), nw, A->wpbf.as<__nv_bfloat16>());
+        HM_LAUNCH_CHECK();
+    }
+    if (A->trans_ready && !A->dense32_t.p) {
+        const int64_t ne = std::max<int64_t>(A->tree->dense_entries, 1);
+        A->dense32_t.alloc(sizeof(float) * ne);
+        to_f32_kernel<<<grid1d(ne), 256, 0, s>>>(A->dense_t.as<double>(), ne, A->dense32_t.as<float>());
+        HM_LAUNCH_CHECK();
+    }
+}
+
 // FP32 copies of the factors (and of the near field) from the FP64 master,
 // when the assembly did not keep them: the precision an inner solve on the
 // BF16 factors falls back to when refinement stops contracting.

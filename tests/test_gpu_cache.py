@@ -72,3 +72,31 @@ def test_trim_returns_memory(orc):
     # the freed matrix stays cached until the trim, which returns it
     assert free1 >= free_cached
     assert abs(free1 - free0) <= 64 << 20
+
+
+@pytest.mark.parametrize("dtype", [1, 2])
+def test_add_copy_matches_assembled_copy(orc, dtype):
+    # a copy added after the assembly is the same rounding of the same FP64
+    # master as the copy the assembly keeps: products agree bit for bit
+    torch = need_gpu()
+    import paper_1806_11558_gb300 as hm
+    V, T, _ = meshgen.bump_sphere(4, 1816)
+    g = GpuH(V, T, leaf=64, eta=1.5, eps=1e-8, factor_dtype=dtype, dense_dtype=hm.HM_F32)
+    try:
+        A2 = hm.hm_assemble(g.tree, aca_eps=1e-8, aca_kmax=64, ss_order=8)
+        try:
+            with pytest.raises(hm.HMError):
+                hm.hm_matvec(A2, torch.zeros(g.n, dtype=torch.float64, device="cuda"),
+                             torch.zeros(g.n, dtype=torch.float64, device="cuda"), prec=dtype)
+            hm.hm_matrix_add_copy(A2, dtype)
+            hm.hm_matrix_add_copy(A2, dtype)  # a second call keeps the copy
+            x = torch.from_numpy(np.random.default_rng(6).standard_normal(g.n)).cuda()
+            y1, y2 = torch.empty_like(x), torch.empty_like(x)
+            hm.hm_matvec(g.A, x, y1, prec=dtype)
+            hm.hm_matvec(A2, x, y2, prec=dtype)
+            torch.cuda.synchronize()
+            assert torch.equal(y1, y2)
+        finally:
+            hm.hm_free(A2)
+    finally:
+        g.close()
