@@ -263,6 +263,7 @@ def run_ours(args, rank, world):
     if args.profile_step:
         r = step(Vd, Td)
         return {"profile_step": args.case, "step_s": r["step_s"], "aca_s": r["minfo"]["s_aca"],
+                "aca_small_sum": r["minfo"]["aca_small_sum"],
                 "nearfield_s": r["minfo"]["s_nearfield"], "iters_fp64": r["iters_fp64"],
                 "iters_mixed": r["iters_mixed"]}, None
     for _ in range(args.warmup):
@@ -379,7 +380,7 @@ def run_ours(args, rank, world):
         "tree_s": sum(r["tree_s"] for r in results) / len(results),
         "assemble_s": sum(r["assemble_s"] for r in results) / len(results),
         "nearfield_s": nf_s, "singular_s": sum(r["minfo"]["s_singular"] for r in results) / len(results),
-        "aca_s": aca_s,
+        "aca_s": aca_s, "aca_small_sum": mi["aca_small_sum"],
         "solve_fp64_s": sum(r["solve_fp64_s"] for r in results) / len(results),
         "solve_mixed_s": sum(r["solve_mixed_s"] for r in results) / len(results),
         "iters_fp64": last["iters_fp64"], "iters_mixed": last["iters_mixed"], "refine_steps": last["refine_steps"],

@@ -80,7 +80,11 @@ def test_forest_products_and_load_vectors(orc, forest):
         alone = GpuH(V, T, leaf=64, eta=1.5, eps=1e-6, factor_dtype=2, dense_dtype=1)
         try:
             ya = alone.matvec(x[sl])
-            assert np.linalg.norm(y[sl] - ya) <= 1e-14 * np.linalg.norm(ya)
+            # the same blocks, but each assembly tunes its own worker split:
+            # a block that one ACA runs on a CTA worker (double-float
+            # residuals) and the other on a warp worker (FP64 residuals) gets
+            # factors that differ by rounding, ~1e-14 relative
+            assert np.linalg.norm(y[sl] - ya) <= 1e-12 * np.linalg.norm(ya)
         finally:
             alone.close()
 
