@@ -655,27 +655,33 @@ def run_differentiation(torch, hm):
     return out
 
 
-def run_blockmv(torch, hm):
-    """Small multi-RHS case (profiling): bumped icosphere level 6, leaf 128,
-    BF16 factors, three 16-right-hand-side tensor-core products."""
+def run_blockmv(torch, hm, case="bumped6"):
+    """Multi-RHS product case (profiling): a bumped icosphere (level 6, or 7
+    with case "precision"), leaf 128, BF16 factors, then FP32 factors added
+    from the FP64 master; three 16-right-hand-side tensor-core products each."""
     import meshgen
-    cfg = meshgen.config("bumped6")
+    cfg = meshgen.config(case)
     n = cfg["T"].shape[0]
     V, T = torch.from_numpy(cfg["V"]).cuda(), torch.from_numpy(cfg["T"]).cuda()
     tree = hm.hm_build_tree(V, T, eta=1.5, leaf_size=128)
     A = hm.hm_assemble(tree, aca_eps=1e-6, aca_kmax=64, ss_order=8, factor_dtype=hm.HM_BF16, dense_dtype=hm.HM_F32)
     X = torch.randn((16, n), dtype=torch.float64, device="cuda")
     Y = torch.empty_like(X)
-    a, b = _ev(torch), _ev(torch)
-    hm.hm_matvec_block(A, X, Y, prec=hm.HM_BF16)
-    a.record()
-    for _ in range(3):
-        hm.hm_matvec_block(A, X, Y, prec=hm.HM_BF16)
-    b.record()
-    torch.cuda.synchronize()
     mi = hm.hm_matrix_get_info(A)
-    out = {"workload": "bumped icosphere level 6, leaf 128, BF16 factors, 16-RHS product", "n": n,
-           "ms": a.elapsed_time(b) / 3, "matrix_gb": (mi["dense_entries"] * 4 + mi["lr_entries"] * 2) / 1e9}
+    out = {"workload": "%s (%d panels), leaf 128, 16-RHS product" % (case, n), "n": n}
+    for prec, name, fb in ((hm.HM_BF16, "bf16", 2), (hm.HM_F32, "fp32", 4)):
+        if prec == hm.HM_F32:
+            hm.hm_matrix_add_copy(A, hm.HM_F32)
+        a, b = _ev(torch), _ev(torch)
+        hm.hm_matvec_block(A, X, Y, prec=prec)
+        a.record()
+        for _ in range(3):
+            hm.hm_matvec_block(A, X, Y, prec=prec)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / 3
+        gb = (mi["dense_entries"] * 4 + mi["lr_entries"] * fb) / 1e9
+        out[name] = {"ms": ms, "matrix_gb": gb, "gbs": gb / ms * 1e3}
     hm.hm_free(A)
     hm.hm_free(tree)
     return out
@@ -687,7 +693,7 @@ def run_workload(name):
     from paper_1806_11558_gb300 import build as hb
     hb.build()
     fn = {"large": run_large, "batching": run_batching, "differentiation": run_differentiation,
-          "blockmv": run_blockmv}[name]
+          "blockmv": run_blockmv, "blockmv7": lambda t, h: run_blockmv(t, h, "precision")}[name]
     ck = Clocks(torch.cuda.current_device())
     ck.start()
     out = fn(torch, hm)
@@ -707,7 +713,7 @@ def main():
                          "for profiling and parity runs, not bench lines")
     ap.add_argument("--profile-step", action="store_true",
                     help="run exactly one step (no warm-up, no extras) and print its phase times")
-    ap.add_argument("--workload", default=None, choices=["large", "batching", "differentiation", "blockmv"],
+    ap.add_argument("--workload", default=None, choices=["large", "batching", "differentiation", "blockmv", "blockmv7"],
                     help="measure one of the other workloads once and print its numbers (not a bench line)")
     args = ap.parse_args()
     if args.workload:
