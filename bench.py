@@ -106,6 +106,10 @@ def algorithmic_work(mi, ti, dense_leaves, n):
     }
 
 
+PAIR_FLOPS = {"nearfield_kernel": FF_FLOPS_PER_PAIR, "aca_kernel": FF_FLOPS_PER_PAIR,
+              "nearfield_kernel.f64": FLOPS_PER_PAIR}
+
+
 def roofline_entry(name, kt, wk, peaks, peak_src):
     bound, amount, unit = wk
     t = kt["ms_per_launch"] / 1e3
@@ -119,10 +123,14 @@ def roofline_entry(name, kt, wk, peaks, peak_src):
     traffic = None
     if tr is not None and _file_sha(tr["source"]) == tr["sha256"]:
         traffic = tr["bytes_per_launch"]
-    return {"kernel": name, "bound": "alu" if bound.startswith("alu") else bound, "achieved": ach, "peak": peak,
-            "unit": u, "frac": ach / peak, "traffic": traffic, "peak_source": src,
-            "algorithmic_" + unit + "s_per_launch": amount, "launch_ms": kt["ms_per_launch"],
-            "launches_per_step": kt["launches_per_step"]}
+    out = {"kernel": name, "bound": "alu" if bound.startswith("alu") else bound, "achieved": ach, "peak": peak,
+           "unit": u, "frac": ach / peak, "traffic": traffic, "peak_source": src,
+           "algorithmic_" + unit + "s_per_launch": amount, "launch_ms": kt["ms_per_launch"],
+           "launches_per_step": kt["launches_per_step"]}
+    if name in PAIR_FLOPS:
+        # entry-evaluation kernels: evaluations of G (one per quadrature-point pair) per second
+        out["kernel_evaluations_per_s"] = amount / PAIR_FLOPS[name] / t
+    return out
 
 
 def _inputs():
