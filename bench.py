@@ -148,8 +148,8 @@ class Clocks:
 
     def __init__(self, gpu_index):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv") if os.path.isdir(
-            os.path.join(ROOT, "gpurun_out")) else "/tmp/hm_clocks.csv"
+        # raw samples (the JSON line carries their summary); HM_BENCH_CLOCKS_CSV keeps them
+        self.path = os.environ.get("HM_BENCH_CLOCKS_CSV", "/tmp/hm_clocks_%d.csv" % os.getpid())
         self.gpu = gpu_index
 
     def start(self):
