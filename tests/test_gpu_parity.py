@@ -266,3 +266,26 @@ def test_kappa_estimate_from_hessenberg(orc):
         assert 1.0 <= ip.kappa_est < kappa
     finally:
         g.close()
+
+
+def test_wide_leaves_use_the_fp64_fallbacks(orc):
+    # 1,016 panels with leaf 254: leaf clusters of 254 panels, wider than the
+    # float-pair staging box (250) and the shared-memory block inversion
+    # (232), so the FP64 near-field kernel and the FP64 global-memory
+    # block-Jacobi inversion run; both against the oracle
+    need_gpu()
+    V, T = meshgen.icosphere(3)
+    T = np.ascontiguousarray(T[:1016])
+    g = GpuH(V, T, leaf=254, eta=1.5, eps=1e-10, kmax=128)
+    try:
+        assert g.info()["max_leaf"] == 254
+        A = orc.dense_matrix(V, T)
+        worst_reg, worst_sing, _, _ = _nearfield_errors(orc, g, A)
+        assert worst_reg < 1e-13 and worst_sing < 1e-12, (worst_reg, worst_sing)
+        b = g.load_vector(np.array([[3.0, 0.0, 0.0]]))[0]
+        x, info = g.solve(b, rel_tol=1e-12, restart=60, precond=1, max_iter=2000)
+        assert info.status == 0
+        x_lu = np.linalg.solve(A, b)
+        assert np.linalg.norm(x - x_lu) <= 1e-7 * np.linalg.norm(x_lu)
+    finally:
+        g.close()
