@@ -303,7 +303,9 @@ __global__ void bj_invert_kernel(const int32_t *begin, const int64_t *bj_off, do
     __shared__ double s_piv;
     for (int p = 0; p < m; ++p) {
         if (threadIdx.x == 0) {
-            s_piv = 1.0 / D[p * m + p];
+            double d = D[p * m + p];
+            if (!(fabs(d) > 0.0) || !isfinite(d)) d = 1.0;  // empty near-field diagonal (see the FP32 kernel)
+            s_piv = 1.0 / d;
             D[p * m + p] = 1.0;
         }
         __syncthreads();
@@ -353,8 +355,18 @@ __global__ void __launch_bounds__(BJ_INV_THREADS) bj_invert_smem_kernel(const in
     constexpr int NB = (BJ_SMEM_M + 31) / 32;  // columns per thread
     for (int p = 0; p < m; ++p) {
         // pivot, the scaled pivot row and the pivot column, both 0 at p so
-        // that the rank-1 update leaves row and column p alone
-        if (threadIdx.x == 0) s_piv = 1.0f / s_D[p * m + p];
+        // that the rank-1 update leaves row and column p alone.  A zero (or
+        // non-finite) pivot is replaced by 1: a degenerate tree can make a
+        // diagonal block admissible (one-panel clusters are at distance 0),
+        // leaving its near-field part empty; the preconditioner then acts as
+        // the identity there, which right preconditioning tolerates (the
+        // residual and the stopping test are those of the unpreconditioned
+        // system)
+        if (threadIdx.x == 0) {
+            float d = s_D[p * m + p];
+            if (!(fabsf(d) > 0.0f) || !isfinite(d)) d = s_D[p * m + p] = 1.0f;
+            s_piv = 1.0f / d;
+        }
         __syncthreads();
         const float piv = s_piv;
         for (int j = threadIdx.x; j < m; j += BJ_INV_THREADS) {

@@ -235,12 +235,26 @@ def test_degenerate_meshes(orc, case):
     else:
         V, T = meshgen.icosphere(2)
         T = np.ascontiguousarray(T[:37])
-    g = GpuH(V, T, leaf=4, eta=1.5, eps=1e-10)
+    g = GpuH(V, T, leaf=4, eta=1.5, eps=1e-10, factor_dtype=1, dense_dtype=1)
     try:
         A = orc.dense_matrix(V, T)
         x = np.linspace(1.0, 2.0, T.shape[0])
         y = g.matvec(x)
         assert np.linalg.norm(y - A @ x) <= 1e-9 * np.linalg.norm(A @ x)
+        # preconditioned solve in its graph form, and the 16-right-hand-side
+        # product, on the same degenerate trees
+        xs, info = g.solve(A @ x, rel_tol=1e-12, restart=30, precond=1, use_graph=1, max_iter=500)
+        assert info.status == 0
+        assert np.linalg.norm(xs - x) <= 1e-8 * np.linalg.norm(x)
+        torch = g.torch
+        X = np.stack([x, x[::-1].copy(), np.ones_like(x)])
+        Xd = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+        Yd = torch.empty_like(Xd)
+        g.hm.hm_matvec_block(g.A, Xd, Yd, prec=1)
+        torch.cuda.synchronize()
+        Y = Yd.cpu().numpy()
+        for r in range(3):
+            assert np.linalg.norm(Y[r] - A @ X[r]) <= 1e-4 * np.linalg.norm(A @ X[r])
     finally:
         g.close()
 
