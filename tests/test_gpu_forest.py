@@ -113,3 +113,63 @@ def test_forest_batched_solve(forest):
                 assert np.linalg.norm(res) <= 1.01e-10 * np.linalg.norm(Fh[r, sl])
         finally:
             alone.close()
+
+
+def test_forest_with_tiny_geometries(orc):
+    # geometries of 1, 2 and 37 panels beside a full icosphere: degenerate
+    # trees (one-panel clusters, admissible diagonal blocks) inside one
+    # forest; products against the dense oracle per geometry, and the batched
+    # preconditioned, refined, graph-driven solve against it too
+    torch = need_gpu()
+    import paper_1806_11558_gb300 as hm
+    Vi, Ti = meshgen.icosphere(2)
+    parts = [
+        (np.array([[0.0, 0, 0], [1, 0, 0], [0, 1, 0]]), np.array([[0, 1, 2]], dtype=np.int32)),
+        (np.array([[0.0, 0, 0], [1, 0, 0], [0, 1, 0], [1, 1, 0.3]]), np.array([[0, 1, 2], [2, 1, 3]], dtype=np.int32)),
+        (Vi, np.ascontiguousarray(Ti[:37])),
+        (Vi * 1.3, Ti),
+    ]
+    Vs, Ts, off, nv = [], [], [0], 0
+    for V, T in parts:
+        Vs.append(V)
+        Ts.append(T + nv)
+        nv += V.shape[0]
+        off.append(off[-1] + T.shape[0])
+    V, T = np.concatenate(Vs), np.ascontiguousarray(np.concatenate(Ts).astype(np.int32))
+    n = T.shape[0]
+    Vd, Td = torch.from_numpy(V).cuda(), torch.from_numpy(T).cuda()
+    tree = hm.hm_build_forest(Vd, Td, off, eta=1.5, leaf_size=4)
+    A = hm.hm_assemble(tree, aca_eps=1e-10, aca_kmax=64, ss_order=8, factor_dtype=1, dense_dtype=1)
+    try:
+        rng = np.random.default_rng(8)
+        x = rng.standard_normal(n)
+        xd = torch.from_numpy(x).cuda()
+        y = torch.empty_like(xd)
+        hm.hm_matvec(A, xd, y, prec=0)
+        torch.cuda.synchronize()
+        y = y.cpu().numpy()
+        dens = []
+        for g, (Vg, Tg) in enumerate(parts):
+            Ag = orc.dense_matrix(Vg, Tg)
+            dens.append(Ag)
+            sl = slice(off[g], off[g + 1])
+            assert np.linalg.norm(y[sl] - Ag @ x[sl]) <= 1e-8 * np.linalg.norm(Ag @ x[sl])
+        # two right-hand sides: systems of every geometry in lockstep
+        X = np.stack([x, np.ones(n)])
+        B = np.zeros_like(X)
+        for g in range(len(parts)):
+            sl = slice(off[g], off[g + 1])
+            for r in range(2):
+                B[r, sl] = dens[g] @ X[r, sl]
+        Bd = torch.from_numpy(np.ascontiguousarray(B)).cuda()
+        Xd = torch.zeros_like(Bd)
+        info = hm.hm_solve(A, Bd, Xd, rel_tol=1e-12, restart=40, max_iter=3000, precond=1, batched=1, refine=1,
+                           inner_dtype=1, inner_tol=1e-4, max_refine=40, use_graph=1)
+        torch.cuda.synchronize()
+        assert info.status == 0
+        Xs = Xd.cpu().numpy()
+        for r in range(2):
+            assert np.linalg.norm(Xs[r] - X[r]) <= 1e-7 * np.linalg.norm(X[r])
+    finally:
+        hm.hm_free(A)
+        hm.hm_free(tree)
