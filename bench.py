@@ -61,8 +61,8 @@ FF_FLOPS_PER_PAIR = 93
 # file is unchanged (sha256 of the file at capture time); null otherwise.
 TRAFFIC = {
     "row_kernel.f64": {"source": "paper_1806_11558_gb300/csrc/mv_kernels.cuh",
-                       "sha256": "70701a252b20d346dcc90698b9f62f416efe2c775bf76cafecdbce7512461e06",
-                       "bytes_per_launch": 14.84e9 + 5.64e6,
+                       "sha256": "436a88d6045d91ce1d484dc204a6a290645be08fafb1c4e852197761fc18c3bb",
+                       "bytes_per_launch": 15109876224 + 5918208,
                        "profile": "profiles/row_kernel_f64_precision.md"},
 }
 

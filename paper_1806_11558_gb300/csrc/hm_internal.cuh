@@ -325,6 +325,8 @@ struct hm_matrix {
     hm_assemble_params params{};
     hm::DBuf dense;     // near-field row panels, double
     hm::DBuf dense32;   // optional FP32 copy
+    hm::DBuf mv_order;  // [4][n_leaf] int32: leaf clusters by decreasing panel work
+                        // (row / column kernel, forward; row / column kernel, transposed)
     hm::DBuf rank;      // [n_adm] int32
     hm::DBuf t_off;     // [n_adm] int64, prefix sum of ranks
     int64_t total_rank = 0;

@@ -14,6 +14,7 @@
 // copies with FP32 accumulation.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "hm_internal.cuh"
@@ -247,6 +248,29 @@ void build_lr_panels(hm_matrix *A, const DBuf &uw, const DBuf &uw_off, cudaStrea
             HM_LAUNCH_CHECK();
         }
     }
+    // dispatch orders of the product's kernels: leaf clusters by decreasing
+    // work (rows x panel width; ties by index), forward and transposed
+    if (nl > 0) {
+        std::vector<int32_t> lb(nl + 1), kd(nl), ku(nl), kw(nl);
+        HM_CUDA_CHECK(cudaMemcpyAsync(lb.data(), tr->leaf_begin.p, sizeof(int32_t) * (nl + 1), cudaMemcpyDeviceToHost, s));
+        HM_CUDA_CHECK(cudaMemcpyAsync(kd.data(), tr->rho_K.p, sizeof(int32_t) * nl, cudaMemcpyDeviceToHost, s));
+        HM_CUDA_CHECK(cudaMemcpyAsync(ku.data(), A->up_K.p, sizeof(int32_t) * nl, cudaMemcpyDeviceToHost, s));
+        HM_CUDA_CHECK(cudaMemcpyAsync(kw.data(), A->wp_K.p, sizeof(int32_t) * nl, cudaMemcpyDeviceToHost, s));
+        HM_CUDA_CHECK(cudaStreamSynchronize(s));
+        std::vector<int32_t> ord(4 * nl);
+        auto by_work = [&](int32_t *o, auto work) {
+            for (int64_t r = 0; r < nl; ++r) o[r] = (int32_t)r;
+            std::stable_sort(o, o + nl, [&](int32_t a, int32_t b) { return work(a) > work(b); });
+        };
+        auto rows = [&](int32_t r) { return (int64_t)(lb[r + 1] - lb[r]); };
+        by_work(ord.data(), [&](int32_t r) { return rows(r) * ((int64_t)kd[r] + ku[r]); });
+        by_work(ord.data() + nl, [&](int32_t r) { return rows(r) * (int64_t)kw[r]; });
+        by_work(ord.data() + 2 * nl, [&](int32_t r) { return rows(r) * ((int64_t)kd[r] + kw[r]); });
+        by_work(ord.data() + 3 * nl, [&](int32_t r) { return rows(r) * (int64_t)ku[r]; });
+        A->mv_order.alloc(sizeof(int32_t) * 4 * nl);
+        HM_CUDA_CHECK(cudaMemcpyAsync(A->mv_order.p, ord.data(), sizeof(int32_t) * 4 * nl, cudaMemcpyHostToDevice, s));
+        HM_CUDA_CHECK(cudaStreamSynchronize(s));
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -400,17 +424,22 @@ struct MvDir {
     const int64_t *bptr, *pofs;
     const int64_t *exp_off, *exp_ptr;
     const int32_t *exp_K, *exp_tidx;
+    const int32_t *row_order, *col_order;
 };
 
 static MvDir mv_dir(const hm_matrix *A, bool trans) {
     const hm_tree *tr = A->tree;
+    const int32_t *ord = A->mv_order.as<int32_t>();
+    const int64_t nl = tr->n_leaf;
     if (!trans)
         return MvDir{A->wp_off.as<int64_t>(), A->wp_colptr.as<int64_t>(), A->wp_K.as<int32_t>(),
                      tr->lr_bcolptr.as<int64_t>(), A->pofs.as<int64_t>(), A->up_off.as<int64_t>(),
-                     A->up_colptr.as<int64_t>(), A->up_K.as<int32_t>(), A->tidx.as<int32_t>()};
+                     A->up_colptr.as<int64_t>(), A->up_K.as<int32_t>(), A->tidx.as<int32_t>(),
+                     ord ? ord : nullptr, ord ? ord + nl : nullptr};
     return MvDir{A->up_off.as<int64_t>(), A->up_colptr.as<int64_t>(), A->up_K.as<int32_t>(),
                  tr->lr_browptr.as<int64_t>(), A->pofs_t.as<int64_t>(), A->wp_off.as<int64_t>(),
-                 A->wp_colptr.as<int64_t>(), A->wp_K.as<int32_t>(), A->tidx_t.as<int32_t>()};
+                 A->wp_colptr.as<int64_t>(), A->wp_K.as<int32_t>(), A->tidx_t.as<int32_t>(),
+                 ord ? ord + 2 * nl : nullptr, ord ? ord + 3 * nl : nullptr};
 }
 
 template <class TD, class TF, class TX, class TT>
@@ -420,7 +449,8 @@ static void matvec_impl(const hm_matrix *A, const TD *dense, const TF *proj, con
     if (tr->n_adm > 0) {
         Trace tr_col(nm.col, s);
         col_kernel<TF, TX, TT><<<(unsigned)tr->n_leaf, COL_THREADS, 0, s>>>(tr->leaf_begin.as<int32_t>(), d.proj_off,
-                                                                            d.proj_K, d.proj_ptr, proj, x, p);
+                                                                            d.proj_K, d.proj_ptr, proj, x, p,
+                                                                            d.col_order);
         HM_LAUNCH_CHECK();
     }
     if (tr->n_adm > 0) {
@@ -429,6 +459,10 @@ static void matvec_impl(const hm_matrix *A, const TD *dense, const TF *proj, con
             tr->n_adm, A->total_rank, A->tsum_b0.as<int32_t>(), A->t_off.as<int64_t>(), d.bptr, d.pofs, p, t);
         HM_LAUNCH_CHECK();
     }
+    // the FP64 row kernel (FP64-pipe-bound) runs its clusters largest first;
+    // the FP32 / BF16 one (HBM-bound) keeps the Morton order, whose
+    // neighbouring clusters share their gathered x and t in L2 (measured:
+    // largest-first 3.50 -> 3.28 ms in FP64, 1.24 -> 1.33 ms in FP32)
     auto kern = row_kernel<12, TD, TF, TX, TT>;
     switch (row_rb_for(tr->max_leaf)) {
         case 4: kern = row_kernel<4, TD, TF, TX, TT>; break;
@@ -440,7 +474,7 @@ static void matvec_impl(const hm_matrix *A, const TD *dense, const TF *proj, con
     kern<<<(unsigned)tr->n_leaf, ROW_THREADS, 0, s>>>(
         tr->leaf_begin.as<int32_t>(), tr->rho_off.as<int64_t>(), tr->rho_K.as<int32_t>(),
         tr->rho_colptr.as<int64_t>(), tr->colidx.as<int32_t>(), dense, d.exp_off, d.exp_K, d.exp_ptr, d.exp_tidx,
-        expd, t, x, ym);
+        expd, t, x, ym, sizeof(TD) == 8 ? d.row_order : nullptr);
     HM_LAUNCH_CHECK();
 }
 

@@ -107,11 +107,11 @@ __global__ void __launch_bounds__(COL_THREADS) col_kernel(const int32_t *__restr
                                                           const int32_t *__restrict__ wp_K,
                                                           const int64_t *__restrict__ wp_colptr,
                                                           const TF *__restrict__ wp, const TX *__restrict__ x,
-                                                          TP *__restrict__ p) {
+                                                          TP *__restrict__ p, const int32_t *__restrict__ order) {
     using A = typename Acc<TF>::type;
     constexpr int N = V16<TF>::N;
     __shared__ A s_x[MAX_LEAF];
-    const int64_t kap = blockIdx.x;
+    const int64_t kap = order ? order[blockIdx.x] : blockIdx.x;  // largest panels first
     const int32_t c0 = leaf_begin[kap], mc = leaf_begin[kap + 1] - c0;
     for (int j = threadIdx.x; j < mc; j += COL_THREADS) s_x[j] = (A)x[c0 + j];
     __syncthreads();
@@ -217,7 +217,9 @@ __global__ void tsum_b0_kernel(int64_t na, const int64_t *__restrict__ t_off, in
 }
 
 // ---------------------------------------------------------------------------
-// y_rho = P_rho x(colidx) + Ut_rho t(tidx): one CTA per leaf row cluster.
+// y_rho = P_rho x(colidx) + Ut_rho t(tidx): one CTA per leaf row cluster,
+// dispatched in decreasing order of panel work (`order`), so the longest
+// CTAs start first and the last wave is made of short ones.
 // Every row of a panel multiplies the same gathered vector, so the CTA
 // gathers it once per column chunk into shared memory; then each warp takes
 // RB rows at a time and streams them with 16-byte loads against the staged
@@ -280,11 +282,11 @@ __global__ void __launch_bounds__(ROW_THREADS) row_kernel(
     const int64_t *__restrict__ rho_colptr, const int32_t *__restrict__ colidx, const TD *__restrict__ dense,
     const int64_t *__restrict__ up_off, const int32_t *__restrict__ up_K, const int64_t *__restrict__ up_colptr,
     const int32_t *__restrict__ tidx, const TF *__restrict__ up, const TT *__restrict__ t, const TX *__restrict__ x,
-    double *__restrict__ ym) {
+    double *__restrict__ ym, const int32_t *__restrict__ order) {
     using AD = typename Acc<TD>::type;
     using AF = typename Acc<TF>::type;
     __shared__ __align__(16) unsigned char s_raw[ROW_CHUNK * sizeof(AD)];
-    const int64_t rho = blockIdx.x;
+    const int64_t rho = order ? order[blockIdx.x] : blockIdx.x;  // largest panels first
     const int32_t r0 = leaf_begin[rho], r1 = leaf_begin[rho + 1];
     const int mr = r1 - r0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
