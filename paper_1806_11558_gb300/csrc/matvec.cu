@@ -463,18 +463,19 @@ static void matvec_impl(const hm_matrix *A, const TD *dense, const TF *proj, con
     // the FP32 / BF16 one (HBM-bound) keeps the Morton order, whose
     // neighbouring clusters share their gathered x and t in L2 (measured:
     // largest-first 3.50 -> 3.28 ms in FP64, 1.24 -> 1.33 ms in FP32)
-    auto kern = row_kernel<12, TD, TF, TX, TT>;
+    constexpr bool ORD = sizeof(TD) == 8;
+    auto kern = row_kernel<12, TD, TF, TX, TT, ORD>;
     switch (row_rb_for(tr->max_leaf)) {
-        case 4: kern = row_kernel<4, TD, TF, TX, TT>; break;
-        case 5: kern = row_kernel<5, TD, TF, TX, TT>; break;
-        case 8: kern = row_kernel<8, TD, TF, TX, TT>; break;
+        case 4: kern = row_kernel<4, TD, TF, TX, TT, ORD>; break;
+        case 5: kern = row_kernel<5, TD, TF, TX, TT, ORD>; break;
+        case 8: kern = row_kernel<8, TD, TF, TX, TT, ORD>; break;
         default: break;
     }
     Trace tr_row(nm.row, s);
     kern<<<(unsigned)tr->n_leaf, ROW_THREADS, 0, s>>>(
         tr->leaf_begin.as<int32_t>(), tr->rho_off.as<int64_t>(), tr->rho_K.as<int32_t>(),
         tr->rho_colptr.as<int64_t>(), tr->colidx.as<int32_t>(), dense, d.exp_off, d.exp_K, d.exp_ptr, d.exp_tidx,
-        expd, t, x, ym, sizeof(TD) == 8 ? d.row_order : nullptr);
+        expd, t, x, ym, d.row_order);
     HM_LAUNCH_CHECK();
 }
 

@@ -276,7 +276,7 @@ __device__ __forceinline__ void panel_rows(const T *__restrict__ P, int L, const
     }
 }
 
-template <int RB, class TD, class TF, class TX, class TT>
+template <int RB, class TD, class TF, class TX, class TT, bool ORD>
 __global__ void __launch_bounds__(ROW_THREADS) row_kernel(
     const int32_t *__restrict__ leaf_begin, const int64_t *__restrict__ rho_off, const int32_t *__restrict__ rho_K,
     const int64_t *__restrict__ rho_colptr, const int32_t *__restrict__ colidx, const TD *__restrict__ dense,
@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(ROW_THREADS) row_kernel(
     using AD = typename Acc<TD>::type;
     using AF = typename Acc<TF>::type;
     __shared__ __align__(16) unsigned char s_raw[ROW_CHUNK * sizeof(AD)];
-    const int64_t rho = order ? order[blockIdx.x] : blockIdx.x;  // largest panels first
+    const int64_t rho = ORD ? order[blockIdx.x] : blockIdx.x;  // largest panels first (ORD)
     const int32_t r0 = leaf_begin[rho], r1 = leaf_begin[rho + 1];
     const int mr = r1 - r0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
