@@ -61,8 +61,8 @@ FF_FLOPS_PER_PAIR = 93
 # file is unchanged (sha256 of the file at capture time); null otherwise.
 TRAFFIC = {
     "row_kernel.f64": {"source": "paper_1806_11558_gb300/csrc/mv_kernels.cuh",
-                       "sha256": "436a88d6045d91ce1d484dc204a6a290645be08fafb1c4e852197761fc18c3bb",
-                       "bytes_per_launch": 15109876224 + 5918208,
+                       "sha256": "317d8d2539db41cb43c4abddd08fe283fb2cbbf21bc763087ebc67cdb6960454",
+                       "bytes_per_launch": 15113751808 + 5691392,
                        "profile": "profiles/row_kernel_f64_precision.md"},
 }
 
