@@ -1,0 +1,62 @@
+"""Host-side arithmetic of bench.py's roofline objects: the per-kernel table
+of the trace, the algorithmic work per launch of each product kernel, and
+the achieved / peak fractions (no GPU involved)."""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_kernel_table_orders_and_normalises():
+    trace = {"a": (10, 30.0), "b": (4, 10.0), "c": (1, 60.0)}
+    kt = bench.kernel_table(trace, 2)
+    assert list(kt) == ["c", "a", "b"]
+    assert kt["a"]["launches_per_step"] == 5 and kt["a"]["ms_per_step"] == 15.0
+    assert kt["a"]["ms_per_launch"] == 3.0
+    assert abs(sum(v["share_of_traced"] for v in kt.values()) - 1.0) < 1e-12
+
+
+def _work():
+    # two dense leaves (one mirrored pair: only the upper one is evaluated)
+    # and made-up matrix sizes
+    mi = {"u_entries": 1000, "lr_entries": 2500, "dense_entries": 800, "mean_rank": 2.0, "aca_entries": 3000}
+    ti = {"n_adm": 10, "n_clusters": 15}
+    leaves = np.array([[0, 20, 20, 40], [20, 40, 0, 20]], dtype=np.int64)
+    return bench.algorithmic_work(mi, ti, leaves, 40)
+
+
+def test_algorithmic_work_counts():
+    w = _work()
+    # FP64 product: 2 flops per stored entry
+    assert w["row_kernel.f64"] == ("alu", 2.0 * (800 + 1000), "flop")
+    assert w["col_kernel.f64"] == ("alu", 2.0 * 1500, "flop")
+    # FP32 row kernel: 4 B per entry + 4 B per gathered x / t value + 8 B per y
+    K = 2.0 * 10
+    assert w["row_kernel.f32"][1] == 4.0 * 1800 + 4.0 * (40 + K) + 8.0 * 40
+    # entry evaluations: one per upper dense entry, 49 pairs each
+    assert w["nearfield_kernel"][1] == 20 * 20 * bench.PAIRS_PER_ENTRY * bench.FF_FLOPS_PER_PAIR
+    assert w["nearfield_kernel.f64"][1] == 20 * 20 * bench.PAIRS_PER_ENTRY * bench.FLOPS_PER_PAIR
+    assert w["aca_kernel"][1] == 3000 * bench.PAIRS_PER_ENTRY * bench.FF_FLOPS_PER_PAIR
+
+
+def test_roofline_entry_fractions():
+    w = _work()
+    peaks = {"hbm_gbs": 6000.0}
+    kt = {"ms_per_launch": 2.0, "launches_per_step": 3.0}
+    r = bench.roofline_entry("row_kernel.f32", kt, w["row_kernel.f32"], peaks, "measured")
+    assert r["unit"] == "GB/s" and r["bound"] == "hbm"
+    assert r["achieved"] == pytest.approx(w["row_kernel.f32"][1] / 2e-3 / 1e9)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6000.0)
+    r = bench.roofline_entry("row_kernel.f64", kt, w["row_kernel.f64"], peaks, "measured")
+    assert r["bound"] == "alu" and r["peak"] == bench.FP64_PEAK_TFLOPS
+    # traffic only while the kernel source matches the recorded capture
+    assert r["traffic"] == bench.TRAFFIC["row_kernel.f64"]["bytes_per_launch"]
+    r = bench.roofline_entry("aca_kernel", kt, w["aca_kernel"], peaks, "measured")
+    assert r["peak"] == bench.FP32_PEAK_TFLOPS
+    assert r["kernel_evaluations_per_s"] == pytest.approx(3000 * bench.PAIRS_PER_ENTRY / 2e-3)
