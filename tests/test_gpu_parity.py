@@ -303,3 +303,30 @@ def test_wide_leaves_use_the_fp64_fallbacks(orc):
         assert np.linalg.norm(x - x_lu) <= 1e-7 * np.linalg.norm(x_lu)
     finally:
         g.close()
+
+
+def test_c1_approximation_error_scales_with_kappa_eps(orc):
+    # the small workload (unit icosphere level 4, 5,120 panels) at
+    # eps = 1e-6: the H-matrix solution differs from the dense LU one by
+    # about kappa * eps (kappa from the oracle's exact eigenvalues); at
+    # eps = 1e-12 with k_max 128 it reaches the LU solution within 1e-8
+    need_gpu()
+    V, T = meshgen.icosphere(4)
+    A = orc.dense_matrix(V, T)
+    ev = np.linalg.eigvalsh(0.5 * (A + A.T))
+    kappa = ev[-1] / ev[0]
+    f = orc.load_vector(V, T, [3.0, 0.0, 0.0])[0]
+    x_lu = orc.lu_solve(A, f)
+    errs = {}
+    for eps, kmax in ((1e-6, 64), (1e-12, 128)):
+        g = GpuH(V, T, leaf=64, eta=1.5, eps=eps, kmax=kmax)
+        try:
+            x, info = g.solve(f, rel_tol=1e-13, restart=30, max_iter=5000)
+            assert info.status == 0
+            errs[eps] = np.linalg.norm(x - x_lu) / np.linalg.norm(x_lu)
+        finally:
+            g.close()
+    print("C1: kappa %.1f, |x_H - x_LU| / |x_LU| = %.2e at eps 1e-6 (kappa eps = %.1e), %.2e at eps 1e-12"
+          % (kappa, errs[1e-6], kappa * 1e-6, errs[1e-12]))
+    assert errs[1e-6] <= 10 * kappa * 1e-6
+    assert errs[1e-12] < 1e-8
