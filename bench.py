@@ -1,17 +1,23 @@
 """Benchmark of the H-matrix BEM hot path on one GB300 (or N replicas).
 
-A step is one pass of the whole path over one synthetic problem:
-Morton tree + block tree, near-field assembly, batched ACA, load vector,
-FP64 GMRES solve and the FP32-factor / FP64-refinement solve.
-Workload: bumped icosphere level 7 (327,680 flat triangles, 8 seeded real
-spherical harmonics l <= 4, amplitude 0.1), point source p = (3, 0, 0),
-C_leaf = 64, eta = 1.5, ACA eps = 1e-7, FP64 master with FP32 copies,
-solves to a relative residual of 1e-12 (1e-8 relative solution accuracy).
+Headline workload (default, `--case large`): the unit icosphere of level 8,
+1,310,720 flat triangles = 1,310,720 piecewise-constant unknowns, C_leaf = 128,
+eta = 1.5, ACA eps = 1e-6, 16 seeded exterior point sources (|p| in [2, 4]).
+A step is one pass of the whole path: Morton tree + block tree, near field,
+batched ACA (with the FP32 copies of near field and factors), the 16 load
+vectors, and the mixed-precision solve of the 16 systems -- lockstep GMRES
+whose inner solves run on the FP32 copies through the 16-right-hand-side
+tensor-core product, FP64 iterative refinement to a relative residual of
+1e-12 (1e-8 relative solution accuracy).
 
-`value` is seconds per step (lower is better); the JSON line also carries the
-per-phase seconds, H-matvec GB/s, the error of the mixed-precision solution
-against the FP64 one, the roofline of the dominant kernel and the CPU oracle
-timed on a bounded sample of the same workload.
+Beside it, in the same run and outside the timed steps: the all-FP64 solve
+of the same 16 systems on the last step's matrix (timed once, it takes about a
+minute), the BF16-factor form, the H-matvec GB/s (one and 16 right-hand
+sides), the error of every mixed solution against the FP64 one, the measured
+FMA peaks, and the precision workload (bumped icosphere of level 7, 327,680
+panels, one source, FP64 solve + FP32-refined solve) as a secondary object.
+
+`value` is seconds per step (lower is better).
 """
 from __future__ import annotations
 
@@ -28,14 +34,22 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = dict(workload="bumped icosphere level 7, Galerkin single-layer Laplace, P0",
-                panels=327680, leaf_size=64, eta=1.5, aca_eps=1e-7, aca_kmax=64, ss_order=8,
-                source=[3.0, 0.0, 0.0], solve_rel_tol=1e-12, inner="fp32 factors + fp32 near field",
-                inner_tol=1e-4, restart=int(os.environ.get("HM_BENCH_RESTART", "128")), precond=os.environ.get("HM_BENCH_PRECOND", "1") == "1",
-                use_graph=os.environ.get("HM_BENCH_GRAPH", "0") == "1")
 METRIC = "H-matrix setup s, H-matvec GB/s, solve s at 1e-8 rel. accuracy: mixed vs FP64"
+
+# the two bench workloads (the other meshgen recipes are profiling / parity cases)
+LARGE = dict(workload="unit icosphere level 8, Galerkin single-layer Laplace, P0, 16 point sources",
+             case="large", panels=1310720, leaf_size=128, eta=1.5, aca_eps=1e-6, aca_kmax=64, ss_order=8,
+             nrhs=16, sources="16 seeded exterior point sources, |p| uniform in [2, 4]", solve_rel_tol=1e-12,
+             form="mixed: FP32 near field + FP32 factors; lockstep GMRES whose inner solves use the 16-RHS "
+                  "tensor-core product; FP64 iterative refinement",
+             inner_tol=1e-4, restart=128, precond=True, batched=True)
+PRECISION = dict(workload="bumped icosphere level 7, Galerkin single-layer Laplace, P0",
+                 case="precision", panels=327680, leaf_size=64, eta=1.5, aca_eps=1e-7, aca_kmax=64, ss_order=8,
+                 nrhs=1, source=[3.0, 0.0, 0.0], solve_rel_tol=1e-12, inner="fp32 factors + fp32 near field",
+                 inner_tol=1e-4, restart=128, precond=True, use_graph=False)
 FLOPS_PER_PAIR = 11  # 3 sub + 3 mul + 2 add (|x-y|^2) + rsqrt + multiply-add (weight)
 PAIRS_PER_ENTRY = 49
+MR = 16  # right-hand sides of one tensor-core pass
 
 
 def _peaks():
@@ -47,10 +61,9 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-CASE = "precision"
-
 # Nominal ALU peaks of GB300 (152 SMs at 2.07 GHz): FP64 2 DFMA / SM / clock,
-# FP32 128 FFMA / SM / clock; FMA = 2 flops.
+# FP32 128 FFMA / SM / clock; FMA = 2 flops.  Used only when no measurement
+# (hm_measure_fma_peak) is passed in.
 FP64_PEAK_TFLOPS = 152 * 2.07e9 * 2 * 2 / 1e12   # 1.26
 FP32_PEAK_TFLOPS = 152 * 2.07e9 * 128 * 2 / 1e12  # 80.5
 # FP32 flops of one pair evaluation in the double-float entry (ACA and the
@@ -63,6 +76,7 @@ TRAFFIC = {
     "row_kernel.f64": {"source": "paper_1806_11558_gb300/csrc/mv_kernels.cuh",
                        "sha256": "317d8d2539db41cb43c4abddd08fe283fb2cbbf21bc763087ebc67cdb6960454",
                        "bytes_per_launch": 15113751808 + 5691392,
+                       "workload": "precision",
                        "profile": "profiles/row_kernel_f64_precision.md"},
 }
 
@@ -93,6 +107,8 @@ def algorithmic_work(mi, ti, dense_leaves, n):
     nf_entries = int(((re_ - rb) * (ce - cb))[rb <= cb].sum())
     K = mi["mean_rank"] * ti["n_adm"]  # sum of ranks = length of t
     nl = (ti["n_clusters"] + 1) // 2  # leaf clusters of the binary cluster tree; partials = sum over them of K_w
+    # 16 right-hand sides: X and t rows as BF16 pairs (16 x 2 x 2 B), Y rows FP64 (16 x 8 B)
+    xr, yr = 4.0 * MR, 8.0 * MR
     return {
         "row_kernel.f64": ("alu", 2.0 * (d + u), "flop"),
         "col_kernel.f64": ("alu", 2.0 * w, "flop"),
@@ -100,6 +116,10 @@ def algorithmic_work(mi, ti, dense_leaves, n):
         "col_kernel.f32": ("hbm", 4.0 * w + 4.0 * n + 4.0 * w * nl / n, "byte"),
         "row_kernel.bf16": ("hbm", 4.0 * d + 2.0 * u + 4.0 * (n + K) + 8.0 * n, "byte"),
         "col_kernel.bf16": ("hbm", 2.0 * w + 4.0 * n + 4.0 * w * nl / n, "byte"),
+        "row_mrhs_kernel.f32": ("hbm", 4.0 * (d + u) + xr * (n + K) + yr * n, "byte"),
+        "row_mrhs_kernel.bf16": ("hbm", 4.0 * d + 2.0 * u + xr * (n + K) + yr * n, "byte"),
+        "col_bcp_kernel.f32": ("hbm", 4.0 * w + xr * (n + K), "byte"),
+        "col_bcp_kernel.bf16": ("hbm", 2.0 * w + xr * (n + K), "byte"),
         "nearfield_kernel": ("alu32", float(nf_entries) * PAIRS_PER_ENTRY * FF_FLOPS_PER_PAIR, "flop"),
         "nearfield_kernel.f64": ("alu", float(nf_entries) * PAIRS_PER_ENTRY * FLOPS_PER_PAIR, "flop"),
         "aca_kernel": ("alu32", float(mi["aca_entries"]) * PAIRS_PER_ENTRY * FF_FLOPS_PER_PAIR, "flop"),
@@ -111,17 +131,28 @@ PAIR_FLOPS = {"nearfield_kernel": FF_FLOPS_PER_PAIR, "aca_kernel": FF_FLOPS_PER_
 
 
 def roofline_entry(name, kt, wk, peaks, peak_src):
+    """Roofline object of one traced kernel.  peaks: hbm_gbs (the driver's
+    copy bandwidth) and, when measured in this run, fp64_tflops / fp32_tflops
+    (hm_measure_fma_peak); the nominal unit-count figures otherwise."""
     bound, amount, unit = wk
     t = kt["ms_per_launch"] / 1e3
     if bound == "hbm":
         ach, peak, u, src = amount / t / 1e9, peaks["hbm_gbs"], "GB/s", peak_src + " HBM copy bandwidth"
     elif bound == "alu":
-        ach, peak, u, src = amount / t / 1e12, FP64_PEAK_TFLOPS, "TFLOP/s", "nominal FP64 (unit counts x clock)"
+        ach, u = amount / t / 1e12, "TFLOP/s"
+        if "fp64_tflops" in peaks:
+            peak, src = peaks["fp64_tflops"], "measured FP64 FMA throughput (hm_measure_fma_peak, this run)"
+        else:
+            peak, src = FP64_PEAK_TFLOPS, "nominal FP64 (unit counts x clock)"
     else:
-        ach, peak, u, src = amount / t / 1e12, FP32_PEAK_TFLOPS, "TFLOP/s", "nominal FP32 (unit counts x clock)"
+        ach, u = amount / t / 1e12, "TFLOP/s"
+        if "fp32_tflops" in peaks:
+            peak, src = peaks["fp32_tflops"], "measured FP32 FMA throughput (hm_measure_fma_peak, this run)"
+        else:
+            peak, src = FP32_PEAK_TFLOPS, "nominal FP32 (unit counts x clock)"
     tr = TRAFFIC.get(name)
     traffic = None
-    if tr is not None and _file_sha(tr["source"]) == tr["sha256"]:
+    if tr is not None and tr.get("workload") == peaks.get("workload") and _file_sha(tr["source"]) == tr["sha256"]:
         traffic = tr["bytes_per_launch"]
     out = {"kernel": name, "bound": "alu" if bound.startswith("alu") else bound, "achieved": ach, "peak": peak,
            "unit": u, "frac": ach / peak, "traffic": traffic, "peak_source": src,
@@ -133,10 +164,20 @@ def roofline_entry(name, kt, wk, peaks, peak_src):
     return out
 
 
-def _inputs():
-    import meshgen
-    cfg = meshgen.config(CASE)
-    return cfg["V"], cfg["T"]
+def rooflines(trace, steps, mi, ti, leaves, n, peaks, peak_src):
+    """(dominant kernel's roofline, the others') from a trace of `steps` steps."""
+    kernels = kernel_table(trace, steps)
+    work = algorithmic_work(mi, ti, leaves, n)
+    dom, others = None, {}
+    for name, kt in kernels.items():
+        if name not in work:
+            continue
+        r = roofline_entry(name, kt, work[name], peaks, peak_src)
+        if dom is None:
+            dom = r
+        else:
+            others[name] = r
+    return dom, others, kernels
 
 
 class Clocks:
@@ -209,59 +250,65 @@ def barrier(world):
         dist.barrier()
 
 
-def run_ours(args, rank, world):
-    import numpy as np
-    import torch
-    import paper_1806_11558_gb300 as hm
-    from paper_1806_11558_gb300 import build as hb
+def _ev(torch):
+    return torch.cuda.Event(enable_timing=True)
 
-    hb.build()
+
+def _mean(rs, key):
+    return sum(r[key] for r in rs) / len(rs)
+
+
+def measured_fma_peaks(hm, torch):
+    """FP64 and FP32 FMA throughput measured now, with the SM clock sampled
+    around the measurement."""
+    ck = Clocks(torch.cuda.current_device())
+    ck.start()
+    f64 = hm.hm_measure_fma_peak(hm.HM_F64)
+    f32 = hm.hm_measure_fma_peak(hm.HM_F32)
+    c = ck.stop()
+    return {"fp64_tflops": f64, "fp32_tflops": f32, "sm_mhz": c.get("sm_mhz"),
+            "how": "hm_measure_fma_peak: every SM full of threads running 8 independent FMA chains each; best of 3 "
+                   "CUDA-event-timed launches"}
+
+
+# ---------------------------------------------------------------------------
+# the headline: level 8, 16 sources, mixed 16-system solve
+# ---------------------------------------------------------------------------
+def run_large(args, world, hm, torch, W=LARGE, case="large"):
+    import meshgen
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
-    torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
-    V, T = _inputs()
+    cfg = meshgen.config(case)
+    V, T = cfg["V"], cfg["T"]
     n = T.shape[0]
+    R = W["nrhs"]
     Vd = torch.from_numpy(V).to(dev)
     Td = torch.from_numpy(T).to(dev)
-    src = torch.tensor([WORKLOAD["source"]], dtype=torch.float64, device=dev)
-    f = torch.empty((1, n), dtype=torch.float64, device=dev)
-    x64 = torch.zeros(n, dtype=torch.float64, device=dev)
-    xmx = torch.zeros(n, dtype=torch.float64, device=dev)
-    W = WORKLOAD
+    srcd = torch.from_numpy(np.ascontiguousarray(cfg["sources"][:R])).to(dev)
+    F = torch.empty((R, n), dtype=torch.float64, device=dev)
+    X = torch.zeros((R, n), dtype=torch.float64, device=dev)
+    opts = dict(rel_tol=W["solve_rel_tol"], restart=W["restart"], max_iter=5000, precond=int(W["precond"]),
+                batched=1)
 
-    def step(Vdev, Tdev, keep=False):
-        t = {}
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    def step(Vdev, Tdev, sdev, keep=False):
+        e = [_ev(torch) for _ in range(5)]
         e[0].record(stream)
         tree = hm.hm_build_tree(Vdev, Tdev, eta=W["eta"], leaf_size=W["leaf_size"])
         e[1].record(stream)
         A = hm.hm_assemble(tree, aca_eps=W["aca_eps"], aca_kmax=W["aca_kmax"], ss_order=W["ss_order"],
                            factor_dtype=hm.HM_F32, dense_dtype=hm.HM_F32)
         e[2].record(stream)
-        hm.hm_load_vector(tree, src, f)
+        hm.hm_load_vector(tree, sdev, F)
         e[3].record(stream)
-        i64 = hm.hm_solve(A, f[0], x64, rel_tol=W["solve_rel_tol"], restart=W["restart"], max_iter=5000,
-                          precond=int(W["precond"]), use_graph=int(W["use_graph"]))
+        info = hm.hm_solve(A, F, X, refine=1, inner_dtype=hm.HM_F32, inner_tol=W["inner_tol"], max_refine=40, **opts)
         e[4].record(stream)
-        imx = hm.hm_solve(A, f[0], xmx, rel_tol=W["solve_rel_tol"], restart=W["restart"], max_iter=5000, refine=1,
-                          inner_tol=W["inner_tol"], inner_dtype=hm.HM_F32, max_refine=50,
-                          precond=int(W["precond"]), use_graph=int(W["use_graph"]))
-        e[5].record(stream)
         torch.cuda.synchronize()
-        t["tree_s"] = e[0].elapsed_time(e[1]) / 1e3
-        t["assemble_s"] = e[1].elapsed_time(e[2]) / 1e3
-        t["load_s"] = e[2].elapsed_time(e[3]) / 1e3
-        t["solve_fp64_s"] = e[3].elapsed_time(e[4]) / 1e3
-        t["solve_mixed_s"] = e[4].elapsed_time(e[5]) / 1e3
-        t["step_s"] = e[0].elapsed_time(e[5]) / 1e3
-        t["minfo"] = hm.hm_matrix_get_info(A)
-        t["tinfo"] = hm.hm_tree_get_info(tree)
-        t["iters_fp64"] = i64.iters
-        t["iters_mixed"] = imx.iters
-        t["refine_steps"] = imx.refine_steps
-        t["resid_fp64"] = i64.rel_resid
-        t["resid_mixed"] = imx.rel_resid
-        t["kappa_est"] = i64.kappa_est
+        mi = hm.hm_matrix_get_info(A)
+        t = {"tree_s": e[0].elapsed_time(e[1]) / 1e3, "assemble_s": e[1].elapsed_time(e[2]) / 1e3,
+             "load_s": e[2].elapsed_time(e[3]) / 1e3, "solve_mixed_s": e[3].elapsed_time(e[4]) / 1e3,
+             "step_s": e[0].elapsed_time(e[4]) / 1e3, "minfo": mi, "tinfo": hm.hm_tree_get_info(tree),
+             "iters": info.iters, "refine_steps": info.refine_steps, "rel_resid": info.rel_resid,
+             "inner_dtype": info.inner_dtype}
         if keep:
             return t, tree, A
         hm.hm_free(A)
@@ -269,23 +316,23 @@ def run_ours(args, rank, world):
         return t
 
     if args.profile_step:
-        r = step(Vd, Td)
-        return {"profile_step": args.case, "step_s": r["step_s"], "aca_s": r["minfo"]["s_aca"],
-                "aca_small_sum": r["minfo"]["aca_small_sum"],
-                "nearfield_s": r["minfo"]["s_nearfield"], "iters_fp64": r["iters_fp64"],
-                "iters_mixed": r["iters_mixed"]}, None
+        r = step(Vd, Td, srcd)
+        return {"profile_step": case, "step_s": r["step_s"], "aca_s": r["minfo"]["s_aca"],
+                "nearfield_s": r["minfo"]["s_nearfield"], "solve_mixed_s": r["solve_mixed_s"],
+                "iters": r["iters"], "refine_steps": r["refine_steps"]}, None
     for _ in range(args.warmup):
-        step(Vd, Td)
+        step(Vd, Td, srcd)
+    peaks, peak_src = _peaks()
+    peaks = dict(peaks, workload=case, **measured_fma_peaks(hm, torch))
     barrier(world)
     torch.cuda.synchronize()
     clocks = Clocks(dev.index)
     clocks.start()
     hm.hm_trace_enable(True)
     l0 = hm.hm_kernel_launches()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0, ev1 = _ev(torch), _ev(torch)
     ev0.record(stream)
-    results = [step(Vd, Td) for _ in range(args.steps)]
+    results = [step(Vd, Td, srcd) for _ in range(args.steps)]
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
@@ -296,259 +343,432 @@ def run_ours(args, rank, world):
     total_s = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, world)
     per_step = total_s / args.steps
 
-    # mixed vs FP64 solution error, matvec GB/s (separate, untimed for `value`)
+    # --- outside the timed steps: the last step kept, FP64 form, BF16 form, products
+    last, tree, A = step(Vd, Td, srcd, keep=True)
+    Xm = X.clone()
+    mi, ti = last["minfo"], last["tinfo"]
+    X64 = torch.zeros_like(F)
+    a, b = _ev(torch), _ev(torch)
+    a.record(stream)
+    i64 = hm.hm_solve(A, F, X64, **opts)
+    b.record(stream)
+    torch.cuda.synchronize()
+    fp64_s = a.elapsed_time(b) / 1e3
+    nx64 = torch.linalg.norm(X64, dim=1)
+    err32 = float(torch.max(torch.linalg.norm(Xm - X64, dim=1) / nx64))
+    # BF16 factors (the copy added from the FP64 master) + FP64 refinement
+    hm.hm_matrix_add_copy(A, hm.HM_BF16)
+    Xb = torch.zeros_like(F)
+    a.record(stream)
+    ib = hm.hm_solve(A, F, Xb, refine=1, inner_dtype=hm.HM_BF16, inner_tol=1e-2, max_refine=80,
+                     raise_on_noconv=False, **opts)
+    b.record(stream)
+    torch.cuda.synchronize()
+    bf16_s = a.elapsed_time(b) / 1e3
+    errbf = float(torch.max(torch.linalg.norm(Xb - X64, dim=1) / nx64))
+    # H-matvec: 16 right-hand sides on the tensor cores, one right-hand side on the CUDA cores
+    Xr = torch.randn((R, n), dtype=torch.float64, device=dev)
+    Yr = torch.empty_like(Xr)
+    mv = {}
+    for name, prec, fb in (("16rhs_fp32", hm.HM_F32, 4), ("16rhs_bf16", hm.HM_BF16, 2)):
+        hm.hm_matvec_block(A, Xr, Yr, prec=prec)
+        a.record(stream)
+        for _ in range(5):
+            hm.hm_matvec_block(A, Xr, Yr, prec=prec)
+        b.record(stream)
+        torch.cuda.synchronize()
+        sec = a.elapsed_time(b) / 5e3
+        byts = mi["dense_entries"] * 4 + mi["lr_entries"] * fb
+        mv[name] = {"s": sec, "matrix_gb": byts / 1e9, "gbs_matrix": byts / sec / 1e9,
+                    "s_per_rhs": sec / R}
+    for name, prec, esz in (("1rhs_fp64", hm.HM_F64, 8), ("1rhs_fp32", hm.HM_F32, 4)):
+        hm.hm_matvec(A, Xr[0], Yr[0], prec=prec)
+        a.record(stream)
+        for _ in range(3):
+            hm.hm_matvec(A, Xr[0], Yr[0], prec=prec)
+        b.record(stream)
+        torch.cuda.synchronize()
+        sec = a.elapsed_time(b) / 3e3
+        byts = (mi["dense_entries"] + mi["lr_entries"]) * esz + n * 8 * 4
+        mv[name] = {"s": sec, "gbs": byts / sec / 1e9, "bytes": byts}
+    leaves = hm.hm_tree_get_leaves(tree, True).cpu().numpy().astype("int64")
+    dom, others, kernels = rooflines(trace, args.steps, mi, ti, leaves, n, peaks, peak_src)
+    hm.hm_free(A)
+    hm.hm_free(tree)
+
+    # e2e: the same step through the C ABI from pinned host buffers, host<->device copies timed
+    Vh = torch.from_numpy(V).pin_memory()
+    Th = torch.from_numpy(T).pin_memory()
+    Sh = torch.from_numpy(np.ascontiguousarray(cfg["sources"][:R])).pin_memory()
+    Xh = torch.empty((R, n), dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 2))
+    torch.cuda.synchronize()
+    c0, c1 = _ev(torch), _ev(torch)
+    c0.record(stream)
+    for _ in range(e2e_steps):
+        step(Vh.to(dev, non_blocking=True), Th.to(dev, non_blocking=True), Sh.to(dev, non_blocking=True))
+        Xh.copy_(X, non_blocking=True)
+    c1.record(stream)
+    torch.cuda.synchronize()
+    e2e_s = c0.elapsed_time(c1) / 1e3 / e2e_steps
+
+    out = {
+        "metric": METRIC, "value": per_step, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64 (mixed solve: f32 near field + f32 factors, f64 refinement)",
+        "data": "synthetic (seeded unit icosphere and point sources, no dataset)",
+        "config": dict(W, parallelism="replicas" if world > 1 else "single GPU",
+                       l2="inputs larger than L2 (near field %.1f GB, factors %.1f GB in FP64)" % (
+                           mi["dense_entries"] * 8 / 1e9, mi["lr_entries"] * 8 / 1e9)),
+        "setup_s": _mean(results, "tree_s") + _mean(results, "assemble_s"),
+        "tree_s": _mean(results, "tree_s"), "assemble_s": _mean(results, "assemble_s"),
+        "nearfield_s": sum(r["minfo"]["s_nearfield"] for r in results) / len(results),
+        "singular_s": sum(r["minfo"]["s_singular"] for r in results) / len(results),
+        "aca_s": sum(r["minfo"]["s_aca"] for r in results) / len(results),
+        "load_s": _mean(results, "load_s"),
+        "solve_mixed_16rhs_s": _mean(results, "solve_mixed_s"),
+        "mixed_iters": last["iters"], "mixed_refine_steps": last["refine_steps"],
+        "mixed_rel_resid": last["rel_resid"], "mixed_inner_dtype": last["inner_dtype"],
+        "fp64_16rhs": {"solve_s": fp64_s, "repetitions": 1, "iters": i64.iters, "rel_resid": i64.rel_resid,
+                       "note": "the all-FP64 GPU form of the same 16 systems (lockstep GMRES, FP64 products), "
+                               "timed once on the last step's matrix"},
+        "mixed_vs_fp64_rel_err": err32,
+        "mixed_vs_fp64_time_ratio": fp64_s / _mean(results, "solve_mixed_s"),
+        "bf16_16rhs": {"solve_s": bf16_s, "repetitions": 1, "iters": ib.iters, "refine_steps": ib.refine_steps,
+                       "rel_resid": ib.rel_resid, "inner_dtype": ib.inner_dtype, "err_vs_fp64": errbf,
+                       "note": "BF16 factors added from the FP64 master, FP32 near field, inner tol 1e-2"},
+        "matvec": mv, "mean_rank": mi["mean_rank"], "max_rank": mi["max_rank"],
+        "dense_entries": mi["dense_entries"], "lr_entries": mi["lr_entries"], "aca_small_sum": mi["aca_small_sum"],
+        "roofline": dom, "rooflines_other": others, "kernels": kernels,
+        "measured_peaks": {k: peaks[k] for k in ("fp64_tflops", "fp32_tflops", "sm_mhz", "how")},
+        "clocks": ck, "gpu_launches": int(launches),
+        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(V.nbytes + T.nbytes + Sh.numel() * 8),
+                "d2h_bytes_per_step": int(R * n * 8)},
+    }
+    return out, (V, T, {"iters_fp64": i64.iters, "n_systems": R, "W": W, "case": case,
+                        "fma_peaks": out["measured_peaks"]})
+
+
+# ---------------------------------------------------------------------------
+# the precision workload (one source): FP64 solve + FP32-refined solve
+# ---------------------------------------------------------------------------
+def run_single(args, world, hm, torch, W=PRECISION, case="precision", extras=True, fma_peaks=None):
+    import meshgen
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    stream = torch.cuda.current_stream()
+    cfg = meshgen.config(case)
+    V, T = cfg["V"], cfg["T"]
+    n = T.shape[0]
+    Vd = torch.from_numpy(V).to(dev)
+    Td = torch.from_numpy(T).to(dev)
+    src = torch.tensor([W["source"]], dtype=torch.float64, device=dev)
+    f = torch.empty((1, n), dtype=torch.float64, device=dev)
+    x64 = torch.zeros(n, dtype=torch.float64, device=dev)
+    xmx = torch.zeros(n, dtype=torch.float64, device=dev)
+    sopts = dict(rel_tol=W["solve_rel_tol"], restart=W["restart"], max_iter=5000, precond=int(W["precond"]),
+                 use_graph=int(W["use_graph"]))
+
+    def step(Vdev, Tdev, keep=False):
+        e = [_ev(torch) for _ in range(6)]
+        e[0].record(stream)
+        tree = hm.hm_build_tree(Vdev, Tdev, eta=W["eta"], leaf_size=W["leaf_size"])
+        e[1].record(stream)
+        A = hm.hm_assemble(tree, aca_eps=W["aca_eps"], aca_kmax=W["aca_kmax"], ss_order=W["ss_order"],
+                           factor_dtype=hm.HM_F32, dense_dtype=hm.HM_F32)
+        e[2].record(stream)
+        hm.hm_load_vector(tree, src, f)
+        e[3].record(stream)
+        i64 = hm.hm_solve(A, f[0], x64, **sopts)
+        e[4].record(stream)
+        imx = hm.hm_solve(A, f[0], xmx, refine=1, inner_tol=W["inner_tol"], inner_dtype=hm.HM_F32, max_refine=50,
+                          **sopts)
+        e[5].record(stream)
+        torch.cuda.synchronize()
+        t = {"tree_s": e[0].elapsed_time(e[1]) / 1e3, "assemble_s": e[1].elapsed_time(e[2]) / 1e3,
+             "load_s": e[2].elapsed_time(e[3]) / 1e3, "solve_fp64_s": e[3].elapsed_time(e[4]) / 1e3,
+             "solve_mixed_s": e[4].elapsed_time(e[5]) / 1e3, "step_s": e[0].elapsed_time(e[5]) / 1e3,
+             "minfo": hm.hm_matrix_get_info(A), "tinfo": hm.hm_tree_get_info(tree), "iters_fp64": i64.iters,
+             "iters_mixed": imx.iters, "refine_steps": imx.refine_steps, "resid_fp64": i64.rel_resid,
+             "resid_mixed": imx.rel_resid, "kappa_est": i64.kappa_est}
+        if keep:
+            return t, tree, A
+        hm.hm_free(A)
+        hm.hm_free(tree)
+        return t
+
+    if args.profile_step and extras:
+        r = step(Vd, Td)
+        return {"profile_step": case, "step_s": r["step_s"], "aca_s": r["minfo"]["s_aca"],
+                "aca_small_sum": r["minfo"]["aca_small_sum"], "nearfield_s": r["minfo"]["s_nearfield"],
+                "iters_fp64": r["iters_fp64"], "iters_mixed": r["iters_mixed"]}, None
+    warmup = args.warmup if extras else 1
+    steps = args.steps if extras else 2
+    for _ in range(warmup):
+        step(Vd, Td)
+    peaks, peak_src = _peaks()
+    peaks = dict(peaks, workload=case, **(fma_peaks or measured_fma_peaks(hm, torch)))
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = Clocks(dev.index)
+    clocks.start()
+    hm.hm_trace_enable(True)
+    l0 = hm.hm_kernel_launches()
+    ev0, ev1 = _ev(torch), _ev(torch)
+    ev0.record(stream)
+    results = [step(Vd, Td) for _ in range(steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = hm.hm_kernel_launches() - l0
+    hm.hm_trace_enable(False)
+    trace = hm.hm_trace_read()
+    ck = clocks.stop()
+    per_step = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, world) / steps
     last, tree, A = step(Vd, Td, keep=True)
     err_mixed = float(torch.linalg.norm(xmx - x64) / torch.linalg.norm(x64))
     mi, ti = last["minfo"], last["tinfo"]
+    summary = {
+        "value": per_step, "unit": "s", "steps": steps, "warmup": warmup,
+        "config": dict(W, l2="inputs larger than L2 (near field %.1f GB, factors %.1f GB)" % (
+            mi["dense_entries"] * 8 / 1e9, mi["lr_entries"] * 8 / 1e9)),
+        "setup_s": _mean(results, "tree_s") + _mean(results, "assemble_s"),
+        "tree_s": _mean(results, "tree_s"), "assemble_s": _mean(results, "assemble_s"),
+        "nearfield_s": sum(r["minfo"]["s_nearfield"] for r in results) / len(results),
+        "singular_s": sum(r["minfo"]["s_singular"] for r in results) / len(results),
+        "aca_s": sum(r["minfo"]["s_aca"] for r in results) / len(results),
+        "solve_fp64_s": _mean(results, "solve_fp64_s"), "solve_mixed_s": _mean(results, "solve_mixed_s"),
+        "iters_fp64": last["iters_fp64"], "iters_mixed": last["iters_mixed"], "refine_steps": last["refine_steps"],
+        "resid_fp64": last["resid_fp64"], "resid_mixed": last["resid_mixed"],
+        "kappa_est_fp64_solve": last["kappa_est"], "mixed_vs_fp64_rel_err": err_mixed,
+        "mean_rank": mi["mean_rank"], "max_rank": mi["max_rank"], "dense_entries": mi["dense_entries"],
+        "lr_entries": mi["lr_entries"], "clocks": ck, "gpu_launches": int(launches),
+    }
+    leaves = hm.hm_tree_get_leaves(tree, True).cpu().numpy().astype("int64")
+    dom, others, kernels = rooflines(trace, steps, mi, ti, leaves, n, peaks, peak_src)
+    summary["roofline"] = dom
+    summary["rooflines_other"] = others
+    if not extras:
+        summary["kernels"] = {k: v for k, v in kernels.items() if v["share_of_traced"] > 0.02}
+        hm.hm_free(A)
+        hm.hm_free(tree)
+        return summary
     xs = torch.randn(n, dtype=torch.float64, device=dev)
     ys = torch.empty_like(xs)
     mv = {}
     for name, prec, esz in (("fp64", hm.HM_F64, 8), ("fp32", hm.HM_F32, 4)):
         for _ in range(3):
             hm.hm_matvec(A, xs, ys, prec=prec)
-        torch.cuda.synchronize()
-        a0 = torch.cuda.Event(enable_timing=True)
-        a1 = torch.cuda.Event(enable_timing=True)
-        reps = 10
-        a0.record(stream)
-        for _ in range(reps):
+        a, b = _ev(torch), _ev(torch)
+        a.record(stream)
+        for _ in range(10):
             hm.hm_matvec(A, xs, ys, prec=prec)
-        a1.record(stream)
+        b.record(stream)
         torch.cuda.synchronize()
-        sec = a0.elapsed_time(a1) / 1e3 / reps
+        sec = a.elapsed_time(b) / 1e4
         byts = (mi["dense_entries"] + mi["lr_entries"]) * esz + n * 8 * 4
         mv[name] = {"s": sec, "gbs": byts / sec / 1e9, "bytes": byts}
-    # BF16 factors: one extra assembly and refined solve, reported beside
-    A16 = hm.hm_assemble(tree, aca_eps=W["aca_eps"], aca_kmax=W["aca_kmax"], ss_order=W["ss_order"],
-                         factor_dtype=hm.HM_BF16, dense_dtype=hm.HM_F32)
-    xbf = torch.zeros_like(x64)
-    b0 = torch.cuda.Event(enable_timing=True)
-    b1 = torch.cuda.Event(enable_timing=True)
-    hm.hm_trace_enable(True)
-    b0.record(stream)
-    ibf = hm.hm_solve(A16, f[0], xbf, rel_tol=W["solve_rel_tol"], restart=W["restart"], max_iter=5000, refine=1,
-                      inner_tol=1e-2, inner_dtype=hm.HM_BF16, max_refine=80, raise_on_noconv=False,
-                      precond=int(W["precond"]))
-    b1.record(stream)
-    torch.cuda.synchronize()
-    hm.hm_trace_enable(False)
-    bf16_kernels = kernel_table(hm.hm_trace_read(), 1)
-    bf16 = {"kernels": {k: v for k, v in bf16_kernels.items() if v["share_of_traced"] > 0.01},
-            "solve_s": b0.elapsed_time(b1) / 1e3, "err_vs_fp64": float(torch.linalg.norm(xbf - x64) /
-                                                                        torch.linalg.norm(x64)),
-            "iters": ibf.iters, "refine_steps": ibf.refine_steps, "rel_resid": ibf.rel_resid}
-    hm.hm_free(A16)
-
-    # e2e: the same step through the C ABI from pinned host buffers, host<->device copies timed
+    hm.hm_free(A)
+    hm.hm_free(tree)
     Vh = torch.from_numpy(V).pin_memory()
     Th = torch.from_numpy(T).pin_memory()
     xh = torch.empty(n, dtype=torch.float64).pin_memory()
-    e2e_steps = max(1, min(args.steps, 2))
+    e2e_steps = max(1, min(steps, 2))
     torch.cuda.synchronize()
-    c0 = torch.cuda.Event(enable_timing=True)
-    c1 = torch.cuda.Event(enable_timing=True)
+    c0, c1 = _ev(torch), _ev(torch)
     c0.record(stream)
     for _ in range(e2e_steps):
-        Vd2 = Vh.to(dev, non_blocking=True)
-        Td2 = Th.to(dev, non_blocking=True)
-        step(Vd2, Td2)
+        step(Vh.to(dev, non_blocking=True), Th.to(dev, non_blocking=True))
         xh.copy_(xmx, non_blocking=True)
     c1.record(stream)
     torch.cuda.synchronize()
     e2e_s = c0.elapsed_time(c1) / 1e3 / e2e_steps
-
-    # roofline of the dominant kernel: the traced kernel with the largest
-    # device time over the timed steps; achieved = its algorithmic work per
-    # launch / its mean launch time (CUDA events on its own stream)
-    peaks, peak_src = _peaks()
-    leaves = hm.hm_tree_get_leaves(tree, True).cpu().numpy().astype("int64")
-    kernels = kernel_table(trace, args.steps)
-    work = algorithmic_work(mi, ti, leaves, n)
-    roofline = None
-    for name, kt in kernels.items():
-        if name in work:
-            roofline = roofline_entry(name, kt, work[name], peaks, peak_src)
-            break
-    others = {name: roofline_entry(name, kt, work[name], peaks, peak_src)
-              for name, kt in kernels.items() if name in work and (roofline is None or name != roofline["kernel"])}
-    nf_s = sum(r["minfo"]["s_nearfield"] for r in results) / len(results)
-    aca_s = sum(r["minfo"]["s_aca"] for r in results) / len(results)
-    hm.hm_free(A)
-    hm.hm_free(tree)
-
-    out = {
-        "metric": METRIC, "value": per_step, "unit": "s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64 (mixed solve: f32 factors, f64 refinement)",
-        "data": "synthetic (seeded bumped icosphere, no dataset)",
-        "config": dict(WORKLOAD, parallelism="replicas" if world > 1 else "single GPU",
-                       l2="inputs larger than L2 (near field %.1f GB, factors %.1f GB)" % (
-                           mi["dense_entries"] * 8 / 1e9, mi["lr_entries"] * 8 / 1e9)),
-        "setup_s": sum(r["tree_s"] + r["assemble_s"] for r in results) / len(results),
-        "tree_s": sum(r["tree_s"] for r in results) / len(results),
-        "assemble_s": sum(r["assemble_s"] for r in results) / len(results),
-        "nearfield_s": nf_s, "singular_s": sum(r["minfo"]["s_singular"] for r in results) / len(results),
-        "aca_s": aca_s, "aca_small_sum": mi["aca_small_sum"],
-        "solve_fp64_s": sum(r["solve_fp64_s"] for r in results) / len(results),
-        "solve_mixed_s": sum(r["solve_mixed_s"] for r in results) / len(results),
-        "iters_fp64": last["iters_fp64"], "iters_mixed": last["iters_mixed"], "refine_steps": last["refine_steps"],
-        "resid_fp64": last["resid_fp64"], "resid_mixed": last["resid_mixed"],
-        "kappa_est_fp64_solve": last["kappa_est"], "mixed_vs_fp64_rel_err": err_mixed,
-        "bf16": bf16, "matvec": mv, "mean_rank": mi["mean_rank"], "max_rank": mi["max_rank"],
-        "dense_entries": mi["dense_entries"], "lr_entries": mi["lr_entries"],
-        "roofline": roofline, "kernels": kernels, "rooflines_other": others,
-        "clocks": ck, "gpu_launches": int(launches),
-        "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(V.nbytes + T.nbytes),
-                "d2h_bytes_per_step": int(n * 8)},
-    }
-    return out, (V, T, last)
+    out = {"metric": METRIC, "n_gpus": world, "ms_per_step": per_step * 1e3, "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64 (mixed solve: f32 factors, f64 refinement)",
+           "data": "synthetic (seeded bumped icosphere, no dataset)", **summary,
+           "config": dict(summary["config"], parallelism="replicas" if world > 1 else "single GPU"),
+           "matvec": mv, "kernels": kernels,
+           "measured_peaks": {k: peaks[k] for k in ("fp64_tflops", "fp32_tflops", "sm_mhz", "how")},
+           "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(V.nbytes + T.nbytes),
+                   "d2h_bytes_per_step": int(n * 8)}}
+    return out, (V, T, {"iters_fp64": last["iters_fp64"], "n_systems": 1, "W": W, "case": case,
+                        "fma_peaks": out["measured_peaks"]})
 
 
-def cpu_oracle_step(V, T, budget_s=20.0, iters=None, seed=0):
-    """The oracle, as it stands, on a bounded sample of the workload; returns
-    the estimated seconds for one full step and what was sampled."""
-    import numpy as np
+# ---------------------------------------------------------------------------
+# the CPU oracle on a bounded sample of the workload
+# ---------------------------------------------------------------------------
+# Admissible leaves drawn per size class (rows = columns; 80 .. 81,920 at level
+# 8 with leaf 128, 40 .. 40,960 at level 7 with leaf 64): many of the small
+# ones, at least one of the largest.
+ACA_SAMPLE = {40: 6000, 80: 4000, 160: 2000, 320: 1000, 640: 400, 1280: 160, 2560: 48, 5120: 16, 10240: 8,
+              20480: 4, 40960: 2, 81920: 1}
+# Lockstep Arnoldi steps of the all-FP64 GPU solve of each workload (block-
+# Jacobi preconditioned), the iteration count of the CPU estimate's solve
+# when the GPU arm has not run in the same process.
+FP64_STEPS = {"large": 111, "precision": 84}
+
+
+class OracleTree:
+    """The oracle's tree of a workload, built once per process and timed."""
+    cache = {}
+
+    @classmethod
+    def get(cls, case, V, T, leaf, eta):
+        import oracle
+        if case not in cls.cache:
+            oracle.build()
+            t0 = time.perf_counter()
+            tr = oracle.Tree(V, T, leaf, eta)
+            cls.cache[case] = (tr, time.perf_counter() - t0)
+        return cls.cache[case]
+
+
+def cpu_oracle_step(case, V, T, W, n_systems, iters_per_system, seed=0, dense_sample=2000, gmres_steps=3):
+    """The oracle, as it stands, on a bounded sample of one step of the
+    workload.  Returns (estimated seconds of a full step, measured seconds of
+    the sampled work, description, parts).
+
+    What runs: the oracle's tree of the whole mesh (built once per process and
+    timed then); the near field of `dense_sample` dense leaves drawn uniformly;
+    the ACA of admissible leaves drawn per size class (ACA_SAMPLE); and
+    oracle.gmres on the sampled operator (those leaves only, at the full
+    dimension n) for `gmres_steps` Arnoldi steps, its products timed apart
+    from its orthogonalisation.  The estimate scales each sampled part to the
+    whole workload: near field by the leaf count, each ACA size class by its
+    leaf count and by the thread parallelism the class had in the sample, the
+    solve by n_systems x iters_per_system Arnoldi steps of a product scaled
+    to the stored entries of the whole matrix plus the measured
+    orthogonalisation cost per step (at the sampled depth)."""
     import oracle
-    oracle.build()
-    W = WORKLOAD
-    t0 = time.perf_counter()
-    tr = oracle.Tree(V, T, W["leaf_size"], W["eta"])
-    t_tree = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    tr, t_tree = OracleTree.get(case, V, T, W["leaf_size"], W["eta"])
     rng = np.random.default_rng(seed)
     quad = oracle.Quad(W["ss_order"])
-    # near field: a random sample of dense leaves
+    w0 = time.perf_counter()
     nd = len(tr.dense)
-    sd = rng.choice(nd, size=min(nd, 60000), replace=False)
+    sd = np.sort(rng.choice(nd, size=min(nd, dense_sample), replace=False))
     t0 = time.perf_counter()
     blocks = []
     for b in sd:
         rb, re, cb, ce = tr.dense[b]
         blocks.append(oracle.assemble(tr.V, tr.T, tr.perm[rb:re], tr.perm[cb:ce], quad).ravel())
     t_nf = (time.perf_counter() - t0) * nd / len(sd)
-    # ACA: a random sample of admissible leaves
-    na = len(tr.adm)
-    sa = rng.choice(na, size=min(na, 100000), replace=False)
-    t0 = time.perf_counter()
-    fac = oracle.aca_blocks(tr.V, tr.T, tr.perm, tr.adm[sa], W["aca_eps"], W["aca_kmax"], quad)
-    t_aca = (time.perf_counter() - t0) * na / len(sa)
-    # H-matvec: the sampled blocks applied, scaled to the whole matrix
+    sizes = tr.adm[:, 1] - tr.adm[:, 0]
+    t_aca, fac, sa_all, aca_note = 0.0, [], [], []
+    for sz in np.unique(sizes):
+        idx = np.flatnonzero(sizes == sz)
+        k = min(len(idx), ACA_SAMPLE.get(int(sz), 16))
+        sa = np.sort(rng.choice(idx, size=k, replace=False))
+        t0 = time.perf_counter()
+        fac += oracle.aca_blocks(tr.V, tr.T, tr.perm, tr.adm[sa], W["aca_eps"], W["aca_kmax"], quad)
+        dt = time.perf_counter() - t0
+        # the class's blocks run on min(count, cores) threads in a full run,
+        # on min(k, cores) in the sample
+        t_aca += dt * (len(idx) / k) * (min(k, cores) / min(len(idx), cores))
+        sa_all.append(sa)
+        aca_note.append("%d/%d" % (k, len(idx)))
+    sa_all = np.concatenate(sa_all)
+    # the sampled operator, applied by oracle.gmres
     dense_val = np.concatenate(blocks)
-    d_off = np.cumsum([0] + [blk.size for blk in blocks])
+    d_off = np.cumsum([0] + [blk.size for blk in blocks])[:-1]
     parts, uo, wo, o = [], [], [], 0
     for U, Wf in fac:
-        uo.append(o); parts.append(U.T.ravel()); o += U.size
-        wo.append(o); parts.append(Wf.T.ravel()); o += Wf.size
+        uo.append(o)
+        parts.append(U.T.ravel())
+        o += U.size
+        wo.append(o)
+        parts.append(Wf.T.ravel())
+        o += Wf.size
     uw = np.concatenate(parts) if parts else np.zeros(1)
     rank = np.array([U.shape[1] for U, _ in fac], dtype=np.int32)
-    x = rng.standard_normal(tr.n)
+    t_mv = [0.0, 0]
+
+    def mv_sample(xm):
+        t1 = time.perf_counter()
+        y = oracle.hmatvec_raw(tr.n, tr.dense[sd], d_off, dense_val, tr.adm[sa_all], rank, uo, wo, uw, xm)
+        t_mv[0] += time.perf_counter() - t1
+        t_mv[1] += 1
+        return y
+
+    b = rng.standard_normal(tr.n)
     t0 = time.perf_counter()
-    reps = 10
-    for _ in range(reps):
-        oracle.hmatvec_raw(tr.n, tr.dense[sd], d_off[:-1], dense_val, tr.adm[sa], rank, uo, wo, uw, x)
-    t_mv_sample = (time.perf_counter() - t0) / reps
+    oracle.gmres(mv_sample, b, restart=30, tol=1e-300, maxiter=gmres_steps)
+    t_gm = time.perf_counter() - t0
+    wall = time.perf_counter() - w0
     dense_total = int(((tr.dense[:, 1] - tr.dense[:, 0]) * (tr.dense[:, 3] - tr.dense[:, 2])).sum())
-    lr_total = uw.size * na / len(sa)
-    t_mv = t_mv_sample * (dense_total + lr_total) / max(1, dense_val.size + uw.size)
-    n_mv = (iters or 200)
-    t_solve = t_mv * n_mv
+    # stored factor entries of the whole matrix: the sampled mean per leaf of each size class
+    lr_total = 0.0
+    for sz in np.unique(sizes):
+        pick = sizes[sa_all] == sz
+        ent = np.array([U.size + Wf.size for (U, Wf), p in zip(fac, pick) if p], dtype=np.float64)
+        lr_total += ent.mean() * np.count_nonzero(sizes == sz) if ent.size else 0.0
+    scale = (dense_total + lr_total) / max(1, dense_val.size + uw.size)
+    per_mv = t_mv[0] / max(1, t_mv[1])
+    per_step_other = max(0.0, t_gm - t_mv[0]) / gmres_steps
+    t_solve = n_systems * iters_per_system * (per_mv * scale + per_step_other)
     total = t_tree + t_nf + t_aca + t_solve
-    sample = ("full Morton + block tree (%.1fs); %d of %d dense leaves and %d of %d admissible leaves (ACA), "
-              "drawn uniformly with a fixed seed, times scaled by the leaf counts; H-matvec of the sampled "
-              "leaves scaled by stored entries x %d matvecs (the GPU's Krylov steps)" % (t_tree, len(sd), nd,
-                                                                                           len(sa), na, n_mv))
-    return total, sample, dict(tree_s=t_tree, nearfield_s=t_nf, aca_s=t_aca, solve_s=t_solve)
+    sample = ("oracle tree of the whole mesh (%.1f s, built once per process); near field of %d of %d dense "
+              "leaves (uniform draw); ACA of admissible leaves per size class (%s, sampled/total); oracle.gmres on "
+              "the sampled operator for %d Arnoldi steps at n = %d. Estimate = tree + near field x %d/%d + ACA per "
+              "class x count (thread parallelism corrected) + %d systems x %d Arnoldi steps x (sampled product "
+              "x %.0f stored-entry ratio + orthogonalisation per step)"
+              % (t_tree, len(sd), nd, ", ".join(aca_note), gmres_steps, tr.n, nd, len(sd), n_systems,
+                 iters_per_system, scale))
+    return total, wall, sample, dict(tree_s=t_tree, nearfield_s=t_nf, aca_s=t_aca, solve_s=t_solve,
+                                     sample_wall_s=wall)
 
 
 def run_reference(args, rank, world):
-    import meshgen  # noqa: F401
-    V, T = _inputs()
-    cores = os.cpu_count()
-    vals = []
-    for _ in range(args.warmup):
-        cpu_oracle_step(V, T, seed=1)
+    """The reference arm: the oracle on the host cores.  Each step is one
+    bounded-sample estimate of a full step (cpu_oracle_step, a fresh sample
+    per step); `value` is the mean estimate (marked as such), `ms_per_step` the
+    wall time the sampled work of a step actually took."""
+    import meshgen
+    case = args.case
+    W = LARGE if case == "large" else PRECISION
+    cfg = meshgen.config(case)
+    V, T = cfg["V"], cfg["T"]
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    nsys = W["nrhs"]
+    its = FP64_STEPS.get(case, 100)
     t0 = time.perf_counter()
+    OracleTree.get(case, V, T, W["leaf_size"], W["eta"])
+    t_setup = time.perf_counter() - t0
+    for k in range(args.warmup):
+        cpu_oracle_step(case, V, T, W, nsys, its, seed=1000 + k)
+    vals, walls = [], []
     for k in range(args.steps):
-        v, sample, parts = cpu_oracle_step(V, T, seed=2 + k)
+        v, wall, sample, parts = cpu_oracle_step(case, V, T, W, nsys, its, seed=2 + k)
         vals.append(v)
-    wall = time.perf_counter() - t0
+        walls.append(wall)
     val = sum(vals) / len(vals)
+    ms = 1e3 * sum(walls) / len(walls)
     return {"impl": "reference", "metric": METRIC, "value": val, "unit": "s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": val * 1e3, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded bumped icosphere)",
-            "config": dict(WORKLOAD), "cpu_baseline": {"value": val, "unit": "s", "cores": cores, "kind": "oracle",
-                                                         "sample": sample, "parts": parts, "wall_s": wall},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded meshes and sources, no dataset)",
+            "value_is_estimate": True,
+            "value_note": "each step is one bounded-sample estimate of a full oracle step of this workload "
+                          "(see cpu_baseline.sample); value = mean estimate in seconds per full step, "
+                          "ms_per_step = wall time of the sampled work one step actually ran",
+            "config": dict(W), "cpu_baseline": {"value": val, "unit": "s", "cores": cores, "kind": "oracle",
+                                                 "sample": sample, "parts": parts,
+                                                 "tree_build_once_s": t_setup,
+                                                 "estimates_min_max": [min(vals), max(vals)]},
             "e2e": {"value": val, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-def _ev(torch):
-    return torch.cuda.Event(enable_timing=True)
-
-
-def run_large(torch, hm):
-    """Large workload: icosphere level 8 (1,310,720 panels), leaf 128, eps 1e-6,
-    16 point sources; FP64 form (16 FP64 solves in lockstep) against the
-    mixed forms (FP32 near field + BF16 factors, then FP32 factors added from
-    the FP64 master; inner solves through the 16-right-hand-side tensor-core
-    product, FP64 refinement)."""
-    import meshgen
-    cfg = meshgen.config("large")
-    n = cfg["T"].shape[0]
-    V, T = torch.from_numpy(cfg["V"]).cuda(), torch.from_numpy(cfg["T"]).cuda()
-    e = [_ev(torch) for _ in range(8)]
-    hm.hm_trace_enable(True)
-    e[0].record()
-    tree = hm.hm_build_tree(V, T, eta=cfg["eta"], leaf_size=cfg["leaf_size"])
-    A = hm.hm_assemble(tree, aca_eps=cfg["aca_eps"], aca_kmax=64, ss_order=8, factor_dtype=hm.HM_BF16,
-                       dense_dtype=hm.HM_F32)
-    e[1].record()
-    src = torch.from_numpy(np.ascontiguousarray(cfg["sources"])).cuda()
-    F = torch.empty((16, n), dtype=torch.float64, device="cuda")
-    hm.hm_load_vector(tree, src, F)
-    X = torch.randn((16, n), dtype=torch.float64, device="cuda")
-    Y = torch.empty_like(X)
-    for _ in range(2):
-        hm.hm_matvec_block(A, X, Y, prec=hm.HM_BF16)
-    e[2].record()
-    for _ in range(5):
-        hm.hm_matvec_block(A, X, Y, prec=hm.HM_BF16)
-    e[3].record()
-    opts = dict(rel_tol=1e-12, restart=128, max_iter=5000, precond=1, batched=1)
-    Xm = torch.zeros_like(F)
-    e[4].record()
-    im = hm.hm_solve(A, F, Xm, refine=1, inner_dtype=hm.HM_BF16, inner_tol=1e-2, max_refine=80, **opts)
-    e[5].record()
-    X64 = torch.zeros_like(F)
-    i64 = hm.hm_solve(A, F, X64, **opts)
-    e[6].record()
-    torch.cuda.synchronize()
-    hm.hm_trace_enable(False)
-    # the same refinement with FP32 factors (the copy made from the FP64 master)
-    hm.hm_matrix_add_copy(A, hm.HM_F32)
-    X32 = torch.zeros_like(F)
-    e[7].record()
-    i32 = hm.hm_solve(A, F, X32, refine=1, inner_dtype=hm.HM_F32, inner_tol=1e-4, max_refine=40, **opts)
-    e8 = _ev(torch)
-    e8.record()
-    torch.cuda.synchronize()
-    err32 = float(torch.max(torch.linalg.norm(X32 - X64, dim=1) / torch.linalg.norm(X64, dim=1)))
-    mi = hm.hm_matrix_get_info(A)
-    mat_bytes = mi["dense_entries"] * 4 + mi["lr_entries"] * 2
-    blk_s = e[2].elapsed_time(e[3]) / 5e3
-    err = float(torch.max(torch.linalg.norm(Xm - X64, dim=1) / torch.linalg.norm(X64, dim=1)))
-    out = {"workload": "large: icosphere level 8, 1,310,720 panels, leaf 128, eta 1.5, ACA eps 1e-6, 16 sources",
-           "setup_s": e[0].elapsed_time(e[1]) / 1e3, "nearfield_s": mi["s_nearfield"], "singular_s": mi["s_singular"],
-           "aca_s": mi["s_aca"], "mean_rank": mi["mean_rank"],
-           "block_matvec_16rhs": {"s": blk_s, "matrix_gb": mat_bytes / 1e9, "gbs": mat_bytes / blk_s / 1e9},
-           "solve_mixed_16rhs_s": e[4].elapsed_time(e[5]) / 1e3, "mixed_iters": im.iters,
-           "mixed_refine_steps": im.refine_steps, "mixed_rel_resid": im.rel_resid,
-           "solve_fp64_16rhs_s": e[5].elapsed_time(e[6]) / 1e3, "fp64_iters": i64.iters,
-           "fp64_rel_resid": i64.rel_resid, "mixed_vs_fp64_max_rel_err": err,
-           "solve_mixed_fp32_16rhs_s": e[7].elapsed_time(e8) / 1e3, "mixed_fp32_iters": i32.iters,
-           "mixed_fp32_refine_steps": i32.refine_steps, "mixed_fp32_rel_resid": i32.rel_resid,
-           "mixed_fp32_vs_fp64_max_rel_err": err32,
-           "kernels": kernel_table(hm.hm_trace_read(), 1)}
-    hm.hm_free(A)
-    hm.hm_free(tree)
+def run_workload(name):
+    import torch
+    import paper_1806_11558_gb300 as hm
+    from paper_1806_11558_gb300 import build as hb
+    hb.build()
+    fn = {"batching": run_batching, "differentiation": run_differentiation,
+          "blockmv": run_blockmv, "blockmv7": lambda t, h: run_blockmv(t, h, "precision")}[name]
+    ck = Clocks(torch.cuda.current_device())
+    ck.start()
+    out = fn(torch, hm)
+    out["clocks"] = ck.stop()
     return out
 
 
@@ -599,7 +819,8 @@ def run_batching(torch, hm):
            "tree_s": e[0].elapsed_time(e[1]) / 1e3, "assemble_s": e[1].elapsed_time(e[2]) / 1e3,
            "aca_s": mi["s_aca"], "nearfield_s": mi["s_nearfield"], "solve_s": e[3].elapsed_time(e[4]) / 1e3,
            "systems": 256, "lockstep_iters": info.iters, "refine_steps": info.refine_steps, **warm,
-           "max_rel_resid": info.rel_resid, "kernels": kernel_table(hm.hm_trace_read(), 1)}
+           "max_rel_resid": info.rel_resid, "aca_small_sum": mi["aca_small_sum"],
+           "kernels": kernel_table(hm.hm_trace_read(), 1)}
     hm.hm_free(A)
     hm.hm_free(tree)
     return out
@@ -695,20 +916,6 @@ def run_blockmv(torch, hm, case="bumped6"):
     return out
 
 
-def run_workload(name):
-    import torch
-    import paper_1806_11558_gb300 as hm
-    from paper_1806_11558_gb300 import build as hb
-    hb.build()
-    fn = {"large": run_large, "batching": run_batching, "differentiation": run_differentiation,
-          "blockmv": run_blockmv, "blockmv7": lambda t, h: run_blockmv(t, h, "precision")}[name]
-    ck = Clocks(torch.cuda.current_device())
-    ck.start()
-    out = fn(torch, hm)
-    out["clocks"] = ck.stop()
-    return out
-
-
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -716,25 +923,18 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--case", default="precision",
-                    help="mesh recipe of meshgen.config (default: the precision workload); other cases are "
-                         "for profiling and parity runs, not bench lines")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the precision workload's secondary object")
+    ap.add_argument("--case", default="large",
+                    help="workload: large (default, the headline), precision (the level-7 one-source workload); "
+                         "other meshgen recipes run with the one-source step for profiling and parity runs")
     ap.add_argument("--profile-step", action="store_true",
                     help="run exactly one step (no warm-up, no extras) and print its phase times")
-    ap.add_argument("--workload", default=None, choices=["large", "batching", "differentiation", "blockmv", "blockmv7"],
+    ap.add_argument("--workload", default=None, choices=["batching", "differentiation", "blockmv", "blockmv7"],
                     help="measure one of the other workloads once and print its numbers (not a bench line)")
     args = ap.parse_args()
     if args.workload:
         print(json.dumps(run_workload(args.workload)))
         return
-    global CASE
-    CASE = args.case
-    if CASE != "precision":
-        # other meshes run with their own recipe's tree and ACA parameters
-        import meshgen
-        cfg = meshgen.config(CASE)
-        WORKLOAD.update(workload="%s (profiling / parity case)" % CASE, panels=int(cfg["T"].shape[0]),
-                        leaf_size=cfg["leaf_size"], eta=cfg["eta"], aca_eps=cfg["aca_eps"])
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count()))
@@ -743,22 +943,41 @@ def main():
             return
         print(json.dumps(run_reference(args, rank, world)))
         return
+    import torch
+    import paper_1806_11558_gb300 as hm
+    from paper_1806_11558_gb300 import build as hb
     if world > 1:
-        import torch
         import torch.distributed as dist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         dist.init_process_group("nccl")
-    out, extra = run_ours(args, rank, world)
+    hb.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    if args.case == "large":
+        out, extra = run_large(args, world, hm, torch)
+    else:
+        W = dict(PRECISION)
+        if args.case != "precision":
+            import meshgen
+            cfg = meshgen.config(args.case)
+            W.update(workload="%s (profiling / parity case)" % args.case, case=args.case,
+                     panels=int(cfg["T"].shape[0]), leaf_size=cfg["leaf_size"], eta=cfg["eta"],
+                     aca_eps=cfg["aca_eps"])
+        out, extra = run_single(args, world, hm, torch, W=W, case=args.case)
     if args.profile_step:
         if rank == 0:
             print(json.dumps(out))
         return
-    V, T, last = extra
+    V, T, solve_info = extra
+    if args.case == "large" and not args.no_secondary:
+        hm.hm_trim()
+        mp = {k: solve_info["fma_peaks"][k] for k in ("fp64_tflops", "fp32_tflops", "sm_mhz", "how")}
+        out["secondary"] = run_single(args, world, hm, torch, extras=False, fma_peaks=mp)
     if rank == 0:
-        if not args.no_cpu_baseline:
-            v, sample, parts = cpu_oracle_step(V, T, iters=last["iters_fp64"] + last["iters_mixed"])
-            out["cpu_baseline"] = {"value": v, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
-                                   "sample": sample, "parts": parts}
+        if not args.no_cpu_baseline and world == 1:
+            v, wall, sample, parts = cpu_oracle_step(solve_info["case"], V, T, solve_info["W"],
+                                                     solve_info["n_systems"], solve_info["iters_fp64"])
+            out["cpu_baseline"] = {"value": v, "unit": "s", "cores": int(os.environ["OMP_NUM_THREADS"]),
+                                   "kind": "oracle", "value_is_estimate": True, "sample": sample, "parts": parts}
         print(json.dumps(out))
     if world > 1:
         import torch.distributed as dist

@@ -377,6 +377,18 @@ HM_API hm_status hm_matrix_add_copy(const hm_matrix *A, hm_dtype dtype, hm_strea
  * the device. */
 HM_API void hm_trim(void);
 
+/* Measured FMA throughput of the current device, in TFLOP/s (an FMA counts
+ * 2 flops): kind = HM_F64 (DFMA) or HM_F32 (FFMA).  A kernel fills every SM
+ * with threads that each run eight independent FMA chains; the best of three
+ * timed launches (after one warm-up launch, CUDA events on `stream`, about
+ * 20-50 ms each) is returned.  The paper has no counterpart: the figures are
+ * the denominators of the ALU rooflines of this library's kernels (the
+ * nominal FP64 rate of unit counts x clock is above what this part's FP64
+ * pipe delivers).  The result depends on the SM clock during the call.
+ * Synchronises the stream.  Errors: HM_EINVAL for a NULL pointer or another
+ * kind. */
+HM_API hm_status hm_measure_fma_peak(hm_dtype kind, double *tflops, hm_stream_t stream);
+
 /* Tree introspection (synchronises the stream of the tree). */
 HM_API hm_status hm_tree_get_info(const hm_tree *tree, hm_tree_info *info);
 

@@ -24,7 +24,7 @@ EXPORTED = ["hm_build_tree", "hm_assemble", "hm_load_vector", "hm_matvec", "hm_s
             "hm_tree_get_info", "hm_tree_get_perm", "hm_tree_get_leaves", "hm_matrix_get_info",
             "hm_matrix_export", "hm_last_error", "hm_kernel_launches", "hm_matvec_noalloc", "hm_matrix_get_block",
             "hm_trace_enable", "hm_trace_read", "hm_potential", "hm_matvec_block", "hm_build_forest",
-            "hm_load_vector_geom", "hm_trim", "hm_matrix_add_copy"]
+            "hm_load_vector_geom", "hm_trim", "hm_matrix_add_copy", "hm_measure_fma_peak"]
 
 
 class HMError(RuntimeError):
@@ -109,6 +109,7 @@ def lib():
             "hm_trace_enable": [I32],
             "hm_potential": [P, P, I64, I32, P, P, P],
             "hm_trace_read": [P, I32, P],
+            "hm_measure_fma_peak": [I, P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -134,6 +135,13 @@ def hm_last_error() -> str:
 
 def hm_kernel_launches() -> int:
     return int(lib().hm_kernel_launches())
+
+
+def hm_measure_fma_peak(kind=HM_F64, stream=None) -> float:
+    """Measured FMA throughput of the current device in TFLOP/s (HM_F64 or HM_F32)."""
+    out = ctypes.c_double(0.0)
+    _check(lib().hm_measure_fma_peak(int(kind), ctypes.byref(out), _stream(stream)))
+    return out.value
 
 
 def hm_trace_enable(on: bool = True):

@@ -44,6 +44,7 @@ void potential_impl(const hm_tree *tr, const double *pts, int64_t K, int trans, 
                     cudaStream_t s);
 void matvec_noalloc(const hm_matrix *A, int32_t nrhs, hm_dtype prec, const double *x, double *y, double alpha,
                     double beta, cudaStream_t s);
+double measure_fma_peak(hm_dtype kind, cudaStream_t s);
 }  // namespace hm
 
 using namespace hm;
@@ -342,6 +343,14 @@ hm_status hm_tree_get_leaves(const hm_tree *tree, int32_t dense, int32_t *d_out,
         if (d_out && capacity >= n && n > 0)
             HM_CUDA_CHECK(cudaMemcpy(d_out, dense ? tree->dense.p : tree->adm.p, sizeof(int32_t) * 4 * n,
                                      cudaMemcpyDeviceToDevice));
+    });
+}
+
+hm_status hm_measure_fma_peak(hm_dtype kind, double *tflops, hm_stream_t stream) {
+    return guard([&] {
+        if (!tflops) fail(HM_EINVAL, "NULL argument");
+        if (kind != HM_F64 && kind != HM_F32) fail(HM_EINVAL, "kind must be HM_F64 or HM_F32");
+        *tflops = measure_fma_peak(kind, (cudaStream_t)stream);
     });
 }
 

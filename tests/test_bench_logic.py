@@ -55,8 +55,52 @@ def test_roofline_entry_fractions():
     assert r["frac"] == pytest.approx(r["achieved"] / 6000.0)
     r = bench.roofline_entry("row_kernel.f64", kt, w["row_kernel.f64"], peaks, "measured")
     assert r["bound"] == "alu" and r["peak"] == bench.FP64_PEAK_TFLOPS
-    # traffic only while the kernel source matches the recorded capture
+    # traffic only for the workload and kernel source of the recorded capture
+    assert r["traffic"] is None
+    r = bench.roofline_entry("row_kernel.f64", kt, w["row_kernel.f64"], dict(peaks, workload="precision"), "m")
     assert r["traffic"] == bench.TRAFFIC["row_kernel.f64"]["bytes_per_launch"]
     r = bench.roofline_entry("aca_kernel", kt, w["aca_kernel"], peaks, "measured")
     assert r["peak"] == bench.FP32_PEAK_TFLOPS
     assert r["kernel_evaluations_per_s"] == pytest.approx(3000 * bench.PAIRS_PER_ENTRY / 2e-3)
+
+
+def test_measured_alu_peaks_are_the_denominators():
+    w = _work()
+    peaks = {"hbm_gbs": 6000.0, "fp64_tflops": 1.0, "fp32_tflops": 70.0}
+    kt = {"ms_per_launch": 2.0, "launches_per_step": 1.0}
+    r = bench.roofline_entry("row_kernel.f64", kt, w["row_kernel.f64"], peaks, "measured")
+    assert r["peak"] == 1.0 and "measured" in r["peak_source"]
+    assert r["frac"] == pytest.approx(2.0 * 1800 / 2e-3 / 1e12)
+    r = bench.roofline_entry("nearfield_kernel", kt, w["nearfield_kernel"], peaks, "measured")
+    assert r["peak"] == 70.0
+
+
+def test_multi_rhs_product_bytes():
+    w = _work()
+    K = 2.0 * 10
+    # 16 right-hand sides: X / t rows as BF16 pairs (64 B), Y rows in FP64 (128 B)
+    assert w["row_mrhs_kernel.f32"] == ("hbm", 4.0 * 1800 + 64.0 * (40 + K) + 128.0 * 40, "byte")
+    assert w["row_mrhs_kernel.bf16"][1] == 4.0 * 800 + 2.0 * 1000 + 64.0 * (40 + K) + 128.0 * 40
+    assert w["col_bcp_kernel.f32"][1] == 4.0 * 1500 + 64.0 * (40 + K)
+    assert w["col_bcp_kernel.bf16"][1] == 2.0 * 1500 + 64.0 * (40 + K)
+
+
+def test_dominant_kernel_is_the_longest_with_known_work():
+    mi = {"u_entries": 1000, "lr_entries": 2500, "dense_entries": 800, "mean_rank": 2.0, "aca_entries": 3000}
+    ti = {"n_adm": 10, "n_clusters": 15}
+    leaves = np.array([[0, 20, 20, 40], [20, 40, 0, 20]], dtype=np.int64)
+    trace = {"batch_dots": (100, 500.0), "row_mrhs_kernel.f32": (10, 300.0), "aca_kernel": (1, 100.0)}
+    dom, others, kernels = bench.rooflines(trace, 1, mi, ti, leaves, 40, {"hbm_gbs": 6000.0}, "measured")
+    assert dom["kernel"] == "row_mrhs_kernel.f32"
+    assert set(others) == {"aca_kernel"}
+    assert list(kernels) == ["batch_dots", "row_mrhs_kernel.f32", "aca_kernel"]
+
+
+def test_cpu_oracle_sample_estimate_runs_on_a_small_mesh():
+    import meshgen
+    V, T = meshgen.icosphere(3)
+    W = dict(leaf_size=32, eta=1.5, ss_order=8, aca_eps=1e-6, aca_kmax=64)
+    est, wall, sample, parts = bench.cpu_oracle_step("test_level3", V, T, W, 2, 10, dense_sample=50)
+    assert est > 0 and wall > 0
+    assert abs(est - (parts["tree_s"] + parts["nearfield_s"] + parts["aca_s"] + parts["solve_s"])) < 1e-9 * est
+    assert "2 systems x 10 Arnoldi steps" in sample

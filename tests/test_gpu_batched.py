@@ -68,3 +68,36 @@ def test_batched_zero_rhs_column(sphere):
                      inner_tol=1e-2, max_refine=60, max_iter=5000)
     assert info.status == 0
     assert np.all(X[1] == 0.0)
+
+
+def _oracle_solutions(orc, g, B, tol):
+    """oracle.gmres on the exported FP64 operator, one system at a time."""
+    perm = g.perm()
+    ex = g.export()
+    dl, al = g.leaves(True), g.leaves(False)
+
+    def mv(x):
+        ym = orc.hmatvec_raw(g.n, dl, ex["dense_off"], ex["dense"], al, ex["rank"], ex["u_off"], ex["w_off"],
+                             ex["uw"], x[perm])
+        y = np.empty(g.n)
+        y[perm] = ym
+        return y
+
+    return np.array([orc.gmres(mv, B[r], restart=60, tol=tol, maxiter=20000)[0] for r in range(B.shape[0])])
+
+
+@pytest.mark.parametrize("form", ["fp64", "refined_bf16", "refined_f32"])
+def test_batched_solutions_match_the_oracle_gmres(orc, sphere, form):
+    g = sphere
+    B = _rhs(g, 17)  # one full pass of 16 right-hand sides and a ragged one
+    kw = dict(rel_tol=1e-12, restart=60, precond=1, batched=1, max_iter=5000)
+    if form != "fp64":
+        kw.update(refine=1, inner_dtype=2 if form == "refined_bf16" else 1,
+                  inner_tol=1e-2 if form == "refined_bf16" else 1e-4, max_refine=60)
+        if form == "refined_f32":
+            g.hm.hm_matrix_add_copy(g.A, 1)
+    X, info = _solve(g, B, **kw)
+    assert info.status == 0 and info.rel_resid <= 1e-12
+    Xo = _oracle_solutions(orc, g, B, 1e-12)
+    err = np.linalg.norm(X - Xo, axis=1) / np.linalg.norm(Xo, axis=1)
+    assert err.max() <= 1e-8, err
