@@ -330,11 +330,14 @@ HM_API hm_status hm_matvec_block(const hm_matrix *A, int32_t nrhs, hm_dtype prec
  *  memory is allocated or freed by the call.
  *  Limit: 2 n + K + P doubles plus n + K + P floats must fit in 2,097,152
  *  doubles (K = sum of the ACA ranks, P = the column-cluster partials of the
- *  low-rank projections, about K times the mean number of leaf clusters an
- *  admissible block spans); larger problems get HM_EINVAL with the required
- *  size in hm_last_error().
+ *  low-rank projections of the forward product, about K times the mean
+ *  number of leaf clusters an admissible block spans); larger problems get
+ *  HM_EINVAL with the required size in hm_last_error().  trans = 1 is
+ *  rejected with HM_EINVAL.
  *  The first call on a device looks up that array's device address (with the
- *  device current); make that first call before any stream capture.
+ *  device current); make that first call before any stream capture.  The
+ *  address is looked up again when the device's context has changed since
+ *  (a cudaDeviceReset makes a new one).
  *  All calls share the array and it keeps the last call's contents: calls
  *  whose work overlaps on the GPU (different streams or host threads) race.
  *  The call is stream-ordered and does not synchronise; d_y is complete when
@@ -356,6 +359,34 @@ HM_API hm_status hm_matvec_noalloc(const hm_matrix *A, int32_t trans, int32_t nr
 HM_API hm_status hm_solve(const hm_matrix *A, int32_t trans, int32_t nrhs, const double *d_b, double *d_x,
                    const hm_solve_params *params, hm_stream_t stream, hm_solve_info *info);
 
+/* Solves the system of the column-scaled operator A(c) = H diag(c): op(A(c)) x = b,
+ * i.e. H diag(c) x = b (trans = 0) or diag(c) H^T x = b (trans = 1).  With
+ * u_j = c_j x_j the density of panel j, A(c) x is the Galerkin single-layer
+ * operator (Sec. 2.2, Eq. 4) applied to a density whose panel values are
+ * scaled by c: the parametrisation whose gradient with respect to c the
+ * adjoint method needs.  The scaling is applied by the library (trans = 0:
+ * H y = b is solved, then x = y / c; trans = 1: H^T x = b / c is solved).
+ *  d_c : [n] per-panel coefficients (device, original order), all nonzero
+ *        (not checked: a zero gives inf / NaN entries).
+ *  Other arguments, results and errors as hm_solve (the batched form is for
+ *  trans = 0); on HM_ENOCONV the best x is scaled and returned too. */
+HM_API hm_status hm_solve_scaled(const hm_matrix *A, int32_t trans, int32_t nrhs, const double *d_c, const double *d_b,
+                                 double *d_x, const hm_solve_params *params, hm_stream_t stream, hm_solve_info *info);
+
+/* The product with diagonal scalings on both sides:
+ *   y = alpha * diag(l) op(H) diag(r) x + beta * y
+ * for nrhs right-hand sides [nrhs][n] (original order; op as in hm_matvec).
+ * d_left (l) and d_right (r) are [n] device vectors, each NULL for the
+ * identity.  Products of the column-scaled operator A(c) = H diag(c) take
+ * d_right = c (A(c) x) or d_left = c with trans = 1 (A(c)^T x); the
+ * gradient of a solution functional with respect to c,
+ * dL/dc_j = -alpha_j (H^T lam)_j, takes trans = 1, d_left = alpha, x = lam,
+ * alpha = -1.  Stream-ordered (working vectors from the stream-ordered pool).
+ * Errors as hm_matvec. */
+HM_API hm_status hm_matvec_scaled(const hm_matrix *A, int32_t trans, int32_t nrhs, hm_dtype prec, const double *d_left,
+                                  const double *d_right, const double *d_x, double *d_y, double alpha, double beta,
+                                  hm_stream_t stream);
+
 /* Frees an hm_tree or hm_matrix handle (NULL is a no-op).  Device buffers of
  * 1 MiB or more are not unmapped but kept by the library for its later
  * allocations (unmapping costs ~0.4 ms per GB), up to a quarter of the
@@ -376,6 +407,30 @@ HM_API hm_status hm_matrix_add_copy(const hm_matrix *A, hm_dtype dtype, hm_strea
  * (for callers that need the memory for other allocations).  Synchronises
  * the device. */
 HM_API void hm_trim(void);
+
+/* Limit, in SM clock cycles, of the library's bounded device-side waits
+ * (the wait of the near-field assembly for its TMA-staged panel tiles), for
+ * the calls that follow, from any thread.  cycles >= 0 sets it; cycles < 0
+ * restores the default of 4e9 cycles (about 2 s at 2 GHz).  A wait that
+ * reaches the limit records the failure and makes the call return
+ * HM_ETIMEOUT; before its thread block exits it waits again, with the
+ * default limit, for the copies it started, so that no copy lands in shared
+ * memory after the block has left.  0 gives up before the first poll: every
+ * assembly with dense leaves then returns HM_ETIMEOUT (a hook for testing
+ * that path).  After HM_ETIMEOUT the assembly's matrix is not created and
+ * the device context stays usable; if the second, default-limit wait also
+ * gave up (a copy that never completed) the context should be treated as
+ * suspect.  The paper has no counterpart.  Always HM_OK. */
+HM_API hm_status hm_set_wait_limit(int64_t cycles);
+
+/* Injected allocation failure, for testing the error paths: with n > 0 the
+ * n-th device allocation the library makes from now on (from any thread)
+ * fails as an exhausted cudaMalloc would, so the call that makes it returns
+ * HM_ENOMEM, releasing what it had allocated; the injection then disarms
+ * itself.  n = 0 disarms it.  The environment variable HM_FAULT_INJECT=<n>
+ * arms it when the library is loaded.  The paper has no counterpart.
+ * Always HM_OK. */
+HM_API hm_status hm_set_fault_injection(int64_t n);
 
 /* Measured FMA throughput of the current device, in TFLOP/s (an FMA counts
  * 2 flops): kind = HM_F64 (DFMA) or HM_F32 (FFMA).  A kernel fills every SM

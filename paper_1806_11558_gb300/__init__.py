@@ -24,7 +24,8 @@ EXPORTED = ["hm_build_tree", "hm_assemble", "hm_load_vector", "hm_matvec", "hm_s
             "hm_tree_get_info", "hm_tree_get_perm", "hm_tree_get_leaves", "hm_matrix_get_info",
             "hm_matrix_export", "hm_last_error", "hm_kernel_launches", "hm_matvec_noalloc", "hm_matrix_get_block",
             "hm_trace_enable", "hm_trace_read", "hm_potential", "hm_matvec_block", "hm_build_forest",
-            "hm_load_vector_geom", "hm_trim", "hm_matrix_add_copy", "hm_measure_fma_peak"]
+            "hm_load_vector_geom", "hm_trim", "hm_matrix_add_copy", "hm_measure_fma_peak",
+            "hm_solve_scaled", "hm_matvec_scaled", "hm_set_wait_limit", "hm_set_fault_injection"]
 
 
 class HMError(RuntimeError):
@@ -110,6 +111,10 @@ def lib():
             "hm_potential": [P, P, I64, I32, P, P, P],
             "hm_trace_read": [P, I32, P],
             "hm_measure_fma_peak": [I, P, P],
+            "hm_solve_scaled": [P, I32, I32, P, P, P, P, P, P],
+            "hm_matvec_scaled": [P, I32, I32, I, P, P, P, P, D, D, P],
+            "hm_set_wait_limit": [I64],
+            "hm_set_fault_injection": [I64],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -135,6 +140,16 @@ def hm_last_error() -> str:
 
 def hm_kernel_launches() -> int:
     return int(lib().hm_kernel_launches())
+
+
+def hm_set_wait_limit(cycles: int = -1):
+    """Limit (SM clock cycles) of the library's bounded device waits; < 0 restores the default."""
+    _check(lib().hm_set_wait_limit(int(cycles)))
+
+
+def hm_set_fault_injection(n: int = 0):
+    """Fail the n-th device allocation of the library from now on (HM_ENOMEM); 0 disarms."""
+    _check(lib().hm_set_fault_injection(int(n)))
 
 
 def hm_measure_fma_peak(kind=HM_F64, stream=None) -> float:
@@ -288,6 +303,33 @@ def hm_solve(A, b, x, trans=0, restart=30, max_iter=3000, rel_tol=1e-10, refine=
         return info
     _check(st)
     return info
+
+
+def hm_solve_scaled(A, b, c, x, trans=0, restart=30, max_iter=3000, rel_tol=1e-10, refine=0, max_refine=20,
+                    inner_tol=1e-4, inner_dtype=HM_F32, precond=0, batched=0, use_graph=0, stall_ratio=0.5,
+                    stream=None, raise_on_noconv=True):
+    """Solves op(H diag(c)) x = b (c: CUDA float64 [n]); returns the SolveInfo."""
+    import torch
+    nrhs = 1 if b.dim() == 1 else b.shape[0]
+    prm = SolveParams(int(restart), int(max_iter), float(rel_tol), int(refine), int(max_refine), float(inner_tol),
+                      int(inner_dtype), int(precond), int(batched), int(use_graph), float(stall_ratio))
+    info = SolveInfo()
+    st = lib().hm_solve_scaled(A, int(trans), nrhs, _ptr(c, torch.float64), _ptr(b, torch.float64),
+                               _ptr(x, torch.float64), ctypes.byref(prm), _stream(stream), ctypes.byref(info))
+    if st == HM_ENOCONV and not raise_on_noconv:
+        return info
+    _check(st)
+    return info
+
+
+def hm_matvec_scaled(A, x, y, trans=0, prec=HM_F64, left=None, right=None, alpha=1.0, beta=0.0, stream=None):
+    """y = alpha diag(left) op(H) diag(right) x + beta y (left / right: CUDA float64 [n] or None)."""
+    import torch
+    nrhs = 1 if x.dim() == 1 else x.shape[0]
+    _check(lib().hm_matvec_scaled(A, int(trans), nrhs, int(prec), _ptr(left, torch.float64),
+                                  _ptr(right, torch.float64), _ptr(x, torch.float64), _ptr(y, torch.float64),
+                                  float(alpha), float(beta), _stream(stream)))
+    return y
 
 
 def hm_matrix_add_copy(A, dtype, stream=None):

@@ -45,6 +45,10 @@ void potential_impl(const hm_tree *tr, const double *pts, int64_t K, int trans, 
 void matvec_noalloc(const hm_matrix *A, int32_t nrhs, hm_dtype prec, const double *x, double *y, double alpha,
                     double beta, cudaStream_t s);
 double measure_fma_peak(hm_dtype kind, cudaStream_t s);
+void div_diag(const double *a, const double *d, int64_t n, int nrhs, double *out, cudaStream_t s);
+void mul_diag(const double *a, const double *d, int64_t n, int nrhs, double *out, cudaStream_t s);
+void axpby_diag(const double *v, const double *d, int64_t n, int nrhs, double alpha, double beta, double *y,
+                cudaStream_t s);
 }  // namespace hm
 
 using namespace hm;
@@ -68,6 +72,32 @@ template <class F> static hm_status guard(F &&f) {
 
 static bool is_tree(const void *p) { return p && static_cast<const hm_tree *>(p)->magic == HM_TREE_MAGIC; }
 static bool is_matrix(const void *p) { return p && static_cast<const hm_matrix *>(p)->magic == HM_MATRIX_MAGIC; }
+
+static void check_matvec_args(const hm_matrix *A, int32_t trans, int32_t nrhs, hm_dtype prec, const double *d_x,
+                              const double *d_y) {
+    if (!is_matrix(A)) fail(HM_EINVAL, "not a matrix handle");
+    if (!d_x || !d_y) fail(HM_EINVAL, "NULL argument");
+    if (nrhs < 1) fail(HM_EINVAL, "nrhs must be >= 1");
+    if (trans != 0 && trans != 1) fail(HM_EINVAL, "trans must be 0 or 1");
+    if (prec < HM_F64 || prec > HM_BF16) fail(HM_EINVAL, "bad precision");
+    if (prec == HM_F32 && !A->up32.p) fail(HM_EINVAL, "FP32 copies were not assembled");
+    if (prec == HM_BF16 && !A->upbf.p) fail(HM_EINVAL, "BF16 factors were not assembled");
+}
+
+// y = alpha op(H) x + beta y, [nrhs][n] in original order, one right-hand side at a time
+static void matvec_orig(const hm_matrix *A, int32_t trans, int32_t nrhs, hm_dtype prec, const double *d_x,
+                        double *d_y, double alpha, double beta, cudaStream_t s) {
+    const int64_t n = A->tree->n;
+    SBuf work;
+    work.alloc(sizeof(double) * matvec_work_doubles(A), s);
+    const MatvecWork w = matvec_work_at(A, work.as<double>());
+    if (trans) build_transposed(A, s);
+    for (int r = 0; r < nrhs; ++r) {
+        permute_to_morton(A->tree, d_x + (int64_t)r * n, w.xm, s);
+        matvec_morton(A, prec, w, s, trans == 1);
+        permute_from_morton(A->tree, w.ym, alpha, beta, d_y + (int64_t)r * n, s);
+    }
+}
 
 extern "C" {
 
@@ -188,24 +218,28 @@ hm_status hm_potential(const hm_tree *tree, const double *d_points, int64_t n_po
 hm_status hm_matvec(const hm_matrix *A, int32_t trans, int32_t nrhs, hm_dtype prec, const double *d_x, double *d_y,
                     double alpha, double beta, hm_stream_t stream) {
     return guard([&] {
-        if (!is_matrix(A)) fail(HM_EINVAL, "not a matrix handle");
-        if (!d_x || !d_y) fail(HM_EINVAL, "NULL argument");
-        if (nrhs < 1) fail(HM_EINVAL, "nrhs must be >= 1");
-        if (trans != 0 && trans != 1) fail(HM_EINVAL, "trans must be 0 or 1");
-        if (prec == HM_F32 && !A->up32.p) fail(HM_EINVAL, "FP32 copies were not assembled");
-        if (prec == HM_BF16 && !A->upbf.p) fail(HM_EINVAL, "BF16 factors were not assembled");
-        if (prec < HM_F64 || prec > HM_BF16) fail(HM_EINVAL, "bad precision");
+        check_matvec_args(A, trans, nrhs, prec, d_x, d_y);
+        matvec_orig(A, trans, nrhs, prec, d_x, d_y, alpha, beta, (cudaStream_t)stream);
+    });
+}
+
+hm_status hm_matvec_scaled(const hm_matrix *A, int32_t trans, int32_t nrhs, hm_dtype prec, const double *d_left,
+                           const double *d_right, const double *d_x, double *d_y, double alpha, double beta,
+                           hm_stream_t stream) {
+    return guard([&] {
+        check_matvec_args(A, trans, nrhs, prec, d_x, d_y);
         cudaStream_t s = (cudaStream_t)stream;
         const int64_t n = A->tree->n;
-        SBuf work;
-        work.alloc(sizeof(double) * matvec_work_doubles(A), s);
-        const MatvecWork w = matvec_work_at(A, work.as<double>());
-        if (trans) build_transposed(A, s);
-        for (int r = 0; r < nrhs; ++r) {
-            permute_to_morton(A->tree, d_x + (int64_t)r * n, w.xm, s);
-            matvec_morton(A, prec, w, s, trans == 1);
-            permute_from_morton(A->tree, w.ym, alpha, beta, d_y + (int64_t)r * n, s);
+        SBuf xs, ys;
+        const double *xin = d_x;
+        if (d_right) {
+            xs.alloc(sizeof(double) * n * nrhs, s);
+            mul_diag(d_x, d_right, n, nrhs, xs.as<double>(), s);
+            xin = xs.as<double>();
         }
+        ys.alloc(sizeof(double) * n * nrhs, s);
+        matvec_orig(A, trans, nrhs, prec, xin, ys.as<double>(), 1.0, 0.0, s);
+        axpby_diag(ys.as<double>(), d_left, n, nrhs, alpha, beta, d_y, s);
     });
 }
 
@@ -283,6 +317,37 @@ hm_status hm_solve(const hm_matrix *A, int32_t trans, int32_t nrhs, const double
     return g != HM_OK ? g : result;
 }
 
+hm_status hm_solve_scaled(const hm_matrix *A, int32_t trans, int32_t nrhs, const double *d_c, const double *d_b,
+                          double *d_x, const hm_solve_params *params, hm_stream_t stream, hm_solve_info *info) {
+    hm_status g = guard([&] {
+        if (!is_matrix(A)) fail(HM_EINVAL, "not a matrix handle");
+        if (!d_c || !d_b || !d_x || !params) fail(HM_EINVAL, "NULL argument");
+        if (nrhs < 1) fail(HM_EINVAL, "nrhs must be >= 1");
+        if (trans != 0 && trans != 1) fail(HM_EINVAL, "trans must be 0 or 1");
+    });
+    if (g != HM_OK) return g;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = A->tree->n;
+    if (trans == 0) {
+        // H diag(c) x = b  <=>  H y = b, x = y / c
+        const hm_status st = hm_solve(A, 0, nrhs, d_b, d_x, params, stream, info);
+        if (st != HM_OK && st != HM_ENOCONV) return st;
+        const std::string msg = last_error_cstr();
+        g = guard([&] { div_diag(d_x, d_c, n, nrhs, d_x, s); });
+        if (g != HM_OK) return g;
+        set_last_error(msg);
+        return st;
+    }
+    // (H diag(c))^T x = diag(c) H^T x = b  <=>  H^T x = b / c
+    SBuf bc;
+    g = guard([&] {
+        bc.alloc(sizeof(double) * n * nrhs, s);
+        div_diag(d_b, d_c, n, nrhs, bc.as<double>(), s);
+    });
+    if (g != HM_OK) return g;
+    return hm_solve(A, 1, nrhs, bc.as<double>(), d_x, params, stream, info);
+}
+
 hm_status hm_matrix_add_copy(const hm_matrix *A, hm_dtype dtype, hm_stream_t stream) {
     return guard([&] {
         if (!is_matrix(A)) fail(HM_EINVAL, "not a matrix handle");
@@ -344,6 +409,16 @@ hm_status hm_tree_get_leaves(const hm_tree *tree, int32_t dense, int32_t *d_out,
             HM_CUDA_CHECK(cudaMemcpy(d_out, dense ? tree->dense.p : tree->adm.p, sizeof(int32_t) * 4 * n,
                                      cudaMemcpyDeviceToDevice));
     });
+}
+
+hm_status hm_set_wait_limit(int64_t cycles) {
+    set_wait_limit((long long)cycles);
+    return HM_OK;
+}
+
+hm_status hm_set_fault_injection(int64_t n) {
+    set_fault_injection((long long)n);
+    return HM_OK;
 }
 
 hm_status hm_measure_fma_peak(hm_dtype kind, double *tflops, hm_stream_t stream) {

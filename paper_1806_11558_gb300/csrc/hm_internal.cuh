@@ -133,6 +133,17 @@ struct DBuf {
 };
 void cache_trim();  // frees every cached block
 
+// Injected allocation failures (hm_set_fault_injection, HM_FAULT_INJECT): every
+// device allocation of the library (DBuf, SBuf) passes this checkpoint first;
+// the armed one throws HM_ENOMEM as a failed cudaMalloc would.
+void fault_checkpoint(size_t nbytes);
+void set_fault_injection(long long n);
+
+// Limit, in SM clock cycles, of the device-side bounded waits (hm_set_wait_limit).
+constexpr long long WAIT_LIMIT_DEFAULT = 4000000000LL;  // ~2 s at 2 GHz
+long long wait_limit();
+void set_wait_limit(long long cycles);
+
 // Stream-ordered scratch (cudaMallocAsync / cudaFreeAsync on one stream): the
 // memory is usable by work queued on that stream after the allocation and is
 // returned to the pool after the work queued before the release, so a call
@@ -150,6 +161,7 @@ struct SBuf {
         if (p) cudaFreeAsync(p, s);
         p = nullptr;
         s = stream;
+        fault_checkpoint(nbytes);
         HM_CUDA_CHECK(cudaMallocAsync(&p, nbytes ? nbytes : 16, stream));
     }
     template <class T> T *as() const { return static_cast<T *>(p); }

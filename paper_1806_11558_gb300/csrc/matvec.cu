@@ -523,15 +523,27 @@ void matvec_morton(const hm_matrix *A, hm_dtype prec, const MatvecWork &w, cudaS
 // Device workspace of hm_matvec / the solver: xm, ym [n], t [K], p [P]
 // doubles, then x32 [n], t32 [K], p32 [P] floats (K = sum of ranks, P = the
 // partial projections of the column panels).
-int64_t matvec_work_doubles(const hm_matrix *A) {
-    const int64_t n = A->tree->n, r = std::max<int64_t>(A->total_rank, 1),
-                  q = std::max<int64_t>(std::max(A->n_partials, A->n_partials_t), 1);
+// Working vectors of a product whose partial-projection vector has q entries
+// (q = P for the forward product, max(P, P_T) to serve both directions).
+static int64_t work_doubles(const hm_matrix *A, int64_t q) {
+    const int64_t n = A->tree->n, r = std::max<int64_t>(A->total_rank, 1);
+    q = std::max<int64_t>(q, 1);
     return 2 * n + r + q + (n + 1) / 2 + (r + 1) / 2 + (q + 1) / 2;
 }
 
+static MatvecWork work_at(const hm_matrix *A, double *base, int64_t q);
+
+int64_t matvec_work_doubles(const hm_matrix *A) {
+    return work_doubles(A, std::max(A->n_partials, A->n_partials_t));
+}
+
 MatvecWork matvec_work_at(const hm_matrix *A, double *base) {
-    const int64_t n = A->tree->n, r = std::max<int64_t>(A->total_rank, 1),
-                  q = std::max<int64_t>(std::max(A->n_partials, A->n_partials_t), 1);
+    return work_at(A, base, std::max(A->n_partials, A->n_partials_t));
+}
+
+static MatvecWork work_at(const hm_matrix *A, double *base, int64_t q) {
+    const int64_t n = A->tree->n, r = std::max<int64_t>(A->total_rank, 1);
+    q = std::max<int64_t>(q, 1);
     MatvecWork w;
     w.xm = base;
     w.ym = base + n;
@@ -943,22 +955,45 @@ static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_MAX_DOUBLES];
 
 constexpr int NOALLOC_MAX_DEVICES = 64;
 static void *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+static CUcontext g_noalloc_ctx[NOALLOC_MAX_DEVICES] = {};
 static std::mutex g_noalloc_mutex;
+
+// The current driver context (resolved through the runtime's driver entry
+// point, like the tensor-map encoder): a device reset makes a new primary
+// context, in which the array has a new address.
+static CUcontext current_context() {
+    typedef CUresult (*PFN_ctxGetCurrent)(CUcontext *);
+    static PFN_ctxGetCurrent fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !p)
+            fail(HM_ECUDA, "cuCtxGetCurrent is not available from the driver");
+        fn = reinterpret_cast<PFN_ctxGetCurrent>(p);
+    }
+    CUcontext c = nullptr;
+    if (fn(&c) != CUDA_SUCCESS) fail(HM_ECUDA, "cuCtxGetCurrent failed");
+    return c;
+}
 
 // Device address of the scratch array on the current device.  The host-side
 // symbol is only a stand-in; the address is looked up once per device (with
-// that device current) on the first call.
+// that device current) on the first call, and again when the device's
+// context has changed since (after a cudaDeviceReset).
 static double *noalloc_scratch() {
     int dev = 0;
     HM_CUDA_CHECK(cudaGetDevice(&dev));
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) fail(HM_EINVAL, "device index %d out of range", dev);
+    const CUcontext ctx = current_context();  // NULL in a thread where the runtime has not made it current yet
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_ptr[dev]) {
+    if (!g_noalloc_ptr[dev] || !ctx || g_noalloc_ctx[dev] != ctx) {
         void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // makes the context current
         if (e != cudaSuccess || !p)
             fail(HM_ECUDA, "cudaGetSymbolAddress of the no-allocation scratch failed: %s", cudaGetErrorString(e));
         g_noalloc_ptr[dev] = p;
+        g_noalloc_ctx[dev] = current_context();
     }
     return static_cast<double *>(g_noalloc_ptr[dev]);
 }
@@ -966,13 +1001,13 @@ static double *noalloc_scratch() {
 void matvec_noalloc(const hm_matrix *A, int32_t nrhs, hm_dtype prec, const double *x, double *y, double alpha,
                     double beta, cudaStream_t s) {
     const int64_t n = A->tree->n;
-    const int64_t need = matvec_work_doubles(A);
+    const int64_t need = work_doubles(A, A->n_partials);  // the forward product only
     if (need > NOALLOC_MAX_DOUBLES)
         fail(HM_EINVAL,
              "problem too large for the allocation-free product: needs %lld scratch doubles "
              "(2 n + K + P doubles and n + K + P floats), the limit is %lld",
              (long long)need, (long long)NOALLOC_MAX_DOUBLES);
-    const MatvecWork w = matvec_work_at(A, noalloc_scratch());
+    const MatvecWork w = work_at(A, noalloc_scratch(), A->n_partials);
     for (int r = 0; r < nrhs; ++r) {
         permute_to_morton(A->tree, x + (int64_t)r * n, w.xm, s);
         matvec_morton(A, prec, w, s, false);

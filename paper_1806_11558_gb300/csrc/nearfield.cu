@@ -68,16 +68,19 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
-// Bounded wait: gives up after about two seconds of SM clock (sets *err), so
-// a lost transaction can never hang the GPU.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase, int *err, int code) {
+// Bounded wait: gives up after `limit` SM clock cycles (sets *err), so a lost
+// transaction can never hang the GPU.  The limit is checked before each poll:
+// a limit of 0 gives up without polling (the test hook of hm_set_wait_limit).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase, int *err, int code,
+                                                  long long limit) {
     const long long t0 = clock64();
-    while (!mbar_try_wait(bar, phase))
-        if (clock64() - t0 > 4000000000LL) {
+    for (;;) {
+        if (clock64() - t0 >= limit) {
             atomicExch(err, code);
             return false;
         }
-    return true;
+        if (mbar_try_wait(bar, phase)) return true;
+    }
 }
 
 // Shared-memory layout of nearfield_kernel: two 128-byte aligned panel tiles
@@ -108,7 +111,7 @@ __global__ void __launch_bounds__(NF_THREADS) nearfield_kernel(const __grid_cons
                                                                 const QuadParams qp, double *__restrict__ arena,
                                                                 SingularItem *__restrict__ sing,
                                                                 unsigned long long *sing_count, int64_t sing_cap,
-                                                                int *err) {
+                                                                int *err, long long wait_limit) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     const int64_t b = blockIdx.x;
@@ -136,9 +139,10 @@ __global__ void __launch_bounds__(NF_THREADS) nearfield_kernel(const __grid_cons
         tma_load_2d(tR, &pt_map, bar, rb_al, 0);
         tma_load_2d(tC, &pt_map, bar, cb_al, 0);
     }
-    if (!mbar_wait_bounded(bar, 0, err, 2)) {
-        // the copies may still land: wait once more (bounded) before leaving
-        mbar_wait_bounded(bar, 0, err, 2);
+    if (!mbar_wait_bounded(bar, 0, err, 2, wait_limit)) {
+        // the copies this block started may still land in its shared memory:
+        // wait for them (with the default bound) before leaving
+        mbar_wait_bounded(bar, 0, err, 2, WAIT_LIMIT_DEFAULT);
         return;
     }
     const int m = re - rb, n = ce - cb, mn = m * n;
@@ -463,7 +467,7 @@ void assemble_nearfield(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, c
         kern<<<(unsigned)tr->n_dense, NF_THREADS, smem, s>>>(
             ff ? tr->pf_map : tr->pt_map, tr->dense.as<int32_t>(), tr->dense_base.as<int64_t>(),
             tr->dense_ld.as<int32_t>(), tr->dense_tp.as<int32_t>(), box, qp, A->dense.as<double>(),
-            items.as<SingularItem>(), cnt.as<unsigned long long>(), tr->singular_cap, d_err);
+            items.as<SingularItem>(), cnt.as<unsigned long long>(), tr->singular_cap, d_err, wait_limit());
         HM_LAUNCH_CHECK();
     }
     HM_CUDA_CHECK(cudaEventRecord(e1, s));

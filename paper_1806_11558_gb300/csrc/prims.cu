@@ -1,8 +1,9 @@
 // prims.cu -- errors, device buffers, quadrature constants, scan, radix sort,
 // TMA descriptors.
-#include <cstdarg>
-#include <cmath>
 #include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdlib>
 #include <map>
 #include <mutex>
 
@@ -183,9 +184,46 @@ void cache_trim() {
     g_cache_bytes = 0;
 }
 
+// ----------------------------------------------------------------------------
+// injected allocation failures and the wait limit
+// ----------------------------------------------------------------------------
+static std::mutex g_fault_mu;
+static long long g_fault_left = 0;  // allocations until the injected failure; 0 = off
+static long long g_fault_seen = 0;  // allocations since the injection was armed
+
+void set_fault_injection(long long n) {
+    std::lock_guard<std::mutex> lk(g_fault_mu);
+    g_fault_left = n > 0 ? n : 0;
+    g_fault_seen = 0;
+}
+
+// HM_FAULT_INJECT=<n> arms the injection when the library is loaded
+static const int g_fault_env = [] {
+    const char *e = std::getenv("HM_FAULT_INJECT");
+    if (e && *e) set_fault_injection(std::atoll(e));
+    return 0;
+}();
+
+void fault_checkpoint(size_t nbytes) {
+    long long k = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_fault_mu);
+        if (g_fault_left == 0) return;
+        ++g_fault_seen;
+        if (--g_fault_left != 0) return;
+        k = g_fault_seen;
+    }
+    fail(HM_ENOMEM, "injected allocation failure (allocation %lld since arming, %zu bytes)", k, nbytes);
+}
+
+static std::atomic<long long> g_wait_limit{WAIT_LIMIT_DEFAULT};
+long long wait_limit() { return g_wait_limit.load(); }
+void set_wait_limit(long long cycles) { g_wait_limit.store(cycles >= 0 ? cycles : WAIT_LIMIT_DEFAULT); }
+
 void DBuf::alloc(size_t nbytes) {
     release();
     if (nbytes == 0) nbytes = 16;
+    fault_checkpoint(nbytes);
     HM_CUDA_CHECK(cudaGetDevice(&dev));
     if (nbytes >= CACHE_MIN) {
         std::lock_guard<std::mutex> lk(g_cache_mu);
@@ -215,10 +253,23 @@ void DBuf::alloc(size_t nbytes) {
     blk = nbytes;
 }
 
+// Waits for the work queued on device `dev` (the device a block belongs to,
+// which need not be the current one).  The library releases no buffer while
+// one of its streams is being captured: buffers that captured work uses are
+// allocated before the capture and released after it.
+static bool sync_device(int dev) {
+    int cur = dev;
+    if (cudaGetDevice(&cur) != cudaSuccess) return false;
+    if (cur != dev && cudaSetDevice(dev) != cudaSuccess) return false;
+    const bool ok = cudaDeviceSynchronize() == cudaSuccess;
+    if (cur != dev) cudaSetDevice(cur);
+    return ok;
+}
+
 void DBuf::release() {
     if (p) {
         bool cached = false;
-        if (blk >= CACHE_MIN && cudaDeviceSynchronize() == cudaSuccess) {
+        if (blk >= CACHE_MIN && sync_device(dev)) {
             std::lock_guard<std::mutex> lk(g_cache_mu);
             if (g_cache_bytes + blk <= cache_cap()) {
                 g_cache.insert({{dev, blk}, p});

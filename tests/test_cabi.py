@@ -3,6 +3,8 @@ every call below is rejected before any CUDA work)."""
 import ctypes
 import os
 import re
+import subprocess
+import sys
 
 import pytest
 
@@ -55,3 +57,33 @@ def test_binding_fails_loudly_without_library(hm, monkeypatch, tmp_path):
     monkeypatch.setattr(hm, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError):
         hm.lib()
+
+
+def test_injected_allocation_failure_on_the_host(hm):
+    """hm_set_fault_injection(1): the first device allocation of the next call
+    fails before any CUDA call is made, so the call returns HM_ENOMEM (here,
+    without a GPU, and on one); the injection disarms itself."""
+    L = hm.lib()
+    out = ctypes.c_void_p(1)
+    fake = ctypes.c_void_p(64)
+    p = hm.TreeParams(1.5, 64)
+    hm.hm_set_fault_injection(1)
+    try:
+        assert L.hm_build_tree(fake, 10, fake, 4, ctypes.byref(p), None, ctypes.byref(out)) == hm.HM_ENOMEM
+        assert out.value is None
+        assert "injected allocation failure (allocation 1" in hm.hm_last_error()
+    finally:
+        hm.hm_set_fault_injection(0)
+    # the wait limit is a host-side setting: any value is accepted, < 0 restores the default
+    hm.hm_set_wait_limit(0)
+    hm.hm_set_wait_limit(-1)
+
+
+def test_fault_injection_from_the_environment(hm):
+    code = ("import ctypes, paper_1806_11558_gb300 as hm; L = hm.lib(); f = ctypes.c_void_p(64); "
+            "o = ctypes.c_void_p(); p = hm.TreeParams(1.5, 64); "
+            "print(L.hm_build_tree(f, 10, f, 4, ctypes.byref(p), None, ctypes.byref(o)))")
+    env = dict(os.environ, HM_FAULT_INJECT="1")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == str(hm.HM_ENOMEM)

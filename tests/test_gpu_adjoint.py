@@ -85,9 +85,18 @@ def test_potential_and_adjoint(orc, lvl4):
     assert float(z.abs().max()) == 0.0
 
 
+def misfit_loss(A, tree, f, c, points, target, opts):
+    """The differentiation workload's objective: L = mean_k (E alpha - target)_k^2
+    with H diag(c) alpha = f, through the library's autograd functions."""
+    import torch
+    from paper_1806_11558_gb300.autograd import DensitySolve, Potential
+    alpha = DensitySolve.apply(A, f, c, opts)
+    phi = Potential.apply(tree, points, alpha)
+    return torch.mean((phi - target) ** 2)
+
+
 def _gpu_loss_and_grads(g, cfg, f, c, opts):
     torch = g.torch
-    from paper_1806_11558_gb300.autograd import misfit_loss
     pts = torch.from_numpy(np.ascontiguousarray(cfg["points"])).cuda()
     target = torch.from_numpy(np.ascontiguousarray(_target(cfg))).cuda()
     fd = torch.from_numpy(np.ascontiguousarray(f)).cuda().requires_grad_(True)
@@ -103,6 +112,45 @@ def _target(cfg):
 
 
 OPTS = dict(rel_tol=1e-13, restart=128, max_iter=5000, precond=1)
+
+
+def test_scaled_product_and_solves(orc, lvl4):
+    """hm_matvec_scaled and hm_solve_scaled (the column-scaled operator
+    H diag(c) of the per-panel coefficients) against the oracle applying the
+    exported operator with the scalings written out."""
+    g, _ = lvl4
+    torch, hm = g.torch, g.hm
+    rng = np.random.default_rng(7)
+    c = 1.0 + 0.2 * rng.uniform(-1.0, 1.0, g.n)
+    l = rng.uniform(0.5, 1.5, g.n)
+    x = rng.standard_normal((2, g.n))
+    y0 = rng.standard_normal((2, g.n))
+    mv, mvt = _exported_operator(orc, g, False), _exported_operator(orc, g, True)
+    cd, ld, xd = (torch.from_numpy(np.ascontiguousarray(v)).cuda() for v in (c, l, x))
+    for trans, op in ((0, mv), (1, mvt)):
+        yd = torch.from_numpy(y0.copy()).cuda()
+        hm.hm_matvec_scaled(g.A, xd, yd, trans=trans, left=ld, right=cd, alpha=-0.75, beta=0.5)
+        torch.cuda.synchronize()
+        ref = np.array([-0.75 * l * op(c * x[r]) + 0.5 * y0[r] for r in range(2)])
+        assert np.linalg.norm(yd.cpu().numpy() - ref) <= 1e-12 * np.linalg.norm(ref)
+        # identities: no scaling on either side
+        yd = torch.empty_like(xd)
+        hm.hm_matvec_scaled(g.A, xd, yd, trans=trans)
+        torch.cuda.synchronize()
+        ref = np.array([op(x[r]) for r in range(2)])
+        assert np.linalg.norm(yd.cpu().numpy() - ref) <= 1e-12 * np.linalg.norm(ref)
+    b = rng.standard_normal(g.n)
+    for trans in (0, 1):
+        if trans == 0:
+            A_c = lambda v: mv(c * v)
+        else:
+            A_c = lambda v: c * mvt(v)
+        xo, _, _ = orc.gmres(A_c, b, restart=60, tol=1e-13)
+        xg = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+        info = hm.hm_solve_scaled(g.A, torch.from_numpy(b).cuda(), cd, xg, trans=trans, **OPTS)
+        torch.cuda.synchronize()
+        assert info.status == 0
+        assert np.linalg.norm(xg.cpu().numpy() - xo) <= 1e-9 * np.linalg.norm(xo)
 
 
 def test_misfit_gradients_vs_dense_oracle(orc, lvl4):
@@ -128,7 +176,6 @@ def test_misfit_gradients_central_differences_level6(orc):
     g = GpuH(cfg["V"], cfg["T"], leaf=64, eta=1.5, eps=1e-6, kmax=64)
     try:
         torch = g.torch
-        from paper_1806_11558_gb300.autograd import misfit_loss
         f = g.load_vector(cfg["sources"])[0]
         c = np.ones(g.n)
         L0, gf, gc = _gpu_loss_and_grads(g, cfg, f, c, OPTS)

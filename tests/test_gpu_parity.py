@@ -328,5 +328,6 @@ def test_c1_approximation_error_scales_with_kappa_eps(orc):
             g.close()
     print("C1: kappa %.1f, |x_H - x_LU| / |x_LU| = %.2e at eps 1e-6 (kappa eps = %.1e), %.2e at eps 1e-12"
           % (kappa, errs[1e-6], kappa * 1e-6, errs[1e-12]))
-    assert errs[1e-6] <= 10 * kappa * 1e-6
+    assert errs[1e-6] <= 10 * kappa * 1e-6  # the stated theory
+    assert errs[1e-6] <= 20 * 1e-6  # near the measured 1.78e-6: a regression of the ACA or quadrature shows here
     assert errs[1e-12] < 1e-8

@@ -46,3 +46,33 @@ def test_noalloc_matvec_matches_hm_matvec_on_consecutive_calls():
                 assert err <= 1e-12, (prec, err)
     finally:
         g.close()
+
+
+def test_noalloc_matvec_rejects_what_it_cannot_do():
+    """trans = 1 is not offered, and a problem whose working vectors exceed the
+    fixed array (2,097,152 doubles; a level-6 icosphere needs more) is refused
+    with the required size in the message, before any device work."""
+    torch = need_gpu()
+    import paper_1806_11558_gb300 as hm
+    V, T = meshgen.icosphere(3)
+    g = GpuH(V, T, leaf=64, eta=1.5, eps=1e-8, factor_dtype=hm.HM_F32, dense_dtype=hm.HM_F32)
+    try:
+        x = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+        with pytest.raises(hm.HMError) as e:
+            hm.hm_matvec_noalloc(g.A, x, torch.empty_like(x), trans=1)
+        assert e.value.status == hm.HM_EINVAL and "trans" in str(e.value)
+    finally:
+        g.close()
+    V, T = meshgen.icosphere(6)
+    g = GpuH(V, T, leaf=64, eta=1.5, eps=1e-4)
+    try:
+        x = torch.zeros(g.n, dtype=torch.float64, device="cuda")
+        y = torch.full_like(x, 7.0)
+        with pytest.raises(hm.HMError) as e:
+            hm.hm_matvec_noalloc(g.A, x, y)
+        assert e.value.status == hm.HM_EINVAL
+        assert "needs" in str(e.value) and "2097152" in str(e.value)
+        torch.cuda.synchronize()
+        assert float(y.min()) == 7.0 and float(y.max()) == 7.0  # nothing was written
+    finally:
+        g.close()
