@@ -76,17 +76,18 @@ constexpr int CM_COLS = 64;                 // panel columns per tile
 
 
 // ---------------------------------------------------------------------------
-// row_mrhs_kernel: Y_rho = P_rho X(colidx) + U~_rho T(tidx), one CTA (4 warps)
-// per leaf row cluster, 16 MT rows per pass.  The panels are walked in slices
-// of 64 columns through a 3-stage cp.async pipeline: the slice's panel rows
-// and its gathered rows of X / T (as BF16 hi and lo, [column][rhs]) land in
-// shared memory while the previous slices are multiplied; warp w owns the
-// 16 columns 16 w .. 16 w + 15 of every slice (A fragments by LDS / ldmatrix,
-// B fragments by ldmatrix.trans), and the four warps' sums are added in a
-// fixed order at the end.
+// row_mrhs_kernel: Y_rho = P_rho X(colidx) + U~_rho T(tidx), one CTA of WARPS
+// (4 or 8) warps per leaf row cluster, 16 MT rows per pass.  The panels are
+// walked in slices of 64 columns through a 3-stage cp.async pipeline: the
+// slice's panel rows and its gathered rows of X / T (as BF16 hi and lo,
+// [column][rhs]) land in shared memory while the previous slices are
+// multiplied; warp w owns the 16 columns 16 (w mod 4) .. 16 (w mod 4) + 15 of
+// every slice (A fragments by LDS / ldmatrix, B fragments by ldmatrix.trans)
+// and, with 8 warps, one half of the MT row tiles (the two halves share the
+// staged slices); the four column groups' sums are added in a fixed order at
+// the end, so 4 and 8 warps give the same result bit for bit.
 // ---------------------------------------------------------------------------
-constexpr int RP_THREADS = 128;
-constexpr int RP_WARPS = RP_THREADS / 32;
+constexpr int RP_KG = 4;           // column groups of 16 per slice
 constexpr int RP_KS = 64;          // panel columns per slice
 constexpr int RP_STAGES = 3;
 constexpr int RP_APAD = 8;         // elements of padding per staged panel row
@@ -106,25 +107,27 @@ template <int MT, class TP> struct RpStage {
 };
 
 // the gathered row indices this thread needs for the slice at column c0
-// (columns (tid >> 2) and (tid >> 2) + 32), loaded ahead of their use
-__device__ __forceinline__ void rp_idx(const int32_t *__restrict__ idx, int K, int c0, int (&ir)[2]) {
+// (columns (tid >> 2) + (THREADS / 4) j), loaded ahead of their use
+template <int THREADS> constexpr int rp_nj() { return 4 * RP_KS / THREADS; }
+template <int THREADS>
+__device__ __forceinline__ void rp_idx(const int32_t *__restrict__ idx, int K, int c0, int (&ir)[rp_nj<THREADS>()]) {
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-        const int col = c0 + (threadIdx.x >> 2) + 32 * j;
+    for (int j = 0; j < rp_nj<THREADS>(); ++j) {
+        const int col = c0 + (threadIdx.x >> 2) + (THREADS / 4) * j;
         ir[j] = col < K ? __ldg(idx + col) : 0;
     }
 }
 
-template <int MT, class TP>
+template <int MT, class TP, int THREADS>
 __device__ __forceinline__ void rp_load(unsigned char *stage, const TP *__restrict__ Pn, int K, int rows_valid, int c0,
-                                        const int (&ir)[2], const __nv_bfloat16 *__restrict__ Zh,
+                                        const int (&ir)[rp_nj<THREADS>()], const __nv_bfloat16 *__restrict__ Zh,
                                         const __nv_bfloat16 *__restrict__ Zl) {
     TP *sA = reinterpret_cast<TP *>(stage);
     __nv_bfloat16 *sBh = reinterpret_cast<__nv_bfloat16 *>(stage + RpStage<MT, TP>::A_BYTES);
     __nv_bfloat16 *sBl = sBh + RP_KS * RP_BSTRIDE;
     constexpr int PER = 16 / (int)sizeof(TP);  // elements per 16-byte copy
     constexpr int VPR = RP_KS / PER;           // copies per row
-    for (int e = threadIdx.x; e < 16 * MT * VPR; e += RP_THREADS) {
+    for (int e = threadIdx.x; e < 16 * MT * VPR; e += THREADS) {
         const int r = e / VPR, v = e - (e / VPR) * VPR;
         const int col = c0 + PER * v;
         const bool ok = r < rows_valid && col < K;
@@ -132,8 +135,8 @@ __device__ __forceinline__ void rp_load(unsigned char *stage, const TP *__restri
                    ok);
     }
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-        const int c = (threadIdx.x >> 2) + 32 * j, q = threadIdx.x & 3;  // q: hi / lo x first / second 8 rhs
+    for (int j = 0; j < rp_nj<THREADS>(); ++j) {
+        const int c = (threadIdx.x >> 2) + (THREADS / 4) * j, q = threadIdx.x & 3;  // q: hi / lo x first / second 8 rhs
         const int col = c0 + c;
         const bool ok = col < K;
         const __nv_bfloat16 *src = ((q & 2) ? Zl : Zh) + (int64_t)ir[j] * MR + 8 * (q & 1);
@@ -142,13 +145,17 @@ __device__ __forceinline__ void rp_load(unsigned char *stage, const TP *__restri
     }
 }
 
-template <int MT, class TP>
-__device__ __forceinline__ void rp_compute(const unsigned char *stage, float (&acc)[MT][2][4]) {
+// row tiles of one warp: all MT with 4 warps, one half with 8
+template <int MT, int WARPS> constexpr int rp_mth() { return WARPS == 4 ? MT : (MT + 1) / 2; }
+
+template <int MT, class TP, int WARPS>
+__device__ __forceinline__ void rp_compute(const unsigned char *stage, float (&acc)[rp_mth<MT, WARPS>()][2][4]) {
+    constexpr int MTH = rp_mth<MT, WARPS>();
     const TP *sA = reinterpret_cast<const TP *>(stage);
     const __nv_bfloat16 *sBh = reinterpret_cast<const __nv_bfloat16 *>(stage + RpStage<MT, TP>::A_BYTES);
     const __nv_bfloat16 *sBl = sBh + RP_KS * RP_BSTRIDE;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
-    const int kb = 16 * warp;
+    const int kb = 16 * (warp % RP_KG), mt0 = MTH * (warp / RP_KG);
     uint32_t bh[2][2], bl[2][2];
 #pragma unroll
     for (int nt = 0; nt < 2; ++nt) {
@@ -156,7 +163,9 @@ __device__ __forceinline__ void rp_compute(const unsigned char *stage, float (&a
         ldmatrix_x2_trans(bl[nt][0], bl[nt][1], sBl + (kb + (lane & 15)) * RP_BSTRIDE + 8 * nt);
     }
 #pragma unroll
-    for (int mt = 0; mt < MT; ++mt) {
+    for (int ml = 0; ml < MTH; ++ml) {
+        const int mt = mt0 + ml;
+        if (MTH != MT && mt >= MT) break;
         if constexpr (sizeof(TP) == 4) {
             const float *r0 = reinterpret_cast<const float *>(sA) + (16 * mt + g) * (RP_KS + RP_APAD) + kb + 2 * t;
             const float *r1 = r0 + 8 * (RP_KS + RP_APAD);
@@ -178,9 +187,9 @@ __device__ __forceinline__ void rp_compute(const unsigned char *stage, float (&a
                            al3 = pack_bf16(l[6], l[7]);
 #pragma unroll
             for (int nt = 0; nt < 2; ++nt) {
-                mma_bf16(acc[mt][nt], ah0, ah1, ah2, ah3, bh[nt][0], bh[nt][1]);
-                mma_bf16(acc[mt][nt], ah0, ah1, ah2, ah3, bl[nt][0], bl[nt][1]);
-                mma_bf16(acc[mt][nt], al0, al1, al2, al3, bh[nt][0], bh[nt][1]);
+                mma_bf16(acc[ml][nt], ah0, ah1, ah2, ah3, bh[nt][0], bh[nt][1]);
+                mma_bf16(acc[ml][nt], ah0, ah1, ah2, ah3, bl[nt][0], bl[nt][1]);
+                mma_bf16(acc[ml][nt], al0, al1, al2, al3, bh[nt][0], bh[nt][1]);
             }
         } else {
             // ldmatrix.x4: matrices (rows 0-7, k 0-7), (rows 8-15, k 0-7), (rows 0-7, k 8-15), (rows 8-15, k 8-15)
@@ -190,44 +199,46 @@ __device__ __forceinline__ void rp_compute(const unsigned char *stage, float (&a
             ldmatrix_x4(a0, a1, a2, a3, base);
 #pragma unroll
             for (int nt = 0; nt < 2; ++nt) {
-                mma_bf16(acc[mt][nt], a0, a1, a2, a3, bh[nt][0], bh[nt][1]);
-                mma_bf16(acc[mt][nt], a0, a1, a2, a3, bl[nt][0], bl[nt][1]);
+                mma_bf16(acc[ml][nt], a0, a1, a2, a3, bh[nt][0], bh[nt][1]);
+                mma_bf16(acc[ml][nt], a0, a1, a2, a3, bl[nt][0], bl[nt][1]);
             }
         }
     }
 }
 
-template <int MT, class TP>
+template <int MT, class TP, int WARPS>
 __device__ __forceinline__ void rp_panel(unsigned char *sm, const TP *__restrict__ Pn, int K, int rows_valid,
                                          const int32_t *__restrict__ idx, const __nv_bfloat16 *__restrict__ Zh,
-                                         const __nv_bfloat16 *__restrict__ Zl, float (&acc)[MT][2][4]) {
-    constexpr int SB = RpStage<MT, TP>::BYTES;
+                                         const __nv_bfloat16 *__restrict__ Zl,
+                                         float (&acc)[rp_mth<MT, WARPS>()][2][4]) {
+    constexpr int SB = RpStage<MT, TP>::BYTES, THREADS = 32 * WARPS;
     const int ns = (K + RP_KS - 1) / RP_KS;
-    int ir[2];
+    int ir[rp_nj<THREADS>()];
 #pragma unroll
     for (int st = 0; st < RP_STAGES - 1; ++st) {
         if (st < ns) {
-            rp_idx(idx, K, st * RP_KS, ir);
-            rp_load<MT, TP>(sm + st * SB, Pn, K, rows_valid, st * RP_KS, ir, Zh, Zl);
+            rp_idx<THREADS>(idx, K, st * RP_KS, ir);
+            rp_load<MT, TP, THREADS>(sm + st * SB, Pn, K, rows_valid, st * RP_KS, ir, Zh, Zl);
         }
         cp_async_commit();
     }
-    rp_idx(idx, K, (RP_STAGES - 1) * RP_KS, ir);  // indices of the next slice to load
+    rp_idx<THREADS>(idx, K, (RP_STAGES - 1) * RP_KS, ir);  // indices of the next slice to load
     for (int sl = 0; sl < ns; ++sl) {
         cp_async_wait<RP_STAGES - 2>();
         __syncthreads();
         const int nx = sl + RP_STAGES - 1;
-        if (nx < ns) rp_load<MT, TP>(sm + (nx % RP_STAGES) * SB, Pn, K, rows_valid, nx * RP_KS, ir, Zh, Zl);
+        if (nx < ns)
+            rp_load<MT, TP, THREADS>(sm + (nx % RP_STAGES) * SB, Pn, K, rows_valid, nx * RP_KS, ir, Zh, Zl);
         cp_async_commit();
-        rp_idx(idx, K, (nx + 1) * RP_KS, ir);  // consumed one iteration later
-        rp_compute<MT, TP>(sm + (sl % RP_STAGES) * SB, acc);
+        rp_idx<THREADS>(idx, K, (nx + 1) * RP_KS, ir);  // consumed one iteration later
+        rp_compute<MT, TP, WARPS>(sm + (sl % RP_STAGES) * SB, acc);
     }
     cp_async_wait<0>();
     __syncthreads();
 }
 
-template <int MT, class TF>
-__global__ void __launch_bounds__(RP_THREADS) row_mrhs_kernel(
+template <int MT, class TF, int WARPS>
+__global__ void __launch_bounds__(32 * WARPS) row_mrhs_kernel(
     const int32_t *__restrict__ leaf_begin, const int64_t *__restrict__ rho_off, const int32_t *__restrict__ rho_K,
     const int64_t *__restrict__ rho_colptr, const int32_t *__restrict__ colidx, const float *__restrict__ dense,
     const int64_t *__restrict__ up_off, const int32_t *__restrict__ up_K, const int64_t *__restrict__ up_colptr,
@@ -239,35 +250,41 @@ __global__ void __launch_bounds__(RP_THREADS) row_mrhs_kernel(
     const int32_t r0 = leaf_begin[rho], mr = leaf_begin[rho + 1] - r0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
     const int Kd = rho_K[rho], Ku = up_K[rho];
+    constexpr int MTH = rp_mth<MT, WARPS>();
+    const int kg = warp % RP_KG, mt0 = MTH * (warp / RP_KG);
     for (int r0t = 0; r0t < mr; r0t += 16 * MT) {
         const int rows = min(16 * MT, mr - r0t);
-        float acc[MT][2][4];
+        float acc[MTH][2][4];
 #pragma unroll
-        for (int mt = 0; mt < MT; ++mt)
+        for (int ml = 0; ml < MTH; ++ml)
 #pragma unroll
             for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
-                for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.0f;
-        rp_panel<MT, float>(sm, dense + rho_off[rho] + (int64_t)r0t * Kd, Kd, rows, colidx + rho_colptr[rho], Xh, Xl,
-                            acc);
-        rp_panel<MT, TF>(sm, up + up_off[rho] + (int64_t)r0t * Ku, Ku, rows, tidx + up_colptr[rho], Th, Tl, acc);
-        // per-warp sums -> shared memory -> fixed-order sum over the 4 warps
+                for (int e = 0; e < 4; ++e) acc[ml][nt][e] = 0.0f;
+        rp_panel<MT, float, WARPS>(sm, dense + rho_off[rho] + (int64_t)r0t * Kd, Kd, rows, colidx + rho_colptr[rho],
+                                   Xh, Xl, acc);
+        rp_panel<MT, TF, WARPS>(sm, up + up_off[rho] + (int64_t)r0t * Ku, Ku, rows, tidx + up_colptr[rho], Th, Tl,
+                                acc);
+        // per-column-group sums -> shared memory -> fixed-order sum over the 4 groups
         float *red = reinterpret_cast<float *>(sm);
 #pragma unroll
-        for (int mt = 0; mt < MT; ++mt)
+        for (int ml = 0; ml < MTH; ++ml) {
+            const int mt = mt0 + ml;
+            if (MTH != MT && mt >= MT) break;
 #pragma unroll
             for (int nt = 0; nt < 2; ++nt) {
-                float *base = red + warp * (16 * MT) * MR;
+                float *base = red + kg * (16 * MT) * MR;
                 const int ra = 16 * mt + g, col = 8 * nt + 2 * t;
-                base[ra * MR + col] = acc[mt][nt][0];
-                base[ra * MR + col + 1] = acc[mt][nt][1];
-                base[(ra + 8) * MR + col] = acc[mt][nt][2];
-                base[(ra + 8) * MR + col + 1] = acc[mt][nt][3];
+                base[ra * MR + col] = acc[ml][nt][0];
+                base[ra * MR + col + 1] = acc[ml][nt][1];
+                base[(ra + 8) * MR + col] = acc[ml][nt][2];
+                base[(ra + 8) * MR + col + 1] = acc[ml][nt][3];
             }
+        }
         __syncthreads();
-        for (int e = threadIdx.x; e < rows * MR; e += RP_THREADS) {
+        for (int e = threadIdx.x; e < rows * MR; e += 32 * WARPS) {
             float sacc = 0.0f;
-            for (int w = 0; w < RP_WARPS; ++w) sacc += red[w * (16 * MT) * MR + e];
+            for (int w = 0; w < RP_KG; ++w) sacc += red[w * (16 * MT) * MR + e];
             Y[(int64_t)(r0 + r0t) * MR + e] = (double)sacc;
         }
         __syncthreads();
@@ -682,9 +699,12 @@ void mrhs_prepare(const hm_matrix *A, hm_dtype prec, cudaStream_t s) {
 
 
 template <int MT> static int row_smem() {
-    const int st = RP_STAGES * RpStage<MT, float>::BYTES, red = RP_WARPS * 16 * MT * MR * 4;
+    const int st = RP_STAGES * RpStage<MT, float>::BYTES, red = RP_KG * 16 * MT * MR * 4;
     return st > red ? st : red;
 }
+
+// warps per CTA of row_mrhs_kernel
+constexpr int RP_WARPS = 8;
 
 template <class TF>
 static void matvec_mrhs_impl(const hm_matrix *A, const TF *up, const float *X, double *Y, __nv_bfloat16 *Xh,
@@ -713,15 +733,15 @@ static void matvec_mrhs_impl(const hm_matrix *A, const TF *up, const float *X, d
     auto launch = [&](auto kern, int smem) {
         HM_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         Trace tr_(f32 ? "row_mrhs_kernel.f32" : "row_mrhs_kernel.bf16", s);
-        kern<<<(unsigned)tr->n_leaf, RP_THREADS, smem, s>>>(
+        kern<<<(unsigned)tr->n_leaf, 32 * RP_WARPS, smem, s>>>(
             tr->leaf_begin.as<int32_t>(), tr->rho_off.as<int64_t>(), tr->rho_K.as<int32_t>(),
             tr->rho_colptr.as<int64_t>(), tr->colidx.as<int32_t>(), A->dense32.as<float>(), A->up_off.as<int64_t>(),
             A->up_K.as<int32_t>(), A->up_colptr.as<int64_t>(), A->tidx.as<int32_t>(), up, Th, Tl, Xh, Xl, Y);
         HM_LAUNCH_CHECK();
     };
-    if (tiles <= 3) launch(row_mrhs_kernel<3, TF>, row_smem<3>());
-    else if (tiles <= 5) launch(row_mrhs_kernel<5, TF>, row_smem<5>());
-    else launch(row_mrhs_kernel<8, TF>, row_smem<8>());
+    if (tiles <= 3) launch(row_mrhs_kernel<3, TF, RP_WARPS>, row_smem<3>());
+    else if (tiles <= 5) launch(row_mrhs_kernel<5, TF, RP_WARPS>, row_smem<5>());
+    else launch(row_mrhs_kernel<8, TF, RP_WARPS>, row_smem<8>());
 }
 
 // Y (Morton [n][16] FP64) = H X (Morton [n][16] FP32) with the FP32 near field

@@ -232,7 +232,9 @@ constexpr int ROW_CHUNK = 4096;  // columns staged per pass (multiple of 8)
 // picks the smallest RB whose group covers the largest leaf cluster, so the
 // gathered vector is staged once per chunk and every warp keeps RB 16-byte
 // loads in flight per step; rows past the cluster's end issue no loads.
-constexpr int row_rb_for(int max_leaf) { return max_leaf <= 32 ? 4 : max_leaf <= 40 ? 5 : max_leaf <= 64 ? 8 : 12; }
+constexpr int row_rb_for(int max_leaf) {
+    return max_leaf <= 32 ? 4 : max_leaf <= 40 ? 5 : max_leaf <= 64 ? 8 : max_leaf <= 80 ? 10 : 12;
+}
 
 // Partial sums (per lane) of rows g0 + warp + ROW_WARPS * u, u < RB, of a
 // row-major panel P (|rho| x L) times z(idx), staging z(idx) chunk by chunk.

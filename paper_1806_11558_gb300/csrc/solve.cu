@@ -429,6 +429,41 @@ __global__ void __launch_bounds__(BJ_THREADS) bj_apply_kernel(const int32_t *beg
     }
 }
 
+// The same for up to BJ_NC columns per CTA (grid.y = column groups): the
+// block's inverse is read once for all of them instead of once per column.
+// Each column's sum runs over j in the same order as in bj_apply_kernel, so
+// the results are the same bit for bit.
+constexpr int BJ_NC = 16;
+template <class TD>
+__global__ void __launch_bounds__(BJ_THREADS) bj_apply_cols_kernel(const int32_t *begin, const int64_t *bj_off,
+                                                                   const TD *bj, const double *v, double *z,
+                                                                   int trans, int64_t n, int cols) {
+    __shared__ TD s_v[BJ_NC][BJ_MAXM];
+    const int64_t r = blockIdx.x;
+    const int32_t r0 = begin[r], m = begin[r + 1] - r0;
+    const int c0 = blockIdx.y * BJ_NC, nc = min(BJ_NC, cols - c0);
+    const TD *D = bj + bj_off[r];
+    for (int e = threadIdx.x; e < BJ_NC * m; e += BJ_THREADS) {
+        const int c = e / m, j = e - c * m;
+        s_v[c][j] = c < nc ? (TD)v[(int64_t)(c0 + c) * n + r0 + j] : (TD)0;
+    }
+    __syncthreads();
+    const int64_t si = trans ? m : 1, sj = trans ? 1 : m;
+    for (int i = threadIdx.x; i < m; i += BJ_THREADS) {
+        TD acc[BJ_NC];
+#pragma unroll
+        for (int c = 0; c < BJ_NC; ++c) acc[c] = 0;
+        for (int j = 0; j < m; ++j) {
+            const TD d = D[j * sj + i * si];
+#pragma unroll
+            for (int c = 0; c < BJ_NC; ++c) acc[c] = fma(d, s_v[c][j], acc[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < BJ_NC; ++c)
+            if (c < nc) z[(int64_t)(c0 + c) * n + r0 + i] = (double)acc[c];
+    }
+}
+
 __global__ void bj_round_kernel(const double *a, int64_t n, float *o) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         o[i] = (float)a[i];
@@ -508,6 +543,19 @@ void bj_setup(const hm_matrix *Ac, cudaStream_t s) {
 // z = M^{-1} v for `cols` vectors [cols][n]; low: the FP32 copy (inner solves)
 void bj_apply_cols(const hm_matrix *A, const double *v, double *z, int cols, bool trans, bool low, cudaStream_t s) {
     Trace trace(low ? "bj_apply_kernel.f32" : "bj_apply_kernel", s);
+    if (cols > 1) {
+        const dim3 grid((unsigned)A->n_bj, (unsigned)((cols + BJ_NC - 1) / BJ_NC));
+        if (low)
+            bj_apply_cols_kernel<float><<<grid, BJ_THREADS, 0, s>>>(A->bj_begin.as<int32_t>(), A->bj_off.as<int64_t>(),
+                                                                    A->bj32.as<float>(), v, z, trans ? 1 : 0,
+                                                                    A->tree->n, cols);
+        else
+            bj_apply_cols_kernel<double><<<grid, BJ_THREADS, 0, s>>>(A->bj_begin.as<int32_t>(),
+                                                                     A->bj_off.as<int64_t>(), A->bj.as<double>(), v,
+                                                                     z, trans ? 1 : 0, A->tree->n, cols);
+        HM_LAUNCH_CHECK();
+        return;
+    }
     const dim3 grid((unsigned)A->n_bj, (unsigned)cols);
     if (low)
         bj_apply_kernel<float><<<grid, BJ_THREADS, 0, s>>>(A->bj_begin.as<int32_t>(), A->bj_off.as<int64_t>(),
