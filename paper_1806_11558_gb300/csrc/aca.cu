@@ -299,8 +299,14 @@ __device__ __forceinline__ FF aca_entry(const float *fix, bool fixed_is_row, int
         return ff_from(fixed_is_row ? singular_entry_serial(A.V, vf, vv, kind, ai, aj, A.qp)
                                     : singular_entry_serial(A.V, vv, vf, kind, ai, aj, A.qp));
     }
-    return fixed_is_row ? far_entry(fix, 1, rec, (int)st, A.qp.w_h, A.qp.w_l)
-                        : far_entry(rec, (int)st, fix, 1, A.qp.w_h, A.qp.w_l);
+    // The regular rule sums over the points of the row-role panel in a rolled
+    // loop that reads that panel's record as it goes, and loads the
+    // column-role record into registers up front.  G(x, y) = G(y, x), so the
+    // pair is evaluated with the fixed (shared-memory) record in the row role
+    // in both passes: the varying record, read from L2, is then loaded once
+    // per entry instead of once per outer step.  The value is the same entry
+    // up to rounding (~1e-14 relative, the order of the double-float sums).
+    return far_entry(fix, 1, rec, (int)st, A.qp.w_h, A.qp.w_l);
 }
 
 // ACA of one block (CTA workers); U (m x kmax) and W (n x kmax) column-major

@@ -376,6 +376,7 @@ struct hm_matrix {
     // side by side), the t index of every panel column (-1 = padding) and the
     // list of 64-column tiles (panel, first column)
     hm::DBuf bcp, bcp_off, bcp_K, bcp_rows, bcp_col0, bcp_tidx, bcp_tiles, bcp_red;
+    hm::DBuf mrhs_err;  // [1] int: a bounded wait of the tensor-memory row pass gave up (0 = none)
     int64_t bcp_ngroups = 0, bcp_ntiles = 0, bcp_nred = 0, bcp_nslots = 0;
     int bcp_dtype = -1;  // hm_dtype of bcp, -1 = not built
     int64_t wp_entries = 0;

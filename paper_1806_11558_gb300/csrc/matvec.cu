@@ -469,7 +469,6 @@ static void matvec_impl(const hm_matrix *A, const TD *dense, const TF *proj, con
         case 4: kern = row_kernel<4, TD, TF, TX, TT, ORD>; break;
         case 5: kern = row_kernel<5, TD, TF, TX, TT, ORD>; break;
         case 8: kern = row_kernel<8, TD, TF, TX, TT, ORD>; break;
-        case 10: kern = row_kernel<10, TD, TF, TX, TT, ORD>; break;
         default: break;
     }
     Trace tr_row(nm.row, s);

