@@ -438,7 +438,9 @@ def run_large(args, world, hm, torch, W=LARGE, case="large"):
                        "rel_resid": ib.rel_resid, "inner_dtype": ib.inner_dtype, "err_vs_fp64": errbf,
                        "note": "BF16 factors added from the FP64 master, FP32 near field, inner tol 1e-2"},
         "matvec": mv, "mean_rank": mi["mean_rank"], "max_rank": mi["max_rank"],
-        "dense_entries": mi["dense_entries"], "lr_entries": mi["lr_entries"], "aca_small_sum": mi["aca_small_sum"],
+        "dense_entries": mi["dense_entries"], "lr_entries": mi["lr_entries"],
+        "aca_tuned": {"small_sum": mi["aca_small_sum"], "threads": mi["aca_threads"],
+                      "ctas_per_sm": mi["aca_ctas_per_sm"]},
         "roofline": dom, "rooflines_other": others, "kernels": kernels,
         "measured_peaks": {k: peaks[k] for k in ("fp64_tflops", "fp32_tflops", "sm_mhz", "how")},
         "clocks": ck, "gpu_launches": int(launches),
@@ -819,7 +821,9 @@ def run_batching(torch, hm):
            "tree_s": e[0].elapsed_time(e[1]) / 1e3, "assemble_s": e[1].elapsed_time(e[2]) / 1e3,
            "aca_s": mi["s_aca"], "nearfield_s": mi["s_nearfield"], "solve_s": e[3].elapsed_time(e[4]) / 1e3,
            "systems": 256, "lockstep_iters": info.iters, "refine_steps": info.refine_steps, **warm,
-           "max_rel_resid": info.rel_resid, "aca_small_sum": mi["aca_small_sum"],
+           "max_rel_resid": info.rel_resid,
+           "aca_tuned": {"small_sum": mi["aca_small_sum"], "threads": mi["aca_threads"],
+                         "ctas_per_sm": mi["aca_ctas_per_sm"]},
            "kernels": kernel_table(hm.hm_trace_read(), 1)}
     hm.hm_free(A)
     hm.hm_free(tree)

@@ -208,6 +208,9 @@ typedef struct {
     int32_t aca_small_sum;  /* ACA worker split chosen by the autotuner: blocks
                                with m + n up to this (and both dims <= 256) run
                                on one warp, larger ones on a whole CTA        */
+    int32_t aca_threads;    /* ACA launch chosen by the autotuner: threads per CTA
+                               (64, 128 or 256) ...                               */
+    int32_t aca_ctas_per_sm; /* ... and CTAs per SM of the persistent launch     */
 } hm_matrix_info;
 
 /* Build the Morton-ordered cluster tree and the block cluster tree of a

@@ -68,7 +68,8 @@ class MatrixInfo(ctypes.Structure):
                 ("kmax_hit", ctypes.c_int32), ("mean_rank", ctypes.c_double), ("s_nearfield", ctypes.c_double),
                 ("s_singular", ctypes.c_double), ("s_aca", ctypes.c_double), ("s_total", ctypes.c_double),
                 ("bytes_f64", ctypes.c_int64), ("bytes_low", ctypes.c_int64), ("aca_entries", ctypes.c_int64),
-                ("u_entries", ctypes.c_int64), ("aca_small_sum", ctypes.c_int32)]
+                ("u_entries", ctypes.c_int64), ("aca_small_sum", ctypes.c_int32), ("aca_threads", ctypes.c_int32),
+                ("aca_ctas_per_sm", ctypes.c_int32)]
 
 
 class TraceEntry(ctypes.Structure):

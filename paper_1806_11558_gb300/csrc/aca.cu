@@ -39,8 +39,9 @@
 
 namespace hm {
 
+// CTA sizes of the persistent kernel (the autotuner picks one; 128 by default)
 constexpr int ACA_THREADS = 128;
-constexpr int ACA_WARPS = ACA_THREADS / 32;
+constexpr int ACA_MAX_WARPS = 8;
 constexpr int SMALL_MAX_DIM = 256;  // warp-mode blocks: m, n <= this
 constexpr int HUGE_SUM = 2560;      // CTA-mode blocks with m + n above this use the large scratch
 // per-warp shared doubles in warp mode: fixed record, U/W row values, bitmaps, norm terms
@@ -110,11 +111,11 @@ __device__ __forceinline__ double warp_sum(double v) {
 struct AcaShared {
     float *fix;     // [64]  fixed panel record (float panel table row)
     double *vec;    // [kmax] U(i_r, :) or W(j_r, :)
-    double *red;    // [ACA_WARPS] sum partials (CTA mode)
-    Best *bred;     // [ACA_WARPS] argmax partials (CTA mode)
+    double *red;    // [warps] sum partials (CTA mode)
+    Best *bred;     // [warps] argmax partials (CTA mode)
     uint32_t *urow, *ucol;
     long long *ibc; // broadcast slot (CTA mode)
-    float *stage;   // norm terms per warp: CTA [ACA_WARPS][NORM_STRIDE], warp [NORM_STRIDE]
+    float *stage;   // norm terms per warp: CTA [warps][NORM_STRIDE], warp [NORM_STRIDE]
     float *res;     // reduced norm terms [NORM_STRIDE]
 };
 
@@ -125,9 +126,9 @@ constexpr int NORM_STRIDE = 2 + 2 * MAX_KMAX;
 // decides when to stop): res[0] = |u_r|^2, res[1] = |w_r|^2,
 // res[2 + l] = u_r . u_l, res[2 + r + l] = w_l . w_r (l < r).  One pass over
 // the columns, per-warp shuffle reductions, one shared-memory round.
-template <bool CTA>
+template <bool CTA, int NT>
 __device__ void norm_terms(const float *Uf, const float *Wf, int m, int n, int r, const AcaShared &sh) {
-    const int gs = CTA ? ACA_THREADS : 32, t = CTA ? (int)threadIdx.x : (int)(threadIdx.x & 31);
+    const int gs = CTA ? NT : 32, t = CTA ? (int)threadIdx.x : (int)(threadIdx.x & 31);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nvals = 2 + 2 * r;
     const float *ur = Uf + (int64_t)r * m, *wr = Wf + (int64_t)r * n;
@@ -166,7 +167,7 @@ __device__ void norm_terms(const float *Uf, const float *Wf, int m, int n, int r
         __syncthreads();
         for (int v = t; v < nvals; v += gs) {
             float a = 0.0f;
-            for (int w = 0; w < ACA_WARPS; ++w) a += sh.stage[w * NORM_STRIDE + v];
+            for (int w = 0; w < NT / 32; ++w) a += sh.stage[w * NORM_STRIDE + v];
             sh.res[v] = a;
         }
         __syncthreads();
@@ -175,9 +176,9 @@ __device__ void norm_terms(const float *Uf, const float *Wf, int m, int n, int r
     }
 }
 
-template <bool CTA>
+template <bool CTA, int NT>
 __device__ void norm_terms(const FF *Uf, const FF *Wf, int m, int n, int r, const AcaShared &sh) {
-    const int gs = CTA ? ACA_THREADS : 32, t = CTA ? (int)threadIdx.x : (int)(threadIdx.x & 31);
+    const int gs = CTA ? NT : 32, t = CTA ? (int)threadIdx.x : (int)(threadIdx.x & 31);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nvals = 2 + 2 * r;
     const FF *ur = Uf + (int64_t)r * m, *wr = Wf + (int64_t)r * n;
@@ -216,7 +217,7 @@ __device__ void norm_terms(const FF *Uf, const FF *Wf, int m, int n, int r, cons
         __syncthreads();
         for (int v = t; v < nvals; v += gs) {
             float a = 0.0f;
-            for (int w = 0; w < ACA_WARPS; ++w) a += sh.stage[w * NORM_STRIDE + v];
+            for (int w = 0; w < NT / 32; ++w) a += sh.stage[w * NORM_STRIDE + v];
             sh.res[v] = a;
         }
         __syncthreads();
@@ -225,9 +226,9 @@ __device__ void norm_terms(const FF *Uf, const FF *Wf, int m, int n, int r, cons
     }
 }
 
-template <bool CTA>
+template <bool CTA, int NT>
 struct Grp {
-    __device__ __forceinline__ static int size() { return CTA ? ACA_THREADS : 32; }
+    __device__ __forceinline__ static int size() { return CTA ? NT : 32; }
     __device__ __forceinline__ static int rank() { return CTA ? (int)threadIdx.x : (int)(threadIdx.x & 31); }
     __device__ __forceinline__ static void sync() {
         if (CTA) __syncthreads();
@@ -240,7 +241,7 @@ struct Grp {
         if (lane == 0) sh.red[w] = v;
         __syncthreads();
         double t = 0.0;
-        for (int k = 0; k < ACA_WARPS; ++k) t += sh.red[k];
+        for (int k = 0; k < NT / 32; ++k) t += sh.red[k];
         __syncthreads();
         return t;
     }
@@ -251,7 +252,7 @@ struct Grp {
         if (lane == 0) sh.bred[w] = b;
         __syncthreads();
         Best t = sh.bred[0];
-        for (int k = 1; k < ACA_WARPS; ++k)
+        for (int k = 1; k < NT / 32; ++k)
             if (better(sh.bred[k], t)) t = sh.bred[k];
         __syncthreads();
         return t;
@@ -313,10 +314,10 @@ __device__ __forceinline__ FF aca_entry(const float *fix, bool fixed_is_row, int
 // in scratch, as float pairs: the residual rows and columns (entry minus the
 // rank-one terms so far) are formed in double-float arithmetic on the FP32
 // units, to ~2^-48 of the largest term, like the entries themselves.
-template <bool CTA>
+template <bool CTA, int NT>
 __device__ int aca_block(const AcaArgs &A, int rb, int m, int cb, int n, FF *U, FF *W, const AcaShared &sh,
                          bool *hit_kmax) {
-    using G = Grp<CTA>;
+    using G = Grp<CTA, NT>;
     const int gs = G::size(), t = G::rank();
     const int wr = (m + 31) >> 5, wc = (n + 31) >> 5;
     for (int k = t; k < wr; k += gs) sh.urow[k] = 0u;
@@ -387,7 +388,7 @@ __device__ int aca_block(const AcaArgs &A, int rb, int m, int cb, int n, FF *U, 
         }
         if (t == 0) sh.ucol[jp >> 5] |= 1u << (jp & 31);
         // ---- Frobenius norm of the approximant ----
-        norm_terms<CTA>(U, W, m, n, r, sh);
+        norm_terms<CTA, NT>(U, W, m, n, r, sh);
         const float *res = CTA ? sh.res : sh.stage;
         const double nu2 = res[0], nw2 = res[1];
         double cross = 0.0;
@@ -405,10 +406,10 @@ __device__ int aca_block(const AcaArgs &A, int rb, int m, int cb, int n, FF *U, 
 }
 
 // copy the first k columns of U and W to the arena (bump allocation)
-template <bool CTA>
+template <bool CTA, int NT>
 __device__ void aca_store(const AcaArgs &A, int64_t b, int m, int n, int k, const FF *U, const FF *W,
                           const AcaShared &sh) {
-    using G = Grp<CTA>;
+    using G = Grp<CTA, NT>;
     const int gs = G::size(), t = G::rank();
     const int64_t need = (int64_t)k * (m + n);
     long long off = 0;
@@ -436,10 +437,10 @@ __device__ void aca_store(const AcaArgs &A, int64_t b, int m, int n, int k, cons
 // Wf) for the norm terms, the rank-one updates of the residuals in FP64.
 // Used by the warp workers (small blocks), where the FP32 units are the
 // busier pipe; the CTA workers (large blocks) use the float-pair form.
-template <bool CTA>
+template <bool CTA, int NT>
 __device__ int aca_block_d(const AcaArgs &A, int rb, int m, int cb, int n, double *U, double *W, float *Uf, float *Wf,
                          const AcaShared &sh, bool *hit_kmax) {
-    using G = Grp<CTA>;
+    using G = Grp<CTA, NT>;
     const int gs = G::size(), t = G::rank();
     const int wr = (m + 31) >> 5, wc = (n + 31) >> 5;
     for (int k = t; k < wr; k += gs) sh.urow[k] = 0u;
@@ -506,7 +507,7 @@ __device__ int aca_block_d(const AcaArgs &A, int rb, int m, int cb, int n, doubl
         }
         if (t == 0) sh.ucol[jp >> 5] |= 1u << (jp & 31);
         // ---- Frobenius norm of the approximant ----
-        norm_terms<CTA>(Uf, Wf, m, n, r, sh);
+        norm_terms<CTA, NT>(Uf, Wf, m, n, r, sh);
         const float *res = CTA ? sh.res : sh.stage;
         const double nu2 = res[0], nw2 = res[1];
         double cross = 0.0;
@@ -523,10 +524,10 @@ __device__ int aca_block_d(const AcaArgs &A, int rb, int m, int cb, int n, doubl
     return r;
 }
 
-template <bool CTA>
+template <bool CTA, int NT>
 __device__ void aca_store(const AcaArgs &A, int64_t b, int m, int n, int k, const double *U, const double *W,
                           const AcaShared &sh) {
-    using G = Grp<CTA>;
+    using G = Grp<CTA, NT>;
     const int gs = G::size(), t = G::rank();
     const int64_t need = (int64_t)k * (m + n);
     long long off = 0;
@@ -550,10 +551,14 @@ __device__ void aca_store(const AcaArgs &A, int64_t b, int m, int n, int k, cons
     }
 }
 
-__global__ void __launch_bounds__(ACA_THREADS, 5) aca_kernel(AcaArgs A) {
+// NT threads per CTA, MINB CTAs per SM in the register budget (about 100
+// registers per thread for every NT)
+template <int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) aca_kernel(AcaArgs A) {
+    constexpr int WARPS = NT / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double s_red[ACA_WARPS];
-    __shared__ Best s_bred[ACA_WARPS];
+    __shared__ double s_red[WARPS];
+    __shared__ Best s_bred[WARPS];
     __shared__ long long s_ibc;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
@@ -573,13 +578,13 @@ __global__ void __launch_bounds__(ACA_THREADS, 5) aca_kernel(AcaArgs A) {
         sh.urow = reinterpret_cast<uint32_t *>(d + 32 + MAX_KMAX);
         sh.ucol = sh.urow + A.big_words_r;
         sh.stage = reinterpret_cast<float *>(sh.ucol + A.big_words_c + ((A.big_words_r + A.big_words_c) & 1));
-        sh.res = sh.stage + ACA_WARPS * NORM_STRIDE;
+        sh.res = sh.stage + WARPS * NORM_STRIDE;
         double *U = tier == 0 ? A.scr_big + (int64_t)blockIdx.x * A.big_stride
                               : A.scr_med + (int64_t)blockIdx.x * A.med_stride;
         for (;;) {
             long long q = 0;
             if (threadIdx.x == 0) q = (long long)atomicAdd(tier == 0 ? A.q_huge : A.q_big, 1ull);
-            q = Grp<true>::bcast(q, sh);
+            q = Grp<true, NT>::bcast(q, sh);
             const int64_t q0 = tier == 0 ? 0 : A.n_huge;
             const int64_t qend = A.todo ? A.n_todo : (tier == 0 ? A.n_huge : A.n_big);
             if (q0 + q >= qend) break;
@@ -589,10 +594,10 @@ __global__ void __launch_bounds__(ACA_THREADS, 5) aca_kernel(AcaArgs A) {
             FF *Uff = reinterpret_cast<FF *>(U);
             FF *W = Uff + (int64_t)m * A.kmax;
             bool hit = false;
-            const int k = aca_block<true>(A, rb, m, cb, n, Uff, W, sh, &hit);
+            const int k = aca_block<true, NT>(A, rb, m, cb, n, Uff, W, sh, &hit);
             if (hit && threadIdx.x == 0) atomicAdd(A.kmax_hit, 1);
             __syncthreads();
-            aca_store<true>(A, b, m, n, k, Uff, W, sh);
+            aca_store<true, NT>(A, b, m, n, k, Uff, W, sh);
             __syncthreads();
         }
     }
@@ -612,7 +617,7 @@ __global__ void __launch_bounds__(ACA_THREADS, 5) aca_kernel(AcaArgs A) {
         sh.ucol = sh.urow + words;
         sh.stage = reinterpret_cast<float *>(d + 32 + MAX_KMAX + words);
         sh.res = sh.stage;
-        double *U = A.scr_small + ((int64_t)blockIdx.x * ACA_WARPS + warp) * A.small_stride;
+        double *U = A.scr_small + ((int64_t)blockIdx.x * WARPS + warp) * A.small_stride;
         for (;;) {
             int q = 0;
             if (lane == 0) q = (int)atomicAdd(A.q_small, 1ull);
@@ -625,10 +630,10 @@ __global__ void __launch_bounds__(ACA_THREADS, 5) aca_kernel(AcaArgs A) {
             float *Uf = reinterpret_cast<float *>(W + (int64_t)n * A.kmax);
             float *Wf = Uf + (int64_t)m * A.kmax;
             bool hit = false;
-            const int k = aca_block_d<false>(A, rb, m, cb, n, U, W, Uf, Wf, sh, &hit);
+            const int k = aca_block_d<false, NT>(A, rb, m, cb, n, U, W, Uf, Wf, sh, &hit);
             if (hit && lane == 0) atomicAdd(A.kmax_hit, 1);
             __syncwarp();
-            aca_store<false>(A, b, m, n, k, U, W, sh);
+            aca_store<false, NT>(A, b, m, n, k, U, W, sh);
             __syncwarp();
         }
     }
@@ -734,16 +739,29 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
         work.insert(work.end(), small.begin(), small.end());
     };
 
-    int occ = 0;
     const int words_r = (max_m_big + 31) / 32, words_c = (max_n_big + 31) / 32;
-    const size_t smem_big = sizeof(double) * (32 + MAX_KMAX) + sizeof(uint32_t) * (words_r + words_c + 1) +
-                            sizeof(float) * (ACA_WARPS + 1) * NORM_STRIDE;
-    const size_t smem_small = (size_t)ACA_WARPS * sizeof(double) * WARP_SMEM_DOUBLES;
-    const size_t smem = std::max(smem_big, smem_small);
-    HM_CUDA_CHECK(cudaFuncSetAttribute(aca_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    HM_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, aca_kernel, ACA_THREADS, smem));
-    if (occ < 1) fail(HM_EINTERNAL, "ACA kernel does not fit on an SM");
-    const int grid = num_sms() * occ;
+    // launch configurations: CTA sizes of 64, 128 and 256 threads, each with
+    // the register budget of about 100 per thread
+    struct Launch {
+        void (*kern)(AcaArgs);
+        int nt, occ;
+        size_t smem;
+    };
+    auto make_launch = [&](void (*kern)(AcaArgs), int nt) {
+        const int warps = nt / 32;
+        const size_t smem_big = sizeof(double) * (32 + MAX_KMAX) + sizeof(uint32_t) * (words_r + words_c + 1) +
+                                sizeof(float) * (warps + 1) * NORM_STRIDE;
+        const size_t smem_small = (size_t)warps * sizeof(double) * WARP_SMEM_DOUBLES;
+        Launch L{kern, nt, 0, std::max(smem_big, smem_small)};
+        HM_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
+        HM_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&L.occ, kern, nt, L.smem));
+        if (L.occ < 1) fail(HM_EINTERNAL, "ACA kernel (%d threads) does not fit on an SM", nt);
+        return L;
+    };
+    const Launch launches[3] = {make_launch(aca_kernel<64, 10>, 64), make_launch(aca_kernel<128, 5>, 128),
+                                make_launch(aca_kernel<256, 2>, 256)};
+    auto launch_of = [&](int nt) -> const Launch & { return launches[nt == 64 ? 0 : nt == 256 ? 2 : 1]; };
+    const int sms = num_sms();
 
     AcaArgs base{};
     base.pt = tr->pt.as<double>();
@@ -762,31 +780,34 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
     // block) for a bounded number of CTAs: two per SM, fewer where that
     // exceeds a quarter of the free memory or 20 GB; every CTA holds scratch
     // for the other large blocks (m + n <= HUGE_SUM)
+    int64_t huge_cap = 0;
     {
         size_t free_b = 0, total_b = 0;
         HM_CUDA_CHECK(cudaMemGetInfo(&free_b, &total_b));
         const int64_t budget = std::min<int64_t>(20LL << 30, (int64_t)(free_b / 4));
-        base.big_ctas = (int)std::min<int64_t>(grid, 2 * (int64_t)num_sms());
-        base.big_ctas = (int)std::max<int64_t>(std::min<int64_t>(num_sms(), grid),
-                                               std::min<int64_t>(base.big_ctas, budget / (8 * base.big_stride)));
+        huge_cap = std::max<int64_t>(sms, std::min<int64_t>(2 * (int64_t)sms, budget / (8 * base.big_stride)));
     }
+    auto huge_ctas = [&](int grid) { return (int)std::min<int64_t>(grid, huge_cap); };
     base.med_stride = std::min<int64_t>(base.big_stride, (int64_t)HUGE_SUM * kmax);
     DBuf scr_big, scr_med;
-    scr_big.alloc(sizeof(double) * base.big_stride * base.big_ctas);
-    scr_med.alloc(sizeof(double) * base.med_stride * grid);
+    scr_big.alloc(sizeof(double) * base.big_stride * huge_cap);
     base.scr_big = scr_big.as<double>();
-    base.scr_med = scr_med.as<double>();
 
-    // Autotuner of the warp / CTA split (the m + n bound of warp-mode
-    // blocks): on the first assembly with a given histogram of block sizes
-    // (log2 of m + n, block counts to two significant digits) every candidate
-    // runs the ACA of an evenly spaced sample of the blocks (scratch outputs,
-    // arena sized for k_max, so nothing overflows) and the fastest (the
-    // default unless another is more than 5 % faster) is kept for every later
-    // assembly with that histogram in this process.
+    // Autotuner of the launch: the warp / CTA split (the m + n bound of
+    // warp-mode blocks), the CTA size and the CTAs per SM.  On the first
+    // assembly with a given histogram of block sizes (log2 of m + n, block
+    // counts to two significant digits) the candidates run the ACA of an
+    // evenly spaced sample of the blocks (scratch outputs, arena sized for
+    // k_max, so nothing overflows), one parameter after the other (split at
+    // 128 threads and full occupancy, then the CTA size, then the CTAs per
+    // SM); in each the default stays unless another is more than 5 % faster.
+    // The choice is kept for every later assembly with that histogram in this
+    // process.
+    struct Tune {
+        int small_sum, nt, ctas;
+    };
     static std::mutex tune_mu;
-    static std::map<std::vector<int64_t>, int> tune_cache;
-    const int cands[] = {160, 320, 512};
+    static std::map<std::vector<int64_t>, Tune> tune_cache;
     std::vector<int64_t> key(32, 0);
     for (int32_t b : upper) {
         int lg = 0;
@@ -800,31 +821,36 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
     }
     key.push_back(kmax);
     key.push_back((int64_t)std::llround(std::log10(A->params.aca_eps) * 4.0));
-    int small_sum = 320;
+    Tune cfg{320, ACA_THREADS, launch_of(ACA_THREADS).occ};
     bool tuned = false;
     {
         std::lock_guard<std::mutex> lk(tune_mu);
         auto it = tune_cache.find(key);
         if (it != tune_cache.end()) {
-            small_sum = it->second;
+            cfg = it->second;
             tuned = true;
         }
     }
-    auto run = [&](const std::vector<int32_t> &blocks, int ss, int32_t *rank, int64_t *uwo, double *arena,
-                   int64_t cap, unsigned long long *ctr4, DBuf &scr_small, DBuf &d_work) -> float {
+    auto run = [&](const std::vector<int32_t> &blocks, const Tune &tc, int32_t *rank, int64_t *uwo, double *arena,
+                   int64_t cap, unsigned long long *ctr4, DBuf &scr_small, DBuf &d_work, AcaArgs *used) -> float {
+        const Launch &L = launch_of(tc.nt);
+        const int grid = sms * std::min(tc.ctas, L.occ);
         std::vector<int32_t> work;
         int64_t n_big = 0, n_huge = 0;
         int max_sum_small = 2;
-        split(blocks, ss, work, n_big, max_sum_small, n_huge);
+        split(blocks, tc.small_sum, work, n_big, max_sum_small, n_huge);
         AcaArgs a = base;
         a.n_huge = n_huge;
+        a.big_ctas = huge_ctas(grid);
+        scr_med.alloc(sizeof(double) * base.med_stride * grid);
+        a.scr_med = scr_med.as<double>();
         d_work.alloc(sizeof(int32_t) * std::max<size_t>(work.size(), 1));
         HM_CUDA_CHECK(cudaMemcpyAsync(d_work.p, work.data(), sizeof(int32_t) * work.size(), cudaMemcpyHostToDevice, s));
         a.work = d_work.as<int32_t>();
         a.n_big = n_big;
         a.n_work = (int64_t)work.size();
         a.small_stride = ((int64_t)max_sum_small * kmax * 3 + 1) / 2;  // U, W in FP64 + FP32 shadows
-        scr_small.alloc(sizeof(double) * a.small_stride * grid * ACA_WARPS);
+        scr_small.alloc(sizeof(double) * a.small_stride * grid * (tc.nt / 32));
         a.scr_small = scr_small.as<double>();
         a.arena_top = ctr4;
         a.q_big = ctr4 + 1;
@@ -844,7 +870,7 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
         HM_CUDA_CHECK(cudaEventRecord(t0, s));
         {
             Trace trace("aca_kernel", s);
-            aca_kernel<<<grid, ACA_THREADS, smem, s>>>(a);
+            L.kern<<<grid, L.nt, L.smem, s>>>(a);
             HM_LAUNCH_CHECK();
         }
         HM_CUDA_CHECK(cudaEventRecord(t1, s));
@@ -853,6 +879,7 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
         HM_CUDA_CHECK(cudaEventElapsedTime(&ms, t0, t1));
         cudaEventDestroy(t0);
         cudaEventDestroy(t1);
+        if (used) *used = a;
         return ms;
     };
     if (!tuned) {
@@ -870,23 +897,41 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
             t_uwo.alloc(sizeof(int64_t) * na);
             t_arena.alloc(sizeof(double) * sum_mn * kmax);
             t_ctr.alloc(sizeof(unsigned long long) * 5);
-            // the default (320) stays unless another candidate is more than
-            // 5 % faster: differences below that are timing noise, and a
-            // stable choice keeps the factors identical from process to
-            // process
-            float t[3];
-            for (int ci = 0; ci < 3; ++ci)
-                t[ci] = run(sample, cands[ci], t_rank.as<int32_t>(), t_uwo.as<int64_t>(), t_arena.as<double>(),
-                            sum_mn * kmax, t_ctr.as<unsigned long long>(), t_scr, t_work);
-            int bi = 1;
-            for (int ci = 0; ci < 3; ++ci)
-                if (t[ci] < t[bi] && t[ci] < 0.95f * t[1]) bi = ci;
-            small_sum = cands[bi];
+            auto time_of = [&](const Tune &tc) {
+                return run(sample, tc, t_rank.as<int32_t>(), t_uwo.as<int64_t>(), t_arena.as<double>(),
+                           sum_mn * kmax, t_ctr.as<unsigned long long>(), t_scr, t_work, nullptr);
+            };
+            // one parameter at a time; the current value stays unless another
+            // is more than 5 % faster (differences below that are timing
+            // noise, and a stable choice keeps the factors identical from
+            // process to process)
+            auto pick = [&](std::vector<Tune> cands) {
+                float t_cur = time_of(cfg);
+                Tune best = cfg;
+                float t_best = t_cur;
+                for (const Tune &c : cands) {
+                    const float t = time_of(c);
+                    if (t < t_best && t < 0.95f * t_cur) {
+                        best = c;
+                        t_best = t;
+                    }
+                }
+                cfg = best;
+            };
+            pick({Tune{160, cfg.nt, cfg.ctas}, Tune{512, cfg.nt, cfg.ctas}});
+            pick({Tune{cfg.small_sum, 64, launch_of(64).occ}, Tune{cfg.small_sum, 256, launch_of(256).occ}});
+            std::vector<Tune> fewer;
+            for (int c = launch_of(cfg.nt).occ - 1; c >= std::max(1, launch_of(cfg.nt).occ - 2); --c)
+                fewer.push_back(Tune{cfg.small_sum, cfg.nt, c});
+            if (!fewer.empty()) pick(fewer);
         }
         std::lock_guard<std::mutex> lk(tune_mu);
-        tune_cache[key] = small_sum;
+        tune_cache[key] = cfg;
     }
+    const int small_sum = cfg.small_sum;
     A->info.aca_small_sum = small_sum;
+    A->info.aca_threads = cfg.nt;
+    A->info.aca_ctas_per_sm = std::min(cfg.ctas, launch_of(cfg.nt).occ);
     HM_CUDA_CHECK(cudaMemsetAsync(uw_off.p, 0, sizeof(int64_t) * na, s));
     HM_CUDA_CHECK(cudaMemsetAsync(A->rank.p, 0, sizeof(int32_t) * na, s));
     // arena: sum (m + n) * k_guess, grown and the overflowed blocks re-run if needed
@@ -895,32 +940,13 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
     DBuf arena, ctr, scr_small, d_work;
     arena.alloc(sizeof(double) * cap);
     ctr.alloc(sizeof(unsigned long long) * 5);
-    const float ms = run(upper, small_sum, A->rank.as<int32_t>(), uw_off.as<int64_t>(), arena.as<double>(), cap,
-                         ctr.as<unsigned long long>(), scr_small, d_work);
+    // the arguments of that run are kept for an overflow re-run
+    AcaArgs a{};
+    const float ms = run(upper, cfg, A->rank.as<int32_t>(), uw_off.as<int64_t>(), arena.as<double>(), cap,
+                         ctr.as<unsigned long long>(), scr_small, d_work, &a);
     *sec = ms * 1e-3;
-    // the arguments of that run, for an overflow re-run
-    AcaArgs a = base;
-    {
-        std::vector<int32_t> work;
-        int64_t n_big = 0, n_huge = 0;
-        int max_sum_small = 2;
-        split(upper, small_sum, work, n_big, max_sum_small, n_huge);
-        a.work = d_work.as<int32_t>();
-        a.n_big = n_big;
-        a.n_huge = n_huge;
-        a.q_huge = ctr.as<unsigned long long>() + 4;
-        a.n_work = (int64_t)work.size();
-        a.small_stride = ((int64_t)max_sum_small * kmax * 3 + 1) / 2;  // U, W in FP64 + FP32 shadows
-        a.scr_small = scr_small.as<double>();
-        a.arena_top = ctr.as<unsigned long long>();
-        a.q_big = ctr.as<unsigned long long>() + 1;
-        a.q_small = ctr.as<unsigned long long>() + 2;
-        a.kmax_hit = reinterpret_cast<int *>(ctr.as<unsigned long long>() + 3);
-        a.rank = A->rank.as<int32_t>();
-        a.uw_off = uw_off.as<int64_t>();
-        a.arena = arena.as<double>();
-        a.arena_cap = cap;
-    }
+    const Launch &LL = launch_of(cfg.nt);
+    const int grid = sms * std::min(cfg.ctas, LL.occ);
     unsigned long long top = read_scalar(a.arena_top, s);
     if ((int64_t)top > cap) {
         // grow: keep what fits, re-run the blocks that did not fit (CTA-wide)
@@ -947,7 +973,7 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
         HM_CUDA_CHECK(cudaMemcpyAsync(a.arena_top, &used_u, sizeof(used_u), cudaMemcpyHostToDevice, s));
         HM_CUDA_CHECK(cudaMemsetAsync(a.q_huge, 0, sizeof(unsigned long long), s));
         Trace trace("aca_kernel", s);
-        aca_kernel<<<grid, ACA_THREADS, smem, s>>>(a);
+        LL.kern<<<grid, LL.nt, LL.smem, s>>>(a);
         HM_LAUNCH_CHECK();
         top = read_scalar(a.arena_top, s);
         if ((int64_t)top > newcap) fail(HM_ENOMEM, "ACA factor arena overflow after growth");
