@@ -907,7 +907,10 @@ def run_blockmv(torch, hm, case="bumped6"):
     X = torch.randn((16, n), dtype=torch.float64, device="cuda")
     Y = torch.empty_like(X)
     mi = hm.hm_matrix_get_info(A)
-    out = {"workload": "%s (%d panels), leaf 128, 16-RHS product" % (case, n), "n": n}
+    ti = hm.hm_tree_get_info(tree)
+    out = {"workload": "%s (%d panels), leaf 128, 16-RHS product" % (case, n), "n": n,
+           "dense_entries": mi["dense_entries"], "u_entries": mi["u_entries"], "lr_entries": mi["lr_entries"],
+           "total_rank": mi["mean_rank"] * ti["n_adm"]}
     for prec, name, fb in ((hm.HM_BF16, "bf16", 2), (hm.HM_F32, "fp32", 4)):
         if prec == hm.HM_F32:
             hm.hm_matrix_add_copy(A, hm.HM_F32)
