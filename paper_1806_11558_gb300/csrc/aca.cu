@@ -797,7 +797,7 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
     // warp-mode blocks), the CTA size and the CTAs per SM.  On the first
     // assembly with a given histogram of block sizes (log2 of m + n, block
     // counts to two significant digits) the candidates run the ACA of an
-    // evenly spaced sample of the blocks (scratch outputs, arena sized for
+    // evenly spaced sample of the blocks up to the huge tier (scratch outputs, arena sized for
     // k_max, so nothing overflows), one parameter after the other (split at
     // 128 threads and full occupancy, then the CTA size, then the CTAs per
     // SM); in each the default stays unless another is more than 5 % faster.
@@ -883,15 +883,22 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
         return ms;
     };
     if (!tuned) {
+        // the sample leaves out the huge blocks (m + n > HUGE_SUM): a handful
+        // of them would make the sample's time the time of its longest block
+        // (one CTA each), not the throughput the launch parameters decide
+        std::vector<int32_t> pool;
+        pool.reserve(upper.size());
+        for (int32_t b : upper)
+            if (msum(b) <= HUGE_SUM) pool.push_back(b);
         const size_t target = 30000;
-        const size_t step = std::max<size_t>(1, upper.size() / target);
+        const size_t step = std::max<size_t>(1, pool.size() / target);
         std::vector<int32_t> sample;
         int64_t sum_mn = 0;
-        for (size_t i = 0; i < upper.size(); i += step) {
-            sample.push_back(upper[i]);
-            sum_mn += msum(upper[i]);
+        for (size_t i = 0; i < pool.size(); i += step) {
+            sample.push_back(pool[i]);
+            sum_mn += msum(pool[i]);
         }
-        if (sample.size() < upper.size() / 2 && sample.size() >= 1000) {
+        if (sample.size() < pool.size() / 2 && sample.size() >= 1000) {
             DBuf t_rank, t_uwo, t_arena, t_ctr, t_scr, t_work;
             t_rank.alloc(sizeof(int32_t) * na);
             t_uwo.alloc(sizeof(int64_t) * na);
