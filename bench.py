@@ -73,6 +73,14 @@ FF_FLOPS_PER_PAIR = 93
 # DRAM traffic per launch from an ncu capture, valid while the kernel's source
 # file is unchanged (sha256 of the file at capture time); null otherwise.
 TRAFFIC = {
+    # ncu capture at the level-6 bumped sphere (leaf 128, 81,920 panels): 1.814 GB per launch, 1.040 x its
+    # algorithmic bytes; scaled to a level-8 launch by the algorithmic bytes (37.87 GB), traffic growing in
+    # proportion with the matrix
+    "row_mrhs_kernel.f32": {"source": "paper_1806_11558_gb300/csrc/mrhs.cu",
+                            "sha256": "be69df80740db256bfad9ec2fe1f06c719ca944e693fe6c8377121cb0e18eb40",
+                            "bytes_per_launch": 39384768988,
+                            "workload": "large",
+                            "profile": "profiles/mrhs_kernels_bumped6.md"},
     "row_kernel.f64": {"source": "paper_1806_11558_gb300/csrc/mv_kernels.cuh",
                        "sha256": "317d8d2539db41cb43c4abddd08fe283fb2cbbf21bc763087ebc67cdb6960454",
                        "bytes_per_launch": 15113751808 + 5691392,

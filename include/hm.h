@@ -87,6 +87,16 @@ typedef struct {
  *                 ~1e-14 relative), like the ACA entries; 1 = in FP64
  *                 arithmetic.  Identical panels are always FP64.  Regular
  *                 entries of leaves wider than 250 panels always use FP64.
+ *  mrhs_tcgen05 : 0 (default) = the row pass of the 16-right-hand-side
+ *                 product (hm_matvec_block, batched inner solves) on
+ *                 mma.sync; 1 = on the fifth-generation tensor cores
+ *                 (tcgen05.mma, accumulators in tensor memory).  Both give
+ *                 the product to the same ~2^-16 accuracy; on a GB300 the
+ *                 tcgen05 form measured about 2x slower on the level-8
+ *                 sphere, so it is kept for comparison, not as the default.
+ *                 Its waits are bounded: one that gives up makes the
+ *                 batched solve, or hm_matvec_block (which then
+ *                 synchronises its stream), return HM_ETIMEOUT.
  *  The FP64 master copy is always kept. */
 typedef struct {
     double aca_eps;
@@ -95,6 +105,7 @@ typedef struct {
     hm_dtype factor_dtype;
     hm_dtype dense_dtype;
     int32_t nearfield_fp64;
+    int32_t mrhs_tcgen05;
 } hm_assemble_params;
 
 /* Solver parameters.

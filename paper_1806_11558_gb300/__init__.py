@@ -40,7 +40,8 @@ class TreeParams(ctypes.Structure):
 
 class AssembleParams(ctypes.Structure):
     _fields_ = [("aca_eps", ctypes.c_double), ("aca_kmax", ctypes.c_int32), ("ss_order", ctypes.c_int32),
-                ("factor_dtype", ctypes.c_int), ("dense_dtype", ctypes.c_int), ("nearfield_fp64", ctypes.c_int32)]
+                ("factor_dtype", ctypes.c_int), ("dense_dtype", ctypes.c_int), ("nearfield_fp64", ctypes.c_int32),
+                ("mrhs_tcgen05", ctypes.c_int32)]
 
 
 class SolveParams(ctypes.Structure):
@@ -230,10 +231,10 @@ def hm_load_vector_geom(tree, sources, f, stream=None):
 
 
 def hm_assemble(tree, aca_eps=1e-6, aca_kmax=64, ss_order=8, factor_dtype=HM_F64, dense_dtype=HM_F64,
-                nearfield_fp64=0, stream=None):
+                nearfield_fp64=0, mrhs_tcgen05=0, stream=None):
     out = ctypes.c_void_p()
     prm = AssembleParams(float(aca_eps), int(aca_kmax), int(ss_order), int(factor_dtype), int(dense_dtype),
-                         int(nearfield_fp64))
+                         int(nearfield_fp64), int(mrhs_tcgen05))
     _check(lib().hm_assemble(tree, ctypes.byref(prm), _stream(stream), ctypes.byref(out)))
     return out
 

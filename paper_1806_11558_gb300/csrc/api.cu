@@ -45,6 +45,7 @@ void potential_impl(const hm_tree *tr, const double *pts, int64_t K, int trans, 
 void matvec_noalloc(const hm_matrix *A, int32_t nrhs, hm_dtype prec, const double *x, double *y, double alpha,
                     double beta, cudaStream_t s);
 double measure_fma_peak(hm_dtype kind, cudaStream_t s);
+int mrhs_error(const hm_matrix *A, cudaStream_t s);
 void div_diag(const double *a, const double *d, int64_t n, int nrhs, double *out, cudaStream_t s);
 void mul_diag(const double *a, const double *d, int64_t n, int nrhs, double *out, cudaStream_t s);
 void axpby_diag(const double *v, const double *d, int64_t n, int nrhs, double alpha, double beta, double *y,
@@ -158,6 +159,7 @@ hm_status hm_assemble(const hm_tree *tree, const hm_assemble_params *params, hm_
         if (params->factor_dtype < HM_F64 || params->factor_dtype > HM_BF16) fail(HM_EINVAL, "bad factor_dtype");
         if (params->dense_dtype != HM_F64 && params->dense_dtype != HM_F32) fail(HM_EINVAL, "bad dense_dtype");
         if (params->nearfield_fp64 != 0 && params->nearfield_fp64 != 1) fail(HM_EINVAL, "nearfield_fp64 must be 0 or 1");
+        if (params->mrhs_tcgen05 != 0 && params->mrhs_tcgen05 != 1) fail(HM_EINVAL, "mrhs_tcgen05 must be 0 or 1");
         cudaStream_t s = (cudaStream_t)stream;
         const auto t0 = std::chrono::steady_clock::now();
         std::unique_ptr<hm_matrix> A(new hm_matrix());
@@ -253,6 +255,9 @@ hm_status hm_matvec_block(const hm_matrix *A, int32_t nrhs, hm_dtype prec, const
         if (!A->dense32.p || (prec == HM_F32 ? !A->up32.p : !A->upbf.p))
             fail(HM_EINVAL, "the low-precision copies for this precision were not assembled");
         matvec_mrhs(A, prec, nrhs, d_x, d_y, alpha, beta, (cudaStream_t)stream);
+        // the tcgen05 row pass reports a bounded wait that gave up (the form compared, not the default)
+        if (A->params.mrhs_tcgen05 && mrhs_error(A, (cudaStream_t)stream))
+            fail(HM_ETIMEOUT, "a bounded wait of the tensor-memory row pass gave up");
     });
 }
 

@@ -35,6 +35,7 @@ void bj_apply_cols(const hm_matrix *A, const double *v, double *z, int cols, boo
 void permute_to_morton(const hm_tree *tr, const double *x, double *xm, cudaStream_t s);
 void permute_from_morton(const hm_tree *tr, const double *ym, double alpha, double beta, double *y, cudaStream_t s);
 hm_dtype raise_inner(const hm_matrix *A, hm_dtype cur, cudaStream_t s);
+int mrhs_error(const hm_matrix *A, cudaStream_t s);
 
 constexpr int BMR = 16;        // columns of one tensor-core product
 constexpr int BITEM = 8192;    // entries of one work item
@@ -641,6 +642,7 @@ hm_status solve_batched(const hm_matrix *A, int nrhs, const double *b_orig, doub
     for (int r = 0; r < nrhs; ++r)
         permute_from_morton(tr, x.as<double>() + (int64_t)r * n, 1.0, 0.0, x_orig + (int64_t)r * n, s);
     HM_CUDA_CHECK(cudaStreamSynchronize(s));
+    if (mrhs_error(A, s)) fail(HM_ETIMEOUT, "a bounded wait of the tensor-memory row pass gave up");
     if (info) {
         info->status = st;
         info->iters = iters;

@@ -725,8 +725,6 @@ template <int MT> static int row_smem() {
 // factors 7.32 against 7.26 ms, BF16 6.32 against 6.47 ms per product)
 constexpr int RP_WARPS = 4;
 
-// the row pass on tcgen05 / TMEM (mrhs_tc.cu) instead of mma.sync
-constexpr bool RP_TCGEN05 = false;
 
 template <class TF>
 static void matvec_mrhs_impl(const hm_matrix *A, const TF *up, const float *X, double *Y, __nv_bfloat16 *Xh,
@@ -761,7 +759,7 @@ static void matvec_mrhs_impl(const hm_matrix *A, const TF *up, const float *X, d
             A->up_K.as<int32_t>(), A->up_colptr.as<int64_t>(), A->tidx.as<int32_t>(), up, Th, Tl, Xh, Xl, Y);
         HM_LAUNCH_CHECK();
     };
-    if (RP_TCGEN05 && A->mrhs_err.p) {
+    if (A->params.mrhs_tcgen05 && A->mrhs_err.p) {  // the measured tcgen05 / TMEM row pass (mrhs_tc.cu)
         row_mrhs_tc<TF>(A, up, Th, Tl, Xh, Xl, Y, A->mrhs_err.as<int>(), s);
         return;
     }

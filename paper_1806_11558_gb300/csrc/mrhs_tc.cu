@@ -12,7 +12,7 @@
 // N = 16); the epilogue adds the two halves of D.
 //
 // One CTA of 128 threads per leaf row cluster (and 128-row tile).  Per slice:
-// the threads load the panel rows with coalesced 16-byte loads two slices
+// the threads load the panel rows with coalesced 16-byte loads one slice
 // ahead into registers, split them and store both planes into shared memory
 // in the canonical K-major layout without swizzle (8 x 16-byte core
 // matrices); the gathered rows of B land by cp.async, one slice ahead, in the
@@ -219,10 +219,11 @@ __device__ bool run_panel(Ctx &c, const Src<TP> &s, int rows, int *err) {
     const int ns = (s.K + KS - 1) / KS;
     if (ns == 0) return true;
     const int plane = a_plane(c.arows);
-    // panel slices are loaded two slices ahead of their conversion (registers)
-    Slice<TP, U> cur, nxt;
+    // panel slices are loaded one slice ahead of their conversion (registers;
+    // two ahead measured slower: 168 registers with spills, 17.7 against
+    // 15.4 ms per level-8 row pass)
+    Slice<TP, U> cur;
     load_slice(cur, s, rows, 0);
-    if (ns > 1) load_slice(nxt, s, rows, KS);
     gather_b(c.b + (c.slice % B_RING) * B_BYTES, s, 0);
     for (int k = 0; k < ns; ++k) {
         const long long sidx = c.slice + k;
@@ -232,9 +233,8 @@ __device__ bool run_panel(Ctx &c, const Src<TP> &s, int rows, int *err) {
         // the stage's previous slice (sidx - 2) must be consumed by its MMAs
         const bool ok = sidx < 2 || wait(c.bar + st, (uint32_t)(((sidx >> 1) - 1) & 1));
         if (ok) store_slice(cur, hi, lo, rows, c.arows);
-        cur = nxt;
-        if (k + 2 < ns) load_slice(nxt, s, rows, (k + 2) * KS);  // consumed two iterations later
         if (k + 1 < ns) {
+            load_slice(cur, s, rows, (k + 1) * KS);  // registers: consumed next iteration
             gather_b(c.b + ((sidx + 1) % B_RING) * B_BYTES, s, (k + 1) * KS);
             asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // this slice's B landed
         } else {

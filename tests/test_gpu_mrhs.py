@@ -7,7 +7,8 @@ are BF16 pairs (hi + lo) that keep ~16 significant bits, so the product
 agrees with that reference to ~2^-16 relative; its error against the FP64
 operator itself is stated as a number.  Leaves of 40, 80 and 160 rows (1,
 5 and 10 row tiles of 16), 16, 5 and 20 right-hand sides (one pass, a
-ragged pass, a full and a ragged pass)."""
+ragged pass, a full and a ragged pass).  Both row passes: mma.sync (the
+default) and the tcgen05 / TMEM one (hm_assemble_params.mrhs_tcgen05)."""
 import numpy as np
 import pytest
 
@@ -53,10 +54,11 @@ def oracle_apply(orc, g, ex, X):
 
 @pytest.mark.parametrize("name,mesh,leaf", CASES, ids=[c[0] for c in CASES])
 @pytest.mark.parametrize("prec", [1, 2], ids=["f32", "bf16"])
-def test_block_product_matches_the_oracle(orc, name, mesh, leaf, prec):
+@pytest.mark.parametrize("tc", [0, 1], ids=["mma_sync", "tcgen05"])
+def test_block_product_matches_the_oracle(orc, name, mesh, leaf, prec, tc):
     torch = need_gpu()
     V, T = mesh()
-    g = GpuH(V, T, leaf=leaf, eta=1.5, eps=1e-6, factor_dtype=prec, dense_dtype=1)
+    g = GpuH(V, T, leaf=leaf, eta=1.5, eps=1e-6, factor_dtype=prec, dense_dtype=1, mrhs_tcgen05=tc)
     try:
         hm = g.hm
         ex = g.export()
