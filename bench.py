@@ -774,7 +774,10 @@ def run_workload(name):
     from paper_1806_11558_gb300 import build as hb
     hb.build()
     fn = {"batching": run_batching, "differentiation": run_differentiation,
-          "blockmv": run_blockmv, "blockmv7": lambda t, h: run_blockmv(t, h, "precision")}[name]
+          "blockmv": run_blockmv, "blockmv7": lambda t, h: run_blockmv(t, h, "precision"),
+          "blockmv_tc": lambda t, h: run_blockmv(t, h, tcgen05=1),
+          "blockmv8": lambda t, h: run_blockmv(t, h, "large"),
+          "blockmv8_tc": lambda t, h: run_blockmv(t, h, "large", tcgen05=1)}[name]
     ck = Clocks(torch.cuda.current_device())
     ck.start()
     out = fn(torch, hm)
@@ -902,21 +905,24 @@ def run_differentiation(torch, hm):
     return out
 
 
-def run_blockmv(torch, hm, case="bumped6"):
+def run_blockmv(torch, hm, case="bumped6", tcgen05=0):
     """Multi-RHS product case (profiling): a bumped icosphere (level 6, or 7
     with case "precision"), leaf 128, BF16 factors, then FP32 factors added
-    from the FP64 master; three 16-right-hand-side tensor-core products each."""
+    from the FP64 master; three 16-right-hand-side tensor-core products each
+    (row pass on mma.sync, or on tcgen05 / TMEM with tcgen05 = 1)."""
     import meshgen
     cfg = meshgen.config(case)
     n = cfg["T"].shape[0]
     V, T = torch.from_numpy(cfg["V"]).cuda(), torch.from_numpy(cfg["T"]).cuda()
     tree = hm.hm_build_tree(V, T, eta=1.5, leaf_size=128)
-    A = hm.hm_assemble(tree, aca_eps=1e-6, aca_kmax=64, ss_order=8, factor_dtype=hm.HM_BF16, dense_dtype=hm.HM_F32)
+    A = hm.hm_assemble(tree, aca_eps=1e-6, aca_kmax=64, ss_order=8, factor_dtype=hm.HM_BF16, dense_dtype=hm.HM_F32,
+                       mrhs_tcgen05=tcgen05)
     X = torch.randn((16, n), dtype=torch.float64, device="cuda")
     Y = torch.empty_like(X)
     mi = hm.hm_matrix_get_info(A)
     ti = hm.hm_tree_get_info(tree)
-    out = {"workload": "%s (%d panels), leaf 128, 16-RHS product" % (case, n), "n": n,
+    out = {"workload": "%s (%d panels), leaf 128, 16-RHS product, row pass on %s" % (
+               case, n, "tcgen05" if tcgen05 else "mma.sync"), "n": n,
            "dense_entries": mi["dense_entries"], "u_entries": mi["u_entries"], "lr_entries": mi["lr_entries"],
            "total_rank": mi["mean_rank"] * ti["n_adm"]}
     for prec, name, fb in ((hm.HM_BF16, "bf16", 2), (hm.HM_F32, "fp32", 4)):
@@ -950,7 +956,8 @@ def main():
                          "other meshgen recipes run with the one-source step for profiling and parity runs")
     ap.add_argument("--profile-step", action="store_true",
                     help="run exactly one step (no warm-up, no extras) and print its phase times")
-    ap.add_argument("--workload", default=None, choices=["batching", "differentiation", "blockmv", "blockmv7"],
+    ap.add_argument("--workload", default=None,
+                    choices=["batching", "differentiation", "blockmv", "blockmv7", "blockmv_tc", "blockmv8", "blockmv8_tc"],
                     help="measure one of the other workloads once and print its numbers (not a bench line)")
     args = ap.parse_args()
     if args.workload:

@@ -48,42 +48,50 @@ struct Item {
 
 static unsigned gx(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 65535)); }
 
-// part[item][l] = V_l(col, i0:i1) . w(col, i0:i1), l < nv (0 for inactive systems)
+// part[item][l] = V_l(col, i0:i1) . w(col, i0:i1), l < nv (0 for inactive systems).
+// Warp k of the CTA takes the k-th contiguous chunk of the item and runs over
+// every vector: per vector its lanes stride the chunk with four independent
+// accumulators (the chunk of w stays in L1 after the first vector) and add
+// them by shuffles; the eight warps' sums of each vector are added in a
+// fixed order at the end, so the CTA synchronises once.
+constexpr int BMAXV = 129;  // restart + 1
 __global__ void __launch_bounds__(BTHREADS) bdots_kernel(const Item *__restrict__ items, const double *__restrict__ V,
                                                          int64_t vstride, int64_t n, int nv,
                                                          const double *__restrict__ w, const int *__restrict__ act,
                                                          double *__restrict__ part, const LoopCtl *ctl) {
-    if (ctl) nv = ctl->j + 1;  // graph form: V_0..V_j of step j
-    __shared__ double s_red[BTHREADS / 32][8];
+    if (ctl) nv = ctl->j + 1;
+    constexpr int BW = BTHREADS / 32;
+    __shared__ double s_part[BW][BMAXV];
     const Item it = items[blockIdx.x];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool on = act[it.sys] != 0;
+    const int64_t len = it.i1 - it.i0;
+    const int64_t chunk = ((len + BW - 1) / BW + 31) / 32 * 32;
+    const int64_t c0 = it.i0 + warp * chunk, c1 = min(it.i1, c0 + chunk);
     const double *wc = w + (int64_t)it.col * n;
-    for (int c0 = 0; c0 < nv; c0 += 8) {
-        double acc[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) acc[c] = 0.0;
+    for (int l = 0; l < nv; ++l) {
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
         if (on) {
-            for (int64_t i = it.i0 + threadIdx.x; i < it.i1; i += BTHREADS) {
-                const double wi = wc[i];
-#pragma unroll
-                for (int c = 0; c < 8; ++c)
-                    if (c0 + c < nv) acc[c] = fma(V[(int64_t)(c0 + c) * vstride + (int64_t)it.col * n + i], wi, acc[c]);
+            const double *vl = V + (int64_t)l * vstride + (int64_t)it.col * n;
+            int64_t i = c0 + lane;
+            for (; i + 96 < c1; i += 128) {
+                a0 = fma(vl[i], wc[i], a0);
+                a1 = fma(vl[i + 32], wc[i + 32], a1);
+                a2 = fma(vl[i + 64], wc[i + 64], a2);
+                a3 = fma(vl[i + 96], wc[i + 96], a3);
             }
+            for (; i < c1; i += 32) a0 = fma(vl[i], wc[i], a0);
         }
+        double t = (a0 + a1) + (a2 + a3);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            double v = acc[c];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) s_red[warp][c] = v;
-        }
-        __syncthreads();
-        if (threadIdx.x < 8 && c0 + (int)threadIdx.x < nv) {
-            double t = 0.0;
-            for (int k = 0; k < BTHREADS / 32; ++k) t += s_red[k][threadIdx.x];
-            part[(int64_t)blockIdx.x * nv + c0 + threadIdx.x] = t;
-        }
-        __syncthreads();
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) s_part[warp][l] = t;
+    }
+    __syncthreads();
+    for (int l = threadIdx.x; l < nv; l += BTHREADS) {
+        double t = 0.0;
+        for (int k = 0; k < BW; ++k) t += s_part[k][l];
+        part[(int64_t)blockIdx.x * nv + l] = t;
     }
 }
 
