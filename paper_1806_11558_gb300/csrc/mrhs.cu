@@ -87,11 +87,18 @@ constexpr int CM_COLS = 64;                 // panel columns per tile
 // staged slices); the four column groups' sums are added in a fixed order at
 // the end, so 4 and 8 warps give the same result bit for bit.
 // ---------------------------------------------------------------------------
-constexpr int RP_KG = 4;           // column groups of 16 per slice
-constexpr int RP_KS = 64;          // panel columns per slice
-constexpr int RP_STAGES = 3;
 constexpr int RP_APAD = 8;         // elements of padding per staged panel row
 constexpr int RP_BSTRIDE = MR + 8; // bf16 per staged column of X / T (48 bytes)
+
+// Shape of the row pass: WARPS warps per CTA, KG column groups of 16 per
+// slice (slices of 16 KG panel columns), ST pipeline stages; the WARPS / KG
+// warp groups split the MT row tiles.
+template <int WARPS_, int KG_, int ST_> struct RpCfg {
+    static constexpr int WARPS = WARPS_, THREADS = 32 * WARPS_, KG = KG_, KS = 16 * KG_, STAGES = ST_;
+    static constexpr int MG = WARPS_ / KG_;                         // warp groups over the row tiles
+    static constexpr int NJ = (4 * KS + THREADS - 1) / THREADS;    // gathered 16-byte pieces per thread
+    template <int MT> static constexpr int mth() { return (MT + MG - 1) / MG; }  // row tiles per warp
+};
 
 __device__ __forceinline__ void ldmatrix_x4(uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3, const void *p) {
     const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
@@ -100,43 +107,43 @@ __device__ __forceinline__ void ldmatrix_x4(uint32_t &r0, uint32_t &r1, uint32_t
                  : "r"(a));
 }
 
-template <int MT, class TP> struct RpStage {
-    static constexpr int A_BYTES = 16 * MT * (RP_KS + RP_APAD) * (int)sizeof(TP);
-    static constexpr int B_BYTES = 2 * RP_KS * RP_BSTRIDE * 2;
+template <int MT, class TP, class C> struct RpStage {
+    static constexpr int A_BYTES = 16 * MT * (C::KS + RP_APAD) * (int)sizeof(TP);
+    static constexpr int B_BYTES = 2 * C::KS * RP_BSTRIDE * 2;
     static constexpr int BYTES = A_BYTES + B_BYTES;
 };
 
 // the gathered row indices this thread needs for the slice at column c0
 // (columns (tid >> 2) + (THREADS / 4) j), loaded ahead of their use
-template <int THREADS> constexpr int rp_nj() { return 4 * RP_KS / THREADS; }
-template <int THREADS>
-__device__ __forceinline__ void rp_idx(const int32_t *__restrict__ idx, int K, int c0, int (&ir)[rp_nj<THREADS>()]) {
+template <class C>
+__device__ __forceinline__ void rp_idx(const int32_t *__restrict__ idx, int K, int c0, int (&ir)[C::NJ]) {
 #pragma unroll
-    for (int j = 0; j < rp_nj<THREADS>(); ++j) {
-        const int col = c0 + (threadIdx.x >> 2) + (THREADS / 4) * j;
-        ir[j] = col < K ? __ldg(idx + col) : 0;
+    for (int j = 0; j < C::NJ; ++j) {
+        const int c = (threadIdx.x >> 2) + (C::THREADS / 4) * j, col = c0 + c;
+        ir[j] = c < C::KS && col < K ? __ldg(idx + col) : 0;
     }
 }
 
-template <int MT, class TP, int THREADS>
+template <int MT, class TP, class C>
 __device__ __forceinline__ void rp_load(unsigned char *stage, const TP *__restrict__ Pn, int K, int rows_valid, int c0,
-                                        const int (&ir)[rp_nj<THREADS>()], const __nv_bfloat16 *__restrict__ Zh,
+                                        const int (&ir)[C::NJ], const __nv_bfloat16 *__restrict__ Zh,
                                         const __nv_bfloat16 *__restrict__ Zl) {
     TP *sA = reinterpret_cast<TP *>(stage);
-    __nv_bfloat16 *sBh = reinterpret_cast<__nv_bfloat16 *>(stage + RpStage<MT, TP>::A_BYTES);
-    __nv_bfloat16 *sBl = sBh + RP_KS * RP_BSTRIDE;
+    __nv_bfloat16 *sBh = reinterpret_cast<__nv_bfloat16 *>(stage + RpStage<MT, TP, C>::A_BYTES);
+    __nv_bfloat16 *sBl = sBh + C::KS * RP_BSTRIDE;
     constexpr int PER = 16 / (int)sizeof(TP);  // elements per 16-byte copy
-    constexpr int VPR = RP_KS / PER;           // copies per row
-    for (int e = threadIdx.x; e < 16 * MT * VPR; e += THREADS) {
+    constexpr int VPR = C::KS / PER;           // copies per row
+    for (int e = threadIdx.x; e < 16 * MT * VPR; e += C::THREADS) {
         const int r = e / VPR, v = e - (e / VPR) * VPR;
         const int col = c0 + PER * v;
         const bool ok = r < rows_valid && col < K;
-        cp_async16(sA + r * (RP_KS + RP_APAD) + PER * v, ok ? (const void *)(Pn + (int64_t)r * K + col) : (const void *)Pn,
+        cp_async16(sA + r * (C::KS + RP_APAD) + PER * v, ok ? (const void *)(Pn + (int64_t)r * K + col) : (const void *)Pn,
                    ok);
     }
 #pragma unroll
-    for (int j = 0; j < rp_nj<THREADS>(); ++j) {
-        const int c = (threadIdx.x >> 2) + (THREADS / 4) * j, q = threadIdx.x & 3;  // q: hi / lo x first / second 8 rhs
+    for (int j = 0; j < C::NJ; ++j) {
+        const int c = (threadIdx.x >> 2) + (C::THREADS / 4) * j, q = threadIdx.x & 3;  // q: hi / lo x first / second 8 rhs
+        if (c >= C::KS) continue;
         const int col = c0 + c;
         const bool ok = col < K;
         const __nv_bfloat16 *src = ((q & 2) ? Zl : Zh) + (int64_t)ir[j] * MR + 8 * (q & 1);
@@ -145,17 +152,14 @@ __device__ __forceinline__ void rp_load(unsigned char *stage, const TP *__restri
     }
 }
 
-// row tiles of one warp: all MT with 4 warps, one half with 8
-template <int MT, int WARPS> constexpr int rp_mth() { return WARPS == 4 ? MT : (MT + 1) / 2; }
-
-template <int MT, class TP, int WARPS>
-__device__ __forceinline__ void rp_compute(const unsigned char *stage, float (&acc)[rp_mth<MT, WARPS>()][2][4]) {
-    constexpr int MTH = rp_mth<MT, WARPS>();
+template <int MT, class TP, class C>
+__device__ __forceinline__ void rp_compute(const unsigned char *stage, float (&acc)[C::template mth<MT>()][2][4]) {
+    constexpr int MTH = C::template mth<MT>();
     const TP *sA = reinterpret_cast<const TP *>(stage);
-    const __nv_bfloat16 *sBh = reinterpret_cast<const __nv_bfloat16 *>(stage + RpStage<MT, TP>::A_BYTES);
-    const __nv_bfloat16 *sBl = sBh + RP_KS * RP_BSTRIDE;
+    const __nv_bfloat16 *sBh = reinterpret_cast<const __nv_bfloat16 *>(stage + RpStage<MT, TP, C>::A_BYTES);
+    const __nv_bfloat16 *sBl = sBh + C::KS * RP_BSTRIDE;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
-    const int kb = 16 * (warp % RP_KG), mt0 = MTH * (warp / RP_KG);
+    const int kb = 16 * (warp % C::KG), mt0 = MTH * (warp / C::KG);
     uint32_t bh[2][2], bl[2][2];
 #pragma unroll
     for (int nt = 0; nt < 2; ++nt) {
@@ -167,8 +171,8 @@ __device__ __forceinline__ void rp_compute(const unsigned char *stage, float (&a
         const int mt = mt0 + ml;
         if (MTH != MT && mt >= MT) break;
         if constexpr (sizeof(TP) == 4) {
-            const float *r0 = reinterpret_cast<const float *>(sA) + (16 * mt + g) * (RP_KS + RP_APAD) + kb + 2 * t;
-            const float *r1 = r0 + 8 * (RP_KS + RP_APAD);
+            const float *r0 = reinterpret_cast<const float *>(sA) + (16 * mt + g) * (C::KS + RP_APAD) + kb + 2 * t;
+            const float *r1 = r0 + 8 * (C::KS + RP_APAD);
             const float2 p0 = *reinterpret_cast<const float2 *>(r0), p1 = *reinterpret_cast<const float2 *>(r0 + 8);
             const float2 q0 = *reinterpret_cast<const float2 *>(r1), q1 = *reinterpret_cast<const float2 *>(r1 + 8);
             float h[8], l[8];
@@ -194,7 +198,7 @@ __device__ __forceinline__ void rp_compute(const unsigned char *stage, float (&a
         } else {
             // ldmatrix.x4: matrices (rows 0-7, k 0-7), (rows 8-15, k 0-7), (rows 0-7, k 8-15), (rows 8-15, k 8-15)
             const __nv_bfloat16 *base = reinterpret_cast<const __nv_bfloat16 *>(sA) +
-                                        (16 * mt + (lane & 15)) * (RP_KS + RP_APAD) + kb + 8 * (lane >> 4);
+                                        (16 * mt + (lane & 15)) * (C::KS + RP_APAD) + kb + 8 * (lane >> 4);
             uint32_t a0, a1, a2, a3;
             ldmatrix_x4(a0, a1, a2, a3, base);
 #pragma unroll
@@ -206,39 +210,38 @@ __device__ __forceinline__ void rp_compute(const unsigned char *stage, float (&a
     }
 }
 
-template <int MT, class TP, int WARPS>
+template <int MT, class TP, class C>
 __device__ __forceinline__ void rp_panel(unsigned char *sm, const TP *__restrict__ Pn, int K, int rows_valid,
                                          const int32_t *__restrict__ idx, const __nv_bfloat16 *__restrict__ Zh,
                                          const __nv_bfloat16 *__restrict__ Zl,
-                                         float (&acc)[rp_mth<MT, WARPS>()][2][4]) {
-    constexpr int SB = RpStage<MT, TP>::BYTES, THREADS = 32 * WARPS;
-    const int ns = (K + RP_KS - 1) / RP_KS;
-    int ir[rp_nj<THREADS>()];
+                                         float (&acc)[C::template mth<MT>()][2][4]) {
+    constexpr int SB = RpStage<MT, TP, C>::BYTES, KS = C::KS, ST = C::STAGES;
+    const int ns = (K + KS - 1) / KS;
+    int ir[C::NJ];
 #pragma unroll
-    for (int st = 0; st < RP_STAGES - 1; ++st) {
+    for (int st = 0; st < ST - 1; ++st) {
         if (st < ns) {
-            rp_idx<THREADS>(idx, K, st * RP_KS, ir);
-            rp_load<MT, TP, THREADS>(sm + st * SB, Pn, K, rows_valid, st * RP_KS, ir, Zh, Zl);
+            rp_idx<C>(idx, K, st * KS, ir);
+            rp_load<MT, TP, C>(sm + st * SB, Pn, K, rows_valid, st * KS, ir, Zh, Zl);
         }
         cp_async_commit();
     }
-    rp_idx<THREADS>(idx, K, (RP_STAGES - 1) * RP_KS, ir);  // indices of the next slice to load
+    rp_idx<C>(idx, K, (ST - 1) * KS, ir);  // indices of the next slice to load
     for (int sl = 0; sl < ns; ++sl) {
-        cp_async_wait<RP_STAGES - 2>();
+        cp_async_wait<ST - 2>();
         __syncthreads();
-        const int nx = sl + RP_STAGES - 1;
-        if (nx < ns)
-            rp_load<MT, TP, THREADS>(sm + (nx % RP_STAGES) * SB, Pn, K, rows_valid, nx * RP_KS, ir, Zh, Zl);
+        const int nx = sl + ST - 1;
+        if (nx < ns) rp_load<MT, TP, C>(sm + (nx % ST) * SB, Pn, K, rows_valid, nx * KS, ir, Zh, Zl);
         cp_async_commit();
-        rp_idx<THREADS>(idx, K, (nx + 1) * RP_KS, ir);  // consumed one iteration later
-        rp_compute<MT, TP, WARPS>(sm + (sl % RP_STAGES) * SB, acc);
+        rp_idx<C>(idx, K, (nx + 1) * KS, ir);  // consumed one iteration later
+        rp_compute<MT, TP, C>(sm + (sl % ST) * SB, acc);
     }
     cp_async_wait<0>();
     __syncthreads();
 }
 
-template <int MT, class TF, int WARPS>
-__global__ void __launch_bounds__(32 * WARPS) row_mrhs_kernel(
+template <int MT, class TF, class C>
+__global__ void __launch_bounds__(C::THREADS) row_mrhs_kernel(
     const int32_t *__restrict__ leaf_begin, const int64_t *__restrict__ rho_off, const int32_t *__restrict__ rho_K,
     const int64_t *__restrict__ rho_colptr, const int32_t *__restrict__ colidx, const float *__restrict__ dense,
     const int64_t *__restrict__ up_off, const int32_t *__restrict__ up_K, const int64_t *__restrict__ up_colptr,
@@ -250,8 +253,8 @@ __global__ void __launch_bounds__(32 * WARPS) row_mrhs_kernel(
     const int32_t r0 = leaf_begin[rho], mr = leaf_begin[rho + 1] - r0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, t = lane & 3;
     const int Kd = rho_K[rho], Ku = up_K[rho];
-    constexpr int MTH = rp_mth<MT, WARPS>();
-    const int kg = warp % RP_KG, mt0 = MTH * (warp / RP_KG);
+    constexpr int MTH = C::template mth<MT>();
+    const int kg = warp % C::KG, mt0 = MTH * (warp / C::KG);
     for (int r0t = 0; r0t < mr; r0t += 16 * MT) {
         const int rows = min(16 * MT, mr - r0t);
         float acc[MTH][2][4];
@@ -261,11 +264,10 @@ __global__ void __launch_bounds__(32 * WARPS) row_mrhs_kernel(
             for (int nt = 0; nt < 2; ++nt)
 #pragma unroll
                 for (int e = 0; e < 4; ++e) acc[ml][nt][e] = 0.0f;
-        rp_panel<MT, float, WARPS>(sm, dense + rho_off[rho] + (int64_t)r0t * Kd, Kd, rows, colidx + rho_colptr[rho],
-                                   Xh, Xl, acc);
-        rp_panel<MT, TF, WARPS>(sm, up + up_off[rho] + (int64_t)r0t * Ku, Ku, rows, tidx + up_colptr[rho], Th, Tl,
-                                acc);
-        // per-column-group sums -> shared memory -> fixed-order sum over the 4 groups
+        rp_panel<MT, float, C>(sm, dense + rho_off[rho] + (int64_t)r0t * Kd, Kd, rows, colidx + rho_colptr[rho], Xh,
+                               Xl, acc);
+        rp_panel<MT, TF, C>(sm, up + up_off[rho] + (int64_t)r0t * Ku, Ku, rows, tidx + up_colptr[rho], Th, Tl, acc);
+        // per-column-group sums -> shared memory -> fixed-order sum over the KG groups
         float *red = reinterpret_cast<float *>(sm);
 #pragma unroll
         for (int ml = 0; ml < MTH; ++ml) {
@@ -282,9 +284,9 @@ __global__ void __launch_bounds__(32 * WARPS) row_mrhs_kernel(
             }
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < rows * MR; e += 32 * WARPS) {
+        for (int e = threadIdx.x; e < rows * MR; e += C::THREADS) {
             float sacc = 0.0f;
-            for (int w = 0; w < RP_KG; ++w) sacc += red[w * (16 * MT) * MR + e];
+            for (int w = 0; w < C::KG; ++w) sacc += red[w * (16 * MT) * MR + e];
             Y[(int64_t)(r0 + r0t) * MR + e] = (double)sacc;
         }
         __syncthreads();
@@ -327,8 +329,14 @@ __device__ __forceinline__ void store_t_pair(__nv_bfloat16 *Th, __nv_bfloat16 *T
 // ldmatrix.trans from the [row][rhs] tile; B = W fragments by ldmatrix.trans
 // (BF16 panels) or by shared-memory loads split into BF16 pairs (FP32
 // panels).  Each of the 8 warps owns 8 of the 64 columns.
-constexpr int BP_KC = 64;               // panel rows per chunk
-constexpr int BP_STAGES = 3;
+// Chunks of 16 panel rows in 6 stages (35 KB of shared memory per CTA; the
+// kernel's 43 registers allow 5 CTAs of 8 warps per SM).  Measured on the
+// level-8 sphere (FP32 factors, rows x stages): 64 x 3 4.70 ms, 64 x 4 5.61,
+// 32 x 3 4.37, 32 x 4 4.23, 32 x 5 4.85, 32 x 6 4.83, 16 x 6 3.85, 16 x 8 4.29;
+// the same t bit for bit (the k order of the MMAs does not depend on them).
+constexpr int BP_KC = 16;               // panel rows per chunk
+static_assert(BP_KC % 16 == 0, "bp_compute takes 16 chunk rows per MMA step");
+constexpr int BP_STAGES = 6;
 constexpr int BP_XSTRIDE = MR + 8;      // bf16 per staged row of X (48 bytes)
 constexpr int BP_WS16 = CM_COLS + 8;    // bf16 per staged W row (144 bytes)
 constexpr int BP_WS32 = CM_COLS + 4;    // floats per staged W row (conflict-free column reads)
@@ -715,16 +723,16 @@ void row_mrhs_tc(const hm_matrix *A, const TF *up, const __nv_bfloat16 *Th, cons
 
 
 
-template <int MT> static int row_smem() {
-    const int st = RP_STAGES * RpStage<MT, float>::BYTES, red = RP_KG * 16 * MT * MR * 4;
+template <int MT, class C> static int row_smem() {
+    const int st = C::STAGES * RpStage<MT, float, C>::BYTES, red = C::KG * 16 * MT * MR * 4;
     return st > red ? st : red;
 }
 
-// warps per CTA of row_mrhs_kernel: 8 warps (two halves of the row tiles
-// over the same stages) measured no faster on the level-8 sphere (FP32
-// factors 7.32 against 7.26 ms, BF16 6.32 against 6.47 ms per product)
-constexpr int RP_WARPS = 4;
-
+// Shape of the row pass (warps, 16-column groups per slice, stages).
+// Measured on the level-8 sphere (FP32 factors): 4 warps x 64-column slices
+// x 3 stages 7.26 ms; 8 warps over the same stages (the row tiles split in
+// two) 7.32 ms.
+using RpDefault = RpCfg<4, 4, 3>;
 
 template <class TF>
 static void matvec_mrhs_impl(const hm_matrix *A, const TF *up, const float *X, double *Y, __nv_bfloat16 *Xh,
@@ -750,10 +758,10 @@ static void matvec_mrhs_impl(const hm_matrix *A, const TF *up, const float *X, d
         }
     }
     const int tiles = (tr->max_leaf + 15) / 16;
-    auto launch = [&](auto kern, int smem) {
+    auto launch = [&](auto kern, int smem, int threads) {
         HM_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         Trace tr_(f32 ? "row_mrhs_kernel.f32" : "row_mrhs_kernel.bf16", s);
-        kern<<<(unsigned)tr->n_leaf, 32 * RP_WARPS, smem, s>>>(
+        kern<<<(unsigned)tr->n_leaf, threads, smem, s>>>(
             tr->leaf_begin.as<int32_t>(), tr->rho_off.as<int64_t>(), tr->rho_K.as<int32_t>(),
             tr->rho_colptr.as<int64_t>(), tr->colidx.as<int32_t>(), A->dense32.as<float>(), A->up_off.as<int64_t>(),
             A->up_K.as<int32_t>(), A->up_colptr.as<int64_t>(), A->tidx.as<int32_t>(), up, Th, Tl, Xh, Xl, Y);
@@ -763,9 +771,10 @@ static void matvec_mrhs_impl(const hm_matrix *A, const TF *up, const float *X, d
         row_mrhs_tc<TF>(A, up, Th, Tl, Xh, Xl, Y, A->mrhs_err.as<int>(), s);
         return;
     }
-    if (tiles <= 3) launch(row_mrhs_kernel<3, TF, RP_WARPS>, row_smem<3>());
-    else if (tiles <= 5) launch(row_mrhs_kernel<5, TF, RP_WARPS>, row_smem<5>());
-    else launch(row_mrhs_kernel<8, TF, RP_WARPS>, row_smem<8>());
+    using C = RpDefault;
+    if (tiles <= 3) launch(row_mrhs_kernel<3, TF, C>, row_smem<3, C>(), C::THREADS);
+    else if (tiles <= 5) launch(row_mrhs_kernel<5, TF, C>, row_smem<5, C>(), C::THREADS);
+    else launch(row_mrhs_kernel<8, TF, C>, row_smem<8, C>(), C::THREADS);
 }
 
 // Y (Morton [n][16] FP64) = H X (Morton [n][16] FP32) with the FP32 near field
