@@ -76,16 +76,15 @@ constexpr int CM_COLS = 64;                 // panel columns per tile
 
 
 // ---------------------------------------------------------------------------
-// row_mrhs_kernel: Y_rho = P_rho X(colidx) + U~_rho T(tidx), one CTA of WARPS
-// (4 or 8) warps per leaf row cluster, 16 MT rows per pass.  The panels are
-// walked in slices of 64 columns through a 3-stage cp.async pipeline: the
-// slice's panel rows and its gathered rows of X / T (as BF16 hi and lo,
-// [column][rhs]) land in shared memory while the previous slices are
-// multiplied; warp w owns the 16 columns 16 (w mod 4) .. 16 (w mod 4) + 15 of
-// every slice (A fragments by LDS / ldmatrix, B fragments by ldmatrix.trans)
-// and, with 8 warps, one half of the MT row tiles (the two halves share the
-// staged slices); the four column groups' sums are added in a fixed order at
-// the end, so 4 and 8 warps give the same result bit for bit.
+// row_mrhs_kernel: Y_rho = P_rho X(colidx) + U~_rho T(tidx), one CTA per leaf
+// row cluster, 16 MT rows per pass.  The panels are walked in slices of 16 KG
+// columns through a cp.async pipeline of ST stages: the slice's panel rows and
+// its gathered rows of X / T (as BF16 hi and lo, [column][rhs]) land in
+// shared memory while the previous slices are multiplied; warp w owns the 16
+// columns 16 (w mod KG) .. of every slice (A fragments by LDS / ldmatrix, B
+// fragments by ldmatrix.trans) and, with more warps than column groups, one
+// part of the MT row tiles (the parts share the staged slices); the KG column
+// groups' sums are added in a fixed order at the end.
 // ---------------------------------------------------------------------------
 constexpr int RP_APAD = 8;         // elements of padding per staged panel row
 constexpr int RP_BSTRIDE = MR + 8; // bf16 per staged column of X / T (48 bytes)
@@ -728,10 +727,14 @@ template <int MT, class C> static int row_smem() {
     return st > red ? st : red;
 }
 
-// Shape of the row pass (warps, 16-column groups per slice, stages).
-// Measured on the level-8 sphere (FP32 factors): 4 warps x 64-column slices
-// x 3 stages 7.26 ms; 8 warps over the same stages (the row tiles split in
-// two) 7.32 ms.
+// Shapes of the row pass (warps x 16-column groups per slice x stages).  For
+// 80-row leaves (MT = 5) measured on the level-8 sphere, FP32 factors, ms per
+// product: 4x4x3 7.25, 4x4x2 7.64, 4x4x4 9.98, 8x4x3 7.32, 4x2x5 12.06,
+// 4x2x4 9.20, 8x2x4 8.64, 8x2x6 9.91, 8x8x3 9.00, 16x8x2 6.85, 16x8x3 8.32,
+// 16x16x2 6.65, 8x8x2 6.42-6.57: wide slices over 8 warps, two stages (111
+// KB of shared memory, two CTAs per SM).  The other tile counts keep 4x4x3
+// (8x8x2 would hold one CTA per SM for 128-row tiles).
+using RpShape5 = RpCfg<8, 8, 2>;
 using RpDefault = RpCfg<4, 4, 3>;
 
 template <class TF>
@@ -772,8 +775,9 @@ static void matvec_mrhs_impl(const hm_matrix *A, const TF *up, const float *X, d
         return;
     }
     using C = RpDefault;
+    using C5 = RpShape5;
     if (tiles <= 3) launch(row_mrhs_kernel<3, TF, C>, row_smem<3, C>(), C::THREADS);
-    else if (tiles <= 5) launch(row_mrhs_kernel<5, TF, C>, row_smem<5, C>(), C::THREADS);
+    else if (tiles <= 5) launch(row_mrhs_kernel<5, TF, C5>, row_smem<5, C5>(), C5::THREADS);
     else launch(row_mrhs_kernel<8, TF, C>, row_smem<8, C>(), C::THREADS);
 }
 
