@@ -73,12 +73,12 @@ FF_FLOPS_PER_PAIR = 93
 # DRAM traffic per launch from an ncu capture, valid while the kernel's source
 # file is unchanged (sha256 of the file at capture time); null otherwise.
 TRAFFIC = {
-    # ncu capture at the level-6 bumped sphere (leaf 128, 81,920 panels): 1.814 GB per launch, 1.040 x its
-    # algorithmic bytes; scaled to a level-8 launch by the algorithmic bytes (37.87 GB), traffic growing in
-    # proportion with the matrix
+    # ncu capture at the level-6 bumped sphere (leaf 128, 81,920 panels): 1.8138 GB per launch, 1.0395 x its
+    # algorithmic bytes (1.7448 GB); scaled to a level-8 launch by the algorithmic bytes (37.87 GB), traffic
+    # growing in proportion with the matrix
     "row_mrhs_kernel.f32": {"source": "paper_1806_11558_gb300/csrc/mrhs.cu",
-                            "sha256": "be69df80740db256bfad9ec2fe1f06c719ca944e693fe6c8377121cb0e18eb40",
-                            "bytes_per_launch": 39384768988,
+                            "sha256": "3cf4eae46d88c8b608c86621bca7d0c6aaacbdae033378d3239f8b6a7024bf2c",
+                            "bytes_per_launch": 39372871231,
                             "workload": "large",
                             "profile": "profiles/mrhs_kernels_bumped6.md"},
     "row_kernel.f64": {"source": "paper_1806_11558_gb300/csrc/mv_kernels.cuh",

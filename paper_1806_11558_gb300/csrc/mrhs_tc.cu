@@ -18,8 +18,9 @@
 // matrices); the gathered rows of B land by cp.async, one slice ahead, in the
 // MN-major layout; one thread issues the MMAs of the slice and commits them
 // to the slice buffer's mbarrier, which the threads wait on before they
-// overwrite that buffer two slices later.  Every wait is bounded: a wait that
-// gives up records an error code, waits (bounded) for the MMAs it issued,
+// overwrite that buffer two slices later.  Every wait is bounded
+// (hm_set_wait_limit): a wait that gives up records an error code, waits for
+// its B copies and (bounded by the default limit) for the MMAs it issued,
 // frees the tensor memory and leaves the CTA.
 #include <cuda_bf16.h>
 
@@ -39,7 +40,6 @@ constexpr int B_BYTES = KS / 8 * B_LBO;       // 4 KB per slice
 constexpr int B_RING = 3;                     // B is gathered one slice ahead
 constexpr int A_SBO = 128;                    // bytes between M-adjacent core matrices of A
 constexpr int TMEM_COLS = 32;
-constexpr long long WAIT_CYCLES = 4000000000LL;  // bound of an mbarrier wait (~2 s at 2 GHz)
 
 __host__ __device__ constexpr int a_lbo(int arows) { return arows * 16; }      // K-adjacent core matrices
 __host__ __device__ constexpr int a_plane(int arows) { return KS / 8 * a_lbo(arows); }
@@ -85,12 +85,14 @@ __device__ __forceinline__ bool try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 
-// bounded by SM clock cycles (try_wait itself may suspend for a while)
-__device__ __forceinline__ bool wait(uint64_t *bar, uint32_t parity) {
+// bounded by `limit` SM clock cycles (try_wait itself may suspend for a
+// while); a limit of 0 gives up without polling (hm_set_wait_limit)
+__device__ __forceinline__ bool wait(uint64_t *bar, uint32_t parity, long long limit) {
     const long long t0 = clock64();
-    while (!try_wait(bar, parity))
-        if (clock64() - t0 > WAIT_CYCLES) return false;
-    return true;
+    for (;;) {
+        if (clock64() - t0 >= limit) return false;
+        if (try_wait(bar, parity)) return true;
+    }
 }
 
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -208,6 +210,7 @@ struct Ctx {
     uint32_t tmem;       // D
     int arows;
     long long slice;     // slices issued by this CTA so far
+    long long limit;     // bound of the waits (SM clock cycles)
     bool first;          // the next MMA starts the tile's accumulation
     bool failed;
 };
@@ -231,7 +234,7 @@ __device__ bool run_panel(Ctx &c, const Src<TP> &s, int rows, int *err) {
         unsigned char *hi = c.a + st * 2 * plane, *lo = hi + plane;
         unsigned char *bb = c.b + (sidx % B_RING) * B_BYTES;
         // the stage's previous slice (sidx - 2) must be consumed by its MMAs
-        const bool ok = sidx < 2 || wait(c.bar + st, (uint32_t)(((sidx >> 1) - 1) & 1));
+        const bool ok = sidx < 2 || wait(c.bar + st, (uint32_t)(((sidx >> 1) - 1) & 1), c.limit);
         if (ok) store_slice(cur, hi, lo, rows, c.arows);
         if (k + 1 < ns) {
             load_slice(cur, s, rows, (k + 1) * KS);  // registers: consumed next iteration
@@ -242,6 +245,7 @@ __device__ bool run_panel(Ctx &c, const Src<TP> &s, int rows, int *err) {
         }
         fence_proxy();
         if (__syncthreads_or(!ok)) {  // a wait that gave up, seen by every thread alike
+            cp_wait_all();            // the next slice's B may still be landing
             if (threadIdx.x == 0) atomicExch(err, 1);
             c.failed = true;
             c.slice += k;
@@ -277,11 +281,12 @@ __global__ void __launch_bounds__(THREADS, 3) row_mrhs_tc_kernel(
     const int64_t *__restrict__ up_off, const int32_t *__restrict__ up_K, const int64_t *__restrict__ up_colptr,
     const int32_t *__restrict__ tidx, const TF *__restrict__ up, const __nv_bfloat16 *__restrict__ Th,
     const __nv_bfloat16 *__restrict__ Tl, const __nv_bfloat16 *__restrict__ Xh, const __nv_bfloat16 *__restrict__ Xl,
-    double *__restrict__ Y, int arows, int *err) {
+    double *__restrict__ Y, int arows, int *err, long long wait_limit) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     Ctx c;
     c.arows = arows;
+    c.limit = wait_limit;
     c.a = sm;
     c.b = sm + 4 * a_plane(arows);
     c.bar = reinterpret_cast<uint64_t *>(c.b + B_RING * B_BYTES);
@@ -317,7 +322,8 @@ __global__ void __launch_bounds__(THREADS, 3) row_mrhs_tc_kernel(
         // the tile's last commit covers every MMA issued so far
         float d[32];
         const bool any = c.slice > 0;
-        const bool ok = !any || wait(c.bar + (int)((c.slice - 1) & 1), (uint32_t)(((c.slice - 1) >> 1) & 1));
+        const bool ok =
+            !any || wait(c.bar + (int)((c.slice - 1) & 1), (uint32_t)(((c.slice - 1) >> 1) & 1), c.limit);
         if (__syncthreads_or(!ok)) {
             if (threadIdx.x == 0) atomicExch(err, 1);
             c.failed = true;
@@ -351,7 +357,7 @@ __global__ void __launch_bounds__(THREADS, 3) row_mrhs_tc_kernel(
     }
     if (c.failed && c.slice > 0) {
         // wait (bounded) for the MMAs this CTA issued before the TMEM goes away
-        wait(c.bar + (int)((c.slice - 1) & 1), (uint32_t)(((c.slice - 1) >> 1) & 1));
+        wait(c.bar + (int)((c.slice - 1) & 1), (uint32_t)(((c.slice - 1) >> 1) & 1), WAIT_LIMIT_DEFAULT);
     }
     fence_before();
     __syncthreads();
@@ -376,7 +382,7 @@ void row_mrhs_tc(const hm_matrix *A, const TF *up, const __nv_bfloat16 *Th, cons
     kern<<<(unsigned)tr->n_leaf, tc::THREADS, smem, s>>>(
         tr->leaf_begin.as<int32_t>(), tr->rho_off.as<int64_t>(), tr->rho_K.as<int32_t>(), tr->rho_colptr.as<int64_t>(),
         tr->colidx.as<int32_t>(), A->dense32.as<float>(), A->up_off.as<int64_t>(), A->up_K.as<int32_t>(),
-        A->up_colptr.as<int64_t>(), A->tidx.as<int32_t>(), up, Th, Tl, Xh, Xl, Y, arows, err);
+        A->up_colptr.as<int64_t>(), A->tidx.as<int32_t>(), up, Th, Tl, Xh, Xl, Y, arows, err, wait_limit());
     HM_LAUNCH_CHECK();
 }
 

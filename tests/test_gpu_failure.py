@@ -5,6 +5,10 @@
   HM_ETIMEOUT, after the blocks have waited (with the default limit) for the
   copies they started, and the context stays usable: the next assembly with
   the default limit gives the same operator as before.
+* The same for the tcgen05 / TMEM row pass of the 16-right-hand-side product
+  (bulk copies, cp.async gathers and MMAs in flight when the waits give up):
+  the product returns HM_ETIMEOUT, every role drains what it started, the
+  TMEM is freed, and the next product is the same bit for bit.
 * Injected allocation failures (hm_set_fault_injection) at every position of
   a build + assembly + product: each failing call returns HM_ENOMEM, frees
   what it had allocated (device memory back to its level before the call
@@ -61,6 +65,33 @@ def test_wait_limit_zero_times_out_and_context_survives(mesh):
         hm.hm_free(tree)
     torch.cuda.synchronize()  # the context still answers
     assert torch.equal(_build(hm, torch, Vd, Td, x), y0)
+
+
+def test_wait_limit_zero_in_the_tensor_memory_row_pass(mesh):
+    hm, torch, Vd, Td, x, y0 = mesh
+    tree = hm.hm_build_tree(Vd, Td, eta=1.5, leaf_size=64)
+    A = hm.hm_assemble(tree, aca_eps=1e-6, factor_dtype=hm.HM_F32, dense_dtype=hm.HM_F32, mrhs_tcgen05=1)
+    try:
+        X = torch.from_numpy(np.random.default_rng(5).standard_normal((16, x.numel()))).cuda()
+        Y0, Y = torch.empty_like(X), torch.empty_like(X)
+        hm.hm_matvec_block(A, X, Y0, prec=hm.HM_F32)
+        torch.cuda.synchronize()
+        try:
+            hm.hm_set_wait_limit(0)
+            with pytest.raises(hm.HMError) as e:
+                hm.hm_matvec_block(A, X, Y, prec=hm.HM_F32)
+            assert e.value.status == hm.HM_ETIMEOUT
+            assert "row pass gave up" in str(e.value)
+        finally:
+            hm.hm_set_wait_limit(-1)
+        torch.cuda.synchronize()  # the context still answers
+        for _ in range(2):
+            hm.hm_matvec_block(A, X, Y, prec=hm.HM_F32)
+            torch.cuda.synchronize()
+            assert torch.equal(Y, Y0)
+    finally:
+        hm.hm_free(A)
+        hm.hm_free(tree)
 
 
 def test_injected_allocation_failures_free_everything(mesh):
