@@ -41,8 +41,9 @@ LARGE = dict(workload="unit icosphere level 8, Galerkin single-layer Laplace, P0
              case="large", panels=1310720, leaf_size=128, eta=1.5, aca_eps=1e-6, aca_kmax=64, ss_order=8,
              nrhs=16, sources="16 seeded exterior point sources, |p| uniform in [2, 4]", solve_rel_tol=1e-12,
              form="mixed: FP32 near field + FP32 factors; lockstep GMRES whose inner solves use the 16-RHS "
-                  "tensor-core product; FP64 iterative refinement",
-             inner_tol=1e-4, restart=128, precond=True, batched=True)
+                  "tensor-core product; iterative refinement on the FP64 master, its residuals by the 16-RHS "
+                  "double-float product",
+             inner_tol=1e-4, restart=128, precond=True, batched=True, resid_df=True)
 PRECISION = dict(workload="bumped icosphere level 7, Galerkin single-layer Laplace, P0",
                  case="precision", panels=327680, leaf_size=64, eta=1.5, aca_eps=1e-7, aca_kmax=64, ss_order=8,
                  nrhs=1, source=[3.0, 0.0, 0.0], solve_rel_tol=1e-12, inner="fp32 factors + fp32 near field",
@@ -69,6 +70,10 @@ FP32_PEAK_TFLOPS = 152 * 2.07e9 * 128 * 2 / 1e12  # 80.5
 # FP32 flops of one pair evaluation in the double-float entry (ACA and the
 # regular near field; TwoSum 6, TwoProduct 2 with its FMA counted 2, ...): 93 per pair
 FF_FLOPS_PER_PAIR = 93
+# FP32 flops of one term of the double-float product (TwoProduct 1 + 2, TwoSum 6, two cross-term FMAs 4,
+# two adds into the compensation 2), FMAs counted 2: 15 flops in 12 instructions, so the instruction mix
+# caps these kernels at 15 / 24 = 0.625 of the FMA peak
+DF_FLOPS_PER_TERM = 15
 
 # DRAM traffic per launch from an ncu capture, valid while the kernel's source
 # file is unchanged (sha256 of the file at capture time); null otherwise.
@@ -129,6 +134,10 @@ def algorithmic_work(mi, ti, dense_leaves, n):
         "col_bcp_kernel.f32": ("hbm", 4.0 * w + xr * (n + K), "byte"),
         "col_bcp_kernel.bf16": ("hbm", 2.0 * w + xr * (n + K), "byte"),
         "nearfield_kernel": ("alu32", float(nf_entries) * PAIRS_PER_ENTRY * FF_FLOPS_PER_PAIR, "flop"),
+        # double-float product of the FP64 master, 16 right-hand sides per launch: DF_FLOPS_PER_TERM per
+        # (entry, right-hand side)
+        "row_df_kernel": ("alu32", DF_FLOPS_PER_TERM * MR * (d + u), "flop"),
+        "col_df_kernel": ("alu32", DF_FLOPS_PER_TERM * MR * w, "flop"),
         "nearfield_kernel.f64": ("alu", float(nf_entries) * PAIRS_PER_ENTRY * FLOPS_PER_PAIR, "flop"),
         "aca_kernel": ("alu32", float(mi["aca_entries"]) * PAIRS_PER_ENTRY * FF_FLOPS_PER_PAIR, "flop"),
     }
@@ -308,7 +317,8 @@ def run_large(args, world, hm, torch, W=LARGE, case="large"):
         e[2].record(stream)
         hm.hm_load_vector(tree, sdev, F)
         e[3].record(stream)
-        info = hm.hm_solve(A, F, X, refine=1, inner_dtype=hm.HM_F32, inner_tol=W["inner_tol"], max_refine=40, **opts)
+        info = hm.hm_solve(A, F, X, refine=1, inner_dtype=hm.HM_F32, inner_tol=W["inner_tol"], max_refine=40,
+                           resid_df=int(W.get("resid_df", False)), **opts)
         e[4].record(stream)
         torch.cuda.synchronize()
         mi = hm.hm_matrix_get_info(A)
@@ -355,6 +365,10 @@ def run_large(args, world, hm, torch, W=LARGE, case="large"):
     last, tree, A = step(Vd, Td, srcd, keep=True)
     Xm = X.clone()
     mi, ti = last["minfo"], last["tinfo"]
+    # the FP64 residual of the mixed solutions (one FP64 product per system)
+    HX = torch.empty_like(F)
+    hm.hm_matvec(A, Xm, HX, prec=hm.HM_F64)
+    resid64 = float(torch.max(torch.linalg.norm(F - HX, dim=1) / torch.linalg.norm(F, dim=1)))
     X64 = torch.zeros_like(F)
     a, b = _ev(torch), _ev(torch)
     a.record(stream)
@@ -389,6 +403,16 @@ def run_large(args, world, hm, torch, W=LARGE, case="large"):
         byts = mi["dense_entries"] * 4 + mi["lr_entries"] * fb
         mv[name] = {"s": sec, "matrix_gb": byts / 1e9, "gbs_matrix": byts / sec / 1e9,
                     "s_per_rhs": sec / R}
+    # the FP64 master, 16 right-hand sides in double-float arithmetic (the residual product of the refinement)
+    hm.hm_matvec_block(A, Xr, Yr, prec=hm.HM_F64)
+    a.record(stream)
+    for _ in range(3):
+        hm.hm_matvec_block(A, Xr, Yr, prec=hm.HM_F64)
+    b.record(stream)
+    torch.cuda.synchronize()
+    sec = a.elapsed_time(b) / 3e3
+    byts = (mi["dense_entries"] + mi["lr_entries"]) * 8
+    mv["16rhs_df64"] = {"s": sec, "matrix_gb": byts / 1e9, "gbs_matrix": byts / sec / 1e9, "s_per_rhs": sec / R}
     for name, prec, esz in (("1rhs_fp64", hm.HM_F64, 8), ("1rhs_fp32", hm.HM_F32, 4)):
         hm.hm_matvec(A, Xr[0], Yr[0], prec=prec)
         a.record(stream)
@@ -437,6 +461,7 @@ def run_large(args, world, hm, torch, W=LARGE, case="large"):
         "solve_mixed_16rhs_s": _mean(results, "solve_mixed_s"),
         "mixed_iters": last["iters"], "mixed_refine_steps": last["refine_steps"],
         "mixed_rel_resid": last["rel_resid"], "mixed_inner_dtype": last["inner_dtype"],
+        "mixed_rel_resid_fp64": resid64,
         "fp64_16rhs": {"solve_s": fp64_s, "repetitions": 1, "iters": i64.iters, "rel_resid": i64.rel_resid,
                        "note": "the all-FP64 GPU form of the same 16 systems (lockstep GMRES, FP64 products), "
                                "timed once on the last step's matrix"},
@@ -777,7 +802,8 @@ def run_workload(name):
           "blockmv": run_blockmv, "blockmv7": lambda t, h: run_blockmv(t, h, "precision"),
           "blockmv_tc": lambda t, h: run_blockmv(t, h, tcgen05=1),
           "blockmv8": lambda t, h: run_blockmv(t, h, "large"),
-          "blockmv8_tc": lambda t, h: run_blockmv(t, h, "large", tcgen05=1)}[name]
+          "blockmv8_tc": lambda t, h: run_blockmv(t, h, "large", tcgen05=1),
+          "dfmv8": lambda t, h: run_dfmv(t, h, "large"), "dfmv6": lambda t, h: run_dfmv(t, h, "bumped6")}[name]
     ck = Clocks(torch.cuda.current_device())
     ck.start()
     out = fn(torch, hm)
@@ -943,6 +969,44 @@ def run_blockmv(torch, hm, case="bumped6", tcgen05=0):
     return out
 
 
+def run_dfmv(torch, hm, case):
+    """The FP64 master applied to 16 right-hand sides: the double-float
+    16-column product (hm_matvec_block, HM_F64) against 16 FP64 products
+    (hm_matvec, one right-hand side each), and their difference."""
+    import meshgen
+    cfg = meshgen.config(case)
+    n = cfg["T"].shape[0]
+    leaf, eps = (128, 1e-6) if case == "large" else (64, 1e-7)
+    V, T = torch.from_numpy(cfg["V"]).cuda(), torch.from_numpy(cfg["T"]).cuda()
+    tree = hm.hm_build_tree(V, T, eta=1.5, leaf_size=leaf)
+    A = hm.hm_assemble(tree, aca_eps=eps, aca_kmax=64, ss_order=8, factor_dtype=hm.HM_F64, dense_dtype=hm.HM_F64)
+    gen = torch.Generator(device="cuda").manual_seed(11)
+    X = torch.randn((16, n), dtype=torch.float64, device="cuda", generator=gen)
+    Y, Y64 = torch.empty_like(X), torch.empty_like(X)
+    hm.hm_matvec_block(A, X, Y, prec=hm.HM_F64)
+    hm.hm_matvec(A, X, Y64, prec=hm.HM_F64)
+    torch.cuda.synchronize()
+    out = {"workload": "%s (%d panels), leaf %d, 16 right-hand sides on the FP64 master" % (case, n, leaf), "n": n}
+    for name, fn in (("df16", lambda: hm.hm_matvec_block(A, X, Y, prec=hm.HM_F64)),
+                     ("fp64_x16", lambda: hm.hm_matvec(A, X, Y64, prec=hm.HM_F64))):
+        hm.hm_trace_enable(True)
+        a, b = _ev(torch), _ev(torch)
+        a.record()
+        for _ in range(3):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        hm.hm_trace_enable(False)
+        tr = hm.hm_trace_read()
+        out[name] = {"ms": a.elapsed_time(b) / 3,
+                     "kernels_ms": {k: v[1] / 3 for k, v in sorted(tr.items(), key=lambda kv: -kv[1][1])[:6]}}
+    d = torch.linalg.norm(Y - Y64, dim=1) / torch.linalg.norm(Y64, dim=1)
+    out["rel_diff_max"] = float(d.max())
+    hm.hm_free(A)
+    hm.hm_free(tree)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -957,7 +1021,8 @@ def main():
     ap.add_argument("--profile-step", action="store_true",
                     help="run exactly one step (no warm-up, no extras) and print its phase times")
     ap.add_argument("--workload", default=None,
-                    choices=["batching", "differentiation", "blockmv", "blockmv7", "blockmv_tc", "blockmv8", "blockmv8_tc"],
+                    choices=["batching", "differentiation", "blockmv", "blockmv7", "blockmv_tc", "blockmv8", "blockmv8_tc",
+                             "dfmv6", "dfmv8"],
                     help="measure one of the other workloads once and print its numbers (not a bench line)")
     args = ap.parse_args()
     if args.workload:

@@ -163,6 +163,14 @@ typedef struct {
                            kept with the matrix when the assembly did not keep
                            them); HM_F32 -> HM_F64.  <= 0 selects 0.5; NaN is
                            HM_EINVAL. */
+    int32_t resid_df;   /* refine = 1 and batched = 1: 1 = the outer residuals
+                           b - H x of all systems by the 16-right-hand-side
+                           product of the FP64 master in double-float
+                           arithmetic (hm_matvec_block with HM_F64: each stored
+                           entry read once per 16 systems, the arithmetic on
+                           the FP32 pipe; ~1e-14 of |H||x| instead of ~1e-16),
+                           and the stopping test on them; 0 = one FP64 product
+                           per system.  Other values: HM_EINVAL. */
 } hm_solve_params;
 
 typedef struct {
@@ -316,19 +324,25 @@ HM_API hm_status hm_potential(const hm_tree *tree, const double *d_points, int64
 HM_API hm_status hm_matvec(const hm_matrix *A, int32_t trans, int32_t nrhs, hm_dtype prec, const double *d_x, double *d_y,
                     double alpha, double beta, hm_stream_t stream);
 
-/* The product with many right-hand sides on the tensor cores (the
- * multi-RHS form of the H-matvec of Sec. 2.3): y = alpha H x + beta y for
- * nrhs right-hand sides [nrhs][n] (original order), 16 at a time, each
- * stored entry read once per 16.  Runs on the low-precision copies:
- * prec = HM_F32 (FP32 near field and factors) or HM_BF16 (FP32 near field,
- * BF16 factors).  The tensor-core operands are BF16 (mma m16n8k16, FP32
- * accumulation): FP32 values, including x, are split into a BF16 pair
- * (hi + lo) and multiplied as hi*hi + hi*lo + lo*hi, so the result carries
- * about 16 significant bits (relative error ~1e-5 on top of the copy's own
- * rounding) — accurate enough for the inner solves of the refinement.
- * Stream-ordered (working vectors from the stream-ordered pool).
- * Errors: HM_EINVAL for NULL pointers, nrhs < 1, or a precision whose copy
- * was not assembled (HM_F64 included: the FP64 master is not used here). */
+/* The product with many right-hand sides (the multi-RHS form of the
+ * H-matvec of Sec. 2.3): y = alpha H x + beta y for nrhs right-hand sides
+ * [nrhs][n] (original order), 16 at a time, each stored entry read once per
+ * 16.
+ *  prec = HM_F32 (FP32 near field and factors) or HM_BF16 (FP32 near field,
+ *  BF16 factors): on the tensor cores.  The operands are BF16 (mma m16n8k16,
+ *  FP32 accumulation): FP32 values, including x, are split into a BF16 pair
+ *  (hi + lo) and multiplied as hi*hi + hi*lo + lo*hi, so the result carries
+ *  about 16 significant bits (relative error ~1e-5 on top of the copy's own
+ *  rounding) — accurate enough for the inner solves of the refinement.
+ *  prec = HM_F64: the FP64 master in double-float arithmetic on the FP32
+ *  pipe (every entry and x split into a pair of floats, error-free products
+ *  and sums: the compensated dot product of Ogita, Rump and Oishi), about
+ *  2^-47 relative error per term, ~1e-14 of the row sums of |H||x| — the
+ *  FP64 residuals of the batched refinement (hm_solve_params.resid_df).
+ * Stream-ordered (working vectors from the stream-ordered pool; HM_F64 uses
+ * 128 bytes per panel, per partial projection and per unit of total rank).
+ * Errors: HM_EINVAL for NULL pointers, nrhs < 1, an unknown precision, or a
+ * low precision whose copy was not assembled. */
 HM_API hm_status hm_matvec_block(const hm_matrix *A, int32_t nrhs, hm_dtype prec, const double *d_x, double *d_y,
                                  double alpha, double beta, hm_stream_t stream);
 

@@ -48,7 +48,7 @@ class SolveParams(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("rel_tol", ctypes.c_double),
                 ("refine", ctypes.c_int32), ("max_refine", ctypes.c_int32), ("inner_tol", ctypes.c_double),
                 ("inner_dtype", ctypes.c_int), ("precond", ctypes.c_int32), ("batched", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32), ("stall_ratio", ctypes.c_double)]
+                ("use_graph", ctypes.c_int32), ("stall_ratio", ctypes.c_double), ("resid_df", ctypes.c_int32)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -270,8 +270,10 @@ def hm_matvec(A, x, y, trans=0, prec=HM_F64, alpha=1.0, beta=0.0, stream=None):
 
 
 def hm_matvec_block(A, x, y, prec=HM_BF16, alpha=1.0, beta=0.0, stream=None):
-    """Tensor-core product for [nrhs, n] right-hand sides (16 at a time) on
-    the FP32 / BF16 copies; ~1e-5 relative accuracy (BF16 operand pairs)."""
+    """Product for [nrhs, n] right-hand sides, 16 at a time: on the tensor
+    cores with the FP32 / BF16 copies (~1e-5 relative accuracy, BF16 operand
+    pairs), or (prec = HM_F64) the FP64 master in double-float arithmetic
+    (~1e-14 of |H||x|)."""
     import torch
     nrhs = 1 if x.dim() == 1 else x.shape[0]
     _check(lib().hm_matvec_block(A, nrhs, int(prec), _ptr(x, torch.float64), _ptr(y, torch.float64), float(alpha),
@@ -291,13 +293,14 @@ def hm_matvec_noalloc(A, x, y, trans=0, prec=HM_F64, alpha=1.0, beta=0.0, stream
 
 
 def hm_solve(A, b, x, trans=0, restart=30, max_iter=3000, rel_tol=1e-10, refine=0, max_refine=20, inner_tol=1e-4,
-             inner_dtype=HM_F32, precond=0, batched=0, use_graph=0, stall_ratio=0.5, stream=None,
+             inner_dtype=HM_F32, precond=0, batched=0, use_graph=0, stall_ratio=0.5, resid_df=0, stream=None,
              raise_on_noconv=True):
     """Solves op(H) x = b; returns the SolveInfo of the (last) right-hand side."""
     import torch
     nrhs = 1 if b.dim() == 1 else b.shape[0]
     prm = SolveParams(int(restart), int(max_iter), float(rel_tol), int(refine), int(max_refine), float(inner_tol),
-                      int(inner_dtype), int(precond), int(batched), int(use_graph), float(stall_ratio))
+                      int(inner_dtype), int(precond), int(batched), int(use_graph), float(stall_ratio),
+                      int(resid_df))
     info = SolveInfo()
     st = lib().hm_solve(A, int(trans), nrhs, _ptr(b, torch.float64), _ptr(x, torch.float64), ctypes.byref(prm),
                         _stream(stream), ctypes.byref(info))
@@ -309,12 +312,13 @@ def hm_solve(A, b, x, trans=0, restart=30, max_iter=3000, rel_tol=1e-10, refine=
 
 def hm_solve_scaled(A, b, c, x, trans=0, restart=30, max_iter=3000, rel_tol=1e-10, refine=0, max_refine=20,
                     inner_tol=1e-4, inner_dtype=HM_F32, precond=0, batched=0, use_graph=0, stall_ratio=0.5,
-                    stream=None, raise_on_noconv=True):
+                    resid_df=0, stream=None, raise_on_noconv=True):
     """Solves op(H diag(c)) x = b (c: CUDA float64 [n]); returns the SolveInfo."""
     import torch
     nrhs = 1 if b.dim() == 1 else b.shape[0]
     prm = SolveParams(int(restart), int(max_iter), float(rel_tol), int(refine), int(max_refine), float(inner_tol),
-                      int(inner_dtype), int(precond), int(batched), int(use_graph), float(stall_ratio))
+                      int(inner_dtype), int(precond), int(batched), int(use_graph), float(stall_ratio),
+                      int(resid_df))
     info = SolveInfo()
     st = lib().hm_solve_scaled(A, int(trans), nrhs, _ptr(c, torch.float64), _ptr(b, torch.float64),
                                _ptr(x, torch.float64), ctypes.byref(prm), _stream(stream), ctypes.byref(info))

@@ -46,6 +46,7 @@ void matvec_noalloc(const hm_matrix *A, int32_t nrhs, hm_dtype prec, const doubl
                     double beta, cudaStream_t s);
 double measure_fma_peak(hm_dtype kind, cudaStream_t s);
 int mrhs_error(const hm_matrix *A, cudaStream_t s);
+void matvec_df(const hm_matrix *A, int nrhs, const double *x, double *y, double alpha, double beta, cudaStream_t s);
 void div_diag(const double *a, const double *d, int64_t n, int nrhs, double *out, cudaStream_t s);
 void mul_diag(const double *a, const double *d, int64_t n, int nrhs, double *out, cudaStream_t s);
 void axpby_diag(const double *v, const double *d, int64_t n, int nrhs, double alpha, double beta, double *y,
@@ -251,7 +252,11 @@ hm_status hm_matvec_block(const hm_matrix *A, int32_t nrhs, hm_dtype prec, const
         if (!is_matrix(A)) fail(HM_EINVAL, "not a matrix handle");
         if (!d_x || !d_y) fail(HM_EINVAL, "NULL argument");
         if (nrhs < 1) fail(HM_EINVAL, "nrhs must be >= 1");
-        if (prec != HM_F32 && prec != HM_BF16) fail(HM_EINVAL, "the block product runs on the FP32 / BF16 copies");
+        if (prec != HM_F64 && prec != HM_F32 && prec != HM_BF16) fail(HM_EINVAL, "unknown precision %d", (int)prec);
+        if (prec == HM_F64) {  // the FP64 master in double-float arithmetic (mrhs_df.cu)
+            matvec_df(A, nrhs, d_x, d_y, alpha, beta, (cudaStream_t)stream);
+            return;
+        }
         if (!A->dense32.p || (prec == HM_F32 ? !A->up32.p : !A->upbf.p))
             fail(HM_EINVAL, "the low-precision copies for this precision were not assembled");
         matvec_mrhs(A, prec, nrhs, d_x, d_y, alpha, beta, (cudaStream_t)stream);
@@ -297,6 +302,7 @@ hm_status hm_solve(const hm_matrix *A, int32_t trans, int32_t nrhs, const double
         if (params->batched != 0 && params->batched != 1) fail(HM_EINVAL, "batched must be 0 or 1");
         if (params->use_graph != 0 && params->use_graph != 1) fail(HM_EINVAL, "use_graph must be 0 or 1");
         if (std::isnan(params->stall_ratio)) fail(HM_EINVAL, "stall_ratio is NaN");
+        if (params->resid_df != 0 && params->resid_df != 1) fail(HM_EINVAL, "resid_df must be 0 or 1");
         if (params->batched && trans) fail(HM_EINVAL, "the batched solve is for trans = 0");
         if (params->batched && params->refine && params->inner_dtype != HM_F64 && !A->dense32.p)
             fail(HM_EINVAL, "the FP32 near-field copy was not assembled");

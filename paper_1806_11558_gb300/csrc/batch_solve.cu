@@ -36,6 +36,8 @@ void permute_to_morton(const hm_tree *tr, const double *x, double *xm, cudaStrea
 void permute_from_morton(const hm_tree *tr, const double *ym, double alpha, double beta, double *y, cudaStream_t s);
 hm_dtype raise_inner(const hm_matrix *A, hm_dtype cur, cudaStream_t s);
 int mrhs_error(const hm_matrix *A, cudaStream_t s);
+int64_t df_work_floats(const hm_matrix *A);
+void matvec_df_morton(const hm_matrix *A, const double *xv, int nr, double *yv, float *work, cudaStream_t s);
 
 constexpr int BMR = 16;        // columns of one tensor-core product
 constexpr int BITEM = 8192;    // entries of one work item
@@ -356,6 +358,19 @@ struct Batch {
     }
     unsigned nitems() const { return (unsigned)items_h.size(); }
 
+    // outer residual products by the double-float 16-column product (resid_df)
+    DBuf dfw;
+    void enable_df() { dfw.alloc(sizeof(float) * df_work_floats(A)); }
+    // y = H_64 x for all R columns ([R][n], Morton): the outer products of the refinement
+    void apply_outer(const double *x, double *yv, cudaStream_t s) {
+        if (!dfw.p) {
+            apply(HM_F64, x, yv, s);
+            return;
+        }
+        for (int r0 = 0; r0 < R; r0 += BMR)
+            matvec_df_morton(A, x + (int64_t)r0 * n, std::min(BMR, R - r0), yv + (int64_t)r0 * n, dfw.as<float>(), s);
+    }
+
     // out[s][l] = V_l . w per system, l < nv
     void dots(const double *Vb, int nv, const double *w, const int *mask, double *out, int ld, int accumulate,
               cudaStream_t s, const LoopCtl *c = nullptr) {
@@ -611,6 +626,7 @@ hm_status solve_batched(const hm_matrix *A, int nrhs, const double *b_orig, doub
         }
         if (worst > p.rel_tol) st = HM_ENOCONV;
     } else {
+        if (p.resid_df) B.enable_df();
         DBuf r, d;
         r.alloc(sizeof(double) * vs);
         d.alloc(sizeof(double) * vs);
@@ -642,7 +658,7 @@ hm_status solve_batched(const hm_matrix *A, int nrhs, const double *b_orig, doub
                                  p.max_iter - iters, cycles, s, p.use_graph != 0);
             badd_vec_kernel<<<gx(vs), 256, 0, s>>>(d.as<double>(), vs, x.as<double>());
             HM_LAUNCH_CHECK();
-            B.apply(HM_F64, x.as<double>(), B.AX.as<double>(), s);
+            B.apply_outer(x.as<double>(), B.AX.as<double>(), s);
             bsub_vec_kernel<<<gx(vs), 256, 0, s>>>(b.as<double>(), B.AX.as<double>(), vs, r.as<double>());
             HM_LAUNCH_CHECK();
         }

@@ -86,7 +86,7 @@ def _oracle_solutions(orc, g, B, tol):
     return np.array([orc.gmres(mv, B[r], restart=60, tol=tol, maxiter=20000)[0] for r in range(B.shape[0])])
 
 
-@pytest.mark.parametrize("form", ["fp64", "refined_bf16", "refined_f32"])
+@pytest.mark.parametrize("form", ["fp64", "refined_bf16", "refined_f32", "refined_f32_df"])
 def test_batched_solutions_match_the_oracle_gmres(orc, sphere, form):
     g = sphere
     B = _rhs(g, 17)  # one full pass of 16 right-hand sides and a ragged one
@@ -94,10 +94,23 @@ def test_batched_solutions_match_the_oracle_gmres(orc, sphere, form):
     if form != "fp64":
         kw.update(refine=1, inner_dtype=2 if form == "refined_bf16" else 1,
                   inner_tol=1e-2 if form == "refined_bf16" else 1e-4, max_refine=60)
-        if form == "refined_f32":
+        if form.startswith("refined_f32"):
             g.hm.hm_matrix_add_copy(g.A, 1)
+        if form == "refined_f32_df":
+            kw.update(resid_df=1)  # outer residuals by the double-float 16-column product
     X, info = _solve(g, B, **kw)
     assert info.status == 0 and info.rel_resid <= 1e-12
     Xo = _oracle_solutions(orc, g, B, 1e-12)
     err = np.linalg.norm(X - Xo, axis=1) / np.linalg.norm(Xo, axis=1)
     assert err.max() <= 1e-8, err
+    if form == "refined_f32_df":
+        # the FP64 residual of the solutions, by the oracle: the double-float
+        # residual the solver stopped on is within ~1e-14 of |H||x| of it
+        perm = g.perm()
+        ex = g.export()
+        dl, al = g.leaves(True), g.leaves(False)
+        for r in range(B.shape[0]):
+            hx = np.empty(g.n)
+            hx[perm] = orc.hmatvec_raw(g.n, dl, ex["dense_off"], ex["dense"], al, ex["rank"], ex["u_off"],
+                                       ex["w_off"], ex["uw"], X[r][perm])
+            assert np.linalg.norm(B[r] - hx) <= 1.05e-12 * np.linalg.norm(B[r]), r

@@ -109,13 +109,19 @@ def test_bf16_rounding_helper():
                                                   dtype=np.float32))
 
 
-def test_block_product_rejects_fp64():
+def test_block_product_rejects_unknown_precision_and_missing_copies():
     torch = need_gpu()
     V, T = meshgen.icosphere(2)
-    g = GpuH(V, T, eps=1e-6, factor_dtype=1, dense_dtype=1)
+    g = GpuH(V, T, eps=1e-6, factor_dtype=0, dense_dtype=0)
     try:
         x = torch.zeros((2, g.n), dtype=torch.float64, device="cuda")
-        with pytest.raises(g.hm.HMError):
-            g.hm.hm_matvec_block(g.A, x, x.clone(), prec=0)
+        for prec in (3, -1):
+            with pytest.raises(g.hm.HMError) as e:
+                g.hm.hm_matvec_block(g.A, x, x.clone(), prec=prec)
+            assert e.value.status == g.hm.HM_EINVAL
+        for prec in (1, 2):  # no FP32 / BF16 copies assembled
+            with pytest.raises(g.hm.HMError) as e:
+                g.hm.hm_matvec_block(g.A, x, x.clone(), prec=prec)
+            assert e.value.status == g.hm.HM_EINVAL
     finally:
         g.close()
