@@ -32,6 +32,7 @@ int64_t mrhs_work_floats(const hm_matrix *A);
 void mrhs_prepare(const hm_matrix *A, hm_dtype prec, cudaStream_t s);
 void bj_setup(const hm_matrix *A, cudaStream_t s);
 void bj_apply_cols(const hm_matrix *A, const double *v, double *z, int cols, bool trans, bool low, cudaStream_t s);
+void bj_apply_cols_f32(const hm_matrix *A, const float *v, float *z, int cols, cudaStream_t s);
 void permute_to_morton(const hm_tree *tr, const double *x, double *xm, cudaStream_t s);
 void permute_from_morton(const hm_tree *tr, const double *ym, double alpha, double beta, double *y, cudaStream_t s);
 hm_dtype raise_inner(const hm_matrix *A, hm_dtype cur, cudaStream_t s);
@@ -55,11 +56,14 @@ static unsigned gx(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<i
 // every vector: per vector its lanes stride the chunk with four independent
 // accumulators (the chunk of w stays in L1 after the first vector) and add
 // them by shuffles; the eight warps' sums of each vector are added in a
-// fixed order at the end, so the CTA synchronises once.
+// fixed order at the end, so the CTA synchronises once.  TV: the type of the
+// Krylov vectors and of the arithmetic up to the warp sums (FP64; FP32 for
+// the FP32 Krylov vectors of the inner solves), FP64 from there on.
 constexpr int BMAXV = 129;  // restart + 1
-__global__ void __launch_bounds__(BTHREADS) bdots_kernel(const Item *__restrict__ items, const double *__restrict__ V,
+template <class TV>
+__global__ void __launch_bounds__(BTHREADS) bdots_kernel(const Item *__restrict__ items, const TV *__restrict__ V,
                                                          int64_t vstride, int64_t n, int nv,
-                                                         const double *__restrict__ w, const int *__restrict__ act,
+                                                         const TV *__restrict__ w, const int *__restrict__ act,
                                                          double *__restrict__ part, const LoopCtl *ctl) {
     if (ctl) nv = ctl->j + 1;
     constexpr int BW = BTHREADS / 32;
@@ -70,11 +74,11 @@ __global__ void __launch_bounds__(BTHREADS) bdots_kernel(const Item *__restrict_
     const int64_t len = it.i1 - it.i0;
     const int64_t chunk = ((len + BW - 1) / BW + 31) / 32 * 32;
     const int64_t c0 = it.i0 + warp * chunk, c1 = min(it.i1, c0 + chunk);
-    const double *wc = w + (int64_t)it.col * n;
+    const TV *wc = w + (int64_t)it.col * n;
     for (int l = 0; l < nv; ++l) {
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+        TV a0 = 0, a1 = 0, a2 = 0, a3 = 0;
         if (on) {
-            const double *vl = V + (int64_t)l * vstride + (int64_t)it.col * n;
+            const TV *vl = V + (int64_t)l * vstride + (int64_t)it.col * n;
             int64_t i = c0 + lane;
             for (; i + 96 < c1; i += 128) {
                 a0 = fma(vl[i], wc[i], a0);
@@ -84,10 +88,10 @@ __global__ void __launch_bounds__(BTHREADS) bdots_kernel(const Item *__restrict_
             }
             for (; i < c1; i += 32) a0 = fma(vl[i], wc[i], a0);
         }
-        double t = (a0 + a1) + (a2 + a3);
+        TV t = (a0 + a1) + (a2 + a3);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-        if (lane == 0) s_part[warp][l] = t;
+        if (lane == 0) s_part[warp][l] = (double)t;
     }
     __syncthreads();
     for (int l = threadIdx.x; l < nv; l += BTHREADS) {
@@ -109,41 +113,54 @@ __global__ void bdots_final_kernel(const int64_t *__restrict__ iptr, int S, int 
     }
 }
 
-// w(col, i) -= sum_l V_l(col, i) h[s][l]   (active systems)
-__global__ void bsub_kernel(const Item *__restrict__ items, const double *__restrict__ V, int64_t vstride, int64_t n,
+// w(col, i) -= sum_l V_l(col, i) h[s][l]   (active systems; h rounded to TV)
+template <class TV>
+__global__ void bsub_kernel(const Item *__restrict__ items, const TV *__restrict__ V, int64_t vstride, int64_t n,
                             int nv, const double *__restrict__ h, int ldh, const int *__restrict__ act,
-                            double *__restrict__ w, const LoopCtl *ctl) {
+                            TV *__restrict__ w, const LoopCtl *ctl) {
+    __shared__ TV s_h[BMAXV];
     if (ctl) nv = ctl->j + 1;
     const Item it = items[blockIdx.x];
     if (!act[it.sys]) return;
     const double *hs = h + (int64_t)it.sys * ldh;
-    double *wc = w + (int64_t)it.col * n;
+    for (int l = threadIdx.x; l < nv; l += blockDim.x) s_h[l] = (TV)hs[l];
+    __syncthreads();
+    TV *wc = w + (int64_t)it.col * n;
     for (int64_t i = it.i0 + threadIdx.x; i < it.i1; i += blockDim.x) {
-        double a = wc[i];
-        for (int l = 0; l < nv; ++l) a -= V[(int64_t)l * vstride + (int64_t)it.col * n + i] * hs[l];
+        TV a = wc[i];
+        // eight vectors' loads in flight (the sum order is unchanged)
+#pragma unroll 8
+        for (int l = 0; l < nv; ++l) a -= V[(int64_t)l * vstride + (int64_t)it.col * n + i] * s_h[l];
         wc[i] = a;
     }
 }
 
-// x(col, i) += sum_{l < k_s} V_l(col, i) y[s][l]
-__global__ void badd_kernel(const Item *__restrict__ items, const double *__restrict__ V, int64_t vstride, int64_t n,
+// x(col, i) += sum_{l < k_s} V_l(col, i) y[s][l]   (the sum in TV, y rounded to TV)
+template <class TV>
+__global__ void badd_kernel(const Item *__restrict__ items, const TV *__restrict__ V, int64_t vstride, int64_t n,
                             const int *__restrict__ k, const double *__restrict__ y, int ldy, double *__restrict__ x) {
+    __shared__ TV s_y[BMAXV];
     const Item it = items[blockIdx.x];
     const int ks = k[it.sys];
     if (ks == 0) return;
     const double *ys = y + (int64_t)it.sys * ldy;
+    for (int l = threadIdx.x; l < ks; l += blockDim.x) s_y[l] = (TV)ys[l];
+    __syncthreads();
     double *xc = x + (int64_t)it.col * n;
     for (int64_t i = it.i0 + threadIdx.x; i < it.i1; i += blockDim.x) {
-        double a = 0.0;
-        for (int l = 0; l < ks; ++l) a += V[(int64_t)l * vstride + (int64_t)it.col * n + i] * ys[l];
-        xc[i] += a;
+        TV a = 0;
+#pragma unroll 8
+        for (int l = 0; l < ks; ++l) a += V[(int64_t)l * vstride + (int64_t)it.col * n + i] * s_y[l];
+        xc[i] += (double)a;
     }
 }
 
-// dst(col, i) = src(col, i) / sqrt(nrm2[s]) for the systems in mask (0 when the norm is 0)
-__global__ void bscale_kernel(const Item *__restrict__ items, const double *__restrict__ src, int64_t n,
+// dst(col, i) = src(col, i) / sqrt(nrm2[s]) for the systems in mask (0 when
+// the norm is 0); FP32 vectors are multiplied by the rounded reciprocal
+template <class TV>
+__global__ void bscale_kernel(const Item *__restrict__ items, const TV *__restrict__ src, int64_t n,
                               const double *__restrict__ nrm2, int nstride, const int *__restrict__ mask,
-                              double *__restrict__ dst, const LoopCtl *ctl, int64_t vs, int m) {
+                              TV *__restrict__ dst, const LoopCtl *ctl, int64_t vs, int m) {
     if (ctl) {
         // graph form: dst = V_j with j = ctl->j (already advanced), 1 <= j <= m
         const int j = ctl->j;
@@ -153,15 +170,28 @@ __global__ void bscale_kernel(const Item *__restrict__ items, const double *__re
     const Item it = items[blockIdx.x];
     if (!mask[it.sys]) return;
     const double nr = sqrt(nrm2[(int64_t)it.sys * nstride]);
-    const double *sc = src + (int64_t)it.col * n;
-    double *dc = dst + (int64_t)it.col * n;
-    for (int64_t i = it.i0 + threadIdx.x; i < it.i1; i += blockDim.x) dc[i] = nr > 0.0 ? sc[i] / nr : 0.0;
+    const TV *sc = src + (int64_t)it.col * n;
+    TV *dc = dst + (int64_t)it.col * n;
+    if (sizeof(TV) == 8) {
+        for (int64_t i = it.i0 + threadIdx.x; i < it.i1; i += blockDim.x) dc[i] = nr > 0.0 ? (TV)(sc[i] / nr) : (TV)0;
+    } else {
+        const TV rinv = nr > 0.0 ? (TV)(1.0 / nr) : (TV)0;
+        for (int64_t i = it.i0 + threadIdx.x; i < it.i1; i += blockDim.x) dc[i] = sc[i] * rinv;
+    }
 }
 
+// out = a - b (rounded to TO)
+template <class TO>
 __global__ void bsub_vec_kernel(const double *__restrict__ a, const double *__restrict__ b, int64_t n,
-                                double *__restrict__ out) {
+                                TO *__restrict__ out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] = a[i] - b[i];
+        out[i] = (TO)(a[i] - b[i]);
+}
+
+// out = a rounded to FP32
+__global__ void round_vec_kernel(const double *__restrict__ a, int64_t n, float *__restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (float)a[i];
 }
 
 __global__ void badd_vec_kernel(const double *__restrict__ a, int64_t n, double *__restrict__ out) {
@@ -235,11 +265,12 @@ __global__ void bstep_end_kernel(int S, int m, const int *__restrict__ act, Loop
 }
 
 // out = V_j (all columns) with j = ctl->j
-__global__ void bvj_copy_kernel(const double *__restrict__ V, int64_t vs, int m, const LoopCtl *ctl,
-                                double *__restrict__ out) {
+template <class TV>
+__global__ void bvj_copy_kernel(const TV *__restrict__ V, int64_t vs, int m, const LoopCtl *ctl,
+                                TV *__restrict__ out) {
     const int j = ctl->j;
     if (j < 0 || j >= m) return;
-    const double *src = V + (int64_t)j * vs;
+    const TV *src = V + (int64_t)j * vs;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < vs; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = src[i];
 }
@@ -270,8 +301,9 @@ __global__ void bset_g0_kernel(int S, int m, const int *__restrict__ mask, const
     gs[0] = sqrt(nrm2[s]);
 }
 
-// [R][n] FP64 <-> [n][16] blocks of the tensor-core product
-__global__ void to_block_kernel(const double *__restrict__ v, int64_t n, int R, float *__restrict__ X) {
+// [R][n] FP64 / FP32 <-> [n][16] blocks of the tensor-core product
+template <class TI>
+__global__ void to_block_kernel(const TI *__restrict__ v, int64_t n, int R, float *__restrict__ X) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * BMR; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = e / BMR;
         const int r = (int)(e - i * BMR);
@@ -279,11 +311,12 @@ __global__ void to_block_kernel(const double *__restrict__ v, int64_t n, int R, 
     }
 }
 
-__global__ void from_block_kernel(const double *__restrict__ Y, int64_t n, int R, double *__restrict__ v) {
+template <class TO>
+__global__ void from_block_kernel(const double *__restrict__ Y, int64_t n, int R, TO *__restrict__ v) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * R; e += (int64_t)gridDim.x * blockDim.x) {
         const int r = (int)(e / n);
         const int64_t i = e - (int64_t)r * n;
-        v[e] = Y[i * BMR + r];
+        v[e] = (TO)Y[i * BMR + r];
     }
 }
 
@@ -298,6 +331,10 @@ struct Batch {
     std::vector<Item> items_h;
     std::vector<int64_t> iptr_h;
     DBuf items, iptr, V, W, Z, AX, part, h, h2, H, cs, sn, g, y, est, hn, nrm, act, cyc, kk, ones, mv, mvf, ctl, thr, xin;
+    // FP32 Krylov vectors of the inner solves on the low-precision copies
+    // (more than one right-hand side): basis, new vector, preconditioned vector
+    DBuf V32, W32, Z32, xin32;
+    bool v32 = false;
     int64_t vstride;
     std::map<int, std::unique_ptr<LoopGraph>> graphs;  // graph form of the Arnoldi loop, keyed by precision
 
@@ -323,10 +360,9 @@ struct Batch {
         HM_CUDA_CHECK(cudaMemcpyAsync(items.p, items_h.data(), sizeof(Item) * items_h.size(), cudaMemcpyHostToDevice, s));
         HM_CUDA_CHECK(cudaMemcpyAsync(iptr.p, iptr_h.data(), sizeof(int64_t) * (S + 1), cudaMemcpyHostToDevice, s));
         vstride = (int64_t)R * n;
-        V.alloc(sizeof(double) * (int64_t)(m + 1) * vstride);
-        HM_CUDA_CHECK(cudaMemsetAsync(V.p, 0, sizeof(double) * (int64_t)(m + 1) * vstride, s));
         W.alloc(sizeof(double) * vstride);
         Z.alloc(sizeof(double) * vstride);
+        v32 = R > 1 && inner != HM_F64;
         AX.alloc(sizeof(double) * vstride);
         part.alloc(sizeof(double) * std::max<size_t>(items_h.size(), 1) * (m + 1));
         h.alloc(sizeof(double) * S * (m + 1));
@@ -358,6 +394,27 @@ struct Batch {
     }
     unsigned nitems() const { return (unsigned)items_h.size(); }
 
+    // the Krylov basis in TV ([m + 1][R][n], Morton), allocated and zeroed on first use
+    template <class TV> TV *basis(cudaStream_t s) {
+        DBuf &b = sizeof(TV) == 4 ? V32 : V;
+        if (!b.p) {
+            b.alloc(sizeof(TV) * (int64_t)(m + 1) * vstride);
+            HM_CUDA_CHECK(cudaMemsetAsync(b.p, 0, sizeof(TV) * (int64_t)(m + 1) * vstride, s));
+        }
+        return b.as<TV>();
+    }
+    // the new Arnoldi vector and its preconditioned input in TV
+    template <class TV> TV *wvec() {
+        if (sizeof(TV) == 8) return W.as<TV>();
+        if (!W32.p) W32.alloc(sizeof(float) * vstride);
+        return W32.as<TV>();
+    }
+    template <class TV> TV *zvec() {
+        if (sizeof(TV) == 8) return Z.as<TV>();
+        if (!Z32.p) Z32.alloc(sizeof(float) * vstride);
+        return Z32.as<TV>();
+    }
+
     // outer residual products by the double-float 16-column product (resid_df)
     DBuf dfw;
     void enable_df() { dfw.alloc(sizeof(float) * df_work_floats(A)); }
@@ -372,31 +429,34 @@ struct Batch {
     }
 
     // out[s][l] = V_l . w per system, l < nv
-    void dots(const double *Vb, int nv, const double *w, const int *mask, double *out, int ld, int accumulate,
+    template <class TV>
+    void dots(const TV *Vb, int nv, const TV *w, const int *mask, double *out, int ld, int accumulate,
               cudaStream_t s, const LoopCtl *c = nullptr) {
         Trace trace("batch_dots", s);
-        bdots_kernel<<<nitems(), BTHREADS, 0, s>>>(items.as<Item>(), Vb, vstride, n, nv, w, mask, part.as<double>(),
-                                                   c);
+        bdots_kernel<TV><<<nitems(), BTHREADS, 0, s>>>(items.as<Item>(), Vb, vstride, n, nv, w, mask,
+                                                       part.as<double>(), c);
         HM_LAUNCH_CHECK();
         bdots_final_kernel<<<gx((int64_t)S * (c ? m : nv)), 256, 0, s>>>(iptr.as<int64_t>(), S, nv, part.as<double>(),
                                                                         out, ld, accumulate, c);
         HM_LAUNCH_CHECK();
     }
     // per-system squared norms of v into nrm (host copy returned)
-    std::vector<double> norms2(const double *v, cudaStream_t s) {
+    template <class TV> std::vector<double> norms2(const TV *v, cudaStream_t s) {
         dots(v, 1, v, ones.as<int>(), nrm.as<double>(), 1, 0, s);
         std::vector<double> out(S);
         HM_CUDA_CHECK(cudaMemcpyAsync(out.data(), nrm.p, sizeof(double) * S, cudaMemcpyDeviceToHost, s));
         HM_CUDA_CHECK(cudaStreamSynchronize(s));
         return out;
     }
-    // y = op x for all R columns ([R][n], Morton)
-    void apply(hm_dtype prec, const double *x, double *yv, cudaStream_t s) {
+    // y = op x for all R columns ([R][n], Morton); FP32 vectors (TI / TO =
+    // float) only with the low-precision copies and R > 1
+    template <class TI, class TO> void apply(hm_dtype prec, const TI *x, TO *yv, cudaStream_t s) {
         if (prec == HM_F64 || R == 1) {
+            if (sizeof(TI) != 8 || sizeof(TO) != 8) fail(HM_EINTERNAL, "FP32 Krylov vectors need the block product");
             for (int r = 0; r < R; ++r) {
                 MatvecWork w = matvec_work_at(A, mv.as<double>());
-                w.xm = const_cast<double *>(x + (int64_t)r * n);
-                w.ym = yv + (int64_t)r * n;
+                w.xm = reinterpret_cast<double *>(const_cast<TI *>(x + (int64_t)r * n));
+                w.ym = reinterpret_cast<double *>(yv + (int64_t)r * n);
                 matvec_morton(A, prec, w, s, false);
             }
             return;
@@ -406,43 +466,45 @@ struct Batch {
         float *work = X + 3 * (int64_t)BMR * n;
         for (int r0 = 0; r0 < R; r0 += BMR) {
             const int nr = std::min(BMR, R - r0);
-            to_block_kernel<<<gx(n * BMR), 256, 0, s>>>(x + (int64_t)r0 * n, n, nr, X);
+            to_block_kernel<TI><<<gx(n * BMR), 256, 0, s>>>(x + (int64_t)r0 * n, n, nr, X);
             HM_LAUNCH_CHECK();
             matvec_mrhs_morton(A, prec, X, Y, work, s);
-            from_block_kernel<<<gx(n * nr), 256, 0, s>>>(Y, n, nr, yv + (int64_t)r0 * n);
+            from_block_kernel<TO><<<gx(n * nr), 256, 0, s>>>(Y, n, nr, yv + (int64_t)r0 * n);
             HM_LAUNCH_CHECK();
         }
     }
     void bj(const double *v, double *z, bool low, cudaStream_t s) { bj_apply_cols(A, v, z, R, false, low, s); }
+    void bj(const float *v, float *z, bool, cudaStream_t s) { bj_apply_cols_f32(A, v, z, R, s); }
 };
 
 // The lockstep Arnoldi loop of a cycle as a graph: one step per iteration of
 // the WHILE node, the step index in B.ctl (the same kernels as the host loop).
-static const LoopGraph &batch_step_graph(Batch &B, hm_dtype prec) {
+template <class TV> static const LoopGraph &batch_step_graph(Batch &B, hm_dtype prec, cudaStream_t s) {
     auto it = B.graphs.find((int)prec);
     if (it != B.graphs.end()) return *it->second;
     const int S = B.S, m = B.m;
     const int64_t vs = B.vstride;
-    if (!B.xin.p) B.xin.alloc(sizeof(double) * vs);
+    DBuf &xb = sizeof(TV) == 4 ? B.xin32 : B.xin;
+    if (!xb.p) xb.alloc(sizeof(TV) * vs);
+    TV *V = B.basis<TV>(s), *w = B.wvec<TV>(), *xin = xb.as<TV>(), *z = B.zvec<TV>();
     auto L = std::make_unique<LoopGraph>();
     L->build([&](cudaStream_t cs, cudaGraphConditionalHandle loop) {
-        double *V = B.V.as<double>(), *w = B.W.as<double>();
         LoopCtl *c = B.ctl.as<LoopCtl>();
-        bvj_copy_kernel<<<gx(vs), 256, 0, cs>>>(V, vs, m, c, B.xin.as<double>());
+        bvj_copy_kernel<TV><<<gx(vs), 256, 0, cs>>>(V, vs, m, c, xin);
         HM_LAUNCH_CHECK();
         if (B.precond) {
-            B.bj(B.xin.as<double>(), B.Z.as<double>(), prec != HM_F64, cs);
-            B.apply(prec, B.Z.as<double>(), w, cs);
+            B.bj(xin, z, prec != HM_F64, cs);
+            B.apply(prec, z, w, cs);
         } else {
-            B.apply(prec, B.xin.as<double>(), w, cs);
+            B.apply(prec, xin, w, cs);
         }
         B.dots(V, 0, w, B.cyc.as<int>(), B.h.as<double>(), m + 1, 0, cs, c);
-        bsub_kernel<<<B.nitems(), 256, 0, cs>>>(B.items.as<Item>(), V, vs, B.n, 0, B.h.as<double>(), m + 1,
-                                                B.cyc.as<int>(), w, c);
+        bsub_kernel<TV><<<B.nitems(), 256, 0, cs>>>(B.items.as<Item>(), V, vs, B.n, 0, B.h.as<double>(), m + 1,
+                                                    B.cyc.as<int>(), w, c);
         HM_LAUNCH_CHECK();
         B.dots(V, 0, w, B.cyc.as<int>(), B.h2.as<double>(), m + 1, 0, cs, c);
-        bsub_kernel<<<B.nitems(), 256, 0, cs>>>(B.items.as<Item>(), V, vs, B.n, 0, B.h2.as<double>(), m + 1,
-                                                B.cyc.as<int>(), w, c);
+        bsub_kernel<TV><<<B.nitems(), 256, 0, cs>>>(B.items.as<Item>(), V, vs, B.n, 0, B.h2.as<double>(), m + 1,
+                                                    B.cyc.as<int>(), w, c);
         HM_LAUNCH_CHECK();
         badd_coef_kernel<<<gx((int64_t)S * m), 256, 0, cs>>>(S, 0, m + 1, B.h2.as<double>(), B.h.as<double>(), c);
         HM_LAUNCH_CHECK();
@@ -454,8 +516,8 @@ static const LoopGraph &batch_step_graph(Batch &B, hm_dtype prec) {
         HM_LAUNCH_CHECK();
         bstep_end_kernel<<<1, 256, 0, cs>>>(S, m, B.cyc.as<int>(), c, loop);
         HM_LAUNCH_CHECK();
-        bscale_kernel<<<B.nitems(), 256, 0, cs>>>(B.items.as<Item>(), w, B.n, B.nrm.as<double>(), 1, B.cyc.as<int>(),
-                                                  V, c, vs, m);
+        bscale_kernel<TV><<<B.nitems(), 256, 0, cs>>>(B.items.as<Item>(), w, B.n, B.nrm.as<double>(), 1,
+                                                      B.cyc.as<int>(), V, c, vs, m);
         HM_LAUNCH_CHECK();
     });
     return *(B.graphs[(int)prec] = std::move(L));
@@ -463,12 +525,16 @@ static const LoopGraph &batch_step_graph(Batch &B, hm_dtype prec) {
 
 // Lockstep GMRES(m) of all systems for op x = b ([R][n], Morton), x = 0 on
 // entry.  `on` marks the systems to solve (others keep x = 0); tol per
-// system relative to ||b_s||.  Returns the Arnoldi steps taken.
-static int gmres_batch(Batch &B, hm_dtype prec, const double *b, double *x, const std::vector<int> &on, double tol,
-                       int maxit, int &cycles, cudaStream_t s, bool use_graph) {
+// system relative to ||b_s||.  Returns the Arnoldi steps taken.  TV: the
+// type of the Krylov vectors and of their CGS2 arithmetic (FP64; FP32 for the
+// inner solves on the low-precision copies, whose tolerance is far above
+// FP32's rounding); Hessenberg, rotations, x and the true residual stay FP64.
+template <class TV>
+static int gmres_batch_t(Batch &B, hm_dtype prec, const double *b, double *x, const std::vector<int> &on, double tol,
+                         int maxit, int &cycles, cudaStream_t s, bool use_graph) {
     const int S = B.S, m = B.m;
     const int64_t vs = B.vstride;
-    double *V = B.V.as<double>();
+    TV *V = B.basis<TV>(s);
     HM_CUDA_CHECK(cudaMemsetAsync(x, 0, sizeof(double) * vs, s));
     std::vector<double> bn2 = B.norms2(b, s);
     std::vector<int> act(S);
@@ -477,7 +543,12 @@ static int gmres_batch(Batch &B, hm_dtype prec, const double *b, double *x, cons
         bnorm[k] = std::sqrt(bn2[k]);
         act[k] = on[k] && bnorm[k] > 0.0;
     }
-    HM_CUDA_CHECK(cudaMemcpyAsync(V, b, sizeof(double) * vs, cudaMemcpyDeviceToDevice, s));
+    if (sizeof(TV) == 8) {
+        HM_CUDA_CHECK(cudaMemcpyAsync(V, b, sizeof(double) * vs, cudaMemcpyDeviceToDevice, s));
+    } else {
+        round_vec_kernel<<<gx(vs), 256, 0, s>>>(b, vs, reinterpret_cast<float *>(V));
+        HM_LAUNCH_CHECK();
+    }
     int iters = 0;
     bool first = true;
     for (;;) {
@@ -499,12 +570,12 @@ static int gmres_batch(Batch &B, hm_dtype prec, const double *b, double *x, cons
         HM_CUDA_CHECK(cudaMemcpyAsync(B.nrm.p, r2.data(), sizeof(double) * S, cudaMemcpyHostToDevice, s));
         bset_g0_kernel<<<(S + 127) / 128, 128, 0, s>>>(S, m, B.cyc.as<int>(), B.nrm.as<double>(), B.g.as<double>());
         HM_LAUNCH_CHECK();
-        bscale_kernel<<<B.nitems(), 256, 0, s>>>(B.items.as<Item>(), V, B.n, B.nrm.as<double>(), 1, B.cyc.as<int>(),
-                                                 V, nullptr, 0, 0);
+        bscale_kernel<TV><<<B.nitems(), 256, 0, s>>>(B.items.as<Item>(), V, B.n, B.nrm.as<double>(), 1,
+                                                     B.cyc.as<int>(), V, nullptr, 0, 0);
         HM_LAUNCH_CHECK();
         std::vector<int> kk(S, 0);
         if (use_graph) {
-            const LoopGraph &L = batch_step_graph(B, prec);
+            const LoopGraph &L = batch_step_graph<TV>(B, prec, s);
             std::vector<double> th(S);
             for (int k = 0; k < S; ++k) th[k] = tol * bnorm[k];
             HM_CUDA_CHECK(cudaMemcpyAsync(B.thr.p, th.data(), sizeof(double) * S, cudaMemcpyHostToDevice, s));
@@ -516,11 +587,12 @@ static int gmres_batch(Batch &B, hm_dtype prec, const double *b, double *x, cons
             iters += steps;
         }
         for (int j = 0; j < (use_graph ? 0 : m); ++j) {
-            double *vj = V + (int64_t)j * vs;
-            double *w = B.W.as<double>();
+            TV *vj = V + (int64_t)j * vs;
+            TV *w = B.wvec<TV>();
             if (B.precond) {
-                B.bj(vj, B.Z.as<double>(), prec != HM_F64, s);
-                B.apply(prec, B.Z.as<double>(), w, s);
+                TV *z = B.zvec<TV>();
+                B.bj(vj, z, prec != HM_F64, s);
+                B.apply(prec, z, w, s);
             } else {
                 B.apply(prec, vj, w, s);
             }
@@ -528,15 +600,15 @@ static int gmres_batch(Batch &B, hm_dtype prec, const double *b, double *x, cons
             B.dots(V, j + 1, w, B.cyc.as<int>(), B.h.as<double>(), m + 1, 0, s);
             {
                 Trace trace("batch_update", s);
-                bsub_kernel<<<B.nitems(), 256, 0, s>>>(B.items.as<Item>(), V, vs, B.n, j + 1, B.h.as<double>(), m + 1,
-                                                       B.cyc.as<int>(), w, nullptr);
+                bsub_kernel<TV><<<B.nitems(), 256, 0, s>>>(B.items.as<Item>(), V, vs, B.n, j + 1, B.h.as<double>(),
+                                                           m + 1, B.cyc.as<int>(), w, nullptr);
                 HM_LAUNCH_CHECK();
             }
             B.dots(V, j + 1, w, B.cyc.as<int>(), B.h2.as<double>(), m + 1, 0, s);
             {
                 Trace trace("batch_update", s);
-                bsub_kernel<<<B.nitems(), 256, 0, s>>>(B.items.as<Item>(), V, vs, B.n, j + 1, B.h2.as<double>(),
-                                                       m + 1, B.cyc.as<int>(), w, nullptr);
+                bsub_kernel<TV><<<B.nitems(), 256, 0, s>>>(B.items.as<Item>(), V, vs, B.n, j + 1, B.h2.as<double>(),
+                                                           m + 1, B.cyc.as<int>(), w, nullptr);
                 HM_LAUNCH_CHECK();
             }
             badd_coef_kernel<<<gx((int64_t)S * (j + 1)), 256, 0, s>>>(S, j + 1, m + 1, B.h2.as<double>(),
@@ -562,8 +634,8 @@ static int gmres_batch(Batch &B, hm_dtype prec, const double *b, double *x, cons
             }
             if (!more) break;
             HM_CUDA_CHECK(cudaMemcpyAsync(B.cyc.p, cyc.data(), sizeof(int) * S, cudaMemcpyHostToDevice, s));
-            bscale_kernel<<<B.nitems(), 256, 0, s>>>(B.items.as<Item>(), w, B.n, B.nrm.as<double>(), 1,
-                                                     B.cyc.as<int>(), V + (int64_t)(j + 1) * vs, nullptr, 0, 0);
+            bscale_kernel<TV><<<B.nitems(), 256, 0, s>>>(B.items.as<Item>(), w, B.n, B.nrm.as<double>(), 1,
+                                                         B.cyc.as<int>(), V + (int64_t)(j + 1) * vs, nullptr, 0, 0);
             HM_LAUNCH_CHECK();
         }
         // x += M^{-1} V y per system (the graph form left k_s on the device)
@@ -573,23 +645,30 @@ static int gmres_batch(Batch &B, hm_dtype prec, const double *b, double *x, cons
         HM_LAUNCH_CHECK();
         if (B.precond) {
             HM_CUDA_CHECK(cudaMemsetAsync(B.W.p, 0, sizeof(double) * vs, s));
-            badd_kernel<<<B.nitems(), 256, 0, s>>>(B.items.as<Item>(), V, vs, B.n, B.kk.as<int>(), B.y.as<double>(), m,
-                                                   B.W.as<double>());
+            badd_kernel<TV><<<B.nitems(), 256, 0, s>>>(B.items.as<Item>(), V, vs, B.n, B.kk.as<int>(),
+                                                       B.y.as<double>(), m, B.W.as<double>());
             HM_LAUNCH_CHECK();
             B.bj(B.W.as<double>(), B.Z.as<double>(), prec != HM_F64, s);
             badd_vec_kernel<<<gx(vs), 256, 0, s>>>(B.Z.as<double>(), vs, x);
             HM_LAUNCH_CHECK();
         } else {
-            badd_kernel<<<B.nitems(), 256, 0, s>>>(B.items.as<Item>(), V, vs, B.n, B.kk.as<int>(), B.y.as<double>(), m,
-                                                   x);
+            badd_kernel<TV><<<B.nitems(), 256, 0, s>>>(B.items.as<Item>(), V, vs, B.n, B.kk.as<int>(),
+                                                       B.y.as<double>(), m, x);
             HM_LAUNCH_CHECK();
         }
         // true residual -> V_0 (systems outside `act` keep their x; their rows of V_0 are not used)
         B.apply(prec, x, B.AX.as<double>(), s);
-        bsub_vec_kernel<<<gx(vs), 256, 0, s>>>(b, B.AX.as<double>(), vs, V);
+        bsub_vec_kernel<TV><<<gx(vs), 256, 0, s>>>(b, B.AX.as<double>(), vs, V);
         HM_LAUNCH_CHECK();
     }
     return iters;
+}
+
+static int gmres_batch(Batch &B, hm_dtype prec, const double *b, double *x, const std::vector<int> &on, double tol,
+                       int maxit, int &cycles, cudaStream_t s, bool use_graph) {
+    if (prec != HM_F64 && B.v32)
+        return gmres_batch_t<float>(B, prec, b, x, on, tol, maxit, cycles, s, use_graph);
+    return gmres_batch_t<double>(B, prec, b, x, on, tol, maxit, cycles, s, use_graph);
 }
 
 hm_status solve_batched(const hm_matrix *A, int nrhs, const double *b_orig, double *x_orig, const hm_solve_params &p,
@@ -617,7 +696,7 @@ hm_status solve_batched(const hm_matrix *A, int nrhs, const double *b_orig, doub
         iters = gmres_batch(B, HM_F64, b.as<double>(), x.as<double>(), on, p.rel_tol, p.max_iter, cycles, s,
                             p.use_graph != 0);
         B.apply(HM_F64, x.as<double>(), B.AX.as<double>(), s);
-        bsub_vec_kernel<<<gx(vs), 256, 0, s>>>(b.as<double>(), B.AX.as<double>(), vs, B.W.as<double>());
+        bsub_vec_kernel<double><<<gx(vs), 256, 0, s>>>(b.as<double>(), B.AX.as<double>(), vs, B.W.as<double>());
         HM_LAUNCH_CHECK();
         std::vector<double> r2 = B.norms2(B.W.as<double>(), s);
         for (int k = 0; k < S; ++k) {
@@ -659,7 +738,7 @@ hm_status solve_batched(const hm_matrix *A, int nrhs, const double *b_orig, doub
             badd_vec_kernel<<<gx(vs), 256, 0, s>>>(d.as<double>(), vs, x.as<double>());
             HM_LAUNCH_CHECK();
             B.apply_outer(x.as<double>(), B.AX.as<double>(), s);
-            bsub_vec_kernel<<<gx(vs), 256, 0, s>>>(b.as<double>(), B.AX.as<double>(), vs, r.as<double>());
+            bsub_vec_kernel<double><<<gx(vs), 256, 0, s>>>(b.as<double>(), B.AX.as<double>(), vs, r.as<double>());
             HM_LAUNCH_CHECK();
         }
     }

@@ -434,9 +434,9 @@ __global__ void __launch_bounds__(BJ_THREADS) bj_apply_kernel(const int32_t *beg
 // Each column's sum runs over j in the same order as in bj_apply_kernel, so
 // the results are the same bit for bit.
 constexpr int BJ_NC = 16;
-template <class TD>
+template <class TD, class TVec>
 __global__ void __launch_bounds__(BJ_THREADS) bj_apply_cols_kernel(const int32_t *begin, const int64_t *bj_off,
-                                                                   const TD *bj, const double *v, double *z,
+                                                                   const TD *bj, const TVec *v, TVec *z,
                                                                    int trans, int64_t n, int cols) {
     __shared__ TD s_v[BJ_NC][BJ_MAXM];
     const int64_t r = blockIdx.x;
@@ -460,7 +460,7 @@ __global__ void __launch_bounds__(BJ_THREADS) bj_apply_cols_kernel(const int32_t
         }
 #pragma unroll
         for (int c = 0; c < BJ_NC; ++c)
-            if (c < nc) z[(int64_t)(c0 + c) * n + r0 + i] = (double)acc[c];
+            if (c < nc) z[(int64_t)(c0 + c) * n + r0 + i] = (TVec)acc[c];
     }
 }
 
@@ -546,13 +546,13 @@ void bj_apply_cols(const hm_matrix *A, const double *v, double *z, int cols, boo
     if (cols > 1) {
         const dim3 grid((unsigned)A->n_bj, (unsigned)((cols + BJ_NC - 1) / BJ_NC));
         if (low)
-            bj_apply_cols_kernel<float><<<grid, BJ_THREADS, 0, s>>>(A->bj_begin.as<int32_t>(), A->bj_off.as<int64_t>(),
-                                                                    A->bj32.as<float>(), v, z, trans ? 1 : 0,
-                                                                    A->tree->n, cols);
+            bj_apply_cols_kernel<float, double><<<grid, BJ_THREADS, 0, s>>>(
+                A->bj_begin.as<int32_t>(), A->bj_off.as<int64_t>(), A->bj32.as<float>(), v, z, trans ? 1 : 0,
+                A->tree->n, cols);
         else
-            bj_apply_cols_kernel<double><<<grid, BJ_THREADS, 0, s>>>(A->bj_begin.as<int32_t>(),
-                                                                     A->bj_off.as<int64_t>(), A->bj.as<double>(), v,
-                                                                     z, trans ? 1 : 0, A->tree->n, cols);
+            bj_apply_cols_kernel<double, double><<<grid, BJ_THREADS, 0, s>>>(
+                A->bj_begin.as<int32_t>(), A->bj_off.as<int64_t>(), A->bj.as<double>(), v, z, trans ? 1 : 0,
+                A->tree->n, cols);
         HM_LAUNCH_CHECK();
         return;
     }
@@ -563,6 +563,16 @@ void bj_apply_cols(const hm_matrix *A, const double *v, double *z, int cols, boo
     else
         bj_apply_kernel<double><<<grid, BJ_THREADS, 0, s>>>(A->bj_begin.as<int32_t>(), A->bj_off.as<int64_t>(),
                                                             A->bj.as<double>(), v, z, trans ? 1 : 0, A->tree->n);
+    HM_LAUNCH_CHECK();
+}
+
+// The FP32 preconditioner on FP32 vectors (the FP32 Krylov vectors of the
+// batched inner solves), any number of columns.
+void bj_apply_cols_f32(const hm_matrix *A, const float *v, float *z, int cols, cudaStream_t s) {
+    Trace trace("bj_apply_kernel.f32", s);
+    const dim3 grid((unsigned)A->n_bj, (unsigned)((cols + BJ_NC - 1) / BJ_NC));
+    bj_apply_cols_kernel<float, float><<<grid, BJ_THREADS, 0, s>>>(A->bj_begin.as<int32_t>(), A->bj_off.as<int64_t>(),
+                                                                   A->bj32.as<float>(), v, z, 0, A->tree->n, cols);
     HM_LAUNCH_CHECK();
 }
 
