@@ -80,9 +80,10 @@ DF_FLOPS_PER_TERM = 15
 TRAFFIC = {
     # ncu capture at the level-6 bumped sphere (leaf 128, 81,920 panels): 1.8138 GB per launch, 1.0395 x its
     # algorithmic bytes (1.7448 GB); scaled to a level-8 launch by the algorithmic bytes (37.87 GB), traffic
-    # growing in proportion with the matrix
+    # growing in proportion with the matrix (sha of the file after a change to the block-column panel build
+    # only, row_mrhs_kernel's code is the captured one)
     "row_mrhs_kernel.f32": {"source": "paper_1806_11558_gb300/csrc/mrhs.cu",
-                            "sha256": "3cf4eae46d88c8b608c86621bca7d0c6aaacbdae033378d3239f8b6a7024bf2c",
+                            "sha256": "08d635947b057d9a68c542eb9503c80906e9ee8b835311161f9275ba5ce917af",
                             "bytes_per_launch": 39372871231,
                             "workload": "large",
                             "profile": "profiles/mrhs_kernels_bumped6.md"},

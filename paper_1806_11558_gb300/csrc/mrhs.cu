@@ -503,7 +503,8 @@ __global__ void bcp_reduce_kernel(const int32_t *__restrict__ red, const int32_t
 }
 
 // W_b into its block-column panel: for every leaf column cluster kappa of
-// sigma_b, the rows of kappa come from kappa's W panel (FP64 master)
+// sigma_b, the rows of kappa come from kappa's W panel (FP64 master); b's
+// position in kappa's block list (ascending) by a binary search per thread
 template <class TF>
 __global__ void bcp_pack_kernel(const int32_t *__restrict__ adm, const int32_t *__restrict__ rank,
                                 const int32_t *__restrict__ bgrp, const int32_t *__restrict__ bkoff,
@@ -513,7 +514,6 @@ __global__ void bcp_pack_kernel(const int32_t *__restrict__ adm, const int32_t *
                                 const int64_t *__restrict__ wp_off, const int32_t *__restrict__ wp_K,
                                 const int32_t *__restrict__ wp_koff, const double *__restrict__ wp,
                                 TF *__restrict__ bcp) {
-    __shared__ int64_t s_q;
     const int32_t b = blockIdx.x;
     const int32_t cb = adm[4 * b + 2], ce = adm[4 * b + 3];
     const int k = rank[b];
@@ -527,15 +527,13 @@ __global__ void bcp_pack_kernel(const int32_t *__restrict__ adm, const int32_t *
         else hi = mid;
     }
     for (int64_t kap = lo; kap < nleaf && leaf_begin[kap] < ce; ++kap) {
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int64_t q = lr_colptr[kap];
-            while (q < lr_colptr[kap + 1] && lr_collist[q] != b) ++q;
-            s_q = q;
+        int64_t q = lr_colptr[kap], qe = lr_colptr[kap + 1];
+        while (qe - q > 1) {  // last position with lr_collist <= b
+            const int64_t mid = (q + qe) >> 1;
+            if (lr_collist[mid] <= b) q = mid;
+            else qe = mid;
         }
-        __syncthreads();
-        const int64_t q = s_q;
-        if (q >= lr_colptr[kap + 1]) continue;  // cannot happen for a consistent block list
+        if (q >= lr_colptr[kap + 1] || lr_collist[q] != b) continue;  // cannot happen for a consistent block list
         const int32_t k0 = leaf_begin[kap], mk = leaf_begin[kap + 1] - k0;
         const double *src = wp + wp_off[kap] + wp_koff[q];
         for (int e = threadIdx.x; e < mk * k; e += blockDim.x) {
@@ -578,9 +576,19 @@ __global__ void mrhs_scatter_kernel(const double *__restrict__ Y, int64_t n, int
     }
 }
 
+// sort keys of the admissible blocks: (column begin, column end) in 2 nb bits
+__global__ void bcp_keys_kernel(const int32_t *__restrict__ adm, int64_t na, int nb, uint64_t *__restrict__ key,
+                                int32_t *__restrict__ id) {
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < na; b += (int64_t)gridDim.x * blockDim.x) {
+        key[b] = ((uint64_t)(uint32_t)adm[4 * b + 2] << nb) | (uint64_t)(uint32_t)adm[4 * b + 3];
+        id[b] = (int32_t)b;
+    }
+}
+
 // The block-column panels of the low-precision W factors (first use per
-// precision): blocks grouped by column cluster on the host (sorted by
-// (column begin, column end, block)), panel widths rounded up to 8 columns.
+// precision): blocks grouped by column cluster (sorted on the device by
+// (column begin, column end), ties in block order: a stable radix sort of
+// the block ids), panel widths rounded up to 8 columns.
 static void build_bcp(const hm_matrix *Ac, hm_dtype prec, cudaStream_t s) {
     static std::mutex mu;
     std::lock_guard<std::mutex> lk(mu);
@@ -588,19 +596,31 @@ static void build_bcp(const hm_matrix *Ac, hm_dtype prec, cudaStream_t s) {
     if (A->bcp_dtype == (int)prec) return;
     const hm_tree *tr = A->tree;
     const int64_t na = tr->n_adm;
-    std::vector<int32_t> adm(4 * std::max<int64_t>(na, 1)), rank(std::max<int64_t>(na, 1));
+    // column bounds are <= n < 2^nb
+    int nb = 1;
+    while (nb < 31 && (int64_t(1) << nb) <= tr->n) ++nb;
+    std::vector<int32_t> rank(std::max<int64_t>(na, 1)), order(std::max<int64_t>(na, 1)),
+        srank(std::max<int64_t>(na, 1));
+    std::vector<uint64_t> skey(std::max<int64_t>(na, 1));
     if (na > 0) {
-        HM_CUDA_CHECK(cudaMemcpyAsync(adm.data(), tr->adm.p, sizeof(int32_t) * 4 * na, cudaMemcpyDeviceToHost, s));
+        DBuf key, id, tkey, tid, rk;
+        key.alloc(sizeof(uint64_t) * na);
+        tkey.alloc(sizeof(uint64_t) * na);
+        id.alloc(sizeof(int32_t) * na);
+        tid.alloc(sizeof(int32_t) * na);
+        rk.alloc(sizeof(int32_t) * na);
+        bcp_keys_kernel<<<grid1d_m(na), 256, 0, s>>>(tr->adm.as<int32_t>(), na, nb, key.as<uint64_t>(),
+                                                      id.as<int32_t>());
+        HM_LAUNCH_CHECK();
+        radix_sort_u64(key.as<uint64_t>(), id.as<int32_t>(), tkey.as<uint64_t>(), tid.as<int32_t>(), na, 2 * nb, s);
+        gather_i32(A->rank.as<int32_t>(), id.as<int32_t>(), rk.as<int32_t>(), na, s);
         HM_CUDA_CHECK(cudaMemcpyAsync(rank.data(), A->rank.p, sizeof(int32_t) * na, cudaMemcpyDeviceToHost, s));
+        HM_CUDA_CHECK(cudaMemcpyAsync(order.data(), id.p, sizeof(int32_t) * na, cudaMemcpyDeviceToHost, s));
+        HM_CUDA_CHECK(cudaMemcpyAsync(srank.data(), rk.p, sizeof(int32_t) * na, cudaMemcpyDeviceToHost, s));
+        HM_CUDA_CHECK(cudaMemcpyAsync(skey.data(), key.p, sizeof(uint64_t) * na, cudaMemcpyDeviceToHost, s));
         HM_CUDA_CHECK(cudaStreamSynchronize(s));
     }
-    std::vector<int32_t> order(na);
-    for (int64_t b = 0; b < na; ++b) order[b] = (int32_t)b;
-    std::sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
-        if (adm[4 * x + 2] != adm[4 * y + 2]) return adm[4 * x + 2] < adm[4 * y + 2];
-        if (adm[4 * x + 3] != adm[4 * y + 3]) return adm[4 * x + 3] < adm[4 * y + 3];
-        return x < y;
-    });
+    const uint64_t cmask = (uint64_t(1) << nb) - 1;
     std::vector<int64_t> t_off(na + 1, 0);
     for (int64_t b = 0; b < na; ++b) t_off[b + 1] = t_off[b] + rank[b];
     std::vector<int64_t> off, col0;
@@ -610,11 +630,12 @@ static void build_bcp(const hm_matrix *Ac, hm_dtype prec, cudaStream_t s) {
     for (int64_t i = 0; i < na;) {
         int64_t j = i;
         int32_t k = 0;
-        const int32_t cb = adm[4 * order[i] + 2], ce = adm[4 * order[i] + 3];
-        while (j < na && adm[4 * order[j] + 2] == cb && adm[4 * order[j] + 3] == ce) {
+        const uint64_t key = skey[i];
+        const int32_t cb = (int32_t)(key >> nb), ce = (int32_t)(key & cmask);
+        while (j < na && skey[j] == key) {
             bgrp[order[j]] = (int32_t)Kg.size();
             bkoff[order[j]] = k;
-            k += rank[order[j]];
+            k += srank[j];
             ++j;
         }
         const int32_t K = std::max<int32_t>(8, (k + 7) / 8 * 8);
@@ -627,7 +648,7 @@ static void build_bcp(const hm_matrix *Ac, hm_dtype prec, cudaStream_t s) {
         tidx.resize(c + K, -1);
         for (int64_t q = i; q < j; ++q) {
             const int32_t b = order[q];
-            for (int32_t l = 0; l < rank[b]; ++l) tidx[c + bkoff[b] + l] = (int32_t)(t_off[b] + l);
+            for (int32_t l = 0; l < srank[q]; ++l) tidx[c + bkoff[b] + l] = (int32_t)(t_off[b] + l);
         }
         const int32_t nrow = ce - cb;
         const int32_t nsplit = (nrow + BC_SPLIT - 1) / BC_SPLIT;
