@@ -33,6 +33,7 @@
 #include <cmath>
 #include <map>
 #include <mutex>
+#include <tuple>
 
 #include "entry.cuh"
 #include "ff.cuh"
@@ -681,6 +682,10 @@ __global__ void rank_stats(const int32_t *rank, int64_t na, unsigned long long *
 // ACA of every admissible leaf.  Output: A->rank, A->t_off, A->total_rank,
 // A->lr_entries, and the factors in `uw` (per block U_b column-major then W_b
 // row-major at uw_off[b]), exactly sized.
+// key of the factor-arena size hint: (admissible blocks, sum of m + n over
+// the approximated ones, eps, kmax)
+using ArenaKey = std::tuple<int64_t, int64_t, double, int>;
+
 void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStream_t s, double *sec, DBuf &uw,
                   DBuf &uw_off) {
     const int64_t na = tr->n_adm;
@@ -808,6 +813,7 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
     };
     static std::mutex tune_mu;
     static std::map<std::vector<int64_t>, Tune> tune_cache;
+    static std::map<ArenaKey, int64_t> arena_hint;  // last used size of the factor arena
     std::vector<int64_t> key(32, 0);
     for (int32_t b : upper) {
         int lg = 0;
@@ -941,9 +947,19 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
     A->info.aca_ctas_per_sm = std::min(cfg.ctas, launch_of(cfg.nt).occ);
     HM_CUDA_CHECK(cudaMemsetAsync(uw_off.p, 0, sizeof(int64_t) * na, s));
     HM_CUDA_CHECK(cudaMemsetAsync(A->rank.p, 0, sizeof(int32_t) * na, s));
-    // arena: sum (m + n) * k_guess, grown and the overflowed blocks re-run if needed
-    int64_t k_guess = std::min<int64_t>(kmax, 20);
-    int64_t cap = tr->adm_rows_cols * k_guess;
+    // arena: sum over the approximated blocks of (m + n) * k_guess, or the size
+    // the last assembly with the same blocks and tolerance used (+ 1/16), grown
+    // and the overflowed blocks re-run if needed (an arena of tens of GB beyond
+    // the block cache costs its mapping and unmapping on every assembly)
+    int64_t upper_sum = 0;
+    for (int32_t b : upper) upper_sum += msum(b);
+    int64_t cap = std::max<int64_t>(upper_sum * std::min<int64_t>(kmax, 20), 1);
+    const ArenaKey akey{na, upper_sum, A->params.aca_eps, kmax};
+    {
+        std::lock_guard<std::mutex> lk(tune_mu);
+        auto it = arena_hint.find(akey);
+        if (it != arena_hint.end()) cap = std::min<int64_t>(cap, it->second + it->second / 16 + 1024);
+    }
     DBuf arena, ctr, scr_small, d_work;
     arena.alloc(sizeof(double) * cap);
     ctr.alloc(sizeof(unsigned long long) * 5);
@@ -985,11 +1001,14 @@ void assemble_aca(const hm_tree *tr, hm_matrix *A, const QuadParams &qp, cudaStr
         top = read_scalar(a.arena_top, s);
         if ((int64_t)top > newcap) fail(HM_ENOMEM, "ACA factor arena overflow after growth");
     }
-    // shrink the arena to what is used
+    // the factors stay in the arena (read once by the panel packing, then freed)
     const int64_t used = (int64_t)top;
     A->info.aca_entries = used;
-    uw.alloc(sizeof(double) * std::max<int64_t>(used, 1));
-    HM_CUDA_CHECK(cudaMemcpyAsync(uw.p, arena.p, sizeof(double) * used, cudaMemcpyDeviceToDevice, s));
+    {
+        std::lock_guard<std::mutex> lk(tune_mu);
+        arena_hint[akey] = used;
+    }
+    uw = std::move(arena);
     mirror_rank_kernel<<<256, 256, 0, s>>>(tr->adm.as<int32_t>(), tr->adm_tp.as<int32_t>(), na, A->rank.as<int32_t>(),
                                            uw_off.as<int64_t>());
     HM_LAUNCH_CHECK();
