@@ -437,16 +437,20 @@ HM_API hm_status hm_matrix_add_copy(const hm_matrix *A, hm_dtype dtype, hm_strea
 HM_API void hm_trim(void);
 
 /* Limit, in SM clock cycles, of the library's bounded device-side waits
- * (the wait of the near-field assembly for its TMA-staged panel tiles), for
- * the calls that follow, from any thread.  cycles >= 0 sets it; cycles < 0
+ * (the wait of the near-field assembly for its TMA-staged panel tiles, and
+ * the mbarrier waits of the tcgen05 row pass of the 16-right-hand-side
+ * product, hm_assemble_params.mrhs_tcgen05), for the calls that follow,
+ * from any thread.  cycles >= 0 sets it; cycles < 0
  * restores the default of 4e9 cycles (about 2 s at 2 GHz).  A wait that
  * reaches the limit records the failure and makes the call return
  * HM_ETIMEOUT; before its thread block exits it waits again, with the
  * default limit, for the copies it started, so that no copy lands in shared
- * memory after the block has left.  0 gives up before the first poll: every
- * assembly with dense leaves then returns HM_ETIMEOUT (a hook for testing
- * that path).  After HM_ETIMEOUT the assembly's matrix is not created and
- * the device context stays usable; if the second, default-limit wait also
+ * memory after the block has left (the tcgen05 row pass likewise waits for
+ * its MMAs and copies before it frees its tensor memory).  0 gives up before
+ * the first poll: every assembly with dense leaves, and every product
+ * through the tcgen05 row pass, then returns HM_ETIMEOUT (a hook for testing
+ * those paths).  After HM_ETIMEOUT the assembly's matrix is not created (a
+ * product's output is undefined) and the device context stays usable; if the second, default-limit wait also
  * gave up (a copy that never completed) the context should be treated as
  * suspect.  The paper has no counterpart.  Always HM_OK. */
 HM_API hm_status hm_set_wait_limit(int64_t cycles);
