@@ -311,12 +311,25 @@ __global__ void to_block_kernel(const TI *__restrict__ v, int64_t n, int R, floa
     }
 }
 
+// v[r][i] = Y[i][r] for r < R: 64 rows per block, read as whole [16] rows
+// (coalesced), transposed through shared memory, written per r (coalesced)
+constexpr int FB_ROWS = 64;
 template <class TO>
-__global__ void from_block_kernel(const double *__restrict__ Y, int64_t n, int R, TO *__restrict__ v) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * R; e += (int64_t)gridDim.x * blockDim.x) {
-        const int r = (int)(e / n);
-        const int64_t i = e - (int64_t)r * n;
-        v[e] = (TO)Y[i * BMR + r];
+__global__ void __launch_bounds__(256) from_block_kernel(const double *__restrict__ Y, int64_t n, int R,
+                                                         TO *__restrict__ v) {
+    __shared__ double s_y[BMR][FB_ROWS + 1];
+    for (int64_t i0 = blockIdx.x * (int64_t)FB_ROWS; i0 < n; i0 += (int64_t)gridDim.x * FB_ROWS) {
+        const int rows = (int)((n - i0) < FB_ROWS ? (n - i0) : (int64_t)FB_ROWS);
+        __syncthreads();
+        for (int e = threadIdx.x; e < rows * BMR; e += blockDim.x) {
+            const int i = e / BMR, r = e - i * BMR;
+            s_y[r][i] = Y[(i0 + i) * BMR + r];
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < R * FB_ROWS; e += blockDim.x) {
+            const int r = e / FB_ROWS, i = e - r * FB_ROWS;
+            if (i < rows) v[(int64_t)r * n + i0 + i] = (TO)s_y[r][i];
+        }
     }
 }
 
@@ -469,7 +482,7 @@ struct Batch {
             to_block_kernel<TI><<<gx(n * BMR), 256, 0, s>>>(x + (int64_t)r0 * n, n, nr, X);
             HM_LAUNCH_CHECK();
             matvec_mrhs_morton(A, prec, X, Y, work, s);
-            from_block_kernel<TO><<<gx(n * nr), 256, 0, s>>>(Y, n, nr, yv + (int64_t)r0 * n);
+            from_block_kernel<TO><<<gx(n), 256, 0, s>>>(Y, n, nr, yv + (int64_t)r0 * n);
             HM_LAUNCH_CHECK();
         }
     }
