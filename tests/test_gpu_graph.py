@@ -74,13 +74,15 @@ def test_graph_step_limit(sphere):
     assert info.iters == 13 and info.status != 0
 
 
-@pytest.mark.parametrize("refine", [0, 1])
+@pytest.mark.parametrize("refine", [0, 1, 2], ids=["fp64", "refined", "refined_df_residuals"])
 def test_graph_batched_identical(sphere, refine):
+    # refined: FP32 Krylov vectors in the inner solves (6 right-hand sides);
+    # refined_df_residuals: and the outer residuals by the double-float product
     g = sphere
     B = g.load_vector(meshgen.point_sources(94, 6))
     kw = dict(rel_tol=1e-12, restart=40, precond=1, batched=1, max_iter=5000)
     if refine:
-        kw.update(refine=1, inner_dtype=2, inner_tol=1e-2, max_refine=60)
+        kw.update(refine=1, inner_dtype=2, inner_tol=1e-2, max_refine=60, resid_df=int(refine == 2))
     X, info = _pair(g, B, **kw)
     assert info.status == 0 and info.rel_resid <= 1e-12
     res = B[3] - g.matvec(X[3])
