@@ -95,6 +95,13 @@ __global__ void up_pack_kernel(const int32_t *leaf_begin, const int64_t *lr_rowp
         }
         for (int l = threadIdx.x; l < k; l += blockDim.x) ti[c + l] = (int32_t)(t_off[b] + l);
     }
+    // the padding columns (the panel width rounded up to 8) are zeros
+    const int64_t qa = lr_rowptr[r], qb = lr_rowptr[r + 1];
+    const int kw = qb > qa ? koff[qb - 1] + rank[lr_list[qb - 1]] : 0, pw = Ku - kw;
+    for (int e = threadIdx.x; e < mr * pw; e += blockDim.x) {
+        const int i = e / pw;
+        Q[(int64_t)i * Ku + kw + (e - i * pw)] = 0.0;
+    }
 }
 
 // column panels of W: per leaf column cluster kappa, W_b(rows of kappa, :)
@@ -126,6 +133,13 @@ __global__ void wp_pack_kernel(const int32_t *leaf_begin, const int64_t *lr_colp
                 Wt[(int64_t)j * Kw + c + l] = W[(int64_t)(off + j) * k + l];
             }
         }
+    }
+    // the padding columns (the panel width rounded up to 8) are zeros
+    const int64_t qa = lr_colptr[kap], qb = lr_colptr[kap + 1];
+    const int kw = qb > qa ? koff[qb - 1] + rank[lr_collist[qb - 1]] : 0, pw = Kw - kw;
+    for (int e = threadIdx.x; e < mc * pw; e += blockDim.x) {
+        const int j = e / pw;
+        Wt[(int64_t)j * Kw + kw + (e - j * pw)] = 0.0;
     }
 }
 
@@ -199,7 +213,6 @@ void build_lr_panels(hm_matrix *A, const DBuf &uw, const DBuf &uw_off, cudaStrea
     const int64_t ncol = exclusive_scan_i64(kpad.as<int64_t>(), A->up_colptr.as<int64_t>(), nl + 1, s);
     A->n_partials_t = ncol;  // projections through the U panels (transposed product)
     A->up.alloc(sizeof(double) * std::max<int64_t>(A->up_entries, 8));
-    HM_CUDA_CHECK(cudaMemsetAsync(A->up.p, 0, sizeof(double) * std::max<int64_t>(A->up_entries, 8), s));
     A->tidx.alloc(sizeof(int32_t) * std::max<int64_t>(ncol, 8));
     HM_CUDA_CHECK(cudaMemsetAsync(A->tidx.p, 0, sizeof(int32_t) * std::max<int64_t>(ncol, 8), s));
     if (na > 0 && nl > 0) {
@@ -226,7 +239,6 @@ void build_lr_panels(hm_matrix *A, const DBuf &uw, const DBuf &uw_off, cudaStrea
     A->wp_entries = exclusive_scan_i64(size.as<int64_t>(), A->wp_off.as<int64_t>(), nl + 1, s);
     A->n_partials = exclusive_scan_i64(kpad.as<int64_t>(), A->wp_colptr.as<int64_t>(), nl + 1, s);
     A->wp.alloc(sizeof(double) * std::max<int64_t>(A->wp_entries, 8));
-    HM_CUDA_CHECK(cudaMemsetAsync(A->wp.p, 0, sizeof(double) * std::max<int64_t>(A->wp_entries, 8), s));
     const int64_t npairs = read_scalar(tr->lr_bcolptr.as<int64_t>() + na, s);
     A->pofs.alloc(sizeof(int64_t) * std::max<int64_t>(npairs, 1));
     if (na > 0 && nl > 0) {
@@ -632,8 +644,15 @@ void get_block(const hm_matrix *A, int dense, int64_t b, double *out, cudaStream
 // ---------------------------------------------------------------------------
 // low-precision copies
 // ---------------------------------------------------------------------------
+// four values per thread and step (16-byte loads and stores; a and o are
+// 16-byte aligned), the last n mod 4 one by one
 __global__ void to_f32_kernel(const double *a, int64_t n, float *o) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    const int64_t n4 = n / 4;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 u = reinterpret_cast<const double2 *>(a)[2 * i], v = reinterpret_cast<const double2 *>(a)[2 * i + 1];
+        reinterpret_cast<float4 *>(o)[i] = make_float4((float)u.x, (float)u.y, (float)v.x, (float)v.y);
+    }
+    for (int64_t i = 4 * n4 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         o[i] = (float)a[i];
 }
 
