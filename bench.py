@@ -43,7 +43,7 @@ LARGE = dict(workload="unit icosphere level 8, Galerkin single-layer Laplace, P0
              form="mixed: FP32 near field + FP32 factors; lockstep GMRES whose inner solves use the 16-RHS "
                   "tensor-core product; iterative refinement on the FP64 master, its residuals by the 16-RHS "
                   "double-float product",
-             inner_tol=1e-4, restart=128, precond=True, batched=True, resid_df=True)
+             inner_tol=1e-4, restart=128, precond=True, batched=True, resid_df=True, factor_tail_bits=0)
 PRECISION = dict(workload="bumped icosphere level 7, Galerkin single-layer Laplace, P0",
                  case="precision", panels=327680, leaf_size=64, eta=1.5, aca_eps=1e-7, aca_kmax=64, ss_order=8,
                  nrhs=1, source=[3.0, 0.0, 0.0], solve_rel_tol=1e-12, inner="fp32 factors + fp32 near field",
@@ -80,10 +80,11 @@ DF_FLOPS_PER_TERM = 15
 TRAFFIC = {
     # ncu capture at the level-6 bumped sphere (leaf 128, 81,920 panels): 1.8138 GB per launch, 1.0395 x its
     # algorithmic bytes (1.7448 GB); scaled to a level-8 launch by the algorithmic bytes (37.87 GB), traffic
-    # growing in proportion with the matrix (sha of the file after a change to the block-column panel build
-    # only, row_mrhs_kernel's code is the captured one)
+    # growing in proportion with the matrix (sha of the file after changes to the block-column panel build
+    # and a kernel variant for BF16 tails, off by default: the default instantiation's code path is the
+    # captured one)
     "row_mrhs_kernel.f32": {"source": "paper_1806_11558_gb300/csrc/mrhs.cu",
-                            "sha256": "08d635947b057d9a68c542eb9503c80906e9ee8b835311161f9275ba5ce917af",
+                            "sha256": "b47e3da3e266f9ff1a0add9660027d4e3b6737971b3e0ce91aee69803643d22c",
                             "bytes_per_launch": 39372871231,
                             "workload": "large",
                             "profile": "profiles/mrhs_kernels_bumped6.md"},
@@ -120,6 +121,11 @@ def algorithmic_work(mi, ti, dense_leaves, n):
     # are counted too)
     nf_entries = int(((re_ - rb) * (ce - cb))[rb <= cb].sum())
     K = mi["mean_rank"] * ti["n_adm"]  # sum of ranks = length of t
+    # FP32 factors with BF16 tails: the trailing terms' entries of U (row pass)
+    # and W (column pass) are 2-byte, and the column pass runs once per part
+    u16 = mi.get("u_tail_entries", 0)
+    w16 = mi.get("lr_tail_entries", 0) - u16
+    K16 = mi.get("factor_tail_terms", 0)
     nl = (ti["n_clusters"] + 1) // 2  # leaf clusters of the binary cluster tree; partials = sum over them of K_w
     # 16 right-hand sides: X and t rows as BF16 pairs (16 x 2 x 2 B), Y rows FP64 (16 x 8 B)
     xr, yr = 4.0 * MR, 8.0 * MR
@@ -130,10 +136,10 @@ def algorithmic_work(mi, ti, dense_leaves, n):
         "col_kernel.f32": ("hbm", 4.0 * w + 4.0 * n + 4.0 * w * nl / n, "byte"),
         "row_kernel.bf16": ("hbm", 4.0 * d + 2.0 * u + 4.0 * (n + K) + 8.0 * n, "byte"),
         "col_kernel.bf16": ("hbm", 2.0 * w + 4.0 * n + 4.0 * w * nl / n, "byte"),
-        "row_mrhs_kernel.f32": ("hbm", 4.0 * (d + u) + xr * (n + K) + yr * n, "byte"),
+        "row_mrhs_kernel.f32": ("hbm", 4.0 * (d + u - u16) + 2.0 * u16 + xr * (n + K) + yr * n, "byte"),
         "row_mrhs_kernel.bf16": ("hbm", 4.0 * d + 2.0 * u + xr * (n + K) + yr * n, "byte"),
-        "col_bcp_kernel.f32": ("hbm", 4.0 * w + xr * (n + K), "byte"),
-        "col_bcp_kernel.bf16": ("hbm", 2.0 * w + xr * (n + K), "byte"),
+        "col_bcp_kernel.f32": ("hbm", 4.0 * (w - w16) + xr * (n + K - K16), "byte"),
+        "col_bcp_kernel.bf16": ("hbm", (2.0 * w16 + xr * (n + K16)) if K16 else (2.0 * w + xr * (n + K)), "byte"),
         "nearfield_kernel": ("alu32", float(nf_entries) * PAIRS_PER_ENTRY * FF_FLOPS_PER_PAIR, "flop"),
         # double-float product of the FP64 master, 16 right-hand sides per launch: DF_FLOPS_PER_TERM per
         # (entry, right-hand side)
@@ -314,7 +320,8 @@ def run_large(args, world, hm, torch, W=LARGE, case="large"):
         tree = hm.hm_build_tree(Vdev, Tdev, eta=W["eta"], leaf_size=W["leaf_size"])
         e[1].record(stream)
         A = hm.hm_assemble(tree, aca_eps=W["aca_eps"], aca_kmax=W["aca_kmax"], ss_order=W["ss_order"],
-                           factor_dtype=hm.HM_F32, dense_dtype=hm.HM_F32)
+                           factor_dtype=hm.HM_F32, dense_dtype=hm.HM_F32,
+                           factor_tail_bits=W.get("factor_tail_bits", 0))
         e[2].record(stream)
         hm.hm_load_vector(tree, sdev, F)
         e[3].record(stream)
@@ -805,6 +812,8 @@ def run_workload(name):
           "blockmv_tc": lambda t, h: run_blockmv(t, h, tcgen05=1),
           "blockmv8": lambda t, h: run_blockmv(t, h, "large"),
           "blockmv8_tc": lambda t, h: run_blockmv(t, h, "large", tcgen05=1),
+          "blockmv8_tail": lambda t, h: run_blockmv(t, h, "large", tail_bits=12),
+          "blockmv_tail": lambda t, h: run_blockmv(t, h, tail_bits=12),
           "dfmv8": lambda t, h: run_dfmv(t, h, "large"), "dfmv6": lambda t, h: run_dfmv(t, h, "bumped6")}[name]
     ck = Clocks(torch.cuda.current_device())
     ck.start()
@@ -933,26 +942,29 @@ def run_differentiation(torch, hm):
     return out
 
 
-def run_blockmv(torch, hm, case="bumped6", tcgen05=0):
+def run_blockmv(torch, hm, case="bumped6", tcgen05=0, tail_bits=0):
     """Multi-RHS product case (profiling): a bumped icosphere (level 6, or 7
     with case "precision"), leaf 128, BF16 factors, then FP32 factors added
-    from the FP64 master; three 16-right-hand-side tensor-core products each
-    (row pass on mma.sync, or on tcgen05 / TMEM with tcgen05 = 1)."""
+    from the FP64 master (with tail_bits > 0: each block's trailing ACA terms
+    in BF16); three 16-right-hand-side tensor-core products each (row pass on
+    mma.sync, or on tcgen05 / TMEM with tcgen05 = 1)."""
     import meshgen
     cfg = meshgen.config(case)
     n = cfg["T"].shape[0]
     V, T = torch.from_numpy(cfg["V"]).cuda(), torch.from_numpy(cfg["T"]).cuda()
     tree = hm.hm_build_tree(V, T, eta=1.5, leaf_size=128)
     A = hm.hm_assemble(tree, aca_eps=1e-6, aca_kmax=64, ss_order=8, factor_dtype=hm.HM_BF16, dense_dtype=hm.HM_F32,
-                       mrhs_tcgen05=tcgen05)
+                       mrhs_tcgen05=tcgen05, factor_tail_bits=tail_bits)
     X = torch.randn((16, n), dtype=torch.float64, device="cuda")
     Y = torch.empty_like(X)
     mi = hm.hm_matrix_get_info(A)
     ti = hm.hm_tree_get_info(tree)
-    out = {"workload": "%s (%d panels), leaf 128, 16-RHS product, row pass on %s" % (
-               case, n, "tcgen05" if tcgen05 else "mma.sync"), "n": n,
+    out = {"workload": "%s (%d panels), leaf 128, 16-RHS product, row pass on %s%s" % (
+               case, n, "tcgen05" if tcgen05 else "mma.sync",
+               ", FP32 factors with BF16 tails (2^-%d)" % tail_bits if tail_bits else ""), "n": n,
            "dense_entries": mi["dense_entries"], "u_entries": mi["u_entries"], "lr_entries": mi["lr_entries"],
-           "total_rank": mi["mean_rank"] * ti["n_adm"]}
+           "total_rank": mi["mean_rank"] * ti["n_adm"], "factor_tail_terms": mi["factor_tail_terms"],
+           "lr_tail_entries": mi["lr_tail_entries"], "u_tail_entries": mi["u_tail_entries"]}
     for prec, name, fb in ((hm.HM_BF16, "bf16", 2), (hm.HM_F32, "fp32", 4)):
         if prec == hm.HM_F32:
             hm.hm_matrix_add_copy(A, hm.HM_F32)
@@ -964,7 +976,8 @@ def run_blockmv(torch, hm, case="bumped6", tcgen05=0):
         b.record()
         torch.cuda.synchronize()
         ms = a.elapsed_time(b) / 3
-        gb = (mi["dense_entries"] * 4 + mi["lr_entries"] * fb) / 1e9
+        tails = mi["lr_tail_entries"] if prec == hm.HM_F32 else 0
+        gb = (mi["dense_entries"] * 4 + (mi["lr_entries"] - tails) * fb + tails * 2) / 1e9
         out[name] = {"ms": ms, "matrix_gb": gb, "gbs": gb / ms * 1e3}
     hm.hm_free(A)
     hm.hm_free(tree)
@@ -1020,10 +1033,14 @@ def main():
     ap.add_argument("--case", default="large",
                     help="workload: large (default, the headline), precision (the level-7 one-source workload); "
                          "other meshgen recipes run with the one-source step for profiling and parity runs")
+    ap.add_argument("--factor-tail-bits", type=int, default=None,
+                    help="large workload: keep each block's ACA terms below 2^-bits of its largest in BF16 for the "
+                         "16-RHS product (hm_assemble_params.factor_tail_bits; default: the workload's setting)")
     ap.add_argument("--profile-step", action="store_true",
                     help="run exactly one step (no warm-up, no extras) and print its phase times")
     ap.add_argument("--workload", default=None,
                     choices=["batching", "differentiation", "blockmv", "blockmv7", "blockmv_tc", "blockmv8", "blockmv8_tc",
+                             "blockmv8_tail", "blockmv_tail",
                              "dfmv6", "dfmv8"],
                     help="measure one of the other workloads once and print its numbers (not a bench line)")
     args = ap.parse_args()
@@ -1048,7 +1065,10 @@ def main():
     hb.build()
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
     if args.case == "large":
-        out, extra = run_large(args, world, hm, torch)
+        W = dict(LARGE)
+        if args.factor_tail_bits is not None:
+            W["factor_tail_bits"] = args.factor_tail_bits
+        out, extra = run_large(args, world, hm, torch, W=W)
     else:
         W = dict(PRECISION)
         if args.case != "precision":

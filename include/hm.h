@@ -97,6 +97,18 @@ typedef struct {
  *                 Its waits are bounded: one that gives up makes the
  *                 batched solve, or hm_matvec_block (which then
  *                 synchronises its stream), return HM_ETIMEOUT.
+ *  factor_tail_bits : 0 (default), or 8 ... 24: with factor_dtype = HM_F32
+ *                 (or a later FP32 copy), the 16-right-hand-side product
+ *                 keeps in BF16 the trailing ACA terms of every block: the
+ *                 terms after the last one whose size ||u_l|| ||w_l|| is at
+ *                 least 2^-factor_tail_bits of the block's largest term
+ *                 (Sec. 2.3: the terms of an ACA fall roughly geometrically
+ *                 to the tolerance).  Each such term's BF16 rounding is
+ *                 below 2^-(9 + factor_tail_bits) of the block's largest
+ *                 term, against ~2^-17 of every term from the product's
+ *                 BF16-pair rounding of FP32 factors; the bytes of those
+ *                 columns halve.  The single-right-hand-side FP32 product
+ *                 and every FP64 product are unchanged.
  *  The FP64 master copy is always kept. */
 typedef struct {
     double aca_eps;
@@ -106,6 +118,7 @@ typedef struct {
     hm_dtype dense_dtype;
     int32_t nearfield_fp64;
     int32_t mrhs_tcgen05;
+    int32_t factor_tail_bits;
 } hm_assemble_params;
 
 /* Solver parameters.
@@ -230,6 +243,12 @@ typedef struct {
     int32_t aca_threads;    /* ACA launch chosen by the autotuner: threads per CTA
                                (64, 128 or 256) ...                               */
     int32_t aca_ctas_per_sm; /* ... and CTAs per SM of the persistent launch     */
+    int64_t factor_tail_terms; /* ACA terms (over all admissible blocks, a
+                               mirrored block counting its partner's) that
+                               the 16-RHS product keeps in BF16
+                               (factor_tail_bits > 0; else 0)                  */
+    int64_t u_tail_entries;  /* their U entries, sum (k_b - k32_b) |tau_b|        */
+    int64_t lr_tail_entries; /* their factor entries, sum (k_b - k32_b)(|tau|+|sigma|) */
 } hm_matrix_info;
 
 /* Build the Morton-ordered cluster tree and the block cluster tree of a

@@ -41,7 +41,7 @@ class TreeParams(ctypes.Structure):
 class AssembleParams(ctypes.Structure):
     _fields_ = [("aca_eps", ctypes.c_double), ("aca_kmax", ctypes.c_int32), ("ss_order", ctypes.c_int32),
                 ("factor_dtype", ctypes.c_int), ("dense_dtype", ctypes.c_int), ("nearfield_fp64", ctypes.c_int32),
-                ("mrhs_tcgen05", ctypes.c_int32)]
+                ("mrhs_tcgen05", ctypes.c_int32), ("factor_tail_bits", ctypes.c_int32)]
 
 
 class SolveParams(ctypes.Structure):
@@ -70,7 +70,8 @@ class MatrixInfo(ctypes.Structure):
                 ("s_singular", ctypes.c_double), ("s_aca", ctypes.c_double), ("s_total", ctypes.c_double),
                 ("bytes_f64", ctypes.c_int64), ("bytes_low", ctypes.c_int64), ("aca_entries", ctypes.c_int64),
                 ("u_entries", ctypes.c_int64), ("aca_small_sum", ctypes.c_int32), ("aca_threads", ctypes.c_int32),
-                ("aca_ctas_per_sm", ctypes.c_int32)]
+                ("aca_ctas_per_sm", ctypes.c_int32), ("factor_tail_terms", ctypes.c_int64),
+                ("u_tail_entries", ctypes.c_int64), ("lr_tail_entries", ctypes.c_int64)]
 
 
 class TraceEntry(ctypes.Structure):
@@ -231,10 +232,10 @@ def hm_load_vector_geom(tree, sources, f, stream=None):
 
 
 def hm_assemble(tree, aca_eps=1e-6, aca_kmax=64, ss_order=8, factor_dtype=HM_F64, dense_dtype=HM_F64,
-                nearfield_fp64=0, mrhs_tcgen05=0, stream=None):
+                nearfield_fp64=0, mrhs_tcgen05=0, factor_tail_bits=0, stream=None):
     out = ctypes.c_void_p()
     prm = AssembleParams(float(aca_eps), int(aca_kmax), int(ss_order), int(factor_dtype), int(dense_dtype),
-                         int(nearfield_fp64), int(mrhs_tcgen05))
+                         int(nearfield_fp64), int(mrhs_tcgen05), int(factor_tail_bits))
     _check(lib().hm_assemble(tree, ctypes.byref(prm), _stream(stream), ctypes.byref(out)))
     return out
 

@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "libhm.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-Xcompiler", "-fvisibility=hidden"]
-SOURCES = ["prims.cu", "tree.cu", "nearfield.cu", "aca.cu", "matvec.cu", "mrhs.cu", "mrhs_tc.cu", "mrhs_df.cu", "solve.cu", "batch_solve.cu", "peaks.cu", "scaled.cu", "api.cu"]
+SOURCES = ["prims.cu", "tree.cu", "nearfield.cu", "aca.cu", "matvec.cu", "mrhs.cu", "mrhs_tc.cu", "mrhs_df.cu", "tails.cu", "solve.cu", "batch_solve.cu", "peaks.cu", "scaled.cu", "api.cu"]
 
 
 def _nvcc():

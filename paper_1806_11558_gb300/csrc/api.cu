@@ -26,6 +26,7 @@ void build_lr_panels(hm_matrix *A, const DBuf &uw, const DBuf &uw_off, cudaStrea
 void ensure_f32_copies(const hm_matrix *A, cudaStream_t s);
 void ensure_bf16_copies(const hm_matrix *A, cudaStream_t s);
 void make_low_copies(hm_matrix *A, cudaStream_t s);
+void split_terms(hm_matrix *A, const DBuf &uw, const DBuf &uw_off, cudaStream_t s);
 void matvec_morton(const hm_matrix *A, hm_dtype prec, const MatvecWork &w, cudaStream_t s, bool trans);
 void build_transposed(const hm_matrix *A, cudaStream_t s);
 int64_t matvec_work_doubles(const hm_matrix *A);
@@ -161,6 +162,8 @@ hm_status hm_assemble(const hm_tree *tree, const hm_assemble_params *params, hm_
         if (params->dense_dtype != HM_F64 && params->dense_dtype != HM_F32) fail(HM_EINVAL, "bad dense_dtype");
         if (params->nearfield_fp64 != 0 && params->nearfield_fp64 != 1) fail(HM_EINVAL, "nearfield_fp64 must be 0 or 1");
         if (params->mrhs_tcgen05 != 0 && params->mrhs_tcgen05 != 1) fail(HM_EINVAL, "mrhs_tcgen05 must be 0 or 1");
+        if (params->factor_tail_bits != 0 && (params->factor_tail_bits < 8 || params->factor_tail_bits > 24))
+            fail(HM_EINVAL, "factor_tail_bits must be 0 or in [8, 24]");
         cudaStream_t s = (cudaStream_t)stream;
         const auto t0 = std::chrono::steady_clock::now();
         std::unique_ptr<hm_matrix> A(new hm_matrix());
@@ -176,6 +179,7 @@ hm_status hm_assemble(const hm_tree *tree, const hm_assemble_params *params, hm_
             DBuf uw, uw_off;
             assemble_aca(tree, A.get(), qp, s, &sa, uw, uw_off);
             build_lr_panels(A.get(), uw, uw_off, s);
+            if (params->factor_tail_bits > 0) split_terms(A.get(), uw, uw_off, s);
             HM_CUDA_CHECK(cudaStreamSynchronize(s));
         }
         make_low_copies(A.get(), s);
@@ -190,7 +194,8 @@ hm_status hm_assemble(const hm_tree *tree, const hm_assemble_params *params, hm_
         I.s_singular = ss;
         I.s_aca = sa;
         I.bytes_f64 = (int64_t)(A->dense.bytes + A->up.bytes + A->wp.bytes);
-        I.bytes_low = (int64_t)(A->dense32.bytes + A->up32.bytes + A->upbf.bytes + A->wp32.bytes + A->wpbf.bytes);
+        I.bytes_low = (int64_t)(A->dense32.bytes + A->up32.bytes + A->upbf.bytes + A->wp32.bytes + A->wpbf.bytes +
+                                A->ut32.data.bytes + A->ut16.data.bytes);
         I.s_total = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         *out = A.release();
     });

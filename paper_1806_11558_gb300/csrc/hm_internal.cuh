@@ -331,6 +331,25 @@ struct MatvecWork {
     float *p32;   // [n_partials] partial projections (low-precision products)
 };
 
+namespace hm {
+// Block-column panels of one precision (the multi-RHS projection t = W^T X):
+// the W factors grouped by block column cluster (one row-major panel
+// |sigma| x K_sigma per cluster sigma, the blocks with that column cluster
+// side by side), the t index of every panel column (-1 = padding) and the
+// work items (panel, first column, rows, partial slot) and reductions.
+struct BcpSet {
+    DBuf data, off, K, rows, col0, tidx, tiles, red;
+    int64_t ngroups = 0, ntiles = 0, nred = 0, nslots = 0;
+    int dtype = -1;  // hm_dtype of data, -1 = not built
+};
+// Row panels of one part of the factors: per leaf row cluster a row-major
+// panel |rho| x K_rho, and the t index of each of its columns.
+struct TailPanels {
+    DBuf data, off, K, colptr, tidx;
+    int64_t entries = 0;
+};
+}  // namespace hm
+
 struct hm_matrix {
     uint32_t magic = HM_MATRIX_MAGIC;
     const hm_tree *tree = nullptr;
@@ -370,15 +389,18 @@ struct hm_matrix {
     hm::DBuf dense_t, dense32_t, pofs_t, tidx_t;
     int64_t n_partials_t = 0;
     bool trans_ready = false;
-    // multi-RHS projection (built on first use): the W factors of the
-    // low-precision copy grouped by block column cluster (one row-major panel
-    // |sigma| x K_sigma per cluster sigma, the blocks with that column cluster
-    // side by side), the t index of every panel column (-1 = padding) and the
-    // list of 64-column tiles (panel, first column)
-    hm::DBuf bcp, bcp_off, bcp_K, bcp_rows, bcp_col0, bcp_tidx, bcp_tiles, bcp_red;
+    // multi-RHS projection (built on first use for a precision)
+    hm::BcpSet bcp;     // the W factors of the copy (with BF16 tails: the leading terms)
+    hm::BcpSet bcp16;   // with BF16 tails: the trailing terms, BF16
     hm::DBuf mrhs_err;  // [1] int: a bounded wait of the tensor-memory row pass gave up (0 = none)
-    int64_t bcp_ngroups = 0, bcp_ntiles = 0, bcp_nred = 0, bcp_nslots = 0;
-    int bcp_dtype = -1;  // hm_dtype of bcp, -1 = not built
+    // FP32 factors with BF16 tails (params.factor_tail_bits > 0): per
+    // admissible block the number of its leading ACA terms kept in FP32 (the
+    // trailing ones, each below 2^-bits of the block's largest term, are kept
+    // in BF16 for the 16-RHS product), and the row panels of the two parts
+    // (built with the FP32 copy), in the layout of the master's row panels
+    hm::DBuf rank32;    // [n_adm] int32
+    hm::DBuf rank16;    // [n_adm] int32: k_b - k32_b
+    hm::TailPanels ut32, ut16;
     int64_t wp_entries = 0;
     int64_t n_partials = 0;  // length of the partial-projection vector
     // block-Jacobi preconditioner: inverse of each leaf cluster's diagonal block

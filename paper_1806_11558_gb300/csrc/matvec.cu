@@ -661,6 +661,8 @@ __global__ void to_bf16_kernel(const double *a, int64_t n, __nv_bfloat16 *o) {
         o[i] = __float2bfloat16_rn((float)a[i]);
 }
 
+void build_tail_panels(hm_matrix *A, cudaStream_t s);
+
 void make_low_copies(hm_matrix *A, cudaStream_t s) {
     const hm_assemble_params &p = A->params;
     const int64_t nd = A->tree->dense_entries, nu = std::max<int64_t>(A->up_entries, 8),
@@ -677,6 +679,7 @@ void make_low_copies(hm_matrix *A, cudaStream_t s) {
         HM_LAUNCH_CHECK();
         to_f32_kernel<<<grid1d(nw), 256, 0, s>>>(A->wp.as<double>(), nw, A->wp32.as<float>());
         HM_LAUNCH_CHECK();
+        if (A->rank32.p) build_tail_panels(A, s);
     } else if (p.factor_dtype == HM_BF16) {
         A->upbf.alloc(sizeof(__nv_bfloat16) * nu);
         A->wpbf.alloc(sizeof(__nv_bfloat16) * nw);
@@ -733,6 +736,7 @@ void ensure_f32_copies(const hm_matrix *Ac, cudaStream_t s) {
         HM_LAUNCH_CHECK();
         to_f32_kernel<<<grid1d(nw), 256, 0, s>>>(A->wp.as<double>(), nw, A->wp32.as<float>());
         HM_LAUNCH_CHECK();
+        if (A->rank32.p) build_tail_panels(A, s);
     }
     if (A->trans_ready && !A->dense32_t.p) {
         const int64_t ne = std::max<int64_t>(A->tree->dense_entries, 1);

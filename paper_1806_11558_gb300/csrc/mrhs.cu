@@ -30,6 +30,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "hm_internal.cuh"
@@ -239,12 +240,17 @@ __device__ __forceinline__ void rp_panel(unsigned char *sm, const TP *__restrict
     __syncthreads();
 }
 
-template <int MT, class TF, class C>
+// TAIL: the U panels come in two parts, the leading terms (up, TF = float)
+// and the trailing ones (u16, BF16), multiplied one after the other into the
+// same accumulators
+template <int MT, class TF, class C, bool TAIL>
 __global__ void __launch_bounds__(C::THREADS) row_mrhs_kernel(
     const int32_t *__restrict__ leaf_begin, const int64_t *__restrict__ rho_off, const int32_t *__restrict__ rho_K,
     const int64_t *__restrict__ rho_colptr, const int32_t *__restrict__ colidx, const float *__restrict__ dense,
     const int64_t *__restrict__ up_off, const int32_t *__restrict__ up_K, const int64_t *__restrict__ up_colptr,
-    const int32_t *__restrict__ tidx, const TF *__restrict__ up, const __nv_bfloat16 *__restrict__ Th,
+    const int32_t *__restrict__ tidx, const TF *__restrict__ up, const int64_t *__restrict__ u16_off,
+    const int32_t *__restrict__ u16_K, const int64_t *__restrict__ u16_colptr, const int32_t *__restrict__ u16_tidx,
+    const __nv_bfloat16 *__restrict__ u16, const __nv_bfloat16 *__restrict__ Th,
     const __nv_bfloat16 *__restrict__ Tl, const __nv_bfloat16 *__restrict__ Xh, const __nv_bfloat16 *__restrict__ Xl,
     double *__restrict__ Y) {
     extern __shared__ __align__(16) unsigned char sm[];
@@ -266,6 +272,11 @@ __global__ void __launch_bounds__(C::THREADS) row_mrhs_kernel(
         rp_panel<MT, float, C>(sm, dense + rho_off[rho] + (int64_t)r0t * Kd, Kd, rows, colidx + rho_colptr[rho], Xh,
                                Xl, acc);
         rp_panel<MT, TF, C>(sm, up + up_off[rho] + (int64_t)r0t * Ku, Ku, rows, tidx + up_colptr[rho], Th, Tl, acc);
+        if constexpr (TAIL) {
+            const int K16 = u16_K[rho];
+            rp_panel<MT, __nv_bfloat16, C>(sm, u16 + u16_off[rho] + (int64_t)r0t * K16, K16, rows,
+                                           u16_tidx + u16_colptr[rho], Th, Tl, acc);
+        }
         // per-column-group sums -> shared memory -> fixed-order sum over the KG groups
         float *red = reinterpret_cast<float *>(sm);
 #pragma unroll
@@ -504,10 +515,13 @@ __global__ void bcp_reduce_kernel(const int32_t *__restrict__ red, const int32_t
 
 // W_b into its block-column panel: for every leaf column cluster kappa of
 // sigma_b, the rows of kappa come from kappa's W panel (FP64 master); b's
-// position in kappa's block list (ascending) by a binary search per thread
+// position in kappa's block list (ascending) by a binary search per thread.
+// rank: the terms of b in this panel set, from term lofs[b] on (lofs null:
+// from the first); blocks without terms in the set have no panel columns.
 template <class TF>
 __global__ void bcp_pack_kernel(const int32_t *__restrict__ adm, const int32_t *__restrict__ rank,
-                                const int32_t *__restrict__ bgrp, const int32_t *__restrict__ bkoff,
+                                const int32_t *__restrict__ lofs, const int32_t *__restrict__ bgrp,
+                                const int32_t *__restrict__ bkoff,
                                 const int64_t *__restrict__ off, const int32_t *__restrict__ Kg,
                                 const int32_t *__restrict__ leaf_begin, int64_t nleaf,
                                 const int64_t *__restrict__ lr_colptr, const int32_t *__restrict__ lr_collist,
@@ -517,6 +531,8 @@ __global__ void bcp_pack_kernel(const int32_t *__restrict__ adm, const int32_t *
     const int32_t b = blockIdx.x;
     const int32_t cb = adm[4 * b + 2], ce = adm[4 * b + 3];
     const int k = rank[b];
+    if (k == 0) return;
+    const int l0 = lofs ? lofs[b] : 0;
     const int grp = bgrp[b], koff = bkoff[b], K = Kg[grp];
     TF *P = bcp + off[grp];
     // first leaf cluster of sigma_b
@@ -535,7 +551,7 @@ __global__ void bcp_pack_kernel(const int32_t *__restrict__ adm, const int32_t *
         }
         if (q >= lr_colptr[kap + 1] || lr_collist[q] != b) continue;  // cannot happen for a consistent block list
         const int32_t k0 = leaf_begin[kap], mk = leaf_begin[kap + 1] - k0;
-        const double *src = wp + wp_off[kap] + wp_koff[q];
+        const double *src = wp + wp_off[kap] + wp_koff[q] + l0;
         for (int e = threadIdx.x; e < mk * k; e += blockDim.x) {
             const int j = e / k, l = e - (e / k) * k;
             const double v = src[(int64_t)j * wp_K[kap] + l];
@@ -576,135 +592,275 @@ __global__ void mrhs_scatter_kernel(const double *__restrict__ Y, int64_t n, int
     }
 }
 
-// sort keys of the admissible blocks: (column begin, column end) in 2 nb bits
-__global__ void bcp_keys_kernel(const int32_t *__restrict__ adm, int64_t na, int nb, uint64_t *__restrict__ key,
-                                int32_t *__restrict__ id) {
+// sort keys of the admissible blocks: (column begin, column end) in 2 nb
+// bits; blocks without terms in the panel set get the all-ones key, which no
+// block's bounds make (column begins are < n < 2^nb - 1), and sort last
+__global__ void bcp_keys_kernel(const int32_t *__restrict__ adm, const int32_t *__restrict__ rank, int64_t na, int nb,
+                                uint64_t *__restrict__ key, int32_t *__restrict__ id) {
+    const uint64_t none = (uint64_t(1) << (2 * nb)) - 1;
     for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < na; b += (int64_t)gridDim.x * blockDim.x) {
-        key[b] = ((uint64_t)(uint32_t)adm[4 * b + 2] << nb) | (uint64_t)(uint32_t)adm[4 * b + 3];
+        key[b] = rank[b] == 0 ? none
+                              : ((uint64_t)(uint32_t)adm[4 * b + 2] << nb) | (uint64_t)(uint32_t)adm[4 * b + 3];
         id[b] = (int32_t)b;
     }
 }
 
-// The block-column panels of the low-precision W factors (first use per
-// precision): blocks grouped by column cluster (sorted on the device by
-// (column begin, column end), ties in block order: a stable radix sort of
-// the block ids), panel widths rounded up to 8 columns.
-static void build_bcp(const hm_matrix *Ac, hm_dtype prec, cudaStream_t s) {
-    static std::mutex mu;
-    std::lock_guard<std::mutex> lk(mu);
-    hm_matrix *A = const_cast<hm_matrix *>(Ac);  // cache owned by the matrix
-    if (A->bcp_dtype == (int)prec) return;
+// Grouping of the sorted admissible blocks into block-column panels, on the
+// device.  A group is a run of equal keys (one column cluster); its panel
+// holds the W factors of its blocks side by side in sorted order, width
+// rounded up to 8 (at least 8), and is cut into work items of CM_COLS panel
+// columns and at most BC_SPLIT rows (taller panels give several items whose
+// partial products go to consecutive slots and are added by one reduction
+// item per column tile).
+
+// head[i] = 1 where a run of equal keys starts (0 for the blocks without
+// terms and for head[na]); rk64 = the sorted ranks as int64 (rk64[na] = 0)
+__global__ void bcp_head_kernel(const uint64_t *__restrict__ key, const int32_t *__restrict__ rk, int64_t na,
+                                uint64_t none, int64_t *__restrict__ head, int64_t *__restrict__ rk64) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= na; i += (int64_t)gridDim.x * blockDim.x) {
+        head[i] = i < na && key[i] != none && (i == 0 || key[i] != key[i - 1]) ? 1 : 0;
+        rk64[i] = i < na ? rk[i] : 0;
+    }
+}
+
+// gs[g] = first sorted position of group g (from the exclusive scan of head),
+// gs[ng] = the end of the last group (the first block without terms, or na)
+__global__ void bcp_gstart_kernel(const uint64_t *__restrict__ key, const int64_t *__restrict__ head,
+                                  const int64_t *__restrict__ gx, int64_t na, int64_t ng, uint64_t none,
+                                  int64_t *__restrict__ gs) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < na; i += (int64_t)gridDim.x * blockDim.x) {
+        if (head[i]) gs[gx[i]] = i;
+        if (key[i] == none && (i == 0 || key[i - 1] != none)) gs[ng] = i;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && key[na - 1] != none) gs[ng] = na;
+}
+
+// per group: panel width K, rows (cb, ce), and the counts that the scans turn
+// into offsets (cnt[q][g], q = panel entries, width, items, reductions, slots)
+__global__ void bcp_group_kernel(const uint64_t *__restrict__ key, const int64_t *__restrict__ gs,
+                                 const int64_t *__restrict__ rpre, int64_t ng, int nb, int32_t *__restrict__ Kg,
+                                 int32_t *__restrict__ rows, int64_t *__restrict__ cnt) {
+    const uint64_t cmask = (uint64_t(1) << nb) - 1;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g <= ng; g += (int64_t)gridDim.x * blockDim.x) {
+        if (g == ng) {  // the scans' last (total) entries
+            for (int q = 0; q < 5; ++q) cnt[q * (ng + 1) + ng] = 0;
+            continue;
+        }
+        const int64_t i0 = gs[g], k = rpre[gs[g + 1]] - rpre[i0];
+        const int32_t K = k <= 8 ? 8 : (int32_t)((k + 7) / 8 * 8);
+        const uint64_t kk = key[i0];
+        const int32_t cb = (int32_t)(kk >> nb), ce = (int32_t)(kk & cmask), nrow = ce - cb;
+        const int32_t ncolt = (K + CM_COLS - 1) / CM_COLS, nsplit = (nrow + BC_SPLIT - 1) / BC_SPLIT;
+        Kg[g] = K;
+        rows[2 * g] = cb;
+        rows[2 * g + 1] = ce;
+        cnt[0 * (ng + 1) + g] = (int64_t)nrow * K;
+        cnt[1 * (ng + 1) + g] = K;
+        cnt[2 * (ng + 1) + g] = nsplit == 1 ? ncolt : (int64_t)ncolt * nsplit;
+        cnt[3 * (ng + 1) + g] = nsplit == 1 ? 0 : ncolt;
+        cnt[4 * (ng + 1) + g] = nsplit == 1 ? 0 : (int64_t)ncolt * nsplit;
+    }
+}
+
+// per sorted block with terms in the set: its group, its column offset in
+// the panel, and the map from its panel columns to its entries of t (the
+// set's terms of b start at term lofs[b], at 0 when lofs is null)
+__global__ void bcp_block_kernel(const int64_t *__restrict__ gx, const int64_t *__restrict__ head,
+                                 const int64_t *__restrict__ gs, const int64_t *__restrict__ rpre,
+                                 const int32_t *__restrict__ id, const int32_t *__restrict__ rk,
+                                 const int32_t *__restrict__ lofs, const int64_t *__restrict__ col0,
+                                 const int64_t *__restrict__ t_off, int64_t ng, int32_t *__restrict__ bgrp,
+                                 int32_t *__restrict__ bkoff, int32_t *__restrict__ tidx) {
+    const int64_t nend = gs[ng];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nend; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t g = gx[i] + head[i] - 1;
+        const int32_t b = id[i], koff = (int32_t)(rpre[i] - rpre[gs[g]]);
+        const int64_t t0 = t_off[b] + (lofs ? lofs[b] : 0);
+        bgrp[b] = (int32_t)g;
+        bkoff[b] = koff;
+        int32_t *ti = tidx + col0[g] + koff;
+        for (int l = 0; l < rk[i]; ++l) ti[l] = (int32_t)(t0 + l);
+    }
+}
+
+// the work items (grp, first column, first row, end row, slot or -1) and the
+// reduction items (grp, first column, first slot, slots), in group order and
+// column-tile order within a group
+__global__ void bcp_items_kernel(const int32_t *__restrict__ Kg, const int32_t *__restrict__ rows,
+                                 const int64_t *__restrict__ toff, const int64_t *__restrict__ roff,
+                                 const int64_t *__restrict__ soff, int64_t ng, int32_t *__restrict__ tiles,
+                                 int32_t *__restrict__ red) {
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < ng; g += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t K = Kg[g], nrow = rows[2 * g + 1] - rows[2 * g];
+        const int32_t ncolt = (K + CM_COLS - 1) / CM_COLS, nsplit = (nrow + BC_SPLIT - 1) / BC_SPLIT;
+        for (int32_t t = 0; t < ncolt; ++t) {
+            const int32_t n0 = t * CM_COLS;
+            if (nsplit == 1) {
+                int32_t *it = tiles + BC_ITEM * (toff[g] + t);
+                it[0] = (int32_t)g;
+                it[1] = n0;
+                it[2] = 0;
+                it[3] = nrow;
+                it[4] = -1;
+                continue;
+            }
+            const int32_t s0 = (int32_t)(soff[g] + (int64_t)t * nsplit);
+            int32_t *rd = red + 4 * (roff[g] + t);
+            rd[0] = (int32_t)g;
+            rd[1] = n0;
+            rd[2] = s0;
+            rd[3] = nsplit;
+            for (int32_t q = 0; q < nsplit; ++q) {
+                int32_t *it = tiles + BC_ITEM * (toff[g] + (int64_t)t * nsplit + q);
+                it[0] = (int32_t)g;
+                it[1] = n0;
+                it[2] = q * BC_SPLIT;
+                it[3] = (q + 1) * BC_SPLIT < nrow ? (q + 1) * BC_SPLIT : nrow;
+                it[4] = s0 + q;
+            }
+        }
+    }
+}
+
+__global__ void fill_i32_kernel(int32_t *__restrict__ a, int64_t n, int32_t v) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = v;
+}
+
+// k_b - k32_b: the trailing terms of every block (BF16 tails)
+__global__ void tail_rank_kernel(const int32_t *__restrict__ rank, const int32_t *__restrict__ rank32, int64_t na,
+                                 int32_t *__restrict__ out) {
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < na; b += (int64_t)gridDim.x * blockDim.x)
+        out[b] = rank[b] - rank32[b];
+}
+
+// The block-column panels of a set of terms of the W factors (built on first
+// use): blocks grouped by column cluster (sorted on the device by (column
+// begin, column end), ties in block order: a stable radix sort of the block
+// ids), panel widths rounded up to 8 columns; the grouping, the panels'
+// offsets and the work items are computed on the device.  rk: the set's
+// terms per block, from term lofs[b] on (lofs null: from the first); prec:
+// the panels' type (HM_F32 or HM_BF16).
+static void build_bcp(hm_matrix *A, BcpSet &S, hm_dtype prec, const int32_t *rk_set, const int32_t *lofs,
+                      cudaStream_t s) {
     const hm_tree *tr = A->tree;
     const int64_t na = tr->n_adm;
-    // column bounds are <= n < 2^nb
+    // column bounds are <= n < 2^nb - 1
     int nb = 1;
-    while (nb < 31 && (int64_t(1) << nb) <= tr->n) ++nb;
-    std::vector<int32_t> rank(std::max<int64_t>(na, 1)), order(std::max<int64_t>(na, 1)),
-        srank(std::max<int64_t>(na, 1));
-    std::vector<uint64_t> skey(std::max<int64_t>(na, 1));
+    while (nb < 31 && (int64_t(1) << nb) <= tr->n + 1) ++nb;
+    const uint64_t none = (uint64_t(1) << (2 * nb)) - 1;
+    DBuf key, id, tkey, tid, rk, head, rk64, gx, rpre, gs, cnt, cx, d_bgrp, d_bkoff;
+    const int64_t na1 = std::max<int64_t>(na, 1);
+    key.alloc(sizeof(uint64_t) * na1);
+    tkey.alloc(sizeof(uint64_t) * na1);
+    id.alloc(sizeof(int32_t) * na1);
+    tid.alloc(sizeof(int32_t) * na1);
+    rk.alloc(sizeof(int32_t) * na1);
+    head.alloc(sizeof(int64_t) * (na + 1));
+    rk64.alloc(sizeof(int64_t) * (na + 1));
+    gx.alloc(sizeof(int64_t) * (na + 1));
+    rpre.alloc(sizeof(int64_t) * (na + 1));
+    d_bgrp.alloc(sizeof(int32_t) * na1);
+    d_bkoff.alloc(sizeof(int32_t) * na1);
+    int64_t ng = 0;
     if (na > 0) {
-        DBuf key, id, tkey, tid, rk;
-        key.alloc(sizeof(uint64_t) * na);
-        tkey.alloc(sizeof(uint64_t) * na);
-        id.alloc(sizeof(int32_t) * na);
-        tid.alloc(sizeof(int32_t) * na);
-        rk.alloc(sizeof(int32_t) * na);
-        bcp_keys_kernel<<<grid1d_m(na), 256, 0, s>>>(tr->adm.as<int32_t>(), na, nb, key.as<uint64_t>(),
+        bcp_keys_kernel<<<grid1d_m(na), 256, 0, s>>>(tr->adm.as<int32_t>(), rk_set, na, nb, key.as<uint64_t>(),
                                                       id.as<int32_t>());
         HM_LAUNCH_CHECK();
         radix_sort_u64(key.as<uint64_t>(), id.as<int32_t>(), tkey.as<uint64_t>(), tid.as<int32_t>(), na, 2 * nb, s);
-        gather_i32(A->rank.as<int32_t>(), id.as<int32_t>(), rk.as<int32_t>(), na, s);
-        HM_CUDA_CHECK(cudaMemcpyAsync(rank.data(), A->rank.p, sizeof(int32_t) * na, cudaMemcpyDeviceToHost, s));
-        HM_CUDA_CHECK(cudaMemcpyAsync(order.data(), id.p, sizeof(int32_t) * na, cudaMemcpyDeviceToHost, s));
-        HM_CUDA_CHECK(cudaMemcpyAsync(srank.data(), rk.p, sizeof(int32_t) * na, cudaMemcpyDeviceToHost, s));
-        HM_CUDA_CHECK(cudaMemcpyAsync(skey.data(), key.p, sizeof(uint64_t) * na, cudaMemcpyDeviceToHost, s));
-        HM_CUDA_CHECK(cudaStreamSynchronize(s));
-    }
-    const uint64_t cmask = (uint64_t(1) << nb) - 1;
-    std::vector<int64_t> t_off(na + 1, 0);
-    for (int64_t b = 0; b < na; ++b) t_off[b + 1] = t_off[b] + rank[b];
-    std::vector<int64_t> off, col0;
-    std::vector<int32_t> Kg, rows, bgrp(std::max<int64_t>(na, 1)), bkoff(std::max<int64_t>(na, 1)), tidx, tiles, red;
-    int64_t o = 0, c = 0;
-    int32_t nslots = 0;
-    for (int64_t i = 0; i < na;) {
-        int64_t j = i;
-        int32_t k = 0;
-        const uint64_t key = skey[i];
-        const int32_t cb = (int32_t)(key >> nb), ce = (int32_t)(key & cmask);
-        while (j < na && skey[j] == key) {
-            bgrp[order[j]] = (int32_t)Kg.size();
-            bkoff[order[j]] = k;
-            k += srank[j];
-            ++j;
-        }
-        const int32_t K = std::max<int32_t>(8, (k + 7) / 8 * 8);
-        const int grp = (int)Kg.size();
-        Kg.push_back(K);
-        rows.push_back(cb);
-        rows.push_back(ce);
-        off.push_back(o);
-        col0.push_back(c);
-        tidx.resize(c + K, -1);
-        for (int64_t q = i; q < j; ++q) {
-            const int32_t b = order[q];
-            for (int32_t l = 0; l < srank[q]; ++l) tidx[c + bkoff[b] + l] = (int32_t)(t_off[b] + l);
-        }
-        const int32_t nrow = ce - cb;
-        const int32_t nsplit = (nrow + BC_SPLIT - 1) / BC_SPLIT;
-        for (int32_t n0 = 0; n0 < K; n0 += CM_COLS) {
-            if (nsplit == 1) {
-                tiles.insert(tiles.end(), {grp, n0, 0, nrow, -1});
-            } else {
-                red.insert(red.end(), {grp, n0, nslots, nsplit});
-                for (int32_t q = 0; q < nsplit; ++q)
-                    tiles.insert(tiles.end(), {grp, n0, q * BC_SPLIT, std::min(nrow, (q + 1) * BC_SPLIT), nslots + q});
-                nslots += nsplit;
-            }
-        }
-        o += (int64_t)(ce - cb) * K;
-        c += K;
-        i = j;
-    }
-    const int64_t ng = (int64_t)Kg.size();
-    auto up = [&](DBuf &d, const void *h, size_t bytes) {
-        d.alloc(std::max<size_t>(bytes, 16));
-        if (bytes) HM_CUDA_CHECK(cudaMemcpyAsync(d.p, h, bytes, cudaMemcpyHostToDevice, s));
-    };
-    up(A->bcp_off, off.data(), sizeof(int64_t) * ng);
-    up(A->bcp_K, Kg.data(), sizeof(int32_t) * ng);
-    up(A->bcp_rows, rows.data(), sizeof(int32_t) * 2 * ng);
-    up(A->bcp_col0, col0.data(), sizeof(int64_t) * ng);
-    up(A->bcp_tidx, tidx.data(), sizeof(int32_t) * tidx.size());
-    up(A->bcp_tiles, tiles.data(), sizeof(int32_t) * tiles.size());
-    up(A->bcp_red, red.data(), sizeof(int32_t) * red.size());
-    DBuf d_bgrp, d_bkoff;
-    up(d_bgrp, bgrp.data(), sizeof(int32_t) * na);
-    up(d_bkoff, bkoff.data(), sizeof(int32_t) * na);
-    const size_t esz = prec == HM_BF16 ? 2 : 4;
-    A->bcp.alloc(esz * std::max<int64_t>(o, 8));
-    HM_CUDA_CHECK(cudaMemsetAsync(A->bcp.p, 0, esz * std::max<int64_t>(o, 8), s));
-    if (na > 0) {
-        if (prec == HM_BF16)
-            bcp_pack_kernel<__nv_bfloat16><<<(unsigned)na, 128, 0, s>>>(
-                tr->adm.as<int32_t>(), A->rank.as<int32_t>(), d_bgrp.as<int32_t>(), d_bkoff.as<int32_t>(),
-                A->bcp_off.as<int64_t>(), A->bcp_K.as<int32_t>(), tr->leaf_begin.as<int32_t>(), tr->n_leaf,
-                tr->lr_colptr.as<int64_t>(), tr->lr_collist.as<int32_t>(), A->wp_off.as<int64_t>(),
-                A->wp_K.as<int32_t>(), A->wp_koff.as<int32_t>(), A->wp.as<double>(), A->bcp.as<__nv_bfloat16>());
-        else
-            bcp_pack_kernel<float><<<(unsigned)na, 128, 0, s>>>(
-                tr->adm.as<int32_t>(), A->rank.as<int32_t>(), d_bgrp.as<int32_t>(), d_bkoff.as<int32_t>(),
-                A->bcp_off.as<int64_t>(), A->bcp_K.as<int32_t>(), tr->leaf_begin.as<int32_t>(), tr->n_leaf,
-                tr->lr_colptr.as<int64_t>(), tr->lr_collist.as<int32_t>(), A->wp_off.as<int64_t>(),
-                A->wp_K.as<int32_t>(), A->wp_koff.as<int32_t>(), A->wp.as<double>(), A->bcp.as<float>());
+        gather_i32(rk_set, id.as<int32_t>(), rk.as<int32_t>(), na, s);
+        bcp_head_kernel<<<grid1d_m(na + 1), 256, 0, s>>>(key.as<uint64_t>(), rk.as<int32_t>(), na, none,
+                                                          head.as<int64_t>(), rk64.as<int64_t>());
         HM_LAUNCH_CHECK();
+        ng = exclusive_scan_i64(head.as<int64_t>(), gx.as<int64_t>(), na + 1, s);
+        exclusive_scan_i64(rk64.as<int64_t>(), rpre.as<int64_t>(), na + 1, s);
+    }
+    gs.alloc(sizeof(int64_t) * (ng + 1));
+    cnt.alloc(sizeof(int64_t) * 5 * (ng + 1));
+    cx.alloc(sizeof(int64_t) * 5 * (ng + 1));
+    S.K.alloc(sizeof(int32_t) * std::max<int64_t>(ng, 4));
+    S.rows.alloc(sizeof(int32_t) * std::max<int64_t>(2 * ng, 4));
+    // the scans of the five counts: panel offsets, first columns, item, reduction and slot offsets
+    int64_t tot[5] = {0, 0, 0, 0, 0};
+    if (ng > 0) {
+        bcp_gstart_kernel<<<grid1d_m(na), 256, 0, s>>>(key.as<uint64_t>(), head.as<int64_t>(), gx.as<int64_t>(), na,
+                                                        ng, none, gs.as<int64_t>());
+        HM_LAUNCH_CHECK();
+        bcp_group_kernel<<<grid1d_m(ng + 1), 256, 0, s>>>(key.as<uint64_t>(), gs.as<int64_t>(), rpre.as<int64_t>(),
+                                                           ng, nb, S.K.as<int32_t>(), S.rows.as<int32_t>(),
+                                                           cnt.as<int64_t>());
+        HM_LAUNCH_CHECK();
+        for (int q = 0; q < 5; ++q)
+            tot[q] = exclusive_scan_i64(cnt.as<int64_t>() + q * (ng + 1), cx.as<int64_t>() + q * (ng + 1), ng + 1, s);
+    }
+    const int64_t o = tot[0], c = tot[1], ntiles = tot[2], nred = tot[3], nslots = tot[4];
+    const int64_t *d_off = cx.as<int64_t>(), *d_col0 = d_off + (ng + 1), *d_toff = d_off + 2 * (ng + 1),
+                  *d_roff = d_off + 3 * (ng + 1), *d_soff = d_off + 4 * (ng + 1);
+    S.off.alloc(sizeof(int64_t) * (ng + 1));
+    S.col0.alloc(sizeof(int64_t) * (ng + 1));
+    S.tidx.alloc(std::max<size_t>(sizeof(int32_t) * c, 16));
+    S.tiles.alloc(std::max<size_t>(sizeof(int32_t) * BC_ITEM * ntiles, 16));
+    S.red.alloc(std::max<size_t>(sizeof(int32_t) * 4 * nred, 16));
+    const size_t esz = prec == HM_BF16 ? 2 : 4;
+    S.data.alloc(esz * std::max<int64_t>(o, 8));
+    HM_CUDA_CHECK(cudaMemsetAsync(S.data.p, 0, esz * std::max<int64_t>(o, 8), s));
+    if (ng > 0) {
+        HM_CUDA_CHECK(cudaMemcpyAsync(S.off.p, d_off, sizeof(int64_t) * (ng + 1), cudaMemcpyDeviceToDevice, s));
+        HM_CUDA_CHECK(cudaMemcpyAsync(S.col0.p, d_col0, sizeof(int64_t) * (ng + 1), cudaMemcpyDeviceToDevice, s));
+        fill_i32_kernel<<<grid1d_m(c), 256, 0, s>>>(S.tidx.as<int32_t>(), c, -1);
+        HM_LAUNCH_CHECK();
+        bcp_block_kernel<<<grid1d_m(na), 256, 0, s>>>(gx.as<int64_t>(), head.as<int64_t>(), gs.as<int64_t>(),
+                                                       rpre.as<int64_t>(), id.as<int32_t>(), rk.as<int32_t>(), lofs,
+                                                       d_col0, A->t_off.as<int64_t>(), ng, d_bgrp.as<int32_t>(),
+                                                       d_bkoff.as<int32_t>(), S.tidx.as<int32_t>());
+        HM_LAUNCH_CHECK();
+        bcp_items_kernel<<<grid1d_m(ng), 256, 0, s>>>(S.K.as<int32_t>(), S.rows.as<int32_t>(), d_toff, d_roff,
+                                                       d_soff, ng, S.tiles.as<int32_t>(), S.red.as<int32_t>());
+        HM_LAUNCH_CHECK();
+        auto pack = [&](auto *out) {
+            using TF = std::remove_pointer_t<decltype(out)>;
+            bcp_pack_kernel<TF><<<(unsigned)na, 128, 0, s>>>(
+                tr->adm.as<int32_t>(), rk_set, lofs, d_bgrp.as<int32_t>(), d_bkoff.as<int32_t>(), S.off.as<int64_t>(),
+                S.K.as<int32_t>(), tr->leaf_begin.as<int32_t>(), tr->n_leaf, tr->lr_colptr.as<int64_t>(),
+                tr->lr_collist.as<int32_t>(), A->wp_off.as<int64_t>(), A->wp_K.as<int32_t>(),
+                A->wp_koff.as<int32_t>(), A->wp.as<double>(), out);
+            HM_LAUNCH_CHECK();
+        };
+        if (prec == HM_BF16) pack(S.data.as<__nv_bfloat16>());
+        else pack(S.data.as<float>());
     }
     HM_CUDA_CHECK(cudaStreamSynchronize(s));
-    A->bcp_ngroups = ng;
-    A->bcp_ntiles = (int64_t)tiles.size() / BC_ITEM;
-    A->bcp_nred = (int64_t)red.size() / 4;
-    A->bcp_nslots = nslots;
-    A->bcp_dtype = (int)prec;
+    S.ngroups = ng;
+    S.ntiles = ntiles;
+    S.nred = nred;
+    S.nslots = nslots;
+    S.dtype = (int)prec;
+}
+
+// The block-column panels of a precision: HM_F32 with BF16 tails gives two
+// sets (leading terms FP32, trailing terms BF16), otherwise one set of all
+// terms in that precision.
+static void build_bcp_sets(const hm_matrix *Ac, hm_dtype prec, cudaStream_t s) {
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    hm_matrix *A = const_cast<hm_matrix *>(Ac);  // cache owned by the matrix
+    if (A->bcp.dtype == (int)prec) return;
+    const bool tails = prec == HM_F32 && A->rank32.p && A->ut16.data.p;
+    if (!tails) {
+        build_bcp(A, A->bcp, prec, A->rank.as<int32_t>(), nullptr, s);
+        return;
+    }
+    const int64_t na = A->tree->n_adm;
+    DBuf r16;
+    r16.alloc(sizeof(int32_t) * std::max<int64_t>(na, 1));
+    if (na > 0) {
+        tail_rank_kernel<<<grid1d_m(na), 256, 0, s>>>(A->rank.as<int32_t>(), A->rank32.as<int32_t>(), na,
+                                                       r16.as<int32_t>());
+        HM_LAUNCH_CHECK();
+    }
+    A->bcp.dtype = -1;
+    build_bcp(A, A->bcp16, HM_BF16, r16.as<int32_t>(), A->rank32.as<int32_t>(), s);
+    build_bcp(A, A->bcp, HM_F32, A->rank32.as<int32_t>(), nullptr, s);
 }
 
 static int bcp_smem(bool f32) {
@@ -717,11 +873,12 @@ static int bcp_smem(bool f32) {
 // projection tiles whose rows were split.  Call mrhs_prepare first.
 int64_t mrhs_work_floats(const hm_matrix *A) {
     const int64_t n = A->tree->n, K = std::max<int64_t>(A->total_rank, 1);
-    return 4 * MR * n + MR * K + std::max<int64_t>(A->bcp_nslots, 1) * CM_COLS * MR;  // 48 n + 16 n + 16 K + P
+    const int64_t P = std::max<int64_t>(std::max(A->bcp.nslots, A->bcp16.nslots), 1);
+    return 4 * MR * n + MR * K + P * CM_COLS * MR;  // 48 n + 16 n + 16 K + P
 }
 
 void mrhs_prepare(const hm_matrix *A, hm_dtype prec, cudaStream_t s) {
-    if ((prec == HM_F32 && A->up32.p) || (prec == HM_BF16 && A->upbf.p)) build_bcp(A, prec, s);
+    if ((prec == HM_F32 && A->up32.p) || (prec == HM_BF16 && A->upbf.p)) build_bcp_sets(A, prec, s);
     hm_matrix *Am = const_cast<hm_matrix *>(A);  // cache owned by the matrix
     if (!Am->mrhs_err.p) {
         Am->mrhs_err.alloc(sizeof(int));
@@ -758,37 +915,57 @@ template <int MT, class C> static int row_smem() {
 using RpShape5 = RpCfg<8, 8, 2>;
 using RpDefault = RpCfg<4, 4, 3>;
 
+// t = W^T X over one set of block-column panels (col_bcp_kernel, then the
+// sums of the work items whose rows were split)
+template <class TF>
+static void col_pass(const BcpSet &S, const __nv_bfloat16 *Xh, const __nv_bfloat16 *Xl, __nv_bfloat16 *Th,
+                     __nv_bfloat16 *Tl, float *part, cudaStream_t s) {
+    if (S.ntiles == 0) return;
+    const bool f32 = sizeof(TF) == 4;
+    const int smem = bcp_smem(f32);
+    HM_CUDA_CHECK(cudaFuncSetAttribute(col_bcp_kernel<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    {
+        Trace tc(f32 ? "col_bcp_kernel.f32" : "col_bcp_kernel.bf16", s);
+        col_bcp_kernel<TF><<<(unsigned)S.ntiles, CM_THREADS, smem, s>>>(
+            S.tiles.as<int32_t>(), S.off.as<int64_t>(), S.K.as<int32_t>(), S.rows.as<int32_t>(), S.col0.as<int64_t>(),
+            S.tidx.as<int32_t>(), S.data.as<TF>(), Xh, Xl, Th, Tl, part);
+        HM_LAUNCH_CHECK();
+    }
+    if (S.nred > 0) {
+        bcp_reduce_kernel<<<(unsigned)S.nred, 256, 0, s>>>(S.red.as<int32_t>(), S.K.as<int32_t>(),
+                                                           S.col0.as<int64_t>(), S.tidx.as<int32_t>(), part, Th, Tl);
+        HM_LAUNCH_CHECK();
+    }
+}
+
 template <class TF>
 static void matvec_mrhs_impl(const hm_matrix *A, const TF *up, const float *X, double *Y, __nv_bfloat16 *Xh,
                              __nv_bfloat16 *Xl, __nv_bfloat16 *Th, __nv_bfloat16 *Tl, float *part, cudaStream_t s) {
     const hm_tree *tr = A->tree;
     const int64_t n = tr->n;
     const bool f32 = sizeof(TF) == 4;
+    // FP32 factors with BF16 tails: leading terms from the FP32 sets, trailing terms from the BF16 ones
+    const bool tails = f32 && A->bcp16.dtype == HM_BF16 && A->ut16.data.p;
     split_rows_kernel<<<grid1d_m(n * MR), 256, 0, s>>>(X, n * MR, Xh, Xl);
     HM_LAUNCH_CHECK();
-    if (tr->n_adm > 0 && A->bcp_ntiles > 0) {
-        const int smem = bcp_smem(f32);
-        HM_CUDA_CHECK(cudaFuncSetAttribute(col_bcp_kernel<TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        Trace tc(f32 ? "col_bcp_kernel.f32" : "col_bcp_kernel.bf16", s);
-        col_bcp_kernel<TF><<<(unsigned)A->bcp_ntiles, CM_THREADS, smem, s>>>(
-            A->bcp_tiles.as<int32_t>(), A->bcp_off.as<int64_t>(), A->bcp_K.as<int32_t>(), A->bcp_rows.as<int32_t>(),
-            A->bcp_col0.as<int64_t>(), A->bcp_tidx.as<int32_t>(), A->bcp.as<TF>(), Xh, Xl, Th, Tl, part);
-        HM_LAUNCH_CHECK();
-        if (A->bcp_nred > 0) {
-            bcp_reduce_kernel<<<(unsigned)A->bcp_nred, 256, 0, s>>>(A->bcp_red.as<int32_t>(), A->bcp_K.as<int32_t>(),
-                                                                    A->bcp_col0.as<int64_t>(),
-                                                                    A->bcp_tidx.as<int32_t>(), part, Th, Tl);
-            HM_LAUNCH_CHECK();
-        }
+    if (tr->n_adm > 0) {
+        col_pass<TF>(A->bcp, Xh, Xl, Th, Tl, part, s);
+        if (tails) col_pass<__nv_bfloat16>(A->bcp16, Xh, Xl, Th, Tl, part, s);
     }
     const int tiles = (tr->max_leaf + 15) / 16;
     auto launch = [&](auto kern, int smem, int threads) {
         HM_CUDA_CHECK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         Trace tr_(f32 ? "row_mrhs_kernel.f32" : "row_mrhs_kernel.bf16", s);
+        const TailPanels &U = tails ? A->ut32 : A->ut16;  // ut16: unused (TAIL = false) unless tails
+        const TF *u = tails ? reinterpret_cast<const TF *>(A->ut32.data.p) : up;
         kern<<<(unsigned)tr->n_leaf, threads, smem, s>>>(
             tr->leaf_begin.as<int32_t>(), tr->rho_off.as<int64_t>(), tr->rho_K.as<int32_t>(),
-            tr->rho_colptr.as<int64_t>(), tr->colidx.as<int32_t>(), A->dense32.as<float>(), A->up_off.as<int64_t>(),
-            A->up_K.as<int32_t>(), A->up_colptr.as<int64_t>(), A->tidx.as<int32_t>(), up, Th, Tl, Xh, Xl, Y);
+            tr->rho_colptr.as<int64_t>(), tr->colidx.as<int32_t>(), A->dense32.as<float>(),
+            tails ? U.off.as<int64_t>() : A->up_off.as<int64_t>(), tails ? U.K.as<int32_t>() : A->up_K.as<int32_t>(),
+            tails ? U.colptr.as<int64_t>() : A->up_colptr.as<int64_t>(),
+            tails ? U.tidx.as<int32_t>() : A->tidx.as<int32_t>(), u, A->ut16.off.as<int64_t>(),
+            A->ut16.K.as<int32_t>(), A->ut16.colptr.as<int64_t>(), A->ut16.tidx.as<int32_t>(),
+            A->ut16.data.as<__nv_bfloat16>(), Th, Tl, Xh, Xl, Y);
         HM_LAUNCH_CHECK();
     };
     if (A->params.mrhs_tcgen05 && A->mrhs_err.p) {  // the measured tcgen05 / TMEM row pass (mrhs_tc.cu)
@@ -797,9 +974,17 @@ static void matvec_mrhs_impl(const hm_matrix *A, const TF *up, const float *X, d
     }
     using C = RpDefault;
     using C5 = RpShape5;
-    if (tiles <= 3) launch(row_mrhs_kernel<3, TF, C>, row_smem<3, C>(), C::THREADS);
-    else if (tiles <= 5) launch(row_mrhs_kernel<5, TF, C5>, row_smem<5, C5>(), C5::THREADS);
-    else launch(row_mrhs_kernel<8, TF, C>, row_smem<8, C>(), C::THREADS);
+    if (tails) {
+        if constexpr (sizeof(TF) == 4) {
+            if (tiles <= 3) launch(row_mrhs_kernel<3, float, C, true>, row_smem<3, C>(), C::THREADS);
+            else if (tiles <= 5) launch(row_mrhs_kernel<5, float, C5, true>, row_smem<5, C5>(), C5::THREADS);
+            else launch(row_mrhs_kernel<8, float, C, true>, row_smem<8, C>(), C::THREADS);
+        }
+        return;
+    }
+    if (tiles <= 3) launch(row_mrhs_kernel<3, TF, C, false>, row_smem<3, C>(), C::THREADS);
+    else if (tiles <= 5) launch(row_mrhs_kernel<5, TF, C5, false>, row_smem<5, C5>(), C5::THREADS);
+    else launch(row_mrhs_kernel<8, TF, C, false>, row_smem<8, C>(), C::THREADS);
 }
 
 // Y (Morton [n][16] FP64) = H X (Morton [n][16] FP32) with the FP32 near field
@@ -808,7 +993,7 @@ static void matvec_mrhs_impl(const hm_matrix *A, const TF *up, const float *X, d
 // have run for this precision.
 void matvec_mrhs_morton(const hm_matrix *A, hm_dtype prec, const float *X, double *Y, float *work, cudaStream_t s) {
     if (!A->dense32.p) fail(HM_EINVAL, "the multi-RHS product needs the FP32 near-field copy");
-    if (A->bcp_dtype != (int)prec) fail(HM_EINTERNAL, "multi-RHS panels not prepared for this precision");
+    if (A->bcp.dtype != (int)prec) fail(HM_EINTERNAL, "multi-RHS panels not prepared for this precision");
     const int64_t n = A->tree->n, K = std::max<int64_t>(A->total_rank, 1);
     __nv_bfloat16 *Xh = reinterpret_cast<__nv_bfloat16 *>(work);
     __nv_bfloat16 *Xl = Xh + MR * n;

@@ -14,7 +14,7 @@ class GpuH:
     """Tree + H-matrix built through the C ABI, freed on close()."""
 
     def __init__(self, V, T, leaf=64, eta=1.5, eps=1e-6, kmax=64, ss_order=8, factor_dtype=0, dense_dtype=0,
-                 nearfield_fp64=0, mrhs_tcgen05=0):
+                 nearfield_fp64=0, mrhs_tcgen05=0, factor_tail_bits=0):
         torch = need_gpu()
         import paper_1806_11558_gb300 as hm
         self.hm = hm
@@ -28,7 +28,8 @@ class GpuH:
         if eps is not None:
             self.A = hm.hm_assemble(self.tree, aca_eps=eps, aca_kmax=kmax, ss_order=ss_order,
                                     factor_dtype=factor_dtype, dense_dtype=dense_dtype,
-                                    nearfield_fp64=nearfield_fp64, mrhs_tcgen05=mrhs_tcgen05)
+                                    nearfield_fp64=nearfield_fp64, mrhs_tcgen05=mrhs_tcgen05,
+                                    factor_tail_bits=factor_tail_bits)
 
     def perm(self):
         return self.hm.hm_tree_get_perm(self.tree, self.n).cpu().numpy()
