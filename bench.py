@@ -127,8 +127,9 @@ def algorithmic_work(mi, ti, dense_leaves, n):
     w16 = mi.get("lr_tail_entries", 0) - u16
     K16 = mi.get("factor_tail_terms", 0)
     nl = (ti["n_clusters"] + 1) // 2  # leaf clusters of the binary cluster tree; partials = sum over them of K_w
-    # 16 right-hand sides: X and t rows as BF16 pairs (16 x 2 x 2 B), Y rows FP64 (16 x 8 B)
-    xr, yr = 4.0 * MR, 8.0 * MR
+    # 16 right-hand sides: X and t rows as BF16 pairs (16 x 2 x 2 B); the timed solve's row pass writes its
+    # rows straight into the block of FP32 Krylov vectors (16 x 4 B)
+    xr, yr = 4.0 * MR, 4.0 * MR
     return {
         "row_kernel.f64": ("alu", 2.0 * (d + u), "flop"),
         "col_kernel.f64": ("alu", 2.0 * w, "flop"),
@@ -814,6 +815,7 @@ def run_workload(name):
           "blockmv8_tc": lambda t, h: run_blockmv(t, h, "large", tcgen05=1),
           "blockmv8_tail": lambda t, h: run_blockmv(t, h, "large", tail_bits=12),
           "blockmv_tail": lambda t, h: run_blockmv(t, h, tail_bits=12),
+          "solve6": run_solve16,
           "dfmv8": lambda t, h: run_dfmv(t, h, "large"), "dfmv6": lambda t, h: run_dfmv(t, h, "bumped6")}[name]
     ck = Clocks(torch.cuda.current_device())
     ck.start()
@@ -984,6 +986,40 @@ def run_blockmv(torch, hm, case="bumped6", tcgen05=0, tail_bits=0):
     return out
 
 
+def run_solve16(torch, hm, level=6):
+    """The large workload's step at a smaller size (profiling): unit icosphere
+    of the given level, leaf 128, ACA eps 1e-6, the large workload's 16
+    sources, FP32 copies, and its batched refined solve (the same solver
+    parameters); one untimed step, then one timed."""
+    import meshgen
+    W = LARGE
+    V, T = meshgen.icosphere(level)
+    n = T.shape[0]
+    Vd, Td = torch.from_numpy(V).cuda(), torch.from_numpy(T).cuda()
+    src = torch.from_numpy(np.ascontiguousarray(meshgen.point_sources(meshgen.MASTER_SEED + 5, W["nrhs"]))).cuda()
+    F = torch.empty((W["nrhs"], n), dtype=torch.float64, device="cuda")
+    out = {"workload": "unit icosphere level %d (%d panels), leaf 128, 16 sources, the large workload's step" % (
+        level, n)}
+    for rep in range(2):
+        a, b = _ev(torch), _ev(torch)
+        a.record()
+        tree = hm.hm_build_tree(Vd, Td, eta=W["eta"], leaf_size=W["leaf_size"])
+        A = hm.hm_assemble(tree, aca_eps=W["aca_eps"], aca_kmax=W["aca_kmax"], ss_order=W["ss_order"],
+                           factor_dtype=hm.HM_F32, dense_dtype=hm.HM_F32)
+        hm.hm_load_vector(tree, src, F)
+        X = torch.zeros_like(F)
+        info = hm.hm_solve(A, F, X, refine=1, inner_dtype=hm.HM_F32, inner_tol=W["inner_tol"], max_refine=40,
+                           resid_df=1, rel_tol=W["solve_rel_tol"], restart=W["restart"], max_iter=5000,
+                           precond=int(W["precond"]), batched=1)
+        b.record()
+        torch.cuda.synchronize()
+        out.update(step_s=a.elapsed_time(b) / 1e3, iters=info.iters, refine_steps=info.refine_steps,
+                   rel_resid=info.rel_resid)
+        hm.hm_free(A)
+        hm.hm_free(tree)
+    return out
+
+
 def run_dfmv(torch, hm, case):
     """The FP64 master applied to 16 right-hand sides: the double-float
     16-column product (hm_matvec_block, HM_F64) against 16 FP64 products
@@ -1040,7 +1076,7 @@ def main():
                     help="run exactly one step (no warm-up, no extras) and print its phase times")
     ap.add_argument("--workload", default=None,
                     choices=["batching", "differentiation", "blockmv", "blockmv7", "blockmv_tc", "blockmv8", "blockmv8_tc",
-                             "blockmv8_tail", "blockmv_tail",
+                             "blockmv8_tail", "blockmv_tail", "solve6",
                              "dfmv6", "dfmv8"],
                     help="measure one of the other workloads once and print its numbers (not a bench line)")
     args = ap.parse_args()

@@ -27,7 +27,8 @@ namespace hm {
 void matvec_morton(const hm_matrix *A, hm_dtype prec, const MatvecWork &w, cudaStream_t s, bool trans);
 int64_t matvec_work_doubles(const hm_matrix *A);
 MatvecWork matvec_work_at(const hm_matrix *A, double *base);
-void matvec_mrhs_morton(const hm_matrix *A, hm_dtype prec, const float *X, double *Y, float *work, cudaStream_t s);
+void matvec_mrhs_morton_cols(const hm_matrix *A, hm_dtype prec, const float *X, double *Y, void *out, bool out_f32,
+                             int nr, int64_t ld, float *work, cudaStream_t s);
 int64_t mrhs_work_floats(const hm_matrix *A);
 void mrhs_prepare(const hm_matrix *A, hm_dtype prec, cudaStream_t s);
 void bj_setup(const hm_matrix *A, cudaStream_t s);
@@ -53,12 +54,14 @@ static unsigned gx(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<i
 
 // part[item][l] = V_l(col, i0:i1) . w(col, i0:i1), l < nv (0 for inactive systems).
 // Warp k of the CTA takes the k-th contiguous chunk of the item and runs over
-// every vector: per vector its lanes stride the chunk with four independent
-// accumulators (the chunk of w stays in L1 after the first vector) and add
-// them by shuffles; the eight warps' sums of each vector are added in a
-// fixed order at the end, so the CTA synchronises once.  TV: the type of the
-// Krylov vectors and of the arithmetic up to the warp sums (FP64; FP32 for
-// the FP32 Krylov vectors of the inner solves), FP64 from there on.
+// the vectors, four per pass over the chunk (the chunk of w is loaded once
+// per pass): per vector its lanes stride the chunk with four independent
+// accumulators and add them by shuffles (the same elements in the same order
+// whether a vector is taken in a pass of four or alone); the eight warps'
+// sums of each vector are added in a fixed order at the end, so the CTA
+// synchronises once.  TV: the type of the Krylov vectors and of the
+// arithmetic up to the warp sums (FP64; FP32 for the FP32 Krylov vectors of
+// the inner solves), FP64 from there on.
 constexpr int BMAXV = 129;  // restart + 1
 template <class TV>
 __global__ void __launch_bounds__(BTHREADS) bdots_kernel(const Item *__restrict__ items, const TV *__restrict__ V,
@@ -66,7 +69,7 @@ __global__ void __launch_bounds__(BTHREADS) bdots_kernel(const Item *__restrict_
                                                          const TV *__restrict__ w, const int *__restrict__ act,
                                                          double *__restrict__ part, const LoopCtl *ctl) {
     if (ctl) nv = ctl->j + 1;
-    constexpr int BW = BTHREADS / 32;
+    constexpr int BW = BTHREADS / 32, NQ = 4;
     __shared__ double s_part[BW][BMAXV];
     const Item it = items[blockIdx.x];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -75,10 +78,47 @@ __global__ void __launch_bounds__(BTHREADS) bdots_kernel(const Item *__restrict_
     const int64_t chunk = ((len + BW - 1) / BW + 31) / 32 * 32;
     const int64_t c0 = it.i0 + warp * chunk, c1 = min(it.i1, c0 + chunk);
     const TV *wc = w + (int64_t)it.col * n;
-    for (int l = 0; l < nv; ++l) {
+    const TV *vb = V + (int64_t)it.col * n;
+    int l = 0;
+    for (; l + NQ <= nv; l += NQ) {
+        TV a[NQ][4];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) a[q][0] = a[q][1] = a[q][2] = a[q][3] = 0;
+        if (on) {
+            const TV *v0 = vb + (int64_t)l * vstride;
+            int64_t i = c0 + lane;
+            for (; i + 96 < c1; i += 128) {
+                const TV w0 = wc[i], w1 = wc[i + 32], w2 = wc[i + 64], w3 = wc[i + 96];
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) {
+                    const TV *vq = v0 + q * vstride;
+                    a[q][0] = fma(vq[i], w0, a[q][0]);
+                    a[q][1] = fma(vq[i + 32], w1, a[q][1]);
+                    a[q][2] = fma(vq[i + 64], w2, a[q][2]);
+                    a[q][3] = fma(vq[i + 96], w3, a[q][3]);
+                }
+            }
+            for (; i < c1; i += 32) {
+                const TV w0 = wc[i];
+#pragma unroll
+                for (int q = 0; q < NQ; ++q) a[q][0] = fma(v0[q * vstride + i], w0, a[q][0]);
+            }
+        }
+        TV t[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) t[q] = (a[q][0] + a[q][1]) + (a[q][2] + a[q][3]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) t[q] += __shfl_xor_sync(0xffffffffu, t[q], o);
+        if (lane == 0)
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) s_part[warp][l + q] = (double)t[q];
+    }
+    for (; l < nv; ++l) {
         TV a0 = 0, a1 = 0, a2 = 0, a3 = 0;
         if (on) {
-            const TV *vl = V + (int64_t)l * vstride + (int64_t)it.col * n;
+            const TV *vl = vb + (int64_t)l * vstride;
             int64_t i = c0 + lane;
             for (; i + 96 < c1; i += 128) {
                 a0 = fma(vl[i], wc[i], a0);
@@ -94,10 +134,10 @@ __global__ void __launch_bounds__(BTHREADS) bdots_kernel(const Item *__restrict_
         if (lane == 0) s_part[warp][l] = (double)t;
     }
     __syncthreads();
-    for (int l = threadIdx.x; l < nv; l += BTHREADS) {
+    for (int l2 = threadIdx.x; l2 < nv; l2 += BTHREADS) {
         double t = 0.0;
-        for (int k = 0; k < BW; ++k) t += s_part[k][l];
-        part[(int64_t)blockIdx.x * nv + l] = t;
+        for (int k = 0; k < BW; ++k) t += s_part[k][l2];
+        part[(int64_t)blockIdx.x * nv + l2] = t;
     }
 }
 
@@ -301,35 +341,14 @@ __global__ void bset_g0_kernel(int S, int m, const int *__restrict__ mask, const
     gs[0] = sqrt(nrm2[s]);
 }
 
-// [R][n] FP64 / FP32 <-> [n][16] blocks of the tensor-core product
+// [R][n] FP64 / FP32 -> [n][16] blocks of the tensor-core product (the
+// product writes its result straight back as [R][n])
 template <class TI>
 __global__ void to_block_kernel(const TI *__restrict__ v, int64_t n, int R, float *__restrict__ X) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * BMR; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = e / BMR;
         const int r = (int)(e - i * BMR);
         X[e] = r < R ? (float)v[(int64_t)r * n + i] : 0.0f;
-    }
-}
-
-// v[r][i] = Y[i][r] for r < R: 64 rows per block, read as whole [16] rows
-// (coalesced), transposed through shared memory, written per r (coalesced)
-constexpr int FB_ROWS = 64;
-template <class TO>
-__global__ void __launch_bounds__(256) from_block_kernel(const double *__restrict__ Y, int64_t n, int R,
-                                                         TO *__restrict__ v) {
-    __shared__ double s_y[BMR][FB_ROWS + 1];
-    for (int64_t i0 = blockIdx.x * (int64_t)FB_ROWS; i0 < n; i0 += (int64_t)gridDim.x * FB_ROWS) {
-        const int rows = (int)((n - i0) < FB_ROWS ? (n - i0) : (int64_t)FB_ROWS);
-        __syncthreads();
-        for (int e = threadIdx.x; e < rows * BMR; e += blockDim.x) {
-            const int i = e / BMR, r = e - i * BMR;
-            s_y[r][i] = Y[(i0 + i) * BMR + r];
-        }
-        __syncthreads();
-        for (int e = threadIdx.x; e < R * FB_ROWS; e += blockDim.x) {
-            const int r = e / FB_ROWS, i = e - r * FB_ROWS;
-            if (i < rows) v[(int64_t)r * n + i0 + i] = (TO)s_y[r][i];
-        }
     }
 }
 
@@ -481,9 +500,7 @@ struct Batch {
             const int nr = std::min(BMR, R - r0);
             to_block_kernel<TI><<<gx(n * BMR), 256, 0, s>>>(x + (int64_t)r0 * n, n, nr, X);
             HM_LAUNCH_CHECK();
-            matvec_mrhs_morton(A, prec, X, Y, work, s);
-            from_block_kernel<TO><<<gx(n), 256, 0, s>>>(Y, n, nr, yv + (int64_t)r0 * n);
-            HM_LAUNCH_CHECK();
+            matvec_mrhs_morton_cols(A, prec, X, Y, yv + (int64_t)r0 * n, sizeof(TO) == 4, nr, n, work, s);
         }
     }
     void bj(const double *v, double *z, bool low, cudaStream_t s) { bj_apply_cols(A, v, z, R, false, low, s); }

@@ -240,6 +240,15 @@ __device__ __forceinline__ void rp_panel(unsigned char *sm, const TP *__restrict
     __syncthreads();
 }
 
+// Output of the row pass: mode 0 = Y [n][16] FP64 (Morton rows); 1 / 2 =
+// the first nr columns into p as [column][ld] FP32 / FP64 (the layout of a
+// block of Krylov vectors), the same values (FP32 sums, widened or not).
+struct YOut {
+    void *p;
+    int64_t ld;
+    int nr, mode;
+};
+
 // TAIL: the U panels come in two parts, the leading terms (up, TF = float)
 // and the trailing ones (u16, BF16), multiplied one after the other into the
 // same accumulators
@@ -252,7 +261,7 @@ __global__ void __launch_bounds__(C::THREADS) row_mrhs_kernel(
     const int32_t *__restrict__ u16_K, const int64_t *__restrict__ u16_colptr, const int32_t *__restrict__ u16_tidx,
     const __nv_bfloat16 *__restrict__ u16, const __nv_bfloat16 *__restrict__ Th,
     const __nv_bfloat16 *__restrict__ Tl, const __nv_bfloat16 *__restrict__ Xh, const __nv_bfloat16 *__restrict__ Xl,
-    double *__restrict__ Y) {
+    double *__restrict__ Y, YOut yo) {
     extern __shared__ __align__(16) unsigned char sm[];
     const int64_t rho = blockIdx.x;
     const int32_t r0 = leaf_begin[rho], mr = leaf_begin[rho + 1] - r0;
@@ -294,10 +303,30 @@ __global__ void __launch_bounds__(C::THREADS) row_mrhs_kernel(
             }
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < rows * MR; e += C::THREADS) {
-            float sacc = 0.0f;
-            for (int w = 0; w < C::KG; ++w) sacc += red[w * (16 * MT) * MR + e];
-            Y[(int64_t)(r0 + r0t) * MR + e] = (double)sacc;
+        if (yo.mode == 0) {
+            for (int e = threadIdx.x; e < rows * MR; e += C::THREADS) {
+                float sacc = 0.0f;
+                for (int w = 0; w < C::KG; ++w) sacc += red[w * (16 * MT) * MR + e];
+                Y[(int64_t)(r0 + r0t) * MR + e] = (double)sacc;
+            }
+        } else {
+            // the same sums through a [column][row] tile to the first yo.nr
+            // columns of [column][ld] (one coalesced row run per column)
+            constexpr int TP = 16 * MT + 1;
+            float *tile = red + C::KG * (16 * MT) * MR;
+            for (int e = threadIdx.x; e < rows * MR; e += C::THREADS) {
+                float sacc = 0.0f;
+                for (int w = 0; w < C::KG; ++w) sacc += red[w * (16 * MT) * MR + e];
+                tile[(e % MR) * TP + e / MR] = sacc;
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < yo.nr * rows; e += C::THREADS) {
+                const int col = e / rows, row = e - col * rows;
+                const float v = tile[col * TP + row];
+                const int64_t at = (int64_t)col * yo.ld + r0 + r0t + row;
+                if (yo.mode == 1) static_cast<float *>(yo.p)[at] = v;
+                else static_cast<double *>(yo.p)[at] = (double)v;
+            }
         }
         __syncthreads();
     }
@@ -901,7 +930,8 @@ void row_mrhs_tc(const hm_matrix *A, const TF *up, const __nv_bfloat16 *Th, cons
 
 
 template <int MT, class C> static int row_smem() {
-    const int st = C::STAGES * RpStage<MT, float, C>::BYTES, red = C::KG * 16 * MT * MR * 4;
+    // the stages, or the per-group sums and the [column][row] output tile
+    const int st = C::STAGES * RpStage<MT, float, C>::BYTES, red = C::KG * 16 * MT * MR * 4 + MR * (16 * MT + 1) * 4;
     return st > red ? st : red;
 }
 
@@ -938,9 +968,20 @@ static void col_pass(const BcpSet &S, const __nv_bfloat16 *Xh, const __nv_bfloat
     }
 }
 
+// Y [n][16] FP64 -> the first nr columns of [column][ld] (FP32 / FP64), after the tcgen05 row pass
+template <class TO>
+__global__ void y_to_cols_kernel(const double *__restrict__ Y, int64_t n, int nr, int64_t ld, TO *__restrict__ out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * nr; e += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(e / n);
+        const int64_t i = e - (int64_t)c * n;
+        out[(int64_t)c * ld + i] = (TO)Y[i * MR + c];
+    }
+}
+
 template <class TF>
 static void matvec_mrhs_impl(const hm_matrix *A, const TF *up, const float *X, double *Y, __nv_bfloat16 *Xh,
-                             __nv_bfloat16 *Xl, __nv_bfloat16 *Th, __nv_bfloat16 *Tl, float *part, cudaStream_t s) {
+                             __nv_bfloat16 *Xl, __nv_bfloat16 *Th, __nv_bfloat16 *Tl, float *part, YOut yo,
+                             cudaStream_t s) {
     const hm_tree *tr = A->tree;
     const int64_t n = tr->n;
     const bool f32 = sizeof(TF) == 4;
@@ -965,11 +1006,16 @@ static void matvec_mrhs_impl(const hm_matrix *A, const TF *up, const float *X, d
             tails ? U.colptr.as<int64_t>() : A->up_colptr.as<int64_t>(),
             tails ? U.tidx.as<int32_t>() : A->tidx.as<int32_t>(), u, A->ut16.off.as<int64_t>(),
             A->ut16.K.as<int32_t>(), A->ut16.colptr.as<int64_t>(), A->ut16.tidx.as<int32_t>(),
-            A->ut16.data.as<__nv_bfloat16>(), Th, Tl, Xh, Xl, Y);
+            A->ut16.data.as<__nv_bfloat16>(), Th, Tl, Xh, Xl, Y, yo);
         HM_LAUNCH_CHECK();
     };
     if (A->params.mrhs_tcgen05 && A->mrhs_err.p) {  // the measured tcgen05 / TMEM row pass (mrhs_tc.cu)
         row_mrhs_tc<TF>(A, up, Th, Tl, Xh, Xl, Y, A->mrhs_err.as<int>(), s);
+        if (yo.mode == 1)
+            y_to_cols_kernel<float><<<grid1d_m(n * yo.nr), 256, 0, s>>>(Y, n, yo.nr, yo.ld, static_cast<float *>(yo.p));
+        else if (yo.mode == 2)
+            y_to_cols_kernel<double><<<grid1d_m(n * yo.nr), 256, 0, s>>>(Y, n, yo.nr, yo.ld, static_cast<double *>(yo.p));
+        HM_LAUNCH_CHECK();
         return;
     }
     using C = RpDefault;
@@ -990,8 +1036,11 @@ static void matvec_mrhs_impl(const hm_matrix *A, const TF *up, const float *X, d
 // Y (Morton [n][16] FP64) = H X (Morton [n][16] FP32) with the FP32 near field
 // and FP32 (prec = HM_F32) or BF16 (HM_BF16) factors.  work: the part of the
 // workspace after X and Y (mrhs_work_floats - 48 n floats); mrhs_prepare must
-// have run for this precision.
-void matvec_mrhs_morton(const hm_matrix *A, hm_dtype prec, const float *X, double *Y, float *work, cudaStream_t s) {
+// have run for this precision.  With out (matvec_mrhs_morton_cols) the
+// product's first nr columns go straight to out as [column][ld] FP32
+// (out_f32) or FP64 instead of Y (Y is then scratch of the tcgen05 form).
+static void mrhs_morton(const hm_matrix *A, hm_dtype prec, const float *X, double *Y, float *work, YOut yo,
+                        cudaStream_t s) {
     if (!A->dense32.p) fail(HM_EINVAL, "the multi-RHS product needs the FP32 near-field copy");
     if (A->bcp.dtype != (int)prec) fail(HM_EINTERNAL, "multi-RHS panels not prepared for this precision");
     const int64_t n = A->tree->n, K = std::max<int64_t>(A->total_rank, 1);
@@ -1002,13 +1051,22 @@ void matvec_mrhs_morton(const hm_matrix *A, hm_dtype prec, const float *X, doubl
     float *part = reinterpret_cast<float *>(Tl + MR * K);
     if (prec == HM_F32) {
         if (!A->up32.p) fail(HM_EINVAL, "FP32 copies were not assembled");
-        matvec_mrhs_impl<float>(A, A->up32.as<float>(), X, Y, Xh, Xl, Th, Tl, part, s);
+        matvec_mrhs_impl<float>(A, A->up32.as<float>(), X, Y, Xh, Xl, Th, Tl, part, yo, s);
     } else if (prec == HM_BF16) {
         if (!A->upbf.p) fail(HM_EINVAL, "BF16 factors were not assembled");
-        matvec_mrhs_impl<__nv_bfloat16>(A, A->upbf.as<__nv_bfloat16>(), X, Y, Xh, Xl, Th, Tl, part, s);
+        matvec_mrhs_impl<__nv_bfloat16>(A, A->upbf.as<__nv_bfloat16>(), X, Y, Xh, Xl, Th, Tl, part, yo, s);
     } else {
         fail(HM_EINVAL, "the multi-RHS product runs on the FP32 / BF16 copies");
     }
+}
+
+void matvec_mrhs_morton(const hm_matrix *A, hm_dtype prec, const float *X, double *Y, float *work, cudaStream_t s) {
+    mrhs_morton(A, prec, X, Y, work, YOut{nullptr, 0, 0, 0}, s);
+}
+
+void matvec_mrhs_morton_cols(const hm_matrix *A, hm_dtype prec, const float *X, double *Y, void *out, bool out_f32,
+                             int nr, int64_t ld, float *work, cudaStream_t s) {
+    mrhs_morton(A, prec, X, Y, work, YOut{out, ld, nr, out_f32 ? 1 : 2}, s);
 }
 
 // y = alpha H x + beta y for up to 16 right-hand sides [nrhs][n] (original

@@ -80,11 +80,25 @@ def test_measured_alu_peaks_are_the_denominators():
 def test_multi_rhs_product_bytes():
     w = _work()
     K = 2.0 * 10
-    # 16 right-hand sides: X / t rows as BF16 pairs (64 B), Y rows in FP64 (128 B)
-    assert w["row_mrhs_kernel.f32"] == ("hbm", 4.0 * 1800 + 64.0 * (40 + K) + 128.0 * 40, "byte")
-    assert w["row_mrhs_kernel.bf16"][1] == 4.0 * 800 + 2.0 * 1000 + 64.0 * (40 + K) + 128.0 * 40
+    # 16 right-hand sides: X / t rows as BF16 pairs (64 B), output rows into the FP32 Krylov block (64 B)
+    assert w["row_mrhs_kernel.f32"] == ("hbm", 4.0 * 1800 + 64.0 * (40 + K) + 64.0 * 40, "byte")
+    assert w["row_mrhs_kernel.bf16"][1] == 4.0 * 800 + 2.0 * 1000 + 64.0 * (40 + K) + 64.0 * 40
     assert w["col_bcp_kernel.f32"][1] == 4.0 * 1500 + 64.0 * (40 + K)
     assert w["col_bcp_kernel.bf16"][1] == 2.0 * 1500 + 64.0 * (40 + K)
+
+
+def test_multi_rhs_product_bytes_with_bf16_tails():
+    # FP32 factors with BF16 tails: 400 of the 1000 U entries and 600 of the
+    # 1500 W entries are trailing terms (2 bytes); 8 of the 20 terms of t
+    mi = {"u_entries": 1000, "lr_entries": 2500, "dense_entries": 800, "mean_rank": 2.0, "aca_entries": 3000,
+          "u_tail_entries": 400, "lr_tail_entries": 1000, "factor_tail_terms": 8}
+    ti = {"n_adm": 10, "n_clusters": 15}
+    leaves = np.array([[0, 20, 20, 40], [20, 40, 0, 20]], dtype=np.int64)
+    w = bench.algorithmic_work(mi, ti, leaves, 40)
+    K = 2.0 * 10
+    assert w["row_mrhs_kernel.f32"][1] == 4.0 * (800 + 600) + 2.0 * 400 + 64.0 * (40 + K) + 64.0 * 40
+    assert w["col_bcp_kernel.f32"][1] == 4.0 * 900 + 64.0 * (40 + K - 8)
+    assert w["col_bcp_kernel.bf16"][1] == 2.0 * 600 + 64.0 * (40 + 8)
 
 
 def test_dominant_kernel_is_the_longest_with_known_work():
