@@ -1013,8 +1013,12 @@ def run_solve16(torch, hm, level=6):
                            precond=int(W["precond"]), batched=1)
         b.record()
         torch.cuda.synchronize()
+        mi, ti = hm.hm_matrix_get_info(A), hm.hm_tree_get_info(tree)
         out.update(step_s=a.elapsed_time(b) / 1e3, iters=info.iters, refine_steps=info.refine_steps,
-                   rel_resid=info.rel_resid)
+                   rel_resid=info.rel_resid, dense_entries=mi["dense_entries"], u_entries=mi["u_entries"],
+                   lr_entries=mi["lr_entries"], total_rank=round(mi["mean_rank"] * ti["n_adm"]),
+                   row_mrhs_bytes=algorithmic_work(mi, ti, hm.hm_tree_get_leaves(tree, True).cpu().numpy()
+                                                   .astype(np.int64), n)["row_mrhs_kernel.f32"][1])
         hm.hm_free(A)
         hm.hm_free(tree)
     return out
