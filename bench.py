@@ -78,16 +78,15 @@ DF_FLOPS_PER_TERM = 15
 # DRAM traffic per launch from an ncu capture, valid while the kernel's source
 # file is unchanged (sha256 of the file at capture time); null otherwise.
 TRAFFIC = {
-    # ncu capture at the level-6 bumped sphere (leaf 128, 81,920 panels): 1.8138 GB per launch, 1.0395 x its
-    # algorithmic bytes (1.7448 GB); scaled to a level-8 launch by the algorithmic bytes (37.87 GB), traffic
-    # growing in proportion with the matrix (sha of the file after changes to the block-column panel build
-    # and a kernel variant for BF16 tails, off by default: the default instantiation's code path is the
-    # captured one)
+    # ncu capture in the level-6 step of the large workload (unit icosphere level 6, leaf 128, 81,920 panels;
+    # the row pass writing into the FP32 Krylov block): 1.7621 GB per launch, 1.0384 x its algorithmic
+    # bytes (1.6969 GB); scaled to a level-8 launch by the algorithmic bytes (37.79 GB), traffic growing in
+    # proportion with the matrix
     "row_mrhs_kernel.f32": {"source": "paper_1806_11558_gb300/csrc/mrhs.cu",
-                            "sha256": "b47e3da3e266f9ff1a0add9660027d4e3b6737971b3e0ce91aee69803643d22c",
-                            "bytes_per_launch": 39372871231,
+                            "sha256": "6e63b5b5cddbf3da4d27d28d467b3f7cd72406caacc4cc7f767a83e4d9ea43c5",
+                            "bytes_per_launch": 39242683441,
                             "workload": "large",
-                            "profile": "profiles/mrhs_kernels_bumped6.md"},
+                            "profile": "profiles/mrhs_kernels_ico6_solve.md"},
     "row_kernel.f64": {"source": "paper_1806_11558_gb300/csrc/mv_kernels.cuh",
                        "sha256": "317d8d2539db41cb43c4abddd08fe283fb2cbbf21bc763087ebc67cdb6960454",
                        "bytes_per_launch": 15113751808 + 5691392,
