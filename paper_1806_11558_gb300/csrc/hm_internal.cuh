@@ -413,5 +413,6 @@ struct hm_matrix {
     hm::DBuf bj_begin;  // [n_bj + 1] int32: first row of each block
     hm::DBuf bj_leaf;   // [n_bj + 1] int32: first leaf cluster of each block
     int64_t n_bj = 0;
+    int bj_mmax = 0;    // rows of the largest block
     hm_matrix_info info{};
 };

@@ -447,13 +447,13 @@ __global__ void __launch_bounds__(BJC_THREADS) bj_apply_cols_kernel(const int32_
     const int32_t r0 = begin[r], m = begin[r + 1] - r0;
     const int c0 = blockIdx.y * BJ_NC, nc = min(BJ_NC, cols - c0);
     const TD *D = bj + bj_off[r];
-    for (int e = threadIdx.x; e < BJ_NC * m; e += BJC_THREADS) {
+    for (int e = threadIdx.x; e < BJ_NC * m; e += blockDim.x) {
         const int c = e / m, j = e - c * m;
         s_v[j][c] = c < nc ? (TD)v[(int64_t)(c0 + c) * n + r0 + j] : (TD)0;
     }
     __syncthreads();
     const int64_t si = trans ? m : 1, sj = trans ? 1 : m;
-    for (int i = threadIdx.x; i < m; i += BJC_THREADS) {
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
         TD acc[BJ_NC];
 #pragma unroll
         for (int c = 0; c < BJ_NC; ++c) acc[c] = 0;
@@ -467,6 +467,13 @@ __global__ void __launch_bounds__(BJC_THREADS) bj_apply_cols_kernel(const int32_
         for (int c = 0; c < BJ_NC; ++c)
             if (c < nc) z[(int64_t)(c0 + c) * n + r0 + i] = (TVec)acc[c];
     }
+}
+
+// threads of a multi-column apply: one per row of the largest block (rounded
+// up to a warp), so that no warp of a CTA sits out the product
+static unsigned bjc_threads(const hm_matrix *A) {
+    const int t = (std::max(A->bj_mmax, 1) + 31) / 32 * 32;
+    return (unsigned)std::min(t, BJC_THREADS);
 }
 
 __global__ void bj_round_kernel(const double *a, int64_t n, float *o) {
@@ -523,6 +530,7 @@ void bj_setup(const hm_matrix *Ac, cudaStream_t s) {
     A->bj32.alloc(sizeof(float) * std::max<int64_t>(tot, 1));
     int mmax = 0;
     for (int64_t r = 0; r < nb; ++r) mmax = std::max(mmax, begin[r + 1] - begin[r]);
+    A->bj_mmax = mmax;
     {
         Trace trace("bj_invert_kernel", s);
         const int msm = std::min(mmax, BJ_SMEM_M);
@@ -551,11 +559,11 @@ void bj_apply_cols(const hm_matrix *A, const double *v, double *z, int cols, boo
     if (cols > 1) {
         const dim3 grid((unsigned)A->n_bj, (unsigned)((cols + BJ_NC - 1) / BJ_NC));
         if (low)
-            bj_apply_cols_kernel<float, double><<<grid, BJC_THREADS, 0, s>>>(
+            bj_apply_cols_kernel<float, double><<<grid, bjc_threads(A), 0, s>>>(
                 A->bj_begin.as<int32_t>(), A->bj_off.as<int64_t>(), A->bj32.as<float>(), v, z, trans ? 1 : 0,
                 A->tree->n, cols);
         else
-            bj_apply_cols_kernel<double, double><<<grid, BJC_THREADS, 0, s>>>(
+            bj_apply_cols_kernel<double, double><<<grid, bjc_threads(A), 0, s>>>(
                 A->bj_begin.as<int32_t>(), A->bj_off.as<int64_t>(), A->bj.as<double>(), v, z, trans ? 1 : 0,
                 A->tree->n, cols);
         HM_LAUNCH_CHECK();
@@ -576,7 +584,7 @@ void bj_apply_cols(const hm_matrix *A, const double *v, double *z, int cols, boo
 void bj_apply_cols_f32(const hm_matrix *A, const float *v, float *z, int cols, cudaStream_t s) {
     Trace trace("bj_apply_kernel.f32", s);
     const dim3 grid((unsigned)A->n_bj, (unsigned)((cols + BJ_NC - 1) / BJ_NC));
-    bj_apply_cols_kernel<float, float><<<grid, BJC_THREADS, 0, s>>>(A->bj_begin.as<int32_t>(), A->bj_off.as<int64_t>(),
+    bj_apply_cols_kernel<float, float><<<grid, bjc_threads(A), 0, s>>>(A->bj_begin.as<int32_t>(), A->bj_off.as<int64_t>(),
                                                                    A->bj32.as<float>(), v, z, 0, A->tree->n, cols);
     HM_LAUNCH_CHECK();
 }
