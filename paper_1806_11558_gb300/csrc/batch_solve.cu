@@ -27,8 +27,8 @@ namespace hm {
 void matvec_morton(const hm_matrix *A, hm_dtype prec, const MatvecWork &w, cudaStream_t s, bool trans);
 int64_t matvec_work_doubles(const hm_matrix *A);
 MatvecWork matvec_work_at(const hm_matrix *A, double *base);
-void matvec_mrhs_morton_cols(const hm_matrix *A, hm_dtype prec, const float *X, double *Y, void *out, bool out_f32,
-                             int nr, int64_t ld, float *work, cudaStream_t s);
+void matvec_mrhs_cols(const hm_matrix *A, hm_dtype prec, const void *x, bool x_f32, int nr, double *Y, void *out,
+                      bool out_f32, float *work, cudaStream_t s);
 int64_t mrhs_work_floats(const hm_matrix *A);
 void mrhs_prepare(const hm_matrix *A, hm_dtype prec, cudaStream_t s);
 void bj_setup(const hm_matrix *A, cudaStream_t s);
@@ -342,17 +342,6 @@ __global__ void bset_g0_kernel(int S, int m, const int *__restrict__ mask, const
     gs[0] = sqrt(nrm2[s]);
 }
 
-// [R][n] FP64 / FP32 -> [n][16] blocks of the tensor-core product (the
-// product writes its result straight back as [R][n])
-template <class TI>
-__global__ void to_block_kernel(const TI *__restrict__ v, int64_t n, int R, float *__restrict__ X) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * BMR; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = e / BMR;
-        const int r = (int)(e - i * BMR);
-        X[e] = r < R ? (float)v[(int64_t)r * n + i] : 0.0f;
-    }
-}
-
 // ---------------------------------------------------------------------------
 // host
 // ---------------------------------------------------------------------------
@@ -494,14 +483,14 @@ struct Batch {
             }
             return;
         }
+        // the workspace of the 16-column product: [n][16] FP32 (unused here), Y, then its work
         float *X = mvf.as<float>();
         double *Y = reinterpret_cast<double *>(X + (int64_t)BMR * n);
         float *work = X + 3 * (int64_t)BMR * n;
         for (int r0 = 0; r0 < R; r0 += BMR) {
             const int nr = std::min(BMR, R - r0);
-            to_block_kernel<TI><<<gx(n * BMR), 256, 0, s>>>(x + (int64_t)r0 * n, n, nr, X);
-            HM_LAUNCH_CHECK();
-            matvec_mrhs_morton_cols(A, prec, X, Y, yv + (int64_t)r0 * n, sizeof(TO) == 4, nr, n, work, s);
+            matvec_mrhs_cols(A, prec, x + (int64_t)r0 * n, sizeof(TI) == 4, nr, Y, yv + (int64_t)r0 * n,
+                             sizeof(TO) == 4, work, s);
         }
     }
     void bj(const double *v, double *z, bool low, cudaStream_t s) { bj_apply_cols(A, v, z, R, false, low, s); }

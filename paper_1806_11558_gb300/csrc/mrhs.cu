@@ -343,6 +343,34 @@ __global__ void split_rows_kernel(const float *__restrict__ X, int64_t n, __nv_b
     }
 }
 
+// The same pairs straight from a block of vectors x [nr][ldx] (FP32 or FP64,
+// Morton order): X[m][r] = (float) x[r][m] (0 for r >= nr), split as above,
+// 64 rows per step transposed through shared memory (read along m, written
+// along r)
+constexpr int GS_ROWS = 64;
+template <class TI>
+__global__ void __launch_bounds__(256) gather_split_kernel(const TI *__restrict__ x, int64_t n, int nr, int64_t ldx,
+                                                           __nv_bfloat16 *__restrict__ Xh,
+                                                           __nv_bfloat16 *__restrict__ Xl) {
+    __shared__ float s_x[MR][GS_ROWS + 1];
+    for (int64_t i0 = blockIdx.x * (int64_t)GS_ROWS; i0 < n; i0 += (int64_t)gridDim.x * GS_ROWS) {
+        const int rows = (int)((n - i0) < GS_ROWS ? (n - i0) : (int64_t)GS_ROWS);
+        __syncthreads();
+        for (int e = threadIdx.x; e < MR * GS_ROWS; e += blockDim.x) {
+            const int r = e / GS_ROWS, i = e - r * GS_ROWS;
+            s_x[r][i] = (r < nr && i < rows) ? (float)x[(int64_t)r * ldx + i0 + i] : 0.0f;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < rows * MR; e += blockDim.x) {
+            const int i = e / MR, r = e - i * MR;
+            float h, l;
+            split_bf16(s_x[r][i], h, l);
+            Xh[(i0 + i) * MR + r] = __float2bfloat16_rn(h);
+            Xl[(i0 + i) * MR + r] = __float2bfloat16_rn(l);
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // col_bcp_kernel: t_b = X_sigma^T W_b for every block, straight from the
 // panels grouped by block column cluster (no partial sums): one CTA per tile
@@ -987,8 +1015,10 @@ static void matvec_mrhs_impl(const hm_matrix *A, const TF *up, const float *X, d
     const bool f32 = sizeof(TF) == 4;
     // FP32 factors with BF16 tails: leading terms from the FP32 sets, trailing terms from the BF16 ones
     const bool tails = f32 && A->bcp16.dtype == HM_BF16 && A->ut16.data.p;
-    split_rows_kernel<<<grid1d_m(n * MR), 256, 0, s>>>(X, n * MR, Xh, Xl);
-    HM_LAUNCH_CHECK();
+    if (X) {  // else the pairs are in place already (matvec_mrhs_cols)
+        split_rows_kernel<<<grid1d_m(n * MR), 256, 0, s>>>(X, n * MR, Xh, Xl);
+        HM_LAUNCH_CHECK();
+    }
     if (tr->n_adm > 0) {
         col_pass<TF>(A->bcp, Xh, Xl, Th, Tl, part, s);
         if (tails) col_pass<__nv_bfloat16>(A->bcp16, Xh, Xl, Th, Tl, part, s);
@@ -1064,9 +1094,22 @@ void matvec_mrhs_morton(const hm_matrix *A, hm_dtype prec, const float *X, doubl
     mrhs_morton(A, prec, X, Y, work, YOut{nullptr, 0, 0, 0}, s);
 }
 
-void matvec_mrhs_morton_cols(const hm_matrix *A, hm_dtype prec, const float *X, double *Y, void *out, bool out_f32,
-                             int nr, int64_t ld, float *work, cudaStream_t s) {
-    mrhs_morton(A, prec, X, Y, work, YOut{out, ld, nr, out_f32 ? 1 : 2}, s);
+// the product of a block of nr <= 16 vectors x [nr][n] (FP32 when x_f32, else
+// FP64; Morton order) into out [nr][n] (FP32 when out_f32, else FP64), the
+// BF16 pairs of x made in one pass (no [n][16] FP32 copy); Y: [n][16] FP64
+// scratch of the tcgen05 form; work as for matvec_mrhs_morton
+void matvec_mrhs_cols(const hm_matrix *A, hm_dtype prec, const void *x, bool x_f32, int nr, double *Y, void *out,
+                      bool out_f32, float *work, cudaStream_t s) {
+    const int64_t n = A->tree->n;
+    __nv_bfloat16 *Xh = reinterpret_cast<__nv_bfloat16 *>(work);
+    __nv_bfloat16 *Xl = Xh + MR * n;
+    const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + GS_ROWS - 1) / GS_ROWS, 65535));
+    if (x_f32)
+        gather_split_kernel<float><<<g, 256, 0, s>>>(static_cast<const float *>(x), n, nr, n, Xh, Xl);
+    else
+        gather_split_kernel<double><<<g, 256, 0, s>>>(static_cast<const double *>(x), n, nr, n, Xh, Xl);
+    HM_LAUNCH_CHECK();
+    mrhs_morton(A, prec, nullptr, Y, work, YOut{out, n, nr, out_f32 ? 1 : 2}, s);
 }
 
 // y = alpha H x + beta y for up to 16 right-hand sides [nrhs][n] (original
