@@ -81,10 +81,10 @@ TRAFFIC = {
     # ncu capture in the level-6 step of the large workload (unit icosphere level 6, leaf 128, 81,920 panels;
     # the row pass writing into the FP32 Krylov block): 1.7621 GB per launch, 1.0384 x its algorithmic
     # bytes (1.6969 GB); scaled to a level-8 launch by the algorithmic bytes (37.79 GB), traffic growing in
-    # proportion with the matrix (sha of the file after adding the input gather of the batched product, a
-    # separate kernel: row_mrhs_kernel's code is the captured one)
+    # proportion with the matrix (sha of the file after adding the input gather of the batched product and
+    # unrolling the partial sums of split panels, separate kernels: row_mrhs_kernel's code is the captured one)
     "row_mrhs_kernel.f32": {"source": "paper_1806_11558_gb300/csrc/mrhs.cu",
-                            "sha256": "9304550aa4796c40767c795a253450e79655172a63da3e874bd9ff2ae426723b",
+                            "sha256": "4ee0899318fd414d930ad2ed2b4ea5ee980fbe587824bd3c25fc26cfe9488c7b",
                             "bytes_per_launch": 39242683441,
                             "workload": "large",
                             "profile": "profiles/mrhs_kernels_ico6_solve.md"},

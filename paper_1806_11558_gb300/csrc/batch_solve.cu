@@ -148,6 +148,8 @@ __global__ void bdots_final_kernel(const int64_t *__restrict__ iptr, int S, int 
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < S * nv; e += gridDim.x * blockDim.x) {
         const int s = e / nv, l = e - (e / nv) * nv;
         double t = 0.0;
+        // eight partials' loads in flight, added in item order
+#pragma unroll 8
         for (int64_t k = iptr[s]; k < iptr[s + 1]; ++k) t += part[k * nv + l];
         out[(int64_t)s * ld + l] = accumulate ? out[(int64_t)s * ld + l] + t : t;
     }

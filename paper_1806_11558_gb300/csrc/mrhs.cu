@@ -565,6 +565,8 @@ __global__ void bcp_reduce_kernel(const int32_t *__restrict__ red, const int32_t
         const int32_t ti = tidx[col0[grp] + n0 + cl];
         if (ti < 0) continue;
         float acc = 0.0f;
+        // eight partials' loads in flight, added in row order
+#pragma unroll 8
         for (int k = 0; k < ns; ++k) acc += part[((int64_t)(s0 + k) * CM_COLS + cl) * MR + r];
         store_t_pair(Th, Tl, ti, r, acc);
     }
