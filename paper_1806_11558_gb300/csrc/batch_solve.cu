@@ -168,6 +168,24 @@ __global__ void bsub_kernel(const Item *__restrict__ items, const TV *__restrict
     for (int l = threadIdx.x; l < nv; l += blockDim.x) s_h[l] = (TV)hs[l];
     __syncthreads();
     TV *wc = w + (int64_t)it.col * n;
+    constexpr int EPT = BITEM / 256;  // elements per thread of a full item
+    if (blockDim.x == 256 && it.i1 - it.i0 == BITEM) {
+        // the thread's elements in registers, the vectors one after the other:
+        // EPT loads in flight per vector, each element's sum in the same order
+        const TV *vb = V + (int64_t)it.col * n + it.i0 + threadIdx.x;
+        TV a[EPT];
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) a[q] = wc[it.i0 + threadIdx.x + 256 * q];
+        for (int l = 0; l < nv; ++l) {
+            const TV *vl = vb + (int64_t)l * vstride;
+            const TV hl = s_h[l];
+#pragma unroll
+            for (int q = 0; q < EPT; ++q) a[q] -= vl[256 * q] * hl;
+        }
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) wc[it.i0 + threadIdx.x + 256 * q] = a[q];
+        return;
+    }
     for (int64_t i = it.i0 + threadIdx.x; i < it.i1; i += blockDim.x) {
         TV a = wc[i];
         // eight vectors' loads in flight (the sum order is unchanged; 16 deep
